@@ -1,0 +1,755 @@
+/*
+ * Plain FP64 CPU oracle for the matrix-free stochastic-reconfiguration (SR)
+ * hot path of a correlator-product-state x pfaffian wavefunction
+ * (Neuscamman, Umrigar, Chan, "Optimizing large parameter sets in variational
+ * quantum Monte Carlo", arXiv:1108.0900).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously-correct
+ * reference the CUDA library is checked against.  Only the test suite, the
+ * package smoke check and the CPU-baseline leg of the benchmark may load it;
+ * the product path never calls it and shares no code with it.
+ *
+ * Everything is written for clarity, not speed: amplitudes are recomputed
+ * from scratch (a fresh pfaffian for every configuration), derivative-ratio
+ * vectors are dense of length n_v, and S is applied exactly as written in
+ * Eq. 7.  Where the paper is silent the readings are:
+ *   - spin orbital p = sigma * n_sites + site; occupied lists are ascending;
+ *   - correlator local state idx_c = sum_j 4^j (n_{s_j,up} + 2 n_{s_j,dn});
+ *   - Hubbard H = -sum_bonds t (c+_i c_j + c+_j c_i) (both spins)
+ *                 + U sum_i n_iup n_idn, bond list taken as given;
+ *   - Metropolis proposal: the a-th occupied orbital (ascending) moves to the
+ *     k-th empty orbital of the same spin (ascending), a and k uniform from
+ *     Philox4x32-10; accept iff u < |Psi'/Psi|^2;
+ *   - S is the covariance form obtained by eliminating x_0 from Eq. 2 with
+ *     O_0 = 1; all sample means use weight 1/n_s; shift eps is absolute.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "oracle.h"
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11, "Parallel random        */
+/* numbers: as easy as 1, 2, 3").  Written from the published definition.   */
+/* ------------------------------------------------------------------------ */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Dense linear algebra on small matrices                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Pfaffian of an antisymmetric n x n matrix (row-major, destroyed), by the
+ * Parlett-Reid reduction with pivoting described by Wimmer (the pfaffian
+ * reference of Sec. II.C).  Returns sign in *sign and log|Pf| in *logabs;
+ * a singular matrix gives sign 0. */
+void orc_pfaffian(int n, double* A, double* logabs, int* sign)
+{
+    *logabs = 0.0;
+    *sign = 1;
+    if (n % 2) { *sign = 0; return; }
+    for (int k = 0; k < n - 1; k += 2) {
+        /* bring the largest entry of column k (below the diagonal) to k+1 */
+        int kp = k + 1;
+        double best = fabs(A[(k + 1) * n + k]);
+        for (int i = k + 2; i < n; ++i) {
+            if (fabs(A[i * n + k]) > best) { best = fabs(A[i * n + k]); kp = i; }
+        }
+        if (kp != k + 1) {
+            for (int j = 0; j < n; ++j) {
+                double t = A[(k + 1) * n + j]; A[(k + 1) * n + j] = A[kp * n + j]; A[kp * n + j] = t;
+            }
+            for (int i = 0; i < n; ++i) {
+                double t = A[i * n + k + 1]; A[i * n + k + 1] = A[i * n + kp]; A[i * n + kp] = t;
+            }
+            *sign = -*sign;
+        }
+        double piv = A[k * n + k + 1];
+        if (piv == 0.0) { *sign = 0; *logabs = -INFINITY; return; }
+        if (piv < 0) *sign = -*sign;
+        *logabs += log(fabs(piv));
+        /* congruence that clears row/column k beyond k+1:
+           A[i][j] += tau_i A[j][k+1] - A[i][k+1] tau_j, tau_i = A[k][i] / A[k][k+1] */
+        for (int i = k + 2; i < n; ++i) {
+            double tau_i = A[k * n + i] / piv;
+            for (int j = k + 2; j < n; ++j) {
+                double tau_j = A[k * n + j] / piv;
+                A[i * n + j] += tau_i * A[j * n + k + 1] - A[i * n + k + 1] * tau_j;
+            }
+        }
+        /* the trailing block stays antisymmetric; k+2.. rows of column k+1 are
+           not needed below because row k now has a single nonzero at k+1 */
+    }
+}
+
+/* Inverse of a general n x n matrix (row-major) by Gauss-Jordan elimination
+ * with partial pivoting.  Returns 0 on success, -1 if singular. */
+int orc_inverse(int n, const double* A_in, double* X)
+{
+    double* A = (double*)malloc(sizeof(double) * n * n);
+    memcpy(A, A_in, sizeof(double) * n * n);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) X[i * n + j] = (i == j) ? 1.0 : 0.0;
+    for (int c = 0; c < n; ++c) {
+        int pr = c;
+        for (int r = c + 1; r < n; ++r)
+            if (fabs(A[r * n + c]) > fabs(A[pr * n + c])) pr = r;
+        if (A[pr * n + c] == 0.0) { free(A); return -1; }
+        if (pr != c) {
+            for (int j = 0; j < n; ++j) {
+                double t = A[c * n + j]; A[c * n + j] = A[pr * n + j]; A[pr * n + j] = t;
+                t = X[c * n + j]; X[c * n + j] = X[pr * n + j]; X[pr * n + j] = t;
+            }
+        }
+        double d = A[c * n + c];
+        for (int j = 0; j < n; ++j) { A[c * n + j] /= d; X[c * n + j] /= d; }
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            double m = A[r * n + c];
+            if (m == 0.0) continue;
+            for (int j = 0; j < n; ++j) {
+                A[r * n + j] -= m * A[c * n + j];
+                X[r * n + j] -= m * X[c * n + j];
+            }
+        }
+    }
+    free(A);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Parameter layout and wavefunction (Eq. 11)                               */
+/* ------------------------------------------------------------------------ */
+
+static int n_orb_M(const orc_problem* P) { return 2 * P->n_sites; }
+
+int64_t orc_n_corr_params(const orc_problem* P)
+{
+    int64_t n = 0;
+    for (int c = 0; c < P->n_corr; ++c) {
+        int m = P->corr_ptr[c + 1] - P->corr_ptr[c];
+        n += (int64_t)1 << (2 * m);
+    }
+    return n;
+}
+
+int64_t orc_n_params(const orc_problem* P)
+{
+    int M = n_orb_M(P);
+    return orc_n_corr_params(P) + (int64_t)M * (M - 1) / 2;
+}
+
+/* index of f_pq (p < q) in the row-major upper triangle */
+static int64_t pf_index(int M, int p, int q)
+{
+    return (int64_t)p * M - (int64_t)p * (p + 1) / 2 + (q - p - 1);
+}
+
+static void occ_to_bits(const orc_problem* P, const uint8_t* occ, uint8_t* bits)
+{
+    int M = n_orb_M(P), N = P->n_up + P->n_dn;
+    memset(bits, 0, M);
+    for (int a = 0; a < N; ++a) bits[occ[a]] = 1;
+}
+
+/* local state of correlator c: sum_j 4^j (n_{s_j up} + 2 n_{s_j dn}) */
+static int64_t corr_state(const orc_problem* P, const uint8_t* bits, int c)
+{
+    int64_t idx = 0, w = 1;
+    for (int j = P->corr_ptr[c]; j < P->corr_ptr[c + 1]; ++j) {
+        int s = P->corr_sites[j];
+        idx += w * (bits[s] + 2 * bits[P->n_sites + s]);
+        w *= 4;
+    }
+    return idx;
+}
+
+int64_t orc_corr_state(const orc_problem* P, const uint8_t* occ, int c)
+{
+    uint8_t bits[512];
+    occ_to_bits(P, occ, bits);
+    return corr_state(P, bits, c);
+}
+
+static void corr_offsets(const orc_problem* P, int64_t* off)
+{
+    off[0] = 0;
+    for (int c = 0; c < P->n_corr; ++c) {
+        int m = P->corr_ptr[c + 1] - P->corr_ptr[c];
+        off[c + 1] = off[c] + ((int64_t)1 << (2 * m));
+    }
+}
+
+/* A = F[occ, occ] with F_pq = f_pq (p < q), F_qp = -f_pq, F_pp = 0 */
+static void pairing_submatrix(const orc_problem* P, const uint8_t* occ, double* A)
+{
+    int M = n_orb_M(P), N = P->n_up + P->n_dn;
+    for (int a = 0; a < N; ++a)
+        for (int b = 0; b < N; ++b) {
+            int p = occ[a], q = occ[b];
+            double v = 0.0;
+            if (p < q) v = P->f[pf_index(M, p, q)];
+            else if (p > q) v = -P->f[pf_index(M, q, p)];
+            A[a * N + b] = v;
+        }
+}
+
+/* log|Psi_n| and sign of Psi_n = prod_c C_c[idx_c(n)] * Pf(F[occ, occ])
+ * (Eq. 11, with the correlators acting diagonally on the pfaffian). */
+void orc_log_psi(const orc_problem* P, const uint8_t* occ, double* logabs, int* sign)
+{
+    int N = P->n_up + P->n_dn;
+    uint8_t bits[512];
+    occ_to_bits(P, occ, bits);
+    int64_t* off = (int64_t*)malloc(sizeof(int64_t) * (P->n_corr + 1));
+    corr_offsets(P, off);
+    double la = 0.0;
+    int sg = 1;
+    for (int c = 0; c < P->n_corr; ++c) {
+        double v = P->C[off[c] + corr_state(P, bits, c)];
+        if (v == 0.0) { sg = 0; la = -INFINITY; break; }
+        if (v < 0) sg = -sg;
+        la += log(fabs(v));
+    }
+    free(off);
+    double* A = (double*)malloc(sizeof(double) * N * N);
+    pairing_submatrix(P, occ, A);
+    double lp;
+    int sp;
+    orc_pfaffian(N, A, &lp, &sp);
+    free(A);
+    *logabs = la + lp;
+    *sign = sg * sp;
+}
+
+/* Dense derivative-ratio vector O_k(n) = (dPsi_n/dalpha_k)/Psi_n (Eq. 3):
+ * correlator part 1/C_c[idx_c] at its own parameter; pairing part
+ * (A^{-1})_{b a} for f_pq with p = occ[a] < q = occ[b] (d ln Pf(A)/dA_ab).
+ * O has length n_v.  Returns -1 if A is singular. */
+int orc_logderiv(const orc_problem* P, const uint8_t* occ, double* O)
+{
+    int M = n_orb_M(P), N = P->n_up + P->n_dn;
+    int64_t ncp = orc_n_corr_params(P), nv = orc_n_params(P);
+    memset(O, 0, sizeof(double) * nv);
+    uint8_t bits[512];
+    occ_to_bits(P, occ, bits);
+    int64_t* off = (int64_t*)malloc(sizeof(int64_t) * (P->n_corr + 1));
+    corr_offsets(P, off);
+    for (int c = 0; c < P->n_corr; ++c) {
+        int64_t k = off[c] + corr_state(P, bits, c);
+        O[k] += 1.0 / P->C[k];
+    }
+    free(off);
+    double* A = (double*)malloc(sizeof(double) * N * N);
+    double* X = (double*)malloc(sizeof(double) * N * N);
+    pairing_submatrix(P, occ, A);
+    int rc = orc_inverse(N, A, X);
+    if (rc == 0) {
+        for (int a = 0; a < N; ++a)
+            for (int b = a + 1; b < N; ++b)
+                O[ncp + pf_index(M, occ[a], occ[b])] = X[b * N + a];
+    }
+    free(A);
+    free(X);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Second quantisation helpers (explicit Jordan-Wigner signs)               */
+/* ------------------------------------------------------------------------ */
+
+/* apply a_q then a+_p to the ascending-ordered determinant `bits`; returns
+ * the sign (0 if the result vanishes) and writes the new occupation. */
+static int hop_sign(int M, const uint8_t* bits, int p, int q, uint8_t* out)
+{
+    if (!bits[q]) return 0;
+    memcpy(out, bits, M);
+    int s = 1;
+    for (int o = 0; o < q; ++o) if (out[o]) s = -s;
+    out[q] = 0;
+    if (out[p]) return 0;
+    for (int o = 0; o < p; ++o) if (out[o]) s = -s;
+    out[p] = 1;
+    return s;
+}
+
+static void bits_to_occ(int M, const uint8_t* bits, uint8_t* occ)
+{
+    int a = 0;
+    for (int o = 0; o < M; ++o) if (bits[o]) occ[a++] = (uint8_t)o;
+}
+
+/* Psi_{n'} / Psi_n from two fresh amplitude evaluations */
+static double amp_ratio(const orc_problem* P, const uint8_t* occ_new, double la0, int s0)
+{
+    double la;
+    int s;
+    orc_log_psi(P, occ_new, &la, &s);
+    if (s == 0) return 0.0;
+    return (double)(s * s0) * exp(la - la0);
+}
+
+/* Local energy E_L(n) = sum_n' <n|H|n'> Psi_n'/Psi_n (the quantity implied by
+ * <Psi^i|H|Psi> in Eq. 2), Hubbard model, every Psi_n' recomputed from
+ * scratch and every matrix element signed explicitly. */
+double orc_local_energy_hubbard(const orc_problem* P, const uint8_t* occ)
+{
+    int M = n_orb_M(P), N = P->n_up + P->n_dn, ns = P->n_sites;
+    uint8_t bits[512], nb[512], occn[256];
+    occ_to_bits(P, occ, bits);
+    double la0;
+    int s0;
+    orc_log_psi(P, occ, &la0, &s0);
+    double E = 0.0;
+    for (int i = 0; i < ns; ++i) E += P->U * bits[i] * bits[ns + i];
+    for (int b = 0; b < P->n_bonds; ++b) {
+        int i = P->bonds[2 * b], j = P->bonds[2 * b + 1];
+        double t = P->bond_t[b];
+        if (i == j) continue;
+        for (int sg = 0; sg < 2; ++sg) {
+            for (int dir = 0; dir < 2; ++dir) {
+                /* term -t a+_x a_y; <n| a+_x a_y |n'> is nonzero for
+                   n' = n with the electron moved x -> y */
+                int x = sg * ns + (dir ? j : i);
+                int y = sg * ns + (dir ? i : j);
+                if (!bits[x] || bits[y]) continue;
+                memcpy(nb, bits, M);
+                nb[x] = 0;
+                nb[y] = 1;
+                uint8_t back[512];
+                int me = hop_sign(M, nb, x, y, back); /* <n|a+_x a_y|n'> */
+                if (me == 0) continue;
+                bits_to_occ(M, nb, occn);
+                E += -t * me * amp_ratio(P, occn, la0, s0);
+            }
+        }
+    }
+    (void)N;
+    return E;
+}
+
+/* One- and two-electron matrix element <n|H|n'> for the ab initio
+ * Hamiltonian H = sum_{pq,s} h_pq a+_ps a_qs
+ *               + 1/2 sum_{pqrs,st} (pq|rs) a+_ps a+_rt a_st a_qs,
+ * (pq|rs) = sum_mu L^mu_pq L^mu_rs  (Eq. 9 with R = L).
+ * Evaluated by applying every operator string to |n'> with explicit signs:
+ * slow, only used on small tests. */
+static double eri(const orc_problem* P, int p, int q, int r, int s)
+{
+    int n = P->n_sites;
+    double v = 0.0;
+    for (int mu = 0; mu < P->n_chol; ++mu)
+        v += P->chol[(size_t)mu * n * n + p * n + q] * P->chol[(size_t)mu * n * n + r * n + s];
+    return v;
+}
+
+static int apply_annihilate(int M, uint8_t* bits, int q)
+{
+    if (!bits[q]) return 0;
+    int s = 1;
+    for (int o = 0; o < q; ++o) if (bits[o]) s = -s;
+    bits[q] = 0;
+    return s;
+}
+
+static int apply_create(int M, uint8_t* bits, int p)
+{
+    if (bits[p]) return 0;
+    int s = 1;
+    for (int o = 0; o < p; ++o) if (bits[o]) s = -s;
+    bits[p] = 1;
+    return s;
+}
+
+double orc_hamiltonian_element(const orc_problem* P, const uint8_t* occ_n, const uint8_t* occ_np)
+{
+    int M = n_orb_M(P), n = P->n_sites;
+    uint8_t bn[512], bnp[512], w[512];
+    occ_to_bits(P, occ_n, bn);
+    occ_to_bits(P, occ_np, bnp);
+    double H = 0.0;
+    if (P->ham == 0) {
+        int same = memcmp(bn, bnp, M) == 0;
+        if (same) for (int i = 0; i < n; ++i) H += P->U * bn[i] * bn[n + i];
+        for (int b = 0; b < P->n_bonds; ++b) {
+            int i = P->bonds[2 * b], j = P->bonds[2 * b + 1];
+            if (i == j) continue;
+            for (int sg = 0; sg < 2; ++sg)
+                for (int dir = 0; dir < 2; ++dir) {
+                    int x = sg * n + (dir ? j : i), y = sg * n + (dir ? i : j);
+                    memcpy(w, bnp, M);
+                    int s = apply_annihilate(M, w, y);
+                    if (!s) continue;
+                    int s2 = apply_create(M, w, x);
+                    if (!s2) continue;
+                    if (memcmp(w, bn, M) == 0) H += -P->bond_t[b] * s * s2;
+                }
+        }
+        return H;
+    }
+    for (int s1 = 0; s1 < 2; ++s1)
+        for (int p = 0; p < n; ++p)
+            for (int q = 0; q < n; ++q) {
+                memcpy(w, bnp, M);
+                int s = apply_annihilate(M, w, s1 * n + q);
+                if (!s) continue;
+                int s2 = apply_create(M, w, s1 * n + p);
+                if (!s2) continue;
+                if (memcmp(w, bn, M) == 0) H += P->h[p * n + q] * s * s2;
+            }
+    for (int s1 = 0; s1 < 2; ++s1)
+        for (int s2 = 0; s2 < 2; ++s2)
+            for (int p = 0; p < n; ++p)
+                for (int q = 0; q < n; ++q)
+                    for (int r = 0; r < n; ++r)
+                        for (int s = 0; s < n; ++s) {
+                            /* a+_{p s1} a+_{r s2} a_{s s2} a_{q s1} acting on |n'> */
+                            memcpy(w, bnp, M);
+                            int g = apply_annihilate(M, w, s1 * n + q);
+                            if (!g) continue;
+                            int g2 = apply_annihilate(M, w, s2 * n + s);
+                            if (!g2) continue;
+                            int g3 = apply_create(M, w, s2 * n + r);
+                            if (!g3) continue;
+                            int g4 = apply_create(M, w, s1 * n + p);
+                            if (!g4) continue;
+                            if (memcmp(w, bn, M) == 0) H += 0.5 * eri(P, p, q, r, s) * g * g2 * g3 * g4;
+                        }
+    return H;
+}
+
+/* Local energy for the ab initio Hamiltonian: sum over every configuration
+ * n' reachable by one or two same-spin-conserving excitations, with
+ * <n|H|n'> from orc_hamiltonian_element and Psi_n' from scratch. */
+double orc_local_energy_abinitio(const orc_problem* P, const uint8_t* occ)
+{
+    int M = n_orb_M(P), N = P->n_up + P->n_dn;
+    uint8_t bits[512], w[512], occn[256];
+    occ_to_bits(P, occ, bits);
+    double la0;
+    int s0;
+    orc_log_psi(P, occ, &la0, &s0);
+    double E = orc_hamiltonian_element(P, occ, occ);
+    /* enumerate distinct n' != n with at most two electrons moved, spin kept */
+    int n = P->n_sites;
+    int nocc = N, nemp = M - N;
+    int occl[256], empl[256];
+    int io = 0, ie = 0;
+    for (int o = 0; o < M; ++o) { if (bits[o]) occl[io++] = o; else empl[ie++] = o; }
+    /* singles */
+    for (int a = 0; a < nocc; ++a)
+        for (int e = 0; e < nemp; ++e) {
+            if ((occl[a] >= n) != (empl[e] >= n)) continue;
+            memcpy(w, bits, M);
+            w[occl[a]] = 0; w[empl[e]] = 1;
+            bits_to_occ(M, w, occn);
+            double h = orc_hamiltonian_element(P, occ, occn);
+            if (h != 0.0) E += h * amp_ratio(P, occn, la0, s0);
+        }
+    /* doubles: remove a1 < a2, add e1 < e2, spin counts conserved */
+    for (int a1 = 0; a1 < nocc; ++a1)
+        for (int a2 = a1 + 1; a2 < nocc; ++a2)
+            for (int e1 = 0; e1 < nemp; ++e1)
+                for (int e2 = e1 + 1; e2 < nemp; ++e2) {
+                    int up_out = (occl[a1] < n) + (occl[a2] < n);
+                    int up_in = (empl[e1] < n) + (empl[e2] < n);
+                    if (up_out != up_in) continue;
+                    memcpy(w, bits, M);
+                    w[occl[a1]] = 0; w[occl[a2]] = 0; w[empl[e1]] = 1; w[empl[e2]] = 1;
+                    bits_to_occ(M, w, occn);
+                    double h = orc_hamiltonian_element(P, occ, occn);
+                    if (h != 0.0) E += h * amp_ratio(P, occn, la0, s0);
+                }
+    return E;
+}
+
+double orc_local_energy(const orc_problem* P, const uint8_t* occ)
+{
+    return P->ham == 0 ? orc_local_energy_hubbard(P, occ) : orc_local_energy_abinitio(P, occ);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Metropolis sampling from |Psi_n|^2 / <Psi|Psi> in the fixed (N_up, N_dn)  */
+/* sector (Sec. II.A, Eq. 3; sector restriction of Sec. III).               */
+/* ------------------------------------------------------------------------ */
+
+/* One proposal of walker w at step `step`.  Returns 1 if accepted and
+ * updates occ in place; *margin receives |u - r^2| / r^2. */
+static int metropolis_step(const orc_problem* P, uint8_t* occ, uint64_t seed, uint32_t walker,
+                           uint64_t step, double* la, int* sg, double* margin)
+{
+    int M = n_orb_M(P), N = P->n_up + P->n_dn, ns = P->n_sites;
+    uint32_t ctr[4] = {walker, (uint32_t)step, (uint32_t)(step >> 32), 0u};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t r[4];
+    orc_philox4x32_10(ctr, key, r);
+    int a = (int)(((uint64_t)r[0] * (uint64_t)N) >> 32);
+    int p = occ[a];
+    int spin = p >= ns;
+    int n_same = spin ? P->n_dn : P->n_up;
+    int n_empty = ns - n_same;
+    uint8_t bits[512], occn[256];
+    occ_to_bits(P, occ, bits);
+    if (n_empty <= 0) { *margin = INFINITY; return 0; }
+    int k = (int)(((uint64_t)r[1] * (uint64_t)n_empty) >> 32);
+    int q = -1;
+    for (int o = spin * ns, seen = 0; o < (spin + 1) * ns; ++o) {
+        if (!bits[o]) {
+            if (seen == k) { q = o; break; }
+            ++seen;
+        }
+    }
+    double u = (double)(r[2] >> 8) * (1.0 / 16777216.0);
+    bits[p] = 0;
+    bits[q] = 1;
+    bits_to_occ(M, bits, occn);
+    double la1;
+    int s1;
+    orc_log_psi(P, occn, &la1, &s1);
+    double ratio2 = (s1 == 0) ? 0.0 : exp(2.0 * (la1 - *la));
+    *margin = ratio2 > 0 ? fabs(u - ratio2) / ratio2 : INFINITY;
+    if (u < ratio2) {
+        memcpy(occ, occn, N);
+        *la = la1;
+        *sg = s1;
+        return 1;
+    }
+    return 0;
+}
+
+/* Run every walker's chain: n_burn sweeps, then n_spw sweeps each ending in
+ * a stored sample; a sweep is N proposals.  occ [n_walkers][N] (ascending) and
+ * step [n_walkers] are updated in place; samples go to
+ * out_occ[(w * n_spw + j) * N + a]; min_margin[w] and accepts[w] are filled. */
+int orc_sample(const orc_problem* P, int n_walkers, uint8_t* occ, uint64_t* step,
+               uint64_t seed, int n_burn, int n_spw, uint8_t* out_occ,
+               double* min_margin, int64_t* accepts)
+{
+    int N = P->n_up + P->n_dn;
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : bad)
+    for (int w = 0; w < n_walkers; ++w) {
+        uint8_t* o = occ + (size_t)w * N;
+        double la;
+        int sg;
+        orc_log_psi(P, o, &la, &sg);
+        if (sg == 0) { bad++; continue; }
+        double mm = INFINITY;
+        int64_t acc = 0;
+        for (int sw = 0; sw < n_burn + n_spw; ++sw) {
+            for (int t = 0; t < N; ++t) {
+                double m;
+                acc += metropolis_step(P, o, seed, (uint32_t)w, step[w], &la, &sg, &m);
+                step[w]++;
+                if (m < mm) mm = m;
+            }
+            if (sw >= n_burn)
+                memcpy(out_occ + ((size_t)w * n_spw + (sw - n_burn)) * N, o, N);
+        }
+        if (min_margin) min_margin[w] = mm;
+        if (accepts) accepts[w] = acc;
+    }
+    return bad ? -1 : 0;
+}
+
+/* Local energy and dense derivative ratios for n_s given configurations. */
+int orc_measure(const orc_problem* P, int64_t n_s, const uint8_t* occ, double* E, double* O)
+{
+    int N = P->n_up + P->n_dn;
+    int64_t nv = orc_n_params(P);
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 4) reduction(+ : bad)
+    for (int64_t s = 0; s < n_s; ++s) {
+        if (E) E[s] = orc_local_energy(P, occ + s * N);
+        if (O && orc_logderiv(P, occ + s * N, O + s * nv) != 0) bad++;
+    }
+    return bad ? -1 : 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* SR linear algebra on stored derivative ratios                            */
+/* ------------------------------------------------------------------------ */
+
+/* mean of O over samples (weight 1/n_s) */
+void orc_mean_O(int64_t n_s, int64_t nv, const double* O, double* Obar)
+{
+    for (int64_t k = 0; k < nv; ++k) Obar[k] = 0.0;
+    for (int64_t s = 0; s < n_s; ++s)
+        for (int64_t k = 0; k < nv; ++k) Obar[k] += O[s * nv + k];
+    for (int64_t k = 0; k < nv; ++k) Obar[k] /= (double)n_s;
+}
+
+/* g_k = <E_L O_k> - <E_L><O_k>: the right-hand side left after x_0 is
+ * eliminated from Eq. 2 (up to the factor -tau). */
+void orc_gradient(int64_t n_s, int64_t nv, const double* O, const double* E, double* g,
+                  double* E_mean)
+{
+    double Em = 0.0;
+    for (int64_t s = 0; s < n_s; ++s) Em += E[s];
+    Em /= (double)n_s;
+    double* Ob = (double*)malloc(sizeof(double) * nv);
+    orc_mean_O(n_s, nv, O, Ob);
+    for (int64_t k = 0; k < nv; ++k) g[k] = 0.0;
+    for (int64_t s = 0; s < n_s; ++s)
+        for (int64_t k = 0; k < nv; ++k) g[k] += E[s] * O[s * nv + k];
+    for (int64_t k = 0; k < nv; ++k) g[k] = g[k] / (double)n_s - Em * Ob[k];
+    free(Ob);
+    if (E_mean) *E_mean = Em;
+}
+
+/* Dense S_ij = <O_i O_j> - <O_i><O_j> (Eq. 3 with the mean part removed);
+ * S is nv x nv.  Only for small nv. */
+void orc_dense_S(int64_t n_s, int64_t nv, const double* O, double* S)
+{
+    double* Ob = (double*)malloc(sizeof(double) * nv);
+    orc_mean_O(n_s, nv, O, Ob);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < nv; ++i) {
+        for (int64_t j = 0; j < nv; ++j) {
+            double acc = 0.0;
+            for (int64_t s = 0; s < n_s; ++s) acc += O[s * nv + i] * O[s * nv + j];
+            S[i * nv + j] = acc / (double)n_s - Ob[i] * Ob[j];
+        }
+    }
+    free(Ob);
+}
+
+/* (S + eps I) v by the interchanged summation of Eq. 7:
+ * out = (1/n_s) sum_s O_s (O_s . v) - Obar (Obar . v) + eps v. */
+void orc_apply_S(int64_t n_s, int64_t nv, const double* O, const double* Obar, const double* v,
+                 double eps, double* out)
+{
+    double ob_v = 0.0;
+    for (int64_t k = 0; k < nv; ++k) ob_v += Obar[k] * v[k];
+    for (int64_t k = 0; k < nv; ++k) out[k] = 0.0;
+    for (int64_t s = 0; s < n_s; ++s) {
+        const double* Os = O + s * nv;
+        double t = 0.0;
+        for (int64_t k = 0; k < nv; ++k) t += Os[k] * v[k];
+        for (int64_t k = 0; k < nv; ++k) out[k] += Os[k] * t;
+    }
+    for (int64_t k = 0; k < nv; ++k) out[k] = out[k] / (double)n_s - Obar[k] * ob_v + eps * v[k];
+}
+
+static double dot(int64_t n, const double* a, const double* b)
+{
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i) s += a[i] * b[i];
+    return s;
+}
+
+/* Conjugate gradient on (S + eps I) x = g with x_0 = 0 (Sec. II.A: S is only
+ * touched through products).  Stops when the recurrence residual satisfies
+ * |r|/|g| <= tol or after max_iter products.  Reports the iterations and the
+ * true relative residual |g - (S + eps I) x| / |g|. */
+int orc_cg(int64_t n_s, int64_t nv, const double* O, const double* g, double eps, double tol,
+           int max_iter, double* x, int* iters, double* true_rel_res)
+{
+    double* Ob = (double*)malloc(sizeof(double) * nv);
+    double* r = (double*)malloc(sizeof(double) * nv);
+    double* p = (double*)malloc(sizeof(double) * nv);
+    double* Ap = (double*)malloc(sizeof(double) * nv);
+    orc_mean_O(n_s, nv, O, Ob);
+    for (int64_t k = 0; k < nv; ++k) { x[k] = 0.0; r[k] = g[k]; p[k] = g[k]; }
+    double gn = sqrt(dot(nv, g, g));
+    double rr = dot(nv, r, r);
+    int it = 0;
+    int conv = gn == 0.0;
+    while (!conv && it < max_iter) {
+        orc_apply_S(n_s, nv, O, Ob, p, eps, Ap);
+        double alpha = rr / dot(nv, p, Ap);
+        for (int64_t k = 0; k < nv; ++k) { x[k] += alpha * p[k]; r[k] -= alpha * Ap[k]; }
+        double rr_new = dot(nv, r, r);
+        ++it;
+        if (sqrt(rr_new) <= tol * gn) { conv = 1; rr = rr_new; break; }
+        double beta = rr_new / rr;
+        rr = rr_new;
+        for (int64_t k = 0; k < nv; ++k) p[k] = r[k] + beta * p[k];
+    }
+    orc_apply_S(n_s, nv, O, Ob, x, eps, Ap);
+    double res = 0.0;
+    for (int64_t k = 0; k < nv; ++k) { double d = g[k] - Ap[k]; res += d * d; }
+    if (true_rel_res) *true_rel_res = gn > 0 ? sqrt(res) / gn : 0.0;
+    if (iters) *iters = it;
+    free(Ob); free(r); free(p); free(Ap);
+    return conv ? 0 : 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Exact enumeration of the sector (tiny lattices only)                      */
+/* ------------------------------------------------------------------------ */
+
+static int next_combination(int* c, int k, int n)
+{
+    int i = k - 1;
+    while (i >= 0 && c[i] == n - k + i) --i;
+    if (i < 0) return 0;
+    c[i]++;
+    for (int j = i + 1; j < k; ++j) c[j] = c[j - 1] + 1;
+    return 1;
+}
+
+/* Number of configurations with n_up up and n_dn down electrons. */
+int64_t orc_sector_size(const orc_problem* P)
+{
+    double a = 1, b = 1;
+    for (int i = 0; i < P->n_up; ++i) a = a * (P->n_sites - i) / (i + 1);
+    for (int i = 0; i < P->n_dn; ++i) b = b * (P->n_sites - i) / (i + 1);
+    return (int64_t)llround(a * b);
+}
+
+/* List every sector configuration (ascending occupied lists, up choice
+ * outer, down choice inner, each in lexicographic order). */
+int64_t orc_enumerate(const orc_problem* P, uint8_t* occ_out)
+{
+    int nu = P->n_up, nd = P->n_dn, ns = P->n_sites, N = nu + nd;
+    int cu[64], cd[64];
+    int64_t cnt = 0;
+    for (int i = 0; i < nu; ++i) cu[i] = i;
+    do {
+        for (int i = 0; i < nd; ++i) cd[i] = i;
+        do {
+            for (int i = 0; i < nu; ++i) occ_out[cnt * N + i] = (uint8_t)cu[i];
+            for (int i = 0; i < nd; ++i) occ_out[cnt * N + nu + i] = (uint8_t)(ns + cd[i]);
+            ++cnt;
+        } while (nd > 0 && next_combination(cd, nd, ns));
+    } while (nu > 0 && next_combination(cu, nu, ns));
+    return cnt;
+}
+
+/* Exact |Psi_n|^2 / <Psi|Psi> over the whole sector, from log amplitudes. */
+void orc_exact_weights(const orc_problem* P, int64_t n_conf, const uint8_t* occ, double* w)
+{
+    int N = P->n_up + P->n_dn;
+    double mx = -INFINITY;
+    double* la = (double*)malloc(sizeof(double) * n_conf);
+    for (int64_t i = 0; i < n_conf; ++i) {
+        int s;
+        orc_log_psi(P, occ + i * N, &la[i], &s);
+        if (s == 0) la[i] = -INFINITY;
+        if (la[i] > mx) mx = la[i];
+    }
+    double tot = 0.0;
+    for (int64_t i = 0; i < n_conf; ++i) { w[i] = exp(2.0 * (la[i] - mx)); tot += w[i]; }
+    for (int64_t i = 0; i < n_conf; ++i) w[i] /= tot;
+    free(la);
+}
