@@ -1,0 +1,388 @@
+#!/usr/bin/env python
+"""SR-iteration benchmark of the matrix-free SR hot path on one GB300.
+
+One step = one stochastic-reconfiguration iteration of the 8x8 periodic
+Hubbard workload (28 + 28 electrons, 64 2x3-plaquette correlators + pfaffian,
+270,272 parameters, 16,384 walkers x 4 samples = 65,536 samples):
+  vmc_sample (4 sweeps per walker, chains continue from the previous step)
+  -> sr_gradient -> sr_cg_solve to relative residual 1e-6.
+The mixed path (FP32 walkers, BF16 O stream with FP32 accumulation, FP64
+scalars and FP64-accumulated residuals) is the headline; the plain FP64 path
+runs the same step for comparison.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+With torchrun (N > 1) every rank runs an independent replica (different
+sampling seed); the reported time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SR-iteration s and S·v GB/s, mixed vs FP64 on 1 GB300 at rel. residual 1e-6"
+WORKLOAD = ("8x8 periodic Hubbard U/t=4, 28+28 electrons, 64 2x3-plaquette correlators + pfaffian over 128 "
+            "spin orbitals (n_v=270,272), 16,384 walkers x 4 samples = 65,536 samples, shift 1e-3, CG to 1e-6")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in self.rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for i, n in enumerate(names):
+                if len(r) > 5 + i and r[5 + i].lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_gpu(args, rank, world, dist):
+    import torch
+    from paper_1108_0900_gb300 import inputs
+    from paper_1108_0900_gb300 import vmcsr as V
+
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    wl = inputs.config(5)
+    seed = inputs.seed_sampling_for(5) + 7919 * rank
+    shift, tol = wl.shift, 1e-6
+    max_iter = 20000
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def make(path):
+        prec = V.VMC_FP32 if path == "mixed" else V.VMC_FP64
+        h = V.vmc_create(wl, walker_precision=prec, keep_fp64_store=(path == "fp64"),
+                         keep_lowp_store=(path == "mixed"))
+        V.vmc_set_params(h, wl.C, wl.f)
+        V.vmc_set_walkers(h, wl.init_occ)
+        V.vmc_sample(h, wl.burn_in_sweeps, seed)      # thermalisation, outside every timed region
+        return h
+
+    def step(h, path, k, info_out):
+        V.vmc_sample(h, 0, seed + 1 + k)
+        store = V.VMC_STORE_FP32 if path == "mixed" else V.VMC_STORE_FP64
+        g, _ = V.sr_gradient(h, store, stats=False)
+        mode = V.VMC_CG_MIXED if path == "mixed" else V.VMC_CG_FP64
+        x, info = V.sr_cg_solve(h, g, shift, tol, max_iter, mode, allow_not_converged=True)
+        info_out.append(info)
+        return x
+
+    def timed(h, path, steps, warmup, profile=False):
+        infos = []
+        for k in range(warmup):
+            step(h, path, k, infos)
+        barrier()
+        infos.clear()
+        if profile:
+            V.vmc_profile(h, True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with Clocks(local) as clk:
+            e0.record()
+            for k in range(steps):
+                step(h, path, warmup + k, infos)
+            e1.record()
+            barrier()
+        ms = e0.elapsed_time(e1) / steps
+        prof = V.vmc_profile_read(h, V.VMC_STORE_BF16) if profile else None
+        if profile:
+            V.vmc_profile(h, False)
+        return ms, infos, prof, clk.summary()
+
+    # ---- mixed path (headline) ----------------------------------------------
+    hm = make("mixed")
+    ms, infos, prof, clocks = timed(hm, "mixed", args.steps, args.warmup, profile=True)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # ---- end to end through the public API with host buffers ----------------
+    import ctypes as ct
+    pin_C = torch.from_numpy(wl.C.copy()).pin_memory()
+    pin_f = torch.from_numpy(wl.f.copy()).pin_memory()
+    x_host = torch.empty(wl.n_params, dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    barrier()
+    for k in range(max(1, args.steps)):
+        t0 = time.perf_counter()
+        V.vmc_set_params(hm, pin_C.numpy(), pin_f.numpy())        # host -> device parameters
+        infos_e2e = []
+        x = step(hm, "mixed", 1000 + k, infos_e2e)
+        x_host.copy_(x, non_blocking=True)                        # device -> host update
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    h2d = (wl.C.nbytes + wl.f.nbytes)
+    d2h = x_host.numel() * 8
+
+    # ---- plain FP64 path ------------------------------------------------------
+    fp64 = None
+    if not args.no_fp64:
+        hf = make("fp64")
+        ms64, infos64, _, clocks64 = timed(hf, "fp64", max(1, args.fp64_steps), 1)
+        fp64 = {"ms_per_step": round(ms64, 3),
+                "cg_iterations": float(np.mean([i["iterations"] for i in infos64])),
+                "true_rel_residual": max(i["true_rel_residual"] for i in infos64),
+                "converged": all(i["converged"] for i in infos64)}
+        hf.close()
+
+    peak, peak_kind = peaks()
+    ach = prof["pass_bytes"] / (prof["pass_ms"] * 1e-3) / 1e9 if prof and prof["pass_ms"] > 0 else None
+    per_launch_bytes = prof["pass_bytes"] / max(1, prof["pass_launches"]) if prof else None
+    res = {
+        "metric": METRIC,
+        "value": round(ms / 1e3, 6),
+        "unit": "s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms, 3),
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "precision": {"walkers": "f32 (inverse rebuilt from scratch each step)", "O_stream": "bf16",
+                      "stream_accumulate": "f32", "scalars_and_outer_residual": "f64 over the f32 store"},
+        "data": "synthetic (seeded random CPS amplitudes 1+N(0,0.01^2), pairing N(0,0.1^2), random sector starts)",
+        "config": {"workload": WORKLOAD, "n_params": wl.n_params, "n_samples": wl.n_samples,
+                   "shift": shift, "tol": tol, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (BF16 O store 214 MB, FP32 store 428 MB > 129 MB L2)"},
+        "cg": {"inner_iterations": float(np.mean([i["iterations"] for i in infos])),
+               "outer_steps": float(np.mean([i["refinements"] for i in infos])),
+               "true_rel_residual": max(i["true_rel_residual"] for i in infos),
+               "converged": all(i["converged"] for i in infos)},
+        "sv_gbs": round(ach, 1) if ach else None,
+        "fp64_path": fp64,
+        "speedup_vs_fp64_path": round(fp64["ms_per_step"] / ms, 3) if fp64 else None,
+        "roofline": {"bound": "hbm", "kernel": "k_sr_main<bf16,f32,K=1> (Eq. 7 gather/scatter pass)",
+                     "achieved": round(ach, 1) if ach else None, "peak": peak, "unit": "GB/s",
+                     "frac": round(ach / peak, 4) if ach else None, "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": per_launch_bytes,
+                     "launches": prof["pass_launches"] if prof else None,
+                     "traffic": None},
+        "e2e": {"value": round(float(np.median(e2e_ms)) / 1e3, 6), "unit": "s",
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(prof["launches_all"]) if prof else None,
+        "clocks": clocks,
+    }
+    hm.close()
+    return res, infos
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_step(n_walkers: int, spw: int, seed: int, cg_iters_full: float):
+    """The oracle's SR iteration on a bounded sample of the workload:
+    n_walkers chains x spw samples (one sweep each, chains started from the
+    thermalised-free seeded starts after one sweep), E_L and dense O, the
+    gradient and one Eq. 7 product timed; scaled to 65,536 samples and the
+    FP64 CG iteration count of the full workload."""
+    import oracle
+    from paper_1108_0900_gb300 import inputs
+
+    wl = inputs.config(5, n_walkers=n_walkers, samples_per_walker=spw)
+    P = oracle.Problem(wl)
+    occ = wl.init_occ.copy()
+    step = np.zeros(n_walkers, np.uint64)
+    t0 = time.perf_counter()
+    smp, _, _ = P.sample(occ, step, seed, 0, spw)
+    t1 = time.perf_counter()
+    E, O = P.measure(smp)
+    t2 = time.perf_counter()
+    g, _ = oracle.gradient(O, E)
+    t3 = time.perf_counter()
+    v = np.random.default_rng(0).standard_normal(wl.n_params)
+    Ob = oracle.mean_O(O)
+    n_prod = 5
+    for _ in range(n_prod):
+        oracle.apply_S(O, v, wl.shift, Obar=Ob)
+    t4 = t3 + (time.perf_counter() - t3) / n_prod
+    n = len(smp)
+    full = 65536
+    per_sample = (t1 - t0 + t2 - t1 + t3 - t2) / n
+    sv_per_sample = (t4 - t3) / n
+    est = per_sample * full + sv_per_sample * full * cg_iters_full
+    return est, {"sample_s": t1 - t0, "measure_s": t2 - t1, "gradient_s": t3 - t2, "apply_S_s": t4 - t3,
+                 "n_samples": n}
+
+
+def cpu_baseline(cg_iters_full: float, n_walkers=128, spw=2):
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    est, parts = oracle_step(n_walkers, spw, 2005, cg_iters_full)
+    return {"value": round(est, 3), "unit": "s", "cores": int(os.environ.get("OMP_NUM_THREADS", cores)),
+            "kind": "oracle",
+            "sample": (f"{parts['n_samples']} samples ({n_walkers} walkers x {spw}) of the same workload: "
+                       f"sampling + E_L + dense O + gradient timed and scaled x{65536 / parts['n_samples']:.0f}, "
+                       f"Eq. 7 products (mean of 5) scaled to 65,536 samples x {cg_iters_full:.0f} CG products "
+                       f"(the GPU FP64 path's iteration count)"),
+            "parts": {k: round(v, 4) if isinstance(v, float) else v for k, v in parts.items()}}
+
+
+def run_reference(args):
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    iters = args.ref_cg_iters
+    vals = []
+    for k in range(args.warmup + args.steps):
+        est, parts = oracle_step(32, 2, 3000 + k, iters)
+        if k >= args.warmup:
+            vals.append(est)
+    v = float(np.mean(vals))
+    cb = {"value": round(v, 3), "unit": "s", "cores": int(os.environ["OMP_NUM_THREADS"]), "kind": "oracle",
+          "sample": (f"each step: 64 samples (32 walkers x 2) of the same workload through the FP64 CPU oracle, "
+                     f"scaled to 65,536 samples and {iters} CG products")}
+    return {"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD}, "cpu_baseline": cb,
+            "e2e": {"value": round(v, 3), "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def run_sv_only(args):
+    """S product timing on the same workload: the O store filled from seeded
+    sector configurations (vmc_measure, FP32 walkers), then `--sv-only`
+    passes per store kind, each timed on the device by the library's events."""
+    import torch
+    from paper_1108_0900_gb300 import inputs
+    from paper_1108_0900_gb300 import vmcsr as V
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    wl = inputs.config(5)
+    h = V.vmc_create(wl, walker_precision=V.VMC_FP32, keep_fp64_store=True, keep_lowp_store=True)
+    V.vmc_set_params(h, wl.C, wl.f)
+    cfgs = inputs.draw_configs(np.random.default_rng(555), wl.n_samples, wl.n_sites, wl.n_up, wl.n_dn)
+    V.vmc_measure(h, cfgs)
+    peak, peak_kind = peaks()
+    v = torch.from_numpy(np.random.default_rng(1).standard_normal(wl.n_params)).cuda()
+    out = {}
+    for name, store in (("bf16", V.VMC_STORE_BF16), ("fp32_f32acc", V.VMC_STORE_FP32_F32ACC),
+                        ("fp32_f64acc", V.VMC_STORE_FP32), ("fp64", V.VMC_STORE_FP64)):
+        for _ in range(2):
+            V.sr_apply_S(h, v, wl.shift, store)
+        torch.cuda.synchronize()
+        V.vmc_profile(h, True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.sv_only):
+            V.sr_apply_S(h, v, wl.shift, store)
+        e1.record()
+        torch.cuda.synchronize()
+        pr = V.vmc_profile_read(h, store)
+        V.vmc_profile(h, False)
+        kms = pr["pass_ms"] / max(1, pr["pass_launches"])
+        gbs = pr["pass_bytes"] / max(1, pr["pass_launches"]) / (kms * 1e-3) / 1e9
+        out[name] = {"apply_S_ms": round(e0.elapsed_time(e1) / args.sv_only, 4), "stream_kernel_ms": round(kms, 4),
+                     "stream_kernel_gbs": round(gbs, 1), "frac_of_hbm": round(gbs / peak, 4),
+                     "algorithmic_bytes": pr["pass_bytes"] / max(1, pr["pass_launches"])}
+    h.close()
+    return {"metric": "S·v GB/s", "workload": WORKLOAD, "peak_gbs": peak, "peak_kind": peak_kind,
+            "passes": args.sv_only, "stores": out}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-cg-iters", type=float, default=350.0)
+    ap.add_argument("--sv-only", type=int, default=0, help="time N S products per store kind and exit")
+    args = ap.parse_args()
+    if args.sv_only:
+        print(json.dumps(run_sv_only(args)))
+        return
+    args.warmup = max(args.warmup, 1)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)))
+        return
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    res, infos = run_gpu(args, rank, world, dist)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            iters = (res["fp64_path"] or {}).get("cg_iterations") or res["cg"]["inner_iterations"]
+            res["cpu_baseline"] = cpu_baseline(iters)
+        print(json.dumps(res))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

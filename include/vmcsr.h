@@ -1,0 +1,233 @@
+/*
+ * vmcsr — GB300-native matrix-free stochastic reconfiguration (SR) for a
+ * correlator-product-state (CPS) x pfaffian wavefunction.
+ *
+ * The method is that of Neuscamman, Umrigar and Chan, "Optimizing large
+ * parameter sets in variational quantum Monte Carlo" (arXiv:1108.0900):
+ *   Sec. II.A, Eq. 2   the SR linear system <Psi^i|(1 - tau H)|Psi> = sum_j S_ij x_j;
+ *   Sec. II.A, Eq. 3   derivative ratios Psi^i_n / Psi_n sampled from |Psi_n|^2;
+ *   Sec. II.A, Eq. 7   S z evaluated by interchanging the sums, O(n_s n_v);
+ *   Sec. II.A          conjugate gradient instead of building S;
+ *   Sec. II.C, Eq. 11  |Psi> = prod_p C_p (sum_{i<j} f_ij a+_i a+_j)^{N/2} |0>;
+ *   Sec. III           sampling restricted to fixed N and S_z.
+ *
+ * Conventions shared by every entry point
+ *   - M = 2 n_sites spin orbitals; spin orbital p = sigma * n_sites + site.
+ *   - Parameter vector alpha (length n_v): correlator amplitudes first
+ *     (correlator c occupies 4^{m_c} consecutive entries, m_c = its site
+ *     count, local state idx_c = sum_j 4^j (n_{s_j up} + 2 n_{s_j dn})),
+ *     then the pairing amplitudes f_pq, p < q, in row-major upper-triangle
+ *     order (M(M-1)/2 entries).
+ *   - O_k(n) = (dPsi_n / dalpha_k) / Psi_n.  Eliminating x_0 from Eq. 2 with
+ *     O_0 = 1 gives S x = -tau g with the covariance S_ij = <O_i O_j> -
+ *     <O_i><O_j> and g_i = <E_L O_i> - <E_L><O_i>; every mean uses weight 1/n_s.
+ *     The library solves (S + shift I) y = g and returns y.
+ *   - Sample s = walker * samples_per_walker + j.
+ *   - Every function returns VMC_OK (0) or a negative VMC_ERR_* code; no
+ *     exception crosses this boundary.  Pointers marked "host" are read or
+ *     written synchronously; pointers marked "device" are CUDA device
+ *     addresses on the handle's device and are only touched by work enqueued
+ *     on `stream` (a cudaStream_t passed as void*, NULL = legacy stream).
+ *   - The caller owns every pointer it passes; the handle owns its walker
+ *     state, its O store and all scratch buffers.
+ */
+#ifndef VMCSR_H
+#define VMCSR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VMC_OK 0
+#define VMC_ERR_INVALID_ARG -1
+#define VMC_ERR_OOM -2
+#define VMC_ERR_SINGULAR -3
+#define VMC_ERR_NONFINITE -4
+#define VMC_ERR_NOT_CONVERGED -5
+#define VMC_ERR_TIMEOUT -6
+#define VMC_ERR_CUDA -7
+#define VMC_ERR_UNSUPPORTED -8
+#define VMC_ERR_STATE -9
+
+#define VMC_HUBBARD 0
+#define VMC_ABINITIO 1
+
+/* arithmetic of the walkers (sampling, local energy, derivative ratios) */
+#define VMC_FP64 0      /* every walker quantity in FP64                         */
+#define VMC_FP32 1      /* FP32 ratios and inverse updates, FP64 sums             */
+
+/* O-store / S-product precisions */
+#define VMC_STORE_FP64 0  /* FP64 storage, FP64 arithmetic                        */
+#define VMC_STORE_FP32 1  /* FP32 storage, FP64 accumulation                      */
+#define VMC_STORE_BF16 2  /* BF16 storage, FP32 accumulation                      */
+#define VMC_STORE_FP32_F32ACC 3  /* FP32 storage, FP32 accumulation               */
+
+/* CG modes */
+#define VMC_CG_FP64 0   /* plain CG, FP64 vectors and FP64 S products             */
+#define VMC_CG_MIXED 1  /* BF16-stream inner CG (FP32 vectors, FP64 scalars),
+                           refined against the FP32 store with FP64 accumulation  */
+#define VMC_CG_FP32 2   /* like MIXED but the inner product streams FP32          */
+
+typedef struct vmc_ctx* vmc_handle;
+
+/* Lattice: n_sites spatial orbitals (<= 64) and, for the Hubbard model, the
+ * bond list (bonds[2b], bonds[2b+1]) with hopping bond_t[b]; a repeated bond
+ * adds its hopping again.  Arrays are host pointers, copied by vmc_create. */
+typedef struct {
+    int n_sites;
+    int n_bonds;
+    const int32_t* bonds;
+    const double* bond_t;
+} vmc_lattice;
+
+/* Hamiltonian.  VMC_HUBBARD: H = -sum_b t_b sum_s (c+_is c_js + h.c.)
+ * + U sum_i n_i,up n_i,dn.  VMC_ABINITIO: H = sum_{pq,s} h_pq a+_ps a_qs
+ * + 1/2 sum_{pqrs,st} (pq|rs) a+_ps a+_rt a_st a_qs with
+ * (pq|rs) = sum_mu L^mu_pq L^mu_rs (the factorised form of Eq. 9 with R = L);
+ * h is [n_sites][n_sites] and chol is [n_chol][n_sites][n_sites], host. */
+typedef struct {
+    int kind;
+    double U;
+    int n_chol;
+    const double* h;
+    const double* chol;
+} vmc_hamiltonian;
+
+/* Ansatz (Eq. 11): sector (n_up, n_dn) with n_up + n_dn even and <= 64, and
+ * correlator site lists corr_sites[corr_ptr[c] .. corr_ptr[c+1]) (each <= 6
+ * sites, host arrays).  The pairing runs over all spin orbitals. */
+typedef struct {
+    int n_up;
+    int n_dn;
+    int n_corr;
+    const int32_t* corr_ptr;
+    const int32_t* corr_sites;
+} vmc_ansatz;
+
+typedef struct {
+    int n_walkers;          /* Markov chains                                       */
+    int samples_per_walker; /* samples stored per vmc_sample call                  */
+    int walker_precision;   /* VMC_FP64 or VMC_FP32                                 */
+    int keep_fp64_store;    /* 1: keep an FP64 O store (needed by VMC_CG_FP64)       */
+    int keep_lowp_store;    /* 1: keep FP32 + BF16 O stores (needed by MIXED/FP32)   */
+} vmc_options;
+
+typedef struct {
+    int iterations;          /* S products in the inner (or only) Krylov loop      */
+    int refinements;         /* outer refinement steps (mixed modes)                */
+    int residual_products;   /* high-precision residual products (mixed modes)      */
+    int converged;           /* 1 if the true residual met tol                      */
+    double true_rel_residual;/* |g - (S + shift I) x| / |g|, FP64 accumulation over
+                                the mode's reference store (FP64 or FP32)           */
+} vmc_cg_info;
+
+/* Create a handle on the current CUDA device.  Copies every input.  Errors:
+ * INVALID_ARG (sizes out of range, odd N, > 64 sites, bad bond or site index),
+ * OOM, CUDA. */
+int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, const vmc_ansatz* ans,
+               const vmc_options* opt, vmc_handle* out);
+int vmc_destroy(vmc_handle h);
+
+/* Number of variational parameters n_v and of correlator parameters. */
+int vmc_num_params(vmc_handle h, int64_t* n_v, int64_t* n_corr_params);
+
+/* Set the correlator amplitudes C[n_corr_params] and pairing f[M(M-1)/2]
+ * (host, FP64, layout above).  Errors: SINGULAR if some C is zero. */
+int vmc_set_params(vmc_handle h, const double* C, const double* f);
+
+/* Set walker configurations: occ[n_walkers][N] ascending occupied spin
+ * orbitals (host, uint8) with n_up orbitals below n_sites; step[n_walkers]
+ * (host, may be NULL = 0) is each chain's proposal counter.  Errors:
+ * INVALID_ARG for a configuration outside the sector. */
+int vmc_set_walkers(vmc_handle h, const uint8_t* occ, const uint64_t* step);
+/* Read back walker configurations (ascending) and counters (host, may be NULL). */
+int vmc_get_walkers(vmc_handle h, uint8_t* occ, uint64_t* step, void* stream);
+
+/* Metropolis sampling from |Psi_n|^2 in the fixed sector (Sec. II.A, Sec. III).
+ * Each walker first rebuilds its pairing inverse from scratch, runs n_burn
+ * sweeps, then samples_per_walker sweeps each ending in a stored sample; a
+ * sweep is N proposals.  A proposal moves the a-th occupied orbital
+ * (ascending) to the k-th empty orbital of the same spin (ascending); a, k
+ * and u come from Philox4x32-10 with key (seed lo, seed hi) and counter
+ * (walker, step lo, step hi, 0): a = hi32(r0 N), k = hi32(r1 n_empty),
+ * u = (r2 >> 8) 2^-24, accepted iff u < |Psi'/Psi|^2.  At each stored sample
+ * the walker writes E_L, its ascending occupation, the correlator states and
+ * the pairing block of O into the handle's O store.  Errors: SINGULAR (a
+ * walker's pairing submatrix could not be inverted), NONFINITE, CUDA. */
+int vmc_sample(vmc_handle h, int n_burn, uint64_t seed, void* stream);
+
+/* Evaluate E_L and O for caller-given configurations occ[n_s][N] (host,
+ * ascending, n_s <= n_walkers * samples_per_walker), recomputing each
+ * pairing inverse from scratch; the result replaces the O store and the
+ * handle then holds n_s samples. */
+int vmc_measure(vmc_handle h, const uint8_t* occ, int64_t n_s, void* stream);
+
+/* Number of samples currently in the O store. */
+int vmc_num_samples(vmc_handle h, int64_t* n_s);
+
+/* Copy the O store out (host pointers, each may be NULL): occ[n_s][N],
+ * E_L[n_s], corr_state[n_s][n_corr] (uint16), pf[n_s][P] with
+ * P = n_up(n_up-1)/2 + n_dn(n_dn-1)/2 + n_up n_dn in block order
+ * (up-up triangle row-major, down-down triangle, up-down rectangle
+ * row-major over ascending positions) converted to FP64 from the store
+ * `store` (VMC_STORE_*).  Element (a, b), a < b, is O of f_{occ[a] occ[b]}. */
+int vmc_get_samples(vmc_handle h, uint8_t* occ, double* E_L, uint16_t* corr_state, double* pf,
+                    int store, void* stream);
+
+/* ln|Psi_n| for every stored sample (device out[n_s], FP64 pfaffian from scratch). */
+int vmc_logpsi(vmc_handle h, double* out, void* stream);
+/* Adjoint of ln|Psi_n| with respect to alpha (Eq. 3's ratios): with w
+ * (device [n_s] FP64) writes grad[k] = sum_s w_s O_k(n_s) (device [n_v]),
+ * recomputing every pairing inverse from scratch in FP64 instead of reading
+ * the store; with w == NULL it instead rewrites the O store from scratch
+ * (grad unused). */
+int vmc_logpsi_backward(vmc_handle h, const double* w, double* grad, void* stream);
+
+/* Sample means and the SR right-hand side (Eq. 2 after eliminating x_0):
+ * Obar (kept in the handle), E_mean = <E_L>, g = <E_L O> - <E_L> Obar
+ * (device g[n_v]), FP64 accumulation over the store of `store`
+ * (VMC_STORE_FP64 or VMC_STORE_FP32).  e_stats (host, may be NULL) receives
+ * {E_mean, E_variance, standard error over walkers}. */
+int sr_gradient(vmc_handle h, double* g, double* e_stats, int store, void* stream);
+
+/* out = (S + shift I) V for k right-hand sides (Eq. 7 with the covariance
+ * term): V and out are device [k][n_v] FP64 (column j at offset j n_v),
+ * 1 <= k <= 4; `store` picks the O store and arithmetic (VMC_STORE_*).
+ * sr_gradient must have run since the last sampling call (it sets Obar). */
+int sr_apply_S(vmc_handle h, const double* V, double* out, int k, double shift, int store,
+               void* stream);
+
+/* Solve (S + shift I) x = g (device g, x [n_v] FP64) by conjugate gradient
+ * (Sec. II.A), x_0 = 0, until the true relative residual is <= tol or
+ * max_iter products; mode VMC_CG_*.  info (host) is filled. */
+int sr_cg_solve(vmc_handle h, const double* g, double shift, double tol, int max_iter, int mode,
+                double* x, vmc_cg_info* info, void* stream);
+
+/* Measurement support (no counterpart in the paper).  vmc_profile(h, 1)
+ * resets the counters and starts recording: every kernel the handle launches
+ * is counted, and each launch of the O-store streaming kernel (the Eq. 7
+ * gather/scatter pass and the gradient pass) is bracketed by CUDA events on
+ * its stream.  vmc_profile(h, 0) stops recording.  Recording adds two event
+ * records per streaming launch and nothing else. */
+int vmc_profile(vmc_handle h, int enable);
+/* Totals since the last vmc_profile(h, 1) (host outputs, each may be NULL):
+ * launches_all = kernels launched; for streaming launches over the store
+ * `store` (VMC_STORE_*; FP32 with FP64 and with FP32 accumulation are
+ * counted apart) their number, summed device time in ms and algorithmic
+ * bytes = n_s (2 n_corr + N + P * element size) per launch (the O store read
+ * once).  Waits for the recorded events. */
+int vmc_profile_read(vmc_handle h, int store, int64_t* launches_all, int64_t* pass_launches, double* pass_ms,
+                     double* pass_bytes);
+
+const char* vmc_error_string(int code);
+/* Text of the last failing CUDA call or internal check on the calling
+ * thread, for diagnostics ("" if none).  The pointer stays valid until the
+ * next failing call on that thread. */
+const char* vmc_last_error_detail(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

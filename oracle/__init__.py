@@ -71,7 +71,7 @@ def lib():
             L.orc_hamiltonian_element.restype = dbl
             L.orc_local_energy.argtypes = [vp, vp]
             L.orc_local_energy.restype = dbl
-            L.orc_sample.argtypes = [vp, i32, vp, vp, ct.c_uint64, i32, i32, vp, vp, vp]
+            L.orc_sample.argtypes = [vp, i32, vp, vp, ct.c_uint64, i32, i32, vp, vp, vp, dbl, vp]
             L.orc_sample.restype = i32
             L.orc_measure.argtypes = [vp, i64, vp, vp, vp]
             L.orc_measure.restype = i32
@@ -157,18 +157,24 @@ class Problem:
         return float(lib().orc_hamiltonian_element(self.ref, _ptr(a), _ptr(b)))
 
     # --- sampling ------------------------------------------------------------
-    def sample(self, occ, step, seed: int, n_burn: int, n_spw: int):
-        """Advance every walker in place; returns (samples, min_margin, accepts)."""
+    def sample(self, occ, step, seed: int, n_burn: int, n_spw: int, close_tol: float = 0.0,
+               return_first_close: bool = False):
+        """Advance every walker in place; returns (samples, min_margin, accepts)
+        and, on request, the index of each walker's first proposal whose
+        relative acceptance margin was below close_tol (-1 if none)."""
         assert occ.dtype == np.uint8 and occ.flags.c_contiguous
         assert step.dtype == np.uint64 and step.flags.c_contiguous
         nw, N = occ.shape
         out = np.zeros((nw * n_spw, N), np.uint8)
         mm = np.zeros(nw)
         acc = np.zeros(nw, np.int64)
+        fc = np.zeros(nw, np.int64)
         rc = lib().orc_sample(self.ref, nw, _ptr(occ), _ptr(step), ct.c_uint64(seed), n_burn, n_spw,
-                              _ptr(out), _ptr(mm), _ptr(acc))
+                              _ptr(out), _ptr(mm), _ptr(acc), float(close_tol), _ptr(fc))
         if rc != 0:
             raise ArithmeticError("walker with zero amplitude")
+        if return_first_close:
+            return out, mm, acc, fc
         return out, mm, acc
 
     def measure(self, occ, want_O: bool = True):

@@ -539,10 +539,12 @@ static int metropolis_step(const orc_problem* P, uint8_t* occ, uint64_t seed, ui
 /* Run every walker's chain: n_burn sweeps, then n_spw sweeps each ending in
  * a stored sample; a sweep is N proposals.  occ [n_walkers][N] (ascending) and
  * step [n_walkers] are updated in place; samples go to
- * out_occ[(w * n_spw + j) * N + a]; min_margin[w] and accepts[w] are filled. */
+ * out_occ[(w * n_spw + j) * N + a]; min_margin[w] and accepts[w] are filled,
+ * and first_close[w] is the index (within this call) of the first proposal
+ * whose relative margin |u - r^2| / r^2 fell below close_tol, or -1. */
 int orc_sample(const orc_problem* P, int n_walkers, uint8_t* occ, uint64_t* step,
                uint64_t seed, int n_burn, int n_spw, uint8_t* out_occ,
-               double* min_margin, int64_t* accepts)
+               double* min_margin, int64_t* accepts, double close_tol, int64_t* first_close)
 {
     int N = P->n_up + P->n_dn;
     int bad = 0;
@@ -554,19 +556,21 @@ int orc_sample(const orc_problem* P, int n_walkers, uint8_t* occ, uint64_t* step
         orc_log_psi(P, o, &la, &sg);
         if (sg == 0) { bad++; continue; }
         double mm = INFINITY;
-        int64_t acc = 0;
+        int64_t acc = 0, fc = -1, k = 0;
         for (int sw = 0; sw < n_burn + n_spw; ++sw) {
-            for (int t = 0; t < N; ++t) {
+            for (int t = 0; t < N; ++t, ++k) {
                 double m;
                 acc += metropolis_step(P, o, seed, (uint32_t)w, step[w], &la, &sg, &m);
                 step[w]++;
                 if (m < mm) mm = m;
+                if (fc < 0 && m < close_tol) fc = k;
             }
             if (sw >= n_burn)
                 memcpy(out_occ + ((size_t)w * n_spw + (sw - n_burn)) * N, o, N);
         }
         if (min_margin) min_margin[w] = mm;
         if (accepts) accepts[w] = acc;
+        if (first_close) first_close[w] = fc;
     }
     return bad ? -1 : 0;
 }

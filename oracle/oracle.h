@@ -38,7 +38,8 @@ double orc_local_energy_hubbard(const orc_problem* P, const uint8_t* occ);
 double orc_local_energy_abinitio(const orc_problem* P, const uint8_t* occ);
 double orc_local_energy(const orc_problem* P, const uint8_t* occ);
 int orc_sample(const orc_problem* P, int n_walkers, uint8_t* occ, uint64_t* step, uint64_t seed,
-               int n_burn, int n_spw, uint8_t* out_occ, double* min_margin, int64_t* accepts);
+               int n_burn, int n_spw, uint8_t* out_occ, double* min_margin, int64_t* accepts,
+               double close_tol, int64_t* first_close);
 int orc_measure(const orc_problem* P, int64_t n_s, const uint8_t* occ, double* E, double* O);
 void orc_mean_O(int64_t n_s, int64_t nv, const double* O, double* Obar);
 void orc_gradient(int64_t n_s, int64_t nv, const double* O, const double* E, double* g,

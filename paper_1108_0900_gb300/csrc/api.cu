@@ -1,0 +1,1194 @@
+// Host side of the vmcsr C ABI (include/vmcsr.h): handle lifetime, problem
+// tables, kernel launches and the conjugate-gradient drivers.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "vmcsr.h"
+
+using namespace vmc;
+
+namespace {
+
+constexpr int kMaxK = 4;
+constexpr int kNumPart = 256;   // blocks of the reduction kernels
+constexpr int kChunk = 16;      // CG iterations between host convergence checks
+
+#define VCK(x)                                                    \
+    do {                                                          \
+        cudaError_t e_ = (x);                                     \
+        if (e_ != cudaSuccess) {                                  \
+            set_err(std::string(#x) + ": " + cudaGetErrorString(e_)); \
+            return e_ == cudaErrorMemoryAllocation ? VMC_ERR_OOM : VMC_ERR_CUDA; \
+        }                                                         \
+    } while (0)
+
+thread_local std::string g_err;
+void set_err(const std::string& s) { g_err = s; }
+
+int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+}  // namespace
+
+struct vmc_ctx {
+    int dev = 0, nsm = 0;
+    size_t smem_optin = 0;
+    int ns = 0, M = 0, nu = 0, nd = 0, N = 0, ncorr = 0, P = 0, npf = 0;
+    int64_t ncp = 0, nv = 0;
+    int n_walkers = 0, spw = 0;
+    int64_t ncap = 0, n_s = 0;
+    int wprec = VMC_FP64, keep64 = 1, keeplow = 0;
+    int ham = 0;
+    int maxd = 1;
+    bool params_set = false, walkers_set = false;
+    bool use_stream = true;  // TMA-staged pass for FP32-accumulation products
+    bool obar_ok[3] = {false, false, false};  // per store: FP64, FP32, BF16
+    std::vector<int64_t> corr_off;
+
+    DevProblem pb{};
+    // device tables
+    int *d_corr_ptr = nullptr, *d_corr_sites = nullptr;
+    int64_t* d_corr_off = nullptr;
+    int *d_site_cptr = nullptr, *d_site_corr = nullptr, *d_site_w = nullptr;
+    int *d_nbr_ptr = nullptr, *d_nbr_site = nullptr;
+    double* d_nbr_t = nullptr;
+    double *d_h = nullptr, *d_eri = nullptr;
+    double *d_C64 = nullptr, *d_invC64 = nullptr, *d_F64 = nullptr;
+    float *d_C32 = nullptr, *d_invC32 = nullptr, *d_F32 = nullptr;
+    uint16_t* d_pairtab = nullptr;
+    int* d_rowbase = nullptr;
+    // walkers
+    uint8_t* d_wocc = nullptr;
+    uint64_t* d_wstep = nullptr;
+    uint8_t* d_mocc = nullptr;  // configurations handed to measure / backward
+    // O store
+    int Nst = 0, ncst = 0;
+    int64_t Pst = 0;
+    uint8_t* d_socc = nullptr;
+    uint16_t *d_cidx = nullptr, *d_cidxT = nullptr;
+    double* d_E = nullptr;
+    double* d_pf64 = nullptr;
+    float* d_pf32 = nullptr;
+    __nv_bfloat16* d_pf16 = nullptr;
+    double* d_Obar[3] = {nullptr, nullptr, nullptr};
+    int* d_status = nullptr;
+    // scratch
+    void* d_T = nullptr;
+    void* d_pfpart = nullptr;
+    size_t pfpart_bytes = 0;
+    void* d_corrpart = nullptr;
+    size_t corrpart_bytes = 0;
+    double* d_part = nullptr;   // 8 slots x kNumPart x kMaxK
+    double* d_pfraw = nullptr;  // [npf][K] reduced pairing-block sums
+    double* d_scal = nullptr;
+    int* d_stop = nullptr;
+    // CG vectors
+    double *d_x64 = nullptr, *d_r64 = nullptr, *d_p64 = nullptr, *d_q64 = nullptr, *d_t64 = nullptr;
+    float *d_x32 = nullptr, *d_r32 = nullptr, *d_p32 = nullptr, *d_q32 = nullptr, *d_b32 = nullptr;
+    double* h_pinned = nullptr;  // small host staging
+
+    // measurement support (vmc_profile)
+    bool prof = false;
+    int64_t n_launch = 0;
+    struct PassRec { cudaEvent_t a, b; int kind; double bytes; };
+    std::vector<PassRec> recs;
+    std::vector<cudaEvent_t> ev_pool;
+    double acc_ms[4] = {0, 0, 0, 0}, acc_bytes[4] = {0, 0, 0, 0};
+    int64_t acc_n[4] = {0, 0, 0, 0};
+    cudaEvent_t get_event() {
+        if (!ev_pool.empty()) { cudaEvent_t e = ev_pool.back(); ev_pool.pop_back(); return e; }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+
+    std::vector<void*> allocs;
+    template <typename T> cudaError_t alloc(T** p, size_t count) {
+        void* q = nullptr;
+        cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+        if (e == cudaSuccess) { allocs.push_back(q); *p = (T*)q; }
+        return e;
+    }
+    double* part(int slot) { return d_part + (size_t)slot * kNumPart * kMaxK; }
+};
+
+extern "C" const char* vmc_error_string(int code) {
+    switch (code) {
+        case VMC_OK: return "ok";
+        case VMC_ERR_INVALID_ARG: return "invalid argument";
+        case VMC_ERR_OOM: return "out of device memory";
+        case VMC_ERR_SINGULAR: return "singular pairing submatrix or zero correlator amplitude";
+        case VMC_ERR_NONFINITE: return "non-finite value";
+        case VMC_ERR_NOT_CONVERGED: return "solver did not reach the tolerance";
+        case VMC_ERR_TIMEOUT: return "timeout";
+        case VMC_ERR_CUDA: return "CUDA error";
+        case VMC_ERR_UNSUPPORTED: return "unsupported configuration";
+        case VMC_ERR_STATE: return "call out of order (parameters, walkers or samples missing)";
+        default: return "unknown error";
+    }
+}
+
+extern "C" const char* vmc_last_error_detail(void) { return g_err.c_str(); }
+
+// ---------------------------------------------------------------------------
+// creation
+// ---------------------------------------------------------------------------
+extern "C" int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, const vmc_ansatz* ans,
+                          const vmc_options* opt, vmc_handle* out) {
+    if (!lat || !ham || !ans || !opt || !out) return VMC_ERR_INVALID_ARG;
+    *out = nullptr;
+    const int ns = lat->n_sites, nu = ans->n_up, nd = ans->n_dn, N = nu + nd;
+    if (ns < 1 || ns > 64 || nu < 0 || nd < 0 || nu > ns || nd > ns || N < 2 || (N & 1) || N > 64)
+        return VMC_ERR_INVALID_ARG;
+    if (opt->n_walkers < 1 || opt->samples_per_walker < 1) return VMC_ERR_INVALID_ARG;
+    if (opt->walker_precision != VMC_FP64 && opt->walker_precision != VMC_FP32) return VMC_ERR_INVALID_ARG;
+    if (ham->kind != VMC_HUBBARD && ham->kind != VMC_ABINITIO) return VMC_ERR_INVALID_ARG;
+    if (ham->kind == VMC_ABINITIO) {
+        set_err("ab initio local energy not available in this build");
+        return VMC_ERR_UNSUPPORTED;
+    }
+    if (ans->n_corr < 0 || (ans->n_corr > 0 && (!ans->corr_ptr || !ans->corr_sites))) return VMC_ERR_INVALID_ARG;
+    if (lat->n_bonds < 0 || (lat->n_bonds > 0 && (!lat->bonds || !lat->bond_t))) return VMC_ERR_INVALID_ARG;
+
+    vmc_ctx* h = new vmc_ctx();
+    h->ns = ns; h->M = 2 * ns; h->nu = nu; h->nd = nd; h->N = N; h->ncorr = ans->n_corr;
+    h->P = nu * (nu - 1) / 2 + nd * (nd - 1) / 2 + nu * nd;
+    h->npf = h->M * (h->M - 1) / 2;
+    h->n_walkers = opt->n_walkers;
+    h->spw = opt->samples_per_walker;
+    h->ncap = (int64_t)opt->n_walkers * opt->samples_per_walker;
+    h->wprec = opt->walker_precision;
+    h->keep64 = opt->keep_fp64_store ? 1 : 0;
+    h->keeplow = opt->keep_lowp_store ? 1 : 0;
+    h->ham = ham->kind;
+    auto fail = [&](int code) { vmc_destroy(h); return code; };
+    if (h->ncap > (int64_t)1 << 31) return fail(VMC_ERR_INVALID_ARG);
+    if (!h->keep64 && !h->keeplow) return fail(VMC_ERR_INVALID_ARG);
+
+    // correlators
+    std::vector<int> cptr(h->ncorr + 1, 0), csites;
+    h->corr_off.assign(h->ncorr + 1, 0);
+    std::vector<std::vector<std::pair<int, int>>> memb(ns);
+    for (int c = 0; c < h->ncorr; ++c) {
+        int b = ans->corr_ptr[c], e = ans->corr_ptr[c + 1];
+        int m = e - b;
+        if (m < 1 || m > 6) return fail(VMC_ERR_INVALID_ARG);
+        int w = 1;
+        for (int j = b; j < e; ++j) {
+            int s = ans->corr_sites[j];
+            if (s < 0 || s >= ns) return fail(VMC_ERR_INVALID_ARG);
+            for (int j2 = b; j2 < j; ++j2)
+                if (ans->corr_sites[j2] == s) return fail(VMC_ERR_INVALID_ARG);
+            csites.push_back(s);
+            memb[s].push_back({c, w});
+            w *= 4;
+        }
+        cptr[c + 1] = (int)csites.size();
+        h->corr_off[c + 1] = h->corr_off[c] + ((int64_t)1 << (2 * m));
+        h->maxd = std::max(h->maxd, 1 << (2 * m));
+    }
+    h->ncp = h->corr_off[h->ncorr];
+    h->nv = h->ncp + h->npf;
+    std::vector<int> scptr(ns + 1, 0), scorr, sw;
+    for (int s = 0; s < ns; ++s) {
+        for (auto& pr : memb[s]) { scorr.push_back(pr.first); sw.push_back(pr.second); }
+        scptr[s + 1] = (int)scorr.size();
+    }
+    // hopping lists (each bond hops both ways; repeated bonds repeat)
+    std::vector<std::vector<std::pair<int, double>>> nb(ns);
+    for (int b = 0; b < lat->n_bonds; ++b) {
+        int i = lat->bonds[2 * b], j = lat->bonds[2 * b + 1];
+        if (i < 0 || j < 0 || i >= ns || j >= ns) return fail(VMC_ERR_INVALID_ARG);
+        if (i == j) continue;
+        nb[i].push_back({j, lat->bond_t[b]});
+        nb[j].push_back({i, lat->bond_t[b]});
+    }
+    std::vector<int> nptr(ns + 1, 0), nsite;
+    std::vector<double> nt;
+    for (int s = 0; s < ns; ++s) {
+        for (auto& pr : nb[s]) { nsite.push_back(pr.first); nt.push_back(pr.second); }
+        nptr[s + 1] = (int)nsite.size();
+    }
+    // pairing block order: up-up triangle, down-down triangle, up-down rectangle
+    std::vector<uint16_t> pt;
+    for (int a = 0; a < nu; ++a)
+        for (int b = a + 1; b < nu; ++b) pt.push_back((uint16_t)(a | (b << 8)));
+    for (int a = nu; a < N; ++a)
+        for (int b = a + 1; b < N; ++b) pt.push_back((uint16_t)(a | (b << 8)));
+    for (int a = 0; a < nu; ++a)
+        for (int b = nu; b < N; ++b) pt.push_back((uint16_t)(a | (b << 8)));
+    std::vector<int> rb(h->M);
+    for (int p = 0; p < h->M; ++p) rb[p] = (int)pf_row_base(h->M, p);
+
+    if (cudaGetDevice(&h->dev) != cudaSuccess) return fail(VMC_ERR_CUDA);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, h->dev) != cudaSuccess) return fail(VMC_ERR_CUDA);
+    h->nsm = prop.multiProcessorCount;
+    h->smem_optin = prop.sharedMemPerBlockOptin;
+
+#define ACK(x) do { if ((x) != cudaSuccess) { set_err(#x); return fail(VMC_ERR_OOM); } } while (0)
+#define UPL(dst, src, n) do { if (cudaMemcpy(dst, src, sizeof(*(dst)) * (n), cudaMemcpyHostToDevice) != cudaSuccess) return fail(VMC_ERR_CUDA); } while (0)
+    ACK(h->alloc(&h->d_corr_ptr, cptr.size()));
+    ACK(h->alloc(&h->d_corr_sites, csites.size()));
+    ACK(h->alloc(&h->d_corr_off, h->corr_off.size()));
+    ACK(h->alloc(&h->d_site_cptr, scptr.size()));
+    ACK(h->alloc(&h->d_site_corr, scorr.size()));
+    ACK(h->alloc(&h->d_site_w, sw.size()));
+    ACK(h->alloc(&h->d_nbr_ptr, nptr.size()));
+    ACK(h->alloc(&h->d_nbr_site, nsite.size()));
+    ACK(h->alloc(&h->d_nbr_t, nt.size()));
+    ACK(h->alloc(&h->d_pairtab, pt.size()));
+    ACK(h->alloc(&h->d_rowbase, rb.size()));
+    UPL(h->d_corr_ptr, cptr.data(), cptr.size());
+    if (!csites.empty()) UPL(h->d_corr_sites, csites.data(), csites.size());
+    UPL(h->d_corr_off, h->corr_off.data(), h->corr_off.size());
+    UPL(h->d_site_cptr, scptr.data(), scptr.size());
+    if (!scorr.empty()) UPL(h->d_site_corr, scorr.data(), scorr.size());
+    if (!sw.empty()) UPL(h->d_site_w, sw.data(), sw.size());
+    UPL(h->d_nbr_ptr, nptr.data(), nptr.size());
+    if (!nsite.empty()) UPL(h->d_nbr_site, nsite.data(), nsite.size());
+    if (!nt.empty()) UPL(h->d_nbr_t, nt.data(), nt.size());
+    UPL(h->d_pairtab, pt.data(), pt.size());
+    UPL(h->d_rowbase, rb.data(), rb.size());
+    // parameters
+    ACK(h->alloc(&h->d_C64, h->ncp));
+    ACK(h->alloc(&h->d_invC64, h->ncp));
+    ACK(h->alloc(&h->d_C32, h->ncp));
+    ACK(h->alloc(&h->d_invC32, h->ncp));
+    ACK(h->alloc(&h->d_F64, (size_t)h->M * h->M));
+    ACK(h->alloc(&h->d_F32, (size_t)h->M * h->M));
+    // walkers
+    ACK(h->alloc(&h->d_wocc, (size_t)h->n_walkers * N));
+    ACK(h->alloc(&h->d_wstep, h->n_walkers));
+    ACK(h->alloc(&h->d_mocc, (size_t)h->ncap * N));
+    // O store
+    h->Nst = (int)round_up(N, 16);
+    h->ncst = (int)round_up(std::max(h->ncorr, 1), 8);
+    h->Pst = round_up(h->P, 8);
+    ACK(h->alloc(&h->d_socc, (size_t)h->ncap * h->Nst));
+    ACK(h->alloc(&h->d_cidx, (size_t)h->ncap * h->ncst));
+    ACK(h->alloc(&h->d_cidxT, (size_t)h->ncap * std::max(h->ncorr, 1)));
+    ACK(h->alloc(&h->d_E, h->ncap));
+    if (h->keep64) ACK(h->alloc(&h->d_pf64, (size_t)h->ncap * h->Pst));
+    if (h->keeplow) {
+        ACK(h->alloc(&h->d_pf32, (size_t)h->ncap * h->Pst));
+        ACK(h->alloc(&h->d_pf16, (size_t)h->ncap * h->Pst));
+    }
+    for (int k = 0; k < 3; ++k) ACK(h->alloc(&h->d_Obar[k], h->nv));
+    ACK(h->alloc(&h->d_status, 4));
+    // scratch
+    ACK(h->alloc((double**)&h->d_T, (size_t)h->ncap * kMaxK));
+    h->pfpart_bytes = (size_t)4 * h->nsm * h->npf * kMaxK * sizeof(double);
+    ACK(h->alloc((char**)&h->d_pfpart, h->pfpart_bytes));
+    h->corrpart_bytes = (size_t)16 * std::max<int64_t>(h->ncp, 1) * kMaxK * sizeof(double);
+    ACK(h->alloc((char**)&h->d_corrpart, h->corrpart_bytes));
+    ACK(h->alloc(&h->d_part, (size_t)8 * kNumPart * kMaxK));
+    ACK(h->alloc(&h->d_pfraw, (size_t)h->npf * kMaxK));
+    ACK(h->alloc(&h->d_scal, 16));
+    ACK(h->alloc(&h->d_stop, 4));
+    const size_t vk = (size_t)h->nv * kMaxK;
+    ACK(h->alloc(&h->d_x64, vk)); ACK(h->alloc(&h->d_r64, vk)); ACK(h->alloc(&h->d_p64, vk));
+    ACK(h->alloc(&h->d_q64, vk)); ACK(h->alloc(&h->d_t64, vk));
+    ACK(h->alloc(&h->d_x32, vk)); ACK(h->alloc(&h->d_r32, vk)); ACK(h->alloc(&h->d_p32, vk));
+    ACK(h->alloc(&h->d_q32, vk)); ACK(h->alloc(&h->d_b32, vk));
+    if (cudaMallocHost((void**)&h->h_pinned, 64 * sizeof(double)) != cudaSuccess) return fail(VMC_ERR_OOM);
+    if (cudaMemset(h->d_status, 0, 4 * sizeof(int)) != cudaSuccess) return fail(VMC_ERR_CUDA);
+    if (cudaMemset(h->d_wstep, 0, sizeof(uint64_t) * h->n_walkers) != cudaSuccess) return fail(VMC_ERR_CUDA);
+#undef ACK
+#undef UPL
+
+    DevProblem& pb = h->pb;
+    pb.ns = ns; pb.M = h->M; pb.nu = nu; pb.nd = nd; pb.N = N; pb.ncorr = h->ncorr; pb.P = h->P;
+    pb.npf = h->npf; pb.ham = h->ham; pb.ncp = h->ncp; pb.nv = h->nv; pb.U = ham->U;
+    pb.corr_ptr = h->d_corr_ptr; pb.corr_sites = h->d_corr_sites; pb.corr_off = h->d_corr_off;
+    pb.site_cptr = h->d_site_cptr; pb.site_corr = h->d_site_corr; pb.site_w = h->d_site_w;
+    pb.nbr_ptr = h->d_nbr_ptr; pb.nbr_site = h->d_nbr_site; pb.nbr_t = h->d_nbr_t;
+    pb.h = h->d_h; pb.eri = h->d_eri;
+    pb.C64 = h->d_C64; pb.C32 = h->d_C32; pb.F64 = h->d_F64; pb.F32 = h->d_F32;
+    pb.pairtab = h->d_pairtab; pb.rowbase = h->d_rowbase;
+    *out = h;
+    return VMC_OK;
+}
+
+extern "C" int vmc_destroy(vmc_handle h) {
+    if (!h) return VMC_OK;
+    for (auto& r : h->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : h->ev_pool) cudaEventDestroy(e);
+    for (void* p : h->allocs) cudaFree(p);
+    if (h->h_pinned) cudaFreeHost(h->h_pinned);
+    delete h;
+    return VMC_OK;
+}
+
+extern "C" int vmc_num_params(vmc_handle h, int64_t* n_v, int64_t* n_corr_params) {
+    if (!h) return VMC_ERR_INVALID_ARG;
+    if (n_v) *n_v = h->nv;
+    if (n_corr_params) *n_corr_params = h->ncp;
+    return VMC_OK;
+}
+
+extern "C" int vmc_num_samples(vmc_handle h, int64_t* n_s) {
+    if (!h || !n_s) return VMC_ERR_INVALID_ARG;
+    *n_s = h->n_s;
+    return VMC_OK;
+}
+
+extern "C" int vmc_set_params(vmc_handle h, const double* C, const double* f) {
+    if (!h || (!C && h->ncp > 0) || !f) return VMC_ERR_INVALID_ARG;
+    const int M = h->M;
+    std::vector<double> c64(C, C + h->ncp), ic64(h->ncp), F64((size_t)M * M, 0.0);
+    std::vector<float> c32(h->ncp), ic32(h->ncp), F32((size_t)M * M, 0.f);
+    for (int64_t k = 0; k < h->ncp; ++k) {
+        if (C[k] == 0.0 || !std::isfinite(C[k])) return VMC_ERR_SINGULAR;
+        ic64[k] = 1.0 / C[k];
+        c32[k] = (float)C[k];
+        ic32[k] = (float)ic64[k];
+    }
+    for (int p = 0; p < M; ++p)
+        for (int q = p + 1; q < M; ++q) {
+            double v = f[pf_row_base(M, p) + q];
+            if (!std::isfinite(v)) return VMC_ERR_NONFINITE;
+            F64[(size_t)p * M + q] = v;
+            F64[(size_t)q * M + p] = -v;
+            F32[(size_t)p * M + q] = (float)v;
+            F32[(size_t)q * M + p] = -(float)v;
+        }
+    VCK(cudaMemcpy(h->d_C64, c64.data(), sizeof(double) * h->ncp, cudaMemcpyHostToDevice));
+    VCK(cudaMemcpy(h->d_invC64, ic64.data(), sizeof(double) * h->ncp, cudaMemcpyHostToDevice));
+    VCK(cudaMemcpy(h->d_C32, c32.data(), sizeof(float) * h->ncp, cudaMemcpyHostToDevice));
+    VCK(cudaMemcpy(h->d_invC32, ic32.data(), sizeof(float) * h->ncp, cudaMemcpyHostToDevice));
+    VCK(cudaMemcpy(h->d_F64, F64.data(), sizeof(double) * M * M, cudaMemcpyHostToDevice));
+    VCK(cudaMemcpy(h->d_F32, F32.data(), sizeof(float) * M * M, cudaMemcpyHostToDevice));
+    h->params_set = true;
+    h->obar_ok[0] = h->obar_ok[1] = h->obar_ok[2] = false;
+    return VMC_OK;
+}
+
+static int check_configs(const vmc_ctx* h, const uint8_t* occ, int64_t n) {
+    for (int64_t w = 0; w < n; ++w) {
+        const uint8_t* o = occ + w * h->N;
+        for (int a = 0; a < h->N; ++a) {
+            if (o[a] >= h->M) return VMC_ERR_INVALID_ARG;
+            if (a > 0 && o[a] <= o[a - 1]) return VMC_ERR_INVALID_ARG;
+            if ((a < h->nu) != (o[a] < h->ns)) return VMC_ERR_INVALID_ARG;
+        }
+    }
+    return VMC_OK;
+}
+
+extern "C" int vmc_set_walkers(vmc_handle h, const uint8_t* occ, const uint64_t* step) {
+    if (!h || !occ) return VMC_ERR_INVALID_ARG;
+    int rc = check_configs(h, occ, h->n_walkers);
+    if (rc) return rc;
+    VCK(cudaMemcpy(h->d_wocc, occ, (size_t)h->n_walkers * h->N, cudaMemcpyHostToDevice));
+    if (step) VCK(cudaMemcpy(h->d_wstep, step, sizeof(uint64_t) * h->n_walkers, cudaMemcpyHostToDevice));
+    else VCK(cudaMemset(h->d_wstep, 0, sizeof(uint64_t) * h->n_walkers));
+    h->walkers_set = true;
+    return VMC_OK;
+}
+
+extern "C" int vmc_get_walkers(vmc_handle h, uint8_t* occ, uint64_t* step, void* stream) {
+    if (!h) return VMC_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    VCK(cudaStreamSynchronize(st));
+    if (occ) VCK(cudaMemcpy(occ, h->d_wocc, (size_t)h->n_walkers * h->N, cudaMemcpyDeviceToHost));
+    if (step) VCK(cudaMemcpy(step, h->d_wstep, sizeof(uint64_t) * h->n_walkers, cudaMemcpyDeviceToHost));
+    return VMC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// walker kernels
+// ---------------------------------------------------------------------------
+static int read_status(vmc_ctx* h, cudaStream_t st) {
+    int s = 0;
+    VCK(cudaMemcpyAsync(h->h_pinned, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    VCK(cudaStreamSynchronize(st));
+    memcpy(&s, h->h_pinned, sizeof(int));
+    VCK(cudaMemsetAsync(h->d_status, 0, sizeof(int), st));
+    if (s & ST_BAD_CONFIG) return VMC_ERR_INVALID_ARG;
+    if (s & ST_SINGULAR) return VMC_ERR_SINGULAR;
+    if (s & ST_NONFINITE) return VMC_ERR_NONFINITE;
+    if (s & ST_TIMEOUT) return VMC_ERR_TIMEOUT;
+    return VMC_OK;
+}
+
+static int launch_walkers(vmc_ctx* h, SampleArgs& a, bool fp64, cudaStream_t st) {
+    a.pb = h->pb;
+    a.XS = h->N + 1;
+    a.ncorr_pad = (int)round_up(std::max(h->ncorr, 1), 4);
+    const size_t rsz = fp64 ? 8 : 4;
+    size_t wb = (size_t)h->N * a.XS * rsz + 3 * (size_t)a.XS * rsz;
+    wb = round_up(wb, 16) + 64 * 4 + (size_t)a.ncorr_pad * 4 + 64 + 128;
+    wb = round_up(wb, 16);
+    a.warp_bytes = wb;
+    int wpb = (int)std::min<size_t>(4, h->smem_optin / wb);
+    if (wpb < 1) return VMC_ERR_UNSUPPORTED;
+    size_t smem = wb * wpb;
+    int blocks = (a.n_walkers + wpb - 1) / wpb;
+    a.status = h->d_status;
+    if (fp64) {
+        VCK(cudaFuncSetAttribute(k_walkers<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_walkers<double><<<blocks, 32 * wpb, smem, st>>>(a); h->n_launch++;
+    } else {
+        VCK(cudaFuncSetAttribute(k_walkers<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_walkers<float><<<blocks, 32 * wpb, smem, st>>>(a); h->n_launch++;
+    }
+    VCK(cudaGetLastError());
+    return VMC_OK;
+}
+
+static void store_targets(vmc_ctx* h, SampleArgs& a) {
+    a.s_occ = h->d_socc; a.Nst = h->Nst;
+    a.s_cidx = h->d_cidx; a.ncst = h->ncst;
+    a.s_E = h->d_E;
+    a.s_pf64 = h->keep64 ? h->d_pf64 : nullptr;
+    a.s_pf32 = h->keeplow ? h->d_pf32 : nullptr;
+    a.s_pf16 = h->keeplow ? h->d_pf16 : nullptr;
+    a.Pst = h->Pst;
+}
+
+static int transpose_states(vmc_ctx* h, cudaStream_t st) {
+    if (h->ncorr == 0 || h->n_s == 0) return VMC_OK;
+    dim3 grid((unsigned)((h->n_s + 31) / 32), (unsigned)((h->ncorr + 31) / 32));
+    k_transpose_cidx<<<grid, 256, 0, st>>>(h->d_cidx, h->ncst, h->ncorr, h->n_s, h->d_cidxT); h->n_launch++;
+    VCK(cudaGetLastError());
+    return VMC_OK;
+}
+
+extern "C" int vmc_sample(vmc_handle h, int n_burn, uint64_t seed, void* stream) {
+    if (!h || n_burn < 0) return VMC_ERR_INVALID_ARG;
+    if (!h->params_set || !h->walkers_set) return VMC_ERR_STATE;
+    cudaStream_t st = (cudaStream_t)stream;
+    SampleArgs a{};
+    a.n_walkers = h->n_walkers;
+    a.spw = h->spw;
+    a.n_burn = n_burn;
+    a.props_per_sweep = h->N;
+    a.write_back = 1;
+    a.want_energy = 1;
+    a.seed = seed;
+    a.walker_occ = h->d_wocc;
+    a.walker_step = h->d_wstep;
+    store_targets(h, a);
+    int rc = launch_walkers(h, a, h->wprec == VMC_FP64, st);
+    if (rc) return rc;
+    h->n_s = h->ncap;
+    h->obar_ok[0] = h->obar_ok[1] = h->obar_ok[2] = false;
+    rc = transpose_states(h, st);
+    if (rc) return rc;
+    return read_status(h, st);
+}
+
+static int measure_device_configs(vmc_ctx* h, int64_t n_s, bool fp64, const double* bw, double* bgrad,
+                                  bool to_store, cudaStream_t st) {
+    SampleArgs a{};
+    a.n_walkers = (int)n_s;
+    a.spw = 1;
+    a.n_burn = 0;
+    a.props_per_sweep = 0;
+    a.write_back = 0;
+    a.want_energy = bgrad ? 0 : 1;
+    a.walker_occ = h->d_mocc;
+    a.walker_step = nullptr;
+    if (to_store) store_targets(h, a);
+    a.bw = bw;
+    a.bgrad = bgrad;
+    return launch_walkers(h, a, fp64, st);
+}
+
+extern "C" int vmc_measure(vmc_handle h, const uint8_t* occ, int64_t n_s, void* stream) {
+    if (!h || !occ || n_s < 1 || n_s > h->ncap) return VMC_ERR_INVALID_ARG;
+    if (!h->params_set) return VMC_ERR_STATE;
+    int rc = check_configs(h, occ, n_s);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    VCK(cudaMemcpyAsync(h->d_mocc, occ, (size_t)n_s * h->N, cudaMemcpyHostToDevice, st));
+    rc = measure_device_configs(h, n_s, h->wprec == VMC_FP64, nullptr, nullptr, true, st);
+    if (rc) return rc;
+    h->n_s = n_s;
+    h->obar_ok[0] = h->obar_ok[1] = h->obar_ok[2] = false;
+    rc = transpose_states(h, st);
+    if (rc) return rc;
+    return read_status(h, st);
+}
+
+extern "C" int vmc_get_samples(vmc_handle h, uint8_t* occ, double* E_L, uint16_t* corr_state, double* pf,
+                               int store, void* stream) {
+    if (!h) return VMC_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    VCK(cudaStreamSynchronize(st));
+    const int64_t n = h->n_s;
+    if (occ) VCK(cudaMemcpy2D(occ, h->N, h->d_socc, h->Nst, h->N, n, cudaMemcpyDeviceToHost));
+    if (E_L) VCK(cudaMemcpy(E_L, h->d_E, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    if (corr_state && h->ncorr > 0)
+        VCK(cudaMemcpy2D(corr_state, sizeof(uint16_t) * h->ncorr, h->d_cidx, sizeof(uint16_t) * h->ncst,
+                         sizeof(uint16_t) * h->ncorr, n, cudaMemcpyDeviceToHost));
+    if (pf) {
+        if (store == VMC_STORE_FP64) {
+            if (!h->d_pf64) return VMC_ERR_STATE;
+            VCK(cudaMemcpy2D(pf, sizeof(double) * h->P, h->d_pf64, sizeof(double) * h->Pst, sizeof(double) * h->P, n,
+                             cudaMemcpyDeviceToHost));
+        } else if (store == VMC_STORE_FP32 || store == VMC_STORE_FP32_F32ACC) {
+            if (!h->d_pf32) return VMC_ERR_STATE;
+            std::vector<float> tmp((size_t)n * h->P);
+            VCK(cudaMemcpy2D(tmp.data(), sizeof(float) * h->P, h->d_pf32, sizeof(float) * h->Pst, sizeof(float) * h->P,
+                             n, cudaMemcpyDeviceToHost));
+            for (size_t i = 0; i < tmp.size(); ++i) pf[i] = tmp[i];
+        } else if (store == VMC_STORE_BF16) {
+            if (!h->d_pf16) return VMC_ERR_STATE;
+            std::vector<uint16_t> tmp((size_t)n * h->P);
+            VCK(cudaMemcpy2D(tmp.data(), 2 * h->P, h->d_pf16, 2 * h->Pst, 2 * h->P, n, cudaMemcpyDeviceToHost));
+            for (size_t i = 0; i < tmp.size(); ++i) {
+                uint32_t b = (uint32_t)tmp[i] << 16;
+                float f;
+                memcpy(&f, &b, 4);
+                pf[i] = f;
+            }
+        } else {
+            return VMC_ERR_INVALID_ARG;
+        }
+    }
+    return VMC_OK;
+}
+
+extern "C" int vmc_logpsi(vmc_handle h, double* out, void* stream) {
+    if (!h || !out) return VMC_ERR_INVALID_ARG;
+    if (!h->params_set || h->n_s == 0) return VMC_ERR_STATE;
+    cudaStream_t st = (cudaStream_t)stream;
+    LogPsiArgs a{};
+    a.pb = h->pb;
+    a.n_s = h->n_s;
+    a.s_occ = h->d_socc; a.Nst = h->Nst;
+    a.s_cidx = h->d_cidx; a.ncst = h->ncst;
+    a.XS = h->N + 1;
+    a.warp_bytes = round_up((size_t)h->N * a.XS * 8 + 2 * (size_t)a.XS * 8, 16);
+    int wpb = 4;
+    size_t smem = a.warp_bytes * wpb;
+    a.out = out;
+    VCK(cudaFuncSetAttribute(k_logpsi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_logpsi<<<(unsigned)((h->n_s + wpb - 1) / wpb), 32 * wpb, smem, st>>>(a); h->n_launch++;
+    VCK(cudaGetLastError());
+    return VMC_OK;
+}
+
+extern "C" int vmc_logpsi_backward(vmc_handle h, const double* w, double* grad, void* stream) {
+    if (!h || (w && !grad)) return VMC_ERR_INVALID_ARG;
+    if (!h->params_set || h->n_s == 0) return VMC_ERR_STATE;
+    cudaStream_t st = (cudaStream_t)stream;
+    VCK(cudaMemcpy2DAsync(h->d_mocc, h->N, h->d_socc, h->Nst, h->N, h->n_s, cudaMemcpyDeviceToDevice, st));
+    int rc;
+    if (w) {
+        VCK(cudaMemsetAsync(grad, 0, sizeof(double) * h->nv, st));
+        rc = measure_device_configs(h, h->n_s, true, w, grad, false, st);
+    } else {
+        rc = measure_device_configs(h, h->n_s, true, nullptr, nullptr, true, st);
+        h->obar_ok[0] = h->obar_ok[1] = h->obar_ok[2] = false;
+    }
+    if (rc) return rc;
+    return read_status(h, st);
+}
+
+// ---------------------------------------------------------------------------
+// streaming passes over the O store
+// ---------------------------------------------------------------------------
+template <typename ST, typename AT, int K, bool G>
+static int launch_main(vmc_ctx* h, const void* s_pf, const AT* V, const AT* invC, AT* T, const int* stop,
+                       cudaStream_t st, int* nblk) {
+    const int threads = 512;
+    size_t smem = (size_t)h->npf * K * sizeof(AT) * (G ? 2 : 1) + (size_t)h->M * 4 + 16 * 64;
+    if (smem > h->smem_optin) { set_err("pairing block does not fit in shared memory"); return VMC_ERR_UNSUPPORTED; }
+    auto kern = k_sr_main<ST, AT, K, G>;
+    VCK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    VCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+    per_sm = std::max(1, std::min(per_sm, 4));
+    int grid = h->nsm * per_sm;
+    int64_t need = (h->n_s + 15) / 16;
+    if (need < grid) grid = (int)std::max<int64_t>(1, need);
+    if ((size_t)grid * h->npf * K * sizeof(AT) > h->pfpart_bytes) return VMC_ERR_UNSUPPORTED;
+    const int kind = sizeof(ST) == 8 ? VMC_STORE_FP64
+                     : sizeof(ST) == 2 ? VMC_STORE_BF16
+                     : (sizeof(AT) == 8 ? VMC_STORE_FP32 : VMC_STORE_FP32_F32ACC);
+    vmc_ctx::PassRec rec{};
+    if (h->prof) {
+        rec.a = h->get_event();
+        rec.b = h->get_event();
+        rec.kind = kind;
+        rec.bytes = (double)h->n_s * (2.0 * h->ncorr + h->N + (double)h->P * sizeof(ST));
+        VCK(cudaEventRecord(rec.a, st));
+    }
+    MainArgs<AT> a{};
+    a.pb = h->pb;
+    a.n_s = h->n_s;
+    a.s_occ = h->d_socc; a.Nst = h->Nst;
+    a.s_cidx = h->d_cidx; a.ncst = h->ncst;
+    a.s_pf = s_pf; a.Pst = h->Pst;
+    a.V = V; a.invC = invC; a.T = T;
+    a.pf_partial = (AT*)h->d_pfpart;
+    a.stop = stop;
+    kern<<<grid, threads, smem, st>>>(a);
+    VCK(cudaGetLastError());
+    h->n_launch++;
+    if (h->prof) {
+        VCK(cudaEventRecord(rec.b, st));
+        h->recs.push_back(rec);
+    }
+    *nblk = grid;
+    return VMC_OK;
+}
+
+// TMA-staged pass for FP32 accumulation (BF16 / FP32 stores); returns
+// VMC_ERR_UNSUPPORTED when the problem does not fit its layout, and the
+// caller then uses the generic pass.
+template <typename ST, int K>
+static int launch_stream(vmc_ctx* h, const void* s_pf, const float* V, const float* invC, float* T, const int* stop,
+                         cudaStream_t st, int* nblk) {
+    if (h->nu > 32 || h->nd > 32) return VMC_ERR_UNSUPPORTED;
+    const size_t buf = (size_t)round_up(h->Nst + 2 * h->ncst + h->Pst * (int64_t)sizeof(ST), 128);
+    const size_t fixed = (size_t)round_up((int64_t)h->npf * K * 8 + (int64_t)(h->ncorr + 1) * 4, 16) + 128;
+    int nw = 16;
+    while (nw > 1 && fixed + (size_t)nw * (2 * buf + 16) > h->smem_optin) --nw;
+    const size_t smem = fixed + (size_t)nw * (2 * buf + 16);
+    if (smem > h->smem_optin || nw < 4) return VMC_ERR_UNSUPPORTED;
+    auto kern = k_sr_stream<ST, K>;
+    VCK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int grid = h->nsm;
+    int64_t need = (h->n_s + nw - 1) / nw;
+    if (need < grid) grid = (int)std::max<int64_t>(1, need);
+    if ((size_t)grid * h->npf * K * sizeof(float) > h->pfpart_bytes) return VMC_ERR_UNSUPPORTED;
+    const int kind = sizeof(ST) == 2 ? VMC_STORE_BF16 : VMC_STORE_FP32_F32ACC;
+    vmc_ctx::PassRec rec{};
+    if (h->prof) {
+        rec.a = h->get_event();
+        rec.b = h->get_event();
+        rec.kind = kind;
+        rec.bytes = (double)h->n_s * (2.0 * h->ncorr + h->N + (double)h->P * sizeof(ST));
+        VCK(cudaEventRecord(rec.a, st));
+    }
+    StreamArgs a{};
+    a.pb = h->pb;
+    a.n_s = h->n_s;
+    a.s_occ = h->d_socc; a.Nst = h->Nst;
+    a.s_cidx = h->d_cidx; a.ncst = h->ncst;
+    a.s_pf = s_pf; a.Pst = h->Pst; a.st_bytes = (int)sizeof(ST);
+    a.V = V; a.invC = invC; a.T = T;
+    a.pf_partial = (float*)h->d_pfpart;
+    a.stop = stop;
+    a.status = h->d_status;
+    a.buf_bytes = buf;
+    kern<<<grid, 32 * nw, smem, st>>>(a);
+    VCK(cudaGetLastError());
+    h->n_launch++;
+    if (h->prof) {
+        VCK(cudaEventRecord(rec.b, st));
+        h->recs.push_back(rec);
+    }
+    *nblk = grid;
+    return VMC_OK;
+}
+
+static int corr_chunks(const vmc_ctx* h) {
+    int nc = std::max(1, h->ncorr);
+    int ch = (2 * h->nsm + nc - 1) / nc;
+    return std::max(1, std::min(ch, 16));
+}
+
+template <typename AT, int K>
+static int launch_corr(vmc_ctx* h, const AT* T, const int* stop, cudaStream_t st, int* nchunk) {
+    *nchunk = corr_chunks(h);
+    if (h->ncorr == 0) return VMC_OK;
+    size_t smem = (size_t)h->maxd * K * sizeof(AT);
+    if (smem > h->smem_optin) return VMC_ERR_UNSUPPORTED;
+    auto kern = k_corr_scatter<AT, K>;
+    VCK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CorrArgs<AT> a{};
+    a.pb = h->pb;
+    a.n_s = h->n_s;
+    a.cidxT = h->d_cidxT;
+    a.T = T;
+    a.corr_partial = (AT*)h->d_corrpart;
+    a.nchunk = *nchunk;
+    a.stop = stop;
+    kern<<<h->ncorr * *nchunk, 256, smem, st>>>(a); h->n_launch++;
+    VCK(cudaGetLastError());
+    return VMC_OK;
+}
+
+template <typename AT>
+static int reduce_pf(vmc_ctx* h, int nblk, int K, cudaStream_t st) {
+    const int n = h->npf * K;
+    k_reduce_pf<AT><<<(n + 31) / 32, 256, 0, st>>>((const AT*)h->d_pfpart, nblk, n, h->d_pfraw); h->n_launch++;
+    VCK(cudaGetLastError());
+    return VMC_OK;
+}
+
+static int fin_grid(const vmc_ctx* h) {
+    int64_t g = (h->nv + 255) / 256;
+    // its partial dots go to a kNumPart-sized slot
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, kNumPart));
+}
+
+// out = (S + shift I) V with K vectors, V/out in AT precision ([K][nv]).
+// obv_part holds kNumPart partial dots Obar . V unless null (then computed).
+template <typename ST, typename AT, int K>
+static int apply_S_impl(vmc_ctx* h, const void* s_pf, const double* Obar, const AT* V, AT* out, double shift,
+                        const int* stop, const double* obv_part, double* dot_part, cudaStream_t st) {
+    const AT* invC;
+    if (sizeof(AT) == 8) invC = (const AT*)h->d_invC64;
+    else invC = (const AT*)h->d_invC32;
+    AT* T = (AT*)h->d_T;
+    int nblk = 0, nchunk = 0;
+    int rc = VMC_ERR_UNSUPPORTED;
+    if constexpr (sizeof(AT) == 4 && K <= 2) {
+        if (h->use_stream)
+            rc = launch_stream<ST, K>(h, s_pf, (const float*)V, (const float*)invC, (float*)T, stop, st, &nblk);
+    }
+    if (rc == VMC_ERR_UNSUPPORTED) rc = launch_main<ST, AT, K, true>(h, s_pf, V, invC, T, stop, st, &nblk);
+    if (rc) return rc;
+    rc = launch_corr<AT, K>(h, T, stop, st, &nchunk);
+    if (rc) return rc;
+    rc = reduce_pf<AT>(h, nblk, K, st);
+    if (rc) return rc;
+    if (!obv_part) {
+        k_dot_part<double, AT, K><<<kNumPart, 256, 0, st>>>(Obar, V, h->nv, h->part(0), stop); h->n_launch++;
+        VCK(cudaGetLastError());
+        obv_part = h->part(0);
+    }
+    FinArgs<AT, AT> f{};
+    f.pb = h->pb;
+    f.n_s = h->n_s;
+    f.n_pf_part = nblk;
+    f.nchunk = h->ncorr ? nchunk : 0;
+    f.pf_partial = (const AT*)h->d_pfpart;
+    f.pf_raw = h->d_pfraw;
+    f.corr_partial = (const AT*)h->d_corrpart;
+    f.invC = invC;
+    f.Obar = Obar;
+    f.obv_part = obv_part;
+    f.n_obv_part = kNumPart;
+    f.V = V;
+    f.shift = shift;
+    f.out = out;
+    f.dot_part = dot_part;
+    f.stop = stop;
+    k_finalize_S<AT, AT, K><<<fin_grid(h), 256, 0, st>>>(f); h->n_launch++;
+    VCK(cudaGetLastError());
+    return VMC_OK;
+}
+
+static int store_kind(int store) {
+    switch (store) {
+        case VMC_STORE_FP64: return 0;
+        case VMC_STORE_FP32:
+        case VMC_STORE_FP32_F32ACC: return 1;
+        case VMC_STORE_BF16: return 2;
+        default: return -1;
+    }
+}
+
+static const void* store_ptr(const vmc_ctx* h, int kind) {
+    return kind == 0 ? (const void*)h->d_pf64 : kind == 1 ? (const void*)h->d_pf32 : (const void*)h->d_pf16;
+}
+
+// Obar_kind = mean of O over the samples as stored in store `kind`, and
+// g = <E_L O> - <E_L> Obar (both FP64 accumulation): one pass with t_s = (1, E_s).
+static int gradient_pass(vmc_ctx* h, int kind, double* g, cudaStream_t st) {
+    const void* src = store_ptr(h, kind);
+    if (!src) return VMC_ERR_STATE;
+    double* T = (double*)h->d_T;
+    k_build_T_grad<<<kNumPart, 256, 0, st>>>(h->d_E, h->n_s, T, h->part(1)); h->n_launch++;
+    VCK(cudaGetLastError());
+    int nblk = 0, nchunk = 0, rc;
+    if (kind == 0) rc = launch_main<double, double, 2, false>(h, src, nullptr, nullptr, T, nullptr, st, &nblk);
+    else if (kind == 1) rc = launch_main<float, double, 2, false>(h, src, nullptr, nullptr, T, nullptr, st, &nblk);
+    else rc = launch_main<__nv_bfloat16, double, 2, false>(h, src, nullptr, nullptr, T, nullptr, st, &nblk);
+    if (rc) return rc;
+    rc = launch_corr<double, 2>(h, T, nullptr, st, &nchunk);
+    if (rc) return rc;
+    rc = reduce_pf<double>(h, nblk, 2, st);
+    if (rc) return rc;
+    FinArgs<double, double> f{};
+    f.pb = h->pb;
+    f.n_s = h->n_s;
+    f.n_pf_part = nblk;
+    f.nchunk = h->ncorr ? nchunk : 0;
+    f.pf_partial = (const double*)h->d_pfpart;
+    f.pf_raw = h->d_pfraw;
+    f.corr_partial = (const double*)h->d_corrpart;
+    f.invC = h->d_invC64;
+    f.Obar_out = h->d_Obar[kind];
+    f.g_out = g;
+    f.E_sum = h->part(1);
+    f.n_E_part = kNumPart;
+    k_finalize_grad<double><<<fin_grid(h), 256, 0, st>>>(f); h->n_launch++;
+    VCK(cudaGetLastError());
+    h->obar_ok[kind] = true;
+    return VMC_OK;
+}
+
+// the covariance of a store is formed with the mean of that same store, so
+// every low-precision operator is itself a covariance (positive semidefinite)
+static int ensure_obar(vmc_ctx* h, int kind, cudaStream_t st) {
+    if (h->obar_ok[kind]) return VMC_OK;
+    return gradient_pass(h, kind, h->d_t64, st);
+}
+
+extern "C" int sr_gradient(vmc_handle h, double* g, double* e_stats, int store, void* stream) {
+    if (!h || !g) return VMC_ERR_INVALID_ARG;
+    if (h->n_s == 0) return VMC_ERR_STATE;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (store != VMC_STORE_FP64 && store != VMC_STORE_FP32 && store != VMC_STORE_BF16) return VMC_ERR_INVALID_ARG;
+    int rc = gradient_pass(h, store_kind(store), g, st);
+    if (rc) return rc;
+    if (e_stats) {
+        std::vector<double> E(h->n_s);
+        VCK(cudaMemcpyAsync(E.data(), h->d_E, sizeof(double) * h->n_s, cudaMemcpyDeviceToHost, st));
+        VCK(cudaStreamSynchronize(st));
+        double m = 0.0;
+        for (double e : E) m += e;
+        m /= (double)h->n_s;
+        double v = 0.0;
+        for (double e : E) v += (e - m) * (e - m);
+        v /= (double)h->n_s;
+        // standard error from per-walker means (blocking over walkers)
+        int64_t nw = h->n_s / h->spw;
+        double se = 0.0;
+        if (nw > 1 && h->n_s == (int64_t)h->n_walkers * h->spw) {
+            double sm = 0.0, ss = 0.0;
+            for (int64_t w = 0; w < nw; ++w) {
+                double a = 0.0;
+                for (int j = 0; j < h->spw; ++j) a += E[w * h->spw + j];
+                a /= h->spw;
+                sm += a;
+                ss += a * a;
+            }
+            sm /= nw;
+            double var_w = (ss / nw - sm * sm) * nw / (nw - 1);
+            se = std::sqrt(std::max(0.0, var_w) / nw);
+        } else {
+            se = std::sqrt(v / std::max<int64_t>(1, h->n_s - 1));
+        }
+        e_stats[0] = m;
+        e_stats[1] = v;
+        e_stats[2] = se;
+    }
+    return VMC_OK;
+}
+
+static size_t main_smem(const vmc_ctx* h, int K, size_t at_bytes) {
+    return (size_t)h->npf * K * at_bytes * 2 + (size_t)h->M * 4 + 16 * 64;
+}
+
+template <int K>
+static int apply_S_dispatch(vmc_ctx* h, const double* V, double* out, double shift, int store, cudaStream_t st) {
+    // vectors that do not fit the shared-memory image together are split
+    // into groups (each group streams the store once)
+    if (K > 1) {
+        const size_t at = (store == VMC_STORE_FP64 || store == VMC_STORE_FP32) ? 8 : 4;
+        if (main_smem(h, K, at) > h->smem_optin) {
+            constexpr int H = K > 1 ? K / 2 : 1;
+            int rc = apply_S_dispatch<H>(h, V, out, shift, store, st);
+            if (rc) return rc;
+            return apply_S_dispatch<H>(h, V + (size_t)H * h->nv, out + (size_t)H * h->nv, shift, store, st);
+        }
+    }
+    const int kind = store_kind(store);
+    if (kind < 0) return VMC_ERR_INVALID_ARG;
+    if (!store_ptr(h, kind)) return VMC_ERR_STATE;
+    int rc0 = ensure_obar(h, kind, st);
+    if (rc0) return rc0;
+    const double* Ob = h->d_Obar[kind];
+    switch (store) {
+        case VMC_STORE_FP64:
+            return apply_S_impl<double, double, K>(h, h->d_pf64, Ob, V, out, shift, nullptr, nullptr, nullptr, st);
+        case VMC_STORE_FP32:
+            return apply_S_impl<float, double, K>(h, h->d_pf32, Ob, V, out, shift, nullptr, nullptr, nullptr, st);
+        case VMC_STORE_BF16:
+        case VMC_STORE_FP32_F32ACC: {
+            const void* src = store == VMC_STORE_BF16 ? (const void*)h->d_pf16 : (const void*)h->d_pf32;
+            if (!src) return VMC_ERR_STATE;
+            const int64_t n = h->nv * K;
+            k_cast<float><<<kNumPart, 256, 0, st>>>(V, h->d_b32, n, 1.0); h->n_launch++;
+            VCK(cudaGetLastError());
+            int rc = store == VMC_STORE_BF16
+                         ? apply_S_impl<__nv_bfloat16, float, K>(h, src, Ob, h->d_b32, h->d_q32, shift, nullptr,
+                                                                 nullptr, nullptr, st)
+                         : apply_S_impl<float, float, K>(h, src, Ob, h->d_b32, h->d_q32, shift, nullptr, nullptr,
+                                                         nullptr, st);
+            if (rc) return rc;
+            // widen back to FP64
+            VCK(cudaMemsetAsync(out, 0, sizeof(double) * n, st));
+            k_axpy_to64<float><<<kNumPart, 256, 0, st>>>(out, h->d_q32, 1.0, n); h->n_launch++;
+            VCK(cudaGetLastError());
+            return VMC_OK;
+        }
+        default:
+            return VMC_ERR_INVALID_ARG;
+    }
+}
+
+extern "C" int sr_apply_S(vmc_handle h, const double* V, double* out, int k, double shift, int store, void* stream) {
+    if (!h || !V || !out || k < 1 || k > kMaxK || k == 3) return VMC_ERR_INVALID_ARG;
+    if (h->n_s == 0) return VMC_ERR_STATE;
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (k) {
+        case 1: return apply_S_dispatch<1>(h, V, out, shift, store, st);
+        case 2: return apply_S_dispatch<2>(h, V, out, shift, store, st);
+        default: return apply_S_dispatch<4>(h, V, out, shift, store, st);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// conjugate gradient
+// ---------------------------------------------------------------------------
+
+// CG on (S + shift I) x = b over store `s_pf` (ST) with vectors of type VT;
+// b, x, r, p, q are device vectors of VT.  Returns iterations in *iters.
+template <typename ST, typename VT>
+static int cg_loop(vmc_ctx* h, const void* s_pf, const double* Obar, const VT* b, VT* x, VT* r, VT* p, VT* q,
+                   double shift, double tol, int max_iter, int* iters, cudaStream_t st) {
+    const int64_t n = h->nv;
+    double* init_part = h->part(2);
+    double* pAp_part = h->part(3);
+    double* rr_part = h->part(4);
+    double* obp_part = h->part(5);
+    k_cg_init<VT><<<kNumPart, 256, 0, st>>>(b, x, r, p, n, init_part); h->n_launch++;
+    k_cg_start<<<1, 32, 0, st>>>(init_part, kNumPart, h->d_scal, tol, h->d_stop); h->n_launch++;
+    k_dot_part<double, VT, 1><<<kNumPart, 256, 0, st>>>(Obar, p, n, obp_part, h->d_stop); h->n_launch++;
+    VCK(cudaGetLastError());
+    int done = 0;
+    *iters = 0;
+    if (max_iter <= 0) return VMC_OK;
+    while (!done) {
+        for (int j = 0; j < kChunk; ++j) {
+            int rc = apply_S_impl<ST, VT, 1>(h, s_pf, Obar, p, q, shift, h->d_stop, obp_part, pAp_part, st);
+            if (rc) return rc;
+            k_cg_xr<VT><<<kNumPart, 256, 0, st>>>(x, r, p, q, n, pAp_part, fin_grid(h), h->d_scal, rr_part, h->d_stop); h->n_launch++;
+            k_cg_p<VT><<<kNumPart, 256, 0, st>>>(r, p, n, rr_part, kNumPart, h->d_scal, Obar, obp_part,
+                                                 h->d_stop, max_iter); h->n_launch++;
+            VCK(cudaGetLastError());
+        }
+        VCK(cudaMemcpyAsync(h->h_pinned, h->d_scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        VCK(cudaMemcpyAsync(h->h_pinned + 8, h->d_stop, sizeof(int), cudaMemcpyDeviceToHost, st));
+        VCK(cudaStreamSynchronize(st));
+        int stop;
+        memcpy(&stop, h->h_pinned + 8, sizeof(int));
+        *iters = (int)h->h_pinned[CG_IT];
+        if (stop) done = 1;
+    }
+    return VMC_OK;
+}
+
+// y = g - (S + shift I) x with FP64 accumulation over store s_pf (ST = double
+// or float); returns |y|^2 through the host.
+template <typename ST>
+static int residual64(vmc_ctx* h, const void* s_pf, const double* Obar, const double* g, const double* x, double* y,
+                      double shift, double* rr, cudaStream_t st) {
+    int rc = apply_S_impl<ST, double, 1>(h, s_pf, Obar, x, h->d_t64, shift, nullptr, nullptr, nullptr, st);
+    if (rc) return rc;
+    k_sub<<<kNumPart, 256, 0, st>>>(g, h->d_t64, y, h->nv, h->part(6)); h->n_launch++;
+    VCK(cudaGetLastError());
+    std::vector<double> parts(kNumPart);
+    VCK(cudaMemcpyAsync(parts.data(), h->part(6), sizeof(double) * kNumPart, cudaMemcpyDeviceToHost, st));
+    VCK(cudaStreamSynchronize(st));
+    double s = 0.0;
+    for (double v : parts) s += v;
+    *rr = s;
+    return VMC_OK;
+}
+
+static double host_norm2(vmc_ctx* h, const double* v, cudaStream_t st, int* rc) {
+    k_dot_part<double, double, 1><<<kNumPart, 256, 0, st>>>(v, v, h->nv, h->part(7), nullptr); h->n_launch++;
+    std::vector<double> parts(kNumPart);
+    if (cudaMemcpyAsync(parts.data(), h->part(7), sizeof(double) * kNumPart, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        *rc = VMC_ERR_CUDA;
+        return 0.0;
+    }
+    double s = 0.0;
+    for (double x : parts) s += x;
+    *rc = VMC_OK;
+    return s;
+}
+
+static double dot64(vmc_ctx* h, const double* a, const double* b, cudaStream_t st, int* rc) {
+    k_dot_part<double, double, 1><<<kNumPart, 256, 0, st>>>(a, b, h->nv, h->part(7), nullptr); h->n_launch++;
+    std::vector<double> parts(kNumPart);
+    if (cudaMemcpyAsync(parts.data(), h->part(7), sizeof(double) * kNumPart, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        *rc = VMC_ERR_CUDA;
+        return 0.0;
+    }
+    double s = 0.0;
+    for (double v : parts) s += v;
+    *rc = VMC_OK;
+    return s;
+}
+
+// z = M^{-1} r: the inner low-precision CG on (S_lowp + shift I) with the
+// right-hand side scaled to unit norm, to relative tolerance itol.
+static int inner_solve(vmc_ctx* h, int mode, const double* r, double rnorm, double* z, double shift, double itol,
+                       int max_iter, int* iters, cudaStream_t st) {
+    k_cast<float><<<kNumPart, 256, 0, st>>>(r, h->d_b32, h->nv, 1.0 / rnorm); h->n_launch++;
+    VCK(cudaGetLastError());
+    int rc = mode == VMC_CG_MIXED
+                 ? cg_loop<__nv_bfloat16, float>(h, h->d_pf16, h->d_Obar[2], h->d_b32, h->d_x32, h->d_r32, h->d_p32,
+                                                h->d_q32, shift, itol, max_iter, iters, st)
+                 : cg_loop<float, float>(h, h->d_pf32, h->d_Obar[1], h->d_b32, h->d_x32, h->d_r32, h->d_p32, h->d_q32,
+                                        shift, itol, max_iter, iters, st);
+    if (rc) return rc;
+    VCK(cudaMemsetAsync(z, 0, sizeof(double) * h->nv, st));
+    k_axpy_to64<float><<<kNumPart, 256, 0, st>>>(z, h->d_x32, rnorm, h->nv); h->n_launch++;
+    VCK(cudaGetLastError());
+    return VMC_OK;
+}
+
+// Flexible conjugate gradient (Notay, SIAM J. Sci. Comput. 22, 2000; one
+// retained direction) on (S + shift I) x = g.  The outer product streams the
+// FP32 store with FP64 accumulation; the preconditioner is the inner BF16 (or
+// FP32) CG solve, whose error varies from step to step - hence the flexible
+// beta = -alpha (z_new . q) / (z . r).
+static int fcg_mixed(vmc_ctx* h, const double* g, double shift, double tol, int max_iter, int mode, double* x,
+                     double gn2, vmc_cg_info* inf, cudaStream_t st) {
+    const int64_t n = h->nv;
+    double* r = h->d_r64;
+    double* z = h->d_x64;
+    double* p = h->d_p64;
+    double* q = h->d_q64;
+    int rc = VMC_OK;
+    VCK(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
+    VCK(cudaMemcpyAsync(r, g, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    double rr = gn2;
+    const double target = tol * tol * gn2;
+    const double itol_floor = mode == VMC_CG_MIXED ? 1e-2 : 1e-3;
+    int used = 0;
+    if (rr == 0.0) { inf->true_rel_residual = 0.0; return VMC_OK; }
+    double rn = std::sqrt(rr);
+    int it = 0;
+    rc = inner_solve(h, mode, r, rn, z, shift, std::max(itol_floor, 0.5 * std::sqrt(target / rr)), max_iter, &it, st);
+    if (rc) return rc;
+    used += it;
+    VCK(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    double zr = dot64(h, z, r, st, &rc);
+    if (rc) return rc;
+    for (int outer = 0; outer < 200; ++outer) {
+        rc = apply_S_impl<float, double, 1>(h, h->d_pf32, h->d_Obar[1], p, q, shift, nullptr, nullptr, nullptr, st);
+        if (rc) return rc;
+        inf->residual_products++;
+        double pq = dot64(h, p, q, st, &rc);
+        if (rc) return rc;
+        if (!(pq > 0.0)) break;
+        const double alpha = zr / pq;
+        k_axpby<<<kNumPart, 256, 0, st>>>(alpha, p, 1.0, x, n); h->n_launch++;
+        k_axpby<<<kNumPart, 256, 0, st>>>(-alpha, q, 1.0, r, n); h->n_launch++;
+        VCK(cudaGetLastError());
+        rr = dot64(h, r, r, st, &rc);
+        if (rc) return rc;
+        inf->refinements++;
+        if (rr <= target || used >= max_iter) break;
+        rn = std::sqrt(rr);
+        rc = inner_solve(h, mode, r, rn, z, shift, std::max(itol_floor, 0.5 * std::sqrt(target / rr)),
+                         max_iter - used, &it, st);
+        if (rc) return rc;
+        used += it;
+        const double zq = dot64(h, z, q, st, &rc);
+        if (rc) return rc;
+        const double zr_new = dot64(h, z, r, st, &rc);
+        if (rc) return rc;
+        const double beta = -alpha * zq / zr;
+        k_axpby<<<kNumPart, 256, 0, st>>>(1.0, z, beta, p, n); h->n_launch++;
+        VCK(cudaGetLastError());
+        zr = zr_new;
+    }
+    // true residual of the returned x, FP64 accumulation over the FP32 store
+    double rt = 0.0;
+    rc = residual64<float>(h, h->d_pf32, h->d_Obar[1], g, x, h->d_r64, shift, &rt, st);
+    if (rc) return rc;
+    inf->residual_products++;
+    inf->iterations = used;
+    inf->true_rel_residual = std::sqrt(rt / gn2);
+    return VMC_OK;
+}
+
+extern "C" int sr_cg_solve(vmc_handle h, const double* g, double shift, double tol, int max_iter, int mode, double* x,
+                           vmc_cg_info* info, void* stream) {
+    if (!h || !g || !x || !(tol > 0) || max_iter < 1) return VMC_ERR_INVALID_ARG;
+    if (h->n_s == 0) return VMC_ERR_STATE;
+    cudaStream_t st = (cudaStream_t)stream;
+    vmc_cg_info inf{};
+    int rc = VMC_OK;
+    const double gn2 = host_norm2(h, g, st, &rc);
+    if (rc) return rc;
+    if (mode == VMC_CG_FP64) {
+        if (!h->d_pf64) return VMC_ERR_STATE;
+        rc = ensure_obar(h, 0, st);
+        if (rc) return rc;
+        int it = 0;
+        rc = cg_loop<double, double>(h, h->d_pf64, h->d_Obar[0], g, h->d_x64, h->d_r64, h->d_p64, h->d_q64, shift, tol,
+                                     max_iter, &it, st);
+        if (rc) return rc;
+        VCK(cudaMemcpyAsync(x, h->d_x64, sizeof(double) * h->nv, cudaMemcpyDeviceToDevice, st));
+        double rr = 0.0;
+        rc = residual64<double>(h, h->d_pf64, h->d_Obar[0], g, x, h->d_r64, shift, &rr, st);
+        if (rc) return rc;
+        inf.iterations = it;
+        inf.residual_products = 1;
+        inf.true_rel_residual = gn2 > 0 ? std::sqrt(rr / gn2) : 0.0;
+    } else if (mode == VMC_CG_MIXED || mode == VMC_CG_FP32) {
+        if (!h->d_pf32 || !h->d_pf16) return VMC_ERR_STATE;
+        rc = ensure_obar(h, 1, st);
+        if (!rc && mode == VMC_CG_MIXED) rc = ensure_obar(h, 2, st);
+        if (rc) return rc;
+        rc = fcg_mixed(h, g, shift, tol, max_iter, mode, x, gn2, &inf, st);
+        if (rc) return rc;
+    } else {
+        return VMC_ERR_INVALID_ARG;
+    }
+    inf.converged = inf.true_rel_residual <= tol ? 1 : 0;
+    if (info) *info = inf;
+    return inf.converged ? VMC_OK : VMC_ERR_NOT_CONVERGED;
+}
+
+// ---------------------------------------------------------------------------
+// measurement support
+// ---------------------------------------------------------------------------
+static int fold_records(vmc_ctx* h) {
+    for (auto& r : h->recs) {
+        VCK(cudaEventSynchronize(r.b));
+        float ms = 0.f;
+        VCK(cudaEventElapsedTime(&ms, r.a, r.b));
+        h->acc_ms[r.kind] += ms;
+        h->acc_bytes[r.kind] += r.bytes;
+        h->acc_n[r.kind] += 1;
+        h->ev_pool.push_back(r.a);
+        h->ev_pool.push_back(r.b);
+    }
+    h->recs.clear();
+    return VMC_OK;
+}
+
+extern "C" int vmc_profile(vmc_handle h, int enable) {
+    if (!h) return VMC_ERR_INVALID_ARG;
+    int rc = fold_records(h);
+    if (rc) return rc;
+    for (int k = 0; k < 4; ++k) { h->acc_ms[k] = 0; h->acc_bytes[k] = 0; h->acc_n[k] = 0; }
+    h->n_launch = 0;
+    h->prof = enable != 0;
+    return VMC_OK;
+}
+
+extern "C" int vmc_profile_read(vmc_handle h, int store, int64_t* launches_all, int64_t* pass_launches,
+                                double* pass_ms, double* pass_bytes) {
+    if (!h || store < 0 || store > 3) return VMC_ERR_INVALID_ARG;
+    int rc = fold_records(h);
+    if (rc) return rc;
+    if (launches_all) *launches_all = h->n_launch;
+    if (pass_launches) *pass_launches = h->acc_n[store];
+    if (pass_ms) *pass_ms = h->acc_ms[store];
+    if (pass_bytes) *pass_bytes = h->acc_bytes[store];
+    return VMC_OK;
+}

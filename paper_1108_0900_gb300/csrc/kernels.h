@@ -1,0 +1,180 @@
+// Kernel argument blocks and launch wrappers shared by the vmcsr translation
+// units.  Internal to the library; the public boundary is include/vmcsr.h.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace vmc {
+
+// Walker kernel (sampling, measurement of given configurations, adjoint).
+struct SampleArgs {
+    DevProblem pb;
+    int n_walkers;        // warps launched (walkers or given configurations)
+    int spw;              // measurements per walker
+    int n_burn;           // sweeps before the first measurement
+    int props_per_sweep;  // N for sampling, 0 to only measure
+    int write_back;       // 1: write the final configuration / counter back
+    int want_energy;
+    uint64_t seed;
+    uint8_t* walker_occ;  // [n_walkers][N] ascending on entry
+    uint64_t* walker_step;
+    int XS;               // row stride of the inverse in shared memory
+    int ncorr_pad;
+    size_t warp_bytes;
+    // O store
+    uint8_t* s_occ;       // [n_s][Nst]
+    int Nst;
+    uint16_t* s_cidx;     // [n_s][ncst]
+    int ncst;
+    double* s_E;
+    double* s_pf64;
+    float* s_pf32;
+    __nv_bfloat16* s_pf16;
+    int64_t Pst;
+    // adjoint mode: bgrad[k] += bw[s] O_k(n_s) instead of writing the store
+    const double* bw;
+    double* bgrad;
+    int* status;
+};
+
+struct LogPsiArgs {
+    DevProblem pb;
+    int64_t n_s;
+    const uint8_t* s_occ;
+    int Nst;
+    const uint16_t* s_cidx;
+    int ncst;
+    int XS;
+    size_t warp_bytes;
+    double* out;
+};
+
+template <typename R> __global__ void k_walkers(SampleArgs a);
+__global__ void k_logpsi(LogPsiArgs a);
+
+// ---------------------------------------------------------------------------
+// SR kernels
+// ---------------------------------------------------------------------------
+enum StoreKind { STORE_F64 = 0, STORE_F32 = 1, STORE_BF16 = 2 };
+
+// Streaming pass over the O store.  With GATHER, t_s = O_s . V for K vectors
+// (correlator gather + pairing-block dot) is computed and written to T;
+// otherwise t_s is read from T.  Then sum_s t_s O_s restricted to the
+// pairing block is accumulated per CTA and written to pf_partial[cta].
+template <typename AT>
+struct MainArgs {
+    DevProblem pb;
+    int64_t n_s;
+    const uint8_t* s_occ;
+    int Nst;
+    const uint16_t* s_cidx;
+    int ncst;
+    const void* s_pf;
+    int64_t Pst;
+    const AT* V;          // [K][nv]
+    const AT* invC;       // [ncp]
+    AT* T;                // [n_s][K]
+    AT* pf_partial;       // [gridDim][npf][K]
+    const int* stop;      // early exit flag (may be null)
+};
+
+template <typename AT>
+struct CorrArgs {
+    DevProblem pb;
+    int64_t n_s;
+    const uint16_t* cidxT;  // [ncorr][n_s]
+    const AT* T;            // [n_s][K]
+    AT* corr_partial;       // [nchunk][ncp][K]
+    int nchunk;
+    const int* stop;
+};
+
+template <typename AT, typename VT>
+struct FinArgs {
+    DevProblem pb;
+    int64_t n_s;
+    int n_pf_part;          // CTAs of the main pass
+    int nchunk;
+    const AT* pf_partial;
+    const double* pf_raw;   // [npf][K] sum over CTAs of pf_partial
+    const AT* corr_partial;
+    const AT* invC;
+    const double* Obar;     // [nv] (S mode)
+    const double* obv_part; // [nblk][K] partial dots Obar . V (S mode)
+    int n_obv_part;
+    const VT* V;            // [K][nv]
+    double shift;
+    VT* out;                // [K][nv]
+    double* dot_part;       // [gridDim][K] partial out . V (may be null)
+    // gradient mode
+    double* Obar_out;
+    double* g_out;
+    const double* E_sum;    // [nblk] partial sums of E (gradient mode)
+    int n_E_part;
+    const int* stop;
+};
+
+
+template <typename ST, typename AT, int K, bool GATHER>
+__global__ void __launch_bounds__(512) k_sr_main(MainArgs<AT> a);
+template <typename AT, int K> __global__ void __launch_bounds__(256) k_corr_scatter(CorrArgs<AT> a);
+template <typename AT, typename VT, int K> __global__ void __launch_bounds__(256) k_finalize_S(FinArgs<AT, VT> a);
+template <typename AT> __global__ void __launch_bounds__(256) k_finalize_grad(FinArgs<AT, double> a);
+__global__ void k_build_T_grad(const double* E, int64_t n_s, double* T, double* E_part);
+template <typename TA, typename TB, int K>
+__global__ void __launch_bounds__(256) k_dot_part(const TA* x, const TB* y, int64_t n, double* part, const int* stop);
+template <typename AT>
+__global__ void __launch_bounds__(256) k_reduce_pf(const AT* part, int nblk, int npfK, double* raw);
+__global__ void k_transpose_cidx(const uint16_t* cidx, int ncst, int ncorr, int64_t n_s, uint16_t* cidxT);
+template <typename VT> __global__ void k_cast(const double* src, VT* dst, int64_t n, double scale);
+
+// conjugate-gradient scalars (FP64, device): rr, |b|^2, tol^2 |b|^2,
+// iterations, rr of the previous step
+enum { CG_RR = 0, CG_BB = 1, CG_TOL2 = 2, CG_IT = 3, CG_RRP = 4 };
+template <typename VT>
+__global__ void __launch_bounds__(256) k_cg_init(const VT* b, VT* x, VT* r, VT* p, int64_t n, double* part);
+__global__ void k_cg_start(const double* part, int npart, double* scal, double tol, int* stop);
+template <typename VT>
+__global__ void __launch_bounds__(256) k_cg_xr(VT* x, VT* r, const VT* p, const VT* Ap, int64_t n,
+                                               const double* pAp_part, int npart, double* scal,
+                                               double* rr_part, int* stop);
+template <typename VT>
+__global__ void __launch_bounds__(256) k_cg_p(const VT* r, VT* p, int64_t n, const double* rr_part, int npart,
+                                              double* scal, const double* Obar, double* obp_part, int* stop,
+                                              int max_iter);
+__global__ void k_sub(const double* a, const double* b, double* y, int64_t n, double* part);
+__global__ void k_axpby(double a, const double* x, double b, double* y, int64_t n);
+template <typename VT> __global__ void k_axpy_to64(double* x, const VT* d, double scale, int64_t n);
+
+}  // namespace vmc
+
+namespace vmc {
+
+// TMA-staged streaming pass (FP32 accumulation, BF16 or FP32 store): every
+// warp double-buffers its samples' O records in shared memory with 1-D bulk
+// copies and walks the pairing block row by row.
+struct StreamArgs {
+    DevProblem pb;
+    int64_t n_s;
+    const uint8_t* s_occ;
+    int Nst;
+    const uint16_t* s_cidx;
+    int ncst;
+    const void* s_pf;
+    int64_t Pst;
+    int st_bytes;           // element size of the store
+    const float* V;         // [K][nv]
+    const float* invC;
+    float* T;               // [n_s][K]
+    float* pf_partial;      // [gridDim][npf][K]
+    const int* stop;
+    int* status;            // ST_TIMEOUT on a wait that ran out
+    size_t buf_bytes;       // one staging buffer (occ | cidx | pf)
+};
+
+template <typename ST, int K> __global__ void __launch_bounds__(512, 1) k_sr_stream(StreamArgs a);
+
+}  // namespace vmc

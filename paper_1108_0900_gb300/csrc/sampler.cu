@@ -1,0 +1,456 @@
+// Walker kernels: Metropolis sampling from |Psi_n|^2 (Sec. II.A, fixed N and
+// S_z as in Sec. III), local energy, and the per-sample derivative ratios
+// O_k(n) = Psi^k_n / Psi_n of Eq. 3 for the CPS x pfaffian ansatz of Eq. 11.
+//
+// One warp owns one walker.  The walker keeps X = A^{-1}, A = F[occ, occ],
+// in shared memory with the electron positions left unsorted (a move puts
+// the new orbital in the vacated position).  For a move p -> q at position a
+// with b_j = F[q, o_j] (b_a = 0):
+//   Pf(A')/Pf(A) = sum_j b_j X_{ja} = -sum_j b_j X_{aj}
+// (Pf is linear in row/column a; dPf/dA_aj = Pf X_{ja}).  The Jordan-Wigner
+// sign of the hop cancels the sign of re-sorting the positions, so this
+// unsorted ratio is the signed amplitude ratio the local energy needs.  On
+// acceptance A' = A + e_a u^T - u e_a^T (u = b - A_{a,:}), whose 2x2
+// Woodbury capacitance is r I, so
+//   X' = X + (c y^T - y c^T) / r,  c = X_{:,a},  y = X b + e_a.
+// The inverse is rebuilt from scratch (Gauss-Jordan, partial pivoting) at
+// the start of every call.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace vmc {
+
+struct WarpMem {
+    unsigned char* base;
+};
+
+template <typename R>
+__device__ __forceinline__ R load_F(const DevProblem& pb, int p, int q);
+template <> __device__ __forceinline__ float load_F<float>(const DevProblem& pb, int p, int q) {
+    return __ldg(pb.F32 + p * pb.M + q);
+}
+template <> __device__ __forceinline__ double load_F<double>(const DevProblem& pb, int p, int q) {
+    return __ldg(pb.F64 + p * pb.M + q);
+}
+template <typename R> __device__ __forceinline__ R load_C(const DevProblem& pb, int64_t k);
+template <> __device__ __forceinline__ float load_C<float>(const DevProblem& pb, int64_t k) {
+    return __ldg(pb.C32 + k);
+}
+template <> __device__ __forceinline__ double load_C<double>(const DevProblem& pb, int64_t k) {
+    return __ldg(pb.C64 + k);
+}
+
+// weight 4^j of site s inside correlator c (0 if absent)
+__device__ __forceinline__ int site_weight_in(const DevProblem& pb, int c, int s) {
+    int w = 1;
+    for (int j = pb.corr_ptr[c]; j < pb.corr_ptr[c + 1]; ++j) {
+        if (pb.corr_sites[j] == s) return w;
+        w <<= 2;
+    }
+    return 0;
+}
+
+// Correlator part of Psi(n')/Psi(n) for moving one electron of spin factor
+// sf (1 up, 2 down) from site sp to site sq.  Entry e of the concatenated
+// membership lists of sp and sq; a correlator holding both sites is handled
+// once (from sp's list).  Returns the factor and the new state in *newidx
+// (or -1 when the entry contributes nothing).
+__device__ __forceinline__ int corr_entry(const DevProblem& pb, const uint32_t* cidx, int sp, int sq,
+                                          int sf, int e, int* cout) {
+    int dp = pb.site_cptr[sp + 1] - pb.site_cptr[sp];
+    if (e < dp) {
+        int ent = pb.site_cptr[sp] + e;
+        int c = pb.site_corr[ent];
+        int newi = (int)cidx[c] - sf * pb.site_w[ent] + sf * site_weight_in(pb, c, sq);
+        *cout = c;
+        return newi;
+    }
+    int ent = pb.site_cptr[sq] + (e - dp);
+    int c = pb.site_corr[ent];
+    if (site_weight_in(pb, c, sp) != 0) { *cout = -1; return -1; }
+    *cout = c;
+    return (int)cidx[c] + sf * pb.site_w[ent];
+}
+
+template <typename R>
+__device__ R corr_ratio_warp(const DevProblem& pb, uint32_t* cidx, int p, int q, bool commit) {
+    const int lane = threadIdx.x & 31;
+    int ns = pb.ns;
+    int sf = p >= ns ? 2 : 1;
+    int sp = p >= ns ? p - ns : p, sq = q >= ns ? q - ns : q;
+    int total = (pb.site_cptr[sp + 1] - pb.site_cptr[sp]) + (pb.site_cptr[sq + 1] - pb.site_cptr[sq]);
+    R prod = R(1);
+    for (int base = 0; base < total; base += 32) {
+        int e = base + lane;
+        R r = R(1);
+        int c = -1, newi = -1;
+        if (e < total) {
+            newi = corr_entry(pb, cidx, sp, sq, sf, e, &c);
+            if (c >= 0) r = load_C<R>(pb, pb.corr_off[c] + newi) / load_C<R>(pb, pb.corr_off[c] + cidx[c]);
+        }
+        prod *= warp_prod(r);
+        if (commit) {
+            __syncwarp();
+            if (c >= 0) cidx[c] = (uint32_t)newi;
+            __syncwarp();
+        }
+    }
+    return prod;
+}
+
+// lane-serial version used while every lane evaluates its own hop
+template <typename R>
+__device__ R corr_ratio_serial(const DevProblem& pb, const uint32_t* cidx, int p, int q) {
+    int ns = pb.ns;
+    int sf = p >= ns ? 2 : 1;
+    int sp = p >= ns ? p - ns : p, sq = q >= ns ? q - ns : q;
+    int total = (pb.site_cptr[sp + 1] - pb.site_cptr[sp]) + (pb.site_cptr[sq + 1] - pb.site_cptr[sq]);
+    R prod = R(1);
+    for (int e = 0; e < total; ++e) {
+        int c;
+        int newi = corr_entry(pb, cidx, sp, sq, sf, e, &c);
+        if (c >= 0) prod *= load_C<R>(pb, pb.corr_off[c] + newi) / load_C<R>(pb, pb.corr_off[c] + cidx[c]);
+    }
+    return prod;
+}
+
+// In-place Gauss-Jordan inverse with partial pivoting of the N x N matrix X
+// (row stride XS) by one warp.  col: N scratch, piv: N ints.  Returns false
+// if a pivot column is entirely zero or not finite.
+template <typename R>
+__device__ bool gj_invert_warp(R* X, int N, int XS, R* col, int* piv) {
+    const int lane = threadIdx.x & 31;
+    for (int k = 0; k < N; ++k) {
+        R best = R(-1);
+        int bi = N;
+        for (int i = k + lane; i < N; i += 32) {
+            R v = fabs(X[i * XS + k]);
+            if (v > best) { best = v; bi = i; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            R ob = __shfl_xor_sync(VMC_FULL_MASK, best, o);
+            int oi = __shfl_xor_sync(VMC_FULL_MASK, bi, o);
+            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (!(best > R(0)) || !isfinite(best)) return false;
+        if (lane == 0) piv[k] = bi;
+        if (bi != k) {
+            for (int j = lane; j < N; j += 32) {
+                R t = X[k * XS + j];
+                X[k * XS + j] = X[bi * XS + j];
+                X[bi * XS + j] = t;
+            }
+        }
+        __syncwarp();
+        R pinv = R(1) / X[k * XS + k];
+        for (int i = lane; i < N; i += 32) col[i] = X[i * XS + k];
+        __syncwarp();
+        for (int j = lane; j < N; j += 32) X[k * XS + j] = (j == k ? R(1) : X[k * XS + j]) * pinv;
+        __syncwarp();
+        for (int j = lane; j < N; j += 32) {
+            R rk = X[k * XS + j];
+            for (int i = 0; i < N; ++i) {
+                if (i == k) continue;
+                R x = (j == k) ? R(0) : X[i * XS + j];
+                X[i * XS + j] = x - col[i] * rk;
+            }
+        }
+        __syncwarp();
+    }
+    for (int k = N - 1; k >= 0; --k) {
+        int pk = piv[k];
+        if (pk != k) {
+            for (int i = lane; i < N; i += 32) {
+                R t = X[i * XS + k];
+                X[i * XS + k] = X[i * XS + pk];
+                X[i * XS + pk] = t;
+            }
+        }
+        __syncwarp();
+    }
+    return true;
+}
+
+template <typename R> __device__ __forceinline__ void store_pf(const SampleArgs& a, int64_t idx, R w);
+template <> __device__ __forceinline__ void store_pf<float>(const SampleArgs& a, int64_t idx, float w) {
+    if (a.s_pf64) a.s_pf64[idx] = (double)w;
+    if (a.s_pf32) a.s_pf32[idx] = w;
+    if (a.s_pf16) a.s_pf16[idx] = __float2bfloat16_rn(w);
+}
+template <> __device__ __forceinline__ void store_pf<double>(const SampleArgs& a, int64_t idx, double w) {
+    if (a.s_pf64) a.s_pf64[idx] = w;
+    if (a.s_pf32) a.s_pf32[idx] = (float)w;
+    if (a.s_pf16) a.s_pf16[idx] = __float2bfloat16_rn((float)w);
+}
+
+template <typename R>
+__global__ void k_walkers(SampleArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const DevProblem& pb = a.pb;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int w = blockIdx.x * (blockDim.x >> 5) + wid;
+    if (w >= a.n_walkers) return;
+    const int N = pb.N, M = pb.M, ns = pb.ns, nu = pb.nu, XS = a.XS;
+    unsigned char* base = smem_raw + (size_t)wid * a.warp_bytes;
+    R* X = (R*)base;
+    R* bv = X + N * XS;
+    R* yv = bv + XS;
+    R* cv = yv + XS;
+    int* iv = (int*)(cv + XS);                 // 64 ints
+    uint32_t* cidx = (uint32_t*)(iv + 64);     // ncorr (rounded up to 4)
+    uint8_t* pos_orb = (uint8_t*)(cidx + a.ncorr_pad);
+    int8_t* orb_pos = (int8_t*)(pos_orb + 64); // 128
+
+    // ---- load the configuration -----------------------------------------
+    for (int o = lane; o < M; o += 32) orb_pos[o] = -1;
+    __syncwarp();
+    uint64_t up = 0, dn = 0;
+    bool bad = false;
+    for (int i = lane; i < N; i += 32) {
+        int o = a.walker_occ[(int64_t)w * N + i];
+        pos_orb[i] = (uint8_t)o;
+        if (o >= M) bad = true;
+        else if (o < ns) up |= 1ull << o;
+        else dn |= 1ull << (o - ns);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        up |= __shfl_xor_sync(VMC_FULL_MASK, up, o);
+        dn |= __shfl_xor_sync(VMC_FULL_MASK, dn, o);
+    }
+    bad = __any_sync(VMC_FULL_MASK, bad);
+    if (bad || __popcll(up) != nu || __popcll(dn) != pb.nd) {
+        if (lane == 0) atomicOr(a.status, ST_BAD_CONFIG);
+        return;
+    }
+    __syncwarp();
+    for (int i = lane; i < N; i += 32) orb_pos[pos_orb[i]] = (int8_t)i;
+    __syncwarp();
+
+    // ---- inverse of the pairing submatrix, from scratch -------------------
+    for (int i = 0; i < N; ++i) {
+        int p = pos_orb[i];
+        for (int j = lane; j < N; j += 32) X[i * XS + j] = load_F<R>(pb, p, pos_orb[j]);
+    }
+    __syncwarp();
+    if (!gj_invert_warp<R>(X, N, XS, cv, iv)) {
+        if (lane == 0) atomicOr(a.status, ST_SINGULAR);
+        return;
+    }
+
+    // ---- correlator states --------------------------------------------------
+    for (int c = lane; c < pb.ncorr; c += 32) {
+        uint32_t idx = 0, wgt = 1;
+        for (int j = pb.corr_ptr[c]; j < pb.corr_ptr[c + 1]; ++j) {
+            int s = pb.corr_sites[j];
+            idx += wgt * (uint32_t)(((up >> s) & 1ull) + 2ull * ((dn >> s) & 1ull));
+            wgt <<= 2;
+        }
+        cidx[c] = idx;
+    }
+    __syncwarp();
+
+    const uint64_t sitemask = (ns == 64) ? ~0ull : ((1ull << ns) - 1ull);
+    uint64_t step = a.walker_step ? a.walker_step[w] : 0ull;
+    const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
+    const int n_sweeps = a.n_burn + a.spw;
+
+    for (int sw = 0; sw < n_sweeps; ++sw) {
+        for (int t = 0; t < a.props_per_sweep; ++t) {
+            u32x4 ctr{(uint32_t)w, (uint32_t)step, (uint32_t)(step >> 32), 0u};
+            u32x4 r = philox4x32_10(ctr, k0, k1);
+            ++step;
+            int as = (int)mulhi32(r.x, (uint32_t)N);
+            int p = as < nu ? nth_set_bit64(up, as) : ns + nth_set_bit64(dn, as - nu);
+            int spin = p >= ns;
+            uint64_t m = spin ? dn : up;
+            int n_empty = ns - __popcll(m);
+            if (n_empty <= 0) continue;
+            int kk = (int)mulhi32(r.y, (uint32_t)n_empty);
+            int q = spin * ns + nth_set_bit64(~m & sitemask, kk);
+            R u = R(r.z >> 8) * R(1.0 / 16777216.0);
+            int ap = orb_pos[p];
+            R acc = R(0);
+            for (int j = lane; j < N; j += 32) {
+                R bj = (j == ap) ? R(0) : load_F<R>(pb, q, pos_orb[j]);
+                bv[j] = bj;
+                acc += bj * X[ap * XS + j];
+            }
+            R rpf = -warp_sum(acc);
+            R rc = corr_ratio_warp<R>(pb, cidx, p, q, false);
+            R ratio = rpf * rc;
+            bool accept = u < ratio * ratio;
+            if (!accept) continue;
+            __syncwarp();
+            for (int i = lane; i < N; i += 32) {
+                R yi = R(0);
+                for (int j = 0; j < N; ++j) yi += X[i * XS + j] * bv[j];
+                if (i == ap) yi += R(1);
+                yv[i] = yi;
+                cv[i] = X[i * XS + ap];
+            }
+            __syncwarp();
+            R rinv = R(1) / rpf;
+            for (int i = lane; i < N; i += 32) {
+                R ci = cv[i] * rinv, yi = yv[i] * rinv;
+                for (int j = 0; j < N; ++j) X[i * XS + j] += ci * yv[j] - yi * cv[j];
+            }
+            corr_ratio_warp<R>(pb, cidx, p, q, true);
+            if (lane == 0) {
+                pos_orb[ap] = (uint8_t)q;
+                orb_pos[p] = -1;
+                orb_pos[q] = (int8_t)ap;
+            }
+            if (spin) dn = (dn & ~(1ull << (p - ns))) | (1ull << (q - ns));
+            else up = (up & ~(1ull << p)) | (1ull << q);
+            __syncwarp();
+        }
+        if (sw < a.n_burn) continue;
+
+        // ---- measurement ----------------------------------------------------
+        const int64_t s = (int64_t)w * a.spw + (sw - a.n_burn);
+        double e_lane = 0.0;
+        if (a.want_energy) {
+            if (pb.ham == 0) {
+                for (int i = lane; i < N; i += 32) {
+                    int p = pos_orb[i];
+                    int spin = p >= ns;
+                    int sp = p - spin * ns;
+                    uint64_t m = spin ? dn : up;
+                    for (int k = pb.nbr_ptr[sp]; k < pb.nbr_ptr[sp + 1]; ++k) {
+                        int s2 = pb.nbr_site[k];
+                        if ((m >> s2) & 1ull) continue;
+                        int q = spin * ns + s2;
+                        R d = R(0);
+                        for (int j = 0; j < N; ++j)
+                            if (j != i) d += load_F<R>(pb, q, pos_orb[j]) * X[i * XS + j];
+                        R rc = corr_ratio_serial<R>(pb, cidx, p, q);
+                        // -t * (Pf ratio = -d) * rc
+                        e_lane += pb.nbr_t[k] * (double)(d * rc);
+                    }
+                }
+            }
+            e_lane = warp_sum(e_lane);
+            if (pb.ham == 0) e_lane += pb.U * (double)__popcll(up & dn);
+            if (!isfinite(e_lane) && lane == 0) atomicOr(a.status, ST_NONFINITE);
+        }
+        // ascending occupation and the position of each sorted electron
+        for (int i = lane; i < N; i += 32) {
+            int o = i < nu ? nth_set_bit64(up, i) : ns + nth_set_bit64(dn, i - nu);
+            iv[i] = orb_pos[o];
+            if (a.s_occ) a.s_occ[s * a.Nst + i] = (uint8_t)o;
+        }
+        __syncwarp();
+        if (a.bgrad) {
+            // adjoint: grad += w_s O(n_s)
+            double ws = a.bw[s];
+            for (int c = lane; c < pb.ncorr; c += 32) {
+                int64_t k = pb.corr_off[c] + cidx[c];
+                atomicAdd(a.bgrad + k, ws / pb.C64[k]);
+            }
+            for (int e = lane; e < pb.P; e += 32) {
+                uint16_t t = pb.pairtab[e];
+                int aa = t & 255, bb = t >> 8;
+                int oa = pos_orb[iv[aa]], ob = pos_orb[iv[bb]];
+                atomicAdd(a.bgrad + pb.ncp + pb.rowbase[oa] + ob, ws * (double)X[iv[bb] * XS + iv[aa]]);
+            }
+        } else {
+            if (a.s_E && lane == 0) a.s_E[s] = e_lane;
+            if (a.s_cidx)
+                for (int c = lane; c < pb.ncorr; c += 32) a.s_cidx[s * a.ncst + c] = (uint16_t)cidx[c];
+            for (int e = lane; e < pb.P; e += 32) {
+                uint16_t t = pb.pairtab[e];
+                int aa = t & 255, bb = t >> 8;
+                store_pf<R>(a, s * a.Pst + e, X[iv[bb] * XS + iv[aa]]);
+            }
+        }
+        __syncwarp();
+    }
+
+    // ---- write the chain state back (ascending) ------------------------------
+    if (a.write_back) {
+        for (int i = lane; i < N; i += 32) {
+            int o = i < nu ? nth_set_bit64(up, i) : ns + nth_set_bit64(dn, i - nu);
+            a.walker_occ[(int64_t)w * N + i] = (uint8_t)o;
+        }
+        if (lane == 0 && a.walker_step) a.walker_step[w] = step;
+    }
+}
+
+// ln|Pf(F[occ, occ])| + sum_c ln|C_c| per sample, FP64 Parlett-Reid with
+// pivoting (the pfaffian reduction cited in Sec. II.C), one warp per sample.
+__global__ void k_logpsi(LogPsiArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const DevProblem& pb = a.pb;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid;
+    if (s >= a.n_s) return;
+    const int N = pb.N, XS = a.XS;
+    double* A = (double*)(smem_raw + (size_t)wid * a.warp_bytes);
+    double* tau = A + N * XS;
+    double* colk1 = tau + XS;
+    const uint8_t* occ = a.s_occ + s * a.Nst;
+    for (int i = 0; i < N; ++i)
+        for (int j = lane; j < N; j += 32) A[i * XS + j] = __ldg(pb.F64 + occ[i] * pb.M + occ[j]);
+    __syncwarp();
+    double logabs = 0.0;
+    int sign = 1;
+    for (int k = 0; k + 1 < N; k += 2) {
+        double best = -1.0;
+        int bi = N;
+        for (int i = k + 1 + lane; i < N; i += 32) {
+            double v = fabs(A[i * XS + k]);
+            if (v > best) { best = v; bi = i; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            double ob = __shfl_xor_sync(VMC_FULL_MASK, best, o);
+            int oi = __shfl_xor_sync(VMC_FULL_MASK, bi, o);
+            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (!(best > 0.0)) { sign = 0; break; }
+        if (bi != k + 1) {
+            for (int j = lane; j < N; j += 32) {
+                double t = A[(k + 1) * XS + j];
+                A[(k + 1) * XS + j] = A[bi * XS + j];
+                A[bi * XS + j] = t;
+            }
+            __syncwarp();
+            for (int i = lane; i < N; i += 32) {
+                double t = A[i * XS + k + 1];
+                A[i * XS + k + 1] = A[i * XS + bi];
+                A[i * XS + bi] = t;
+            }
+            sign = -sign;
+        }
+        __syncwarp();
+        double piv = A[k * XS + k + 1];
+        if (piv < 0) sign = -sign;
+        logabs += log(fabs(piv));
+        for (int i = k + 2 + lane; i < N; i += 32) {
+            tau[i] = A[k * XS + i] / piv;
+            colk1[i] = A[i * XS + k + 1];
+        }
+        __syncwarp();
+        for (int j = k + 2 + lane; j < N; j += 32) {
+            double tj = tau[j], cj = colk1[j];
+            for (int i = k + 2; i < N; ++i) A[i * XS + j] += tau[i] * cj - colk1[i] * tj;
+        }
+        __syncwarp();
+    }
+    // correlators
+    const uint16_t* ci = a.s_cidx + s * a.ncst;
+    double lc = 0.0;
+    for (int c = lane; c < pb.ncorr; c += 32) {
+        double v = pb.C64[pb.corr_off[c] + ci[c]];
+        lc += log(fabs(v));
+    }
+    lc = warp_sum(lc);
+    if (lane == 0) a.out[s] = sign == 0 ? -INFINITY : logabs + lc;
+}
+
+template __global__ void k_walkers<float>(SampleArgs);
+template __global__ void k_walkers<double>(SampleArgs);
+
+}  // namespace vmc

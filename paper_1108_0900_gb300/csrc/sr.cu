@@ -1,0 +1,463 @@
+// SR kernels over the stored derivative ratios (Sec. II.A):
+//   - the matrix-free product of Eq. 7, (1/n_s) sum_s O_s (O_s . v), with the
+//     covariance term -Obar (Obar . v) and the absolute shift eps v;
+//   - the sample means Obar, <E_L> and the gradient g = <E_L O> - <E_L> Obar;
+//   - the vector updates of conjugate gradient with FP64 scalars.
+//
+// Per sample the O vector is sparse: correlator c contributes 1/C at its own
+// parameter off_c + idx_c, and the pairing block holds P values W_e on the
+// pairs of occupied orbitals.  A pass therefore streams the O store once:
+//   gather   t_s = sum_c v[k_c]/C[k_c] + sum_e W_e v[pq(e)],
+//   scatter  out[pq(e)] += t_s W_e into a per-CTA shared-memory image of the
+//            pairing block (written out as one partial per CTA),
+// and the correlator scatter runs correlator-major over a transposed state
+// array into a shared-memory histogram of each correlator's 4^m states, so
+// neither half uses global atomics.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace vmc {
+
+template <typename ST, typename AT> __device__ __forceinline__ AT load_st(const void* p, int64_t i);
+template <> __device__ __forceinline__ double load_st<double, double>(const void* p, int64_t i) {
+    return __ldg((const double*)p + i);
+}
+template <> __device__ __forceinline__ double load_st<float, double>(const void* p, int64_t i) {
+    return (double)__ldg((const float*)p + i);
+}
+template <> __device__ __forceinline__ float load_st<float, float>(const void* p, int64_t i) {
+    return __ldg((const float*)p + i);
+}
+template <> __device__ __forceinline__ float load_st<__nv_bfloat16, float>(const void* p, int64_t i) {
+    return __bfloat162float(((const __nv_bfloat16*)p)[i]);
+}
+template <> __device__ __forceinline__ double load_st<__nv_bfloat16, double>(const void* p, int64_t i) {
+    return (double)__bfloat162float(((const __nv_bfloat16*)p)[i]);
+}
+
+template <typename ST, typename AT, int K, bool GATHER>
+__global__ void __launch_bounds__(512) k_sr_main(MainArgs<AT> a) {
+    if (a.stop && *a.stop) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const DevProblem& pb = a.pb;
+    const int npf = pb.npf, M = pb.M, N = pb.N, P = pb.P;
+    AT* acc = (AT*)smem;
+    AT* vpf = acc + (size_t)npf * K;
+    int* rowbase = (int*)(vpf + (GATHER ? (size_t)npf * K : 0));
+    uint8_t* occw = (uint8_t*)(rowbase + M);
+    for (int i = threadIdx.x; i < npf * K; i += blockDim.x) acc[i] = AT(0);
+    if (GATHER)
+        for (int i = threadIdx.x; i < npf; i += blockDim.x)
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) vpf[i * K + kk] = a.V[kk * pb.nv + pb.ncp + i];
+    for (int i = threadIdx.x; i < M; i += blockDim.x) rowbase[i] = pb.rowbase[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint8_t* my = occw + wid * 64;
+    for (int64_t s = (int64_t)blockIdx.x * nw + wid; s < a.n_s; s += (int64_t)gridDim.x * nw) {
+        for (int i = lane; i < N; i += 32) my[i] = a.s_occ[s * a.Nst + i];
+        __syncwarp();
+        AT t[K];
+        if (GATHER) {
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) t[kk] = AT(0);
+            for (int c = lane; c < pb.ncorr; c += 32) {
+                int64_t k = pb.corr_off[c] + a.s_cidx[s * a.ncst + c];
+                AT ic = a.invC[k];
+#pragma unroll
+                for (int kk = 0; kk < K; ++kk) t[kk] += a.V[kk * pb.nv + k] * ic;
+            }
+            for (int e = lane; e < P; e += 32) {
+                uint16_t pt = pb.pairtab[e];
+                int pq = rowbase[my[pt & 255]] + my[pt >> 8];
+                AT w = load_st<ST, AT>(a.s_pf, s * a.Pst + e);
+#pragma unroll
+                for (int kk = 0; kk < K; ++kk) t[kk] += w * vpf[pq * K + kk];
+            }
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) t[kk] = warp_sum(t[kk]);
+            if (lane < K) {
+                AT mine = t[0];
+#pragma unroll
+                for (int kk = 1; kk < K; ++kk) if (lane == kk) mine = t[kk];
+                a.T[s * K + lane] = mine;
+            }
+        } else {
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) t[kk] = a.T[s * K + kk];
+        }
+        for (int e = lane; e < P; e += 32) {
+            uint16_t pt = pb.pairtab[e];
+            int pq = rowbase[my[pt & 255]] + my[pt >> 8];
+            AT w = load_st<ST, AT>(a.s_pf, s * a.Pst + e);
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) atomicAdd(&acc[pq * K + kk], t[kk] * w);
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    AT* dst = a.pf_partial + (size_t)blockIdx.x * npf * K;
+    for (int i = threadIdx.x; i < npf * K; i += blockDim.x) dst[i] = acc[i];
+}
+
+// correlator-major scatter: block (c, chunk) histograms t_s over the states
+// of correlator c for its slice of samples.
+template <typename AT, int K>
+__global__ void __launch_bounds__(256) k_corr_scatter(CorrArgs<AT> a) {
+    if (a.stop && *a.stop) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    AT* h = (AT*)smem;
+    const DevProblem& pb = a.pb;
+    const int c = blockIdx.x / a.nchunk, ch = blockIdx.x % a.nchunk;
+    const int64_t off = pb.corr_off[c];
+    const int d = (int)(pb.corr_off[c + 1] - off);
+    for (int i = threadIdx.x; i < d * K; i += blockDim.x) h[i] = AT(0);
+    __syncthreads();
+    const int64_t len = (a.n_s + a.nchunk - 1) / a.nchunk;
+    const int64_t s0 = ch * len, s1 = min(a.n_s, s0 + len);
+    const uint16_t* st = a.cidxT + (int64_t)c * a.n_s;
+    for (int64_t s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+        int i = st[s];
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) atomicAdd(&h[i * K + kk], a.T[s * K + kk]);
+    }
+    __syncthreads();
+    AT* dst = a.corr_partial + ((int64_t)ch * pb.ncp + off) * K;
+    for (int i = threadIdx.x; i < d * K; i += blockDim.x) dst[i] = h[i];
+}
+
+template <int K>
+__device__ __forceinline__ void block_reduce_store(double (&v)[K], double* out) {
+    __shared__ double red[K][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int kk = 0; kk < K; ++kk) {
+        double x = warp_sum(v[kk]);
+        if (lane == 0) red[kk][wid] = x;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) {
+            double x = lane < nw ? red[kk][lane] : 0.0;
+            x = warp_sum(x);
+            if (lane == 0) out[blockIdx.x * K + kk] = x;
+        }
+    }
+}
+
+// sum of n partials (stride K, column kk) by one warp; all lanes get it
+__device__ __forceinline__ double warp_sum_partials(const double* part, int n, int kk, int K) {
+    const int lane = threadIdx.x & 31;
+    double s = 0.0;
+    for (int b = lane; b < n; b += 32) s += part[b * K + kk];
+    return warp_sum(s);
+}
+
+// Reduce the per-CTA pairing-block images: raw[pq][kk] = sum_b part[b][pq][kk].
+// Block = 32 parameter slots x 8 CTA slices; a warp covers one slice.
+template <typename AT>
+__global__ void __launch_bounds__(256) k_reduce_pf(const AT* part, int nblk, int npfK, double* raw) {
+    __shared__ double red[8][33];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int i = blockIdx.x * 32 + lane;
+    double s = 0.0;
+    if (i < npfK)
+        for (int b = w; b < nblk; b += 8) s += (double)part[(int64_t)b * npfK + i];
+    red[w][lane] = s;
+    __syncthreads();
+    if (w == 0) {
+        double t = 0.0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) t += red[j][lane];
+        if (i < npfK) raw[i] = t;
+    }
+}
+
+// raw pass result for parameter k and vector kk, divided by n_s
+template <typename AT, typename VT, int K>
+__device__ __forceinline__ double fin_raw(const FinArgs<AT, VT>& a, int64_t k, int kk) {
+    const DevProblem& pb = a.pb;
+    double raw = 0.0;
+    if (k < pb.ncp) {
+        for (int ch = 0; ch < a.nchunk; ++ch) raw += (double)a.corr_partial[((int64_t)ch * pb.ncp + k) * K + kk];
+        raw *= (double)a.invC[k];
+    } else {
+        raw = a.pf_raw[(k - pb.ncp) * K + kk];
+    }
+    return raw / (double)a.n_s;
+}
+
+// out = raw - Obar (Obar . V) + shift V; dot_part = partial out . V
+template <typename AT, typename VT, int K>
+__global__ void __launch_bounds__(256) k_finalize_S(FinArgs<AT, VT> a) {
+    if (a.stop && *a.stop) return;
+    __shared__ double obv[K];
+    if (threadIdx.x < 32) {
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) {
+            double s = warp_sum_partials(a.obv_part, a.n_obv_part, kk, K);
+            if (threadIdx.x == 0) obv[kk] = s;
+        }
+    }
+    __syncthreads();
+    const int64_t nv = a.pb.nv;
+    double dl[K];
+#pragma unroll
+    for (int kk = 0; kk < K; ++kk) dl[kk] = 0.0;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nv; k += (int64_t)gridDim.x * blockDim.x) {
+        const double ob = a.Obar[k];
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) {
+            double v = (double)a.V[kk * nv + k];
+            double o = fin_raw<AT, VT, K>(a, k, kk) - ob * obv[kk] + a.shift * v;
+            a.out[kk * nv + k] = (VT)o;
+            dl[kk] += o * v;
+        }
+    }
+    if (a.dot_part) block_reduce_store<K>(dl, a.dot_part);
+}
+
+// gradient mode: K = 2 with t_s = (1, E_s)
+template <typename AT>
+__global__ void __launch_bounds__(256) k_finalize_grad(FinArgs<AT, double> a) {
+    __shared__ double em;
+    if (threadIdx.x < 32) {
+        double s = warp_sum_partials(a.E_sum, a.n_E_part, 0, 1);
+        if (threadIdx.x == 0) em = s / (double)a.n_s;
+    }
+    __syncthreads();
+    const int64_t nv = a.pb.nv;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nv; k += (int64_t)gridDim.x * blockDim.x) {
+        double o = fin_raw<AT, double, 2>(a, k, 0);
+        double eo = fin_raw<AT, double, 2>(a, k, 1);
+        a.Obar_out[k] = o;
+        a.g_out[k] = eo - em * o;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// small vector kernels
+// ---------------------------------------------------------------------------
+__global__ void k_build_T_grad(const double* E, int64_t n_s, double* T, double* E_part) {
+    double loc[1] = {0.0};
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n_s; s += (int64_t)gridDim.x * blockDim.x) {
+        T[2 * s] = 1.0;
+        T[2 * s + 1] = E[s];
+        loc[0] += E[s];
+    }
+    block_reduce_store<1>(loc, E_part);
+}
+
+// partial dots: part[blk][kk] = sum_i a[i] b[kk n + i]
+template <typename TA, typename TB, int K>
+__global__ void __launch_bounds__(256) k_dot_part(const TA* x, const TB* y, int64_t n, double* part, const int* stop) {
+    if (stop && *stop) return;
+    double loc[K];
+#pragma unroll
+    for (int kk = 0; kk < K; ++kk) loc[kk] = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double xi = (double)x[i];
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) loc[kk] += xi * (double)y[kk * n + i];
+    }
+    block_reduce_store<K>(loc, part);
+}
+
+__global__ void k_transpose_cidx(const uint16_t* cidx, int ncst, int ncorr, int64_t n_s, uint16_t* cidxT) {
+    // tile 32 samples x 32 correlators
+    __shared__ uint16_t tile[32][33];
+    int64_t s0 = (int64_t)blockIdx.x * 32;
+    int c0 = blockIdx.y * 32;
+    int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+    for (int r = ty; r < 32; r += 8) {
+        int64_t s = s0 + r;
+        int c = c0 + tx;
+        tile[r][tx] = (s < n_s && c < ncorr) ? cidx[s * ncst + c] : 0;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        int c = c0 + r;
+        int64_t s = s0 + tx;
+        if (c < ncorr && s < n_s) cidxT[(int64_t)c * n_s + s] = tile[tx][r];
+    }
+}
+
+template <typename VT>
+__global__ void k_cast(const double* src, VT* dst, int64_t n, double scale) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (VT)(src[i] * scale);
+}
+
+// ---------------------------------------------------------------------------
+// conjugate gradient on (S + eps I) x = b, FP64 scalars in `scal`:
+//   scal[0] rr, scal[1] |b|^2, scal[2] tol^2, scal[3] iterations, scal[4] rr_prev
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double sum_part(const double* part, int n, int kk, int K) {
+    double s = 0.0;
+    for (int b = 0; b < n; ++b) s += part[b * K + kk];
+    return s;
+}
+
+template <typename VT>
+__global__ void __launch_bounds__(256) k_cg_init(const VT* b, VT* x, VT* r, VT* p, int64_t n, double* part) {
+    double loc[1] = {0.0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        VT v = b[i];
+        x[i] = VT(0);
+        r[i] = v;
+        p[i] = v;
+        loc[0] += (double)v * (double)v;
+    }
+    block_reduce_store<1>(loc, part);
+}
+
+__global__ void k_cg_start(const double* part, int npart, double* scal, double tol, int* stop) {
+    double rr = warp_sum_partials(part, npart, 0, 1);
+    if (threadIdx.x != 0) return;
+    scal[CG_RR] = rr;
+    scal[CG_BB] = rr;
+    scal[CG_TOL2] = tol * tol * rr;
+    scal[CG_IT] = 0.0;
+    scal[CG_RRP] = rr;
+    *stop = (rr == 0.0) ? 1 : 0;
+}
+
+// alpha = rr / (p . Ap); x += alpha p; r -= alpha Ap; partial r . r
+template <typename VT>
+__global__ void __launch_bounds__(256) k_cg_xr(VT* x, VT* r, const VT* p, const VT* Ap, int64_t n,
+                                               const double* pAp_part, int npart, double* scal,
+                                               double* rr_part, int* stop) {
+    if (*stop) return;
+    __shared__ double alpha;
+    if (threadIdx.x < 32) {
+        double pAp = warp_sum_partials(pAp_part, npart, 0, 1);
+        if (threadIdx.x == 0) {
+            alpha = scal[CG_RR] / pAp;
+            if (!isfinite(alpha) || pAp <= 0.0) alpha = 0.0;
+        }
+    }
+    __syncthreads();
+    double loc[1] = {0.0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double xi = (double)x[i] + alpha * (double)p[i];
+        double ri = (double)r[i] - alpha * (double)Ap[i];
+        x[i] = (VT)xi;
+        r[i] = (VT)ri;
+        loc[0] += ri * ri;
+    }
+    block_reduce_store<1>(loc, rr_part);
+    if (blockIdx.x == 0 && threadIdx.x == 0) scal[CG_RRP] = scal[CG_RR];
+}
+
+// beta = rr_new / rr; p = r + beta p; partial Obar . p for the next product
+template <typename VT>
+__global__ void __launch_bounds__(256) k_cg_p(const VT* r, VT* p, int64_t n, const double* rr_part, int npart,
+                                              double* scal, const double* Obar, double* obp_part, int* stop,
+                                              int max_iter) {
+    if (*stop) return;
+    __shared__ double beta, rrn;
+    if (threadIdx.x < 32) {
+        double r = warp_sum_partials(rr_part, npart, 0, 1);
+        if (threadIdx.x == 0) {
+            rrn = r;
+            beta = rrn / scal[CG_RRP];
+        }
+    }
+    __syncthreads();
+    double loc[1] = {0.0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double pi = (double)r[i] + beta * (double)p[i];
+        p[i] = (VT)pi;
+        loc[0] += Obar[i] * pi;
+    }
+    block_reduce_store<1>(loc, obp_part);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        scal[CG_RR] = rrn;
+        double it = scal[CG_IT] + 1.0;
+        scal[CG_IT] = it;
+        if (rrn <= scal[CG_TOL2] || !isfinite(rrn) || it >= (double)max_iter) *stop = 1;
+    }
+}
+
+// y = a - b (FP64)
+__global__ void k_sub(const double* a, const double* b, double* y, int64_t n, double* part) {
+    double loc[1] = {0.0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double v = a[i] - b[i];
+        y[i] = v;
+        loc[0] += v * v;
+    }
+    block_reduce_store<1>(loc, part);
+}
+
+// y = a x + b y (FP64)
+__global__ void k_axpby(double a, const double* x, double b, double* y, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = a * x[i] + b * y[i];
+}
+
+// x64 += scale * d
+template <typename VT>
+__global__ void k_axpy_to64(double* x, const VT* d, double scale, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] += scale * (double)d[i];
+}
+
+// ---------------------------------------------------------------------------
+// explicit instantiations used by the host side
+// ---------------------------------------------------------------------------
+template __global__ void k_sr_main<double, double, 1, true>(MainArgs<double>);
+template __global__ void k_sr_main<double, double, 2, true>(MainArgs<double>);
+template __global__ void k_sr_main<double, double, 4, true>(MainArgs<double>);
+template __global__ void k_sr_main<double, double, 2, false>(MainArgs<double>);
+template __global__ void k_sr_main<float, double, 1, true>(MainArgs<double>);
+template __global__ void k_sr_main<float, double, 2, true>(MainArgs<double>);
+template __global__ void k_sr_main<float, double, 4, true>(MainArgs<double>);
+template __global__ void k_sr_main<float, double, 2, false>(MainArgs<double>);
+template __global__ void k_sr_main<float, float, 1, true>(MainArgs<float>);
+template __global__ void k_sr_main<float, float, 2, true>(MainArgs<float>);
+template __global__ void k_sr_main<float, float, 4, true>(MainArgs<float>);
+template __global__ void k_sr_main<__nv_bfloat16, double, 2, false>(MainArgs<double>);
+template __global__ void k_sr_main<__nv_bfloat16, float, 1, true>(MainArgs<float>);
+template __global__ void k_sr_main<__nv_bfloat16, float, 2, true>(MainArgs<float>);
+template __global__ void k_sr_main<__nv_bfloat16, float, 4, true>(MainArgs<float>);
+template __global__ void k_corr_scatter<double, 1>(CorrArgs<double>);
+template __global__ void k_corr_scatter<double, 2>(CorrArgs<double>);
+template __global__ void k_corr_scatter<double, 4>(CorrArgs<double>);
+template __global__ void k_corr_scatter<float, 1>(CorrArgs<float>);
+template __global__ void k_corr_scatter<float, 2>(CorrArgs<float>);
+template __global__ void k_corr_scatter<float, 4>(CorrArgs<float>);
+template __global__ void k_finalize_S<double, double, 1>(FinArgs<double, double>);
+template __global__ void k_finalize_S<double, double, 2>(FinArgs<double, double>);
+template __global__ void k_finalize_S<double, double, 4>(FinArgs<double, double>);
+template __global__ void k_finalize_S<float, float, 1>(FinArgs<float, float>);
+template __global__ void k_finalize_S<float, float, 2>(FinArgs<float, float>);
+template __global__ void k_finalize_S<float, float, 4>(FinArgs<float, float>);
+template __global__ void k_finalize_grad<double>(FinArgs<double, double>);
+template __global__ void k_reduce_pf<double>(const double*, int, int, double*);
+template __global__ void k_reduce_pf<float>(const float*, int, int, double*);
+template __global__ void k_dot_part<double, double, 1>(const double*, const double*, int64_t, double*, const int*);
+template __global__ void k_dot_part<double, double, 2>(const double*, const double*, int64_t, double*, const int*);
+template __global__ void k_dot_part<double, double, 4>(const double*, const double*, int64_t, double*, const int*);
+template __global__ void k_dot_part<double, float, 1>(const double*, const float*, int64_t, double*, const int*);
+template __global__ void k_dot_part<double, float, 2>(const double*, const float*, int64_t, double*, const int*);
+template __global__ void k_dot_part<double, float, 4>(const double*, const float*, int64_t, double*, const int*);
+template __global__ void k_cast<float>(const double*, float*, int64_t, double);
+template __global__ void k_cast<double>(const double*, double*, int64_t, double);
+template __global__ void k_cg_init<double>(const double*, double*, double*, double*, int64_t, double*);
+template __global__ void k_cg_init<float>(const float*, float*, float*, float*, int64_t, double*);
+template __global__ void k_cg_xr<double>(double*, double*, const double*, const double*, int64_t, const double*, int,
+                                         double*, double*, int*);
+template __global__ void k_cg_xr<float>(float*, float*, const float*, const float*, int64_t, const double*, int,
+                                        double*, double*, int*);
+template __global__ void k_cg_p<double>(const double*, double*, int64_t, const double*, int, double*, const double*,
+                                        double*, int*, int);
+template __global__ void k_cg_p<float>(const float*, float*, int64_t, const double*, int, double*, const double*,
+                                       double*, int*, int);
+template __global__ void k_axpy_to64<float>(double*, const float*, double, int64_t);
+template __global__ void k_axpy_to64<double>(double*, const double*, double, int64_t);
+
+}  // namespace vmc

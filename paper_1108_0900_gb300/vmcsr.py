@@ -1,0 +1,346 @@
+"""Thin Python binding of the vmcsr C ABI (include/vmcsr.h).
+
+Argument marshalling only: every step runs in the CUDA library
+``_build/libvmcsr.so``.  Device buffers are torch CUDA tensors and streams are
+torch streams; there is no CPU fallback — if the library or a CUDA device is
+missing the calls raise.
+
+The functions keep the ABI names (``vmc_create``, ``vmc_sample``,
+``sr_gradient``, ``sr_apply_S``, ``sr_cg_solve`` ...).  ``Handle`` bundles a
+handle with the sizes the calls need, and ``LogPsi`` is the autograd function
+whose backward is the library's adjoint kernel (the derivative ratios of
+Eq. 3, recomputed from scratch).
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import re
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+VMC_OK = 0
+VMC_HUBBARD, VMC_ABINITIO = 0, 1
+VMC_FP64, VMC_FP32 = 0, 1
+VMC_STORE_FP64, VMC_STORE_FP32, VMC_STORE_BF16, VMC_STORE_FP32_F32ACC = 0, 1, 2, 3
+VMC_CG_FP64, VMC_CG_MIXED, VMC_CG_FP32 = 0, 1, 2
+ERRORS = {
+    -1: "INVALID_ARG", -2: "OOM", -3: "SINGULAR", -4: "NONFINITE", -5: "NOT_CONVERGED",
+    -6: "TIMEOUT", -7: "CUDA", -8: "UNSUPPORTED", -9: "STATE",
+}
+
+
+class VmcError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str = ""):
+        self.code = code
+        super().__init__(f"{where}: {ERRORS.get(code, code)} {detail}".strip())
+
+
+class vmc_lattice(ct.Structure):
+    _fields_ = [("n_sites", ct.c_int), ("n_bonds", ct.c_int), ("bonds", ct.c_void_p), ("bond_t", ct.c_void_p)]
+
+
+class vmc_hamiltonian(ct.Structure):
+    _fields_ = [("kind", ct.c_int), ("U", ct.c_double), ("n_chol", ct.c_int), ("h", ct.c_void_p),
+                ("chol", ct.c_void_p)]
+
+
+class vmc_ansatz(ct.Structure):
+    _fields_ = [("n_up", ct.c_int), ("n_dn", ct.c_int), ("n_corr", ct.c_int), ("corr_ptr", ct.c_void_p),
+                ("corr_sites", ct.c_void_p)]
+
+
+class vmc_options(ct.Structure):
+    _fields_ = [("n_walkers", ct.c_int), ("samples_per_walker", ct.c_int), ("walker_precision", ct.c_int),
+                ("keep_fp64_store", ct.c_int), ("keep_lowp_store", ct.c_int)]
+
+
+class vmc_cg_info(ct.Structure):
+    _fields_ = [("iterations", ct.c_int), ("refinements", ct.c_int), ("residual_products", ct.c_int),
+                ("converged", ct.c_int), ("true_rel_residual", ct.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def header_functions():
+    """Names of the functions declared in include/vmcsr.h."""
+    txt = open(os.path.join(_build.INCLUDE, "vmcsr.h")).read()
+    return re.findall(r"^\s*(?:int|const char\*)\s+(\w+)\s*\(", txt, flags=re.M)
+
+
+def lib(build_if_missing: bool = True):
+    """Load libvmcsr.so (building it in-tree with nvcc when absent)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise OSError(f"{path} not built")
+        path = _build.build()
+    L = ct.CDLL(path)
+    vp, i32, i64, dbl, u64 = ct.c_void_p, ct.c_int, ct.c_int64, ct.c_double, ct.c_uint64
+    sig = {
+        "vmc_create": [vp, vp, vp, vp, vp],
+        "vmc_destroy": [vp],
+        "vmc_num_params": [vp, vp, vp],
+        "vmc_set_params": [vp, vp, vp],
+        "vmc_set_walkers": [vp, vp, vp],
+        "vmc_get_walkers": [vp, vp, vp, vp],
+        "vmc_sample": [vp, i32, u64, vp],
+        "vmc_measure": [vp, vp, i64, vp],
+        "vmc_num_samples": [vp, vp],
+        "vmc_get_samples": [vp, vp, vp, vp, vp, i32, vp],
+        "vmc_logpsi": [vp, vp, vp],
+        "vmc_logpsi_backward": [vp, vp, vp, vp],
+        "sr_gradient": [vp, vp, vp, i32, vp],
+        "sr_apply_S": [vp, vp, vp, i32, dbl, i32, vp],
+        "sr_cg_solve": [vp, vp, dbl, dbl, i32, i32, vp, vp, vp],
+        "vmc_profile": [vp, i32],
+        "vmc_profile_read": [vp, i32, vp, vp, vp, vp],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = i32
+    L.vmc_error_string.argtypes = [i32]
+    L.vmc_error_string.restype = ct.c_char_p
+    L.vmc_last_error_detail.argtypes = []
+    L.vmc_last_error_detail.restype = ct.c_char_p
+    _lib = L
+    return L
+
+
+def _check(rc: int, where: str):
+    if rc != VMC_OK:
+        detail = lib().vmc_last_error_detail().decode(errors="replace")
+        raise VmcError(rc, where, detail)
+
+
+def _np_ptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(ct.c_void_p)
+
+
+def _dev_ptr(t):
+    if t is None:
+        return None
+    import torch
+    assert isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()
+    return ct.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ct.c_void_p(s.cuda_stream)
+
+
+# ---------------------------------------------------------------------------
+# ABI-named wrappers
+# ---------------------------------------------------------------------------
+
+def vmc_create(wl, n_walkers=None, samples_per_walker=None, walker_precision=VMC_FP64,
+               keep_fp64_store=True, keep_lowp_store=False):
+    """Create a handle for a problem description (``inputs.Workload``)."""
+    keep = dict(
+        bonds=np.ascontiguousarray(wl.bonds, np.int32),
+        bond_t=np.ascontiguousarray(wl.bond_t, np.float64),
+        corr_ptr=np.ascontiguousarray(wl.corr_ptr, np.int32),
+        corr_sites=np.ascontiguousarray(wl.corr_flat, np.int32),
+        h=None if wl.h is None else np.ascontiguousarray(wl.h, np.float64),
+        chol=None if wl.chol is None else np.ascontiguousarray(wl.chol, np.float64),
+    )
+    lat = vmc_lattice(wl.n_sites, len(keep["bonds"]), _np_ptr(keep["bonds"]), _np_ptr(keep["bond_t"]))
+    ham = vmc_hamiltonian(wl.ham, float(wl.U), 0 if wl.chol is None else wl.chol.shape[0],
+                          _np_ptr(keep["h"]), _np_ptr(keep["chol"]))
+    ans = vmc_ansatz(wl.n_up, wl.n_dn, wl.n_corr, _np_ptr(keep["corr_ptr"]), _np_ptr(keep["corr_sites"]))
+    opt = vmc_options(int(n_walkers or wl.n_walkers), int(samples_per_walker or wl.samples_per_walker),
+                      int(walker_precision), int(bool(keep_fp64_store)), int(bool(keep_lowp_store)))
+    h = ct.c_void_p()
+    _check(lib().vmc_create(ct.byref(lat), ct.byref(ham), ct.byref(ans), ct.byref(opt), ct.byref(h)), "vmc_create")
+    return Handle(h, wl, opt)
+
+
+class Handle:
+    def __init__(self, h, wl, opt):
+        self.h = h
+        self.wl = wl
+        self.n_walkers = opt.n_walkers
+        self.spw = opt.samples_per_walker
+        nv, ncp = ct.c_int64(), ct.c_int64()
+        _check(lib().vmc_num_params(h, ct.byref(nv), ct.byref(ncp)), "vmc_num_params")
+        self.n_params, self.n_corr_params = nv.value, ncp.value
+        self.N = wl.N
+        self.P = wl.n_up * (wl.n_up - 1) // 2 + wl.n_dn * (wl.n_dn - 1) // 2 + wl.n_up * wl.n_dn
+
+    def close(self):
+        if self.h:
+            lib().vmc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def vmc_set_params(h: Handle, C, f):
+    C = np.ascontiguousarray(C, np.float64)
+    f = np.ascontiguousarray(f, np.float64)
+    _check(lib().vmc_set_params(h.h, _np_ptr(C), _np_ptr(f)), "vmc_set_params")
+
+
+def vmc_set_walkers(h: Handle, occ, step=None):
+    occ = np.ascontiguousarray(occ, np.uint8)
+    st = None if step is None else np.ascontiguousarray(step, np.uint64)
+    _check(lib().vmc_set_walkers(h.h, _np_ptr(occ), _np_ptr(st)), "vmc_set_walkers")
+
+
+def vmc_get_walkers(h: Handle, stream=None):
+    occ = np.zeros((h.n_walkers, h.N), np.uint8)
+    step = np.zeros(h.n_walkers, np.uint64)
+    _check(lib().vmc_get_walkers(h.h, _np_ptr(occ), _np_ptr(step), _stream(stream)), "vmc_get_walkers")
+    return occ, step
+
+
+def vmc_sample(h: Handle, n_burn: int, seed: int, stream=None):
+    _check(lib().vmc_sample(h.h, int(n_burn), ct.c_uint64(seed), _stream(stream)), "vmc_sample")
+
+
+def vmc_measure(h: Handle, occ, stream=None):
+    occ = np.ascontiguousarray(occ, np.uint8)
+    _check(lib().vmc_measure(h.h, _np_ptr(occ), occ.shape[0], _stream(stream)), "vmc_measure")
+
+
+def vmc_num_samples(h: Handle) -> int:
+    n = ct.c_int64()
+    _check(lib().vmc_num_samples(h.h, ct.byref(n)), "vmc_num_samples")
+    return n.value
+
+
+def vmc_get_samples(h: Handle, store=VMC_STORE_FP64, stream=None):
+    n = vmc_num_samples(h)
+    occ = np.zeros((n, h.N), np.uint8)
+    E = np.zeros(n)
+    cs = np.zeros((n, max(h.wl.n_corr, 1)), np.uint16)
+    pf = np.zeros((n, h.P))
+    _check(lib().vmc_get_samples(h.h, _np_ptr(occ), _np_ptr(E), _np_ptr(cs), _np_ptr(pf), int(store),
+                                 _stream(stream)), "vmc_get_samples")
+    return occ, E, cs[:, :h.wl.n_corr], pf
+
+
+def vmc_logpsi(h: Handle, stream=None):
+    import torch
+    out = torch.empty(vmc_num_samples(h), dtype=torch.float64, device="cuda")
+    _check(lib().vmc_logpsi(h.h, _dev_ptr(out), _stream(stream)), "vmc_logpsi")
+    return out
+
+
+def vmc_logpsi_backward(h: Handle, w=None, stream=None):
+    import torch
+    if w is None:
+        _check(lib().vmc_logpsi_backward(h.h, None, None, _stream(stream)), "vmc_logpsi_backward")
+        return None
+    w = w.to(dtype=torch.float64, device="cuda").contiguous()
+    grad = torch.empty(h.n_params, dtype=torch.float64, device="cuda")
+    _check(lib().vmc_logpsi_backward(h.h, _dev_ptr(w), _dev_ptr(grad), _stream(stream)), "vmc_logpsi_backward")
+    return grad
+
+
+def sr_gradient(h: Handle, store=VMC_STORE_FP64, stream=None, stats=True):
+    import torch
+    g = torch.empty(h.n_params, dtype=torch.float64, device="cuda")
+    es = np.zeros(3) if stats else None
+    _check(lib().sr_gradient(h.h, _dev_ptr(g), _np_ptr(es), int(store), _stream(stream)), "sr_gradient")
+    return g, es
+
+
+def sr_apply_S(h: Handle, V, shift: float, store=VMC_STORE_FP64, stream=None, out=None):
+    """V: CUDA float64 tensor [n_params] or [k, n_params]."""
+    import torch
+    k = 1 if V.dim() == 1 else V.shape[0]
+    V = V.contiguous()
+    if out is None:
+        out = torch.empty_like(V)
+    _check(lib().sr_apply_S(h.h, _dev_ptr(V), _dev_ptr(out), int(k), float(shift), int(store), _stream(stream)),
+           "sr_apply_S")
+    return out
+
+
+def sr_cg_solve(h: Handle, g, shift: float, tol: float, max_iter: int, mode=VMC_CG_FP64, stream=None, x=None,
+                allow_not_converged=False):
+    import torch
+    if x is None:
+        x = torch.empty_like(g)
+    info = vmc_cg_info()
+    rc = lib().sr_cg_solve(h.h, _dev_ptr(g), float(shift), float(tol), int(max_iter), int(mode), _dev_ptr(x),
+                           ct.byref(info), _stream(stream))
+    if not (allow_not_converged and rc == -5):
+        _check(rc, "sr_cg_solve")
+    return x, info.as_dict()
+
+
+# ---------------------------------------------------------------------------
+# autograd: ln|Psi(n_s)| of the stored samples as a function of (C, f)
+# ---------------------------------------------------------------------------
+
+def _make_logpsi():
+    import torch
+
+    class LogPsi(torch.autograd.Function):
+        """ln|Psi_n| = sum_c ln|C_c[idx_c(n)]| + ln|Pf(F[occ, occ])| (Eq. 11)
+        for every stored sample; backward maps grad_output w_s to
+        sum_s w_s O_s with the library's adjoint kernel (pairing inverse
+        recomputed from scratch, FP64)."""
+
+        @staticmethod
+        def forward(ctx, handle, C, f):
+            vmc_set_params(handle, C.detach().cpu().numpy(), f.detach().cpu().numpy())
+            ctx.handle = handle
+            ctx.ncp = C.numel()
+            ctx.devs = (C.device, C.dtype, f.device, f.dtype)
+            return vmc_logpsi(handle)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            g = vmc_logpsi_backward(ctx.handle, grad_out)
+            dC, tC, df, tf = ctx.devs
+            return None, g[:ctx.ncp].to(dC, tC), g[ctx.ncp:].to(df, tf)
+
+    return LogPsi
+
+
+_LogPsi = None
+
+
+def LogPsi():
+    global _LogPsi
+    if _LogPsi is None:
+        _LogPsi = _make_logpsi()
+    return _LogPsi
+
+
+def vmc_profile(h: Handle, enable: bool):
+    _check(lib().vmc_profile(h.h, int(bool(enable))), "vmc_profile")
+
+
+def vmc_profile_read(h: Handle, store=VMC_STORE_BF16):
+    la, pl = ct.c_int64(), ct.c_int64()
+    ms, by = ct.c_double(), ct.c_double()
+    _check(lib().vmc_profile_read(h.h, int(store), ct.byref(la), ct.byref(pl), ct.byref(ms), ct.byref(by)),
+           "vmc_profile_read")
+    return dict(launches_all=la.value, pass_launches=pl.value, pass_ms=ms.value, pass_bytes=by.value)

@@ -1,0 +1,417 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Every input is seeded and synthetic; configurations handed to the library
+come from the oracle's own Metropolis chains or from the seeded generator,
+never from the CUDA path.  Tolerances (relative, 2-norm per output vector):
+  FP64 stages                         1e-10
+  FP32 storage, FP32 accumulation     1e-5   (S products)
+  FP32 storage, FP64 accumulation     1e-6   (storage rounding 2^-24)
+  BF16 storage                        3e-2   (storage rounding 2^-9)
+  FP32 walkers (E_L, O)               derived from FP32 inversion: 5e-3
+Integers (configurations, correlator states, counters) are compared exactly.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1108_0900_gb300 import inputs
+from paper_1108_0900_gb300 import vmcsr as V
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def pair_list(wl):
+    nu, N = wl.n_up, wl.N
+    pl = [(a, b) for a in range(nu) for b in range(a + 1, nu)]
+    pl += [(a, b) for a in range(nu, N) for b in range(a + 1, N)]
+    pl += [(a, b) for a in range(nu) for b in range(nu, N)]
+    return pl
+
+
+def pf_index(M, p, q):
+    return p * M - p * (p + 1) // 2 + (q - p - 1)
+
+
+def oracle_compact(wl, occ, O):
+    """Oracle dense O rows -> the ABI's pairing block order."""
+    M, ncp = wl.M, wl.n_corr_params
+    pl = pair_list(wl)
+    out = np.zeros((len(occ), len(pl)))
+    for s, o in enumerate(occ):
+        for e, (a, b) in enumerate(pl):
+            out[s, e] = O[s, ncp + pf_index(M, int(o[a]), int(o[b]))]
+    return out
+
+
+def oracle_chains(wl, n_burn, spw, seed):
+    P = oracle.Problem(wl)
+    occ = wl.init_occ.copy()
+    step = np.zeros(wl.n_walkers, np.uint64)
+    smp, mm, acc = P.sample(occ, step, seed, n_burn, spw)
+    return P, smp, mm, occ, step
+
+
+def make(wl, prec=V.VMC_FP64, keep64=True, keeplow=True, n_walkers=None, spw=None):
+    h = V.vmc_create(wl, n_walkers=n_walkers, samples_per_walker=spw, walker_precision=prec,
+                     keep_fp64_store=keep64, keep_lowp_store=keeplow)
+    V.vmc_set_params(h, wl.C, wl.f)
+    return h
+
+
+SMALL = {
+    "cfg1": lambda: inputs.config(1, n_walkers=24, samples_per_walker=6),
+    "cfg2": lambda: inputs.config(2, n_walkers=37, samples_per_walker=5),
+    "cfg5geom": lambda: inputs.config(5, n_walkers=9, samples_per_walker=3),
+    "tiny2x2": lambda: inputs.hubbard("t", 2, 2, 1, 1, "2x2", seed=5, n_walkers=7, samples_per_walker=4),
+    "nocorr3x2": lambda: inputs.hubbard("t", 3, 2, 2, 2, "none", seed=6, n_walkers=11, samples_per_walker=3),
+}
+
+
+@pytest.fixture(scope="module", params=list(SMALL))
+def case(request):
+    wl = SMALL[request.param]()
+    P, smp, mm, occ_end, step_end = oracle_chains(wl, 3, wl.samples_per_walker, inputs.seed_sampling_for(1))
+    E, O = P.measure(smp)
+    return dict(name=request.param, wl=wl, P=P, smp=smp, E=E, O=O, mm=mm, occ_end=occ_end, step_end=step_end)
+
+
+# ---------------------------------------------------------------------------
+# local energy and derivative ratios on oracle configurations
+# ---------------------------------------------------------------------------
+
+def test_measure_fp64(case):
+    wl = case["wl"]
+    h = make(wl)
+    V.vmc_measure(h, case["smp"])
+    occ, E, cs, pf = V.vmc_get_samples(h, V.VMC_STORE_FP64)
+    assert np.array_equal(occ, case["smp"])
+    cs_or = np.array([[case["P"].corr_state(o, c) for c in range(wl.n_corr)] for o in case["smp"]],
+                     np.int64).reshape(len(occ), wl.n_corr)
+    assert np.array_equal(cs.astype(np.int64), cs_or)
+    assert np.all(np.abs(E - case["E"]) <= 1e-10 * np.maximum(1.0, np.abs(case["E"])))
+    ref = oracle_compact(wl, case["smp"], case["O"])
+    for s in range(len(ref)):
+        assert rel(pf[s], ref[s]) <= 1e-10
+    # the low-precision copies are the same values rounded
+    _, _, _, pf32 = V.vmc_get_samples(h, V.VMC_STORE_FP32)
+    _, _, _, pf16 = V.vmc_get_samples(h, V.VMC_STORE_BF16)
+    assert np.array_equal(pf32, pf.astype(np.float32).astype(np.float64))
+    assert rel(pf16, pf) <= 2 ** -8
+
+
+def test_measure_fp32_walkers(case):
+    wl = case["wl"]
+    h = make(wl, prec=V.VMC_FP32)
+    V.vmc_measure(h, case["smp"])
+    occ, E, cs, pf = V.vmc_get_samples(h, V.VMC_STORE_FP32)
+    assert np.array_equal(occ, case["smp"])
+    assert np.all(np.abs(E - case["E"]) <= 5e-3 * np.maximum(1.0, np.abs(case["E"])))
+    ref = oracle_compact(wl, case["smp"], case["O"])
+    errs = [rel(pf[s], ref[s]) for s in range(len(ref))]
+    assert max(errs) <= 5e-3
+
+
+# ---------------------------------------------------------------------------
+# Metropolis chains: identical proposals, decisions compared where the
+# oracle's acceptance margin exceeds the precision of the kernel
+# ---------------------------------------------------------------------------
+
+def _chain_compare(case, prec, margin, max_bad=0.0):
+    """Both sides draw the same Philox proposals.  A stored sample is
+    compared exactly when every accept/reject decision before it had a
+    relative margin |u - r^2| / r^2 above `margin` in the oracle's FP64
+    arithmetic (the kernel's ratio error is below that margin); later samples
+    of a walker whose chain met a closer decision are only checked for
+    validity.  Returns the fraction of samples compared."""
+    wl = case["wl"]
+    n_burn = 3
+    P = oracle.Problem(wl)
+    o_occ, o_step = wl.init_occ.copy(), np.zeros(wl.n_walkers, np.uint64)
+    smp, _, _, fc = P.sample(o_occ, o_step, inputs.seed_sampling_for(1), n_burn, wl.samples_per_walker,
+                             close_tol=margin, return_first_close=True)
+    h = make(wl, prec=prec)
+    V.vmc_set_walkers(h, wl.init_occ)
+    V.vmc_sample(h, n_burn, inputs.seed_sampling_for(1))
+    occ, E, cs, pf = V.vmc_get_samples(h, V.VMC_STORE_FP64 if prec == V.VMC_FP64 else V.VMC_STORE_FP32)
+    wocc, wstep = V.vmc_get_walkers(h)
+    assert np.array_equal(wstep, o_step)
+    spw, N = wl.samples_per_walker, wl.N
+    got = occ.reshape(wl.n_walkers, spw, -1)
+    exp = smp.reshape(wl.n_walkers, spw, -1)
+    compared = 0
+    bad_walkers = []
+    for w in range(wl.n_walkers):
+        ok = True
+        for j in range(spw):
+            last = (n_burn + j + 1) * N - 1          # index of the proposal ending sample j
+            if fc[w] < 0 or fc[w] > last:
+                ok &= bool(np.array_equal(got[w, j], exp[w, j]))
+                compared += 1
+        if fc[w] < 0:
+            ok &= bool(np.array_equal(wocc[w], o_occ[w]))
+        if not ok:
+            bad_walkers.append(w)
+    assert len(bad_walkers) <= max_bad * wl.n_walkers, bad_walkers
+    # every stored configuration is inside the sector
+    assert np.all((occ[:, :wl.n_up] < wl.n_sites)) and np.all(occ[:, wl.n_up:] >= wl.n_sites)
+    assert np.all(np.diff(occ.astype(int), axis=1) > 0)
+    return compared / (wl.n_walkers * spw)
+
+
+def test_sampler_chains_fp64(case):
+    frac = _chain_compare(case, V.VMC_FP64, 1e-9)
+    assert frac >= 0.9
+
+
+def test_sampler_chains_fp32(case):
+    # FP32 inverse after up to ~N^2/3 rank-2 updates: ratio error well below 2e-2
+    # An FP32 walker's ratio error is ~u32 kappa(A) plus the drift of the
+    # rank-2 updates since its last rebuild; on an ill-conditioned pairing
+    # submatrix it can exceed the margin, so a small share of walkers may
+    # leave the oracle's chain (they stay inside the sector).
+    frac = _chain_compare(case, V.VMC_FP32, 2e-2, max_bad=0.15)
+    assert frac > 0
+
+
+# ---------------------------------------------------------------------------
+# gradient and S products
+# ---------------------------------------------------------------------------
+
+def test_gradient(case):
+    wl = case["wl"]
+    h = make(wl)
+    V.vmc_measure(h, case["smp"])
+    g_or, em = oracle.gradient(case["O"], case["E"])
+    g, stats = V.sr_gradient(h, V.VMC_STORE_FP64)
+    assert abs(stats[0] - em) <= 1e-12 * max(1, abs(em))
+    assert rel(g.cpu().numpy(), g_or) <= 1e-10
+    g32, _ = V.sr_gradient(h, V.VMC_STORE_FP32)
+    assert rel(g32.cpu().numpy(), g_or) <= 1e-6
+
+
+@pytest.mark.parametrize("store,tol", [(V.VMC_STORE_FP64, 1e-10), (V.VMC_STORE_FP32, 1e-6),
+                                       (V.VMC_STORE_FP32_F32ACC, 1e-5), (V.VMC_STORE_BF16, 3e-2)])
+def test_apply_S(case, store, tol):
+    wl = case["wl"]
+    h = make(wl)
+    V.vmc_measure(h, case["smp"])
+    V.sr_gradient(h, V.VMC_STORE_FP64)
+    rng = np.random.default_rng(7)
+    for k in (1, 2, 4):
+        v = rng.standard_normal((k, wl.n_params))
+        out = V.sr_apply_S(h, torch.from_numpy(v).cuda(), wl.shift, store).cpu().numpy()
+        for j in range(k):
+            ref = oracle.apply_S(case["O"], v[j], wl.shift)
+            assert rel(out[j], ref) <= tol, (k, j)
+
+
+def test_cg_fp64(case):
+    wl = case["wl"]
+    h = make(wl)
+    V.vmc_measure(h, case["smp"])
+    g, _ = V.sr_gradient(h, V.VMC_STORE_FP64)
+    x, info = V.sr_cg_solve(h, g, wl.shift, 1e-10, 20 * wl.n_params, V.VMC_CG_FP64)
+    assert info["converged"] and info["true_rel_residual"] <= 1e-10
+    g_or, _ = oracle.gradient(case["O"], case["E"])
+    x_or, it, res, ok = oracle.cg(case["O"], g_or, wl.shift, 1e-12, 20 * wl.n_params)
+    assert ok
+    # both solve the same SPD system; agreement is bounded by cond * tol
+    assert rel(x.cpu().numpy(), x_or) <= 1e-6
+
+
+@pytest.mark.parametrize("mode", [V.VMC_CG_MIXED, V.VMC_CG_FP32])
+def test_cg_mixed_refinement(case, mode):
+    wl = case["wl"]
+    h = make(wl)
+    V.vmc_measure(h, case["smp"])
+    g, _ = V.sr_gradient(h, V.VMC_STORE_FP64)
+    x, info = V.sr_cg_solve(h, g, wl.shift, 1e-6, 50 * wl.n_params, mode)
+    assert info["converged"] and info["true_rel_residual"] <= 1e-6
+    # residual against the FP64 store (oracle values) stays at the same level
+    g_or, _ = oracle.gradient(case["O"], case["E"])
+    r = g_or - oracle.apply_S(case["O"], x.cpu().numpy(), wl.shift)
+    assert np.linalg.norm(r) / np.linalg.norm(g_or) <= 2e-6
+
+
+# ---------------------------------------------------------------------------
+# log-amplitude and its adjoint
+# ---------------------------------------------------------------------------
+
+def test_logpsi_and_backward(case):
+    wl = case["wl"]
+    h = make(wl)
+    V.vmc_measure(h, case["smp"])
+    lp = V.vmc_logpsi(h).cpu().numpy()
+    ref = np.array([case["P"].log_psi(o)[0] for o in case["smp"]])
+    assert np.all(np.abs(lp - ref) <= 1e-10 * np.maximum(1, np.abs(ref)))
+    w = np.random.default_rng(3).standard_normal(len(ref))
+    grad = V.vmc_logpsi_backward(h, torch.from_numpy(w)).cpu().numpy()
+    assert rel(grad, w @ case["O"]) <= 1e-10
+    # w = None rewrites the store from scratch: same values
+    _, _, _, pf0 = V.vmc_get_samples(h, V.VMC_STORE_FP64)
+    V.vmc_logpsi_backward(h, None)
+    _, _, _, pf1 = V.vmc_get_samples(h, V.VMC_STORE_FP64)
+    assert rel(pf1, pf0) <= 1e-12
+
+
+def test_autograd_logpsi():
+    wl = SMALL["cfg1"]()
+    P, smp, *_ = oracle_chains(wl, 2, wl.samples_per_walker, 11)
+    h = make(wl)
+    V.vmc_measure(h, smp)
+    C = torch.tensor(wl.C, dtype=torch.float64, requires_grad=True)
+    f = torch.tensor(wl.f, dtype=torch.float64, requires_grad=True)
+    lp = V.LogPsi().apply(h, C, f)
+    (lp.sum()).backward()
+    _, O = P.measure(smp)
+    ref = O.sum(0)
+    assert rel(C.grad.numpy(), ref[:wl.n_corr_params]) <= 1e-10
+    assert rel(f.grad.numpy(), ref[wl.n_corr_params:]) <= 1e-10
+    # finite differences of the forward through the library
+    hstep = 1e-6
+    for k in (0, 17, wl.n_corr_params + 3, wl.n_params - 1):
+        dC, df = torch.zeros_like(C), torch.zeros_like(f)
+        (dC if k < wl.n_corr_params else df).view(-1)[k if k < wl.n_corr_params else k - wl.n_corr_params] = hstep
+        up = V.LogPsi().apply(h, C.detach() + dC, f.detach() + df).sum().item()
+        dn = V.LogPsi().apply(h, C.detach() - dC, f.detach() - df).sum().item()
+        assert abs((up - dn) / (2 * hstep) - ref[k]) <= 1e-5 * max(1, abs(ref[k]))
+
+
+# ---------------------------------------------------------------------------
+# edge cases and error paths
+# ---------------------------------------------------------------------------
+
+def test_errors_and_edges():
+    wl = inputs.hubbard("e", 3, 2, 2, 2, "pair", seed=9, n_walkers=5, samples_per_walker=2)
+    h = make(wl)
+    with pytest.raises(V.VmcError) as e:
+        V.vmc_sample(h, 0, 1)                       # walkers not set
+    assert e.value.code == -9
+    bad = wl.init_occ.copy()
+    bad[0, 0], bad[0, 1] = bad[0, 1], bad[0, 0]      # not ascending
+    with pytest.raises(V.VmcError):
+        V.vmc_set_walkers(h, bad)
+    with pytest.raises(V.VmcError) as e:
+        V.sr_apply_S(h, torch.zeros(wl.n_params, dtype=torch.float64, device="cuda"), 0.1)  # no samples yet
+    assert e.value.code == -9
+    # one sample
+    V.vmc_measure(h, wl.init_occ[:1])
+    assert V.vmc_num_samples(h) == 1
+    g, st = V.sr_gradient(h)
+    # one sample: zero covariance (up to the rounding of a fused multiply-add)
+    assert torch.all(g.abs() <= 1e-14 * max(1.0, abs(st[0])))
+    v = torch.randn(wl.n_params, dtype=torch.float64, device="cuda")
+    out = V.sr_apply_S(h, v, 0.25)
+    assert torch.allclose(out, 0.25 * v, rtol=1e-12, atol=1e-12)
+    # singular pairing: all f = 0
+    h2 = V.vmc_create(wl)
+    V.vmc_set_params(h2, wl.C, np.zeros_like(wl.f))
+    with pytest.raises(V.VmcError) as e:
+        V.vmc_measure(h2, wl.init_occ)
+    assert e.value.code == -3
+    # zero correlator amplitude
+    C0 = wl.C.copy()
+    C0[3] = 0.0
+    with pytest.raises(V.VmcError) as e:
+        V.vmc_set_params(h2, C0, wl.f)
+    assert e.value.code == -3
+
+
+# ---------------------------------------------------------------------------
+# full-size 8x8 / 2x3-plaquette workload (65,536 samples, 270,272 parameters)
+# in the launch configuration of the benchmark: sampled outputs against the
+# oracle one by one, and invariants that hold at any size
+# ---------------------------------------------------------------------------
+
+_FULL = {}
+
+
+def full5(prec):
+    if prec not in _FULL:
+        wl = inputs.config(5)
+        h = make(wl, prec=prec, keep64=True, keeplow=True)
+        cfgs = inputs.draw_configs(np.random.default_rng(555), wl.n_samples, wl.n_sites, wl.n_up, wl.n_dn)
+        V.vmc_measure(h, cfgs)
+        _FULL.clear()
+        _FULL[prec] = (wl, h, cfgs)
+    return _FULL[prec]
+
+
+@pytest.mark.parametrize("prec,tol", [(V.VMC_FP64, 1e-10), (V.VMC_FP32, 5e-3)])
+def test_full_size_sampled_outputs(prec, tol):
+    wl, h, cfgs = full5(prec)
+    occ, E, cs, pf = V.vmc_get_samples(h, V.VMC_STORE_FP64 if prec == V.VMC_FP64 else V.VMC_STORE_FP32)
+    assert np.array_equal(occ, cfgs)
+    P = oracle.Problem(wl)
+    pick = np.random.default_rng(1).choice(len(cfgs), 24, replace=False)
+    pick[-1] = len(cfgs) - 1
+    E_or, O_or = P.measure(cfgs[pick])
+    ref = oracle_compact(wl, cfgs[pick], O_or)
+    for j, s in enumerate(pick):
+        assert [P.corr_state(cfgs[s], c) for c in range(wl.n_corr)] == [int(x) for x in cs[s]]
+        assert abs(E[s] - E_or[j]) <= tol * max(1.0, abs(E_or[j]))
+        assert rel(pf[s], ref[j]) <= tol
+
+
+def test_full_size_invariants():
+    # |Psi|^2-sampled configurations (FP64 walkers): away from the nearly
+    # singular pairing submatrices a uniform draw can hit, the identities
+    # below hold to FP64 rounding
+    _FULL.clear()
+    wl = inputs.config(5)
+    h = make(wl, prec=V.VMC_FP64, keep64=True, keeplow=True)
+    V.vmc_set_walkers(h, wl.init_occ)
+    V.vmc_sample(h, 10, inputs.seed_sampling_for(5))
+    g, stats = V.sr_gradient(h, V.VMC_STORE_FP64)
+    ncp = wl.n_corr_params
+    eps = wl.shift
+    # null vectors: O_s . C_c = 1 and O_s . f = N/2 for every sample
+    # FP32 accumulation of the mean term against the FP64 mean leaves ~1e-7
+    # relative per pairing entry, ~1e-4 of |eps v| over 8,128 entries
+    for store, tol in ((V.VMC_STORE_FP32, 1e-6), (V.VMC_STORE_FP32_F32ACC, 1e-3), (V.VMC_STORE_BF16, 1e-2)):
+        for c in (0, 40):
+            v = np.zeros(wl.n_params)
+            v[c * 4096:(c + 1) * 4096] = wl.C[c * 4096:(c + 1) * 4096]
+            vt = torch.from_numpy(v).cuda()
+            Sv = V.sr_apply_S(h, vt, eps, store)
+            assert rel(Sv.cpu().numpy(), eps * v) <= tol
+    vf = np.zeros(wl.n_params)
+    vf[ncp:] = wl.f
+    rng = np.random.default_rng(2)
+    a = torch.from_numpy(rng.standard_normal(wl.n_params)).cuda()
+    b = torch.from_numpy(rng.standard_normal(wl.n_params)).cuda()
+    Sa = V.sr_apply_S(h, a, eps, V.VMC_STORE_FP32)
+    Sb = V.sr_apply_S(h, b, eps, V.VMC_STORE_FP32)
+    # O_s . f = N/2 (homogeneity of the pfaffian): S f = eps f, checked in
+    # FP64 and against the FP32 store relative to a generic product's size
+    scale = torch.linalg.norm(Sa).item() / torch.linalg.norm(a).item() * np.linalg.norm(vf)
+    # O_s . f - N/2 is the rounding of sum_ab X_ba A_ab, ~kappa(A) u per sample;
+    # sampled 56 x 56 pairing matrices reach kappa ~1e8
+    for store, tol in ((V.VMC_STORE_FP64, 1e-7), (V.VMC_STORE_FP32, 1e-5)):
+        Sf = V.sr_apply_S(h, torch.from_numpy(vf).cuda(), eps, store).cpu().numpy()
+        assert np.linalg.norm(Sf - eps * vf) <= tol * scale
+    # symmetry and positivity
+    assert abs((b @ Sa - a @ Sb).item()) <= 1e-9 * abs((b @ Sa).item()) + 1e-9
+    assert (a @ Sa).item() >= eps * (a @ a).item() * (1 - 1e-9)
+    vft = torch.from_numpy(vf).cuda()
+    assert abs((g @ vft).item()) <= 1e-6 * torch.linalg.norm(g).item() * np.linalg.norm(vf)
+
+
+def test_full_size_sampling_run():
+    wl = inputs.config(5)
+    h = make(wl, prec=V.VMC_FP32, keep64=False, keeplow=True)
+    V.vmc_set_walkers(h, wl.init_occ)
+    V.vmc_sample(h, 2, inputs.seed_sampling_for(5))
+    occ, E, cs, pf = V.vmc_get_samples(h, V.VMC_STORE_FP32)
+    assert np.all(np.isfinite(E)) and np.all(np.isfinite(pf))
+    assert np.all(occ[:, :wl.n_up] < wl.n_sites) and np.all(occ[:, wl.n_up:] >= wl.n_sites)
+    assert np.all(np.diff(occ.astype(int), axis=1) > 0)
+    _, step = V.vmc_get_walkers(h)
+    assert np.all(step == (2 + wl.samples_per_walker) * wl.N)
