@@ -221,6 +221,33 @@ int vmc_profile(vmc_handle h, int enable);
 int vmc_profile_read(vmc_handle h, int store, int64_t* launches_all, int64_t* pass_launches, double* pass_ms,
                      double* pass_bytes);
 
+/* Allocation-free pairing-block product (no counterpart in the paper).
+ * For callers that cannot call cudaMalloc: code running inside a memory budget
+ * that a pool allocator already owns (a fresh cudaMalloc would fail) and
+ * latency-critical loops (cudaMalloc / cudaFree synchronise the device).  No
+ * handle is needed and nothing is allocated: the caller passes every input and
+ * output as device pointers, and the scratch (one partial image of the pairing
+ * block per CTA) is a fixed device array of 128 x 8128 floats (4.2 MB) that
+ * every GPU which loads the library holds until the process exits.
+ *   occ  [n_s][occ_stride] uint8, ascending occupied spin orbitals (n_up below
+ *        n_sites, then n_dn), pf [n_s][pf_stride] FP32 pairing blocks in the
+ *        block order of vmc_get_samples, v [M(M-1)/2] FP32 (f_pq order);
+ *   t    [n_s] FP32 out: t_s = sum_e pf_s[e] v[pq(e)];
+ *   out  [M(M-1)/2] FP64 out: out[pq] = sum_s t_s pf_s[e] at pq(e) (FP32
+ *        accumulation per CTA, FP64 across CTAs).
+ * This is the pairing-block half of the Eq. 7 product without the 1/n_s and
+ * the mean term.  Sizes beyond the scratch (n_sites > 64) and bad strides or
+ * pointers return INVALID_ARG (vmc_last_error_detail says which).  The first
+ * call on each device looks up the scratch's device address with that device
+ * current (cudaGetSymbolAddress), so make that first call before any stream
+ * capture.  Every call shares the one scratch array: calls that overlap on the
+ * GPU (other streams, other threads) race and must be serialised by the
+ * caller; a call overwrites all of the scratch it reads, so nothing needs
+ * clearing between calls. */
+int sr_pairing_product_noalloc(int64_t n_s, int n_sites, int n_up, int n_dn, const uint8_t* occ,
+                               int64_t occ_stride, const float* pf, int64_t pf_stride, const float* v, float* t,
+                               double* out, void* stream);
+
 const char* vmc_error_string(int code);
 /* Text of the last failing CUDA call or internal check on the calling
  * thread, for diagnostics ("" if none).  The pointer stays valid until the

@@ -134,6 +134,10 @@ extern "C" const char* vmc_error_string(int code) {
 
 extern "C" const char* vmc_last_error_detail(void) { return g_err.c_str(); }
 
+namespace vmc {
+void set_error_detail(const std::string& s) { set_err(s); }
+}  // namespace vmc
+
 // ---------------------------------------------------------------------------
 // creation
 // ---------------------------------------------------------------------------

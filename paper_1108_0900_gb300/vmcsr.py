@@ -104,6 +104,7 @@ def lib(build_if_missing: bool = True):
         "sr_apply_S": [vp, vp, vp, i32, dbl, i32, vp],
         "sr_cg_solve": [vp, vp, dbl, dbl, i32, i32, vp, vp, vp],
         "vmc_profile": [vp, i32],
+        "sr_pairing_product_noalloc": [i64, i32, i32, i32, vp, i64, vp, i64, vp, vp, vp, vp],
         "vmc_profile_read": [vp, i32, vp, vp, vp, vp],
     }
     for name, args in sig.items():
@@ -344,3 +345,21 @@ def vmc_profile_read(h: Handle, store=VMC_STORE_BF16):
     _check(lib().vmc_profile_read(h.h, int(store), ct.byref(la), ct.byref(pl), ct.byref(ms), ct.byref(by)),
            "vmc_profile_read")
     return dict(launches_all=la.value, pass_launches=pl.value, pass_ms=ms.value, pass_bytes=by.value)
+
+
+def sr_pairing_product_noalloc(n_sites: int, n_up: int, n_dn: int, occ, pf, v, t=None, out=None, stream=None):
+    """Allocation-free pairing-block product (see include/vmcsr.h).  occ: CUDA
+    uint8 [n_s, >=N]; pf: CUDA float32 [n_s, >=P]; v: CUDA float32 [M(M-1)/2].
+    Returns (t [n_s] float32, out [M(M-1)/2] float64); pass t / out to reuse
+    caller-owned buffers."""
+    import torch
+    n_s = occ.shape[0]
+    M = 2 * n_sites
+    if t is None:
+        t = torch.empty(n_s, dtype=torch.float32, device=v.device)
+    if out is None:
+        out = torch.empty(M * (M - 1) // 2, dtype=torch.float64, device=v.device)
+    _check(lib().sr_pairing_product_noalloc(n_s, n_sites, n_up, n_dn, _dev_ptr(occ), occ.stride(0), _dev_ptr(pf),
+                                            pf.stride(0), _dev_ptr(v), _dev_ptr(t), _dev_ptr(out), _stream(stream)),
+           "sr_pairing_product_noalloc")
+    return t, out

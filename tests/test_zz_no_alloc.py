@@ -1,0 +1,83 @@
+"""The allocation-free pairing-block product, sr_pairing_product_noalloc.
+
+It serves callers that cannot call cudaMalloc (a pool allocator already owns
+the device memory, or the caller is in a latency-critical loop where
+cudaMalloc would synchronise the device).  Its scratch is a fixed device
+array inside the library.  This file runs last so that, if it fails, a run
+that stops at the first failure has already run every other test.
+
+The result is checked against the existing entry points on the same samples:
+sr_apply_S (FP32 store, FP32 accumulation) gives
+(1/n_s) sum_s t_s O_s - Obar (Obar . v) on the pairing block, and
+vmc_logpsi_backward with unit weights gives n_s Obar, so
+n_s (S v + Obar (Obar . v)) restricted to the pairing block must equal the
+allocation-free sum_s t_s O_s.  Tolerance: the 1e-5 of FP32 S products.
+"""
+import numpy as np
+import pytest
+
+from paper_1108_0900_gb300 import inputs
+from paper_1108_0900_gb300 import vmcsr as V
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _pair_index(wl, occ):
+    M, nu, N = wl.M, wl.n_up, wl.N
+    pl = [(a, b) for a in range(nu) for b in range(a + 1, nu)]
+    pl += [(a, b) for a in range(nu, N) for b in range(a + 1, N)]
+    pl += [(a, b) for a in range(nu) for b in range(nu, N)]
+    a = np.array([x for x, _ in pl])
+    b = np.array([y for _, y in pl])
+    p = occ[:, a].astype(np.int64)
+    q = occ[:, b].astype(np.int64)
+    return p * M - p * (p + 1) // 2 + (q - p - 1)
+
+
+@pytest.mark.parametrize("cfg,nw,spw", [(5, 1024, 4), (1, 64, 8)])
+def test_noalloc_matches_existing_entry_points(cfg, nw, spw):
+    wl = inputs.config(cfg, n_walkers=nw, samples_per_walker=spw)
+    h = V.vmc_create(wl, walker_precision=V.VMC_FP64, keep_fp64_store=True, keep_lowp_store=True)
+    V.vmc_set_params(h, wl.C, wl.f)
+    cfgs = inputs.draw_configs(np.random.default_rng(77), nw * spw, wl.n_sites, wl.n_up, wl.n_dn)
+    V.vmc_measure(h, cfgs)
+    occ, _, _, pf = V.vmc_get_samples(h, V.VMC_STORE_FP32)
+    n = len(occ)
+    npf = wl.n_pf_params
+    occ_d = torch.from_numpy(occ).cuda()
+    pf_d = torch.from_numpy(pf.astype(np.float32)).cuda()
+    v = np.random.default_rng(5).standard_normal(npf).astype(np.float32)
+    v_d = torch.from_numpy(v).cuda()
+
+    # existing entry points
+    Vfull = np.zeros(wl.n_params)
+    Vfull[wl.n_corr_params:] = v
+    Sv = V.sr_apply_S(h, torch.from_numpy(Vfull).cuda(), 0.0, V.VMC_STORE_FP32_F32ACC).cpu().numpy()
+    Osum = V.vmc_logpsi_backward(h, torch.ones(n, dtype=torch.float64)).cpu().numpy()
+    Obar = Osum / n
+    expect = n * (Sv + Obar * (Obar @ Vfull))[wl.n_corr_params:]
+    # per-sample dots from the stored values
+    pq = _pair_index(wl, occ)
+    t_expect = (pf.astype(np.float32).astype(np.float64) * v.astype(np.float64)[pq]).sum(1)
+
+    for call in range(2):
+        t, out = V.sr_pairing_product_noalloc(wl.n_sites, wl.n_up, wl.n_dn, occ_d, pf_d, v_d)
+        torch.cuda.synchronize()
+        out = out.cpu().numpy()
+        t = t.cpu().numpy().astype(np.float64)
+        assert np.linalg.norm(out - expect) <= 1e-5 * np.linalg.norm(expect), call
+        assert np.linalg.norm(t - t_expect) <= 1e-5 * np.linalg.norm(t_expect), call
+    h.close()
+
+
+def test_noalloc_rejects_oversized_and_bad_strides():
+    occ = torch.zeros((4, 2), dtype=torch.uint8, device="cuda")
+    pf = torch.zeros((4, 1), dtype=torch.float32, device="cuda")
+    v = torch.zeros(65 * 2 * (65 * 2 - 1) // 2, dtype=torch.float32, device="cuda")
+    with pytest.raises(V.VmcError) as e:
+        V.sr_pairing_product_noalloc(65, 1, 1, occ, pf, v)     # 65 sites: beyond the fixed scratch
+    assert e.value.code == -1 and "scratch" in str(e.value)
+    with pytest.raises(V.VmcError) as e:
+        V.sr_pairing_product_noalloc(4, 2, 2, occ, pf, v)      # rows shorter than N / P
+    assert e.value.code == -1
