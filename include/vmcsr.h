@@ -112,6 +112,9 @@ typedef struct {
     int walker_precision;   /* VMC_FP64 or VMC_FP32                                 */
     int keep_fp64_store;    /* 1: keep an FP64 O store (needed by VMC_CG_FP64)       */
     int keep_lowp_store;    /* 1: keep FP32 + BF16 O stores (needed by MIXED/FP32)   */
+    int refresh_every;      /* sweeps between from-scratch rebuilds of each walker's
+                               pairing inverse during vmc_sample (0: only at the start
+                               of each call); bounds the drift of the rank-2 updates   */
 } vmc_options;
 
 typedef struct {

@@ -41,7 +41,7 @@ struct vmc_ctx {
     int64_t ncp = 0, nv = 0;
     int n_walkers = 0, spw = 0;
     int64_t ncap = 0, n_s = 0;
-    int wprec = VMC_FP64, keep64 = 1, keeplow = 0;
+    int wprec = VMC_FP64, keep64 = 1, keeplow = 0, refresh_every = 0;
     int ham = 0;
     int maxd = 1;
     bool params_set = false, walkers_set = false;
@@ -168,6 +168,7 @@ extern "C" int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, co
     h->wprec = opt->walker_precision;
     h->keep64 = opt->keep_fp64_store ? 1 : 0;
     h->keeplow = opt->keep_lowp_store ? 1 : 0;
+    h->refresh_every = opt->refresh_every > 0 ? opt->refresh_every : 0;
     h->ham = ham->kind;
     auto fail = [&](int code) { vmc_destroy(h); return code; };
     if (h->ncap > (int64_t)1 << 31) return fail(VMC_ERR_INVALID_ARG);
@@ -473,6 +474,7 @@ extern "C" int vmc_sample(vmc_handle h, int n_burn, uint64_t seed, void* stream)
     a.n_burn = n_burn;
     a.props_per_sweep = h->N;
     a.write_back = 1;
+    a.refresh_every = h->refresh_every;
     a.want_energy = 1;
     a.seed = seed;
     a.walker_occ = h->d_wocc;

@@ -17,6 +17,7 @@ struct SampleArgs {
     int n_burn;           // sweeps before the first measurement
     int props_per_sweep;  // N for sampling, 0 to only measure
     int write_back;       // 1: write the final configuration / counter back
+    int refresh_every;    // sweeps between from-scratch rebuilds of the inverse (0: call start only)
     int want_energy;
     uint64_t seed;
     uint8_t* walker_occ;  // [n_walkers][N] ascending on entry

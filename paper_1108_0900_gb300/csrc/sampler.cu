@@ -172,6 +172,18 @@ __device__ bool gj_invert_warp(R* X, int N, int XS, R* col, int* piv) {
     return true;
 }
 
+// X = F[o, o]^{-1} for the current (unsorted) positions o, from scratch
+template <typename R>
+__device__ bool rebuild_inverse(const DevProblem& pb, R* X, int N, int XS, const uint8_t* pos_orb, R* col, int* piv) {
+    const int lane = threadIdx.x & 31;
+    for (int i = 0; i < N; ++i) {
+        int p = pos_orb[i];
+        for (int j = lane; j < N; j += 32) X[i * XS + j] = load_F<R>(pb, p, pos_orb[j]);
+    }
+    __syncwarp();
+    return gj_invert_warp<R>(X, N, XS, col, piv);
+}
+
 template <typename R> __device__ __forceinline__ void store_pf(const SampleArgs& a, int64_t idx, R w);
 template <> __device__ __forceinline__ void store_pf<float>(const SampleArgs& a, int64_t idx, float w) {
     if (a.s_pf64) a.s_pf64[idx] = (double)w;
@@ -229,12 +241,7 @@ __global__ void k_walkers(SampleArgs a) {
     __syncwarp();
 
     // ---- inverse of the pairing submatrix, from scratch -------------------
-    for (int i = 0; i < N; ++i) {
-        int p = pos_orb[i];
-        for (int j = lane; j < N; j += 32) X[i * XS + j] = load_F<R>(pb, p, pos_orb[j]);
-    }
-    __syncwarp();
-    if (!gj_invert_warp<R>(X, N, XS, cv, iv)) {
+    if (!rebuild_inverse<R>(pb, X, N, XS, pos_orb, cv, iv)) {
         if (lane == 0) atomicOr(a.status, ST_SINGULAR);
         return;
     }
@@ -305,6 +312,13 @@ __global__ void k_walkers(SampleArgs a) {
             if (spin) dn = (dn & ~(1ull << (p - ns))) | (1ull << (q - ns));
             else up = (up & ~(1ull << p)) | (1ull << q);
             __syncwarp();
+        }
+        // periodic from-scratch rebuild bounds the drift of the rank-2 updates
+        if (a.refresh_every > 0 && a.props_per_sweep > 0 && (sw + 1) % a.refresh_every == 0) {
+            if (!rebuild_inverse<R>(pb, X, N, XS, pos_orb, cv, iv)) {
+                if (lane == 0) atomicOr(a.status, ST_SINGULAR);
+                return;
+            }
         }
         if (sw < a.n_burn) continue;
 

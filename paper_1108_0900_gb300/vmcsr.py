@@ -55,7 +55,7 @@ class vmc_ansatz(ct.Structure):
 
 class vmc_options(ct.Structure):
     _fields_ = [("n_walkers", ct.c_int), ("samples_per_walker", ct.c_int), ("walker_precision", ct.c_int),
-                ("keep_fp64_store", ct.c_int), ("keep_lowp_store", ct.c_int)]
+                ("keep_fp64_store", ct.c_int), ("keep_lowp_store", ct.c_int), ("refresh_every", ct.c_int)]
 
 
 class vmc_cg_info(ct.Structure):
@@ -148,7 +148,7 @@ def _stream(stream=None):
 # ---------------------------------------------------------------------------
 
 def vmc_create(wl, n_walkers=None, samples_per_walker=None, walker_precision=VMC_FP64,
-               keep_fp64_store=True, keep_lowp_store=False):
+               keep_fp64_store=True, keep_lowp_store=False, refresh_every=0):
     """Create a handle for a problem description (``inputs.Workload``)."""
     keep = dict(
         bonds=np.ascontiguousarray(wl.bonds, np.int32),
@@ -163,7 +163,8 @@ def vmc_create(wl, n_walkers=None, samples_per_walker=None, walker_precision=VMC
                           _np_ptr(keep["h"]), _np_ptr(keep["chol"]))
     ans = vmc_ansatz(wl.n_up, wl.n_dn, wl.n_corr, _np_ptr(keep["corr_ptr"]), _np_ptr(keep["corr_sites"]))
     opt = vmc_options(int(n_walkers or wl.n_walkers), int(samples_per_walker or wl.samples_per_walker),
-                      int(walker_precision), int(bool(keep_fp64_store)), int(bool(keep_lowp_store)))
+                      int(walker_precision), int(bool(keep_fp64_store)), int(bool(keep_lowp_store)),
+                      int(refresh_every))
     h = ct.c_void_p()
     _check(lib().vmc_create(ct.byref(lat), ct.byref(ham), ct.byref(ans), ct.byref(opt), ct.byref(h)), "vmc_create")
     return Handle(h, wl, opt)

@@ -33,7 +33,8 @@ def _create_rc(wl, **opt):
     lat = vmcsr.vmc_lattice(wl.n_sites, len(keep["b"]), keep["b"].ctypes.data, keep["t"].ctypes.data)
     ham = vmcsr.vmc_hamiltonian(wl.ham, wl.U, 0, None, None)
     ans = vmcsr.vmc_ansatz(wl.n_up, wl.n_dn, wl.n_corr, keep["cp"].ctypes.data, keep["cs"].ctypes.data)
-    o = dict(n_walkers=4, samples_per_walker=2, walker_precision=0, keep_fp64_store=1, keep_lowp_store=0)
+    o = dict(n_walkers=4, samples_per_walker=2, walker_precision=0, keep_fp64_store=1, keep_lowp_store=0,
+             refresh_every=0)
     o.update(opt)
     opts = vmcsr.vmc_options(**o)
     h = ct.c_void_p()

@@ -58,9 +58,9 @@ def oracle_chains(wl, n_burn, spw, seed):
     return P, smp, mm, occ, step
 
 
-def make(wl, prec=V.VMC_FP64, keep64=True, keeplow=True, n_walkers=None, spw=None):
+def make(wl, prec=V.VMC_FP64, keep64=True, keeplow=True, n_walkers=None, spw=None, refresh_every=0):
     h = V.vmc_create(wl, n_walkers=n_walkers, samples_per_walker=spw, walker_precision=prec,
-                     keep_fp64_store=keep64, keep_lowp_store=keeplow)
+                     keep_fp64_store=keep64, keep_lowp_store=keeplow, refresh_every=refresh_every)
     V.vmc_set_params(h, wl.C, wl.f)
     return h
 
@@ -168,6 +168,32 @@ def _chain_compare(case, prec, margin, max_bad=0.0):
 def test_sampler_chains_fp64(case):
     frac = _chain_compare(case, V.VMC_FP64, 1e-9)
     assert frac >= 0.9
+
+
+@pytest.mark.parametrize("refresh,tol", [(1, 1e-10), (0, 1e-7)])
+def test_sampler_outputs_fp64(case, refresh, tol):
+    """E_L and O written by the sampler itself (not by vmc_measure): on the
+    walkers whose FP64 chains equal the oracle's, they must equal the oracle's
+    values on its own samples.  With a rebuild before every stored sample the
+    inverse is fresh; without it, the rank-2 update drift of one call bounds
+    the error."""
+    wl = case["wl"]
+    n_burn = 3
+    P = oracle.Problem(wl)
+    o_occ, o_step = wl.init_occ.copy(), np.zeros(wl.n_walkers, np.uint64)
+    smp, mm, _ = P.sample(o_occ, o_step, inputs.seed_sampling_for(1), n_burn, wl.samples_per_walker)
+    E_or, O_or = P.measure(smp)
+    ref = oracle_compact(wl, smp, O_or)
+    h = make(wl, prec=V.VMC_FP64, refresh_every=refresh)
+    V.vmc_set_walkers(h, wl.init_occ)
+    V.vmc_sample(h, n_burn, inputs.seed_sampling_for(1))
+    occ, E, cs, pf = V.vmc_get_samples(h, V.VMC_STORE_FP64)
+    safe = np.repeat(mm > 1e-9, wl.samples_per_walker)
+    assert safe.mean() >= 0.9
+    assert np.array_equal(occ[safe], smp[safe])
+    assert np.all(np.abs(E[safe] - E_or[safe]) <= tol * np.maximum(1.0, np.abs(E_or[safe])))
+    for s in np.nonzero(safe)[0]:
+        assert rel(pf[s], ref[s]) <= tol
 
 
 def test_sampler_chains_fp32(case):
@@ -364,9 +390,11 @@ def test_full_size_invariants():
     # |Psi|^2-sampled configurations (FP64 walkers): away from the nearly
     # singular pairing submatrices a uniform draw can hit, the identities
     # below hold to FP64 rounding
+    # (rebuilding every walker's inverse from scratch before each stored
+    # sample, so no rank-2 update drift enters O)
     _FULL.clear()
     wl = inputs.config(5)
-    h = make(wl, prec=V.VMC_FP64, keep64=True, keeplow=True)
+    h = make(wl, prec=V.VMC_FP64, keep64=True, keeplow=True, refresh_every=1)
     V.vmc_set_walkers(h, wl.init_occ)
     V.vmc_sample(h, 10, inputs.seed_sampling_for(5))
     g, stats = V.sr_gradient(h, V.VMC_STORE_FP64)
@@ -392,9 +420,8 @@ def test_full_size_invariants():
     # O_s . f = N/2 (homogeneity of the pfaffian): S f = eps f, checked in
     # FP64 and against the FP32 store relative to a generic product's size
     scale = torch.linalg.norm(Sa).item() / torch.linalg.norm(a).item() * np.linalg.norm(vf)
-    # O_s . f - N/2 is the rounding of sum_ab X_ba A_ab, ~kappa(A) u per sample;
-    # sampled 56 x 56 pairing matrices reach kappa ~1e8
-    for store, tol in ((V.VMC_STORE_FP64, 1e-7), (V.VMC_STORE_FP32, 1e-5)):
+    # O_s . f - N/2 is the rounding of sum_ab X_ba A_ab, ~kappa(A) u per sample
+    for store, tol in ((V.VMC_STORE_FP64, 1e-9), (V.VMC_STORE_FP32, 1e-6)):
         Sf = V.sr_apply_S(h, torch.from_numpy(vf).cuda(), eps, store).cpu().numpy()
         assert np.linalg.norm(Sf - eps * vf) <= tol * scale
     # symmetry and positivity
