@@ -173,9 +173,44 @@ struct StreamArgs {
     float* pf_partial;      // [gridDim][npf][K]
     const int* stop;
     int* status;            // ST_TIMEOUT on a wait that ran out
-    size_t buf_bytes;       // one staging buffer (occ | cidx | pf)
+    size_t buf_bytes;       // one staging buffer (occ | pf)
 };
 
-template <typename ST, int K> __global__ void __launch_bounds__(512, 1) k_sr_stream(StreamArgs a);
+template <typename ST, int K> __global__ void __launch_bounds__(768, 1) k_sr_stream(StreamArgs a);
+__global__ void __launch_bounds__(512, 1) k_sr_stream_bf16c(StreamArgs a);
+
+}  // namespace vmc
+
+namespace vmc {
+
+// Sorted two-pass product over the BF16 store (sorted.cu).
+struct SortedArgs {
+    DevProblem pb;
+    int64_t n_s;
+    const uint16_t* s_cidx;
+    int ncst;
+    const uint32_t* G;      // [n_s][Pst] (pq << 16) | bf16
+    int64_t Pst;
+    const float* V;         // [K][nv]
+    const float* invC;
+    float* Tv;              // [n_s][K] per-sample dots
+    const uint32_t* T;      // parameter-major (s_local << 16) | bf16
+    const uint32_t* base;   // [nchunk][npf + 1] run offsets
+    int nchunk;
+    double* raw;            // [npf][K] scatter result
+    const int* stop;
+};
+
+__global__ void __launch_bounds__(256) k_build_G(DevProblem pb, int64_t n_s, const uint8_t* s_occ, int Nst,
+                                                 const __nv_bfloat16* pf16, int64_t Pst, uint32_t* G);
+__global__ void __launch_bounds__(512) k_count_G(const uint32_t* G, int64_t Pst, int P, int64_t s_begin,
+                                                 int64_t s_end, int npf, uint32_t* counts);
+__global__ void k_scan_blocks(uint32_t* counts, int nblk, int npf, uint32_t* total);
+__global__ void __launch_bounds__(1024) k_scan_params(const uint32_t* total, int npf, uint32_t base0, uint32_t* base);
+__global__ void __launch_bounds__(512) k_fill_T(const uint32_t* G, int64_t Pst, int P, int64_t s_begin,
+                                                int64_t s_end, int npf, const uint32_t* offs, const uint32_t* base,
+                                                uint32_t* T);
+template <int K> __global__ void __launch_bounds__(512) k_gather_G(SortedArgs a);
+template <int K> __global__ void __launch_bounds__(256) k_scatter_T(SortedArgs a);
 
 }  // namespace vmc

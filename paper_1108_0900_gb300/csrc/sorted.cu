@@ -1,0 +1,223 @@
+// Sorted two-pass Eq. 7 product for the BF16 store.
+//
+// The per-sample pass with shared-memory scatter is bound by shared atomics
+// and index arithmetic (every pairing element of every sample costs an
+// occupation lookup and a shared atomic).  Because the O store is fixed for
+// all CG iterations of an SR step, the index work is done once per step:
+//
+//   G  [n_s][Pst] u32   (pq << 16) | bf16 value, sample-major: the gather
+//      t_s = sum_e W_e v[pq(e)] is a pure stream with a shared-memory lookup of
+//      v and no atomics;
+//   T  u32 entries (s_local << 16) | bf16 value, parameter-major per chunk of
+//      at most 65,536 samples (a counting sort of G by pq): the scatter
+//      out[pq] = sum_s t_s W_s[pq] is one warp per parameter summing a
+//      contiguous run, with no atomics and no per-CTA partial images.
+//
+// The build (count, scan, fill) streams G three times once per SR step.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace vmc {
+
+// G rows: element e of sample s, padding elements are (0, 0.0)
+__global__ void __launch_bounds__(256) k_build_G(DevProblem pb, int64_t n_s, const uint8_t* s_occ, int Nst,
+                                                 const __nv_bfloat16* pf16, int64_t Pst, uint32_t* G) {
+    __shared__ uint8_t occw[8][64];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t s = (int64_t)blockIdx.x * 8 + wid;
+    if (s >= n_s) return;
+    for (int i = lane; i < pb.N; i += 32) occw[wid][i] = s_occ[s * Nst + i];
+    __syncwarp();
+    const uint16_t* src = (const uint16_t*)(pf16 + s * Pst);
+    uint32_t* dst = G + s * Pst;
+    for (int e = lane; e < Pst; e += 32) {
+        uint32_t g = 0u;
+        if (e < pb.P) {
+            const uint16_t pt = pb.pairtab[e];
+            const int p = occw[wid][pt & 255], q = occw[wid][pt >> 8];
+            const uint32_t pq = (uint32_t)(pf_row_base(pb.M, p) + q);
+            g = (pq << 16) | (uint32_t)src[e];
+        }
+        dst[e] = g;
+    }
+}
+
+// Block b of a chunk [s_begin, s_end) owns samples s_begin + [b*per, (b+1)*per).
+__device__ __forceinline__ void block_range(int64_t s_begin, int64_t s_end, int nblk, int64_t* lo, int64_t* hi) {
+    const int64_t n = s_end - s_begin;
+    const int64_t per = (n + nblk - 1) / nblk;
+    *lo = s_begin + min(n, (int64_t)blockIdx.x * per);
+    *hi = s_begin + min(n, (int64_t)(blockIdx.x + 1) * per);
+}
+
+// counts[b][pq] = occurrences of pq in block b's samples
+__global__ void __launch_bounds__(512) k_count_G(const uint32_t* G, int64_t Pst, int P, int64_t s_begin,
+                                                 int64_t s_end, int npf, uint32_t* counts) {
+    extern __shared__ uint32_t cnt[];
+    for (int i = threadIdx.x; i < npf; i += blockDim.x) cnt[i] = 0u;
+    __syncthreads();
+    int64_t lo, hi;
+    block_range(s_begin, s_end, gridDim.x, &lo, &hi);
+    for (int64_t s = lo; s < hi; ++s) {
+        const uint32_t* g = G + s * Pst;
+        for (int e = threadIdx.x; e < P; e += blockDim.x) atomicAdd(&cnt[g[e] >> 16], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < npf; i += blockDim.x) counts[(size_t)blockIdx.x * npf + i] = cnt[i];
+}
+
+// per parameter: running offsets over the blocks (in place) and the total
+__global__ void k_scan_blocks(uint32_t* counts, int nblk, int npf, uint32_t* total) {
+    const int pq = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pq >= npf) return;
+    uint32_t run = 0u;
+    for (int b = 0; b < nblk; ++b) {
+        const uint32_t c = counts[(size_t)b * npf + pq];
+        counts[(size_t)b * npf + pq] = run;
+        run += c;
+    }
+    total[pq] = run;
+}
+
+// base[pq] = exclusive prefix of total over pq (single block), base[npf] = sum
+__global__ void __launch_bounds__(1024) k_scan_params(const uint32_t* total, int npf, uint32_t base0,
+                                                      uint32_t* base) {
+    __shared__ uint32_t part[1024];
+    const int per = (npf + blockDim.x - 1) / blockDim.x;
+    const int lo = threadIdx.x * per, hi = min(npf, lo + per);
+    uint32_t s = 0u;
+    for (int i = lo; i < hi; ++i) s += total[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+        uint32_t v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    uint32_t run = base0 + (threadIdx.x ? part[threadIdx.x - 1] : 0u);
+    for (int i = lo; i < hi; ++i) {
+        base[i] = run;
+        run += total[i];
+    }
+    if (threadIdx.x == blockDim.x - 1) base[npf] = base0 + part[blockDim.x - 1];
+}
+
+// T[base[pq] + offset[b][pq] + k] = (s - s_begin) << 16 | bf16, in block order
+__global__ void __launch_bounds__(512) k_fill_T(const uint32_t* G, int64_t Pst, int P, int64_t s_begin,
+                                                int64_t s_end, int npf, const uint32_t* offs, const uint32_t* base,
+                                                uint32_t* T) {
+    extern __shared__ uint32_t cur[];
+    for (int i = threadIdx.x; i < npf; i += blockDim.x) cur[i] = base[i] + offs[(size_t)blockIdx.x * npf + i];
+    __syncthreads();
+    int64_t lo, hi;
+    block_range(s_begin, s_end, gridDim.x, &lo, &hi);
+    for (int64_t s = lo; s < hi; ++s) {
+        const uint32_t* g = G + s * Pst;
+        const uint32_t sl = (uint32_t)(s - s_begin) << 16;
+        for (int e = threadIdx.x; e < P; e += blockDim.x) {
+            const uint32_t v = g[e];
+            const uint32_t pos = atomicAdd(&cur[v >> 16], 1u);
+            T[pos] = sl | (v & 0xFFFFu);
+        }
+    }
+}
+
+// gather: t_s = sum_c V[k_c]/C[k_c] + sum_e W_e v[pq(e)], warp per sample
+template <int K>
+__global__ void __launch_bounds__(512) k_gather_G(SortedArgs a) {
+    if (a.stop && *a.stop) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const DevProblem& pb = a.pb;
+    float* vpf = (float*)smem;
+    int* coff = (int*)(vpf + (size_t)pb.npf * K);
+    for (int i = threadIdx.x; i < pb.npf; i += blockDim.x)
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) vpf[i * K + kk] = a.V[kk * pb.nv + pb.ncp + i];
+    for (int i = threadIdx.x; i <= pb.ncorr; i += blockDim.x) coff[i] = (int)pb.corr_off[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int n4 = (int)(a.Pst >> 2);
+    for (int64_t s = (int64_t)blockIdx.x * nw + wid; s < a.n_s; s += (int64_t)gridDim.x * nw) {
+        float t[K], u[K];
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) t[kk] = u[kk] = 0.f;
+        const uint16_t* cid = a.s_cidx + s * a.ncst;
+        for (int c = lane; c < pb.ncorr; c += 32) {
+            const int k = coff[c] + (int)__ldg(cid + c);
+            const float ic = __ldg(a.invC + k);
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) t[kk] += __ldg(a.V + kk * pb.nv + k) * ic;
+        }
+        const uint4* g4 = (const uint4*)(a.G + s * a.Pst);
+#pragma unroll 4
+        for (int i = lane; i < n4; i += 32) {
+            const uint4 g = __ldcs(g4 + i);
+            const uint32_t w[4] = {g.x, g.y, g.z, g.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float val = __uint_as_float(w[j] << 16);
+                const int pq = (int)(w[j] >> 16);
+#pragma unroll
+                for (int kk = 0; kk < K; ++kk) {
+                    if (j & 1) u[kk] += val * vpf[pq * K + kk];
+                    else t[kk] += val * vpf[pq * K + kk];
+                }
+            }
+        }
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) t[kk] = warp_sum(t[kk] + u[kk]);
+        if (lane == 0)
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) a.Tv[s * K + kk] = t[kk];
+    }
+}
+
+// scatter: raw[pq][kk] = sum over samples containing pq of W t_s, warp per pq
+template <int K>
+__global__ void __launch_bounds__(256) k_scatter_T(SortedArgs a) {
+    if (a.stop && *a.stop) return;
+    const int lane = threadIdx.x & 31;
+    const int pq = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (pq >= a.pb.npf) return;
+    float acc[K], acc2[K];
+#pragma unroll
+    for (int kk = 0; kk < K; ++kk) acc[kk] = acc2[kk] = 0.f;
+    for (int c = 0; c < a.nchunk; ++c) {
+        const uint32_t* base = a.base + (size_t)c * (a.pb.npf + 1);
+        const uint32_t lo = base[pq], hi = base[pq + 1];
+        const int64_t s0 = (int64_t)c * 65536;
+        uint32_t j = lo + lane;
+        for (; j + 32 < hi; j += 64) {
+            const uint32_t v0 = __ldcs(a.T + j), v1 = __ldcs(a.T + j + 32);
+            const float w0 = __uint_as_float(v0 << 16), w1 = __uint_as_float(v1 << 16);
+            const int64_t t0 = (s0 + (v0 >> 16)) * K, t1 = (s0 + (v1 >> 16)) * K;
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) {
+                acc[kk] += w0 * __ldg(a.Tv + t0 + kk);
+                acc2[kk] += w1 * __ldg(a.Tv + t1 + kk);
+            }
+        }
+        if (j < hi) {
+            const uint32_t v0 = __ldcs(a.T + j);
+            const float w0 = __uint_as_float(v0 << 16);
+            const int64_t t0 = (s0 + (v0 >> 16)) * K;
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) acc[kk] += w0 * __ldg(a.Tv + t0 + kk);
+        }
+    }
+#pragma unroll
+    for (int kk = 0; kk < K; ++kk) {
+        const float v = warp_sum(acc[kk] + acc2[kk]);
+        if (lane == 0) a.raw[(size_t)pq * K + kk] = (double)v;
+    }
+}
+
+template __global__ void k_gather_G<1>(SortedArgs);
+template __global__ void k_gather_G<2>(SortedArgs);
+template __global__ void k_gather_G<4>(SortedArgs);
+template __global__ void k_scatter_T<1>(SortedArgs);
+template __global__ void k_scatter_T<2>(SortedArgs);
+template __global__ void k_scatter_T<4>(SortedArgs);
+
+}  // namespace vmc

@@ -101,7 +101,10 @@ __global__ void __launch_bounds__(512) k_sr_main(MainArgs<AT> a) {
 }
 
 // correlator-major scatter: block (c, chunk) histograms t_s over the states
-// of correlator c for its slice of samples.
+// of correlator c for its slice of samples.  Slices start on multiples of 8
+// samples; each thread takes 8 consecutive samples per step (one 16-byte
+// load of states, K x 8 values of t) so the loads of several samples are in
+// flight before their shared-memory atomics.
 template <typename AT, int K>
 __global__ void __launch_bounds__(256) k_corr_scatter(CorrArgs<AT> a) {
     if (a.stop && *a.stop) return;
@@ -113,13 +116,32 @@ __global__ void __launch_bounds__(256) k_corr_scatter(CorrArgs<AT> a) {
     const int d = (int)(pb.corr_off[c + 1] - off);
     for (int i = threadIdx.x; i < d * K; i += blockDim.x) h[i] = AT(0);
     __syncthreads();
-    const int64_t len = (a.n_s + a.nchunk - 1) / a.nchunk;
-    const int64_t s0 = ch * len, s1 = min(a.n_s, s0 + len);
+    const int64_t len = ((a.n_s + a.nchunk - 1) / a.nchunk + 7) & ~(int64_t)7;
+    const int64_t s0 = min(a.n_s, ch * len), s1 = min(a.n_s, s0 + len);
     const uint16_t* st = a.cidxT + (int64_t)c * a.n_s;
-    for (int64_t s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
-        int i = st[s];
+    // 16-byte loads need the row to start on a 16-byte boundary
+    const bool vec = ((a.n_s & 7) == 0);
+    int64_t s = s0;
+    if (vec) {
+        for (int64_t g = s0 + 8 * (int64_t)threadIdx.x; g + 8 <= s1; g += 8 * (int64_t)blockDim.x) {
+            const uint4 sv = *(const uint4*)(st + g);
+            const uint32_t w4[4] = {sv.x, sv.y, sv.z, sv.w};
+            AT tv[8 * K];
 #pragma unroll
-        for (int kk = 0; kk < K; ++kk) atomicAdd(&h[i * K + kk], a.T[s * K + kk]);
+            for (int j = 0; j < 8 * K; ++j) tv[j] = a.T[g * K + j];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int i = (int)((w4[j >> 1] >> (16 * (j & 1))) & 0xFFFFu);
+#pragma unroll
+                for (int kk = 0; kk < K; ++kk) atomicAdd(&h[i * K + kk], tv[j * K + kk]);
+            }
+        }
+        s = s0 + ((s1 - s0) & ~(int64_t)7);
+    }
+    for (int64_t q = s + threadIdx.x; q < s1; q += blockDim.x) {
+        int i = st[q];
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) atomicAdd(&h[i * K + kk], a.T[q * K + kk]);
     }
     __syncthreads();
     AT* dst = a.corr_partial + ((int64_t)ch * pb.ncp + off) * K;
