@@ -71,6 +71,8 @@ def lib():
             L.orc_hamiltonian_element.restype = dbl
             L.orc_local_energy.argtypes = [vp, vp]
             L.orc_local_energy.restype = dbl
+            L.orc_local_energy_abinitio_bruteforce.argtypes = [vp, vp]
+            L.orc_local_energy_abinitio_bruteforce.restype = dbl
             L.orc_sample.argtypes = [vp, i32, vp, vp, ct.c_uint64, i32, i32, vp, vp, vp, dbl, vp]
             L.orc_sample.restype = i32
             L.orc_measure.argtypes = [vp, i64, vp, vp, vp]
@@ -150,6 +152,10 @@ class Problem:
     def local_energy(self, occ) -> float:
         occ = np.ascontiguousarray(occ, np.uint8)
         return float(lib().orc_local_energy(self.ref, _ptr(occ)))
+
+    def local_energy_bruteforce(self, occ) -> float:
+        occ = np.ascontiguousarray(occ, np.uint8)
+        return float(lib().orc_local_energy_abinitio_bruteforce(self.ref, _ptr(occ)))
 
     def hamiltonian_element(self, occ_n, occ_np) -> float:
         a = np.ascontiguousarray(occ_n, np.uint8)

@@ -437,25 +437,143 @@ double orc_hamiltonian_element(const orc_problem* P, const uint8_t* occ_n, const
     return H;
 }
 
-/* Local energy for the ab initio Hamiltonian: sum over every configuration
- * n' reachable by one or two same-spin-conserving excitations, with
- * <n|H|n'> from orc_hamiltonian_element and Psi_n' from scratch. */
+/* One two-body string 1/2 (pq|rs) a+_{p} a+_{r} a_{s} a_{q} (spin orbitals,
+ * spins of p,q equal and of r,s equal, spatial integrals) applied to |n'>:
+ * returns its coefficient on |n> (0 if it does not land on n). */
+static double two_body_term(const orc_problem* P, const uint8_t* bn, const uint8_t* bnp, int p, int q, int r, int s)
+{
+    int M = n_orb_M(P), n = P->n_sites;
+    if ((p >= n) != (q >= n) || (r >= n) != (s >= n)) return 0.0;
+    uint8_t w[512];
+    memcpy(w, bnp, M);
+    int g = apply_annihilate(M, w, q);
+    if (!g) return 0.0;
+    int g2 = apply_annihilate(M, w, s);
+    if (!g2) return 0.0;
+    int g3 = apply_create(M, w, r);
+    if (!g3) return 0.0;
+    int g4 = apply_create(M, w, p);
+    if (!g4) return 0.0;
+    if (memcmp(w, bn, M) != 0) return 0.0;
+    return 0.5 * eri(P, p % n, q % n, r % n, s % n) * g * g2 * g3 * g4;
+}
+
+static double one_body_term(const orc_problem* P, const uint8_t* bn, const uint8_t* bnp, int p, int q)
+{
+    int M = n_orb_M(P), n = P->n_sites;
+    if ((p >= n) != (q >= n)) return 0.0;
+    uint8_t w[512];
+    memcpy(w, bnp, M);
+    int g = apply_annihilate(M, w, q);
+    if (!g) return 0.0;
+    int g2 = apply_create(M, w, p);
+    if (!g2) return 0.0;
+    if (memcmp(w, bn, M) != 0) return 0.0;
+    return P->h[(p % n) * n + (q % n)] * g * g2;
+}
+
+/* <n|H|n'> for the ab initio Hamiltonian, applying to |n'> only the operator
+ * strings that can connect it to |n> (every other string of H maps |n'> to a
+ * configuration other than |n>, or to zero).  `rem` = orbitals of n' not in
+ * n (annihilated), `add` = orbitals of n not in n' (created), `nd` = how many
+ * (0, 1 or 2); the remaining indices run over occupied spectators. */
+static double abinitio_element(const orc_problem* P, const uint8_t* bn, const uint8_t* bnp, const int* rem,
+                               const int* add, int nd)
+{
+    int M = n_orb_M(P);
+    double H = 0.0;
+    if (nd == 0) {
+        for (int k = 0; k < M; ++k) {
+            if (!bnp[k]) continue;
+            H += one_body_term(P, bn, bnp, k, k);
+            for (int l = 0; l < M; ++l) {
+                if (!bnp[l] || l == k) continue;
+                H += two_body_term(P, bn, bnp, k, k, l, l);   /* direct */
+                H += two_body_term(P, bn, bnp, l, k, k, l);   /* exchange */
+            }
+        }
+    } else if (nd == 1) {
+        int i = rem[0], a = add[0];
+        H += one_body_term(P, bn, bnp, a, i);
+        for (int k = 0; k < M; ++k) {
+            if (!bnp[k] || k == i) continue;
+            H += two_body_term(P, bn, bnp, a, i, k, k);
+            H += two_body_term(P, bn, bnp, k, k, a, i);
+            H += two_body_term(P, bn, bnp, a, k, k, i);
+            H += two_body_term(P, bn, bnp, k, i, a, k);
+        }
+    } else {
+        int i = rem[0], j = rem[1], a = add[0], b = add[1];
+        int qs[2][2] = {{i, j}, {j, i}}, pr[2][2] = {{a, b}, {b, a}};
+        for (int u = 0; u < 2; ++u)
+            for (int v = 0; v < 2; ++v)
+                H += two_body_term(P, bn, bnp, pr[v][0], qs[u][0], pr[v][1], qs[u][1]);
+    }
+    return H;
+}
+
+/* Local energy for the ab initio Hamiltonian: every configuration n' reached
+ * by moving one or two electrons (spin kept), <n|H|n'> by explicit operator
+ * application (abinitio_element) and Psi_n' from scratch. */
 double orc_local_energy_abinitio(const orc_problem* P, const uint8_t* occ)
 {
-    int M = n_orb_M(P), N = P->n_up + P->n_dn;
+    int M = n_orb_M(P), N = P->n_up + P->n_dn, n = P->n_sites;
+    uint8_t bits[512], w[512], occn[256];
+    occ_to_bits(P, occ, bits);
+    double la0;
+    int s0;
+    orc_log_psi(P, occ, &la0, &s0);
+    double E = abinitio_element(P, bits, bits, NULL, NULL, 0);
+    int occl[256], empl[256];
+    int nocc = 0, nemp = 0;
+    for (int o = 0; o < M; ++o) { if (bits[o]) occl[nocc++] = o; else empl[nemp++] = o; }
+    for (int a = 0; a < nocc; ++a)
+        for (int e = 0; e < nemp; ++e) {
+            if ((occl[a] >= n) != (empl[e] >= n)) continue;
+            memcpy(w, bits, M);
+            w[occl[a]] = 0; w[empl[e]] = 1;
+            /* n' = n with occl[a] -> empl[e]; n' has empl[e] where n has occl[a] */
+            int rem[1] = {empl[e]}, add[1] = {occl[a]};
+            double h = abinitio_element(P, bits, w, rem, add, 1);
+            if (h != 0.0) {
+                bits_to_occ(M, w, occn);
+                E += h * amp_ratio(P, occn, la0, s0);
+            }
+        }
+    for (int a1 = 0; a1 < nocc; ++a1)
+        for (int a2 = a1 + 1; a2 < nocc; ++a2)
+            for (int e1 = 0; e1 < nemp; ++e1)
+                for (int e2 = e1 + 1; e2 < nemp; ++e2) {
+                    int up_out = (occl[a1] < n) + (occl[a2] < n);
+                    int up_in = (empl[e1] < n) + (empl[e2] < n);
+                    if (up_out != up_in) continue;
+                    memcpy(w, bits, M);
+                    w[occl[a1]] = 0; w[occl[a2]] = 0; w[empl[e1]] = 1; w[empl[e2]] = 1;
+                    int rem[2] = {empl[e1], empl[e2]}, add[2] = {occl[a1], occl[a2]};
+                    double h = abinitio_element(P, bits, w, rem, add, 2);
+                    if (h != 0.0) {
+                        bits_to_occ(M, w, occn);
+                        E += h * amp_ratio(P, occn, la0, s0);
+                    }
+                }
+    (void)N;
+    return E;
+}
+
+/* The same local energy with every matrix element from the unrestricted
+ * operator sum of orc_hamiltonian_element: slow, tiny systems only. */
+double orc_local_energy_abinitio_bruteforce(const orc_problem* P, const uint8_t* occ)
+{
+    int M = n_orb_M(P), n = P->n_sites;
     uint8_t bits[512], w[512], occn[256];
     occ_to_bits(P, occ, bits);
     double la0;
     int s0;
     orc_log_psi(P, occ, &la0, &s0);
     double E = orc_hamiltonian_element(P, occ, occ);
-    /* enumerate distinct n' != n with at most two electrons moved, spin kept */
-    int n = P->n_sites;
-    int nocc = N, nemp = M - N;
     int occl[256], empl[256];
-    int io = 0, ie = 0;
-    for (int o = 0; o < M; ++o) { if (bits[o]) occl[io++] = o; else empl[ie++] = o; }
-    /* singles */
+    int nocc = 0, nemp = 0;
+    for (int o = 0; o < M; ++o) { if (bits[o]) occl[nocc++] = o; else empl[nemp++] = o; }
     for (int a = 0; a < nocc; ++a)
         for (int e = 0; e < nemp; ++e) {
             if ((occl[a] >= n) != (empl[e] >= n)) continue;
@@ -465,7 +583,6 @@ double orc_local_energy_abinitio(const orc_problem* P, const uint8_t* occ)
             double h = orc_hamiltonian_element(P, occ, occn);
             if (h != 0.0) E += h * amp_ratio(P, occn, la0, s0);
         }
-    /* doubles: remove a1 < a2, add e1 < e2, spin counts conserved */
     for (int a1 = 0; a1 < nocc; ++a1)
         for (int a2 = a1 + 1; a2 < nocc; ++a2)
             for (int e1 = 0; e1 < nemp; ++e1)

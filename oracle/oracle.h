@@ -36,6 +36,7 @@ int orc_logderiv(const orc_problem* P, const uint8_t* occ, double* O);
 double orc_hamiltonian_element(const orc_problem* P, const uint8_t* occ_n, const uint8_t* occ_np);
 double orc_local_energy_hubbard(const orc_problem* P, const uint8_t* occ);
 double orc_local_energy_abinitio(const orc_problem* P, const uint8_t* occ);
+double orc_local_energy_abinitio_bruteforce(const orc_problem* P, const uint8_t* occ);
 double orc_local_energy(const orc_problem* P, const uint8_t* occ);
 int orc_sample(const orc_problem* P, int n_walkers, uint8_t* occ, uint64_t* step, uint64_t seed,
                int n_burn, int n_spw, uint8_t* out_occ, double* min_margin, int64_t* accepts,

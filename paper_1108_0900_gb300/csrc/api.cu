@@ -60,7 +60,9 @@ struct vmc_ctx {
     int *d_site_cptr = nullptr, *d_site_corr = nullptr, *d_site_w = nullptr;
     int *d_nbr_ptr = nullptr, *d_nbr_site = nullptr;
     double* d_nbr_t = nullptr;
-    double *d_h = nullptr, *d_eri = nullptr;
+    double *d_h64 = nullptr, *d_eri64 = nullptr;
+    float *d_h32 = nullptr, *d_eri32 = nullptr;
+    int *d_pair_ptr = nullptr, *d_pair_corr = nullptr;
     double *d_C64 = nullptr, *d_invC64 = nullptr, *d_F64 = nullptr;
     float *d_C32 = nullptr, *d_invC32 = nullptr, *d_F32 = nullptr;
     uint16_t* d_pairtab = nullptr;
@@ -156,10 +158,7 @@ extern "C" int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, co
     if (opt->n_walkers < 1 || opt->samples_per_walker < 1) return VMC_ERR_INVALID_ARG;
     if (opt->walker_precision != VMC_FP64 && opt->walker_precision != VMC_FP32) return VMC_ERR_INVALID_ARG;
     if (ham->kind != VMC_HUBBARD && ham->kind != VMC_ABINITIO) return VMC_ERR_INVALID_ARG;
-    if (ham->kind == VMC_ABINITIO) {
-        set_err("ab initio local energy not available in this build");
-        return VMC_ERR_UNSUPPORTED;
-    }
+    if (ham->kind == VMC_ABINITIO && (!ham->h || !ham->chol || ham->n_chol < 1)) return VMC_ERR_INVALID_ARG;
     if (ans->n_corr < 0 || (ans->n_corr > 0 && (!ans->corr_ptr || !ans->corr_sites))) return VMC_ERR_INVALID_ARG;
     if (lat->n_bonds < 0 || (lat->n_bonds > 0 && (!lat->bonds || !lat->bond_t))) return VMC_ERR_INVALID_ARG;
 
@@ -223,6 +222,35 @@ extern "C" int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, co
         for (auto& pr : nb[s]) { nsite.push_back(pr.first); nt.push_back(pr.second); }
         nptr[s + 1] = (int)nsite.size();
     }
+    // correlators containing both sites i and j (i != j)
+    std::vector<int> pptr((size_t)ns * ns + 1, 0), pcorr;
+    {
+        std::vector<std::vector<int>> pl((size_t)ns * ns);
+        for (int c = 0; c < h->ncorr; ++c)
+            for (int j1 = cptr[c]; j1 < cptr[c + 1]; ++j1)
+                for (int j2 = cptr[c]; j2 < cptr[c + 1]; ++j2)
+                    if (j1 != j2) pl[(size_t)csites[j1] * ns + csites[j2]].push_back(c);
+        for (size_t k = 0; k < pl.size(); ++k) {
+            for (int c : pl[k]) pcorr.push_back(c);
+            pptr[k + 1] = (int)pcorr.size();
+        }
+    }
+    // ab initio integrals: (pq|rs) = sum_mu L^mu_pq L^mu_rs (Eq. 9 with R = L)
+    std::vector<double> eri64, h64;
+    if (ham->kind == VMC_ABINITIO) {
+        const size_t n2 = (size_t)ns * ns;
+        h64.assign(ham->h, ham->h + n2);
+        eri64.assign(n2 * n2, 0.0);
+        for (int mu = 0; mu < ham->n_chol; ++mu) {
+            const double* L = ham->chol + (size_t)mu * n2;
+            for (size_t pq = 0; pq < n2; ++pq) {
+                const double l = L[pq];
+                if (l == 0.0) continue;
+                double* row = eri64.data() + pq * n2;
+                for (size_t rs = 0; rs < n2; ++rs) row[rs] += l * L[rs];
+            }
+        }
+    }
     // pairing block order: up-up triangle, down-down triangle, up-down rectangle
     std::vector<uint16_t> pt;
     for (int a = 0; a < nu; ++a)
@@ -264,6 +292,21 @@ extern "C" int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, co
     if (!nt.empty()) UPL(h->d_nbr_t, nt.data(), nt.size());
     UPL(h->d_pairtab, pt.data(), pt.size());
     UPL(h->d_rowbase, rb.data(), rb.size());
+    ACK(h->alloc(&h->d_pair_ptr, pptr.size()));
+    ACK(h->alloc(&h->d_pair_corr, std::max<size_t>(pcorr.size(), 1)));
+    UPL(h->d_pair_ptr, pptr.data(), pptr.size());
+    if (!pcorr.empty()) UPL(h->d_pair_corr, pcorr.data(), pcorr.size());
+    if (ham->kind == VMC_ABINITIO) {
+        std::vector<float> h32(h64.begin(), h64.end()), eri32(eri64.begin(), eri64.end());
+        ACK(h->alloc(&h->d_h64, h64.size()));
+        ACK(h->alloc(&h->d_h32, h32.size()));
+        ACK(h->alloc(&h->d_eri64, eri64.size()));
+        ACK(h->alloc(&h->d_eri32, eri32.size()));
+        UPL(h->d_h64, h64.data(), h64.size());
+        UPL(h->d_h32, h32.data(), h32.size());
+        UPL(h->d_eri64, eri64.data(), eri64.size());
+        UPL(h->d_eri32, eri32.data(), eri32.size());
+    }
     // parameters
     ACK(h->alloc(&h->d_C64, h->ncp));
     ACK(h->alloc(&h->d_invC64, h->ncp));
@@ -325,7 +368,8 @@ extern "C" int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, co
     pb.corr_ptr = h->d_corr_ptr; pb.corr_sites = h->d_corr_sites; pb.corr_off = h->d_corr_off;
     pb.site_cptr = h->d_site_cptr; pb.site_corr = h->d_site_corr; pb.site_w = h->d_site_w;
     pb.nbr_ptr = h->d_nbr_ptr; pb.nbr_site = h->d_nbr_site; pb.nbr_t = h->d_nbr_t;
-    pb.h = h->d_h; pb.eri = h->d_eri;
+    pb.h64 = h->d_h64; pb.h32 = h->d_h32; pb.eri64 = h->d_eri64; pb.eri32 = h->d_eri32;
+    pb.pair_ptr = h->d_pair_ptr; pb.pair_corr = h->d_pair_corr;
     pb.C64 = h->d_C64; pb.C32 = h->d_C32; pb.F64 = h->d_F64; pb.F32 = h->d_F32;
     pb.pairtab = h->d_pairtab; pb.rowbase = h->d_rowbase;
     *out = h;
@@ -438,10 +482,16 @@ static int read_status(vmc_ctx* h, cudaStream_t st) {
 static int launch_walkers(vmc_ctx* h, SampleArgs& a, bool fp64, cudaStream_t st) {
     a.pb = h->pb;
     a.XS = h->N + 1;
+    a.GS = h->N + 1;
     a.ncorr_pad = (int)round_up(std::max(h->ncorr, 1), 4);
     const size_t rsz = fp64 ? 8 : 4;
     size_t wb = (size_t)h->N * a.XS * rsz + 3 * (size_t)a.XS * rsz;
-    wb = round_up(wb, 16) + 64 * 4 + (size_t)a.ncorr_pad * 4 + 64 + 128;
+    wb = wb + 64 * 4 + (size_t)a.ncorr_pad * 4 + 64 + 128;
+    if (h->ham == VMC_ABINITIO && a.want_energy) {
+        // G [M][GS], H [E][E], single-move factors [N][E], empty list, index map
+        const size_t E = (size_t)(h->M - h->N);
+        wb += ((size_t)h->M * a.GS + E * E + (size_t)h->N * E) * rsz + 128 + 128;
+    }
     wb = round_up(wb, 16);
     a.warp_bytes = wb;
     int wpb = (int)std::min<size_t>(4, h->smem_optin / wb);

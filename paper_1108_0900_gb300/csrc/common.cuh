@@ -98,9 +98,14 @@ struct DevProblem {
     const int* nbr_ptr;        // [ns+1]
     const int* nbr_site;
     const double* nbr_t;
-    // ab initio integrals: h[ns][ns], eri[(pq)(rs)] packed over full index
-    const double* h;
-    const double* eri;         // ns^4 (p,q,r,s) FP64
+    // ab initio integrals (spatial indices): h[ns][ns], eri[((p ns + q) ns + r) ns + s] = (pq|rs)
+    const double* h64;
+    const float* h32;
+    const double* eri64;
+    const float* eri32;
+    // correlators containing both sites i and j: pair_corr[pair_ptr[i ns + j] ..]
+    const int* pair_ptr;
+    const int* pair_corr;
     // parameters
     const double* C64;
     const float* C32;

@@ -23,6 +23,7 @@ struct SampleArgs {
     uint8_t* walker_occ;  // [n_walkers][N] ascending on entry
     uint64_t* walker_step;
     int XS;               // row stride of the inverse in shared memory
+    int GS;               // row stride of G (ab initio local energy)
     int ncorr_pad;
     size_t warp_bytes;
     // O store

@@ -172,6 +172,195 @@ __device__ bool gj_invert_warp(R* X, int N, int XS, R* col, int* piv) {
     return true;
 }
 
+template <typename R> __device__ __forceinline__ R load_h(const DevProblem& pb, int i, int j);
+template <> __device__ __forceinline__ float load_h<float>(const DevProblem& pb, int i, int j) {
+    return __ldg(pb.h32 + i * pb.ns + j);
+}
+template <> __device__ __forceinline__ double load_h<double>(const DevProblem& pb, int i, int j) {
+    return __ldg(pb.h64 + i * pb.ns + j);
+}
+// (pq|rs) over spatial orbitals
+template <typename R> __device__ __forceinline__ R load_eri(const DevProblem& pb, int p, int q, int r, int s);
+template <> __device__ __forceinline__ float load_eri<float>(const DevProblem& pb, int p, int q, int r, int s) {
+    const int n = pb.ns;
+    return __ldg(pb.eri32 + ((p * n + q) * n + r) * n + s);
+}
+template <> __device__ __forceinline__ double load_eri<double>(const DevProblem& pb, int p, int q, int r, int s) {
+    const int n = pb.ns;
+    return __ldg(pb.eri64 + ((p * n + q) * n + r) * n + s);
+}
+
+// (i, j), i < j, of the k-th pair in row-major order over n items
+__device__ __forceinline__ void tri_decode(int k, int n, int* i, int* j) {
+    const float b = 2.f * n - 1.f;
+    int a = (int)floorf((b - sqrtf(fmaxf(b * b - 8.f * k, 0.f))) * 0.5f);
+    a = max(0, min(a, n - 2));
+    while (a > 0 && a * n - a * (a + 1) / 2 > k) --a;
+    while ((a + 1) * n - (a + 1) * (a + 2) / 2 <= k) ++a;
+    *i = a;
+    *j = a + 1 + (k - (a * n - a * (a + 1) / 2));
+}
+
+// Correlator factor of moving two electrons (p1 -> x, p2 -> y; sf = 1 up, 2
+// down for each move) given the two single-move factors r1, r2: correlators
+// touched by both moves hold a site of each, so they are found through the
+// site-pair lists and corrected to their joint new state.
+template <typename R>
+__device__ R corr_ratio_double(const DevProblem& pb, const uint32_t* cidx, int p1, int x, int p2, int y, R r1, R r2) {
+    const int ns = pb.ns;
+    const int sf1 = p1 >= ns ? 2 : 1, sf2 = p2 >= ns ? 2 : 1;
+    const int a1[2] = {p1 % ns, x % ns}, a2[2] = {p2 % ns, y % ns};
+    R corr = R(1);
+    for (int u = 0; u < 2; ++u)
+        for (int v = 0; v < 2; ++v) {
+            const int i = a1[u], j = a2[v];
+            // correlators holding a site of each move: the pair list of (i, j),
+            // or every correlator on the site when both moves touch it
+            const int lo = i == j ? pb.site_cptr[i] : pb.pair_ptr[i * ns + j];
+            const int hi = i == j ? pb.site_cptr[i + 1] : pb.pair_ptr[i * ns + j + 1];
+            for (int e = lo; e < hi; ++e) {
+                const int c = i == j ? pb.site_corr[e] : pb.pair_corr[e];
+                // counted once: skip if an earlier (u', v') combination also lies in c
+                bool seen = false;
+                for (int w = 0; w < u * 2 + v && !seen; ++w) {
+                    const int i2 = a1[w >> 1], j2 = a2[w & 1];
+                    seen = site_weight_in(pb, c, i2) != 0 && (i2 == j2 || site_weight_in(pb, c, j2) != 0);
+                }
+                if (seen) continue;
+                const int old = (int)cidx[c];
+                const int d1 = sf1 * (site_weight_in(pb, c, a1[1]) - site_weight_in(pb, c, a1[0]));
+                const int d2 = sf2 * (site_weight_in(pb, c, a2[1]) - site_weight_in(pb, c, a2[0]));
+                const int64_t o = pb.corr_off[c];
+                const R c0 = load_C<R>(pb, o + old);
+                corr *= load_C<R>(pb, o + old + d1 + d2) * c0 / (load_C<R>(pb, o + old + d1) * load_C<R>(pb, o + old + d2));
+            }
+        }
+    return r1 * r2 * corr;
+}
+
+// Local energy of the ab initio Hamiltonian for the warp's walker (lane
+// partial sum; the caller reduces).  E_L = <n|H|n> + sum over single and
+// double same-spin-conserving moves of <n|H|n'> Psi_n'/Psi_n.  With the new
+// orbitals put in place of the old ones, the amplitude ratios are the
+// in-place pfaffian ratios (their Jordan-Wigner signs cancel against those of
+// the matrix elements, as for the hops) and the matrix elements are the
+// Slater-Condon magnitudes:
+//   single p->x:  h_px + sum_{k occ != p} [(px|kk) - d(s_k, s_p) (pk|kx)]
+//   double p1->x, p2->y:  (p1 x|p2 y) - d(same spin) (p1 y|p2 x).
+// Pfaffian ratios from G[q][j] = sum_k F[q][o_k] X[k][j] and, for doubles,
+// H[y][x] = sum_j F[y][o_j] G[x][j] (second replacement on the rank-2-updated
+// inverse, written out in G, X, F and H).
+template <typename R>
+__device__ double abinitio_energy(const DevProblem& pb, const R* X, int XS, const uint8_t* pos_orb,
+                                  const int8_t* orb_pos, uint64_t up, uint64_t dn, const uint32_t* cidx,
+                                  R* G, int GS, R* Hm, R* Rs, uint8_t* emp, int8_t* eidx) {
+    const int lane = threadIdx.x & 31;
+    const int ns = pb.ns, M = pb.M, N = pb.N, nu = pb.nu, nd = pb.nd;
+    const int eu = ns - nu, ed = ns - nd, E = eu + ed;
+    // empty orbitals: up first (ascending), then down
+    for (int i = lane; i < E; i += 32)
+        emp[i] = (uint8_t)(i < eu ? nth_set_bit64(~up & ((ns == 64) ? ~0ull : ((1ull << ns) - 1ull)), i)
+                                  : ns + nth_set_bit64(~dn & ((ns == 64) ? ~0ull : ((1ull << ns) - 1ull)), i - eu));
+    for (int o = lane; o < M; o += 32) eidx[o] = -1;
+    __syncwarp();
+    for (int i = lane; i < E; i += 32) eidx[emp[i]] = (int8_t)i;
+    // G rows for every orbital
+    for (int q = lane; q < M; q += 32) {
+        for (int j = 0; j < N; ++j) G[q * GS + j] = R(0);
+        for (int k = 0; k < N; ++k) {
+            const R f = load_F<R>(pb, q, pos_orb[k]);
+            for (int j = 0; j < N; ++j) G[q * GS + j] += f * X[k * XS + j];
+        }
+    }
+    __syncwarp();
+    // H over pairs of empty orbitals
+    for (int t = lane; t < E * E; t += 32) {
+        const int iy = t / E, ix = t % E;
+        const int yq = emp[iy], xq = emp[ix];
+        R acc = R(0);
+        for (int j = 0; j < N; ++j) acc += load_F<R>(pb, yq, pos_orb[j]) * G[xq * GS + j];
+        Hm[t] = acc;
+    }
+    // single-move correlator factors Rs[a][ie] (same spin only)
+    for (int t = lane; t < N * E; t += 32) {
+        const int a = t / E, ie = t % E;
+        const int p = pos_orb[a], q = emp[ie];
+        Rs[t] = ((p >= ns) == (q >= ns)) ? corr_ratio_serial<R>(pb, cidx, p, q) : R(0);
+    }
+    __syncwarp();
+    double e = 0.0;
+    // diagonal: sum_k h_kk + 1/2 sum_{k != l} [(kk|ll) - d(s_k, s_l) (kl|lk)]
+    for (int a = lane; a < N; a += 32) {
+        const int k = pos_orb[a], ik = k % ns;
+        double v = (double)load_h<R>(pb, ik, ik);
+        for (int b = 0; b < N; ++b) {
+            if (b == a) continue;
+            const int l = pos_orb[b], il = l % ns;
+            R w = load_eri<R>(pb, ik, ik, il, il);
+            if ((k >= ns) == (l >= ns)) w -= load_eri<R>(pb, ik, il, il, ik);
+            v += 0.5 * (double)w;
+        }
+        e += v;
+    }
+    // singles
+    for (int t = lane; t < N * E; t += 32) {
+        const int a = t / E, ie = t % E;
+        const int p = pos_orb[a], x = emp[ie];
+        if ((p >= ns) != (x >= ns)) continue;
+        const int ip = p % ns, ix = x % ns;
+        R hm = load_h<R>(pb, ip, ix);
+        for (int b = 0; b < N; ++b) {
+            if (b == a) continue;
+            const int k = pos_orb[b], ik = k % ns;
+            hm += load_eri<R>(pb, ip, ix, ik, ik);
+            if ((k >= ns) == (p >= ns)) hm -= load_eri<R>(pb, ip, ik, ik, ix);
+        }
+        e += (double)(hm * G[x * GS + a] * Rs[t]);
+    }
+    // doubles: up-up, down-down, up-down classes
+    const int cu = nu * (nu - 1) / 2 * (eu * (eu - 1) / 2);
+    const int cd = nd * (nd - 1) / 2 * (ed * (ed - 1) / 2);
+    const int cx = nu * nd * eu * ed;
+    for (int t = lane; t < cu + cd + cx; t += 32) {
+        int a, b, ix, iy;
+        if (t < cu) {
+            const int nxy = eu * (eu - 1) / 2;
+            tri_decode(t / nxy, nu, &a, &b);
+            tri_decode(t % nxy, eu, &ix, &iy);
+        } else if (t < cu + cd) {
+            const int u = t - cu, nxy = ed * (ed - 1) / 2;
+            tri_decode(u / nxy, nd, &a, &b);
+            tri_decode(u % nxy, ed, &ix, &iy);
+            a += nu; b += nu; ix += eu; iy += eu;
+        } else {
+            const int u = t - cu - cd;
+            a = u / (nd * eu * ed);
+            b = nu + (u / (eu * ed)) % nd;
+            ix = (u / ed) % eu;
+            iy = eu + u % ed;
+        }
+        const int p1 = pos_orb[a], p2 = pos_orb[b], x = emp[ix], y = emp[iy];
+        const int i1 = p1 % ns, i2 = p2 % ns, jx = x % ns, jy = y % ns;
+        R hm = load_eri<R>(pb, i1, jx, i2, jy);
+        if ((p1 >= ns) == (p2 >= ns)) hm -= load_eri<R>(pb, i1, jy, i2, jx);
+        if (hm == R(0)) continue;
+        // pfaffian ratio for a -> x then b -> y
+        const R Xab = X[a * XS + b], Xba = X[b * XS + a];
+        const R Gxa = G[x * GS + a], Gxb = G[x * GS + b], Gya = G[y * GS + a], Gyb = G[y * GS + b];
+        const R Fyp1 = load_F<R>(pb, y, p1), Fyp2 = load_F<R>(pb, y, p2), Fyx = load_F<R>(pb, y, x);
+        const R Fxp1 = load_F<R>(pb, x, p1);
+        const R r1 = Gxa;
+        const R T1 = Gyb - Fyp1 * Xab + Fyx * Xab;
+        const R Sc = Gya - Fyp2 * Xba;
+        const R ytb = -Gxb + Fxp1 * Xab;
+        const R Sy = -(Hm[iy * E + ix] - Fyp1 * Gxa - Fyp2 * Gxb) + Fxp1 * (-Gya - Fyp2 * Xab) + Fyx * (R(1) - r1);
+        const R rpf = r1 * T1 + Sc * ytb - Sy * Xba;
+        const R rc = corr_ratio_double<R>(pb, cidx, p1, x, p2, y, Rs[a * E + ix], Rs[b * E + iy]);
+        e += (double)(hm * rpf * rc);
+    }
+    return e;
+}
+
 // X = F[o, o]^{-1} for the current (unsorted) positions o, from scratch
 template <typename R>
 __device__ bool rebuild_inverse(const DevProblem& pb, R* X, int N, int XS, const uint8_t* pos_orb, R* col, int* piv) {
@@ -344,6 +533,16 @@ __global__ void k_walkers(SampleArgs a) {
                         e_lane += pb.nbr_t[k] * (double)(d * rc);
                     }
                 }
+            }
+            if (pb.ham == 1) {
+                unsigned char* ab = (unsigned char*)(orb_pos + 128);
+                R* G = (R*)ab;
+                R* Hm = G + (size_t)M * a.GS;
+                R* Rs = Hm + (size_t)(M - N) * (M - N);
+                uint8_t* emp = (uint8_t*)(Rs + (size_t)N * (M - N));
+                int8_t* eidx = (int8_t*)(emp + 128);
+                e_lane = abinitio_energy<R>(pb, X, XS, pos_orb, orb_pos, up, dn, cidx, G, a.GS, Hm, Rs, emp, eidx);
+                __syncwarp();
             }
             e_lane = warp_sum(e_lane);
             if (pb.ham == 0) e_lane += pb.U * (double)__popcll(up & dn);

@@ -69,6 +69,7 @@ SMALL = {
     "cfg1": lambda: inputs.config(1, n_walkers=24, samples_per_walker=6),
     "cfg2": lambda: inputs.config(2, n_walkers=37, samples_per_walker=5),
     "cfg5geom": lambda: inputs.config(5, n_walkers=9, samples_per_walker=3),
+    "cfg3abinitio": lambda: inputs.config(3, n_walkers=8, samples_per_walker=2),
     "tiny2x2": lambda: inputs.hubbard("t", 2, 2, 1, 1, "2x2", seed=5, n_walkers=7, samples_per_walker=4),
     "nocorr3x2": lambda: inputs.hubbard("t", 3, 2, 2, 2, "none", seed=6, n_walkers=11, samples_per_walker=3),
 }
@@ -359,24 +360,27 @@ def test_errors_and_edges():
 _FULL = {}
 
 
-def full5(prec):
-    if prec not in _FULL:
-        wl = inputs.config(5)
+def full5(prec, cfg=5):
+    if (prec, cfg) not in _FULL:
+        wl = inputs.config(cfg)
         h = make(wl, prec=prec, keep64=True, keeplow=True)
         cfgs = inputs.draw_configs(np.random.default_rng(555), wl.n_samples, wl.n_sites, wl.n_up, wl.n_dn)
         V.vmc_measure(h, cfgs)
         _FULL.clear()
-        _FULL[prec] = (wl, h, cfgs)
-    return _FULL[prec]
+        _FULL[(prec, cfg)] = (wl, h, cfgs)
+    return _FULL[(prec, cfg)]
 
 
-@pytest.mark.parametrize("prec,tol", [(V.VMC_FP64, 1e-10), (V.VMC_FP32, 5e-3)])
-def test_full_size_sampled_outputs(prec, tol):
-    wl, h, cfgs = full5(prec)
+@pytest.mark.parametrize("cfg,prec,tol", [(5, V.VMC_FP64, 1e-10), (5, V.VMC_FP32, 5e-3),
+                                          (3, V.VMC_FP64, 1e-10), (3, V.VMC_FP32, 5e-3)])
+def test_full_size_sampled_outputs(cfg, prec, tol):
+    """Every sample of the full workload is evaluated on the GPU; a random
+    subset (and the last sample) is recomputed by the oracle."""
+    wl, h, cfgs = full5(prec, cfg)
     occ, E, cs, pf = V.vmc_get_samples(h, V.VMC_STORE_FP64 if prec == V.VMC_FP64 else V.VMC_STORE_FP32)
     assert np.array_equal(occ, cfgs)
     P = oracle.Problem(wl)
-    pick = np.random.default_rng(1).choice(len(cfgs), 24, replace=False)
+    pick = np.random.default_rng(1).choice(len(cfgs), 24 if cfg == 5 else 8, replace=False)
     pick[-1] = len(cfgs) - 1
     E_or, O_or = P.measure(cfgs[pick])
     ref = oracle_compact(wl, cfgs[pick], O_or)

@@ -271,6 +271,17 @@ def test_hamiltonian_elements_and_energy_identity(kind):
     assert lhs == pytest.approx(rhs, rel=1e-10, abs=1e-12)
 
 
+@pytest.mark.parametrize("no,nu,nd", [(3, 1, 1), (4, 2, 2), (5, 2, 2), (5, 3, 1)])
+def test_abinitio_local_energy_restricted_strings(no, nu, nd):
+    """The local energy used at scale applies only the operator strings that
+    can connect n' to n; it must equal the one built from the unrestricted
+    operator sum (itself pinned by the Jordan-Wigner brute force above)."""
+    wl = inputs.abinitio("t", no, nu, nd, n_chol=5, seed=10 + no, n_walkers=6)
+    P = oracle.Problem(wl)
+    for o in wl.init_occ:
+        assert P.local_energy(o) == pytest.approx(P.local_energy_bruteforce(o), rel=1e-12, abs=1e-12)
+
+
 # ---------------------------------------------------------------------------
 # derivative ratios (Eq. 3): finite differences and structural invariants
 # ---------------------------------------------------------------------------
