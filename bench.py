@@ -219,7 +219,7 @@ def run_gpu(args, rank, world, dist):
         "sv_gbs": round(ach, 1) if ach else None,
         "fp64_path": fp64,
         "speedup_vs_fp64_path": round(fp64["ms_per_step"] / ms, 3) if fp64 else None,
-        "roofline": {"bound": "hbm", "kernel": "k_sr_main<bf16,f32,K=1> (Eq. 7 gather/scatter pass)",
+        "roofline": {"bound": "hbm", "kernel": "k_gather_G<1,U> + k_scatter_T<1> (sorted two-pass Eq. 7 product, BF16 store)",
                      "achieved": round(ach, 1) if ach else None, "peak": peak, "unit": "GB/s",
                      "frac": round(ach / peak, 4) if ach else None, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": per_launch_bytes,

@@ -86,8 +86,7 @@ struct vmc_ctx {
     void* d_T = nullptr;
     void* d_pfpart = nullptr;
     size_t pfpart_bytes = 0;
-    void* d_corrpart = nullptr;
-    size_t corrpart_bytes = 0;
+    double* d_corrraw = nullptr;   // [ncp][kMaxK] correlator sums of a pass
     double* d_part = nullptr;   // 8 slots x kNumPart x kMaxK
     double* d_pfraw = nullptr;  // [npf][K] reduced pairing-block sums
     uint32_t *d_G = nullptr, *d_Tsort = nullptr, *d_counts = nullptr, *d_total = nullptr, *d_base = nullptr;
@@ -345,8 +344,7 @@ extern "C" int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, co
     ACK(h->alloc((double**)&h->d_T, (size_t)h->ncap * kMaxK));
     h->pfpart_bytes = (size_t)4 * h->nsm * h->npf * kMaxK * sizeof(double);
     ACK(h->alloc((char**)&h->d_pfpart, h->pfpart_bytes));
-    h->corrpart_bytes = (size_t)16 * std::max<int64_t>(h->ncp, 1) * kMaxK * sizeof(double);
-    ACK(h->alloc((char**)&h->d_corrpart, h->corrpart_bytes));
+    ACK(h->alloc(&h->d_corrraw, (size_t)std::max<int64_t>(h->ncp, 1) * kMaxK));
     ACK(h->alloc(&h->d_part, (size_t)8 * kNumPart * kMaxK));
     ACK(h->alloc(&h->d_pfraw, (size_t)h->npf * kMaxK));
     ACK(h->alloc(&h->d_scal, 16));
@@ -768,15 +766,10 @@ static int launch_stream(vmc_ctx* h, const void* s_pf, const float* V, const flo
     return VMC_OK;
 }
 
-static int corr_chunks(const vmc_ctx* h) {
-    int nc = std::max(1, h->ncorr);
-    int ch = (4 * h->nsm + nc - 1) / nc;
-    return std::max(1, std::min(ch, 16));
-}
-
+// correlator scatter: one thread-block cluster of kCorrCluster CTAs per
+// correlator, the sums over samples go to d_corrraw
 template <typename AT, int K>
-static int launch_corr(vmc_ctx* h, const AT* T, const int* stop, cudaStream_t st, int* nchunk) {
-    *nchunk = corr_chunks(h);
+static int launch_corr(vmc_ctx* h, const AT* T, const int* stop, cudaStream_t st) {
     if (h->ncorr == 0) return VMC_OK;
     size_t smem = (size_t)h->maxd * K * sizeof(AT);
     if (smem > h->smem_optin) return VMC_ERR_UNSUPPORTED;
@@ -787,10 +780,9 @@ static int launch_corr(vmc_ctx* h, const AT* T, const int* stop, cudaStream_t st
     a.n_s = h->n_s;
     a.cidxT = h->d_cidxT;
     a.T = T;
-    a.corr_partial = (AT*)h->d_corrpart;
-    a.nchunk = *nchunk;
+    a.corr_raw = h->d_corrraw;
     a.stop = stop;
-    kern<<<h->ncorr * *nchunk, 256, smem, st>>>(a); h->n_launch++;
+    kern<<<h->ncorr * kCorrCluster, 256, smem, st>>>(a); h->n_launch++;
     VCK(cudaGetLastError());
     return VMC_OK;
 }
@@ -803,8 +795,14 @@ static int reduce_pf(vmc_ctx* h, int nblk, int K, cudaStream_t st) {
     return VMC_OK;
 }
 
-// blocks of the finalize kernels; their K partial dots per block go to one
-// slot of kNumPart * kMaxK doubles
+// blocks of the unrolled vector kernels (4 elements per thread); their K
+// partial dots per block go to one slot of kNumPart * kMaxK doubles
+static int vgrid(const vmc_ctx* h, int K = 1) {
+    int64_t g = (h->nv + 1023) / 1024;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)kNumPart * kMaxK / K));
+}
+
+// blocks of the gradient finalize kernel
 static int fin_grid(const vmc_ctx* h, int K = 1) {
     int64_t g = (h->nv + 255) / 256;
     return (int)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)kNumPart * kMaxK / K));
@@ -836,6 +834,25 @@ static int ensure_sorted(vmc_ctx* h, cudaStream_t st) {
     return VMC_OK;
 }
 
+// gather kernel holding a whole G row in registers: U 16-byte loads per lane
+using GatherKern = void (*)(SortedArgs);
+template <int K>
+static GatherKern gather_kernel(int u) {
+    if constexpr (K == 1) {
+        static const GatherKern tab[16] = {
+            k_gather_G<1, 1>,  k_gather_G<1, 2>,  k_gather_G<1, 3>,  k_gather_G<1, 4>,
+            k_gather_G<1, 5>,  k_gather_G<1, 6>,  k_gather_G<1, 7>,  k_gather_G<1, 8>,
+            k_gather_G<1, 9>,  k_gather_G<1, 10>, k_gather_G<1, 11>, k_gather_G<1, 12>,
+            k_gather_G<1, 13>, k_gather_G<1, 14>, k_gather_G<1, 15>, k_gather_G<1, 16>};
+        return u >= 1 && u <= 16 ? tab[u - 1] : nullptr;
+    } else {
+        if (u <= 4) return k_gather_G<K, 4>;
+        if (u <= 8) return k_gather_G<K, 8>;
+        if (u <= 16) return k_gather_G<K, 16>;
+        return nullptr;
+    }
+}
+
 // gather + parameter-major scatter for the BF16 store; the pairing sums go
 // to d_pfraw (FP64) and t_s to T
 template <int K>
@@ -862,14 +879,15 @@ static int launch_sorted(vmc_ctx* h, const float* V, const float* invC, float* T
     a.stop = stop;
     const size_t smem = (size_t)h->npf * K * 4 + (size_t)(h->ncorr + 1) * 4;
     if (smem > h->smem_optin) return VMC_ERR_UNSUPPORTED;
-    auto gk = k_gather_G<K>;
+    auto gk = gather_kernel<K>((int)((h->Pst / 4 + 31) / 32));
+    if (!gk) return VMC_ERR_UNSUPPORTED;
     VCK(cudaFuncSetAttribute(gk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    VCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gk, 512, smem));
+    VCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gk, 256, smem));
     int grid = h->nsm * std::max(1, per_sm);
-    int64_t need = (h->n_s + 15) / 16;
+    int64_t need = (h->n_s + 7) / 8;
     if (need < grid) grid = (int)std::max<int64_t>(1, need);
-    gk<<<grid, 512, smem, st>>>(a); h->n_launch++;
+    gk<<<grid, 256, smem, st>>>(a); h->n_launch++;
     k_scatter_T<K><<<(h->npf + 7) / 8, 256, 0, st>>>(a); h->n_launch++;
     VCK(cudaGetLastError());
     if (h->prof) {
@@ -880,7 +898,8 @@ static int launch_sorted(vmc_ctx* h, const float* V, const float* invC, float* T
 }
 
 // out = (S + shift I) V with K vectors, V/out in AT precision ([K][nv]).
-// obv_part holds kNumPart partial dots Obar . V unless null (then computed).
+// obv_part holds vgrid(h, K) partial dots Obar . V unless null (then computed);
+// dot_part receives vgrid(h, K) partial dots out . V.
 template <typename ST, typename AT, int K>
 static int apply_S_impl(vmc_ctx* h, const void* s_pf, const double* Obar, const AT* V, AT* out, double shift,
                         const int* stop, const double* obv_part, double* dot_part, cudaStream_t st) {
@@ -888,7 +907,7 @@ static int apply_S_impl(vmc_ctx* h, const void* s_pf, const double* Obar, const 
     if (sizeof(AT) == 8) invC = (const AT*)h->d_invC64;
     else invC = (const AT*)h->d_invC32;
     AT* T = (AT*)h->d_T;
-    int nblk = 0, nchunk = 0;
+    int nblk = 0;
     int rc = VMC_ERR_UNSUPPORTED;
     bool sorted = false;
     if constexpr (sizeof(AT) == 4 && sizeof(ST) == 2) {
@@ -903,14 +922,14 @@ static int apply_S_impl(vmc_ctx* h, const void* s_pf, const double* Obar, const 
     }
     if (rc == VMC_ERR_UNSUPPORTED) rc = launch_main<ST, AT, K, true>(h, s_pf, V, invC, T, stop, st, &nblk);
     if (rc) return rc;
-    rc = launch_corr<AT, K>(h, T, stop, st, &nchunk);
+    rc = launch_corr<AT, K>(h, T, stop, st);
     if (rc) return rc;
     if (!sorted) {
         rc = reduce_pf<AT>(h, nblk, K, st);
         if (rc) return rc;
     }
     if (!obv_part) {
-        k_dot_part<double, AT, K><<<kNumPart, 256, 0, st>>>(Obar, V, h->nv, h->part(0), stop); h->n_launch++;
+        k_dot_part<double, AT, K><<<vgrid(h, K), 256, 0, st>>>(Obar, V, h->nv, h->part(0), stop); h->n_launch++;
         VCK(cudaGetLastError());
         obv_part = h->part(0);
     }
@@ -918,20 +937,19 @@ static int apply_S_impl(vmc_ctx* h, const void* s_pf, const double* Obar, const 
     f.pb = h->pb;
     f.n_s = h->n_s;
     f.n_pf_part = nblk;
-    f.nchunk = h->ncorr ? nchunk : 0;
     f.pf_partial = (const AT*)h->d_pfpart;
     f.pf_raw = h->d_pfraw;
-    f.corr_partial = (const AT*)h->d_corrpart;
+    f.corr_raw = h->d_corrraw;
     f.invC = invC;
     f.Obar = Obar;
     f.obv_part = obv_part;
-    f.n_obv_part = kNumPart;
+    f.n_obv_part = vgrid(h, K);
     f.V = V;
     f.shift = shift;
     f.out = out;
     f.dot_part = dot_part;
     f.stop = stop;
-    k_finalize_S<AT, AT, K><<<fin_grid(h, K), 256, 0, st>>>(f); h->n_launch++;
+    k_finalize_S<AT, AT, K><<<vgrid(h, K), 256, 0, st>>>(f); h->n_launch++;
     VCK(cudaGetLastError());
     return VMC_OK;
 }
@@ -958,12 +976,12 @@ static int gradient_pass(vmc_ctx* h, int kind, double* g, cudaStream_t st) {
     double* T = (double*)h->d_T;
     k_build_T_grad<<<kNumPart, 256, 0, st>>>(h->d_E, h->n_s, T, h->part(1)); h->n_launch++;
     VCK(cudaGetLastError());
-    int nblk = 0, nchunk = 0, rc;
+    int nblk = 0, rc;
     if (kind == 0) rc = launch_main<double, double, 2, false>(h, src, nullptr, nullptr, T, nullptr, st, &nblk);
     else if (kind == 1) rc = launch_main<float, double, 2, false>(h, src, nullptr, nullptr, T, nullptr, st, &nblk);
     else rc = launch_main<__nv_bfloat16, double, 2, false>(h, src, nullptr, nullptr, T, nullptr, st, &nblk);
     if (rc) return rc;
-    rc = launch_corr<double, 2>(h, T, nullptr, st, &nchunk);
+    rc = launch_corr<double, 2>(h, T, nullptr, st);
     if (rc) return rc;
     rc = reduce_pf<double>(h, nblk, 2, st);
     if (rc) return rc;
@@ -971,10 +989,9 @@ static int gradient_pass(vmc_ctx* h, int kind, double* g, cudaStream_t st) {
     f.pb = h->pb;
     f.n_s = h->n_s;
     f.n_pf_part = nblk;
-    f.nchunk = h->ncorr ? nchunk : 0;
     f.pf_partial = (const double*)h->d_pfpart;
     f.pf_raw = h->d_pfraw;
-    f.corr_partial = (const double*)h->d_corrpart;
+    f.corr_raw = h->d_corrraw;
     f.invC = h->d_invC64;
     f.Obar_out = h->d_Obar[kind];
     f.g_out = g;
@@ -1112,9 +1129,10 @@ static int cg_loop(vmc_ctx* h, const void* s_pf, const double* Obar, const VT* b
     double* pAp_part = h->part(3);
     double* rr_part = h->part(4);
     double* obp_part = h->part(5);
-    k_cg_init<VT><<<kNumPart, 256, 0, st>>>(b, x, r, p, n, init_part); h->n_launch++;
-    k_cg_start<<<1, 32, 0, st>>>(init_part, kNumPart, h->d_scal, tol, h->d_stop); h->n_launch++;
-    k_dot_part<double, VT, 1><<<kNumPart, 256, 0, st>>>(Obar, p, n, obp_part, h->d_stop); h->n_launch++;
+    const int vg = vgrid(h, 1);
+    k_cg_init<VT><<<vg, 256, 0, st>>>(b, x, r, p, n, init_part); h->n_launch++;
+    k_cg_start<<<1, 32, 0, st>>>(init_part, vg, h->d_scal, tol, h->d_stop); h->n_launch++;
+    k_dot_part<double, VT, 1><<<vg, 256, 0, st>>>(Obar, p, n, obp_part, h->d_stop); h->n_launch++;
     VCK(cudaGetLastError());
     int done = 0;
     *iters = 0;
@@ -1123,8 +1141,8 @@ static int cg_loop(vmc_ctx* h, const void* s_pf, const double* Obar, const VT* b
         for (int j = 0; j < kChunk; ++j) {
             int rc = apply_S_impl<ST, VT, 1>(h, s_pf, Obar, p, q, shift, h->d_stop, obp_part, pAp_part, st);
             if (rc) return rc;
-            k_cg_xr<VT><<<kNumPart, 256, 0, st>>>(x, r, p, q, n, pAp_part, fin_grid(h, 1), h->d_scal, rr_part, h->d_stop); h->n_launch++;
-            k_cg_p<VT><<<kNumPart, 256, 0, st>>>(r, p, n, rr_part, kNumPart, h->d_scal, Obar, obp_part,
+            k_cg_xr<VT><<<vg, 256, 0, st>>>(x, r, p, q, n, pAp_part, vg, h->d_scal, rr_part, h->d_stop); h->n_launch++;
+            k_cg_p<VT><<<vg, 256, 0, st>>>(r, p, n, rr_part, vg, h->d_scal, Obar, obp_part,
                                                  h->d_stop, max_iter); h->n_launch++;
             VCK(cudaGetLastError());
         }

@@ -89,20 +89,20 @@ struct CorrArgs {
     int64_t n_s;
     const uint16_t* cidxT;  // [ncorr][n_s]
     const AT* T;            // [n_s][K]
-    AT* corr_partial;       // [nchunk][ncp][K]
-    int nchunk;
+    double* corr_raw;       // [ncp][K] sum over samples of t_s per state
     const int* stop;
 };
+
+constexpr int kCorrCluster = 8;  // CTAs per correlator (one thread-block cluster)
 
 template <typename AT, typename VT>
 struct FinArgs {
     DevProblem pb;
     int64_t n_s;
     int n_pf_part;          // CTAs of the main pass
-    int nchunk;
     const AT* pf_partial;
     const double* pf_raw;   // [npf][K] sum over CTAs of pf_partial
-    const AT* corr_partial;
+    const double* corr_raw; // [ncp][K] correlator sums
     const AT* invC;
     const double* Obar;     // [nv] (S mode)
     const double* obv_part; // [nblk][K] partial dots Obar . V (S mode)
@@ -122,7 +122,8 @@ struct FinArgs {
 
 template <typename ST, typename AT, int K, bool GATHER>
 __global__ void __launch_bounds__(512) k_sr_main(MainArgs<AT> a);
-template <typename AT, int K> __global__ void __launch_bounds__(256) k_corr_scatter(CorrArgs<AT> a);
+template <typename AT, int K>
+__global__ void __cluster_dims__(kCorrCluster, 1, 1) __launch_bounds__(256) k_corr_scatter(CorrArgs<AT> a);
 template <typename AT, typename VT, int K> __global__ void __launch_bounds__(256) k_finalize_S(FinArgs<AT, VT> a);
 template <typename AT> __global__ void __launch_bounds__(256) k_finalize_grad(FinArgs<AT, double> a);
 __global__ void k_build_T_grad(const double* E, int64_t n_s, double* T, double* E_part);
@@ -211,7 +212,7 @@ __global__ void __launch_bounds__(1024) k_scan_params(const uint32_t* total, int
 __global__ void __launch_bounds__(512) k_fill_T(const uint32_t* G, int64_t Pst, int P, int64_t s_begin,
                                                 int64_t s_end, int npf, const uint32_t* offs, const uint32_t* base,
                                                 uint32_t* T);
-template <int K> __global__ void __launch_bounds__(512) k_gather_G(SortedArgs a);
+template <int K, int U> __global__ void __launch_bounds__(256) k_gather_G(SortedArgs a);
 template <int K> __global__ void __launch_bounds__(256) k_scatter_T(SortedArgs a);
 
 }  // namespace vmc

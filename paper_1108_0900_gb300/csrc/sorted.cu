@@ -123,9 +123,12 @@ __global__ void __launch_bounds__(512) k_fill_T(const uint32_t* G, int64_t Pst, 
     }
 }
 
-// gather: t_s = sum_c V[k_c]/C[k_c] + sum_e W_e v[pq(e)], warp per sample
-template <int K>
-__global__ void __launch_bounds__(512) k_gather_G(SortedArgs a) {
+// gather: t_s = sum_c V[k_c]/C[k_c] + sum_e W_e v[pq(e)], warp per sample.
+// U = ceil(Pst / 128): every lane issues all of its U 16-byte loads of the
+// sample's row before the correlator lookups and before consuming any, so a
+// whole row (6 KB at 56 electrons) is in flight per warp.
+template <int K, int U>
+__global__ void __launch_bounds__(256) k_gather_G(SortedArgs a) {
     if (a.stop && *a.stop) return;
     extern __shared__ __align__(16) unsigned char smem[];
     const DevProblem& pb = a.pb;
@@ -139,9 +142,16 @@ __global__ void __launch_bounds__(512) k_gather_G(SortedArgs a) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int n4 = (int)(a.Pst >> 2);
     for (int64_t s = (int64_t)blockIdx.x * nw + wid; s < a.n_s; s += (int64_t)gridDim.x * nw) {
-        float t[K], u[K];
+        const uint4* g4 = (const uint4*)(a.G + s * a.Pst);
+        uint4 g[U];
 #pragma unroll
-        for (int kk = 0; kk < K; ++kk) t[kk] = u[kk] = 0.f;
+        for (int u = 0; u < U; ++u) {
+            const int i = lane + 32 * u;
+            g[u] = i < n4 ? __ldcs(g4 + i) : make_uint4(0u, 0u, 0u, 0u);
+        }
+        float t[K], w[K];
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) t[kk] = w[kk] = 0.f;
         const uint16_t* cid = a.s_cidx + s * a.ncst;
         for (int c = lane; c < pb.ncorr; c += 32) {
             const int k = coff[c] + (int)__ldg(cid + c);
@@ -149,31 +159,40 @@ __global__ void __launch_bounds__(512) k_gather_G(SortedArgs a) {
 #pragma unroll
             for (int kk = 0; kk < K; ++kk) t[kk] += __ldg(a.V + kk * pb.nv + k) * ic;
         }
-        const uint4* g4 = (const uint4*)(a.G + s * a.Pst);
-#pragma unroll 4
-        for (int i = lane; i < n4; i += 32) {
-            const uint4 g = __ldcs(g4 + i);
-            const uint32_t w[4] = {g.x, g.y, g.z, g.w};
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t e[4] = {g[u].x, g[u].y, g[u].z, g[u].w};
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const float val = __uint_as_float(w[j] << 16);
-                const int pq = (int)(w[j] >> 16);
+                const float val = __uint_as_float(e[j] << 16);
+                const int pq = (int)(e[j] >> 16);
 #pragma unroll
                 for (int kk = 0; kk < K; ++kk) {
-                    if (j & 1) u[kk] += val * vpf[pq * K + kk];
+                    if (j & 1) w[kk] += val * vpf[pq * K + kk];
                     else t[kk] += val * vpf[pq * K + kk];
                 }
             }
         }
 #pragma unroll
-        for (int kk = 0; kk < K; ++kk) t[kk] = warp_sum(t[kk] + u[kk]);
+        for (int kk = 0; kk < K; ++kk) t[kk] = warp_sum(t[kk] + w[kk]);
         if (lane == 0)
 #pragma unroll
             for (int kk = 0; kk < K; ++kk) a.Tv[s * K + kk] = t[kk];
     }
 }
 
-// scatter: raw[pq][kk] = sum over samples containing pq of W t_s, warp per pq
+// one T entry of a parameter's run: acc += W * t_s
+template <int K>
+__device__ __forceinline__ void scatter_entry(const float* __restrict__ Tv, int64_t s0, uint32_t v, float (&acc)[K]) {
+    const float wv = __uint_as_float(v << 16);
+    const int64_t t0 = (s0 + (v >> 16)) * K;
+#pragma unroll
+    for (int kk = 0; kk < K; ++kk) acc[kk] += wv * __ldg(Tv + t0 + kk);
+}
+
+// scatter: raw[pq][kk] = sum over samples containing pq of W t_s, warp per
+// pq.  The run [lo, hi) of T is read as an unaligned head, 16-byte loads
+// (2 per lane per step, 256 entries per warp in flight) and a tail.
 template <int K>
 __global__ void __launch_bounds__(256) k_scatter_T(SortedArgs a) {
     if (a.stop && *a.stop) return;
@@ -183,28 +202,35 @@ __global__ void __launch_bounds__(256) k_scatter_T(SortedArgs a) {
     float acc[K], acc2[K];
 #pragma unroll
     for (int kk = 0; kk < K; ++kk) acc[kk] = acc2[kk] = 0.f;
+    const uint4* T4 = (const uint4*)a.T;
     for (int c = 0; c < a.nchunk; ++c) {
         const uint32_t* base = a.base + (size_t)c * (a.pb.npf + 1);
         const uint32_t lo = base[pq], hi = base[pq + 1];
         const int64_t s0 = (int64_t)c * 65536;
-        uint32_t j = lo + lane;
-        for (; j + 32 < hi; j += 64) {
-            const uint32_t v0 = __ldcs(a.T + j), v1 = __ldcs(a.T + j + 32);
-            const float w0 = __uint_as_float(v0 << 16), w1 = __uint_as_float(v1 << 16);
-            const int64_t t0 = (s0 + (v0 >> 16)) * K, t1 = (s0 + (v1 >> 16)) * K;
-#pragma unroll
-            for (int kk = 0; kk < K; ++kk) {
-                acc[kk] += w0 * __ldg(a.Tv + t0 + kk);
-                acc2[kk] += w1 * __ldg(a.Tv + t1 + kk);
-            }
+        const uint32_t a4 = min(hi, (lo + 3u) & ~3u);   // end of the head
+        const uint32_t q0 = a4 >> 2, q1 = a4 < hi ? hi >> 2 : q0;
+        if (lo + lane < a4) scatter_entry<K>(a.Tv, s0, __ldcs(a.T + lo + lane), acc);
+        uint32_t q = q0 + lane;
+        for (; q + 32 < q1; q += 64) {
+            const uint4 u0 = __ldcs(T4 + q), u1 = __ldcs(T4 + q + 32);
+            scatter_entry<K>(a.Tv, s0, u0.x, acc);
+            scatter_entry<K>(a.Tv, s0, u0.y, acc2);
+            scatter_entry<K>(a.Tv, s0, u0.z, acc);
+            scatter_entry<K>(a.Tv, s0, u0.w, acc2);
+            scatter_entry<K>(a.Tv, s0, u1.x, acc);
+            scatter_entry<K>(a.Tv, s0, u1.y, acc2);
+            scatter_entry<K>(a.Tv, s0, u1.z, acc);
+            scatter_entry<K>(a.Tv, s0, u1.w, acc2);
         }
-        if (j < hi) {
-            const uint32_t v0 = __ldcs(a.T + j);
-            const float w0 = __uint_as_float(v0 << 16);
-            const int64_t t0 = (s0 + (v0 >> 16)) * K;
-#pragma unroll
-            for (int kk = 0; kk < K; ++kk) acc[kk] += w0 * __ldg(a.Tv + t0 + kk);
+        if (q < q1) {
+            const uint4 u0 = __ldcs(T4 + q);
+            scatter_entry<K>(a.Tv, s0, u0.x, acc);
+            scatter_entry<K>(a.Tv, s0, u0.y, acc2);
+            scatter_entry<K>(a.Tv, s0, u0.z, acc);
+            scatter_entry<K>(a.Tv, s0, u0.w, acc2);
         }
+        const uint32_t t0 = max(a4, q1 << 2);           // start of the tail
+        if (t0 + lane < hi) scatter_entry<K>(a.Tv, s0, __ldcs(a.T + t0 + lane), acc2);
     }
 #pragma unroll
     for (int kk = 0; kk < K; ++kk) {
@@ -213,9 +239,28 @@ __global__ void __launch_bounds__(256) k_scatter_T(SortedArgs a) {
     }
 }
 
-template __global__ void k_gather_G<1>(SortedArgs);
-template __global__ void k_gather_G<2>(SortedArgs);
-template __global__ void k_gather_G<4>(SortedArgs);
+template __global__ void k_gather_G<1, 1>(SortedArgs);
+template __global__ void k_gather_G<1, 2>(SortedArgs);
+template __global__ void k_gather_G<1, 3>(SortedArgs);
+template __global__ void k_gather_G<1, 4>(SortedArgs);
+template __global__ void k_gather_G<1, 5>(SortedArgs);
+template __global__ void k_gather_G<1, 6>(SortedArgs);
+template __global__ void k_gather_G<1, 7>(SortedArgs);
+template __global__ void k_gather_G<1, 8>(SortedArgs);
+template __global__ void k_gather_G<1, 9>(SortedArgs);
+template __global__ void k_gather_G<1, 10>(SortedArgs);
+template __global__ void k_gather_G<1, 11>(SortedArgs);
+template __global__ void k_gather_G<1, 12>(SortedArgs);
+template __global__ void k_gather_G<1, 13>(SortedArgs);
+template __global__ void k_gather_G<1, 14>(SortedArgs);
+template __global__ void k_gather_G<1, 15>(SortedArgs);
+template __global__ void k_gather_G<1, 16>(SortedArgs);
+template __global__ void k_gather_G<2, 4>(SortedArgs);
+template __global__ void k_gather_G<2, 8>(SortedArgs);
+template __global__ void k_gather_G<2, 16>(SortedArgs);
+template __global__ void k_gather_G<4, 4>(SortedArgs);
+template __global__ void k_gather_G<4, 8>(SortedArgs);
+template __global__ void k_gather_G<4, 16>(SortedArgs);
 template __global__ void k_scatter_T<1>(SortedArgs);
 template __global__ void k_scatter_T<2>(SortedArgs);
 template __global__ void k_scatter_T<4>(SortedArgs);

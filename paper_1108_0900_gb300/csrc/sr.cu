@@ -11,8 +11,11 @@
 //   scatter  out[pq(e)] += t_s W_e into a per-CTA shared-memory image of the
 //            pairing block (written out as one partial per CTA),
 // and the correlator scatter runs correlator-major over a transposed state
-// array into a shared-memory histogram of each correlator's 4^m states, so
-// neither half uses global atomics.
+// array into shared-memory histograms of each correlator's 4^m states, one
+// per CTA of a thread-block cluster, summed through distributed shared
+// memory, so neither half uses global atomics.
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -100,24 +103,29 @@ __global__ void __launch_bounds__(512) k_sr_main(MainArgs<AT> a) {
     for (int i = threadIdx.x; i < npf * K; i += blockDim.x) dst[i] = acc[i];
 }
 
-// correlator-major scatter: block (c, chunk) histograms t_s over the states
-// of correlator c for its slice of samples.  Slices start on multiples of 8
-// samples; each thread takes 8 consecutive samples per step (one 16-byte
-// load of states, K x 8 values of t) so the loads of several samples are in
-// flight before their shared-memory atomics.
+// correlator-major scatter on a thread-block cluster: the kCorrCluster CTAs
+// of cluster c histogram t_s over the 4^m states of correlator c, each for a
+// slice of the samples, into their own shared memory; after a cluster barrier
+// CTA r sums its share of the states over the cluster's histograms through
+// distributed shared memory (fixed order) and writes raw[off_c + state].
+// Slices start on multiples of 8 samples; each thread takes 8 consecutive
+// samples per step (one 16-byte load of states, K x 8 values of t).
 template <typename AT, int K>
-__global__ void __launch_bounds__(256) k_corr_scatter(CorrArgs<AT> a) {
-    if (a.stop && *a.stop) return;
+__global__ void __cluster_dims__(kCorrCluster, 1, 1) __launch_bounds__(256) k_corr_scatter(CorrArgs<AT> a) {
+    if (a.stop && *a.stop) return;   // uniform over the grid: no CTA reaches a cluster barrier
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char smem[];
     AT* h = (AT*)smem;
     const DevProblem& pb = a.pb;
-    const int c = blockIdx.x / a.nchunk, ch = blockIdx.x % a.nchunk;
+    const int c = blockIdx.x / kCorrCluster;
+    const int rank = (int)cluster.block_rank();
     const int64_t off = pb.corr_off[c];
     const int d = (int)(pb.corr_off[c + 1] - off);
     for (int i = threadIdx.x; i < d * K; i += blockDim.x) h[i] = AT(0);
     __syncthreads();
-    const int64_t len = ((a.n_s + a.nchunk - 1) / a.nchunk + 7) & ~(int64_t)7;
-    const int64_t s0 = min(a.n_s, ch * len), s1 = min(a.n_s, s0 + len);
+    const int64_t len = ((a.n_s + kCorrCluster - 1) / kCorrCluster + 7) & ~(int64_t)7;
+    const int64_t s0 = min(a.n_s, rank * len), s1 = min(a.n_s, s0 + len);
     const uint16_t* st = a.cidxT + (int64_t)c * a.n_s;
     // 16-byte loads need the row to start on a 16-byte boundary
     const bool vec = ((a.n_s & 7) == 0);
@@ -143,9 +151,16 @@ __global__ void __launch_bounds__(256) k_corr_scatter(CorrArgs<AT> a) {
 #pragma unroll
         for (int kk = 0; kk < K; ++kk) atomicAdd(&h[i * K + kk], a.T[q * K + kk]);
     }
-    __syncthreads();
-    AT* dst = a.corr_partial + ((int64_t)ch * pb.ncp + off) * K;
-    for (int i = threadIdx.x; i < d * K; i += blockDim.x) dst[i] = h[i];
+    cluster.sync();
+    const int per = (d + kCorrCluster - 1) / kCorrCluster;
+    const int b0 = min(d, rank * per) * K, b1 = min(d, (rank + 1) * per) * K;
+    for (int i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+        double acc = 0.0;
+#pragma unroll
+        for (int q = 0; q < kCorrCluster; ++q) acc += (double)cluster.map_shared_rank(h, q)[i];
+        a.corr_raw[off * K + i] = acc;
+    }
+    cluster.sync();   // keep this CTA's histogram alive until the cluster has read it
 }
 
 template <int K>
@@ -203,13 +218,17 @@ __device__ __forceinline__ double fin_raw(const FinArgs<AT, VT>& a, int64_t k, i
     const DevProblem& pb = a.pb;
     double raw = 0.0;
     if (k < pb.ncp) {
-        for (int ch = 0; ch < a.nchunk; ++ch) raw += (double)a.corr_partial[((int64_t)ch * pb.ncp + k) * K + kk];
-        raw *= (double)a.invC[k];
+        raw = a.corr_raw[k * K + kk] * (double)a.invC[k];
     } else {
         raw = a.pf_raw[(k - pb.ncp) * K + kk];
     }
     return raw / (double)a.n_s;
 }
+
+// Vector kernels cover kVecUnroll elements per thread, strided by the grid,
+// with every load of the body issued before the arithmetic: one launch over
+// the 270k-parameter vectors is one round trip to memory per thread.
+constexpr int kVecUnroll = 4;
 
 // out = raw - Obar (Obar . V) + shift V; dot_part = partial out . V
 template <typename AT, typename VT, int K>
@@ -225,17 +244,38 @@ __global__ void __launch_bounds__(256) k_finalize_S(FinArgs<AT, VT> a) {
     }
     __syncthreads();
     const int64_t nv = a.pb.nv;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     double dl[K];
 #pragma unroll
     for (int kk = 0; kk < K; ++kk) dl[kk] = 0.0;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nv; k += (int64_t)gridDim.x * blockDim.x) {
-        const double ob = a.Obar[k];
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < nv; i0 += kVecUnroll * stride) {
+        double ob[kVecUnroll], v[kVecUnroll][K], raw[kVecUnroll][K];
 #pragma unroll
-        for (int kk = 0; kk < K; ++kk) {
-            double v = (double)a.V[kk * nv + k];
-            double o = fin_raw<AT, VT, K>(a, k, kk) - ob * obv[kk] + a.shift * v;
-            a.out[kk * nv + k] = (VT)o;
-            dl[kk] += o * v;
+        for (int u = 0; u < kVecUnroll; ++u) {
+            const int64_t k = i0 + u * stride;
+            ob[u] = 0.0;
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) v[u][kk] = raw[u][kk] = 0.0;
+            if (k < nv) {
+                ob[u] = a.Obar[k];
+#pragma unroll
+                for (int kk = 0; kk < K; ++kk) {
+                    v[u][kk] = (double)a.V[kk * nv + k];
+                    raw[u][kk] = fin_raw<AT, VT, K>(a, k, kk);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kVecUnroll; ++u) {
+            const int64_t k = i0 + u * stride;
+            if (k < nv) {
+#pragma unroll
+                for (int kk = 0; kk < K; ++kk) {
+                    const double o = raw[u][kk] - ob[u] * obv[kk] + a.shift * v[u][kk];
+                    a.out[kk * nv + k] = (VT)o;
+                    dl[kk] += o * v[u][kk];
+                }
+            }
         }
     }
     if (a.dot_part) block_reduce_store<K>(dl, a.dot_part);
@@ -276,13 +316,23 @@ __global__ void k_build_T_grad(const double* E, int64_t n_s, double* T, double* 
 template <typename TA, typename TB, int K>
 __global__ void __launch_bounds__(256) k_dot_part(const TA* x, const TB* y, int64_t n, double* part, const int* stop) {
     if (stop && *stop) return;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     double loc[K];
 #pragma unroll
     for (int kk = 0; kk < K; ++kk) loc[kk] = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double xi = (double)x[i];
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += kVecUnroll * stride) {
+        double xv[kVecUnroll], yv[kVecUnroll][K];
 #pragma unroll
-        for (int kk = 0; kk < K; ++kk) loc[kk] += xi * (double)y[kk * n + i];
+        for (int u = 0; u < kVecUnroll; ++u) {
+            const int64_t i = i0 + u * stride;
+            xv[u] = i < n ? (double)x[i] : 0.0;
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) yv[u][kk] = i < n ? (double)y[kk * n + i] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kVecUnroll; ++u)
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) loc[kk] += xv[u] * yv[u][kk];
     }
     block_reduce_store<K>(loc, part);
 }
@@ -325,13 +375,25 @@ __device__ __forceinline__ double sum_part(const double* part, int n, int kk, in
 
 template <typename VT>
 __global__ void __launch_bounds__(256) k_cg_init(const VT* b, VT* x, VT* r, VT* p, int64_t n, double* part) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     double loc[1] = {0.0};
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        VT v = b[i];
-        x[i] = VT(0);
-        r[i] = v;
-        p[i] = v;
-        loc[0] += (double)v * (double)v;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += kVecUnroll * stride) {
+        VT bv[kVecUnroll];
+#pragma unroll
+        for (int u = 0; u < kVecUnroll; ++u) {
+            const int64_t i = i0 + u * stride;
+            bv[u] = i < n ? b[i] : VT(0);
+        }
+#pragma unroll
+        for (int u = 0; u < kVecUnroll; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (i < n) {
+                x[i] = VT(0);
+                r[i] = bv[u];
+                p[i] = bv[u];
+                loc[0] += (double)bv[u] * (double)bv[u];
+            }
+        }
     }
     block_reduce_store<1>(loc, part);
 }
@@ -362,13 +424,30 @@ __global__ void __launch_bounds__(256) k_cg_xr(VT* x, VT* r, const VT* p, const 
         }
     }
     __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     double loc[1] = {0.0};
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double xi = (double)x[i] + alpha * (double)p[i];
-        double ri = (double)r[i] - alpha * (double)Ap[i];
-        x[i] = (VT)xi;
-        r[i] = (VT)ri;
-        loc[0] += ri * ri;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += kVecUnroll * stride) {
+        double xv[kVecUnroll], rv[kVecUnroll], pv[kVecUnroll], qv[kVecUnroll];
+#pragma unroll
+        for (int u = 0; u < kVecUnroll; ++u) {
+            const int64_t i = i0 + u * stride;
+            const bool in = i < n;
+            xv[u] = in ? (double)x[i] : 0.0;
+            rv[u] = in ? (double)r[i] : 0.0;
+            pv[u] = in ? (double)p[i] : 0.0;
+            qv[u] = in ? (double)Ap[i] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kVecUnroll; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (i < n) {
+                const double xi = xv[u] + alpha * pv[u];
+                const double ri = rv[u] - alpha * qv[u];
+                x[i] = (VT)xi;
+                r[i] = (VT)ri;
+                loc[0] += ri * ri;
+            }
+        }
     }
     block_reduce_store<1>(loc, rr_part);
     if (blockIdx.x == 0 && threadIdx.x == 0) scal[CG_RRP] = scal[CG_RR];
@@ -389,11 +468,27 @@ __global__ void __launch_bounds__(256) k_cg_p(const VT* r, VT* p, int64_t n, con
         }
     }
     __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     double loc[1] = {0.0};
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double pi = (double)r[i] + beta * (double)p[i];
-        p[i] = (VT)pi;
-        loc[0] += Obar[i] * pi;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += kVecUnroll * stride) {
+        double rv[kVecUnroll], pv[kVecUnroll], ov[kVecUnroll];
+#pragma unroll
+        for (int u = 0; u < kVecUnroll; ++u) {
+            const int64_t i = i0 + u * stride;
+            const bool in = i < n;
+            rv[u] = in ? (double)r[i] : 0.0;
+            pv[u] = in ? (double)p[i] : 0.0;
+            ov[u] = in ? Obar[i] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kVecUnroll; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (i < n) {
+                const double pi = rv[u] + beta * pv[u];
+                p[i] = (VT)pi;
+                loc[0] += ov[u] * pi;
+            }
+        }
     }
     block_reduce_store<1>(loc, obp_part);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
