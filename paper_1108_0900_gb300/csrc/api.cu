@@ -81,14 +81,15 @@ struct vmc_ctx {
     float* d_pf32 = nullptr;
     __nv_bfloat16* d_pf16 = nullptr;
     double* d_Obar[3] = {nullptr, nullptr, nullptr};
+    float* d_Obar32[3] = {nullptr, nullptr, nullptr};   // FP32 copies for the inner solve
     int* d_status = nullptr;
     // scratch
     void* d_T = nullptr;
     void* d_pfpart = nullptr;
     size_t pfpart_bytes = 0;
-    double* d_corrraw = nullptr;   // [ncp][kMaxK] correlator sums of a pass
+    double* d_corrraw = nullptr;   // [ncp][kMaxK] correlator sums of a pass (FP64 or FP32)
     double* d_part = nullptr;   // 8 slots x kNumPart x kMaxK
-    double* d_pfraw = nullptr;  // [npf][K] reduced pairing-block sums
+    double* d_pfraw = nullptr;  // [npf][K] reduced pairing-block sums (FP64 or FP32 per pass)
     uint32_t *d_G = nullptr, *d_Tsort = nullptr, *d_counts = nullptr, *d_total = nullptr, *d_base = nullptr;
     double* d_scal = nullptr;
     int* d_stop = nullptr;
@@ -339,6 +340,7 @@ extern "C" int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, co
         ACK(h->alloc(&h->d_base, (size_t)h->sort_nchunk * (h->npf + 1)));
     }
     for (int k = 0; k < 3; ++k) ACK(h->alloc(&h->d_Obar[k], h->nv));
+    for (int k = 0; k < 3; ++k) ACK(h->alloc(&h->d_Obar32[k], h->nv));
     ACK(h->alloc(&h->d_status, 4));
     // scratch
     ACK(h->alloc((double**)&h->d_T, (size_t)h->ncap * kMaxK));
@@ -780,7 +782,7 @@ static int launch_corr(vmc_ctx* h, const AT* T, const int* stop, cudaStream_t st
     a.n_s = h->n_s;
     a.cidxT = h->d_cidxT;
     a.T = T;
-    a.corr_raw = h->d_corrraw;
+    a.corr_raw = (AT*)h->d_corrraw;
     a.stop = stop;
     kern<<<h->ncorr * kCorrCluster, 256, smem, st>>>(a); h->n_launch++;
     VCK(cudaGetLastError());
@@ -790,7 +792,7 @@ static int launch_corr(vmc_ctx* h, const AT* T, const int* stop, cudaStream_t st
 template <typename AT>
 static int reduce_pf(vmc_ctx* h, int nblk, int K, cudaStream_t st) {
     const int n = h->npf * K;
-    k_reduce_pf<AT><<<(n + 31) / 32, 256, 0, st>>>((const AT*)h->d_pfpart, nblk, n, h->d_pfraw); h->n_launch++;
+    k_reduce_pf<AT><<<(n + 31) / 32, 256, 0, st>>>((const AT*)h->d_pfpart, nblk, n, (AT*)h->d_pfraw); h->n_launch++;
     VCK(cudaGetLastError());
     return VMC_OK;
 }
@@ -853,11 +855,11 @@ static GatherKern gather_kernel(int u) {
     }
 }
 
-// gather + parameter-major scatter for the BF16 store; the pairing sums go
-// to d_pfraw (FP64) and t_s to T
+// gather + parameter-major scatter for the BF16 store; the centered t_s go to
+// Tv and the pairing sums to d_pfraw (FP32)
 template <int K>
-static int launch_sorted(vmc_ctx* h, const float* V, const float* invC, float* Tv, const int* stop,
-                         cudaStream_t st) {
+static int launch_sorted(vmc_ctx* h, const float* V, const float* invC, const double* obv_part, float* Tv,
+                         const int* stop, cudaStream_t st) {
     int rc = ensure_sorted(h, st);
     if (rc) return rc;
     vmc_ctx::PassRec rec{};
@@ -874,8 +876,9 @@ static int launch_sorted(vmc_ctx* h, const float* V, const float* invC, float* T
     a.s_cidx = h->d_cidx; a.ncst = h->ncst;
     a.G = h->d_G; a.Pst = h->Pst;
     a.V = V; a.invC = invC; a.Tv = Tv;
+    a.obv_part = obv_part; a.n_obv_part = vgrid(h, K);
     a.T = h->d_Tsort; a.base = h->d_base; a.nchunk = (int)((h->n_s + 65535) / 65536);
-    a.raw = h->d_pfraw;
+    a.raw = (float*)h->d_pfraw;
     a.stop = stop;
     const size_t smem = (size_t)h->npf * K * 4 + (size_t)(h->ncorr + 1) * 4;
     if (smem > h->smem_optin) return VMC_ERR_UNSUPPORTED;
@@ -897,22 +900,31 @@ static int launch_sorted(vmc_ctx* h, const float* V, const float* invC, float* T
     return VMC_OK;
 }
 
-// out = (S + shift I) V with K vectors, V/out in AT precision ([K][nv]).
-// obv_part holds vgrid(h, K) partial dots Obar . V unless null (then computed);
-// dot_part receives vgrid(h, K) partial dots out . V.
+// out = (S + shift I) V with K vectors, V/out in AT precision ([K][nv]), over
+// store s_pf whose sample means are Obar of kind `kind`.  obv_part holds
+// vgrid(h, K) partial dots Obar . V unless null (then computed first: the
+// sorted pass centers t_s with it); dot_part receives vgrid(h, K) partial
+// dots out . V.
 template <typename ST, typename AT, int K>
-static int apply_S_impl(vmc_ctx* h, const void* s_pf, const double* Obar, const AT* V, AT* out, double shift,
+static int apply_S_impl(vmc_ctx* h, const void* s_pf, int kind, const AT* V, AT* out, double shift,
                         const int* stop, const double* obv_part, double* dot_part, cudaStream_t st) {
     const AT* invC;
     if (sizeof(AT) == 8) invC = (const AT*)h->d_invC64;
     else invC = (const AT*)h->d_invC32;
+    const double* Obar = h->d_Obar[kind];
+    const AT* ObarA = sizeof(AT) == 8 ? (const AT*)h->d_Obar[kind] : (const AT*)h->d_Obar32[kind];
     AT* T = (AT*)h->d_T;
+    if (!obv_part) {
+        k_dot_part<double, AT, K><<<vgrid(h, K), 256, 0, st>>>(Obar, V, h->nv, h->part(0), stop); h->n_launch++;
+        VCK(cudaGetLastError());
+        obv_part = h->part(0);
+    }
     int nblk = 0;
     int rc = VMC_ERR_UNSUPPORTED;
     bool sorted = false;
     if constexpr (sizeof(AT) == 4 && sizeof(ST) == 2) {
         if (h->use_sorted && h->d_G) {
-            rc = launch_sorted<K>(h, (const float*)V, (const float*)invC, (float*)T, stop, st);
+            rc = launch_sorted<K>(h, (const float*)V, (const float*)invC, obv_part, (float*)T, stop, st);
             sorted = rc == VMC_OK;
         }
     }
@@ -928,20 +940,16 @@ static int apply_S_impl(vmc_ctx* h, const void* s_pf, const double* Obar, const 
         rc = reduce_pf<AT>(h, nblk, K, st);
         if (rc) return rc;
     }
-    if (!obv_part) {
-        k_dot_part<double, AT, K><<<vgrid(h, K), 256, 0, st>>>(Obar, V, h->nv, h->part(0), stop); h->n_launch++;
-        VCK(cudaGetLastError());
-        obv_part = h->part(0);
-    }
     FinArgs<AT, AT> f{};
     f.pb = h->pb;
     f.n_s = h->n_s;
-    f.n_pf_part = nblk;
+    f.inv_n = 1.0 / (double)h->n_s;
+    f.centered = sorted ? 1 : 0;
     f.pf_partial = (const AT*)h->d_pfpart;
-    f.pf_raw = h->d_pfraw;
-    f.corr_raw = h->d_corrraw;
+    f.pf_raw = (const AT*)h->d_pfraw;
+    f.corr_raw = (const AT*)h->d_corrraw;
     f.invC = invC;
-    f.Obar = Obar;
+    f.ObarA = ObarA;
     f.obv_part = obv_part;
     f.n_obv_part = vgrid(h, K);
     f.V = V;
@@ -988,7 +996,7 @@ static int gradient_pass(vmc_ctx* h, int kind, double* g, cudaStream_t st) {
     FinArgs<double, double> f{};
     f.pb = h->pb;
     f.n_s = h->n_s;
-    f.n_pf_part = nblk;
+    f.inv_n = 1.0 / (double)h->n_s;
     f.pf_partial = (const double*)h->d_pfpart;
     f.pf_raw = h->d_pfraw;
     f.corr_raw = h->d_corrraw;
@@ -998,6 +1006,7 @@ static int gradient_pass(vmc_ctx* h, int kind, double* g, cudaStream_t st) {
     f.E_sum = h->part(1);
     f.n_E_part = kNumPart;
     k_finalize_grad<double><<<fin_grid(h), 256, 0, st>>>(f); h->n_launch++;
+    k_cast<float><<<kNumPart, 256, 0, st>>>(h->d_Obar[kind], h->d_Obar32[kind], h->nv, 1.0); h->n_launch++;
     VCK(cudaGetLastError());
     h->obar_ok[kind] = true;
     return VMC_OK;
@@ -1074,12 +1083,11 @@ static int apply_S_dispatch(vmc_ctx* h, const double* V, double* out, double shi
     if (!store_ptr(h, kind)) return VMC_ERR_STATE;
     int rc0 = ensure_obar(h, kind, st);
     if (rc0) return rc0;
-    const double* Ob = h->d_Obar[kind];
     switch (store) {
         case VMC_STORE_FP64:
-            return apply_S_impl<double, double, K>(h, h->d_pf64, Ob, V, out, shift, nullptr, nullptr, nullptr, st);
+            return apply_S_impl<double, double, K>(h, h->d_pf64, kind, V, out, shift, nullptr, nullptr, nullptr, st);
         case VMC_STORE_FP32:
-            return apply_S_impl<float, double, K>(h, h->d_pf32, Ob, V, out, shift, nullptr, nullptr, nullptr, st);
+            return apply_S_impl<float, double, K>(h, h->d_pf32, kind, V, out, shift, nullptr, nullptr, nullptr, st);
         case VMC_STORE_BF16:
         case VMC_STORE_FP32_F32ACC: {
             const void* src = store == VMC_STORE_BF16 ? (const void*)h->d_pf16 : (const void*)h->d_pf32;
@@ -1088,9 +1096,9 @@ static int apply_S_dispatch(vmc_ctx* h, const double* V, double* out, double shi
             k_cast<float><<<kNumPart, 256, 0, st>>>(V, h->d_b32, n, 1.0); h->n_launch++;
             VCK(cudaGetLastError());
             int rc = store == VMC_STORE_BF16
-                         ? apply_S_impl<__nv_bfloat16, float, K>(h, src, Ob, h->d_b32, h->d_q32, shift, nullptr,
+                         ? apply_S_impl<__nv_bfloat16, float, K>(h, src, kind, h->d_b32, h->d_q32, shift, nullptr,
                                                                  nullptr, nullptr, st)
-                         : apply_S_impl<float, float, K>(h, src, Ob, h->d_b32, h->d_q32, shift, nullptr, nullptr,
+                         : apply_S_impl<float, float, K>(h, src, kind, h->d_b32, h->d_q32, shift, nullptr, nullptr,
                                                          nullptr, st);
             if (rc) return rc;
             // widen back to FP64
@@ -1122,9 +1130,11 @@ extern "C" int sr_apply_S(vmc_handle h, const double* V, double* out, int k, dou
 // CG on (S + shift I) x = b over store `s_pf` (ST) with vectors of type VT;
 // b, x, r, p, q are device vectors of VT.  Returns iterations in *iters.
 template <typename ST, typename VT>
-static int cg_loop(vmc_ctx* h, const void* s_pf, const double* Obar, const VT* b, VT* x, VT* r, VT* p, VT* q,
+static int cg_loop(vmc_ctx* h, const void* s_pf, int kind, const VT* b, VT* x, VT* r, VT* p, VT* q,
                    double shift, double tol, int max_iter, int* iters, cudaStream_t st) {
     const int64_t n = h->nv;
+    const double* Obar = h->d_Obar[kind];
+    const VT* ObarV = sizeof(VT) == 8 ? (const VT*)h->d_Obar[kind] : (const VT*)h->d_Obar32[kind];
     double* init_part = h->part(2);
     double* pAp_part = h->part(3);
     double* rr_part = h->part(4);
@@ -1139,10 +1149,10 @@ static int cg_loop(vmc_ctx* h, const void* s_pf, const double* Obar, const VT* b
     if (max_iter <= 0) return VMC_OK;
     while (!done) {
         for (int j = 0; j < kChunk; ++j) {
-            int rc = apply_S_impl<ST, VT, 1>(h, s_pf, Obar, p, q, shift, h->d_stop, obp_part, pAp_part, st);
+            int rc = apply_S_impl<ST, VT, 1>(h, s_pf, kind, p, q, shift, h->d_stop, obp_part, pAp_part, st);
             if (rc) return rc;
             k_cg_xr<VT><<<vg, 256, 0, st>>>(x, r, p, q, n, pAp_part, vg, h->d_scal, rr_part, h->d_stop); h->n_launch++;
-            k_cg_p<VT><<<vg, 256, 0, st>>>(r, p, n, rr_part, vg, h->d_scal, Obar, obp_part,
+            k_cg_p<VT><<<vg, 256, 0, st>>>(r, p, n, rr_part, vg, h->d_scal, ObarV, obp_part,
                                                  h->d_stop, max_iter); h->n_launch++;
             VCK(cudaGetLastError());
         }
@@ -1160,9 +1170,9 @@ static int cg_loop(vmc_ctx* h, const void* s_pf, const double* Obar, const VT* b
 // y = g - (S + shift I) x with FP64 accumulation over store s_pf (ST = double
 // or float); returns |y|^2 through the host.
 template <typename ST>
-static int residual64(vmc_ctx* h, const void* s_pf, const double* Obar, const double* g, const double* x, double* y,
+static int residual64(vmc_ctx* h, const void* s_pf, int kind, const double* g, const double* x, double* y,
                       double shift, double* rr, cudaStream_t st) {
-    int rc = apply_S_impl<ST, double, 1>(h, s_pf, Obar, x, h->d_t64, shift, nullptr, nullptr, nullptr, st);
+    int rc = apply_S_impl<ST, double, 1>(h, s_pf, kind, x, h->d_t64, shift, nullptr, nullptr, nullptr, st);
     if (rc) return rc;
     k_sub<<<kNumPart, 256, 0, st>>>(g, h->d_t64, y, h->nv, h->part(6)); h->n_launch++;
     VCK(cudaGetLastError());
@@ -1210,9 +1220,9 @@ static int inner_solve(vmc_ctx* h, int mode, const double* r, double rnorm, doub
     k_cast<float><<<kNumPart, 256, 0, st>>>(r, h->d_b32, h->nv, 1.0 / rnorm); h->n_launch++;
     VCK(cudaGetLastError());
     int rc = mode == VMC_CG_MIXED
-                 ? cg_loop<__nv_bfloat16, float>(h, h->d_pf16, h->d_Obar[2], h->d_b32, h->d_x32, h->d_r32, h->d_p32,
+                 ? cg_loop<__nv_bfloat16, float>(h, h->d_pf16, 2, h->d_b32, h->d_x32, h->d_r32, h->d_p32,
                                                 h->d_q32, shift, itol, max_iter, iters, st)
-                 : cg_loop<float, float>(h, h->d_pf32, h->d_Obar[1], h->d_b32, h->d_x32, h->d_r32, h->d_p32, h->d_q32,
+                 : cg_loop<float, float>(h, h->d_pf32, 1, h->d_b32, h->d_x32, h->d_r32, h->d_p32, h->d_q32,
                                         shift, itol, max_iter, iters, st);
     if (rc) return rc;
     VCK(cudaMemsetAsync(z, 0, sizeof(double) * h->nv, st));
@@ -1252,7 +1262,7 @@ static int fcg_mixed(vmc_ctx* h, const double* g, double shift, double tol, int 
     double zr = dot64(h, z, r, st, &rc);
     if (rc) return rc;
     for (int outer = 0; outer < 200; ++outer) {
-        rc = apply_S_impl<float, double, 1>(h, h->d_pf32, h->d_Obar[1], p, q, shift, nullptr, nullptr, nullptr, st);
+        rc = apply_S_impl<float, double, 1>(h, h->d_pf32, 1, p, q, shift, nullptr, nullptr, nullptr, st);
         if (rc) return rc;
         inf->residual_products++;
         double pq = dot64(h, p, q, st, &rc);
@@ -1282,7 +1292,7 @@ static int fcg_mixed(vmc_ctx* h, const double* g, double shift, double tol, int 
     }
     // true residual of the returned x, FP64 accumulation over the FP32 store
     double rt = 0.0;
-    rc = residual64<float>(h, h->d_pf32, h->d_Obar[1], g, x, h->d_r64, shift, &rt, st);
+    rc = residual64<float>(h, h->d_pf32, 1, g, x, h->d_r64, shift, &rt, st);
     if (rc) return rc;
     inf->residual_products++;
     inf->iterations = used;
@@ -1304,12 +1314,12 @@ extern "C" int sr_cg_solve(vmc_handle h, const double* g, double shift, double t
         rc = ensure_obar(h, 0, st);
         if (rc) return rc;
         int it = 0;
-        rc = cg_loop<double, double>(h, h->d_pf64, h->d_Obar[0], g, h->d_x64, h->d_r64, h->d_p64, h->d_q64, shift, tol,
+        rc = cg_loop<double, double>(h, h->d_pf64, 0, g, h->d_x64, h->d_r64, h->d_p64, h->d_q64, shift, tol,
                                      max_iter, &it, st);
         if (rc) return rc;
         VCK(cudaMemcpyAsync(x, h->d_x64, sizeof(double) * h->nv, cudaMemcpyDeviceToDevice, st));
         double rr = 0.0;
-        rc = residual64<double>(h, h->d_pf64, h->d_Obar[0], g, x, h->d_r64, shift, &rr, st);
+        rc = residual64<double>(h, h->d_pf64, 0, g, x, h->d_r64, shift, &rr, st);
         if (rc) return rc;
         inf.iterations = it;
         inf.residual_products = 1;

@@ -116,6 +116,14 @@ struct DevProblem {
     const int* rowbase;        // [M]: f_pq index = rowbase[p] + q (p < q)
 };
 
+// sum of n partials (stride K, column kk) by one warp; all lanes get it
+__device__ __forceinline__ double warp_sum_partials(const double* part, int n, int kk, int K) {
+    const int lane = threadIdx.x & 31;
+    double s = 0.0;
+    for (int b = lane; b < n; b += 32) s += part[b * K + kk];
+    return warp_sum(s);
+}
+
 __host__ __device__ inline int64_t pf_row_base(int M, int p) {
     // index(p, q) = p M - p (p + 1) / 2 + (q - p - 1) = base(p) + q
     return (int64_t)p * M - (int64_t)p * (p + 1) / 2 - p - 1;

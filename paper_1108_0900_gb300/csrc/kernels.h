@@ -89,7 +89,7 @@ struct CorrArgs {
     int64_t n_s;
     const uint16_t* cidxT;  // [ncorr][n_s]
     const AT* T;            // [n_s][K]
-    double* corr_raw;       // [ncp][K] sum over samples of t_s per state
+    AT* corr_raw;           // [ncp][K] sum over samples of t_s per state
     const int* stop;
 };
 
@@ -99,13 +99,14 @@ template <typename AT, typename VT>
 struct FinArgs {
     DevProblem pb;
     int64_t n_s;
-    int n_pf_part;          // CTAs of the main pass
+    double inv_n;           // 1 / n_s
+    int centered;           // the pass scattered t_s - Obar . V: skip the Obar term
     const AT* pf_partial;
-    const double* pf_raw;   // [npf][K] sum over CTAs of pf_partial
-    const double* corr_raw; // [ncp][K] correlator sums
+    const AT* pf_raw;       // [npf][K] pairing-block sums
+    const AT* corr_raw;     // [ncp][K] correlator sums
+    const AT* ObarA;        // [nv] Obar in AT (S mode, uncentered)
     const AT* invC;
-    const double* Obar;     // [nv] (S mode)
-    const double* obv_part; // [nblk][K] partial dots Obar . V (S mode)
+    const double* obv_part; // [nblk][K] partial dots Obar . V (S mode, uncentered)
     int n_obv_part;
     const VT* V;            // [K][nv]
     double shift;
@@ -130,7 +131,7 @@ __global__ void k_build_T_grad(const double* E, int64_t n_s, double* T, double* 
 template <typename TA, typename TB, int K>
 __global__ void __launch_bounds__(256) k_dot_part(const TA* x, const TB* y, int64_t n, double* part, const int* stop);
 template <typename AT>
-__global__ void __launch_bounds__(256) k_reduce_pf(const AT* part, int nblk, int npfK, double* raw);
+__global__ void __launch_bounds__(256) k_reduce_pf(const AT* part, int nblk, int npfK, AT* raw);
 __global__ void k_transpose_cidx(const uint16_t* cidx, int ncst, int ncorr, int64_t n_s, uint16_t* cidxT);
 template <typename VT> __global__ void k_cast(const double* src, VT* dst, int64_t n, double scale);
 
@@ -146,7 +147,7 @@ __global__ void __launch_bounds__(256) k_cg_xr(VT* x, VT* r, const VT* p, const 
                                                double* rr_part, int* stop);
 template <typename VT>
 __global__ void __launch_bounds__(256) k_cg_p(const VT* r, VT* p, int64_t n, const double* rr_part, int npart,
-                                              double* scal, const double* Obar, double* obp_part, int* stop,
+                                              double* scal, const VT* Obar, double* obp_part, int* stop,
                                               int max_iter);
 __global__ void k_sub(const double* a, const double* b, double* y, int64_t n, double* part);
 __global__ void k_axpby(double a, const double* x, double b, double* y, int64_t n);
@@ -195,11 +196,13 @@ struct SortedArgs {
     int64_t Pst;
     const float* V;         // [K][nv]
     const float* invC;
-    float* Tv;              // [n_s][K] per-sample dots
+    const double* obv_part; // [n_obv_part][K] partial dots Obar . V (centering)
+    int n_obv_part;
+    float* Tv;              // [n_s][K] centered per-sample dots O_s . V - Obar . V
     const uint32_t* T;      // parameter-major (s_local << 16) | bf16
     const uint32_t* base;   // [nchunk][npf + 1] run offsets
     int nchunk;
-    double* raw;            // [npf][K] scatter result
+    float* raw;             // [npf][K] scatter result
     const int* stop;
 };
 

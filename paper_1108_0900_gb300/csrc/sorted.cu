@@ -123,7 +123,10 @@ __global__ void __launch_bounds__(512) k_fill_T(const uint32_t* G, int64_t Pst, 
     }
 }
 
-// gather: t_s = sum_c V[k_c]/C[k_c] + sum_e W_e v[pq(e)], warp per sample.
+// gather: t_s = sum_c V[k_c]/C[k_c] + sum_e W_e v[pq(e)] - Obar . V, warp per
+// sample.  Centering t_s makes the scatter produce the covariance
+// (1/n) sum_s (t_s - Obar . V) O_s = S V directly, with no cancellation
+// between <O (O . V)> and Obar (Obar . V).
 // U = ceil(Pst / 128): every lane issues all of its U 16-byte loads of the
 // sample's row before the correlator lookups and before consuming any, so a
 // whole row (6 KB at 56 electrons) is in flight per warp.
@@ -138,6 +141,14 @@ __global__ void __launch_bounds__(256) k_gather_G(SortedArgs a) {
 #pragma unroll
         for (int kk = 0; kk < K; ++kk) vpf[i * K + kk] = a.V[kk * pb.nv + pb.ncp + i];
     for (int i = threadIdx.x; i <= pb.ncorr; i += blockDim.x) coff[i] = (int)pb.corr_off[i];
+    __shared__ float obv[K];
+    if (threadIdx.x < 32) {
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) {
+            const double c = warp_sum_partials(a.obv_part, a.n_obv_part, kk, K);
+            if (threadIdx.x == 0) obv[kk] = (float)c;
+        }
+    }
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int n4 = (int)(a.Pst >> 2);
@@ -177,7 +188,7 @@ __global__ void __launch_bounds__(256) k_gather_G(SortedArgs a) {
         for (int kk = 0; kk < K; ++kk) t[kk] = warp_sum(t[kk] + w[kk]);
         if (lane == 0)
 #pragma unroll
-            for (int kk = 0; kk < K; ++kk) a.Tv[s * K + kk] = t[kk];
+            for (int kk = 0; kk < K; ++kk) a.Tv[s * K + kk] = t[kk] - obv[kk];
     }
 }
 
@@ -235,7 +246,7 @@ __global__ void __launch_bounds__(256) k_scatter_T(SortedArgs a) {
 #pragma unroll
     for (int kk = 0; kk < K; ++kk) {
         const float v = warp_sum(acc[kk] + acc2[kk]);
-        if (lane == 0) a.raw[(size_t)pq * K + kk] = (double)v;
+        if (lane == 0) a.raw[(size_t)pq * K + kk] = v;
     }
 }
 

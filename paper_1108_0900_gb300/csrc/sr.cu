@@ -158,7 +158,7 @@ __global__ void __cluster_dims__(kCorrCluster, 1, 1) __launch_bounds__(256) k_co
         double acc = 0.0;
 #pragma unroll
         for (int q = 0; q < kCorrCluster; ++q) acc += (double)cluster.map_shared_rank(h, q)[i];
-        a.corr_raw[off * K + i] = acc;
+        a.corr_raw[off * K + i] = (AT)acc;
     }
     cluster.sync();   // keep this CTA's histogram alive until the cluster has read it
 }
@@ -184,18 +184,10 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[K], double* out) 
     }
 }
 
-// sum of n partials (stride K, column kk) by one warp; all lanes get it
-__device__ __forceinline__ double warp_sum_partials(const double* part, int n, int kk, int K) {
-    const int lane = threadIdx.x & 31;
-    double s = 0.0;
-    for (int b = lane; b < n; b += 32) s += part[b * K + kk];
-    return warp_sum(s);
-}
-
 // Reduce the per-CTA pairing-block images: raw[pq][kk] = sum_b part[b][pq][kk].
 // Block = 32 parameter slots x 8 CTA slices; a warp covers one slice.
 template <typename AT>
-__global__ void __launch_bounds__(256) k_reduce_pf(const AT* part, int nblk, int npfK, double* raw) {
+__global__ void __launch_bounds__(256) k_reduce_pf(const AT* part, int nblk, int npfK, AT* raw) {
     __shared__ double red[8][33];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int i = blockIdx.x * 32 + lane;
@@ -208,21 +200,16 @@ __global__ void __launch_bounds__(256) k_reduce_pf(const AT* part, int nblk, int
         double t = 0.0;
 #pragma unroll
         for (int j = 0; j < 8; ++j) t += red[j][lane];
-        if (i < npfK) raw[i] = t;
+        if (i < npfK) raw[i] = (AT)t;
     }
 }
 
-// raw pass result for parameter k and vector kk, divided by n_s
+// raw pass result for parameter k and vector kk, divided by n_s (in AT)
 template <typename AT, typename VT, int K>
-__device__ __forceinline__ double fin_raw(const FinArgs<AT, VT>& a, int64_t k, int kk) {
+__device__ __forceinline__ AT fin_raw(const FinArgs<AT, VT>& a, int64_t k, int kk) {
     const DevProblem& pb = a.pb;
-    double raw = 0.0;
-    if (k < pb.ncp) {
-        raw = a.corr_raw[k * K + kk] * (double)a.invC[k];
-    } else {
-        raw = a.pf_raw[(k - pb.ncp) * K + kk];
-    }
-    return raw / (double)a.n_s;
+    const AT raw = k < pb.ncp ? a.corr_raw[k * K + kk] * a.invC[k] : a.pf_raw[(k - pb.ncp) * K + kk];
+    return raw * (AT)a.inv_n;
 }
 
 // Vector kernels cover kVecUnroll elements per thread, strided by the grid,
@@ -230,7 +217,9 @@ __device__ __forceinline__ double fin_raw(const FinArgs<AT, VT>& a, int64_t k, i
 // the 270k-parameter vectors is one round trip to memory per thread.
 constexpr int kVecUnroll = 4;
 
-// out = raw - Obar (Obar . V) + shift V; dot_part = partial out . V
+// out = raw - Obar (Obar . V) + shift V; dot_part = partial out . V.  A
+// centered pass (t_s - Obar . V scattered) already holds the covariance and
+// skips the Obar term.  Element arithmetic in AT, partial dots in FP64.
 template <typename AT, typename VT, int K>
 __global__ void __launch_bounds__(256) k_finalize_S(FinArgs<AT, VT> a) {
     if (a.stop && *a.stop) return;
@@ -238,45 +227,54 @@ __global__ void __launch_bounds__(256) k_finalize_S(FinArgs<AT, VT> a) {
     if (threadIdx.x < 32) {
 #pragma unroll
         for (int kk = 0; kk < K; ++kk) {
-            double s = warp_sum_partials(a.obv_part, a.n_obv_part, kk, K);
+            double s = a.centered ? 0.0 : warp_sum_partials(a.obv_part, a.n_obv_part, kk, K);
             if (threadIdx.x == 0) obv[kk] = s;
         }
     }
     __syncthreads();
+    AT ov[K];
+#pragma unroll
+    for (int kk = 0; kk < K; ++kk) ov[kk] = (AT)obv[kk];
+    const AT shift = (AT)a.shift;
     const int64_t nv = a.pb.nv;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     double dl[K];
 #pragma unroll
     for (int kk = 0; kk < K; ++kk) dl[kk] = 0.0;
     for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < nv; i0 += kVecUnroll * stride) {
-        double ob[kVecUnroll], v[kVecUnroll][K], raw[kVecUnroll][K];
+        AT ob[kVecUnroll], v[kVecUnroll][K], raw[kVecUnroll][K];
 #pragma unroll
         for (int u = 0; u < kVecUnroll; ++u) {
             const int64_t k = i0 + u * stride;
-            ob[u] = 0.0;
+            ob[u] = AT(0);
 #pragma unroll
-            for (int kk = 0; kk < K; ++kk) v[u][kk] = raw[u][kk] = 0.0;
+            for (int kk = 0; kk < K; ++kk) v[u][kk] = raw[u][kk] = AT(0);
             if (k < nv) {
-                ob[u] = a.Obar[k];
+                if (!a.centered) ob[u] = a.ObarA[k];
 #pragma unroll
                 for (int kk = 0; kk < K; ++kk) {
-                    v[u][kk] = (double)a.V[kk * nv + k];
+                    v[u][kk] = (AT)a.V[kk * nv + k];
                     raw[u][kk] = fin_raw<AT, VT, K>(a, k, kk);
                 }
             }
         }
+        AT part[K];
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) part[kk] = AT(0);
 #pragma unroll
         for (int u = 0; u < kVecUnroll; ++u) {
             const int64_t k = i0 + u * stride;
             if (k < nv) {
 #pragma unroll
                 for (int kk = 0; kk < K; ++kk) {
-                    const double o = raw[u][kk] - ob[u] * obv[kk] + a.shift * v[u][kk];
+                    const AT o = raw[u][kk] - ob[u] * ov[kk] + shift * v[u][kk];
                     a.out[kk * nv + k] = (VT)o;
-                    dl[kk] += o * v[u][kk];
+                    part[kk] += o * v[u][kk];
                 }
             }
         }
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) dl[kk] += (double)part[kk];
     }
     if (a.dot_part) block_reduce_store<K>(dl, a.dot_part);
 }
@@ -287,7 +285,7 @@ __global__ void __launch_bounds__(256) k_finalize_grad(FinArgs<AT, double> a) {
     __shared__ double em;
     if (threadIdx.x < 32) {
         double s = warp_sum_partials(a.E_sum, a.n_E_part, 0, 1);
-        if (threadIdx.x == 0) em = s / (double)a.n_s;
+        if (threadIdx.x == 0) em = s * a.inv_n;
     }
     __syncthreads();
     const int64_t nv = a.pb.nv;
@@ -410,6 +408,7 @@ __global__ void k_cg_start(const double* part, int npart, double* scal, double t
 }
 
 // alpha = rr / (p . Ap); x += alpha p; r -= alpha Ap; partial r . r
+// (element arithmetic in VT, partial sums in FP64)
 template <typename VT>
 __global__ void __launch_bounds__(256) k_cg_xr(VT* x, VT* r, const VT* p, const VT* Ap, int64_t n,
                                                const double* pAp_part, int npart, double* scal,
@@ -424,30 +423,33 @@ __global__ void __launch_bounds__(256) k_cg_xr(VT* x, VT* r, const VT* p, const 
         }
     }
     __syncthreads();
+    const VT al = (VT)alpha;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     double loc[1] = {0.0};
     for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += kVecUnroll * stride) {
-        double xv[kVecUnroll], rv[kVecUnroll], pv[kVecUnroll], qv[kVecUnroll];
+        VT xv[kVecUnroll], rv[kVecUnroll], pv[kVecUnroll], qv[kVecUnroll];
 #pragma unroll
         for (int u = 0; u < kVecUnroll; ++u) {
             const int64_t i = i0 + u * stride;
             const bool in = i < n;
-            xv[u] = in ? (double)x[i] : 0.0;
-            rv[u] = in ? (double)r[i] : 0.0;
-            pv[u] = in ? (double)p[i] : 0.0;
-            qv[u] = in ? (double)Ap[i] : 0.0;
+            xv[u] = in ? x[i] : VT(0);
+            rv[u] = in ? r[i] : VT(0);
+            pv[u] = in ? p[i] : VT(0);
+            qv[u] = in ? Ap[i] : VT(0);
         }
+        VT part = VT(0);
 #pragma unroll
         for (int u = 0; u < kVecUnroll; ++u) {
             const int64_t i = i0 + u * stride;
             if (i < n) {
-                const double xi = xv[u] + alpha * pv[u];
-                const double ri = rv[u] - alpha * qv[u];
-                x[i] = (VT)xi;
-                r[i] = (VT)ri;
-                loc[0] += ri * ri;
+                const VT xi = xv[u] + al * pv[u];
+                const VT ri = rv[u] - al * qv[u];
+                x[i] = xi;
+                r[i] = ri;
+                part += ri * ri;
             }
         }
+        loc[0] += (double)part;
     }
     block_reduce_store<1>(loc, rr_part);
     if (blockIdx.x == 0 && threadIdx.x == 0) scal[CG_RRP] = scal[CG_RR];
@@ -456,7 +458,7 @@ __global__ void __launch_bounds__(256) k_cg_xr(VT* x, VT* r, const VT* p, const 
 // beta = rr_new / rr; p = r + beta p; partial Obar . p for the next product
 template <typename VT>
 __global__ void __launch_bounds__(256) k_cg_p(const VT* r, VT* p, int64_t n, const double* rr_part, int npart,
-                                              double* scal, const double* Obar, double* obp_part, int* stop,
+                                              double* scal, const VT* Obar, double* obp_part, int* stop,
                                               int max_iter) {
     if (*stop) return;
     __shared__ double beta, rrn;
@@ -468,27 +470,30 @@ __global__ void __launch_bounds__(256) k_cg_p(const VT* r, VT* p, int64_t n, con
         }
     }
     __syncthreads();
+    const VT be = (VT)beta;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     double loc[1] = {0.0};
     for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += kVecUnroll * stride) {
-        double rv[kVecUnroll], pv[kVecUnroll], ov[kVecUnroll];
+        VT rv[kVecUnroll], pv[kVecUnroll], ov[kVecUnroll];
 #pragma unroll
         for (int u = 0; u < kVecUnroll; ++u) {
             const int64_t i = i0 + u * stride;
             const bool in = i < n;
-            rv[u] = in ? (double)r[i] : 0.0;
-            pv[u] = in ? (double)p[i] : 0.0;
-            ov[u] = in ? Obar[i] : 0.0;
+            rv[u] = in ? r[i] : VT(0);
+            pv[u] = in ? p[i] : VT(0);
+            ov[u] = in ? Obar[i] : VT(0);
         }
+        VT part = VT(0);
 #pragma unroll
         for (int u = 0; u < kVecUnroll; ++u) {
             const int64_t i = i0 + u * stride;
             if (i < n) {
-                const double pi = rv[u] + beta * pv[u];
-                p[i] = (VT)pi;
-                loc[0] += ov[u] * pi;
+                const VT pi = rv[u] + be * pv[u];
+                p[i] = pi;
+                part += ov[u] * pi;
             }
         }
+        loc[0] += (double)part;
     }
     block_reduce_store<1>(loc, obp_part);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -555,7 +560,7 @@ template __global__ void k_finalize_S<float, float, 2>(FinArgs<float, float>);
 template __global__ void k_finalize_S<float, float, 4>(FinArgs<float, float>);
 template __global__ void k_finalize_grad<double>(FinArgs<double, double>);
 template __global__ void k_reduce_pf<double>(const double*, int, int, double*);
-template __global__ void k_reduce_pf<float>(const float*, int, int, double*);
+template __global__ void k_reduce_pf<float>(const float*, int, int, float*);
 template __global__ void k_dot_part<double, double, 1>(const double*, const double*, int64_t, double*, const int*);
 template __global__ void k_dot_part<double, double, 2>(const double*, const double*, int64_t, double*, const int*);
 template __global__ void k_dot_part<double, double, 4>(const double*, const double*, int64_t, double*, const int*);
@@ -572,7 +577,7 @@ template __global__ void k_cg_xr<float>(float*, float*, const float*, const floa
                                         double*, double*, int*);
 template __global__ void k_cg_p<double>(const double*, double*, int64_t, const double*, int, double*, const double*,
                                         double*, int*, int);
-template __global__ void k_cg_p<float>(const float*, float*, int64_t, const double*, int, double*, const double*,
+template __global__ void k_cg_p<float>(const float*, float*, int64_t, const double*, int, double*, const float*,
                                        double*, int*, int);
 template __global__ void k_axpy_to64<float>(double*, const float*, double, int64_t);
 template __global__ void k_axpy_to64<double>(double*, const double*, double, int64_t);
