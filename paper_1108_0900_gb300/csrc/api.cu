@@ -48,6 +48,7 @@ struct vmc_ctx {
     bool use_stream = true;     // TMA-staged pass for FP32-accumulation products
     bool stream_cached = false;  // register-cached variant for BF16, one vector (slower: 16 warps)
     bool use_sorted = true;      // sorted two-pass product for the BF16 store
+    int last_gather_grid = 0;    // CTAs (tt partials) of the last sorted gather
     bool sorted_ok = false;      // G / T built for the current samples
     int sort_nblk = 0, sort_nchunk = 0;
     bool obar_ok[3] = {false, false, false};  // per store: FP64, FP32, BF16
@@ -91,6 +92,7 @@ struct vmc_ctx {
     double* d_part = nullptr;   // 8 slots x kNumPart x kMaxK
     double* d_pfraw = nullptr;  // [npf][K] reduced pairing-block sums (FP64 or FP32 per pass)
     uint32_t *d_G = nullptr, *d_Tsort = nullptr, *d_counts = nullptr, *d_total = nullptr, *d_base = nullptr;
+    uint32_t *d_Tc = nullptr, *d_ccount = nullptr, *d_cbase = nullptr;   // correlator runs
     double* d_scal = nullptr;
     int* d_stop = nullptr;
     // CG vectors
@@ -338,6 +340,9 @@ extern "C" int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, co
         ACK(h->alloc(&h->d_counts, (size_t)h->sort_nblk * h->npf));
         ACK(h->alloc(&h->d_total, (size_t)h->npf));
         ACK(h->alloc(&h->d_base, (size_t)h->sort_nchunk * (h->npf + 1)));
+        ACK(h->alloc(&h->d_Tc, (size_t)h->ncap * std::max(h->ncorr, 1)));
+        ACK(h->alloc(&h->d_ccount, (size_t)std::max<int64_t>(h->ncp, 1)));
+        ACK(h->alloc(&h->d_cbase, (size_t)h->ncp + 1));
     }
     for (int k = 0; k < 3; ++k) ACK(h->alloc(&h->d_Obar[k], h->nv));
     for (int k = 0; k < 3; ++k) ACK(h->alloc(&h->d_Obar32[k], h->nv));
@@ -832,6 +837,15 @@ static int ensure_sorted(vmc_ctx* h, cudaStream_t st) {
                                                   h->d_Tsort); h->n_launch++;
         VCK(cudaGetLastError());
     }
+    if (h->ncorr > 0) {
+        const size_t csm = (size_t)h->maxd * 4;
+        VCK(cudaFuncSetAttribute(k_count_C, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
+        VCK(cudaFuncSetAttribute(k_fill_C, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
+        k_count_C<<<h->ncorr, 512, csm, st>>>(h->pb, h->n_s, h->d_cidxT, h->d_ccount); h->n_launch++;
+        k_scan_params<<<1, 1024, 0, st>>>(h->d_ccount, (int)h->ncp, 0u, h->d_cbase); h->n_launch++;
+        k_fill_C<<<h->ncorr, 512, csm, st>>>(h->pb, h->n_s, h->d_cidxT, h->d_cbase, h->d_Tc); h->n_launch++;
+        VCK(cudaGetLastError());
+    }
     h->sorted_ok = true;
     return VMC_OK;
 }
@@ -855,11 +869,23 @@ static GatherKern gather_kernel(int u) {
     }
 }
 
+// the sorted product applies: BF16 store with its sorted copies, the gather's
+// table and the run builders' counters within shared memory, rows of at most
+// 2048 elements
+template <int K>
+static bool sorted_usable(const vmc_ctx* h) {
+    if (!h->use_sorted || !h->d_G) return false;
+    if ((size_t)h->maxd * 4 > h->smem_optin) return false;                                  // run counters
+    if ((size_t)h->npf * K * 4 + (size_t)(h->ncorr + 1) * 4 > h->smem_optin) return false;   // gather table
+    return gather_kernel<K>((int)((h->Pst / 4 + 31) / 32)) != nullptr;
+}
+
 // gather + parameter-major scatter for the BF16 store; the centered t_s go to
-// Tv and the pairing sums to d_pfraw (FP32)
+// Tv, the pairing sums to d_pfraw and the correlator sums to d_corrraw (FP32)
 template <int K>
 static int launch_sorted(vmc_ctx* h, const float* V, const float* invC, const double* obv_part, float* Tv,
-                         const int* stop, cudaStream_t st) {
+                         const int* stop, cudaStream_t st, double* tt_part = nullptr) {
+    if (!sorted_usable<K>(h)) return VMC_ERR_UNSUPPORTED;
     int rc = ensure_sorted(h, st);
     if (rc) return rc;
     vmc_ctx::PassRec rec{};
@@ -879,19 +905,21 @@ static int launch_sorted(vmc_ctx* h, const float* V, const float* invC, const do
     a.obv_part = obv_part; a.n_obv_part = vgrid(h, K);
     a.T = h->d_Tsort; a.base = h->d_base; a.nchunk = (int)((h->n_s + 65535) / 65536);
     a.raw = (float*)h->d_pfraw;
+    a.Tc = h->d_Tc; a.cbase = h->d_cbase; a.craw = (float*)h->d_corrraw;
+    a.tt_part = tt_part;
     a.stop = stop;
     const size_t smem = (size_t)h->npf * K * 4 + (size_t)(h->ncorr + 1) * 4;
-    if (smem > h->smem_optin) return VMC_ERR_UNSUPPORTED;
     auto gk = gather_kernel<K>((int)((h->Pst / 4 + 31) / 32));
-    if (!gk) return VMC_ERR_UNSUPPORTED;
     VCK(cudaFuncSetAttribute(gk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     VCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gk, 256, smem));
     int grid = h->nsm * std::max(1, per_sm);
     int64_t need = (h->n_s + 7) / 8;
     if (need < grid) grid = (int)std::max<int64_t>(1, need);
+    grid = std::min(grid, kNumPart * kMaxK);   // one partial slot of tt sums
     gk<<<grid, 256, smem, st>>>(a); h->n_launch++;
-    k_scatter_T<K><<<(h->npf + 7) / 8, 256, 0, st>>>(a); h->n_launch++;
+    h->last_gather_grid = grid;
+    k_scatter_T<K><<<(int)((h->ncp + 255) / 256) + (h->npf + 7) / 8, 256, 0, st>>>(a); h->n_launch++;
     VCK(cudaGetLastError());
     if (h->prof) {
         VCK(cudaEventRecord(rec.b, st));
@@ -934,9 +962,9 @@ static int apply_S_impl(vmc_ctx* h, const void* s_pf, int kind, const AT* V, AT*
     }
     if (rc == VMC_ERR_UNSUPPORTED) rc = launch_main<ST, AT, K, true>(h, s_pf, V, invC, T, stop, st, &nblk);
     if (rc) return rc;
-    rc = launch_corr<AT, K>(h, T, stop, st);
-    if (rc) return rc;
-    if (!sorted) {
+    if (!sorted) {   // the sorted pass scatters the correlators itself
+        rc = launch_corr<AT, K>(h, T, stop, st);
+        if (rc) return rc;
         rc = reduce_pf<AT>(h, nblk, K, st);
         if (rc) return rc;
     }
@@ -1135,25 +1163,50 @@ static int cg_loop(vmc_ctx* h, const void* s_pf, int kind, const VT* b, VT* x, V
     const int64_t n = h->nv;
     const double* Obar = h->d_Obar[kind];
     const VT* ObarV = sizeof(VT) == 8 ? (const VT*)h->d_Obar[kind] : (const VT*)h->d_Obar32[kind];
-    double* init_part = h->part(2);
+    double* pp_part = h->part(2);    // |p|^2 partials (the first from k_cg_init)
     double* pAp_part = h->part(3);
     double* rr_part = h->part(4);
     double* obp_part = h->part(5);
+    double* tt_part = h->part(6);
     const int vg = vgrid(h, 1);
-    k_cg_init<VT><<<vg, 256, 0, st>>>(b, x, r, p, n, init_part); h->n_launch++;
-    k_cg_start<<<1, 32, 0, st>>>(init_part, vg, h->d_scal, tol, h->d_stop); h->n_launch++;
+    k_cg_init<VT><<<vg, 256, 0, st>>>(b, x, r, p, n, pp_part); h->n_launch++;
+    k_cg_start<<<1, 32, 0, st>>>(pp_part, vg, h->d_scal, tol, h->d_stop); h->n_launch++;
     k_dot_part<double, VT, 1><<<vg, 256, 0, st>>>(Obar, p, n, obp_part, h->d_stop); h->n_launch++;
     VCK(cudaGetLastError());
     int done = 0;
     *iters = 0;
     if (max_iter <= 0) return VMC_OK;
+    // centered sorted product with the fused update: gather, scatter, x/r, p
+    bool fused = false;
+    if constexpr (sizeof(ST) == 2 && sizeof(VT) == 4) fused = sorted_usable<1>(h);
     while (!done) {
         for (int j = 0; j < kChunk; ++j) {
-            int rc = apply_S_impl<ST, VT, 1>(h, s_pf, kind, p, q, shift, h->d_stop, obp_part, pAp_part, st);
-            if (rc) return rc;
-            k_cg_xr<VT><<<vg, 256, 0, st>>>(x, r, p, q, n, pAp_part, vg, h->d_scal, rr_part, h->d_stop); h->n_launch++;
-            k_cg_p<VT><<<vg, 256, 0, st>>>(r, p, n, rr_part, vg, h->d_scal, ObarV, obp_part,
-                                                 h->d_stop, max_iter); h->n_launch++;
+            if (fused) {
+                if constexpr (sizeof(ST) == 2 && sizeof(VT) == 4) {
+                    int rc = launch_sorted<1>(h, p, h->d_invC32, obp_part, (float*)h->d_T, h->d_stop, st, tt_part);
+                    if (rc) return rc;
+                    CgFusedArgs<float> f{};
+                    f.x = x; f.r = r; f.p = p;
+                    f.pf_raw = (const float*)h->d_pfraw;
+                    f.corr_raw = (const float*)h->d_corrraw;
+                    f.invC = h->d_invC32;
+                    f.n = n; f.ncp = h->ncp;
+                    f.inv_n = 1.0 / (double)h->n_s;
+                    f.shift = shift;
+                    f.tt_part = tt_part; f.ntt = h->last_gather_grid;
+                    f.pp_part = pp_part; f.npp = vg;
+                    f.scal = h->d_scal;
+                    f.rr_part = rr_part;
+                    f.stop = h->d_stop;
+                    k_cg_fxr<float><<<vg, 256, 0, st>>>(f); h->n_launch++;
+                }
+            } else {
+                int rc = apply_S_impl<ST, VT, 1>(h, s_pf, kind, p, q, shift, h->d_stop, obp_part, pAp_part, st);
+                if (rc) return rc;
+                k_cg_xr<VT><<<vg, 256, 0, st>>>(x, r, p, q, n, pAp_part, vg, h->d_scal, rr_part, h->d_stop); h->n_launch++;
+            }
+            k_cg_p<VT><<<vg, 256, 0, st>>>(r, p, n, rr_part, vg, h->d_scal, ObarV, obp_part, pp_part,
+                                           h->d_stop, max_iter); h->n_launch++;
             VCK(cudaGetLastError());
         }
         VCK(cudaMemcpyAsync(h->h_pinned, h->d_scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));

@@ -116,11 +116,22 @@ struct DevProblem {
     const int* rowbase;        // [M]: f_pq index = rowbase[p] + q (p < q)
 };
 
-// sum of n partials (stride K, column kk) by one warp; all lanes get it
+// sum of n partials (stride K, column kk) by one warp; all lanes get it.
+// Eight loads per lane are issued before they are added (fixed order), so up
+// to 256 partials cost one round trip to L2.
 __device__ __forceinline__ double warp_sum_partials(const double* part, int n, int kk, int K) {
     const int lane = threadIdx.x & 31;
     double s = 0.0;
-    for (int b = lane; b < n; b += 32) s += part[b * K + kk];
+    for (int b0 = 0; b0 < n; b0 += 256) {
+        double v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int b = b0 + lane + 32 * j;
+            v[j] = b < n ? part[b * K + kk] : 0.0;
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) s += v[j];
+    }
     return warp_sum(s);
 }
 

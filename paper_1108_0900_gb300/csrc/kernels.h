@@ -137,6 +137,26 @@ template <typename VT> __global__ void k_cast(const double* src, VT* dst, int64_
 
 // conjugate-gradient scalars (FP64, device): rr, |b|^2, tol^2 |b|^2,
 // iterations, rr of the previous step
+// fused CG update after a centered product (see k_cg_fxr)
+template <typename VT>
+struct CgFusedArgs {
+    VT* x;
+    VT* r;
+    const VT* p;
+    const VT* pf_raw;       // [npf] pairing sums of the centered pass
+    const VT* corr_raw;     // [ncp] correlator sums
+    const VT* invC;         // [ncp]
+    int64_t n, ncp;
+    double inv_n, shift;
+    const double* tt_part;  // partial sums of centered t_s^2 (gather)
+    int ntt;
+    const double* pp_part;  // partial sums of |p|^2
+    int npp;
+    double* scal;
+    double* rr_part;        // out: partial r . r
+    const int* stop;
+};
+
 enum { CG_RR = 0, CG_BB = 1, CG_TOL2 = 2, CG_IT = 3, CG_RRP = 4 };
 template <typename VT>
 __global__ void __launch_bounds__(256) k_cg_init(const VT* b, VT* x, VT* r, VT* p, int64_t n, double* part);
@@ -147,8 +167,9 @@ __global__ void __launch_bounds__(256) k_cg_xr(VT* x, VT* r, const VT* p, const 
                                                double* rr_part, int* stop);
 template <typename VT>
 __global__ void __launch_bounds__(256) k_cg_p(const VT* r, VT* p, int64_t n, const double* rr_part, int npart,
-                                              double* scal, const VT* Obar, double* obp_part, int* stop,
-                                              int max_iter);
+                                              double* scal, const VT* Obar, double* obp_part, double* pp_part,
+                                              int* stop, int max_iter);
+template <typename VT> __global__ void __launch_bounds__(256) k_cg_fxr(CgFusedArgs<VT> a);
 __global__ void k_sub(const double* a, const double* b, double* y, int64_t n, double* part);
 __global__ void k_axpby(double a, const double* x, double b, double* y, int64_t n);
 template <typename VT> __global__ void k_axpy_to64(double* x, const VT* d, double scale, int64_t n);
@@ -203,6 +224,10 @@ struct SortedArgs {
     const uint32_t* base;   // [nchunk][npf + 1] run offsets
     int nchunk;
     float* raw;             // [npf][K] scatter result
+    const uint32_t* Tc;     // correlator runs: sample indices grouped by state
+    const uint32_t* cbase;  // [ncp + 1] run offsets
+    float* craw;            // [ncp][K] correlator sums (without the 1/C factor)
+    double* tt_part;        // [gridDim] partial sums of centered t_s^2 (K = 1; may be null)
     const int* stop;
 };
 
@@ -217,5 +242,9 @@ __global__ void __launch_bounds__(512) k_fill_T(const uint32_t* G, int64_t Pst, 
                                                 uint32_t* T);
 template <int K, int U> __global__ void __launch_bounds__(256) k_gather_G(SortedArgs a);
 template <int K> __global__ void __launch_bounds__(256) k_scatter_T(SortedArgs a);
+__global__ void __launch_bounds__(512) k_count_C(DevProblem pb, int64_t n_s, const uint16_t* cidxT,
+                                                 uint32_t* ccount);
+__global__ void __launch_bounds__(512) k_fill_C(DevProblem pb, int64_t n_s, const uint16_t* cidxT,
+                                                const uint32_t* cbase, uint32_t* Tc);
 
 }  // namespace vmc

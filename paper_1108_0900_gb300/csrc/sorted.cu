@@ -123,6 +123,35 @@ __global__ void __launch_bounds__(512) k_fill_T(const uint32_t* G, int64_t Pst, 
     }
 }
 
+// Correlator runs: the samples of each correlator state, grouped by state
+// (global parameter index off_c + state), built once per set of samples from
+// the transposed state array.  Block per correlator, shared-memory counters.
+__global__ void __launch_bounds__(512) k_count_C(DevProblem pb, int64_t n_s, const uint16_t* cidxT,
+                                                 uint32_t* ccount) {
+    extern __shared__ uint32_t hist[];
+    const int c = blockIdx.x;
+    const int64_t off = pb.corr_off[c];
+    const int d = (int)(pb.corr_off[c + 1] - off);
+    for (int i = threadIdx.x; i < d; i += blockDim.x) hist[i] = 0u;
+    __syncthreads();
+    const uint16_t* st = cidxT + (int64_t)c * n_s;
+    for (int64_t s = threadIdx.x; s < n_s; s += blockDim.x) atomicAdd(&hist[st[s]], 1u);
+    __syncthreads();
+    for (int i = threadIdx.x; i < d; i += blockDim.x) ccount[off + i] = hist[i];
+}
+
+__global__ void __launch_bounds__(512) k_fill_C(DevProblem pb, int64_t n_s, const uint16_t* cidxT,
+                                                const uint32_t* cbase, uint32_t* Tc) {
+    extern __shared__ uint32_t cur[];
+    const int c = blockIdx.x;
+    const int64_t off = pb.corr_off[c];
+    const int d = (int)(pb.corr_off[c + 1] - off);
+    for (int i = threadIdx.x; i < d; i += blockDim.x) cur[i] = cbase[off + i];
+    __syncthreads();
+    const uint16_t* st = cidxT + (int64_t)c * n_s;
+    for (int64_t s = threadIdx.x; s < n_s; s += blockDim.x) Tc[atomicAdd(&cur[st[s]], 1u)] = (uint32_t)s;
+}
+
 // gather: t_s = sum_c V[k_c]/C[k_c] + sum_e W_e v[pq(e)] - Obar . V, warp per
 // sample.  Centering t_s makes the scatter produce the covariance
 // (1/n) sum_s (t_s - Obar . V) O_s = S V directly, with no cancellation
@@ -152,6 +181,7 @@ __global__ void __launch_bounds__(256) k_gather_G(SortedArgs a) {
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int n4 = (int)(a.Pst >> 2);
+    double tt = 0.0;   // lane 0: sum of the warp's centered t_s^2
     for (int64_t s = (int64_t)blockIdx.x * nw + wid; s < a.n_s; s += (int64_t)gridDim.x * nw) {
         const uint4* g4 = (const uint4*)(a.G + s * a.Pst);
         uint4 g[U];
@@ -186,9 +216,22 @@ __global__ void __launch_bounds__(256) k_gather_G(SortedArgs a) {
         }
 #pragma unroll
         for (int kk = 0; kk < K; ++kk) t[kk] = warp_sum(t[kk] + w[kk]);
-        if (lane == 0)
+        if (lane == 0) {
 #pragma unroll
             for (int kk = 0; kk < K; ++kk) a.Tv[s * K + kk] = t[kk] - obv[kk];
+            const double c = (double)(t[0] - obv[0]);
+            tt += c * c;
+        }
+    }
+    if (K == 1 && a.tt_part) {   // p . S p of a centered product, for CG
+        __shared__ double red[32];
+        if (lane == 0) red[wid] = tt;
+        __syncthreads();
+        if (wid == 0) {
+            double v = lane < nw ? red[lane] : 0.0;
+            v = warp_sum(v);
+            if (lane == 0) a.tt_part[blockIdx.x] = v;
+        }
     }
 }
 
@@ -201,15 +244,12 @@ __device__ __forceinline__ void scatter_entry(const float* __restrict__ Tv, int6
     for (int kk = 0; kk < K; ++kk) acc[kk] += wv * __ldg(Tv + t0 + kk);
 }
 
-// scatter: raw[pq][kk] = sum over samples containing pq of W t_s, warp per
-// pq.  The run [lo, hi) of T is read as an unaligned head, 16-byte loads
-// (2 per lane per step, 256 entries per warp in flight) and a tail.
+// scatter: raw[pq][kk] = sum over samples containing pq of W t_s for the warp's
+// pq.  The run [lo, hi) of T is read as an unaligned head, 16-byte loads (2
+// per lane per step, 256 entries per warp in flight) and a tail.
 template <int K>
-__global__ void __launch_bounds__(256) k_scatter_T(SortedArgs a) {
-    if (a.stop && *a.stop) return;
+__device__ __forceinline__ void scatter_T_param(const SortedArgs& a, int pq) {
     const int lane = threadIdx.x & 31;
-    const int pq = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (pq >= a.pb.npf) return;
     float acc[K], acc2[K];
 #pragma unroll
     for (int kk = 0; kk < K; ++kk) acc[kk] = acc2[kk] = 0.f;
@@ -248,6 +288,45 @@ __global__ void __launch_bounds__(256) k_scatter_T(SortedArgs a) {
         const float v = warp_sum(acc[kk] + acc2[kk]);
         if (lane == 0) a.raw[(size_t)pq * K + kk] = v;
     }
+}
+
+// correlator state k: raw[k] = sum over the samples in state k of t_s (the
+// 1/C factor is applied by the caller), one thread per state
+template <int K>
+__device__ __forceinline__ void scatter_C_state(const SortedArgs& a, int64_t k) {
+    const uint32_t lo = a.cbase[k], hi = a.cbase[k + 1];
+    float acc[K];
+#pragma unroll
+    for (int kk = 0; kk < K; ++kk) acc[kk] = 0.f;
+    for (uint32_t j = lo; j < hi; j += 4) {
+        uint32_t sv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) sv[u] = j + u < hi ? __ldcs(a.Tc + j + u) : 0xFFFFFFFFu;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (sv[u] != 0xFFFFFFFFu)
+#pragma unroll
+                for (int kk = 0; kk < K; ++kk) acc[kk] += __ldg(a.Tv + (int64_t)sv[u] * K + kk);
+    }
+#pragma unroll
+    for (int kk = 0; kk < K; ++kk) a.craw[k * K + kk] = acc[kk];
+}
+
+// Both halves of the scatter in one launch: CTAs [0, ncb) take 256
+// correlator states each (a thread per state), the rest one pairing
+// amplitude per warp.  The short correlator CTAs go first so that they do
+// not form a tail behind the long pairing runs.
+template <int K>
+__global__ void __launch_bounds__(256) k_scatter_T(SortedArgs a) {
+    if (a.stop && *a.stop) return;
+    const int ncb = (int)((a.pb.ncp + 255) / 256);
+    if ((int)blockIdx.x < ncb) {
+        const int64_t k = (int64_t)blockIdx.x * 256 + threadIdx.x;
+        if (k < a.pb.ncp) scatter_C_state<K>(a, k);
+        return;
+    }
+    const int pq = ((int)blockIdx.x - ncb) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (pq < a.pb.npf) scatter_T_param<K>(a, pq);
 }
 
 template __global__ void k_gather_G<1, 1>(SortedArgs);

@@ -14,9 +14,8 @@
 // array into shared-memory histograms of each correlator's 4^m states, one
 // per CTA of a thread-block cluster, summed through distributed shared
 // memory, so neither half uses global atomics.
-#include <cooperative_groups.h>
-
 #include "common.cuh"
+#include "corr.cuh"
 #include "kernels.h"
 
 namespace vmc {
@@ -103,64 +102,12 @@ __global__ void __launch_bounds__(512) k_sr_main(MainArgs<AT> a) {
     for (int i = threadIdx.x; i < npf * K; i += blockDim.x) dst[i] = acc[i];
 }
 
-// correlator-major scatter on a thread-block cluster: the kCorrCluster CTAs
-// of cluster c histogram t_s over the 4^m states of correlator c, each for a
-// slice of the samples, into their own shared memory; after a cluster barrier
-// CTA r sums its share of the states over the cluster's histograms through
-// distributed shared memory (fixed order) and writes raw[off_c + state].
-// Slices start on multiples of 8 samples; each thread takes 8 consecutive
-// samples per step (one 16-byte load of states, K x 8 values of t).
+// correlator-major scatter: one thread-block cluster per correlator
 template <typename AT, int K>
 __global__ void __cluster_dims__(kCorrCluster, 1, 1) __launch_bounds__(256) k_corr_scatter(CorrArgs<AT> a) {
     if (a.stop && *a.stop) return;   // uniform over the grid: no CTA reaches a cluster barrier
-    namespace cg = cooperative_groups;
-    cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char smem[];
-    AT* h = (AT*)smem;
-    const DevProblem& pb = a.pb;
-    const int c = blockIdx.x / kCorrCluster;
-    const int rank = (int)cluster.block_rank();
-    const int64_t off = pb.corr_off[c];
-    const int d = (int)(pb.corr_off[c + 1] - off);
-    for (int i = threadIdx.x; i < d * K; i += blockDim.x) h[i] = AT(0);
-    __syncthreads();
-    const int64_t len = ((a.n_s + kCorrCluster - 1) / kCorrCluster + 7) & ~(int64_t)7;
-    const int64_t s0 = min(a.n_s, rank * len), s1 = min(a.n_s, s0 + len);
-    const uint16_t* st = a.cidxT + (int64_t)c * a.n_s;
-    // 16-byte loads need the row to start on a 16-byte boundary
-    const bool vec = ((a.n_s & 7) == 0);
-    int64_t s = s0;
-    if (vec) {
-        for (int64_t g = s0 + 8 * (int64_t)threadIdx.x; g + 8 <= s1; g += 8 * (int64_t)blockDim.x) {
-            const uint4 sv = *(const uint4*)(st + g);
-            const uint32_t w4[4] = {sv.x, sv.y, sv.z, sv.w};
-            AT tv[8 * K];
-#pragma unroll
-            for (int j = 0; j < 8 * K; ++j) tv[j] = a.T[g * K + j];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int i = (int)((w4[j >> 1] >> (16 * (j & 1))) & 0xFFFFu);
-#pragma unroll
-                for (int kk = 0; kk < K; ++kk) atomicAdd(&h[i * K + kk], tv[j * K + kk]);
-            }
-        }
-        s = s0 + ((s1 - s0) & ~(int64_t)7);
-    }
-    for (int64_t q = s + threadIdx.x; q < s1; q += blockDim.x) {
-        int i = st[q];
-#pragma unroll
-        for (int kk = 0; kk < K; ++kk) atomicAdd(&h[i * K + kk], a.T[q * K + kk]);
-    }
-    cluster.sync();
-    const int per = (d + kCorrCluster - 1) / kCorrCluster;
-    const int b0 = min(d, rank * per) * K, b1 = min(d, (rank + 1) * per) * K;
-    for (int i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
-        double acc = 0.0;
-#pragma unroll
-        for (int q = 0; q < kCorrCluster; ++q) acc += (double)cluster.map_shared_rank(h, q)[i];
-        a.corr_raw[off * K + i] = (AT)acc;
-    }
-    cluster.sync();   // keep this CTA's histogram alive until the cluster has read it
+    corr_cluster_histogram<AT, K>(a, (AT*)smem, blockIdx.x / kCorrCluster);
 }
 
 template <int K>
@@ -455,11 +402,80 @@ __global__ void __launch_bounds__(256) k_cg_xr(VT* x, VT* r, const VT* p, const 
     if (blockIdx.x == 0 && threadIdx.x == 0) scal[CG_RRP] = scal[CG_RR];
 }
 
-// beta = rr_new / rr; p = r + beta p; partial Obar . p for the next product
+// two block sums to two partial arrays
+__device__ __forceinline__ void block_reduce_store2(double a, double b, double* out_a, double* out_b) {
+    __shared__ double red[2][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if (lane == 0) { red[0][wid] = a; red[1][wid] = b; }
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        double x = lane < nw ? red[0][lane] : 0.0, y = lane < nw ? red[1][lane] : 0.0;
+        x = warp_sum(x);
+        y = warp_sum(y);
+        if (lane == 0) { out_a[blockIdx.x] = x; out_b[blockIdx.x] = y; }
+    }
+}
+
+// Fused CG update after a centered product.  With t_s - Obar . p scattered,
+// the curvature is p . (S + eps) p = (1/n) sum_s (t_s - Obar . p)^2 + eps |p|^2,
+// both known from partial sums (gather, previous p update), so alpha needs no
+// separate dot product and Ap = raw / n + eps p is formed element by element
+// and never stored: x += alpha p; r -= alpha Ap; partial r . r.
+template <typename VT>
+__global__ void __launch_bounds__(256) k_cg_fxr(CgFusedArgs<VT> a) {
+    if (*a.stop) return;
+    __shared__ double alpha;
+    if (threadIdx.x < 32) {
+        const double tt = warp_sum_partials(a.tt_part, a.ntt, 0, 1);
+        const double pp = warp_sum_partials(a.pp_part, a.npp, 0, 1);
+        if (threadIdx.x == 0) {
+            const double pAp = tt * a.inv_n + a.shift * pp;
+            alpha = a.scal[CG_RR] / pAp;
+            if (!isfinite(alpha) || pAp <= 0.0) alpha = 0.0;
+        }
+    }
+    __syncthreads();
+    const VT al = (VT)alpha, inv_n = (VT)a.inv_n, sh = (VT)a.shift;
+    const int64_t n = a.n, stride = (int64_t)gridDim.x * blockDim.x;
+    double loc[1] = {0.0};
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += kVecUnroll * stride) {
+        VT xv[kVecUnroll], rv[kVecUnroll], pv[kVecUnroll], raw[kVecUnroll];
+#pragma unroll
+        for (int u = 0; u < kVecUnroll; ++u) {
+            const int64_t i = i0 + u * stride;
+            const bool in = i < n;
+            xv[u] = in ? a.x[i] : VT(0);
+            rv[u] = in ? a.r[i] : VT(0);
+            pv[u] = in ? a.p[i] : VT(0);
+            raw[u] = !in ? VT(0) : i < a.ncp ? a.corr_raw[i] * a.invC[i] : a.pf_raw[i - a.ncp];
+        }
+        VT part = VT(0);
+#pragma unroll
+        for (int u = 0; u < kVecUnroll; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (i < n) {
+                const VT q = raw[u] * inv_n + sh * pv[u];
+                const VT ri = rv[u] - al * q;
+                a.x[i] = xv[u] + al * pv[u];
+                a.r[i] = ri;
+                part += ri * ri;
+            }
+        }
+        loc[0] += (double)part;
+    }
+    block_reduce_store<1>(loc, a.rr_part);
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.scal[CG_RRP] = a.scal[CG_RR];
+}
+
+// beta = rr_new / rr; p = r + beta p; partials Obar . p (centering of the next
+// product) and |p|^2 (its curvature)
 template <typename VT>
 __global__ void __launch_bounds__(256) k_cg_p(const VT* r, VT* p, int64_t n, const double* rr_part, int npart,
-                                              double* scal, const VT* Obar, double* obp_part, int* stop,
-                                              int max_iter) {
+                                              double* scal, const VT* Obar, double* obp_part, double* pp_part,
+                                              int* stop, int max_iter) {
     if (*stop) return;
     __shared__ double beta, rrn;
     if (threadIdx.x < 32) {
@@ -472,7 +488,7 @@ __global__ void __launch_bounds__(256) k_cg_p(const VT* r, VT* p, int64_t n, con
     __syncthreads();
     const VT be = (VT)beta;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    double loc[1] = {0.0};
+    double lo = 0.0, lp = 0.0;
     for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += kVecUnroll * stride) {
         VT rv[kVecUnroll], pv[kVecUnroll], ov[kVecUnroll];
 #pragma unroll
@@ -483,19 +499,21 @@ __global__ void __launch_bounds__(256) k_cg_p(const VT* r, VT* p, int64_t n, con
             pv[u] = in ? p[i] : VT(0);
             ov[u] = in ? Obar[i] : VT(0);
         }
-        VT part = VT(0);
+        VT po = VT(0), pp = VT(0);
 #pragma unroll
         for (int u = 0; u < kVecUnroll; ++u) {
             const int64_t i = i0 + u * stride;
             if (i < n) {
                 const VT pi = rv[u] + be * pv[u];
                 p[i] = pi;
-                part += ov[u] * pi;
+                po += ov[u] * pi;
+                pp += pi * pi;
             }
         }
-        loc[0] += (double)part;
+        lo += (double)po;
+        lp += (double)pp;
     }
-    block_reduce_store<1>(loc, obp_part);
+    block_reduce_store2(lo, lp, obp_part, pp_part);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         scal[CG_RR] = rrn;
         double it = scal[CG_IT] + 1.0;
@@ -576,9 +594,10 @@ template __global__ void k_cg_xr<double>(double*, double*, const double*, const 
 template __global__ void k_cg_xr<float>(float*, float*, const float*, const float*, int64_t, const double*, int,
                                         double*, double*, int*);
 template __global__ void k_cg_p<double>(const double*, double*, int64_t, const double*, int, double*, const double*,
-                                        double*, int*, int);
+                                        double*, double*, int*, int);
 template __global__ void k_cg_p<float>(const float*, float*, int64_t, const double*, int, double*, const float*,
-                                       double*, int*, int);
+                                       double*, double*, int*, int);
+template __global__ void k_cg_fxr<float>(CgFusedArgs<float>);
 template __global__ void k_axpy_to64<float>(double*, const float*, double, int64_t);
 template __global__ void k_axpy_to64<double>(double*, const double*, double, int64_t);
 
