@@ -870,11 +870,11 @@ static GatherKern gather_kernel(int u) {
 }
 
 // the sorted product applies: BF16 store with its sorted copies, the gather's
-// table and the run builders' counters within shared memory, rows of at most
-// 2048 elements
+// table and the run builders' counters within shared memory, at most 128
+// correlators, rows of at most 2048 elements
 template <int K>
 static bool sorted_usable(const vmc_ctx* h) {
-    if (!h->use_sorted || !h->d_G) return false;
+    if (!h->use_sorted || !h->d_G || h->ncorr > 32 * kCorrPerLane) return false;
     if ((size_t)h->maxd * 4 > h->smem_optin) return false;                                  // run counters
     if ((size_t)h->npf * K * 4 + (size_t)(h->ncorr + 1) * 4 > h->smem_optin) return false;   // gather table
     return gather_kernel<K>((int)((h->Pst / 4 + 31) / 32)) != nullptr;
@@ -914,7 +914,7 @@ static int launch_sorted(vmc_ctx* h, const float* V, const float* invC, const do
     int per_sm = 0;
     VCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gk, 256, smem));
     int grid = h->nsm * std::max(1, per_sm);
-    int64_t need = (h->n_s + 7) / 8;
+    const int64_t need = (h->n_s + 7) / 8;
     if (need < grid) grid = (int)std::max<int64_t>(1, need);
     grid = std::min(grid, kNumPart * kMaxK);   // one partial slot of tt sums
     gk<<<grid, 256, smem, st>>>(a); h->n_launch++;

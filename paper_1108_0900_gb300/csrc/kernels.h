@@ -231,6 +231,8 @@ struct SortedArgs {
     const int* stop;
 };
 
+constexpr int kCorrPerLane = 4;    // the sorted gather handles up to 128 correlators
+
 __global__ void __launch_bounds__(256) k_build_G(DevProblem pb, int64_t n_s, const uint8_t* s_occ, int Nst,
                                                  const __nv_bfloat16* pf16, int64_t Pst, uint32_t* G);
 __global__ void __launch_bounds__(512) k_count_G(const uint32_t* G, int64_t Pst, int P, int64_t s_begin,

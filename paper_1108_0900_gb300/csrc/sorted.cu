@@ -19,27 +19,83 @@
 
 namespace vmc {
 
-// G rows: element e of sample s, padding elements are (0, 0.0)
+// G rows in a bank-aware order.  The gather reads lane L's 16-byte word
+// L + 32 u of a row and looks up v[pq] in shared memory for its element j, so
+// the 32 lanes of one lookup instruction (u, j) read the row slots
+// 128 u + 4 L + j.  Lookups whose pq fall in the same shared-memory bank
+// (pq mod 32) but at different addresses serialise, and random pq give about
+// 3.5-way conflicts.  Here the P elements of a sample are ranked within their
+// bank and placed in rank-major order (rank 0 of every bank, then rank 1, ...)
+// along the instruction groups, so a group holds at most two elements of a
+// bank: all ranks below the smallest bank count fill whole conflict-free
+// groups.  Padding slots hold (0, 0.0); samples whose largest bank count
+// exceeds kBankRanks keep the plain element order.
+constexpr int kBankRanks = 128;
+
+// row position of slot k in the gather's instruction-group order
+__device__ __forceinline__ int group_slot_pos(int k, int n4) {
+    const int nfull = n4 >> 5, m = n4 & 31;
+    if (k < 128 * nfull) return 128 * (k >> 7) + 4 * (k & 31) + ((k >> 5) & 3);
+    const int kr = k - 128 * nfull;
+    return 128 * nfull + 4 * (kr % m) + kr / m;
+}
+
 __global__ void __launch_bounds__(256) k_build_G(DevProblem pb, int64_t n_s, const uint8_t* s_occ, int Nst,
                                                  const __nv_bfloat16* pf16, int64_t Pst, uint32_t* G) {
     __shared__ uint8_t occw[8][64];
+    __shared__ uint32_t cnt[8][32];
+    __shared__ uint32_t msk[8][kBankRanks];
+    __shared__ uint16_t rbase[8][kBankRanks];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t s = (int64_t)blockIdx.x * 8 + wid;
     if (s >= n_s) return;
     for (int i = lane; i < pb.N; i += 32) occw[wid][i] = s_occ[s * Nst + i];
+    cnt[wid][lane] = 0u;
     __syncwarp();
     const uint16_t* src = (const uint16_t*)(pf16 + s * Pst);
     uint32_t* dst = G + s * Pst;
-    for (int e = lane; e < Pst; e += 32) {
-        uint32_t g = 0u;
-        if (e < pb.P) {
-            const uint16_t pt = pb.pairtab[e];
-            const int p = occw[wid][pt & 255], q = occw[wid][pt >> 8];
-            const uint32_t pq = (uint32_t)(pf_row_base(pb.M, p) + q);
-            g = (pq << 16) | (uint32_t)src[e];
-        }
-        dst[e] = g;
+    const int P = pb.P, n4 = (int)(Pst >> 2);
+    for (int e = lane; e < P; e += 32) {
+        const uint16_t pt = pb.pairtab[e];
+        const int pq = (int)pf_row_base(pb.M, occw[wid][pt & 255]) + occw[wid][pt >> 8];
+        atomicAdd(&cnt[wid][pq & 31], 1u);
     }
+    __syncwarp();
+    const uint32_t c = cnt[wid][lane];
+    uint32_t maxc = c;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) maxc = max(maxc, __shfl_xor_sync(0xffffffffu, maxc, o));
+    const bool ranked = maxc <= (uint32_t)kBankRanks;
+    if (ranked) {
+        // banks with more than r elements, and the slots before rank r
+        for (int r = 0; r < (int)maxc; ++r) {
+            const uint32_t m = __ballot_sync(0xffffffffu, c > (uint32_t)r);
+            if (lane == 0) msk[wid][r] = m;
+        }
+        __syncwarp();
+        if (lane == 0) {
+            uint32_t run = 0;
+            for (int r = 0; r < (int)maxc; ++r) {
+                rbase[wid][r] = (uint16_t)run;
+                run += __popc(msk[wid][r]);
+            }
+        }
+        cnt[wid][lane] = 0u;
+        __syncwarp();
+    }
+    for (int e = lane; e < P; e += 32) {
+        const uint16_t pt = pb.pairtab[e];
+        const int pq = (int)pf_row_base(pb.M, occw[wid][pt & 255]) + occw[wid][pt >> 8];
+        const uint32_t g = ((uint32_t)pq << 16) | (uint32_t)src[e];
+        int slot = e;
+        if (ranked) {
+            const int b = pq & 31;
+            const uint32_t r = atomicAdd(&cnt[wid][b], 1u);
+            slot = rbase[wid][r] + __popc(msk[wid][r] & ((1u << b) - 1u));
+        }
+        dst[group_slot_pos(slot, n4)] = g;
+    }
+    for (int k = P + lane; k < (int)Pst; k += 32) dst[group_slot_pos(k, n4)] = 0u;
 }
 
 // Block b of a chunk [s_begin, s_end) owns samples s_begin + [b*per, (b+1)*per).
@@ -60,7 +116,10 @@ __global__ void __launch_bounds__(512) k_count_G(const uint32_t* G, int64_t Pst,
     block_range(s_begin, s_end, gridDim.x, &lo, &hi);
     for (int64_t s = lo; s < hi; ++s) {
         const uint32_t* g = G + s * Pst;
-        for (int e = threadIdx.x; e < P; e += blockDim.x) atomicAdd(&cnt[g[e] >> 16], 1u);
+        for (int e = threadIdx.x; e < Pst; e += blockDim.x) {
+            const uint32_t v = g[e];
+            if (v) atomicAdd(&cnt[v >> 16], 1u);   // padding (and exact zeros) carry nothing
+        }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < npf; i += blockDim.x) counts[(size_t)blockIdx.x * npf + i] = cnt[i];
@@ -115,8 +174,9 @@ __global__ void __launch_bounds__(512) k_fill_T(const uint32_t* G, int64_t Pst, 
     for (int64_t s = lo; s < hi; ++s) {
         const uint32_t* g = G + s * Pst;
         const uint32_t sl = (uint32_t)(s - s_begin) << 16;
-        for (int e = threadIdx.x; e < P; e += blockDim.x) {
+        for (int e = threadIdx.x; e < Pst; e += blockDim.x) {
             const uint32_t v = g[e];
+            if (!v) continue;
             const uint32_t pos = atomicAdd(&cur[v >> 16], 1u);
             T[pos] = sl | (v & 0xFFFFu);
         }
@@ -150,6 +210,27 @@ __global__ void __launch_bounds__(512) k_fill_C(DevProblem pb, int64_t n_s, cons
     __syncthreads();
     const uint16_t* st = cidxT + (int64_t)c * n_s;
     for (int64_t s = threadIdx.x; s < n_s; s += blockDim.x) Tc[atomicAdd(&cur[st[s]], 1u)] = (uint32_t)s;
+}
+
+// Correlator part of the gather for one sample: lane L looks up V[k_c] / C[k_c]
+// for c = L + 32 j (at most 32 kCorrPerLane correlators).  The loads are only
+// issued here; the caller adds cv after its pairing work, which hides them.
+template <int K>
+__device__ __forceinline__ void corr_lookups(const DevProblem& pb, const int* coff, const uint16_t* cid,
+                                             const float* V, const float* invC, int lane,
+                                             float (&cv)[kCorrPerLane][K]) {
+#pragma unroll
+    for (int j = 0; j < kCorrPerLane; ++j) {
+        const int c = lane + 32 * j;
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) cv[j][kk] = 0.f;
+        if (c < pb.ncorr) {
+            const int k = coff[c] + (int)cid[c];
+            const float ic = __ldg(invC + k);
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) cv[j][kk] = __ldg(V + kk * pb.nv + k) * ic;
+        }
+    }
 }
 
 // gather: t_s = sum_c V[k_c]/C[k_c] + sum_e W_e v[pq(e)] - Obar . V, warp per
@@ -193,13 +274,9 @@ __global__ void __launch_bounds__(256) k_gather_G(SortedArgs a) {
         float t[K], w[K];
 #pragma unroll
         for (int kk = 0; kk < K; ++kk) t[kk] = w[kk] = 0.f;
-        const uint16_t* cid = a.s_cidx + s * a.ncst;
-        for (int c = lane; c < pb.ncorr; c += 32) {
-            const int k = coff[c] + (int)__ldg(cid + c);
-            const float ic = __ldg(a.invC + k);
-#pragma unroll
-            for (int kk = 0; kk < K; ++kk) t[kk] += __ldg(a.V + kk * pb.nv + k) * ic;
-        }
+        // correlator lookups issued now, added after the row is consumed
+        float cv[kCorrPerLane][K];
+        corr_lookups<K>(pb, coff, a.s_cidx + s * a.ncst, a.V, a.invC, lane, cv);
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const uint32_t e[4] = {g[u].x, g[u].y, g[u].z, g[u].w};
@@ -214,6 +291,10 @@ __global__ void __launch_bounds__(256) k_gather_G(SortedArgs a) {
                 }
             }
         }
+#pragma unroll
+        for (int j = 0; j < kCorrPerLane; ++j)
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) t[kk] += cv[j][kk];
 #pragma unroll
         for (int kk = 0; kk < K; ++kk) t[kk] = warp_sum(t[kk] + w[kk]);
         if (lane == 0) {
