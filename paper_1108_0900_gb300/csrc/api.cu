@@ -59,6 +59,7 @@ struct vmc_ctx {
     int *d_corr_ptr = nullptr, *d_corr_sites = nullptr;
     int64_t* d_corr_off = nullptr;
     int *d_site_cptr = nullptr, *d_site_corr = nullptr, *d_site_w = nullptr;
+    uint16_t* d_corr_site_w = nullptr;
     int *d_nbr_ptr = nullptr, *d_nbr_site = nullptr;
     double* d_nbr_t = nullptr;
     double *d_h64 = nullptr, *d_eri64 = nullptr;
@@ -204,6 +205,10 @@ extern "C" int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, co
     }
     h->ncp = h->corr_off[h->ncorr];
     h->nv = h->ncp + h->npf;
+    // dense (correlator, site) -> 4^j weight table, 0 where the site is absent
+    std::vector<uint16_t> csw((size_t)std::max(h->ncorr, 1) * ns, 0);
+    for (int s = 0; s < ns; ++s)
+        for (auto& pr : memb[s]) csw[(size_t)pr.first * ns + s] = (uint16_t)pr.second;
     std::vector<int> scptr(ns + 1, 0), scorr, sw;
     for (int s = 0; s < ns; ++s) {
         for (auto& pr : memb[s]) { scorr.push_back(pr.first); sw.push_back(pr.second); }
@@ -278,6 +283,7 @@ extern "C" int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, co
     ACK(h->alloc(&h->d_site_cptr, scptr.size()));
     ACK(h->alloc(&h->d_site_corr, scorr.size()));
     ACK(h->alloc(&h->d_site_w, sw.size()));
+    ACK(h->alloc(&h->d_corr_site_w, csw.size()));
     ACK(h->alloc(&h->d_nbr_ptr, nptr.size()));
     ACK(h->alloc(&h->d_nbr_site, nsite.size()));
     ACK(h->alloc(&h->d_nbr_t, nt.size()));
@@ -289,6 +295,7 @@ extern "C" int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, co
     UPL(h->d_site_cptr, scptr.data(), scptr.size());
     if (!scorr.empty()) UPL(h->d_site_corr, scorr.data(), scorr.size());
     if (!sw.empty()) UPL(h->d_site_w, sw.data(), sw.size());
+    UPL(h->d_corr_site_w, csw.data(), csw.size());
     UPL(h->d_nbr_ptr, nptr.data(), nptr.size());
     if (!nsite.empty()) UPL(h->d_nbr_site, nsite.data(), nsite.size());
     if (!nt.empty()) UPL(h->d_nbr_t, nt.data(), nt.size());
@@ -372,6 +379,7 @@ extern "C" int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, co
     pb.npf = h->npf; pb.ham = h->ham; pb.ncp = h->ncp; pb.nv = h->nv; pb.U = ham->U;
     pb.corr_ptr = h->d_corr_ptr; pb.corr_sites = h->d_corr_sites; pb.corr_off = h->d_corr_off;
     pb.site_cptr = h->d_site_cptr; pb.site_corr = h->d_site_corr; pb.site_w = h->d_site_w;
+    pb.corr_site_w = h->d_corr_site_w;
     pb.nbr_ptr = h->d_nbr_ptr; pb.nbr_site = h->d_nbr_site; pb.nbr_t = h->d_nbr_t;
     pb.h64 = h->d_h64; pb.h32 = h->d_h32; pb.eri64 = h->d_eri64; pb.eri32 = h->d_eri32;
     pb.pair_ptr = h->d_pair_ptr; pb.pair_corr = h->d_pair_corr;

@@ -94,6 +94,7 @@ struct DevProblem {
     const int* site_cptr;      // [ns+1]
     const int* site_corr;      // correlator id
     const int* site_w;         // 4^j weight of the site inside that correlator
+    const uint16_t* corr_site_w;   // [ncorr][ns] 4^j weight of site s in correlator c, 0 if absent
     // Hubbard hopping lists: site s hops to nbr_site[k] with amplitude nbr_t[k]
     const int* nbr_ptr;        // [ns+1]
     const int* nbr_site;

@@ -40,14 +40,9 @@ template <> __device__ __forceinline__ double load_C<double>(const DevProblem& p
     return __ldg(pb.C64 + k);
 }
 
-// weight 4^j of site s inside correlator c (0 if absent)
+// weight 4^j of site s inside correlator c (0 if absent): one table load
 __device__ __forceinline__ int site_weight_in(const DevProblem& pb, int c, int s) {
-    int w = 1;
-    for (int j = pb.corr_ptr[c]; j < pb.corr_ptr[c + 1]; ++j) {
-        if (pb.corr_sites[j] == s) return w;
-        w <<= 2;
-    }
-    return 0;
+    return (int)__ldg(pb.corr_site_w + c * pb.ns + s);
 }
 
 // Correlator part of Psi(n')/Psi(n) for moving one electron of spin factor
@@ -106,6 +101,7 @@ __device__ R corr_ratio_serial(const DevProblem& pb, const uint32_t* cidx, int p
     int sp = p >= ns ? p - ns : p, sq = q >= ns ? q - ns : q;
     int total = (pb.site_cptr[sp + 1] - pb.site_cptr[sp]) + (pb.site_cptr[sq + 1] - pb.site_cptr[sq]);
     R prod = R(1);
+#pragma unroll 4
     for (int e = 0; e < total; ++e) {
         int c;
         int newi = corr_entry(pb, cidx, sp, sq, sf, e, &c);
@@ -526,6 +522,7 @@ __global__ void k_walkers(SampleArgs a) {
                         if ((m >> s2) & 1ull) continue;
                         int q = spin * ns + s2;
                         R d = R(0);
+#pragma unroll 8
                         for (int j = 0; j < N; ++j)
                             if (j != i) d += load_F<R>(pb, q, pos_orb[j]) * X[i * XS + j];
                         R rc = corr_ratio_serial<R>(pb, cidx, p, q);
