@@ -140,6 +140,10 @@ int vmc_num_params(vmc_handle h, int64_t* n_v, int64_t* n_corr_params);
  * (host, FP64, layout above).  Errors: SINGULAR if some C is zero. */
 int vmc_set_params(vmc_handle h, const double* C, const double* f);
 
+/* Read the current parameters back (host C[n_corr_params], f[M(M-1)/2],
+ * FP64, the layout of vmc_set_params); either pointer may be NULL. */
+int vmc_get_params(vmc_handle h, double* C, double* f, void* stream);
+
 /* Set walker configurations: occ[n_walkers][N] ascending occupied spin
  * orbitals (host, uint8) with n_up orbitals below n_sites; step[n_walkers]
  * (host, may be NULL = 0) is each chain's proposal counter.  Errors:
@@ -207,6 +211,20 @@ int sr_apply_S(vmc_handle h, const double* V, double* out, int k, double shift, 
  * max_iter products; mode VMC_CG_*.  info (host) is filled. */
 int sr_cg_solve(vmc_handle h, const double* g, double shift, double tol, int max_iter, int mode,
                 double* x, vmc_cg_info* info, void* stream);
+
+/* SR parameter update (Sec. II.A): after the solve of Eq. 2 with x_0
+ * eliminated, (S + shift I) y = g, the coefficients of the projected state
+ * (1 - tau H)|Psi> are x = -tau y and x_0 = 1 - tau <E_L> - Obar . x, and
+ * every parameter moves to alpha_k + x_k / x_0 on the device (the FP32
+ * copies, 1/C and the antisymmetric F matrices follow).  y is device [n_v]
+ * FP64; <E_L> and Obar are those of the last sr_gradient over `store`
+ * (VMC_STORE_FP64, VMC_STORE_FP32 or VMC_STORE_BF16).  x0 (host, may be
+ * NULL) receives x_0.  The stored samples then belong to the old
+ * parameters: sample again before the next gradient.  Errors: STATE when no
+ * gradient was taken over `store`; NONFINITE when x_0 <= 0 or not finite (tau
+ * beyond the first-order projector; nothing is changed), or when an updated
+ * parameter is not finite; SINGULAR when an updated C is zero. */
+int sr_update(vmc_handle h, const double* y, double tau, int store, double* x0, void* stream);
 
 /* Measurement support (no counterpart in the paper).  vmc_profile(h, 1)
  * resets the counters and starts recording: every kernel the handle launches

@@ -83,6 +83,8 @@ def lib():
             L.orc_apply_S.argtypes = [i64, i64, vp, vp, vp, dbl, vp]
             L.orc_cg.argtypes = [i64, i64, vp, vp, dbl, dbl, i32, vp, vp, vp]
             L.orc_cg.restype = i32
+            L.orc_sr_update.argtypes = [i64, vp, vp, dbl, dbl, vp, vp]
+            L.orc_sr_update.restype = dbl
             L.orc_sector_size.argtypes = [vp]
             L.orc_sector_size.restype = i64
             L.orc_enumerate.argtypes = [vp, vp]
@@ -270,6 +272,16 @@ def apply_S(O, v, eps, Obar=None):
     lib().orc_apply_S(O.shape[0], O.shape[1], _ptr(O), _ptr(np.ascontiguousarray(Obar)), _ptr(v),
                       float(eps), _ptr(out))
     return out
+
+
+def sr_update(alpha, y, tau, E_mean, Obar):
+    """Sec. II.A update after Eq. 2: returns (alpha + x / x_0, x_0) with x = -tau y."""
+    alpha = np.ascontiguousarray(alpha, np.float64)
+    y = np.ascontiguousarray(y, np.float64)
+    Obar = np.ascontiguousarray(Obar, np.float64)
+    out = np.zeros_like(alpha)
+    x0 = lib().orc_sr_update(alpha.size, _ptr(alpha), _ptr(y), float(tau), float(E_mean), _ptr(Obar), _ptr(out))
+    return out, x0
 
 
 def cg(O, g, eps, tol, max_iter=None):

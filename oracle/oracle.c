@@ -816,6 +816,24 @@ int orc_cg(int64_t n_s, int64_t nv, const double* O, const double* g, double eps
 }
 
 /* ------------------------------------------------------------------------ */
+/* SR parameter update (Sec. II.A).  Eq. 2 projects (1 - tau H)|Psi> onto the */
+/* span of |Psi> and its derivatives with coefficients x_0, x.  Its row 0,    */
+/* divided by <Psi|Psi>, reads 1 - tau <E> = x_0 + sum_j Obar_j x_j; the     */
+/* remaining rows reduce to S x = -tau g, so x = -tau y for the solution y of */
+/* (S + eps) y = g.  The new parameters are alpha_k + x_k / x_0.              */
+/* ------------------------------------------------------------------------ */
+
+double orc_sr_update(int64_t nv, const double* alpha, const double* y, double tau, double E_mean,
+                     const double* Obar, double* alpha_out)
+{
+    double ox = 0.0;
+    for (int64_t k = 0; k < nv; ++k) ox += Obar[k] * (-tau * y[k]);
+    const double x0 = 1.0 - tau * E_mean - ox;
+    for (int64_t k = 0; k < nv; ++k) alpha_out[k] = alpha[k] + (-tau * y[k]) / x0;
+    return x0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Exact enumeration of the sector (tiny lattices only)                      */
 /* ------------------------------------------------------------------------ */
 

@@ -50,6 +50,10 @@ void orc_apply_S(int64_t n_s, int64_t nv, const double* O, const double* Obar, c
                  double eps, double* out);
 int orc_cg(int64_t n_s, int64_t nv, const double* O, const double* g, double eps, double tol,
            int max_iter, double* x, int* iters, double* true_rel_res);
+/* SR parameter update (Sec. II.A, after Eq. 2): x = -tau y, x_0 = 1 - tau E_mean - Obar . x,
+ * alpha_out = alpha + x / x_0.  Returns x_0. */
+double orc_sr_update(int64_t nv, const double* alpha, const double* y, double tau, double E_mean,
+                     const double* Obar, double* alpha_out);
 int64_t orc_sector_size(const orc_problem* P);
 int64_t orc_enumerate(const orc_problem* P, uint8_t* occ_out);
 void orc_exact_weights(const orc_problem* P, int64_t n_conf, const uint8_t* occ, double* w);

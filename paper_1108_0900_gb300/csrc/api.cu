@@ -17,6 +17,7 @@ namespace {
 constexpr int kMaxK = 4;
 constexpr int kNumPart = 256;   // blocks of the reduction kernels
 constexpr int kChunk = 16;      // CG iterations between host convergence checks
+constexpr int kScalX0 = 7;      // d_scal slot of the SR update's x_0
 
 #define VCK(x)                                                    \
     do {                                                          \
@@ -60,6 +61,7 @@ struct vmc_ctx {
     int64_t* d_corr_off = nullptr;
     int *d_site_cptr = nullptr, *d_site_corr = nullptr, *d_site_w = nullptr;
     uint16_t* d_corr_site_w = nullptr;
+    uint32_t* d_pq_of = nullptr;   // pairing index -> p | q << 16
     int *d_nbr_ptr = nullptr, *d_nbr_site = nullptr;
     double* d_nbr_t = nullptr;
     double *d_h64 = nullptr, *d_eri64 = nullptr;
@@ -268,6 +270,9 @@ extern "C" int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, co
         for (int b = nu; b < N; ++b) pt.push_back((uint16_t)(a | (b << 8)));
     std::vector<int> rb(h->M);
     for (int p = 0; p < h->M; ++p) rb[p] = (int)pf_row_base(h->M, p);
+    std::vector<uint32_t> pqo((size_t)h->M * (h->M - 1) / 2);
+    for (int p = 0; p < h->M; ++p)
+        for (int q = p + 1; q < h->M; ++q) pqo[(size_t)rb[p] + q] = (uint32_t)p | ((uint32_t)q << 16);
 
     if (cudaGetDevice(&h->dev) != cudaSuccess) return fail(VMC_ERR_CUDA);
     cudaDeviceProp prop;
@@ -289,6 +294,7 @@ extern "C" int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, co
     ACK(h->alloc(&h->d_nbr_t, nt.size()));
     ACK(h->alloc(&h->d_pairtab, pt.size()));
     ACK(h->alloc(&h->d_rowbase, rb.size()));
+    ACK(h->alloc(&h->d_pq_of, std::max<size_t>(pqo.size(), 1)));
     UPL(h->d_corr_ptr, cptr.data(), cptr.size());
     if (!csites.empty()) UPL(h->d_corr_sites, csites.data(), csites.size());
     UPL(h->d_corr_off, h->corr_off.data(), h->corr_off.size());
@@ -301,6 +307,7 @@ extern "C" int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, co
     if (!nt.empty()) UPL(h->d_nbr_t, nt.data(), nt.size());
     UPL(h->d_pairtab, pt.data(), pt.size());
     UPL(h->d_rowbase, rb.data(), rb.size());
+    if (!pqo.empty()) UPL(h->d_pq_of, pqo.data(), pqo.size());
     ACK(h->alloc(&h->d_pair_ptr, pptr.size()));
     ACK(h->alloc(&h->d_pair_corr, std::max<size_t>(pcorr.size(), 1)));
     UPL(h->d_pair_ptr, pptr.data(), pptr.size());
@@ -441,6 +448,24 @@ extern "C" int vmc_set_params(vmc_handle h, const double* C, const double* f) {
     h->params_set = true;
     h->obar_ok[0] = h->obar_ok[1] = h->obar_ok[2] = false;
     h->sorted_ok = false;
+    return VMC_OK;
+}
+
+extern "C" int vmc_get_params(vmc_handle h, double* C, double* f, void* stream) {
+    if (!h) return VMC_ERR_INVALID_ARG;
+    if (!h->params_set) return VMC_ERR_STATE;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int M = h->M;
+    std::vector<double> F64;
+    if (C && h->ncp > 0) VCK(cudaMemcpyAsync(C, h->d_C64, sizeof(double) * h->ncp, cudaMemcpyDeviceToHost, st));
+    if (f) {
+        F64.resize((size_t)M * M);
+        VCK(cudaMemcpyAsync(F64.data(), h->d_F64, sizeof(double) * M * M, cudaMemcpyDeviceToHost, st));
+    }
+    VCK(cudaStreamSynchronize(st));
+    if (f)
+        for (int p = 0; p < M; ++p)
+            for (int q = p + 1; q < M; ++q) f[pf_row_base(M, p) + q] = F64[(size_t)p * M + q];
     return VMC_OK;
 }
 
@@ -1398,6 +1423,36 @@ extern "C" int sr_cg_solve(vmc_handle h, const double* g, double shift, double t
     inf.converged = inf.true_rel_residual <= tol ? 1 : 0;
     if (info) *info = inf;
     return inf.converged ? VMC_OK : VMC_ERR_NOT_CONVERGED;
+}
+
+extern "C" int sr_update(vmc_handle h, const double* y, double tau, int store, double* x0, void* stream) {
+    if (!h || !y || !std::isfinite(tau)) return VMC_ERR_INVALID_ARG;
+    const int kind = store_kind(store);
+    if (kind < 0) return VMC_ERR_INVALID_ARG;
+    if (!h->params_set || h->n_s == 0 || !h->obar_ok[kind]) return VMC_ERR_STATE;
+    cudaStream_t st = (cudaStream_t)stream;
+    k_vec_sum<<<kNumPart, 256, 0, st>>>(h->d_E, h->n_s, h->part(0)); h->n_launch++;
+    k_dot_part<double, double, 1><<<kNumPart, 256, 0, st>>>(h->d_Obar[kind], y, h->nv, h->part(1), nullptr);
+    h->n_launch++;
+    UpdateArgs a{};
+    a.C64 = h->d_C64; a.C32 = h->d_C32; a.invC64 = h->d_invC64; a.invC32 = h->d_invC32;
+    a.F64 = h->d_F64; a.F32 = h->d_F32; a.pq_of = h->d_pq_of;
+    a.y = y;
+    a.ncp = h->ncp; a.npf = h->npf; a.M = h->M;
+    a.tau = tau; a.inv_n = 1.0 / (double)h->n_s;
+    a.e_part = h->part(0); a.ne = kNumPart;
+    a.oy_part = h->part(1); a.noy = kNumPart;
+    a.x0 = h->d_scal + kScalX0;
+    a.status = h->d_status;
+    k_sr_update<<<vgrid(h, 1), 256, 0, st>>>(a); h->n_launch++;
+    VCK(cudaGetLastError());
+    // the stored samples belong to the old parameters
+    h->obar_ok[0] = h->obar_ok[1] = h->obar_ok[2] = false;
+    h->sorted_ok = false;
+    VCK(cudaMemcpyAsync(h->h_pinned + 1, h->d_scal + kScalX0, sizeof(double), cudaMemcpyDeviceToHost, st));
+    int rc = read_status(h, st);   // synchronizes the stream
+    if (x0) *x0 = h->h_pinned[1];
+    return rc;
 }
 
 // ---------------------------------------------------------------------------

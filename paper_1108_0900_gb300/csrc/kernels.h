@@ -157,6 +157,27 @@ struct CgFusedArgs {
     const int* stop;
 };
 
+// SR parameter update (k_sr_update)
+struct UpdateArgs {
+    double* C64;
+    float* C32;
+    double* invC64;
+    float* invC32;
+    double* F64;            // [M][M] antisymmetric
+    float* F32;
+    const uint32_t* pq_of;  // [npf] p | q << 16 of pairing index rowbase(p) + q
+    const double* y;        // [nv] solution of (S + eps) y = g
+    int64_t ncp, npf;
+    int M;
+    double tau, inv_n;
+    const double* e_part;   // partial sums of E_L
+    int ne;
+    const double* oy_part;  // partial sums of Obar . y
+    int noy;
+    double* x0;             // out: x_0
+    int* status;
+};
+
 enum { CG_RR = 0, CG_BB = 1, CG_TOL2 = 2, CG_IT = 3, CG_RRP = 4 };
 template <typename VT>
 __global__ void __launch_bounds__(256) k_cg_init(const VT* b, VT* x, VT* r, VT* p, int64_t n, double* part);
@@ -171,6 +192,8 @@ __global__ void __launch_bounds__(256) k_cg_p(const VT* r, VT* p, int64_t n, con
                                               int* stop, int max_iter);
 template <typename VT> __global__ void __launch_bounds__(256) k_cg_fxr(CgFusedArgs<VT> a);
 __global__ void k_sub(const double* a, const double* b, double* y, int64_t n, double* part);
+__global__ void __launch_bounds__(256) k_vec_sum(const double* x, int64_t n, double* part);
+__global__ void __launch_bounds__(256) k_sr_update(UpdateArgs a);
 __global__ void k_axpby(double a, const double* x, double b, double* y, int64_t n);
 template <typename VT> __global__ void k_axpy_to64(double* x, const VT* d, double scale, int64_t n);
 

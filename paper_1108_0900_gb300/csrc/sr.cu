@@ -522,6 +522,60 @@ __global__ void __launch_bounds__(256) k_cg_p(const VT* r, VT* p, int64_t n, con
     }
 }
 
+// partial sums of x (FP64)
+__global__ void __launch_bounds__(256) k_vec_sum(const double* x, int64_t n, double* part) {
+    double loc[1] = {0.0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        loc[0] += x[i];
+    block_reduce_store<1>(loc, part);
+}
+
+// SR parameter update (Sec. II.A, after Eq. 2).  x_0 = 1 - tau <E_L> + tau Obar . y
+// from the partial sums (every block forms the same value), then alpha_k +=
+// -tau y_k / x_0 with the derived copies: C in FP32, 1/C in both precisions,
+// and both triangles of the antisymmetric F.  A non-positive or non-finite
+// x_0 changes nothing and sets ST_NONFINITE.
+__global__ void __launch_bounds__(256) k_sr_update(UpdateArgs a) {
+    __shared__ double x0s;
+    if (threadIdx.x < 32) {
+        const double e = warp_sum_partials(a.e_part, a.ne, 0, 1) * a.inv_n;
+        const double oy = warp_sum_partials(a.oy_part, a.noy, 0, 1);
+        if (threadIdx.x == 0) x0s = 1.0 - a.tau * e + a.tau * oy;
+    }
+    __syncthreads();
+    const double x0 = x0s;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a.x0 = x0;
+    if (!(x0 > 0.0) || !isfinite(x0)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(a.status, ST_NONFINITE);
+        return;
+    }
+    const double s = -a.tau / x0;
+    const int64_t nv = a.ncp + a.npf;
+    int bad = 0;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nv; k += (int64_t)gridDim.x * blockDim.x) {
+        const double d = s * a.y[k];
+        if (k < a.ncp) {
+            const double c = a.C64[k] + d;
+            if (c == 0.0) bad |= ST_SINGULAR;
+            if (!isfinite(c)) bad |= ST_NONFINITE;
+            a.C64[k] = c;
+            a.C32[k] = (float)c;
+            a.invC64[k] = 1.0 / c;
+            a.invC32[k] = (float)(1.0 / c);
+        } else {
+            const uint32_t pq = a.pq_of[k - a.ncp];
+            const int p = (int)(pq & 0xFFFFu), q = (int)(pq >> 16);
+            const double f = a.F64[(int64_t)p * a.M + q] + d;
+            if (!isfinite(f)) bad |= ST_NONFINITE;
+            a.F64[(int64_t)p * a.M + q] = f;
+            a.F64[(int64_t)q * a.M + p] = -f;
+            a.F32[(int64_t)p * a.M + q] = (float)f;
+            a.F32[(int64_t)q * a.M + p] = -(float)f;
+        }
+    }
+    if (bad) atomicOr(a.status, bad);
+}
+
 // y = a - b (FP64)
 __global__ void k_sub(const double* a, const double* b, double* y, int64_t n, double* part) {
     double loc[1] = {0.0};

@@ -92,6 +92,8 @@ def lib(build_if_missing: bool = True):
         "vmc_destroy": [vp],
         "vmc_num_params": [vp, vp, vp],
         "vmc_set_params": [vp, vp, vp],
+        "vmc_get_params": [vp, vp, vp, vp],
+        "sr_update": [vp, vp, dbl, i32, vp, vp],
         "vmc_set_walkers": [vp, vp, vp],
         "vmc_get_walkers": [vp, vp, vp, vp],
         "vmc_sample": [vp, i32, u64, vp],
@@ -206,6 +208,14 @@ def vmc_set_params(h: Handle, C, f):
     _check(lib().vmc_set_params(h.h, _np_ptr(C), _np_ptr(f)), "vmc_set_params")
 
 
+def vmc_get_params(h: Handle, stream=None):
+    """Current parameters (C, f) as host FP64 arrays."""
+    C = np.zeros(h.n_corr_params)
+    f = np.zeros(h.n_params - h.n_corr_params)
+    _check(lib().vmc_get_params(h.h, _np_ptr(C), _np_ptr(f), _stream(stream)), "vmc_get_params")
+    return C, f
+
+
 def vmc_set_walkers(h: Handle, occ, step=None):
     occ = np.ascontiguousarray(occ, np.uint8)
     st = None if step is None else np.ascontiguousarray(step, np.uint64)
@@ -294,6 +304,33 @@ def sr_cg_solve(h: Handle, g, shift: float, tol: float, max_iter: int, mode=VMC_
     if not (allow_not_converged and rc == -5):
         _check(rc, "sr_cg_solve")
     return x, info.as_dict()
+
+
+def sr_update(h: Handle, y, tau: float, store=VMC_STORE_FP64, stream=None):
+    """alpha += x / x_0 with x = -tau y (Sec. II.A); returns x_0."""
+    x0 = ct.c_double()
+    _check(lib().sr_update(h.h, _dev_ptr(y), float(tau), int(store), ct.byref(x0), _stream(stream)), "sr_update")
+    return x0.value
+
+
+def sr_optimize(h: Handle, n_iter: int, tau: float, shift: float, tol: float, mode=VMC_CG_FP64, seed: int = 1,
+                max_iter: int = 20000, callback=None):
+    """The SR loop of Sec. II.A: sample, gradient, CG solve of Eq. 2, update;
+    returns one record per iteration (energy statistics before the update,
+    CG info, x_0).  The walkers must be set and thermalised."""
+    store = VMC_STORE_FP64 if mode == VMC_CG_FP64 else VMC_STORE_FP32
+    hist = []
+    for it in range(n_iter):
+        vmc_sample(h, 0, seed + it)
+        g, es = sr_gradient(h, store)
+        y, info = sr_cg_solve(h, g, shift, tol, max_iter, mode, allow_not_converged=True)
+        x0 = sr_update(h, y, tau, store)
+        rec = {"iteration": it, "E_mean": float(es[0]), "E_var": float(es[1]), "E_err": float(es[2]),
+               "x0": x0, "cg": info}
+        hist.append(rec)
+        if callback is not None:
+            callback(rec)
+    return hist
 
 
 # ---------------------------------------------------------------------------

@@ -5,6 +5,7 @@ known-answer vectors, closed forms, library routines, exact eigenstates,
 structural invariants of Eq. 3 / Eq. 7 / Eq. 11, or brute force on tiny
 Hilbert spaces.  None of these need a GPU.
 """
+import copy
 import itertools
 import os
 
@@ -412,6 +413,66 @@ def test_exact_enumeration_gradient_and_S():
     S_ex = (O_all * w[:, None]).T @ O_all - np.outer(Ob_ex, Ob_ex)
     assert np.allclose(S_ex, S_ex.T)
     assert np.linalg.eigvalsh(S_ex).min() > -1e-12
+
+
+def test_sr_update_solves_the_full_projection():
+    """Sec. II.A update: solving the whole Eq. 2 system (row 0 with O_0 = 1
+    included, eps on the derivative block only) by a dense solve gives the
+    same x_0 and new parameters as the eliminated covariance solve plus the
+    x_0 formula of the oracle."""
+    wl, P, samples, E, O = _small_samples(seed=47, nw=16, spw=8)
+    n, nv = O.shape
+    eps, tau = 1e-3, 0.05
+    Ob = O.mean(0)
+    Oa = np.hstack([np.ones((n, 1)), O])                      # O_0 = 1
+    G = Oa.T @ Oa / n
+    G[1:, 1:] += eps * np.eye(nv)
+    b = Oa.mean(0) - tau * (E[:, None] * Oa).mean(0)          # <Psi^i|(1 - tau H)|Psi> / <Psi|Psi>
+    xf = np.linalg.solve(G, b)
+    alpha = np.concatenate([wl.C, wl.f])
+    ref = alpha + xf[1:] / xf[0]
+    g, Em = oracle.gradient(O, E)
+    y = np.linalg.solve(O.T @ O / n - np.outer(Ob, Ob) + eps * np.eye(nv), g)
+    out, x0 = oracle.sr_update(alpha, y, tau, Em, Ob)
+    assert x0 == pytest.approx(xf[0], rel=1e-10)
+    assert np.linalg.norm(out - ref) <= 1e-10 * np.linalg.norm(ref)
+    # no step for tau = 0
+    out0, x00 = oracle.sr_update(alpha, y, 0.0, Em, Ob)
+    assert x00 == 1.0 and np.array_equal(out0, alpha)
+
+
+def test_sr_update_lowers_the_exact_energy_at_first_order():
+    """With exact (enumerated) E, g and S on a 2x2 lattice the update moves
+    alpha by -tau y / x_0, y = (S + eps)^-1 g, and the exact energy changes by
+    2 g . dalpha + O(tau^2) (g is half the energy gradient): it goes down."""
+    wl = inputs.hubbard("ex", 2, 2, 2, 2, "2x2", seed=53, n_walkers=8)
+    P = oracle.Problem(wl)
+    occ_all, w = P.enumerate()
+    E_all, O_all = P.measure(occ_all)
+    E_ex = w @ E_all
+    Ob = w @ O_all
+    g = w @ (E_all[:, None] * O_all) - E_ex * Ob
+    S = (O_all * w[:, None]).T @ O_all - np.outer(Ob, Ob)
+    eps = 1e-3
+    y = np.linalg.solve(S + eps * np.eye(len(g)), g)
+    alpha = np.concatenate([wl.C, wl.f])
+    nc = len(wl.C)
+
+    def exact_energy(a):
+        wl2 = copy.copy(wl)
+        wl2.C, wl2.f = a[:nc].copy(), a[nc:].copy()
+        P2 = oracle.Problem(wl2)
+        o2, w2 = P2.enumerate()
+        return w2 @ P2.measure(o2)[0]
+
+    slopes = []
+    for tau in (1e-3, 1e-4):
+        a2, x0 = oracle.sr_update(alpha, y, tau, E_ex, Ob)
+        dE = exact_energy(a2) - E_ex
+        assert dE < 0
+        slopes.append(dE / tau)
+        assert dE == pytest.approx(2 * g @ (a2 - alpha), rel=5e-2)
+    assert slopes[1] == pytest.approx(-2 * g @ y, rel=1e-2)
 
 
 def test_sampler_matches_exact_distribution():
