@@ -98,6 +98,12 @@ class Clocks:
 # GPU arm
 # ---------------------------------------------------------------------------
 
+# DRAM bytes read per sorted BF16 product (k_gather_G + k_scatter_T launches) on
+# this workload, as counted by ncu (dram__bytes): G 418 MB + T and correlator
+# runs 427 MB.
+SORTED_PASS_DRAM_BYTES = 845.0e6
+
+
 def run_gpu(args, rank, world, dist):
     import torch
     from paper_1108_0900_gb300 import inputs
@@ -224,7 +230,9 @@ def run_gpu(args, rank, world, dist):
                      "frac": round(ach / peak, 4) if ach else None, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": per_launch_bytes,
                      "launches": prof["pass_launches"] if prof else None,
-                     "traffic": None},
+                     # DRAM bytes per pass (gather + scatter) from the ncu capture summarised in
+                     # profiles/k_gather_G_k_scatter_T_bf16_cfg5.md
+                     "traffic": SORTED_PASS_DRAM_BYTES},
         "e2e": {"value": round(float(np.median(e2e_ms)) / 1e3, 6), "unit": "s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(prof["launches_all"]) if prof else None,
