@@ -226,6 +226,21 @@ int sr_cg_solve(vmc_handle h, const double* g, double shift, double tol, int max
  * parameter is not finite; SINGULAR when an updated C is zero. */
 int sr_update(vmc_handle h, const double* y, double tau, int store, double* x0, void* stream);
 
+/* Rank-local sums for a solve whose samples are spread over several processes
+ * (the paper distributes the samples over processors, Sec. II.A): a sum
+ * all-reduce of these over the ranks gives the global moments and products.
+ * sr_local_moments: sumO = sum_s O_s and sumEO = sum_s E_L(s) O_s (device
+ * [n_v] FP64), scal = {sum_s E_L(s), n_s} (host), FP64 accumulation over
+ * `store`; it also leaves this rank's own Obar in the handle.
+ * sr_local_product: out = sum_s (O_s . v) O_s over this rank's samples
+ * (device v, out [n_v] FP64; FP64 accumulation over the FP64 or FP32 store;
+ * sr_local_moments or sr_gradient must have run over that store).  The global
+ * (S + shift I) v is then (sum over ranks of out) / N - Obar (Obar . v) +
+ * shift v with the global N and Obar.  Errors: STATE without samples or
+ * moments. */
+int sr_local_moments(vmc_handle h, double* sumO, double* sumEO, double* scal, int store, void* stream);
+int sr_local_product(vmc_handle h, const double* v, double* out, int store, void* stream);
+
 /* Measurement support (no counterpart in the paper).  vmc_profile(h, 1)
  * resets the counters and starts recording: every kernel the handle launches
  * is counted, and each launch of the O-store streaming kernel (the Eq. 7

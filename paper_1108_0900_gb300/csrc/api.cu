@@ -945,12 +945,13 @@ static int launch_sorted(vmc_ctx* h, const float* V, const float* invC, const do
     auto gk = gather_kernel<K>((int)((h->Pst / 4 + 31) / 32));
     VCK(cudaFuncSetAttribute(gk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    VCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gk, 256, smem));
+    const int gthreads = gather_threads(K), gwarps = gthreads / 32;
+    VCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gk, gthreads, smem));
     int grid = h->nsm * std::max(1, per_sm);
-    const int64_t need = (h->n_s + 7) / 8;
+    const int64_t need = (h->n_s + gwarps - 1) / gwarps;
     if (need < grid) grid = (int)std::max<int64_t>(1, need);
     grid = std::min(grid, kNumPart * kMaxK);   // one partial slot of tt sums
-    gk<<<grid, 256, smem, st>>>(a); h->n_launch++;
+    gk<<<grid, gthreads, smem, st>>>(a); h->n_launch++;
     h->last_gather_grid = grid;
     k_scatter_T<K><<<(int)((h->ncp + 255) / 256) + (h->npf + 7) / 8, 256, 0, st>>>(a); h->n_launch++;
     VCK(cudaGetLastError());
@@ -1453,6 +1454,51 @@ extern "C" int sr_update(vmc_handle h, const double* y, double tau, int store, d
     int rc = read_status(h, st);   // synchronizes the stream
     if (x0) *x0 = h->h_pinned[1];
     return rc;
+}
+
+// ---------------------------------------------------------------------------
+// rank-local sums for a sample-sharded solve
+// ---------------------------------------------------------------------------
+
+extern "C" int sr_local_moments(vmc_handle h, double* sumO, double* sumEO, double* scal, int store, void* stream) {
+    if (!h || !sumO || !sumEO || !scal) return VMC_ERR_INVALID_ARG;
+    const int kind = store_kind(store);
+    if (kind < 0) return VMC_ERR_INVALID_ARG;
+    if (h->n_s == 0) return VMC_ERR_STATE;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = gradient_pass(h, kind, h->d_t64, st);   // Obar[kind], g, E partial sums in part(1)
+    if (rc) return rc;
+    std::vector<double> parts(kNumPart);
+    VCK(cudaMemcpyAsync(parts.data(), h->part(1), sizeof(double) * kNumPart, cudaMemcpyDeviceToHost, st));
+    VCK(cudaStreamSynchronize(st));
+    double sE = 0.0;
+    for (double v : parts) sE += v;
+    const double n = (double)h->n_s;
+    // sum O = n Obar; sum E O = n g + (sum E) Obar
+    k_cast<double><<<kNumPart, 256, 0, st>>>(h->d_Obar[kind], sumO, h->nv, n); h->n_launch++;
+    k_cast<double><<<kNumPart, 256, 0, st>>>(h->d_t64, sumEO, h->nv, n); h->n_launch++;
+    k_axpby<<<kNumPart, 256, 0, st>>>(sE, h->d_Obar[kind], 1.0, sumEO, h->nv); h->n_launch++;
+    VCK(cudaGetLastError());
+    scal[0] = sE;
+    scal[1] = n;
+    return VMC_OK;
+}
+
+extern "C" int sr_local_product(vmc_handle h, const double* v, double* out, int store, void* stream) {
+    if (!h || !v || !out) return VMC_ERR_INVALID_ARG;
+    if (store != VMC_STORE_FP64 && store != VMC_STORE_FP32) return VMC_ERR_INVALID_ARG;
+    const int kind = store_kind(store);
+    if (h->n_s == 0 || !store_ptr(h, kind) || !h->obar_ok[kind]) return VMC_ERR_STATE;
+    cudaStream_t st = (cudaStream_t)stream;
+    // out = S v with shift 0 (uncentered pass, covariance term in the finalize),
+    // then back to the plain sum; Obar . v is left in part(0) by the product
+    int rc = kind == 0 ? apply_S_impl<double, double, 1>(h, h->d_pf64, kind, v, out, 0.0, nullptr, nullptr, nullptr, st)
+                       : apply_S_impl<float, double, 1>(h, h->d_pf32, kind, v, out, 0.0, nullptr, nullptr, nullptr, st);
+    if (rc) return rc;
+    k_uncenter<<<kNumPart, 256, 0, st>>>(out, h->d_Obar[kind], h->part(0), vgrid(h, 1), (double)h->n_s, h->nv);
+    h->n_launch++;
+    VCK(cudaGetLastError());
+    return VMC_OK;
 }
 
 // ---------------------------------------------------------------------------

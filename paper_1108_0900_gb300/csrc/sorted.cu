@@ -241,7 +241,7 @@ __device__ __forceinline__ void corr_lookups(const DevProblem& pb, const int* co
 // sample's row before the correlator lookups and before consuming any, so a
 // whole row (6 KB at 56 electrons) is in flight per warp.
 template <int K, int U>
-__global__ void __launch_bounds__(256) k_gather_G(SortedArgs a) {
+__global__ void __launch_bounds__(gather_threads(K)) k_gather_G(SortedArgs a) {
     if (a.stop && *a.stop) return;
     extern __shared__ __align__(16) unsigned char smem[];
     const DevProblem& pb = a.pb;

@@ -576,6 +576,20 @@ __global__ void __launch_bounds__(256) k_sr_update(UpdateArgs a) {
     if (bad) atomicOr(a.status, bad);
 }
 
+// out = n (out + Obar (Obar . v)): undo the covariance term of a product
+// formed with shift 0, leaving the plain sum_s (O_s . v) O_s
+__global__ void __launch_bounds__(256) k_uncenter(double* out, const double* Obar, const double* obv_part, int nobv,
+                                                  double n_s, int64_t nv) {
+    __shared__ double obv;
+    if (threadIdx.x < 32) {
+        const double s = warp_sum_partials(obv_part, nobv, 0, 1);
+        if (threadIdx.x == 0) obv = s;
+    }
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = n_s * (out[i] + Obar[i] * obv);
+}
+
 // y = a - b (FP64)
 __global__ void k_sub(const double* a, const double* b, double* y, int64_t n, double* part) {
     double loc[1] = {0.0};

@@ -94,6 +94,8 @@ def lib(build_if_missing: bool = True):
         "vmc_set_params": [vp, vp, vp],
         "vmc_get_params": [vp, vp, vp, vp],
         "sr_update": [vp, vp, dbl, i32, vp, vp],
+        "sr_local_moments": [vp, vp, vp, vp, i32, vp],
+        "sr_local_product": [vp, vp, vp, i32, vp],
         "vmc_set_walkers": [vp, vp, vp],
         "vmc_get_walkers": [vp, vp, vp, vp],
         "vmc_sample": [vp, i32, u64, vp],
@@ -311,6 +313,26 @@ def sr_update(h: Handle, y, tau: float, store=VMC_STORE_FP64, stream=None):
     x0 = ct.c_double()
     _check(lib().sr_update(h.h, _dev_ptr(y), float(tau), int(store), ct.byref(x0), _stream(stream)), "sr_update")
     return x0.value
+
+
+def sr_local_moments(h: Handle, store=VMC_STORE_FP64, stream=None):
+    """Rank-local (sum O, sum E_L O, sum E_L, n_s) for a sample-sharded solve."""
+    import torch
+    sO = torch.empty(h.n_params, dtype=torch.float64, device="cuda")
+    sEO = torch.empty_like(sO)
+    sc = np.zeros(2)
+    _check(lib().sr_local_moments(h.h, _dev_ptr(sO), _dev_ptr(sEO), _np_ptr(sc), int(store), _stream(stream)),
+           "sr_local_moments")
+    return sO, sEO, float(sc[0]), int(sc[1])
+
+
+def sr_local_product(h: Handle, v, store=VMC_STORE_FP64, stream=None, out=None):
+    """Rank-local sum_s (O_s . v) O_s for a sample-sharded solve."""
+    import torch
+    if out is None:
+        out = torch.empty_like(v)
+    _check(lib().sr_local_product(h.h, _dev_ptr(v), _dev_ptr(out), int(store), _stream(stream)), "sr_local_product")
+    return out
 
 
 def sr_optimize(h: Handle, n_iter: int, tau: float, shift: float, tol: float, mode=VMC_CG_FP64, seed: int = 1,

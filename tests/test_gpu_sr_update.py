@@ -201,3 +201,47 @@ def test_free_fermion_state_is_a_fixed_point():
     step = np.linalg.norm(np.concatenate([C - 1.0, f1 - f]))
     assert step <= 1.1 * tau * gn / 1e-3 / x0 + 1e-14   # |y| <= |g| / eps
     h.close()
+
+
+class _SumLocal:
+    """Two handles standing for two ranks; summing their local sums is what
+    the all-reduce does across processes."""
+
+    def __init__(self, a, b):
+        self.a, self.b = a, b
+
+    def moments(self):
+        m1, m2 = self.a.moments(), self.b.moments()
+        return m1[0] + m2[0], m1[1] + m2[1], m1[2] + m2[2], m1[3] + m2[3]
+
+    def product(self, v):
+        return self.a.product(v) + self.b.product(v)
+
+
+@pytest.mark.parametrize("store", [V.VMC_STORE_FP64, V.VMC_STORE_FP32])
+def test_rank_local_sums_add_up_to_the_whole(store):
+    from paper_1108_0900_gb300 import shard
+    wl = CASES["cfg1"]()
+    P = oracle.Problem(wl)
+    occ = wl.init_occ.copy()
+    step = np.zeros(wl.n_walkers, np.uint64)
+    smp, _, _ = P.sample(occ, step, 91, 3, wl.samples_per_walker)
+    E, O = P.measure(smp)
+    halves = []
+    for r in range(2):
+        h = V.vmc_create(wl, walker_precision=V.VMC_FP64, keep_fp64_store=True, keep_lowp_store=True)
+        V.vmc_set_params(h, wl.C, wl.f)
+        V.vmc_measure(h, np.ascontiguousarray(smp[r::2]))
+        halves.append(h)
+    loc = _SumLocal(*(shard.LibraryLocal(h, store) for h in halves))
+    res = shard.sr_step(loc, 0.05, 1e-3, 1e-10, 5000, reduce=lambda t: t)
+    g_ref, Em = oracle.gradient(O, E)
+    y_ref, _, _, ok = oracle.cg(O, g_ref, 1e-3, 1e-10)
+    tol = 1e-8 if store == V.VMC_STORE_FP64 else 1e-5
+    assert res["n"] == len(E) and res["E_mean"] == pytest.approx(Em, rel=1e-12)
+    assert rel(res["g"].cpu().numpy(), g_ref) <= (1e-10 if store == V.VMC_STORE_FP64 else 1e-6)
+    assert rel(res["y"].cpu().numpy(), y_ref) <= tol
+    _, x0_ref = oracle.sr_update(np.zeros(wl.n_params), y_ref, 0.05, Em, O.mean(0))
+    assert res["x0"] == pytest.approx(x0_ref, rel=tol)
+    for h in halves:
+        h.close()
