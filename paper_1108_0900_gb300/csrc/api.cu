@@ -52,6 +52,7 @@ struct vmc_ctx {
     int last_gather_grid = 0;    // CTAs (tt partials) of the last sorted gather
     bool sorted_ok = false;      // G / T built for the current samples
     int sort_nblk = 0, sort_nchunk = 0;
+    size_t t_chunk = 0;          // T entries reserved per 65,536-sample chunk
     bool obar_ok[3] = {false, false, false};  // per store: FP64, FP32, BF16
     std::vector<int64_t> corr_off;
 
@@ -350,7 +351,8 @@ extern "C" int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, co
         h->sort_nblk = 2 * h->nsm;
         h->sort_nchunk = (int)((h->ncap + 65535) / 65536);
         ACK(h->alloc(&h->d_G, (size_t)h->ncap * h->Pst));
-        ACK(h->alloc(&h->d_Tsort, (size_t)h->ncap * h->P));
+        h->t_chunk = (size_t)65536 * h->P + (size_t)h->npf * kTRun;   // padded runs of one chunk
+        ACK(h->alloc(&h->d_Tsort, (size_t)h->sort_nchunk * h->t_chunk));
         ACK(h->alloc(&h->d_counts, (size_t)h->sort_nblk * h->npf));
         ACK(h->alloc(&h->d_total, (size_t)h->npf));
         ACK(h->alloc(&h->d_base, (size_t)h->sort_nchunk * (h->npf + 1)));
@@ -858,15 +860,17 @@ static int ensure_sorted(vmc_ctx* h, cudaStream_t st) {
     VCK(cudaGetLastError());
     const size_t smem = (size_t)h->npf * 4;
     VCK(cudaFuncSetAttribute(k_count_G, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    VCK(cudaFuncSetAttribute(k_fill_T, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    VCK(cudaFuncSetAttribute(k_fill_T, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * smem)));
     const int nchunk = (int)((h->n_s + 65535) / 65536);
+    // run padding must read as weight 0
+    VCK(cudaMemsetAsync(h->d_Tsort, 0, sizeof(uint32_t) * h->t_chunk * nchunk, st));
     for (int c = 0; c < nchunk; ++c) {
         const int64_t sb = (int64_t)c * 65536, se = std::min<int64_t>(h->n_s, sb + 65536);
         uint32_t* base = h->d_base + (size_t)c * (h->npf + 1);
         k_count_G<<<h->sort_nblk, 512, smem, st>>>(h->d_G, h->Pst, h->P, sb, se, h->npf, h->d_counts); h->n_launch++;
         k_scan_blocks<<<(h->npf + 255) / 256, 256, 0, st>>>(h->d_counts, h->sort_nblk, h->npf, h->d_total); h->n_launch++;
-        k_scan_params<<<1, 1024, 0, st>>>(h->d_total, h->npf, (uint32_t)(sb * h->P), base); h->n_launch++;
-        k_fill_T<<<h->sort_nblk, 512, smem, st>>>(h->d_G, h->Pst, h->P, sb, se, h->npf, h->d_counts, base,
+        k_scan_params<<<1, 1024, 0, st>>>(h->d_total, h->npf, (uint32_t)(c * h->t_chunk), base); h->n_launch++;
+        k_fill_T<<<h->sort_nblk, 512, 2 * smem, st>>>(h->d_G, h->Pst, h->P, sb, se, h->npf, h->d_counts, base,
                                                   h->d_Tsort); h->n_launch++;
         VCK(cudaGetLastError());
     }

@@ -257,6 +257,7 @@ struct SortedArgs {
 };
 
 constexpr int kCorrPerLane = 4;    // the sorted gather handles up to 128 correlators
+constexpr int kTRun = 128;         // T runs are padded to whole blocks of this many entries
 
 __global__ void __launch_bounds__(256) k_build_G(DevProblem pb, int64_t n_s, const uint8_t* s_occ, int Nst,
                                                  const __nv_bfloat16* pf16, int64_t Pst, uint32_t* G);

@@ -9,7 +9,8 @@
 //      t_s = sum_e W_e v[pq(e)] is a pure stream with a shared-memory lookup of
 //      v and no atomics;
 //   T  u32 entries (s_local << 16) | bf16 value, parameter-major per chunk of
-//      at most 65,536 samples (a counting sort of G by pq): the scatter
+//      at most 65,536 samples (a counting sort of G by pq), each run padded to
+//      whole 128-entry blocks and interleaved inside a block: the scatter
 //      out[pq] = sum_s t_s W_s[pq] is one warp per parameter summing a
 //      contiguous run, with no atomics and no per-CTA partial images.
 //
@@ -125,7 +126,8 @@ __global__ void __launch_bounds__(512) k_count_G(const uint32_t* G, int64_t Pst,
     for (int i = threadIdx.x; i < npf; i += blockDim.x) counts[(size_t)blockIdx.x * npf + i] = cnt[i];
 }
 
-// per parameter: running offsets over the blocks (in place) and the total
+// per parameter: running offsets over the blocks (in place) and the run
+// length padded to a whole number of kTRun-entry blocks
 __global__ void k_scan_blocks(uint32_t* counts, int nblk, int npf, uint32_t* total) {
     const int pq = blockIdx.x * blockDim.x + threadIdx.x;
     if (pq >= npf) return;
@@ -135,7 +137,16 @@ __global__ void k_scan_blocks(uint32_t* counts, int nblk, int npf, uint32_t* tot
         counts[(size_t)b * npf + pq] = run;
         run += c;
     }
-    total[pq] = run;
+    total[pq] = (run + kTRun - 1) / kTRun * kTRun;
+}
+
+// Position inside a run of logical entry r.  Within each kTRun = 128 entry
+// block, entry 32 j + L sits at 4 L + j, so lane L's 16-byte word holds
+// entries L, L + 32, L + 64, L + 96 and the j-th lookup instruction of the
+// scatter covers 32 consecutive entries (consecutive, sorted samples: a few
+// cache lines instead of 32).
+__device__ __forceinline__ uint32_t run_slot(uint32_t r) {
+    return (r & ~(uint32_t)(kTRun - 1)) + 4u * (r & 31u) + ((r >> 5) & 3u);
 }
 
 // base[pq] = exclusive prefix of total over pq (single block), base[npf] = sum
@@ -162,12 +173,17 @@ __global__ void __launch_bounds__(1024) k_scan_params(const uint32_t* total, int
     if (threadIdx.x == blockDim.x - 1) base[npf] = base0 + part[blockDim.x - 1];
 }
 
-// T[base[pq] + offset[b][pq] + k] = (s - s_begin) << 16 | bf16, in block order
+// T[base[pq] + run_slot(offset[b][pq] + k)] = (s - s_begin) << 16 | bf16, in
+// block order; the padding of each run stays zero (weight 0)
 __global__ void __launch_bounds__(512) k_fill_T(const uint32_t* G, int64_t Pst, int P, int64_t s_begin,
                                                 int64_t s_end, int npf, const uint32_t* offs, const uint32_t* base,
                                                 uint32_t* T) {
     extern __shared__ uint32_t cur[];
-    for (int i = threadIdx.x; i < npf; i += blockDim.x) cur[i] = base[i] + offs[(size_t)blockIdx.x * npf + i];
+    uint32_t* rb = cur + npf;
+    for (int i = threadIdx.x; i < npf; i += blockDim.x) {
+        cur[i] = offs[(size_t)blockIdx.x * npf + i];
+        rb[i] = base[i];
+    }
     __syncthreads();
     int64_t lo, hi;
     block_range(s_begin, s_end, gridDim.x, &lo, &hi);
@@ -177,8 +193,9 @@ __global__ void __launch_bounds__(512) k_fill_T(const uint32_t* G, int64_t Pst, 
         for (int e = threadIdx.x; e < Pst; e += blockDim.x) {
             const uint32_t v = g[e];
             if (!v) continue;
-            const uint32_t pos = atomicAdd(&cur[v >> 16], 1u);
-            T[pos] = sl | (v & 0xFFFFu);
+            const uint32_t pq = v >> 16;
+            const uint32_t r = atomicAdd(&cur[pq], 1u);
+            T[rb[pq] + run_slot(r)] = sl | (v & 0xFFFFu);
         }
     }
 }
@@ -326,8 +343,10 @@ __device__ __forceinline__ void scatter_entry(const float* __restrict__ Tv, int6
 }
 
 // scatter: raw[pq][kk] = sum over samples containing pq of W t_s for the warp's
-// pq.  The run [lo, hi) of T is read as an unaligned head, 16-byte loads (2
-// per lane per step, 256 entries per warp in flight) and a tail.
+// pq.  A run is a whole number of kTRun-entry blocks starting on a 512-byte
+// boundary (padding entries weigh zero); lane L's 16-byte word of a block
+// holds entries L, L + 32, L + 64, L + 96, so each t_s lookup instruction
+// covers 32 consecutive entries.  Two blocks (256 entries) per warp in flight.
 template <int K>
 __device__ __forceinline__ void scatter_T_param(const SortedArgs& a, int pq) {
     const int lane = threadIdx.x & 31;
@@ -337,11 +356,8 @@ __device__ __forceinline__ void scatter_T_param(const SortedArgs& a, int pq) {
     const uint4* T4 = (const uint4*)a.T;
     for (int c = 0; c < a.nchunk; ++c) {
         const uint32_t* base = a.base + (size_t)c * (a.pb.npf + 1);
-        const uint32_t lo = base[pq], hi = base[pq + 1];
+        const uint32_t q0 = base[pq] >> 2, q1 = base[pq + 1] >> 2;
         const int64_t s0 = (int64_t)c * 65536;
-        const uint32_t a4 = min(hi, (lo + 3u) & ~3u);   // end of the head
-        const uint32_t q0 = a4 >> 2, q1 = a4 < hi ? hi >> 2 : q0;
-        if (lo + lane < a4) scatter_entry<K>(a.Tv, s0, __ldcs(a.T + lo + lane), acc);
         uint32_t q = q0 + lane;
         for (; q + 32 < q1; q += 64) {
             const uint4 u0 = __ldcs(T4 + q), u1 = __ldcs(T4 + q + 32);
@@ -361,8 +377,6 @@ __device__ __forceinline__ void scatter_T_param(const SortedArgs& a, int pq) {
             scatter_entry<K>(a.Tv, s0, u0.z, acc);
             scatter_entry<K>(a.Tv, s0, u0.w, acc2);
         }
-        const uint32_t t0 = max(a4, q1 << 2);           // start of the tail
-        if (t0 + lane < hi) scatter_entry<K>(a.Tv, s0, __ldcs(a.T + t0 + lane), acc2);
     }
 #pragma unroll
     for (int kk = 0; kk < K; ++kk) {
