@@ -226,7 +226,12 @@ __global__ void __launch_bounds__(512) k_fill_C(DevProblem pb, int64_t n_s, cons
     for (int i = threadIdx.x; i < d; i += blockDim.x) cur[i] = cbase[off + i];
     __syncthreads();
     const uint16_t* st = cidxT + (int64_t)c * n_s;
-    for (int64_t s = threadIdx.x; s < n_s; s += blockDim.x) Tc[atomicAdd(&cur[st[s]], 1u)] = (uint32_t)s;
+    // entry = sample << 5 | (parameter index mod 32): the scatter's warps own
+    // 32 consecutive parameters and sum each one's contiguous segment
+    for (int64_t s = threadIdx.x; s < n_s; s += blockDim.x) {
+        const uint32_t state = st[s];
+        Tc[atomicAdd(&cur[state], 1u)] = ((uint32_t)s << 5) | (uint32_t)((off + state) & 31);
+    }
 }
 
 // Correlator part of the gather for one sample: lane L looks up V[k_c] / C[k_c]
@@ -385,39 +390,61 @@ __device__ __forceinline__ void scatter_T_param(const SortedArgs& a, int pq) {
     }
 }
 
-// correlator state k: raw[k] = sum over the samples in state k of t_s (the
-// 1/C factor is applied by the caller), one thread per state
+// correlator states 32 w .. 32 w + 31: raw[k] = sum over the samples in state
+// k of t_s (the 1/C factor is applied by the caller).  The 32 runs are
+// contiguous, so the warp reads them as one coalesced stream; entries carry
+// k mod 32, equal values are contiguous, and a segmented warp scan hands each
+// segment's sum to its last lane, which adds it to the state's slot in shared
+// memory (one writer per state per step).
 template <int K>
-__device__ __forceinline__ void scatter_C_state(const SortedArgs& a, int64_t k) {
-    const uint32_t lo = a.cbase[k], hi = a.cbase[k + 1];
-    float acc[K];
+__device__ __forceinline__ void scatter_C_group(const SortedArgs& a, int64_t w, float* slot) {
+    const int lane = threadIdx.x & 31;
+    const int64_t k0 = w * 32;
+    const int64_t kend = min(a.pb.ncp, k0 + 32);
 #pragma unroll
-    for (int kk = 0; kk < K; ++kk) acc[kk] = 0.f;
-    for (uint32_t j = lo; j < hi; j += 4) {
-        uint32_t sv[4];
+    for (int kk = 0; kk < K; ++kk) slot[lane * K + kk] = 0.f;
+    __syncwarp();
+    const uint32_t lo = a.cbase[k0], hi = a.cbase[kend];
+    for (uint32_t e0 = lo; e0 < hi; e0 += 32) {
+        const uint32_t e = e0 + lane;
+        const bool in = e < hi;
+        const uint32_t v = in ? __ldcs(a.Tc + e) : 0u;
+        const int ls = in ? (int)(v & 31u) : 32 + lane;        // past the end: a segment of its own
+        float t[K];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) sv[u] = j + u < hi ? __ldcs(a.Tc + j + u) : 0xFFFFFFFFu;
+        for (int kk = 0; kk < K; ++kk) t[kk] = in ? __ldg(a.Tv + (int64_t)(v >> 5) * K + kk) : 0.f;
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (sv[u] != 0xFFFFFFFFu)
+        for (int o = 1; o < 32; o <<= 1) {
+            const int lo_ls = __shfl_up_sync(0xffffffffu, ls, o);
 #pragma unroll
-                for (int kk = 0; kk < K; ++kk) acc[kk] += __ldg(a.Tv + (int64_t)sv[u] * K + kk);
+            for (int kk = 0; kk < K; ++kk) {
+                const float u = __shfl_up_sync(0xffffffffu, t[kk], o);
+                if (lane >= o && lo_ls == ls) t[kk] += u;
+            }
+        }
+        const int next_ls = __shfl_down_sync(0xffffffffu, ls, 1);
+        if (in && (lane == 31 || next_ls != ls))
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) slot[ls * K + kk] += t[kk];
+        __syncwarp();
     }
+    if (k0 + lane < kend)
 #pragma unroll
-    for (int kk = 0; kk < K; ++kk) a.craw[k * K + kk] = acc[kk];
+        for (int kk = 0; kk < K; ++kk) a.craw[(k0 + lane) * K + kk] = slot[lane * K + kk];
 }
 
 // Both halves of the scatter in one launch: CTAs [0, ncb) take 256
-// correlator states each (a thread per state), the rest one pairing
+// correlator states each (a warp per 32 states), the rest one pairing
 // amplitude per warp.  The short correlator CTAs go first so that they do
 // not form a tail behind the long pairing runs.
 template <int K>
 __global__ void __launch_bounds__(256) k_scatter_T(SortedArgs a) {
     if (a.stop && *a.stop) return;
+    __shared__ float slots[8][32 * K];
     const int ncb = (int)((a.pb.ncp + 255) / 256);
     if ((int)blockIdx.x < ncb) {
-        const int64_t k = (int64_t)blockIdx.x * 256 + threadIdx.x;
-        if (k < a.pb.ncp) scatter_C_state<K>(a, k);
+        const int64_t w = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+        if (w * 32 < a.pb.ncp) scatter_C_group<K>(a, w, slots[threadIdx.x >> 5]);
         return;
     }
     const int pq = ((int)blockIdx.x - ncb) * (blockDim.x >> 5) + (threadIdx.x >> 5);
