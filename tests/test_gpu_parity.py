@@ -446,3 +446,33 @@ def test_full_size_sampling_run():
     assert np.all(np.diff(occ.astype(int), axis=1) > 0)
     _, step = V.vmc_get_walkers(h)
     assert np.all(step == (2 + wl.samples_per_walker) * wl.N)
+
+
+def test_bf16_product_over_several_sample_chunks():
+    """The sorted BF16 product splits its parameter-major copy into chunks of
+    65,536 samples; with 132,096 samples (two full chunks and a ragged third)
+    it must equal the FP64 product of the same stored BF16 values
+    (FP32 accumulation: 2e-5)."""
+    sp = pytest.importorskip("scipy.sparse")
+    wl = inputs.config(1, n_walkers=16512, samples_per_walker=8)
+    n = wl.n_walkers * wl.samples_per_walker
+    assert n > 2 * 65536
+    cfgs = inputs.draw_configs(np.random.default_rng(31), n, wl.n_sites, wl.n_up, wl.n_dn)
+    h = make(wl)
+    V.vmc_measure(h, cfgs)
+    V.sr_gradient(h, V.VMC_STORE_BF16)
+    occ, _, cs, pf = V.vmc_get_samples(h, V.VMC_STORE_BF16)
+    M, ncp = wl.M, wl.n_corr_params
+    off = np.concatenate([[0], np.cumsum([4 ** len(c) for c in wl.corr_sites])])
+    pl = np.array(pair_list(wl))
+    p, q = occ[:, pl[:, 0]].astype(np.int64), occ[:, pl[:, 1]].astype(np.int64)
+    cols = np.hstack([off[None, :-1] + cs.astype(np.int64), ncp + p * M - p * (p + 1) // 2 + (q - p - 1)])
+    vals = np.hstack([1.0 / wl.C[off[None, :-1] + cs.astype(np.int64)], pf])
+    O = sp.csr_matrix((vals.ravel(), cols.ravel(), np.arange(0, vals.size + 1, vals.shape[1])),
+                      shape=(n, wl.n_params))
+    Ob = np.asarray(O.mean(0)).ravel()
+    v = np.random.default_rng(8).standard_normal(wl.n_params)
+    ref = O.T @ (O @ v) / n - Ob * (Ob @ v) + wl.shift * v
+    out = V.sr_apply_S(h, torch.from_numpy(v).cuda(), wl.shift, V.VMC_STORE_BF16).cpu().numpy()
+    assert rel(out, ref) <= 2e-5
+    h.close()
