@@ -97,13 +97,20 @@ typedef struct {
 
 /* Ansatz (Eq. 11): sector (n_up, n_dn) with n_up + n_dn even and <= 64, and
  * correlator site lists corr_sites[corr_ptr[c] .. corr_ptr[c+1]) (each <= 6
- * sites, host arrays).  The pairing runs over all spin orbitals. */
+ * sites, host arrays).  The pairing runs over all spin orbitals.
+ * corr_class[n_corr] (host, may be NULL = every correlator its own class)
+ * lets correlators share parameters: the correlators of one class (the
+ * translates of one correlator, as in Sec. III.A's translationally invariant
+ * 3x3 correlators) read one block of 4^m amplitudes, so O of a shared
+ * amplitude sums over them.  Classes are numbered 0 .. n_class-1, all used,
+ * with one site count per class; the parameter blocks follow class order. */
 typedef struct {
     int n_up;
     int n_dn;
     int n_corr;
     const int32_t* corr_ptr;
     const int32_t* corr_sites;
+    const int32_t* corr_class;
 } vmc_ansatz;
 
 typedef struct {

@@ -44,7 +44,7 @@ class _Problem(ct.Structure):
         ("n_bonds", ct.c_int), ("bonds", ct.c_void_p), ("bond_t", ct.c_void_p),
         ("U", ct.c_double), ("n_chol", ct.c_int), ("h", ct.c_void_p), ("chol", ct.c_void_p),
         ("n_corr", ct.c_int), ("corr_ptr", ct.c_void_p), ("corr_sites", ct.c_void_p),
-        ("C", ct.c_void_p), ("f", ct.c_void_p),
+        ("corr_class", ct.c_void_p), ("C", ct.c_void_p), ("f", ct.c_void_p),
     ]
 
 
@@ -108,6 +108,8 @@ class Problem:
             bond_t=np.ascontiguousarray(wl.bond_t, np.float64),
             corr_ptr=np.ascontiguousarray(wl.corr_ptr, np.int32),
             corr_sites=np.ascontiguousarray(wl.corr_flat, np.int32),
+            corr_class=None if getattr(wl, "corr_class", None) is None
+            else np.ascontiguousarray(wl.corr_class, np.int32),
             C=np.ascontiguousarray(wl.C, np.float64),
             f=np.ascontiguousarray(wl.f, np.float64),
             h=None if wl.h is None else np.ascontiguousarray(wl.h, np.float64),
@@ -120,7 +122,7 @@ class Problem:
             U=float(wl.U), n_chol=0 if wl.chol is None else wl.chol.shape[0],
             h=_ptr(k["h"]), chol=_ptr(k["chol"]),
             n_corr=wl.n_corr, corr_ptr=_ptr(k["corr_ptr"]), corr_sites=_ptr(k["corr_sites"]),
-            C=_ptr(k["C"]), f=_ptr(k["f"]))
+            corr_class=_ptr(k["corr_class"]), C=_ptr(k["C"]), f=_ptr(k["f"]))
 
     @property
     def ref(self):

@@ -142,13 +142,14 @@ int orc_inverse(int n, const double* A_in, double* X)
 
 static int n_orb_M(const orc_problem* P) { return 2 * P->n_sites; }
 
+static void corr_offsets(const orc_problem* P, int64_t* off);
+
 int64_t orc_n_corr_params(const orc_problem* P)
 {
-    int64_t n = 0;
-    for (int c = 0; c < P->n_corr; ++c) {
-        int m = P->corr_ptr[c + 1] - P->corr_ptr[c];
-        n += (int64_t)1 << (2 * m);
-    }
+    int64_t* off = (int64_t*)malloc(sizeof(int64_t) * (P->n_corr + 1));
+    corr_offsets(P, off);
+    int64_t n = off[P->n_corr];
+    free(off);
     return n;
 }
 
@@ -190,13 +191,31 @@ int64_t orc_corr_state(const orc_problem* P, const uint8_t* occ, int c)
     return corr_state(P, bits, c);
 }
 
+/* off[c] = parameter index of state 0 of correlator c; off[n_corr] = number
+ * of correlator parameters.  Each class owns one block of 4^m parameters,
+ * classes in index order; a correlator reads its class's block. */
 static void corr_offsets(const orc_problem* P, int64_t* off)
 {
-    off[0] = 0;
+    if (!P->corr_class) {
+        off[0] = 0;
+        for (int c = 0; c < P->n_corr; ++c) {
+            int m = P->corr_ptr[c + 1] - P->corr_ptr[c];
+            off[c + 1] = off[c] + ((int64_t)1 << (2 * m));
+        }
+        return;
+    }
+    int n_class = 0;
+    for (int c = 0; c < P->n_corr; ++c)
+        if (P->corr_class[c] + 1 > n_class) n_class = P->corr_class[c] + 1;
+    int64_t* cls = (int64_t*)calloc((size_t)n_class + 1, sizeof(int64_t));
     for (int c = 0; c < P->n_corr; ++c) {
         int m = P->corr_ptr[c + 1] - P->corr_ptr[c];
-        off[c + 1] = off[c] + ((int64_t)1 << (2 * m));
+        cls[P->corr_class[c] + 1] = (int64_t)1 << (2 * m);
     }
+    for (int q = 0; q < n_class; ++q) cls[q + 1] += cls[q];
+    for (int c = 0; c < P->n_corr; ++c) off[c] = cls[P->corr_class[c]];
+    off[P->n_corr] = cls[n_class];
+    free(cls);
 }
 
 /* A = F[occ, occ] with F_pq = f_pq (p < q), F_qp = -f_pq, F_pp = 0 */

@@ -21,7 +21,10 @@ typedef struct orc_problem {
     int n_corr;             /* correlators: sites corr_sites[corr_ptr[c]..]    */
     const int32_t* corr_ptr;
     const int32_t* corr_sites;
-    const double* C;        /* correlator amplitudes, correlator-major          */
+    const int32_t* corr_class; /* class of every correlator (NULL: each its own);
+                               correlators of one class share one parameter
+                               block (translation-invariant correlators)     */
+    const double* C;        /* correlator amplitudes, class-major              */
     const double* f;        /* pairing f_pq, p < q, row-major upper triangle    */
 } orc_problem;
 

@@ -59,7 +59,11 @@ struct vmc_ctx {
     DevProblem pb{};
     // device tables
     int *d_corr_ptr = nullptr, *d_corr_sites = nullptr;
-    int64_t* d_corr_off = nullptr;
+    int64_t* d_corr_off = nullptr;        // [ncorr + 1] first parameter of each correlator's block, then ncp
+    int64_t* d_class_off = nullptr;       // [n_class + 1] parameter blocks of the classes
+    int* d_class_ptr = nullptr;           // [n_class + 1] into d_class_inst
+    int* d_class_inst = nullptr;          // correlators grouped by class
+    int n_class = 0;
     int *d_site_cptr = nullptr, *d_site_corr = nullptr, *d_site_w = nullptr;
     uint16_t* d_corr_site_w = nullptr;
     uint32_t* d_pq_of = nullptr;   // pairing index -> p | q << 16
@@ -203,10 +207,38 @@ extern "C" int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, co
             w *= 4;
         }
         cptr[c + 1] = (int)csites.size();
-        h->corr_off[c + 1] = h->corr_off[c] + ((int64_t)1 << (2 * m));
         h->maxd = std::max(h->maxd, 1 << (2 * m));
     }
-    h->ncp = h->corr_off[h->ncorr];
+    // classes: correlators of one class share one parameter block; blocks in
+    // class order, corr_off[c] = first parameter of c's block
+    std::vector<int> cls(h->ncorr);
+    for (int c = 0; c < h->ncorr; ++c) cls[c] = ans->corr_class ? ans->corr_class[c] : c;
+    h->n_class = 0;
+    for (int c = 0; c < h->ncorr; ++c) {
+        if (cls[c] < 0 || cls[c] >= h->ncorr) return fail(VMC_ERR_INVALID_ARG);
+        h->n_class = std::max(h->n_class, cls[c] + 1);
+    }
+    std::vector<int> cm(h->n_class, 0);
+    for (int c = 0; c < h->ncorr; ++c) {
+        const int m = cptr[c + 1] - cptr[c];
+        if (cm[cls[c]] != 0 && cm[cls[c]] != m) return fail(VMC_ERR_INVALID_ARG);   // one size per class
+        cm[cls[c]] = m;
+    }
+    std::vector<int64_t> class_off(h->n_class + 1, 0);
+    for (int q = 0; q < h->n_class; ++q) {
+        if (cm[q] == 0) return fail(VMC_ERR_INVALID_ARG);                             // unused class id
+        class_off[q + 1] = class_off[q] + ((int64_t)1 << (2 * cm[q]));
+    }
+    std::vector<int> class_ptr(h->n_class + 1, 0), class_inst;
+    for (int q = 0; q < h->n_class; ++q) {
+        for (int c = 0; c < h->ncorr; ++c)
+            if (cls[c] == q) class_inst.push_back(c);
+        class_ptr[q + 1] = (int)class_inst.size();
+    }
+    h->corr_off.assign(h->ncorr + 1, 0);
+    for (int c = 0; c < h->ncorr; ++c) h->corr_off[c] = class_off[cls[c]];
+    h->ncp = class_off[h->n_class];
+    h->corr_off[h->ncorr] = h->ncp;
     h->nv = h->ncp + h->npf;
     // dense (correlator, site) -> 4^j weight table, 0 where the site is absent
     std::vector<uint16_t> csw((size_t)std::max(h->ncorr, 1) * ns, 0);
@@ -286,6 +318,9 @@ extern "C" int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, co
     ACK(h->alloc(&h->d_corr_ptr, cptr.size()));
     ACK(h->alloc(&h->d_corr_sites, csites.size()));
     ACK(h->alloc(&h->d_corr_off, h->corr_off.size()));
+    ACK(h->alloc(&h->d_class_off, class_off.size()));
+    ACK(h->alloc(&h->d_class_ptr, class_ptr.size()));
+    ACK(h->alloc(&h->d_class_inst, std::max<size_t>(class_inst.size(), 1)));
     ACK(h->alloc(&h->d_site_cptr, scptr.size()));
     ACK(h->alloc(&h->d_site_corr, scorr.size()));
     ACK(h->alloc(&h->d_site_w, sw.size()));
@@ -299,6 +334,9 @@ extern "C" int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, co
     UPL(h->d_corr_ptr, cptr.data(), cptr.size());
     if (!csites.empty()) UPL(h->d_corr_sites, csites.data(), csites.size());
     UPL(h->d_corr_off, h->corr_off.data(), h->corr_off.size());
+    UPL(h->d_class_off, class_off.data(), class_off.size());
+    UPL(h->d_class_ptr, class_ptr.data(), class_ptr.size());
+    if (!class_inst.empty()) UPL(h->d_class_inst, class_inst.data(), class_inst.size());
     UPL(h->d_site_cptr, scptr.data(), scptr.size());
     if (!scorr.empty()) UPL(h->d_site_corr, scorr.data(), scorr.size());
     if (!sw.empty()) UPL(h->d_site_w, sw.data(), sw.size());
@@ -387,6 +425,8 @@ extern "C" int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, co
     pb.ns = ns; pb.M = h->M; pb.nu = nu; pb.nd = nd; pb.N = N; pb.ncorr = h->ncorr; pb.P = h->P;
     pb.npf = h->npf; pb.ham = h->ham; pb.ncp = h->ncp; pb.nv = h->nv; pb.U = ham->U;
     pb.corr_ptr = h->d_corr_ptr; pb.corr_sites = h->d_corr_sites; pb.corr_off = h->d_corr_off;
+    pb.n_class = h->n_class; pb.class_off = h->d_class_off;
+    pb.class_ptr = h->d_class_ptr; pb.class_inst = h->d_class_inst;
     pb.site_cptr = h->d_site_cptr; pb.site_corr = h->d_site_corr; pb.site_w = h->d_site_w;
     pb.corr_site_w = h->d_corr_site_w;
     pb.nbr_ptr = h->d_nbr_ptr; pb.nbr_site = h->d_nbr_site; pb.nbr_t = h->d_nbr_t;
@@ -824,7 +864,7 @@ static int launch_corr(vmc_ctx* h, const AT* T, const int* stop, cudaStream_t st
     a.T = T;
     a.corr_raw = (AT*)h->d_corrraw;
     a.stop = stop;
-    kern<<<h->ncorr * kCorrCluster, 256, smem, st>>>(a); h->n_launch++;
+    kern<<<h->n_class * kCorrCluster, 256, smem, st>>>(a); h->n_launch++;
     VCK(cudaGetLastError());
     return VMC_OK;
 }
@@ -878,9 +918,9 @@ static int ensure_sorted(vmc_ctx* h, cudaStream_t st) {
         const size_t csm = (size_t)h->maxd * 4;
         VCK(cudaFuncSetAttribute(k_count_C, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
         VCK(cudaFuncSetAttribute(k_fill_C, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
-        k_count_C<<<h->ncorr, 512, csm, st>>>(h->pb, h->n_s, h->d_cidxT, h->d_ccount); h->n_launch++;
+        k_count_C<<<h->n_class, 512, csm, st>>>(h->pb, h->n_s, h->d_cidxT, h->d_ccount); h->n_launch++;
         k_scan_params<<<1, 1024, 0, st>>>(h->d_ccount, (int)h->ncp, 0u, h->d_cbase); h->n_launch++;
-        k_fill_C<<<h->ncorr, 512, csm, st>>>(h->pb, h->n_s, h->d_cidxT, h->d_cbase, h->d_Tc); h->n_launch++;
+        k_fill_C<<<h->n_class, 512, csm, st>>>(h->pb, h->n_s, h->d_cidxT, h->d_cbase, h->d_Tc); h->n_launch++;
         VCK(cudaGetLastError());
     }
     h->sorted_ok = true;

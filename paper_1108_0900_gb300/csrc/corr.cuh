@@ -8,50 +8,53 @@
 
 namespace vmc {
 
-// The kCorrCluster CTAs of the cluster for correlator c histogram t_s over
-// its 4^m states, each for a slice of the samples, into their own shared
-// memory h (4^m x K values of AT); after a cluster barrier CTA r sums its
-// share of the states over the cluster's histograms through distributed
-// shared memory (fixed order) and writes corr_raw[off_c + state].  Slices
-// start on multiples of 8 samples; each thread takes 8 consecutive samples
-// per step (one 16-byte load of states, K x 8 values of t).  Every CTA of the
-// cluster must call this.
+// The kCorrCluster CTAs of the cluster for class q histogram t_s over the
+// 4^m states of the class's correlators (all of them share the class's
+// parameter block), each CTA for a slice of the samples, into their own
+// shared memory h (4^m x K values of AT); after a cluster barrier CTA r sums
+// its share of the states over the cluster's histograms through distributed
+// shared memory (fixed order) and writes corr_raw[class_off_q + state].
+// Slices start on multiples of 8 samples; each thread takes 8 consecutive
+// samples per step (one 16-byte load of states, K x 8 values of t).  Every
+// CTA of the cluster must call this.
 template <typename AT, int K>
-__device__ __forceinline__ void corr_cluster_histogram(const CorrArgs<AT>& a, AT* h, int c) {
+__device__ __forceinline__ void corr_cluster_histogram(const CorrArgs<AT>& a, AT* h, int q) {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
     const DevProblem& pb = a.pb;
     const int rank = (int)cluster.block_rank();
-    const int64_t off = pb.corr_off[c];
-    const int d = (int)(pb.corr_off[c + 1] - off);
+    const int64_t off = pb.class_off[q];
+    const int d = (int)(pb.class_off[q + 1] - off);
     for (int i = threadIdx.x; i < d * K; i += blockDim.x) h[i] = AT(0);
     __syncthreads();
     const int64_t len = ((a.n_s + kCorrCluster - 1) / kCorrCluster + 7) & ~(int64_t)7;
     const int64_t s0 = min(a.n_s, rank * len), s1 = min(a.n_s, s0 + len);
-    const uint16_t* st = a.cidxT + (int64_t)c * a.n_s;
-    // 16-byte loads need the row to start on a 16-byte boundary
+    // 16-byte loads need the rows to start on a 16-byte boundary
     const bool vec = ((a.n_s & 7) == 0);
-    int64_t s = s0;
-    if (vec) {
-        for (int64_t g = s0 + 8 * (int64_t)threadIdx.x; g + 8 <= s1; g += 8 * (int64_t)blockDim.x) {
-            const uint4 sv = *(const uint4*)(st + g);
-            const uint32_t w4[4] = {sv.x, sv.y, sv.z, sv.w};
-            AT tv[8 * K];
+    for (int ji = pb.class_ptr[q]; ji < pb.class_ptr[q + 1]; ++ji) {
+        const uint16_t* st = a.cidxT + (int64_t)pb.class_inst[ji] * a.n_s;
+        int64_t s = s0;
+        if (vec) {
+            for (int64_t g = s0 + 8 * (int64_t)threadIdx.x; g + 8 <= s1; g += 8 * (int64_t)blockDim.x) {
+                const uint4 sv = *(const uint4*)(st + g);
+                const uint32_t w4[4] = {sv.x, sv.y, sv.z, sv.w};
+                AT tv[8 * K];
 #pragma unroll
-            for (int j = 0; j < 8 * K; ++j) tv[j] = a.T[g * K + j];
+                for (int j = 0; j < 8 * K; ++j) tv[j] = a.T[g * K + j];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int i = (int)((w4[j >> 1] >> (16 * (j & 1))) & 0xFFFFu);
+                for (int j = 0; j < 8; ++j) {
+                    const int i = (int)((w4[j >> 1] >> (16 * (j & 1))) & 0xFFFFu);
 #pragma unroll
-                for (int kk = 0; kk < K; ++kk) atomicAdd(&h[i * K + kk], tv[j * K + kk]);
+                    for (int kk = 0; kk < K; ++kk) atomicAdd(&h[i * K + kk], tv[j * K + kk]);
+                }
             }
+            s = s0 + ((s1 - s0) & ~(int64_t)7);
         }
-        s = s0 + ((s1 - s0) & ~(int64_t)7);
-    }
-    for (int64_t q = s + threadIdx.x; q < s1; q += blockDim.x) {
-        int i = st[q];
+        for (int64_t qs = s + threadIdx.x; qs < s1; qs += blockDim.x) {
+            int i = st[qs];
 #pragma unroll
-        for (int kk = 0; kk < K; ++kk) atomicAdd(&h[i * K + kk], a.T[q * K + kk]);
+            for (int kk = 0; kk < K; ++kk) atomicAdd(&h[i * K + kk], a.T[qs * K + kk]);
+        }
     }
     cluster.sync();
     const int per = (d + kCorrCluster - 1) / kCorrCluster;
@@ -59,7 +62,7 @@ __device__ __forceinline__ void corr_cluster_histogram(const CorrArgs<AT>& a, AT
     for (int i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
         double acc = 0.0;
 #pragma unroll
-        for (int q = 0; q < kCorrCluster; ++q) acc += (double)cluster.map_shared_rank(h, q)[i];
+        for (int r = 0; r < kCorrCluster; ++r) acc += (double)cluster.map_shared_rank(h, r)[i];
         a.corr_raw[off * K + i] = (AT)acc;
     }
     cluster.sync();   // keep this CTA's histogram alive until the cluster has read it

@@ -200,19 +200,23 @@ __global__ void __launch_bounds__(512) k_fill_T(const uint32_t* G, int64_t Pst, 
     }
 }
 
-// Correlator runs: the samples of each correlator state, grouped by state
-// (global parameter index off_c + state), built once per set of samples from
-// the transposed state array.  Block per correlator, shared-memory counters.
+// Correlator runs: the samples of each correlator parameter, grouped by
+// parameter (class block off_q + state), built once per set of samples from
+// the transposed state array.  Block per class (its correlators share the
+// block, so a sample can appear once per correlator of the class),
+// shared-memory counters.
 __global__ void __launch_bounds__(512) k_count_C(DevProblem pb, int64_t n_s, const uint16_t* cidxT,
                                                  uint32_t* ccount) {
     extern __shared__ uint32_t hist[];
-    const int c = blockIdx.x;
-    const int64_t off = pb.corr_off[c];
-    const int d = (int)(pb.corr_off[c + 1] - off);
+    const int q = blockIdx.x;
+    const int64_t off = pb.class_off[q];
+    const int d = (int)(pb.class_off[q + 1] - off);
     for (int i = threadIdx.x; i < d; i += blockDim.x) hist[i] = 0u;
     __syncthreads();
-    const uint16_t* st = cidxT + (int64_t)c * n_s;
-    for (int64_t s = threadIdx.x; s < n_s; s += blockDim.x) atomicAdd(&hist[st[s]], 1u);
+    for (int j = pb.class_ptr[q]; j < pb.class_ptr[q + 1]; ++j) {
+        const uint16_t* st = cidxT + (int64_t)pb.class_inst[j] * n_s;
+        for (int64_t s = threadIdx.x; s < n_s; s += blockDim.x) atomicAdd(&hist[st[s]], 1u);
+    }
     __syncthreads();
     for (int i = threadIdx.x; i < d; i += blockDim.x) ccount[off + i] = hist[i];
 }
@@ -220,17 +224,19 @@ __global__ void __launch_bounds__(512) k_count_C(DevProblem pb, int64_t n_s, con
 __global__ void __launch_bounds__(512) k_fill_C(DevProblem pb, int64_t n_s, const uint16_t* cidxT,
                                                 const uint32_t* cbase, uint32_t* Tc) {
     extern __shared__ uint32_t cur[];
-    const int c = blockIdx.x;
-    const int64_t off = pb.corr_off[c];
-    const int d = (int)(pb.corr_off[c + 1] - off);
+    const int q = blockIdx.x;
+    const int64_t off = pb.class_off[q];
+    const int d = (int)(pb.class_off[q + 1] - off);
     for (int i = threadIdx.x; i < d; i += blockDim.x) cur[i] = cbase[off + i];
     __syncthreads();
-    const uint16_t* st = cidxT + (int64_t)c * n_s;
     // entry = sample << 5 | (parameter index mod 32): the scatter's warps own
     // 32 consecutive parameters and sum each one's contiguous segment
-    for (int64_t s = threadIdx.x; s < n_s; s += blockDim.x) {
-        const uint32_t state = st[s];
-        Tc[atomicAdd(&cur[state], 1u)] = ((uint32_t)s << 5) | (uint32_t)((off + state) & 31);
+    for (int j = pb.class_ptr[q]; j < pb.class_ptr[q + 1]; ++j) {
+        const uint16_t* st = cidxT + (int64_t)pb.class_inst[j] * n_s;
+        for (int64_t s = threadIdx.x; s < n_s; s += blockDim.x) {
+            const uint32_t state = st[s];
+            Tc[atomicAdd(&cur[state], 1u)] = ((uint32_t)s << 5) | (uint32_t)((off + state) & 31);
+        }
     }
 }
 

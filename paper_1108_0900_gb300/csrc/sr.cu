@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(512) k_sr_main(MainArgs<AT> a) {
     for (int i = threadIdx.x; i < npf * K; i += blockDim.x) dst[i] = acc[i];
 }
 
-// correlator-major scatter: one thread-block cluster per correlator
+// correlator-major scatter: one thread-block cluster per correlator class
 template <typename AT, int K>
 __global__ void __cluster_dims__(kCorrCluster, 1, 1) __launch_bounds__(256) k_corr_scatter(CorrArgs<AT> a) {
     if (a.stop && *a.stop) return;   // uniform over the grid: no CTA reaches a cluster barrier

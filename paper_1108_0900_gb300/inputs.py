@@ -59,6 +59,7 @@ class Workload:
     seed_problem: int = 0
     seed_sampling: int = 0
     init_occ: Optional[np.ndarray] = None  # uint8 [n_walkers, N] ascending
+    corr_class: Optional[np.ndarray] = None  # int32 [n_corr]: correlators of one class share parameters
 
     @property
     def M(self) -> int:
@@ -85,8 +86,30 @@ class Workload:
         return np.concatenate(self.corr_sites).astype(np.int32)
 
     @property
+    def classes(self) -> np.ndarray:
+        """Class of every correlator (each its own class unless shared)."""
+        if self.corr_class is None:
+            return np.arange(self.n_corr, dtype=np.int32)
+        return np.asarray(self.corr_class, np.int32)
+
+    @property
+    def class_off(self) -> np.ndarray:
+        """Parameter offset of every class block (classes in index order), plus the total."""
+        cl = self.classes
+        n_class = int(cl.max()) + 1 if len(cl) else 0
+        dim = np.zeros(n_class, np.int64)
+        for c, q in enumerate(cl):
+            dim[q] = 4 ** len(self.corr_sites[c])
+        return np.concatenate([[0], np.cumsum(dim)]).astype(np.int64)
+
+    @property
+    def corr_param_off(self) -> np.ndarray:
+        """Parameter index of state 0 of every correlator."""
+        return self.class_off[self.classes]
+
+    @property
     def n_corr_params(self) -> int:
-        return int(sum(4 ** len(s) for s in self.corr_sites))
+        return int(self.class_off[-1])
 
     @property
     def n_pf_params(self) -> int:
@@ -141,8 +164,22 @@ def all_pair_correlators(n: int) -> List[np.ndarray]:
 # draws
 # --------------------------------------------------------------------------
 
-def draw_params(rng: np.random.Generator, corr_sites, M: int):
-    n_corr_params = int(sum(4 ** len(s) for s in corr_sites))
+def translation_classes(corr: str, n_corr: int) -> np.ndarray:
+    """Translation classes of the generated correlators: bond correlators
+    alternate x and y bonds (two classes), plaquettes of one shape form one."""
+    if corr == "pair":
+        return (np.arange(n_corr) % 2).astype(np.int32)
+    return np.zeros(n_corr, np.int32)
+
+
+def draw_params(rng: np.random.Generator, corr_sites, M: int, corr_class=None):
+    if corr_class is None:
+        n_corr_params = int(sum(4 ** len(s) for s in corr_sites))
+    else:
+        dims = {}
+        for c, q in enumerate(corr_class):
+            dims[int(q)] = 4 ** len(corr_sites[c])
+        n_corr_params = int(sum(dims.values()))
     C = 1.0 + 0.01 * rng.standard_normal(n_corr_params)
     f = 0.1 * rng.standard_normal(M * (M - 1) // 2)
     return C, f
@@ -177,7 +214,7 @@ def draw_abinitio(rng: np.random.Generator, n: int, n_chol: int):
 
 def hubbard(name, Lx, Ly, n_up, n_dn, corr, U=4.0, t=1.0, seed=0,
             n_walkers=64, samples_per_walker=64, burn_in_sweeps=50,
-            shift=1e-3, tol=1e-8, seed_sampling=None) -> Workload:
+            shift=1e-3, tol=1e-8, seed_sampling=None, shared=False) -> Workload:
     rng = np.random.default_rng(seed)
     n_sites = Lx * Ly
     if corr == "pair":
@@ -190,7 +227,8 @@ def hubbard(name, Lx, Ly, n_up, n_dn, corr, U=4.0, t=1.0, seed=0,
         cs = []
     else:
         raise ValueError(corr)
-    C, f = draw_params(rng, cs, 2 * n_sites)
+    cls = translation_classes(corr, len(cs)) if shared and cs else None
+    C, f = draw_params(rng, cs, 2 * n_sites, cls)
     bonds = square_bonds(Lx, Ly)
     init = draw_configs(rng, n_walkers, n_sites, n_up, n_dn)
     return Workload(name=name, n_sites=n_sites, n_up=n_up, n_dn=n_dn, ham=HUBBARD,
@@ -200,7 +238,7 @@ def hubbard(name, Lx, Ly, n_up, n_dn, corr, U=4.0, t=1.0, seed=0,
                     burn_in_sweeps=burn_in_sweeps, shift=shift, tol=tol,
                     seed_problem=seed,
                     seed_sampling=seed + 1000 if seed_sampling is None else seed_sampling,
-                    init_occ=init)
+                    init_occ=init, corr_class=cls)
 
 
 def abinitio(name, n_orb, n_up, n_dn, n_chol=48, seed=0, n_walkers=64,

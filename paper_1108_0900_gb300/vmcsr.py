@@ -50,7 +50,7 @@ class vmc_hamiltonian(ct.Structure):
 
 class vmc_ansatz(ct.Structure):
     _fields_ = [("n_up", ct.c_int), ("n_dn", ct.c_int), ("n_corr", ct.c_int), ("corr_ptr", ct.c_void_p),
-                ("corr_sites", ct.c_void_p)]
+                ("corr_sites", ct.c_void_p), ("corr_class", ct.c_void_p)]
 
 
 class vmc_options(ct.Structure):
@@ -159,13 +159,15 @@ def vmc_create(wl, n_walkers=None, samples_per_walker=None, walker_precision=VMC
         bond_t=np.ascontiguousarray(wl.bond_t, np.float64),
         corr_ptr=np.ascontiguousarray(wl.corr_ptr, np.int32),
         corr_sites=np.ascontiguousarray(wl.corr_flat, np.int32),
+        corr_class=None if getattr(wl, "corr_class", None) is None else np.ascontiguousarray(wl.corr_class, np.int32),
         h=None if wl.h is None else np.ascontiguousarray(wl.h, np.float64),
         chol=None if wl.chol is None else np.ascontiguousarray(wl.chol, np.float64),
     )
     lat = vmc_lattice(wl.n_sites, len(keep["bonds"]), _np_ptr(keep["bonds"]), _np_ptr(keep["bond_t"]))
     ham = vmc_hamiltonian(wl.ham, float(wl.U), 0 if wl.chol is None else wl.chol.shape[0],
                           _np_ptr(keep["h"]), _np_ptr(keep["chol"]))
-    ans = vmc_ansatz(wl.n_up, wl.n_dn, wl.n_corr, _np_ptr(keep["corr_ptr"]), _np_ptr(keep["corr_sites"]))
+    ans = vmc_ansatz(wl.n_up, wl.n_dn, wl.n_corr, _np_ptr(keep["corr_ptr"]), _np_ptr(keep["corr_sites"]),
+                     _np_ptr(keep["corr_class"]))
     opt = vmc_options(int(n_walkers or wl.n_walkers), int(samples_per_walker or wl.samples_per_walker),
                       int(walker_precision), int(bool(keep_fp64_store)), int(bool(keep_lowp_store)),
                       int(refresh_every))

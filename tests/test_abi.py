@@ -32,7 +32,9 @@ def _create_rc(wl, **opt):
                 cp=np.ascontiguousarray(wl.corr_ptr, np.int32), cs=np.ascontiguousarray(wl.corr_flat, np.int32))
     lat = vmcsr.vmc_lattice(wl.n_sites, len(keep["b"]), keep["b"].ctypes.data, keep["t"].ctypes.data)
     ham = vmcsr.vmc_hamiltonian(wl.ham, wl.U, 0, None, None)
-    ans = vmcsr.vmc_ansatz(wl.n_up, wl.n_dn, wl.n_corr, keep["cp"].ctypes.data, keep["cs"].ctypes.data)
+    cl = opt.pop("corr_class", None)
+    ans = vmcsr.vmc_ansatz(wl.n_up, wl.n_dn, wl.n_corr, keep["cp"].ctypes.data, keep["cs"].ctypes.data,
+                           None if cl is None else cl.ctypes.data)
     o = dict(n_walkers=4, samples_per_walker=2, walker_precision=0, keep_fp64_store=1, keep_lowp_store=0,
              refresh_every=0)
     o.update(opt)

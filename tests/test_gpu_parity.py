@@ -72,6 +72,12 @@ SMALL = {
     "cfg3abinitio": lambda: inputs.config(3, n_walkers=8, samples_per_walker=2),
     "tiny2x2": lambda: inputs.hubbard("t", 2, 2, 1, 1, "2x2", seed=5, n_walkers=7, samples_per_walker=4),
     "nocorr3x2": lambda: inputs.hubbard("t", 3, 2, 2, 2, "none", seed=6, n_walkers=11, samples_per_walker=3),
+    # translation-invariant correlators: x and y bonds share two blocks; every
+    # 2x3 plaquette of the 8x8 lattice reads one block of 4,096 amplitudes
+    "cfg1shared": lambda: inputs.hubbard("s1", 4, 4, 8, 8, "pair", seed=12, n_walkers=24, samples_per_walker=6,
+                                         shared=True),
+    "cfg5shared": lambda: inputs.hubbard("s5", 8, 8, 28, 28, "2x3", seed=13, n_walkers=9, samples_per_walker=3,
+                                         shared=True),
 }
 
 

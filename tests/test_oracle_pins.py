@@ -317,6 +317,58 @@ def test_logderiv_matches_finite_differences():
         assert np.abs(O - fd).max() <= 1e-6 * max(1.0, np.abs(O).max())
 
 
+def test_shared_correlators_logderiv_finite_differences():
+    """Translation-invariant correlators (one parameter block per class):
+    O of a shared parameter is the sum over the correlators reading it, which
+    central differences of ln|Psi| see directly."""
+    for corr in ("pair", "2x2"):
+        wl = inputs.hubbard("fds", 3, 2, 2, 2, corr, seed=23, n_walkers=2, shared=True)
+        assert wl.corr_class is not None and wl.n_corr_params == len(set(wl.corr_class)) * 4 ** len(wl.corr_sites[0])
+        P = oracle.Problem(wl)
+        ncp = wl.n_corr_params
+        h = 1e-6
+        for occ in wl.init_occ:
+            O = P.logderiv(occ)
+            for k in range(ncp):
+                C1, C2 = wl.C.copy(), wl.C.copy()
+                C1[k] += h
+                C2[k] -= h
+                lp = _with_params(wl, C1, wl.f).log_psi(occ)[0]
+                lm = _with_params(wl, C2, wl.f).log_psi(occ)[0]
+                assert abs(O[k] - (lp - lm) / (2 * h)) <= 1e-6 * max(1.0, abs(O[k]))
+            # the states the correlators occupy, counted with multiplicity
+            cnt = np.zeros(ncp)
+            for c in range(wl.n_corr):
+                cnt[wl.corr_param_off[c] + P.corr_state(occ, c)] += 1
+            assert np.allclose(O[:ncp] * wl.C, cnt, atol=1e-12)
+
+
+def test_shared_correlator_null_vectors_and_paper_count():
+    """O_s . C_q = (number of correlators of class q) for every sample, so
+    S C_q = eps C_q; and the paper's 4x4 layout, a 3x3 correlator at every
+    site shared within each sublattice, has 2 x 4^9 + 496 = 524,784 parameters."""
+    wl = inputs.hubbard("nvs", 4, 4, 5, 5, "2x2", seed=33, n_walkers=8, shared=True)
+    P = oracle.Problem(wl)
+    occ = wl.init_occ.copy()
+    step = np.zeros(wl.n_walkers, np.uint64)
+    samples, _, _ = P.sample(occ, step, 79, 3, 5)
+    E, O = P.measure(samples)
+    v = np.zeros(wl.n_params)
+    v[:wl.n_corr_params] = wl.C
+    assert np.allclose(O @ v, wl.n_corr, atol=1e-10)
+    Sv = oracle.apply_S(O, v, 1e-3)
+    assert np.abs(Sv - 1e-3 * v).max() < 1e-9
+    g, _ = oracle.gradient(O, E)
+    assert abs(g @ v) < 1e-8
+    golden = {l.split()[0]: int(l.split()[1]) for l in open(os.path.join(GOLDEN, "param_counts.txt"))
+              if l.strip() and l[0] != "#"}
+    c33 = inputs.plaquette_correlators(4, 4, 3, 3)
+    cls = np.array([(x + y) % 2 for y in range(4) for x in range(4)], np.int32)
+    wl33 = inputs.Workload(name="c", n_sites=16, n_up=1, n_dn=1, ham=inputs.HUBBARD, corr_sites=c33,
+                           C=np.ones(2 * 4 ** 9), f=np.zeros(32 * 31 // 2), corr_class=cls)
+    assert oracle.Problem(wl33).n_params() == wl33.n_params == golden["hubbard4x4_two_3x3"]
+
+
 def test_homogeneity_null_vectors():
     """O_s . C_c = 1 for every correlator block c and O_s . f = N/2 (the
     pfaffian is homogeneous of degree N/2 in f), so S C_c = eps C_c,
