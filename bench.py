@@ -186,6 +186,27 @@ def run_gpu(args, rank, world, dist):
     h2d = (wl.C.nbytes + wl.f.nbytes)
     d2h = x_host.numel() * 8
 
+    # ---- translation-invariant correlators (every 2x3 plaquette of the 8x8
+    # lattice reads one shared block of 4,096 amplitudes), mixed path ---------
+    shared = None
+    if args.shared_steps > 0:
+        wls = inputs.hubbard("8x8-2x3-shared", 8, 8, 28, 28, "2x3", seed=1005, n_walkers=16384,
+                             samples_per_walker=4, shared=True)
+        hs = V.vmc_create(wls, walker_precision=V.VMC_FP32, keep_fp64_store=False, keep_lowp_store=True)
+        V.vmc_set_params(hs, wls.C, wls.f)
+        V.vmc_set_walkers(hs, wls.init_occ)
+        V.vmc_sample(hs, wls.burn_in_sweeps, seed + 17)
+        ms_s, infos_s, prof_s, _ = timed(hs, "mixed", args.shared_steps, 1, profile=True)
+        shared = {"workload": "8x8 periodic Hubbard U/t=4, 28+28 electrons, 64 2x3 plaquettes sharing one block "
+                              f"of 4,096 amplitudes + pfaffian (n_v={wls.n_params:,}), 16,384 walkers x 4 samples",
+                  "ms_per_step": round(ms_s, 3),
+                  "sv_gbs": round(prof_s["pass_bytes"] / (prof_s["pass_ms"] * 1e-3) / 1e9, 1)
+                  if prof_s and prof_s["pass_ms"] > 0 else None,
+                  "cg_inner_iterations": float(np.mean([i["iterations"] for i in infos_s])),
+                  "true_rel_residual": max(i["true_rel_residual"] for i in infos_s),
+                  "converged": all(i["converged"] for i in infos_s)}
+        hs.close()
+
     # ---- plain FP64 path ------------------------------------------------------
     fp64 = None
     if not args.no_fp64:
@@ -224,6 +245,7 @@ def run_gpu(args, rank, world, dist):
                "converged": all(i["converged"] for i in infos)},
         "sv_gbs": round(ach, 1) if ach else None,
         "fp64_path": fp64,
+        "shared_correlators": shared,
         "speedup_vs_fp64_path": round(fp64["ms_per_step"] / ms, 3) if fp64 else None,
         "roofline": {"bound": "hbm", "kernel": "k_gather_G<1,U> + k_scatter_T<1> (sorted two-pass Eq. 7 product, BF16 store)",
                      "achieved": round(ach, 1) if ach else None, "peak": peak, "unit": "GB/s",
@@ -362,6 +384,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--shared-steps", type=int, default=2,
+                    help="SR steps timed on the shared-correlator 8x8 workload (0: skip)")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-cg-iters", type=float, default=350.0)
