@@ -64,6 +64,12 @@ struct vmc_ctx {
     int* d_class_ptr = nullptr;           // [n_class + 1] into d_class_inst
     int* d_class_inst = nullptr;          // correlators grouped by class
     int n_class = 0;
+    int4* d_units = nullptr;              // histogram-scatter work units (class, first, end)
+    int n_units = 0;
+    uint2* d_items = nullptr;             // sorted correlator-scatter work items (group, first entry)
+    uint32_t* d_nitems = nullptr;         // items per group
+    uint32_t* d_item_base = nullptr;      // [groups + 1] exclusive scan, total at the end
+    int64_t max_items = 0;
     int *d_site_cptr = nullptr, *d_site_corr = nullptr, *d_site_w = nullptr;
     uint16_t* d_corr_site_w = nullptr;
     uint32_t* d_pq_of = nullptr;   // pairing index -> p | q << 16
@@ -235,6 +241,12 @@ extern "C" int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, co
             if (cls[c] == q) class_inst.push_back(c);
         class_ptr[q + 1] = (int)class_inst.size();
     }
+    // histogram-scatter work units: up to kInstPerUnit correlators of one class
+    std::vector<int4> units;
+    for (int q = 0; q < h->n_class; ++q)
+        for (int j = class_ptr[q]; j < class_ptr[q + 1]; j += kInstPerUnit)
+            units.push_back(make_int4(q, j, std::min(j + kInstPerUnit, class_ptr[q + 1]), 0));
+    h->n_units = (int)units.size();
     h->corr_off.assign(h->ncorr + 1, 0);
     for (int c = 0; c < h->ncorr; ++c) h->corr_off[c] = class_off[cls[c]];
     h->ncp = class_off[h->n_class];
@@ -321,6 +333,7 @@ extern "C" int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, co
     ACK(h->alloc(&h->d_class_off, class_off.size()));
     ACK(h->alloc(&h->d_class_ptr, class_ptr.size()));
     ACK(h->alloc(&h->d_class_inst, std::max<size_t>(class_inst.size(), 1)));
+    ACK(h->alloc(&h->d_units, std::max<size_t>(units.size(), 1)));
     ACK(h->alloc(&h->d_site_cptr, scptr.size()));
     ACK(h->alloc(&h->d_site_corr, scorr.size()));
     ACK(h->alloc(&h->d_site_w, sw.size()));
@@ -337,6 +350,7 @@ extern "C" int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, co
     UPL(h->d_class_off, class_off.data(), class_off.size());
     UPL(h->d_class_ptr, class_ptr.data(), class_ptr.size());
     if (!class_inst.empty()) UPL(h->d_class_inst, class_inst.data(), class_inst.size());
+    if (!units.empty()) UPL(h->d_units, units.data(), units.size());
     UPL(h->d_site_cptr, scptr.data(), scptr.size());
     if (!scorr.empty()) UPL(h->d_site_corr, scorr.data(), scorr.size());
     if (!sw.empty()) UPL(h->d_site_w, sw.data(), sw.size());
@@ -397,6 +411,11 @@ extern "C" int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, co
         ACK(h->alloc(&h->d_Tc, (size_t)h->ncap * std::max(h->ncorr, 1)));
         ACK(h->alloc(&h->d_ccount, (size_t)std::max<int64_t>(h->ncp, 1)));
         ACK(h->alloc(&h->d_cbase, (size_t)h->ncp + 1));
+        const int64_t ng = (h->ncp + 31) / 32;
+        h->max_items = ng + (h->ncap * std::max(h->ncorr, 1) + kCorrItem - 1) / kCorrItem;
+        ACK(h->alloc(&h->d_items, (size_t)std::max<int64_t>(h->max_items, 1)));
+        ACK(h->alloc(&h->d_nitems, (size_t)std::max<int64_t>(ng, 1)));
+        ACK(h->alloc(&h->d_item_base, (size_t)ng + 1));
     }
     for (int k = 0; k < 3; ++k) ACK(h->alloc(&h->d_Obar[k], h->nv));
     for (int k = 0; k < 3; ++k) ACK(h->alloc(&h->d_Obar32[k], h->nv));
@@ -863,8 +882,10 @@ static int launch_corr(vmc_ctx* h, const AT* T, const int* stop, cudaStream_t st
     a.cidxT = h->d_cidxT;
     a.T = T;
     a.corr_raw = (AT*)h->d_corrraw;
+    a.units = h->d_units;
     a.stop = stop;
-    kern<<<h->n_class * kCorrCluster, 256, smem, st>>>(a); h->n_launch++;
+    VCK(cudaMemsetAsync(h->d_corrraw, 0, sizeof(AT) * h->ncp * K, st));
+    kern<<<h->n_units * kCorrCluster, 256, smem, st>>>(a); h->n_launch++;
     VCK(cudaGetLastError());
     return VMC_OK;
 }
@@ -915,12 +936,23 @@ static int ensure_sorted(vmc_ctx* h, cudaStream_t st) {
         VCK(cudaGetLastError());
     }
     if (h->ncorr > 0) {
+        // (class, slice) grid: a class shared by many correlators spreads over
+        // several CTAs
         const size_t csm = (size_t)h->maxd * 4;
+        const int nsl = std::max(1, std::min(64, (2 * h->nsm + h->n_class - 1) / h->n_class));
+        const dim3 cgrid((unsigned)h->n_class, (unsigned)nsl);
         VCK(cudaFuncSetAttribute(k_count_C, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
-        VCK(cudaFuncSetAttribute(k_fill_C, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
-        k_count_C<<<h->n_class, 512, csm, st>>>(h->pb, h->n_s, h->d_cidxT, h->d_ccount); h->n_launch++;
+        VCK(cudaMemsetAsync(h->d_ccount, 0, sizeof(uint32_t) * h->ncp, st));
+        k_count_C<<<cgrid, 512, csm, st>>>(h->pb, h->n_s, h->d_cidxT, h->d_ccount); h->n_launch++;
         k_scan_params<<<1, 1024, 0, st>>>(h->d_ccount, (int)h->ncp, 0u, h->d_cbase); h->n_launch++;
-        k_fill_C<<<h->n_class, 512, csm, st>>>(h->pb, h->n_s, h->d_cidxT, h->d_cbase, h->d_Tc); h->n_launch++;
+        VCK(cudaMemcpyAsync(h->d_ccount, h->d_cbase, sizeof(uint32_t) * h->ncp, cudaMemcpyDeviceToDevice, st));
+        k_fill_C<<<cgrid, 512, 0, st>>>(h->pb, h->n_s, h->d_cidxT, h->d_ccount, h->d_Tc); h->n_launch++;
+        // work items of the correlator scatter
+        const int64_t ng = (h->ncp + 31) / 32;
+        k_corr_item_count<<<(unsigned)((ng + 255) / 256), 256, 0, st>>>(h->d_cbase, h->ncp, h->d_nitems); h->n_launch++;
+        k_scan_params<<<1, 1024, 0, st>>>(h->d_nitems, (int)ng, 0u, h->d_item_base); h->n_launch++;
+        k_corr_item_fill<<<(unsigned)((ng + 255) / 256), 256, 0, st>>>(h->d_cbase, h->ncp, h->d_item_base,
+                                                                        h->d_items); h->n_launch++;
         VCK(cudaGetLastError());
     }
     h->sorted_ok = true;
@@ -983,6 +1015,9 @@ static int launch_sorted(vmc_ctx* h, const float* V, const float* invC, const do
     a.T = h->d_Tsort; a.base = h->d_base; a.nchunk = (int)((h->n_s + 65535) / 65536);
     a.raw = (float*)h->d_pfraw;
     a.Tc = h->d_Tc; a.cbase = h->d_cbase; a.craw = (float*)h->d_corrraw;
+    a.items = h->d_items;
+    a.n_items = h->d_item_base + (h->ncp + 31) / 32;
+    a.ncb = h->ncorr > 0 ? (int)((h->max_items + 7) / 8) : 0;
     a.tt_part = tt_part;
     a.stop = stop;
     const size_t smem = (size_t)h->npf * K * 4 + (size_t)(h->ncorr + 1) * 4;
@@ -997,7 +1032,8 @@ static int launch_sorted(vmc_ctx* h, const float* V, const float* invC, const do
     grid = std::min(grid, kNumPart * kMaxK);   // one partial slot of tt sums
     gk<<<grid, gthreads, smem, st>>>(a); h->n_launch++;
     h->last_gather_grid = grid;
-    k_scatter_T<K><<<(int)((h->ncp + 255) / 256) + (h->npf + 7) / 8, 256, 0, st>>>(a); h->n_launch++;
+    if (h->ncp > 0) VCK(cudaMemsetAsync(h->d_corrraw, 0, sizeof(float) * h->ncp * K, st));
+    k_scatter_T<K><<<a.ncb + (h->npf + 7) / 8, 256, 0, st>>>(a); h->n_launch++;
     VCK(cudaGetLastError());
     if (h->prof) {
         VCK(cudaEventRecord(rec.b, st));

@@ -8,21 +8,25 @@
 
 namespace vmc {
 
-// The kCorrCluster CTAs of the cluster for class q histogram t_s over the
-// 4^m states of the class's correlators (all of them share the class's
-// parameter block), each CTA for a slice of the samples, into their own
-// shared memory h (4^m x K values of AT); after a cluster barrier CTA r sums
-// its share of the states over the cluster's histograms through distributed
-// shared memory (fixed order) and writes corr_raw[class_off_q + state].
+// The kCorrCluster CTAs of the cluster for work unit u (a class q and up to
+// kInstPerUnit of its correlators, which share the class's parameter block)
+// histogram t_s over the 4^m states, each CTA for a slice of the samples, into
+// their own shared memory h (4^m x K values of AT); after a cluster barrier
+// CTA r sums its share of the states over the cluster's histograms through
+// distributed shared memory (fixed order) and adds them to
+// corr_raw[class_off_q + state] (zeroed by the caller; a class with more
+// correlators spreads over several units).
 // Slices start on multiples of 8 samples; each thread takes 8 consecutive
 // samples per step (one 16-byte load of states, K x 8 values of t).  Every
 // CTA of the cluster must call this.
 template <typename AT, int K>
-__device__ __forceinline__ void corr_cluster_histogram(const CorrArgs<AT>& a, AT* h, int q) {
+__device__ __forceinline__ void corr_cluster_histogram(const CorrArgs<AT>& a, AT* h, int u) {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
     const DevProblem& pb = a.pb;
     const int rank = (int)cluster.block_rank();
+    const int4 unit = a.units[u];                 // class, correlators [y, z) of class_inst
+    const int q = unit.x;
     const int64_t off = pb.class_off[q];
     const int d = (int)(pb.class_off[q + 1] - off);
     for (int i = threadIdx.x; i < d * K; i += blockDim.x) h[i] = AT(0);
@@ -31,7 +35,7 @@ __device__ __forceinline__ void corr_cluster_histogram(const CorrArgs<AT>& a, AT
     const int64_t s0 = min(a.n_s, rank * len), s1 = min(a.n_s, s0 + len);
     // 16-byte loads need the rows to start on a 16-byte boundary
     const bool vec = ((a.n_s & 7) == 0);
-    for (int ji = pb.class_ptr[q]; ji < pb.class_ptr[q + 1]; ++ji) {
+    for (int ji = unit.y; ji < unit.z; ++ji) {
         const uint16_t* st = a.cidxT + (int64_t)pb.class_inst[ji] * a.n_s;
         int64_t s = s0;
         if (vec) {
@@ -63,7 +67,7 @@ __device__ __forceinline__ void corr_cluster_histogram(const CorrArgs<AT>& a, AT
         double acc = 0.0;
 #pragma unroll
         for (int r = 0; r < kCorrCluster; ++r) acc += (double)cluster.map_shared_rank(h, r)[i];
-        a.corr_raw[off * K + i] = (AT)acc;
+        if (acc != 0.0) atomicAdd(a.corr_raw + off * K + i, (AT)acc);   // several units may share a class
     }
     cluster.sync();   // keep this CTA's histogram alive until the cluster has read it
 }

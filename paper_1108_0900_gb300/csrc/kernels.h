@@ -89,7 +89,8 @@ struct CorrArgs {
     int64_t n_s;
     const uint16_t* cidxT;  // [ncorr][n_s]
     const AT* T;            // [n_s][K]
-    AT* corr_raw;           // [ncp][K] sum over samples of t_s per state
+    AT* corr_raw;           // [ncp][K] sum over samples of t_s per state (zeroed by the caller)
+    const int4* units;      // cluster work units (class, first, end into class_inst)
     const int* stop;
 };
 
@@ -249,15 +250,20 @@ struct SortedArgs {
     const uint32_t* base;   // [nchunk][npf + 1] run offsets
     int nchunk;
     float* raw;             // [npf][K] scatter result
-    const uint32_t* Tc;     // correlator runs: sample indices grouped by state
+    const uint32_t* Tc;     // correlator runs: sample << 5 | k mod 32, grouped by parameter k
     const uint32_t* cbase;  // [ncp + 1] run offsets
-    float* craw;            // [ncp][K] correlator sums (without the 1/C factor)
+    const uint2* items;     // correlator work items (group, first entry)
+    const uint32_t* n_items;// device count of items
+    int ncb;                // CTAs of the correlator part (8 items each)
+    float* craw;            // [ncp][K] correlator sums (without the 1/C factor), zeroed by the caller
     double* tt_part;        // [gridDim] partial sums of centered t_s^2 (K = 1; may be null)
     const int* stop;
 };
 
 constexpr int kCorrPerLane = 4;    // the sorted gather handles up to 128 correlators
 constexpr int kTRun = 128;         // T runs are padded to whole blocks of this many entries
+constexpr int kCorrItem = 2048;    // entries per correlator work item of the sorted scatter
+constexpr int kInstPerUnit = 4;    // correlators of one class per cluster of the histogram scatter
 
 __global__ void __launch_bounds__(256) k_build_G(DevProblem pb, int64_t n_s, const uint8_t* s_occ, int Nst,
                                                  const __nv_bfloat16* pf16, int64_t Pst, uint32_t* G);
@@ -277,6 +283,8 @@ template <int K> __global__ void __launch_bounds__(256) k_scatter_T(SortedArgs a
 __global__ void __launch_bounds__(512) k_count_C(DevProblem pb, int64_t n_s, const uint16_t* cidxT,
                                                  uint32_t* ccount);
 __global__ void __launch_bounds__(512) k_fill_C(DevProblem pb, int64_t n_s, const uint16_t* cidxT,
-                                                const uint32_t* cbase, uint32_t* Tc);
+                                                uint32_t* cursor, uint32_t* Tc);
+__global__ void k_corr_item_count(const uint32_t* cbase, int64_t ncp, uint32_t* n_items);
+__global__ void k_corr_item_fill(const uint32_t* cbase, int64_t ncp, const uint32_t* item_base, uint2* items);
 
 }  // namespace vmc

@@ -202,9 +202,17 @@ __global__ void __launch_bounds__(512) k_fill_T(const uint32_t* G, int64_t Pst, 
 
 // Correlator runs: the samples of each correlator parameter, grouped by
 // parameter (class block off_q + state), built once per set of samples from
-// the transposed state array.  Block per class (its correlators share the
-// block, so a sample can appear once per correlator of the class),
-// shared-memory counters.
+// the transposed state array.  Grid (class, slice): a CTA counts the states
+// of its class's correlators over one slice of the samples in shared memory
+// and adds its counts to the global ones (a class shared by many correlators
+// spreads over many CTAs); the fill then places every entry through global
+// cursors.  A sample appears once per correlator of the class in that state.
+__device__ __forceinline__ void corr_slice(int64_t n_s, int nsl, int64_t* s0, int64_t* s1) {
+    const int64_t per = (n_s + nsl - 1) / nsl;
+    *s0 = min(n_s, (int64_t)blockIdx.y * per);
+    *s1 = min(n_s, *s0 + per);
+}
+
 __global__ void __launch_bounds__(512) k_count_C(DevProblem pb, int64_t n_s, const uint16_t* cidxT,
                                                  uint32_t* ccount) {
     extern __shared__ uint32_t hist[];
@@ -213,31 +221,53 @@ __global__ void __launch_bounds__(512) k_count_C(DevProblem pb, int64_t n_s, con
     const int d = (int)(pb.class_off[q + 1] - off);
     for (int i = threadIdx.x; i < d; i += blockDim.x) hist[i] = 0u;
     __syncthreads();
+    int64_t s0, s1;
+    corr_slice(n_s, gridDim.y, &s0, &s1);
     for (int j = pb.class_ptr[q]; j < pb.class_ptr[q + 1]; ++j) {
         const uint16_t* st = cidxT + (int64_t)pb.class_inst[j] * n_s;
-        for (int64_t s = threadIdx.x; s < n_s; s += blockDim.x) atomicAdd(&hist[st[s]], 1u);
+        for (int64_t s = s0 + threadIdx.x; s < s1; s += blockDim.x) atomicAdd(&hist[st[s]], 1u);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < d; i += blockDim.x) ccount[off + i] = hist[i];
+    for (int i = threadIdx.x; i < d; i += blockDim.x)
+        if (hist[i]) atomicAdd(&ccount[off + i], hist[i]);
 }
 
+// cursor[k] starts at the run start of parameter k (a copy of cbase)
 __global__ void __launch_bounds__(512) k_fill_C(DevProblem pb, int64_t n_s, const uint16_t* cidxT,
-                                                const uint32_t* cbase, uint32_t* Tc) {
-    extern __shared__ uint32_t cur[];
+                                                uint32_t* cursor, uint32_t* Tc) {
     const int q = blockIdx.x;
     const int64_t off = pb.class_off[q];
-    const int d = (int)(pb.class_off[q + 1] - off);
-    for (int i = threadIdx.x; i < d; i += blockDim.x) cur[i] = cbase[off + i];
-    __syncthreads();
+    int64_t s0, s1;
+    corr_slice(n_s, gridDim.y, &s0, &s1);
     // entry = sample << 5 | (parameter index mod 32): the scatter's warps own
     // 32 consecutive parameters and sum each one's contiguous segment
     for (int j = pb.class_ptr[q]; j < pb.class_ptr[q + 1]; ++j) {
         const uint16_t* st = cidxT + (int64_t)pb.class_inst[j] * n_s;
-        for (int64_t s = threadIdx.x; s < n_s; s += blockDim.x) {
+        for (int64_t s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
             const uint32_t state = st[s];
-            Tc[atomicAdd(&cur[state], 1u)] = ((uint32_t)s << 5) | (uint32_t)((off + state) & 31);
+            Tc[atomicAdd(&cursor[off + state], 1u)] = ((uint32_t)s << 5) | (uint32_t)((off + state) & 31);
         }
     }
+}
+
+// Work items of the correlator scatter: group g (parameters 32 g .. 32 g + 31,
+// one contiguous stretch of entries) is cut into pieces of at most
+// kCorrItem entries.  n_items[g] then its exclusive scan give item_base.
+__global__ void k_corr_item_count(const uint32_t* cbase, int64_t ncp, uint32_t* n_items) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t ng = (ncp + 31) / 32;
+    if (g >= ng) return;
+    const uint32_t len = cbase[min(ncp, 32 * g + 32)] - cbase[32 * g];
+    n_items[g] = len == 0 ? 1u : (len + kCorrItem - 1) / kCorrItem;
+}
+
+__global__ void k_corr_item_fill(const uint32_t* cbase, int64_t ncp, const uint32_t* item_base, uint2* items) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t ng = (ncp + 31) / 32;
+    if (g >= ng) return;
+    const uint32_t e0 = cbase[32 * g], e1 = cbase[min(ncp, 32 * g + 32)];
+    uint32_t i = item_base[g];
+    for (uint32_t e = e0; e == e0 || e < e1; e += kCorrItem) items[i++] = make_uint2((uint32_t)g, e);
 }
 
 // Correlator part of the gather for one sample: lane L looks up V[k_c] / C[k_c]
@@ -396,21 +426,22 @@ __device__ __forceinline__ void scatter_T_param(const SortedArgs& a, int pq) {
     }
 }
 
-// correlator states 32 w .. 32 w + 31: raw[k] = sum over the samples in state
-// k of t_s (the 1/C factor is applied by the caller).  The 32 runs are
-// contiguous, so the warp reads them as one coalesced stream; entries carry
-// k mod 32, equal values are contiguous, and a segmented warp scan hands each
-// segment's sum to its last lane, which adds it to the state's slot in shared
-// memory (one writer per state per step).
+// Correlator work item (group g, entries e0 .. min(e0 + kCorrItem, end of g)):
+// the group's parameters 32 g .. 32 g + 31 have contiguous runs, read as one
+// coalesced stream; entries carry k mod 32, equal values are contiguous, and
+// a segmented warp scan hands each segment's sum to its last lane, which adds
+// it to the parameter's slot in shared memory (one writer per parameter per
+// step).  The slots are then added to craw (zeroed by the caller): a long run
+// (a parameter shared by many correlators) spreads over several items.
 template <int K>
-__device__ __forceinline__ void scatter_C_group(const SortedArgs& a, int64_t w, float* slot) {
+__device__ __forceinline__ void scatter_C_item(const SortedArgs& a, uint2 item, float* slot) {
     const int lane = threadIdx.x & 31;
-    const int64_t k0 = w * 32;
+    const int64_t k0 = (int64_t)item.x * 32;
     const int64_t kend = min(a.pb.ncp, k0 + 32);
 #pragma unroll
     for (int kk = 0; kk < K; ++kk) slot[lane * K + kk] = 0.f;
     __syncwarp();
-    const uint32_t lo = a.cbase[k0], hi = a.cbase[kend];
+    const uint32_t lo = item.y, hi = min(a.cbase[kend], lo + (uint32_t)kCorrItem);
     for (uint32_t e0 = lo; e0 < hi; e0 += 32) {
         const uint32_t e = e0 + lane;
         const bool in = e < hi;
@@ -436,24 +467,26 @@ __device__ __forceinline__ void scatter_C_group(const SortedArgs& a, int64_t w, 
     }
     if (k0 + lane < kend)
 #pragma unroll
-        for (int kk = 0; kk < K; ++kk) a.craw[(k0 + lane) * K + kk] = slot[lane * K + kk];
+        for (int kk = 0; kk < K; ++kk) {
+            const float v = slot[lane * K + kk];
+            if (v != 0.f) atomicAdd(a.craw + (k0 + lane) * K + kk, v);
+        }
 }
 
-// Both halves of the scatter in one launch: CTAs [0, ncb) take 256
-// correlator states each (a warp per 32 states), the rest one pairing
-// amplitude per warp.  The short correlator CTAs go first so that they do
-// not form a tail behind the long pairing runs.
+// Both halves of the scatter in one launch: CTAs [0, ncb) take 8 correlator
+// work items each (a warp per item), the rest one pairing amplitude per
+// warp.  The short correlator CTAs go first so that they do not form a tail
+// behind the long pairing runs.
 template <int K>
 __global__ void __launch_bounds__(256) k_scatter_T(SortedArgs a) {
     if (a.stop && *a.stop) return;
     __shared__ float slots[8][32 * K];
-    const int ncb = (int)((a.pb.ncp + 255) / 256);
-    if ((int)blockIdx.x < ncb) {
-        const int64_t w = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-        if (w * 32 < a.pb.ncp) scatter_C_group<K>(a, w, slots[threadIdx.x >> 5]);
+    if ((int)blockIdx.x < a.ncb) {
+        const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+        if (i < (int64_t)*a.n_items) scatter_C_item<K>(a, a.items[i], slots[threadIdx.x >> 5]);
         return;
     }
-    const int pq = ((int)blockIdx.x - ncb) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int pq = ((int)blockIdx.x - a.ncb) * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (pq < a.pb.npf) scatter_T_param<K>(a, pq);
 }
 
