@@ -96,7 +96,7 @@ typedef struct {
 } vmc_hamiltonian;
 
 /* Ansatz (Eq. 11): sector (n_up, n_dn) with n_up + n_dn even and <= 64, and
- * correlator site lists corr_sites[corr_ptr[c] .. corr_ptr[c+1]) (each <= 6
+ * correlator site lists corr_sites[corr_ptr[c] .. corr_ptr[c+1]) (each <= 9
  * sites, host arrays).  The pairing runs over all spin orbitals.
  * corr_class[n_corr] (host, may be NULL = every correlator its own class)
  * lets correlators share parameters: the correlators of one class (the
@@ -182,12 +182,12 @@ int vmc_measure(vmc_handle h, const uint8_t* occ, int64_t n_s, void* stream);
 int vmc_num_samples(vmc_handle h, int64_t* n_s);
 
 /* Copy the O store out (host pointers, each may be NULL): occ[n_s][N],
- * E_L[n_s], corr_state[n_s][n_corr] (uint16), pf[n_s][P] with
+ * E_L[n_s], corr_state[n_s][n_corr] (uint32), pf[n_s][P] with
  * P = n_up(n_up-1)/2 + n_dn(n_dn-1)/2 + n_up n_dn in block order
  * (up-up triangle row-major, down-down triangle, up-down rectangle
  * row-major over ascending positions) converted to FP64 from the store
  * `store` (VMC_STORE_*).  Element (a, b), a < b, is O of f_{occ[a] occ[b]}. */
-int vmc_get_samples(vmc_handle h, uint8_t* occ, double* E_L, uint16_t* corr_state, double* pf,
+int vmc_get_samples(vmc_handle h, uint8_t* occ, double* E_L, uint32_t* corr_state, double* pf,
                     int store, void* stream);
 
 /* ln|Psi_n| for every stored sample (device out[n_s], FP64 pfaffian from scratch). */

@@ -71,7 +71,7 @@ struct vmc_ctx {
     uint32_t* d_item_base = nullptr;      // [groups + 1] exclusive scan, total at the end
     int64_t max_items = 0;
     int *d_site_cptr = nullptr, *d_site_corr = nullptr, *d_site_w = nullptr;
-    uint16_t* d_corr_site_w = nullptr;
+    uint32_t* d_corr_site_w = nullptr;
     uint32_t* d_pq_of = nullptr;   // pairing index -> p | q << 16
     int *d_nbr_ptr = nullptr, *d_nbr_site = nullptr;
     double* d_nbr_t = nullptr;
@@ -90,7 +90,7 @@ struct vmc_ctx {
     int Nst = 0, ncst = 0;
     int64_t Pst = 0;
     uint8_t* d_socc = nullptr;
-    uint16_t *d_cidx = nullptr, *d_cidxT = nullptr;
+    cstate_t *d_cidx = nullptr, *d_cidxT = nullptr;
     double* d_E = nullptr;
     double* d_pf64 = nullptr;
     float* d_pf32 = nullptr;
@@ -201,7 +201,7 @@ extern "C" int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, co
     for (int c = 0; c < h->ncorr; ++c) {
         int b = ans->corr_ptr[c], e = ans->corr_ptr[c + 1];
         int m = e - b;
-        if (m < 1 || m > 6) return fail(VMC_ERR_INVALID_ARG);
+        if (m < 1 || m > 9) return fail(VMC_ERR_INVALID_ARG);
         int w = 1;
         for (int j = b; j < e; ++j) {
             int s = ans->corr_sites[j];
@@ -253,9 +253,9 @@ extern "C" int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, co
     h->corr_off[h->ncorr] = h->ncp;
     h->nv = h->ncp + h->npf;
     // dense (correlator, site) -> 4^j weight table, 0 where the site is absent
-    std::vector<uint16_t> csw((size_t)std::max(h->ncorr, 1) * ns, 0);
+    std::vector<uint32_t> csw((size_t)std::max(h->ncorr, 1) * ns, 0);
     for (int s = 0; s < ns; ++s)
-        for (auto& pr : memb[s]) csw[(size_t)pr.first * ns + s] = (uint16_t)pr.second;
+        for (auto& pr : memb[s]) csw[(size_t)pr.first * ns + s] = (uint32_t)pr.second;
     std::vector<int> scptr(ns + 1, 0), scorr, sw;
     for (int s = 0; s < ns; ++s) {
         for (auto& pr : memb[s]) { scorr.push_back(pr.first); sw.push_back(pr.second); }
@@ -687,7 +687,7 @@ extern "C" int vmc_measure(vmc_handle h, const uint8_t* occ, int64_t n_s, void* 
     return read_status(h, st);
 }
 
-extern "C" int vmc_get_samples(vmc_handle h, uint8_t* occ, double* E_L, uint16_t* corr_state, double* pf,
+extern "C" int vmc_get_samples(vmc_handle h, uint8_t* occ, double* E_L, uint32_t* corr_state, double* pf,
                                int store, void* stream) {
     if (!h) return VMC_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
@@ -696,8 +696,8 @@ extern "C" int vmc_get_samples(vmc_handle h, uint8_t* occ, double* E_L, uint16_t
     if (occ) VCK(cudaMemcpy2D(occ, h->N, h->d_socc, h->Nst, h->N, n, cudaMemcpyDeviceToHost));
     if (E_L) VCK(cudaMemcpy(E_L, h->d_E, sizeof(double) * n, cudaMemcpyDeviceToHost));
     if (corr_state && h->ncorr > 0)
-        VCK(cudaMemcpy2D(corr_state, sizeof(uint16_t) * h->ncorr, h->d_cidx, sizeof(uint16_t) * h->ncst,
-                         sizeof(uint16_t) * h->ncorr, n, cudaMemcpyDeviceToHost));
+        VCK(cudaMemcpy2D(corr_state, sizeof(cstate_t) * h->ncorr, h->d_cidx, sizeof(cstate_t) * h->ncst,
+                         sizeof(cstate_t) * h->ncorr, n, cudaMemcpyDeviceToHost));
     if (pf) {
         if (store == VMC_STORE_FP64) {
             if (!h->d_pf64) return VMC_ERR_STATE;
@@ -873,9 +873,6 @@ template <typename AT, int K>
 static int launch_corr(vmc_ctx* h, const AT* T, const int* stop, cudaStream_t st) {
     if (h->ncorr == 0) return VMC_OK;
     size_t smem = (size_t)h->maxd * K * sizeof(AT);
-    if (smem > h->smem_optin) return VMC_ERR_UNSUPPORTED;
-    auto kern = k_corr_scatter<AT, K>;
-    VCK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     CorrArgs<AT> a{};
     a.pb = h->pb;
     a.n_s = h->n_s;
@@ -885,6 +882,15 @@ static int launch_corr(vmc_ctx* h, const AT* T, const int* stop, cudaStream_t st
     a.units = h->d_units;
     a.stop = stop;
     VCK(cudaMemsetAsync(h->d_corrraw, 0, sizeof(AT) * h->ncp * K, st));
+    if (smem + 1024 > h->smem_optin) {   // histograms beyond shared memory: global additions
+        const dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((h->n_s + 255) / 256, 64)),
+                        (unsigned)h->ncorr);
+        k_corr_scatter_global<AT, K><<<grid, 256, 0, st>>>(a); h->n_launch++;
+        VCK(cudaGetLastError());
+        return VMC_OK;
+    }
+    auto kern = k_corr_scatter<AT, K>;
+    VCK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<h->n_units * kCorrCluster, 256, smem, st>>>(a); h->n_launch++;
     VCK(cudaGetLastError());
     return VMC_OK;
@@ -938,12 +944,13 @@ static int ensure_sorted(vmc_ctx* h, cudaStream_t st) {
     if (h->ncorr > 0) {
         // (class, slice) grid: a class shared by many correlators spreads over
         // several CTAs
-        const size_t csm = (size_t)h->maxd * 4;
+        const bool shist = (size_t)h->maxd * 4 + 1024 <= h->smem_optin;   // shared-memory counters fit
+        const size_t csm = shist ? (size_t)h->maxd * 4 : 0;
         const int nsl = std::max(1, std::min(64, (2 * h->nsm + h->n_class - 1) / h->n_class));
         const dim3 cgrid((unsigned)h->n_class, (unsigned)nsl);
         VCK(cudaFuncSetAttribute(k_count_C, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
         VCK(cudaMemsetAsync(h->d_ccount, 0, sizeof(uint32_t) * h->ncp, st));
-        k_count_C<<<cgrid, 512, csm, st>>>(h->pb, h->n_s, h->d_cidxT, h->d_ccount); h->n_launch++;
+        k_count_C<<<cgrid, 512, csm, st>>>(h->pb, h->n_s, h->d_cidxT, h->d_ccount, shist ? 1 : 0); h->n_launch++;
         k_scan_params<<<1, 1024, 0, st>>>(h->d_ccount, (int)h->ncp, 0u, h->d_cbase); h->n_launch++;
         VCK(cudaMemcpyAsync(h->d_ccount, h->d_cbase, sizeof(uint32_t) * h->ncp, cudaMemcpyDeviceToDevice, st));
         k_fill_C<<<cgrid, 512, 0, st>>>(h->pb, h->n_s, h->d_cidxT, h->d_ccount, h->d_Tc); h->n_launch++;
@@ -979,12 +986,11 @@ static GatherKern gather_kernel(int u) {
 }
 
 // the sorted product applies: BF16 store with its sorted copies, the gather's
-// table and the run builders' counters within shared memory, at most 128
-// correlators, rows of at most 2048 elements
+// table within shared memory, at most 128 correlators, rows of at most 2048
+// elements
 template <int K>
 static bool sorted_usable(const vmc_ctx* h) {
     if (!h->use_sorted || !h->d_G || h->ncorr > 32 * kCorrPerLane) return false;
-    if ((size_t)h->maxd * 4 > h->smem_optin) return false;                                  // run counters
     if ((size_t)h->npf * K * 4 + (size_t)(h->ncorr + 1) * 4 > h->smem_optin) return false;   // gather table
     return gather_kernel<K>((int)((h->Pst / 4 + 31) / 32)) != nullptr;
 }

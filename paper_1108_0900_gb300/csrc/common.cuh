@@ -75,6 +75,10 @@ enum StatusBits : int {
 // Device view of a problem.  All arrays are device pointers owned by the
 // handle.
 // ---------------------------------------------------------------------------
+// correlator state index sum_j 4^j (n_up + 2 n_dn) of one correlator (up to
+// 9 sites: 18 bits)
+using cstate_t = uint32_t;
+
 struct DevProblem {
     int ns;        // spatial orbitals
     int M;         // spin orbitals
@@ -98,7 +102,7 @@ struct DevProblem {
     const int* site_cptr;      // [ns+1]
     const int* site_corr;      // correlator id
     const int* site_w;         // 4^j weight of the site inside that correlator
-    const uint16_t* corr_site_w;   // [ncorr][ns] 4^j weight of site s in correlator c, 0 if absent
+    const uint32_t* corr_site_w;   // [ncorr][ns] 4^j weight of site s in correlator c, 0 if absent
     // Hubbard hopping lists: site s hops to nbr_site[k] with amplitude nbr_t[k]
     const int* nbr_ptr;        // [ns+1]
     const int* nbr_site;

@@ -17,7 +17,7 @@ namespace vmc {
 // corr_raw[class_off_q + state] (zeroed by the caller; a class with more
 // correlators spreads over several units).
 // Slices start on multiples of 8 samples; each thread takes 8 consecutive
-// samples per step (one 16-byte load of states, K x 8 values of t).  Every
+// samples per step (two 16-byte loads of states, K x 8 values of t).  Every
 // CTA of the cluster must call this.
 template <typename AT, int K>
 __device__ __forceinline__ void corr_cluster_histogram(const CorrArgs<AT>& a, AT* h, int u) {
@@ -36,18 +36,18 @@ __device__ __forceinline__ void corr_cluster_histogram(const CorrArgs<AT>& a, AT
     // 16-byte loads need the rows to start on a 16-byte boundary
     const bool vec = ((a.n_s & 7) == 0);
     for (int ji = unit.y; ji < unit.z; ++ji) {
-        const uint16_t* st = a.cidxT + (int64_t)pb.class_inst[ji] * a.n_s;
+        const cstate_t* st = a.cidxT + (int64_t)pb.class_inst[ji] * a.n_s;
         int64_t s = s0;
         if (vec) {
             for (int64_t g = s0 + 8 * (int64_t)threadIdx.x; g + 8 <= s1; g += 8 * (int64_t)blockDim.x) {
-                const uint4 sv = *(const uint4*)(st + g);
-                const uint32_t w4[4] = {sv.x, sv.y, sv.z, sv.w};
+                const uint4 sa = *(const uint4*)(st + g), sb = *(const uint4*)(st + g + 4);
+                const uint32_t w8[8] = {sa.x, sa.y, sa.z, sa.w, sb.x, sb.y, sb.z, sb.w};
                 AT tv[8 * K];
 #pragma unroll
                 for (int j = 0; j < 8 * K; ++j) tv[j] = a.T[g * K + j];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    const int i = (int)((w4[j >> 1] >> (16 * (j & 1))) & 0xFFFFu);
+                    const int i = (int)w8[j];
 #pragma unroll
                     for (int kk = 0; kk < K; ++kk) atomicAdd(&h[i * K + kk], tv[j * K + kk]);
                 }

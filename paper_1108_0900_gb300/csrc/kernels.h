@@ -29,7 +29,7 @@ struct SampleArgs {
     // O store
     uint8_t* s_occ;       // [n_s][Nst]
     int Nst;
-    uint16_t* s_cidx;     // [n_s][ncst]
+    cstate_t* s_cidx;     // [n_s][ncst]
     int ncst;
     double* s_E;
     double* s_pf64;
@@ -47,7 +47,7 @@ struct LogPsiArgs {
     int64_t n_s;
     const uint8_t* s_occ;
     int Nst;
-    const uint16_t* s_cidx;
+    const cstate_t* s_cidx;
     int ncst;
     int XS;
     size_t warp_bytes;
@@ -72,7 +72,7 @@ struct MainArgs {
     int64_t n_s;
     const uint8_t* s_occ;
     int Nst;
-    const uint16_t* s_cidx;
+    const cstate_t* s_cidx;
     int ncst;
     const void* s_pf;
     int64_t Pst;
@@ -87,7 +87,7 @@ template <typename AT>
 struct CorrArgs {
     DevProblem pb;
     int64_t n_s;
-    const uint16_t* cidxT;  // [ncorr][n_s]
+    const cstate_t* cidxT;  // [ncorr][n_s]
     const AT* T;            // [n_s][K]
     AT* corr_raw;           // [ncp][K] sum over samples of t_s per state (zeroed by the caller)
     const int4* units;      // cluster work units (class, first, end into class_inst)
@@ -126,6 +126,7 @@ template <typename ST, typename AT, int K, bool GATHER>
 __global__ void __launch_bounds__(512) k_sr_main(MainArgs<AT> a);
 template <typename AT, int K>
 __global__ void __cluster_dims__(kCorrCluster, 1, 1) __launch_bounds__(256) k_corr_scatter(CorrArgs<AT> a);
+template <typename AT, int K> __global__ void __launch_bounds__(256) k_corr_scatter_global(CorrArgs<AT> a);
 template <typename AT, typename VT, int K> __global__ void __launch_bounds__(256) k_finalize_S(FinArgs<AT, VT> a);
 template <typename AT> __global__ void __launch_bounds__(256) k_finalize_grad(FinArgs<AT, double> a);
 __global__ void k_build_T_grad(const double* E, int64_t n_s, double* T, double* E_part);
@@ -133,7 +134,7 @@ template <typename TA, typename TB, int K>
 __global__ void __launch_bounds__(256) k_dot_part(const TA* x, const TB* y, int64_t n, double* part, const int* stop);
 template <typename AT>
 __global__ void __launch_bounds__(256) k_reduce_pf(const AT* part, int nblk, int npfK, AT* raw);
-__global__ void k_transpose_cidx(const uint16_t* cidx, int ncst, int ncorr, int64_t n_s, uint16_t* cidxT);
+__global__ void k_transpose_cidx(const cstate_t* cidx, int ncst, int ncorr, int64_t n_s, cstate_t* cidxT);
 template <typename VT> __global__ void k_cast(const double* src, VT* dst, int64_t n, double scale);
 
 // conjugate-gradient scalars (FP64, device): rr, |b|^2, tol^2 |b|^2,
@@ -212,7 +213,7 @@ struct StreamArgs {
     int64_t n_s;
     const uint8_t* s_occ;
     int Nst;
-    const uint16_t* s_cidx;
+    const cstate_t* s_cidx;
     int ncst;
     const void* s_pf;
     int64_t Pst;
@@ -237,7 +238,7 @@ namespace vmc {
 struct SortedArgs {
     DevProblem pb;
     int64_t n_s;
-    const uint16_t* s_cidx;
+    const cstate_t* s_cidx;
     int ncst;
     const uint32_t* G;      // [n_s][Pst] (pq << 16) | bf16
     int64_t Pst;
@@ -280,9 +281,9 @@ __global__ void __launch_bounds__(512) k_fill_T(const uint32_t* G, int64_t Pst, 
 constexpr int gather_threads(int K) { return K == 1 ? 1024 : 256; }
 template <int K, int U> __global__ void __launch_bounds__(gather_threads(K)) k_gather_G(SortedArgs a);
 template <int K> __global__ void __launch_bounds__(256) k_scatter_T(SortedArgs a);
-__global__ void __launch_bounds__(512) k_count_C(DevProblem pb, int64_t n_s, const uint16_t* cidxT,
-                                                 uint32_t* ccount);
-__global__ void __launch_bounds__(512) k_fill_C(DevProblem pb, int64_t n_s, const uint16_t* cidxT,
+__global__ void __launch_bounds__(512) k_count_C(DevProblem pb, int64_t n_s, const cstate_t* cidxT,
+                                                 uint32_t* ccount, int shared_hist);
+__global__ void __launch_bounds__(512) k_fill_C(DevProblem pb, int64_t n_s, const cstate_t* cidxT,
                                                 uint32_t* cursor, uint32_t* Tc);
 __global__ void k_corr_item_count(const uint32_t* cbase, int64_t ncp, uint32_t* n_items);
 __global__ void k_corr_item_fill(const uint32_t* cbase, int64_t ncp, const uint32_t* item_base, uint2* items);

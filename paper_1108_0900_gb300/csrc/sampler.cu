@@ -568,7 +568,7 @@ __global__ void k_walkers(SampleArgs a) {
         } else {
             if (a.s_E && lane == 0) a.s_E[s] = e_lane;
             if (a.s_cidx)
-                for (int c = lane; c < pb.ncorr; c += 32) a.s_cidx[s * a.ncst + c] = (uint16_t)cidx[c];
+                for (int c = lane; c < pb.ncorr; c += 32) a.s_cidx[s * a.ncst + c] = (cstate_t)cidx[c];
             for (int e = lane; e < pb.P; e += 32) {
                 uint16_t t = pb.pairtab[e];
                 int aa = t & 255, bb = t >> 8;
@@ -650,7 +650,7 @@ __global__ void k_logpsi(LogPsiArgs a) {
         __syncwarp();
     }
     // correlators
-    const uint16_t* ci = a.s_cidx + s * a.ncst;
+    const cstate_t* ci = a.s_cidx + s * a.ncst;
     double lc = 0.0;
     for (int c = lane; c < pb.ncorr; c += 32) {
         double v = pb.C64[pb.corr_off[c] + ci[c]];

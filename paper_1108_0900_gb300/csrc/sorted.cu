@@ -213,27 +213,36 @@ __device__ __forceinline__ void corr_slice(int64_t n_s, int nsl, int64_t* s0, in
     *s1 = min(n_s, *s0 + per);
 }
 
-__global__ void __launch_bounds__(512) k_count_C(DevProblem pb, int64_t n_s, const uint16_t* cidxT,
-                                                 uint32_t* ccount) {
+// shared_hist = 0 (classes of more states than shared memory holds): count
+// straight into the global counters
+__global__ void __launch_bounds__(512) k_count_C(DevProblem pb, int64_t n_s, const cstate_t* cidxT,
+                                                 uint32_t* ccount, int shared_hist) {
     extern __shared__ uint32_t hist[];
     const int q = blockIdx.x;
     const int64_t off = pb.class_off[q];
     const int d = (int)(pb.class_off[q + 1] - off);
-    for (int i = threadIdx.x; i < d; i += blockDim.x) hist[i] = 0u;
-    __syncthreads();
+    if (shared_hist) {
+        for (int i = threadIdx.x; i < d; i += blockDim.x) hist[i] = 0u;
+        __syncthreads();
+    }
     int64_t s0, s1;
     corr_slice(n_s, gridDim.y, &s0, &s1);
     for (int j = pb.class_ptr[q]; j < pb.class_ptr[q + 1]; ++j) {
-        const uint16_t* st = cidxT + (int64_t)pb.class_inst[j] * n_s;
-        for (int64_t s = s0 + threadIdx.x; s < s1; s += blockDim.x) atomicAdd(&hist[st[s]], 1u);
+        const cstate_t* st = cidxT + (int64_t)pb.class_inst[j] * n_s;
+        for (int64_t s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+            if (shared_hist) atomicAdd(&hist[st[s]], 1u);
+            else atomicAdd(&ccount[off + st[s]], 1u);
+        }
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < d; i += blockDim.x)
-        if (hist[i]) atomicAdd(&ccount[off + i], hist[i]);
+    if (shared_hist) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < d; i += blockDim.x)
+            if (hist[i]) atomicAdd(&ccount[off + i], hist[i]);
+    }
 }
 
 // cursor[k] starts at the run start of parameter k (a copy of cbase)
-__global__ void __launch_bounds__(512) k_fill_C(DevProblem pb, int64_t n_s, const uint16_t* cidxT,
+__global__ void __launch_bounds__(512) k_fill_C(DevProblem pb, int64_t n_s, const cstate_t* cidxT,
                                                 uint32_t* cursor, uint32_t* Tc) {
     const int q = blockIdx.x;
     const int64_t off = pb.class_off[q];
@@ -242,7 +251,7 @@ __global__ void __launch_bounds__(512) k_fill_C(DevProblem pb, int64_t n_s, cons
     // entry = sample << 5 | (parameter index mod 32): the scatter's warps own
     // 32 consecutive parameters and sum each one's contiguous segment
     for (int j = pb.class_ptr[q]; j < pb.class_ptr[q + 1]; ++j) {
-        const uint16_t* st = cidxT + (int64_t)pb.class_inst[j] * n_s;
+        const cstate_t* st = cidxT + (int64_t)pb.class_inst[j] * n_s;
         for (int64_t s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
             const uint32_t state = st[s];
             Tc[atomicAdd(&cursor[off + state], 1u)] = ((uint32_t)s << 5) | (uint32_t)((off + state) & 31);
@@ -274,7 +283,7 @@ __global__ void k_corr_item_fill(const uint32_t* cbase, int64_t ncp, const uint3
 // for c = L + 32 j (at most 32 kCorrPerLane correlators).  The loads are only
 // issued here; the caller adds cv after its pairing work, which hides them.
 template <int K>
-__device__ __forceinline__ void corr_lookups(const DevProblem& pb, const int* coff, const uint16_t* cid,
+__device__ __forceinline__ void corr_lookups(const DevProblem& pb, const int* coff, const cstate_t* cid,
                                              const float* V, const float* invC, int lane,
                                              float (&cv)[kCorrPerLane][K]) {
 #pragma unroll

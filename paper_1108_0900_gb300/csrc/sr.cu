@@ -102,6 +102,22 @@ __global__ void __launch_bounds__(512) k_sr_main(MainArgs<AT> a) {
     for (int i = threadIdx.x; i < npf * K; i += blockDim.x) dst[i] = acc[i];
 }
 
+// correlator scatter for classes of more states than shared memory holds:
+// every (correlator, sample) adds t_s to its parameter in global memory
+template <typename AT, int K>
+__global__ void __launch_bounds__(256) k_corr_scatter_global(CorrArgs<AT> a) {
+    if (a.stop && *a.stop) return;
+    const DevProblem& pb = a.pb;
+    const int c = blockIdx.y;
+    const cstate_t* st = a.cidxT + (int64_t)c * a.n_s;
+    const int64_t off = pb.corr_off[c];
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < a.n_s; s += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = off + st[s];
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) atomicAdd(a.corr_raw + k * K + kk, a.T[s * K + kk]);
+    }
+}
+
 // correlator-major scatter: one thread-block cluster per correlator class
 template <typename AT, int K>
 __global__ void __cluster_dims__(kCorrCluster, 1, 1) __launch_bounds__(256) k_corr_scatter(CorrArgs<AT> a) {
@@ -282,9 +298,9 @@ __global__ void __launch_bounds__(256) k_dot_part(const TA* x, const TB* y, int6
     block_reduce_store<K>(loc, part);
 }
 
-__global__ void k_transpose_cidx(const uint16_t* cidx, int ncst, int ncorr, int64_t n_s, uint16_t* cidxT) {
+__global__ void k_transpose_cidx(const cstate_t* cidx, int ncst, int ncorr, int64_t n_s, cstate_t* cidxT) {
     // tile 32 samples x 32 correlators
-    __shared__ uint16_t tile[32][33];
+    __shared__ cstate_t tile[32][33];
     int64_t s0 = (int64_t)blockIdx.x * 32;
     int c0 = blockIdx.y * 32;
     int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
@@ -632,6 +648,12 @@ template __global__ void k_sr_main<__nv_bfloat16, double, 2, false>(MainArgs<dou
 template __global__ void k_sr_main<__nv_bfloat16, float, 1, true>(MainArgs<float>);
 template __global__ void k_sr_main<__nv_bfloat16, float, 2, true>(MainArgs<float>);
 template __global__ void k_sr_main<__nv_bfloat16, float, 4, true>(MainArgs<float>);
+template __global__ void k_corr_scatter_global<double, 1>(CorrArgs<double>);
+template __global__ void k_corr_scatter_global<double, 2>(CorrArgs<double>);
+template __global__ void k_corr_scatter_global<double, 4>(CorrArgs<double>);
+template __global__ void k_corr_scatter_global<float, 1>(CorrArgs<float>);
+template __global__ void k_corr_scatter_global<float, 2>(CorrArgs<float>);
+template __global__ void k_corr_scatter_global<float, 4>(CorrArgs<float>);
 template __global__ void k_corr_scatter<double, 1>(CorrArgs<double>);
 template __global__ void k_corr_scatter<double, 2>(CorrArgs<double>);
 template __global__ void k_corr_scatter<double, 4>(CorrArgs<double>);

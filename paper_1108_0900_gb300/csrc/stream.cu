@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(768, 1) k_sr_stream(StreamArgs a) {
         float t[K];
 #pragma unroll
         for (int kk = 0; kk < K; ++kk) t[kk] = 0.f;
-        const uint16_t* cid = a.s_cidx + s * a.ncst;
+        const cstate_t* cid = a.s_cidx + s * a.ncst;
         for (int c = lane; c < pb.ncorr; c += 32) {
             const int k = coff[c] + (int)__ldg(cid + c);
             const float ic = __ldg(a.invC + k);
@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(512, 1) k_sr_stream_bf16c(StreamArgs a) {
     for (int64_t s = s0; s < a.n_s; s += stride, ++it) {
         const int b = it & 1;
         float t = 0.f;
-        const uint16_t* cid = a.s_cidx + s * a.ncst;
+        const cstate_t* cid = a.s_cidx + s * a.ncst;
         for (int c = lane; c < pb.ncorr; c += 32) {
             const int k = coff[c] + (int)__ldg(cid + c);
             t += __ldg(a.V + k) * __ldg(a.invC + k);

@@ -164,11 +164,16 @@ def all_pair_correlators(n: int) -> List[np.ndarray]:
 # draws
 # --------------------------------------------------------------------------
 
-def translation_classes(corr: str, n_corr: int) -> np.ndarray:
+def translation_classes(corr: str, n_corr: int, Lx: int = 1) -> np.ndarray:
     """Translation classes of the generated correlators: bond correlators
-    alternate x and y bonds (two classes), plaquettes of one shape form one."""
+    alternate x and y bonds (two classes); 3x3 plaquettes form one class per
+    sublattice of their anchor site (the two 3x3 correlators of the paper's
+    4x4 study, Sec. III.A); other plaquettes of one shape form one class."""
     if corr == "pair":
         return (np.arange(n_corr) % 2).astype(np.int32)
+    if corr == "3x3":
+        a = np.arange(n_corr)
+        return ((a % Lx + a // Lx) % 2).astype(np.int32)
     return np.zeros(n_corr, np.int32)
 
 
@@ -223,11 +228,13 @@ def hubbard(name, Lx, Ly, n_up, n_dn, corr, U=4.0, t=1.0, seed=0,
         cs = plaquette_correlators(Lx, Ly, 2, 2)
     elif corr == "2x3":
         cs = plaquette_correlators(Lx, Ly, 2, 3)
+    elif corr == "3x3":
+        cs = plaquette_correlators(Lx, Ly, 3, 3)
     elif corr == "none":
         cs = []
     else:
         raise ValueError(corr)
-    cls = translation_classes(corr, len(cs)) if shared and cs else None
+    cls = translation_classes(corr, len(cs), Lx) if shared and cs else None
     C, f = draw_params(rng, cs, 2 * n_sites, cls)
     bonds = square_bonds(Lx, Ly)
     init = draw_configs(rng, n_walkers, n_sites, n_up, n_dn)

@@ -252,7 +252,7 @@ def vmc_get_samples(h: Handle, store=VMC_STORE_FP64, stream=None):
     n = vmc_num_samples(h)
     occ = np.zeros((n, h.N), np.uint8)
     E = np.zeros(n)
-    cs = np.zeros((n, max(h.wl.n_corr, 1)), np.uint16)
+    cs = np.zeros((n, max(h.wl.n_corr, 1)), np.uint32)
     pf = np.zeros((n, h.P))
     _check(lib().vmc_get_samples(h.h, _np_ptr(occ), _np_ptr(E), _np_ptr(cs), _np_ptr(pf), int(store),
                                  _stream(stream)), "vmc_get_samples")

@@ -54,9 +54,13 @@ def test_create_rejects_invalid_problems():
     dup = inputs.hubbard("x", 3, 2, 2, 2, "pair", n_walkers=1)
     dup.corr_sites = [np.array([0, 0], np.int32)]                       # repeated site
     assert _create_rc(dup) == -1
-    seven = inputs.hubbard("x", 4, 4, 2, 2, "none", n_walkers=1)
-    seven.corr_sites = [np.arange(7, dtype=np.int32)]                   # 4^7 states: too many
-    assert _create_rc(seven) == -1
+    ten = inputs.hubbard("x", 4, 4, 2, 2, "none", n_walkers=1)
+    ten.corr_sites = [np.arange(10, dtype=np.int32)]                    # 4^10 states: beyond 9 sites
+    assert _create_rc(ten) == -1
+    mixed = inputs.hubbard("x", 3, 2, 2, 2, "pair", n_walkers=1)
+    mixed.corr_sites = [np.array([0, 1], np.int32), np.array([0, 1, 2], np.int32)]
+    assert _create_rc(mixed, corr_class=np.zeros(2, np.int32)) == -1   # one class, two sizes
+    assert _create_rc(mixed, corr_class=np.array([1, 1], np.int32)) == -1   # class 0 unused
     badbond = inputs.hubbard("x", 3, 2, 2, 2, "pair", n_walkers=1)
     badbond.bonds = np.array([[0, 9]], np.int32)
     badbond.bond_t = np.ones(1)

@@ -78,6 +78,10 @@ SMALL = {
                                          shared=True),
     "cfg5shared": lambda: inputs.hubbard("s5", 8, 8, 28, 28, "2x3", seed=13, n_walkers=9, samples_per_walker=3,
                                          shared=True),
+    # the paper's 4x4 layout: a 3x3 correlator at every site, one shared block
+    # of 4^9 amplitudes per sublattice (524,784 parameters)
+    "paper4x4_3x3": lambda: inputs.hubbard("p33", 4, 4, 8, 8, "3x3", seed=14, n_walkers=6, samples_per_walker=3,
+                                           shared=True),
 }
 
 
