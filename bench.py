@@ -99,9 +99,9 @@ class Clocks:
 # ---------------------------------------------------------------------------
 
 # DRAM bytes read per sorted BF16 product (k_gather_G + k_scatter_T launches) on
-# this workload, as counted by ncu (dram__bytes): G 418 MB + T and correlator
-# runs 427 MB.
-SORTED_PASS_DRAM_BYTES = 845.0e6
+# this workload, as counted by ncu (dram__bytes): G 427 MB + T and correlator
+# runs 428 MB.
+SORTED_PASS_DRAM_BYTES = 855.0e6
 
 
 def run_gpu(args, rank, world, dist):
@@ -186,26 +186,37 @@ def run_gpu(args, rank, world, dist):
     h2d = (wl.C.nbytes + wl.f.nbytes)
     d2h = x_host.numel() * 8
 
-    # ---- translation-invariant correlators (every 2x3 plaquette of the 8x8
-    # lattice reads one shared block of 4,096 amplitudes), mixed path ---------
+    # ---- translation-invariant (shared) correlators, mixed path: every 2x3
+    # plaquette of the 8x8 lattice reading one block of 4,096 amplitudes, and
+    # the paper's 4x4 layout (a 3x3 correlator at every site, one block of 4^9
+    # amplitudes per sublattice, 524,784 parameters) -------------------------
     shared = None
     if args.shared_steps > 0:
-        wls = inputs.hubbard("8x8-2x3-shared", 8, 8, 28, 28, "2x3", seed=1005, n_walkers=16384,
-                             samples_per_walker=4, shared=True)
-        hs = V.vmc_create(wls, walker_precision=V.VMC_FP32, keep_fp64_store=False, keep_lowp_store=True)
-        V.vmc_set_params(hs, wls.C, wls.f)
-        V.vmc_set_walkers(hs, wls.init_occ)
-        V.vmc_sample(hs, wls.burn_in_sweeps, seed + 17)
-        ms_s, infos_s, prof_s, _ = timed(hs, "mixed", args.shared_steps, 1, profile=True)
-        shared = {"workload": "8x8 periodic Hubbard U/t=4, 28+28 electrons, 64 2x3 plaquettes sharing one block "
-                              f"of 4,096 amplitudes + pfaffian (n_v={wls.n_params:,}), 16,384 walkers x 4 samples",
-                  "ms_per_step": round(ms_s, 3),
-                  "sv_gbs": round(prof_s["pass_bytes"] / (prof_s["pass_ms"] * 1e-3) / 1e9, 1)
-                  if prof_s and prof_s["pass_ms"] > 0 else None,
-                  "cg_inner_iterations": float(np.mean([i["iterations"] for i in infos_s])),
-                  "true_rel_residual": max(i["true_rel_residual"] for i in infos_s),
-                  "converged": all(i["converged"] for i in infos_s)}
-        hs.close()
+        shared = {}
+        cases = {
+            "8x8_2x3_shared": (inputs.hubbard("8x8-2x3-shared", 8, 8, 28, 28, "2x3", seed=1005, n_walkers=16384,
+                                              samples_per_walker=4, shared=True),
+                               "8x8 periodic Hubbard U/t=4, 28+28 electrons, 64 2x3 plaquettes sharing one block "
+                               "of 4,096 amplitudes + pfaffian"),
+            "4x4_3x3_sublattice": (inputs.hubbard("4x4-3x3", 4, 4, 8, 8, "3x3", seed=1006, n_walkers=16384,
+                                                  samples_per_walker=4, shared=True),
+                                   "4x4 periodic Hubbard U/t=4, 8+8 electrons, a 3x3 correlator at every site "
+                                   "sharing one block of 4^9 amplitudes per sublattice + pfaffian"),
+        }
+        for key, (wls, text) in cases.items():
+            hs = V.vmc_create(wls, walker_precision=V.VMC_FP32, keep_fp64_store=False, keep_lowp_store=True)
+            V.vmc_set_params(hs, wls.C, wls.f)
+            V.vmc_set_walkers(hs, wls.init_occ)
+            V.vmc_sample(hs, wls.burn_in_sweeps, seed + 17)
+            ms_s, infos_s, prof_s, _ = timed(hs, "mixed", args.shared_steps, 1, profile=True)
+            shared[key] = {"workload": f"{text} (n_v={wls.n_params:,}), 16,384 walkers x 4 samples",
+                           "ms_per_step": round(ms_s, 3),
+                           "sv_gbs": round(prof_s["pass_bytes"] / (prof_s["pass_ms"] * 1e-3) / 1e9, 1)
+                           if prof_s and prof_s["pass_ms"] > 0 else None,
+                           "cg_inner_iterations": float(np.mean([i["iterations"] for i in infos_s])),
+                           "true_rel_residual": max(i["true_rel_residual"] for i in infos_s),
+                           "converged": all(i["converged"] for i in infos_s)}
+            hs.close()
 
     # ---- plain FP64 path ------------------------------------------------------
     fp64 = None

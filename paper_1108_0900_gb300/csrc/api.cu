@@ -999,7 +999,7 @@ static bool sorted_usable(const vmc_ctx* h) {
 // Tv, the pairing sums to d_pfraw and the correlator sums to d_corrraw (FP32)
 template <int K>
 static int launch_sorted(vmc_ctx* h, const float* V, const float* invC, const double* obv_part, float* Tv,
-                         const int* stop, cudaStream_t st, double* tt_part = nullptr) {
+                         const int* stop, cudaStream_t st, double* tt_part = nullptr, bool craw_zero = false) {
     if (!sorted_usable<K>(h)) return VMC_ERR_UNSUPPORTED;
     int rc = ensure_sorted(h, st);
     if (rc) return rc;
@@ -1038,7 +1038,9 @@ static int launch_sorted(vmc_ctx* h, const float* V, const float* invC, const do
     grid = std::min(grid, kNumPart * kMaxK);   // one partial slot of tt sums
     gk<<<grid, gthreads, smem, st>>>(a); h->n_launch++;
     h->last_gather_grid = grid;
-    if (h->ncp > 0) VCK(cudaMemsetAsync(h->d_corrraw, 0, sizeof(float) * h->ncp * K, st));
+    // correlator sums accumulate into zero (the fused CG update re-zeroes
+    // them as it reads them, so its products skip this)
+    if (h->ncp > 0 && !craw_zero) VCK(cudaMemsetAsync(h->d_corrraw, 0, sizeof(float) * h->ncp * K, st));
     k_scatter_T<K><<<a.ncb + (h->npf + 7) / 8, 256, 0, st>>>(a); h->n_launch++;
     VCK(cudaGetLastError());
     if (h->prof) {
@@ -1299,16 +1301,18 @@ static int cg_loop(vmc_ctx* h, const void* s_pf, int kind, const VT* b, VT* x, V
     // centered sorted product with the fused update: gather, scatter, x/r, p
     bool fused = false;
     if constexpr (sizeof(ST) == 2 && sizeof(VT) == 4) fused = sorted_usable<1>(h);
+    if (fused && h->ncp > 0) VCK(cudaMemsetAsync(h->d_corrraw, 0, sizeof(float) * h->ncp, st));
     while (!done) {
         for (int j = 0; j < kChunk; ++j) {
             if (fused) {
                 if constexpr (sizeof(ST) == 2 && sizeof(VT) == 4) {
-                    int rc = launch_sorted<1>(h, p, h->d_invC32, obp_part, (float*)h->d_T, h->d_stop, st, tt_part);
+                    int rc = launch_sorted<1>(h, p, h->d_invC32, obp_part, (float*)h->d_T, h->d_stop, st, tt_part,
+                                              true);
                     if (rc) return rc;
                     CgFusedArgs<float> f{};
                     f.x = x; f.r = r; f.p = p;
                     f.pf_raw = (const float*)h->d_pfraw;
-                    f.corr_raw = (const float*)h->d_corrraw;
+                    f.corr_raw = (float*)h->d_corrraw;
                     f.invC = h->d_invC32;
                     f.n = n; f.ncp = h->ncp;
                     f.inv_n = 1.0 / (double)h->n_s;

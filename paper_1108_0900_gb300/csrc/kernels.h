@@ -146,7 +146,7 @@ struct CgFusedArgs {
     VT* r;
     const VT* p;
     const VT* pf_raw;       // [npf] pairing sums of the centered pass
-    const VT* corr_raw;     // [ncp] correlator sums
+    VT* corr_raw;           // [ncp] correlator sums (zeroed after reading)
     const VT* invC;         // [ncp]
     int64_t n, ncp;
     double inv_n, shift;

@@ -467,6 +467,7 @@ __global__ void __launch_bounds__(256) k_cg_fxr(CgFusedArgs<VT> a) {
             rv[u] = in ? a.r[i] : VT(0);
             pv[u] = in ? a.p[i] : VT(0);
             raw[u] = !in ? VT(0) : i < a.ncp ? a.corr_raw[i] * a.invC[i] : a.pf_raw[i - a.ncp];
+            if (in && i < a.ncp) a.corr_raw[i] = VT(0);   // ready for the next product's additions
         }
         VT part = VT(0);
 #pragma unroll
