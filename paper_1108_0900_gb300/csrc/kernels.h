@@ -275,10 +275,10 @@ __global__ void __launch_bounds__(1024) k_scan_params(const uint32_t* total, int
 __global__ void __launch_bounds__(512) k_fill_T(const uint32_t* G, int64_t Pst, int P, int64_t s_begin,
                                                 int64_t s_end, int npf, const uint32_t* offs, const uint32_t* base,
                                                 uint32_t* T);
-// threads per CTA of the sorted gather: one v table per CTA, so the one-vector
-// gather runs one 1024-thread CTA per SM, which leaves the most L1 for the G
-// stream (measured 5 % faster than five 256-thread CTAs)
-constexpr int gather_threads(int K) { return K == 1 ? 1024 : 256; }
+// threads per CTA of the sorted gather: one v table per CTA, so the
+// one-vector gather runs few, large CTAs, which leaves L1 to the G stream
+// (512 threads with the next row prefetched measured best)
+constexpr int gather_threads(int K) { return K == 1 ? 512 : 256; }
 template <int K, int U> __global__ void __launch_bounds__(gather_threads(K)) k_gather_G(SortedArgs a);
 template <int K> __global__ void __launch_bounds__(256) k_scatter_T(SortedArgs a);
 __global__ void __launch_bounds__(512) k_count_C(DevProblem pb, int64_t n_s, const cstate_t* cidxT,

@@ -303,10 +303,10 @@ __device__ __forceinline__ void corr_lookups(const DevProblem& pb, const int* co
 // gather: t_s = sum_c V[k_c]/C[k_c] + sum_e W_e v[pq(e)] - Obar . V, warp per
 // sample.  Centering t_s makes the scatter produce the covariance
 // (1/n) sum_s (t_s - Obar . V) O_s = S V directly, with no cancellation
-// between <O (O . V)> and Obar (Obar . V).
-// U = ceil(Pst / 128): every lane issues all of its U 16-byte loads of the
-// sample's row before the correlator lookups and before consuming any, so a
-// whole row (6 KB at 56 electrons) is in flight per warp.
+// between <O (O . V)> and Obar (Obar . V).  U = ceil(Pst / 128): every lane
+// holds its U 16-byte words of a row, and the warp loads its next row while
+// it works on the current one, so a whole row (6 KB at 56 electrons) is
+// always in flight per warp.
 template <int K, int U>
 __global__ void __launch_bounds__(gather_threads(K)) k_gather_G(SortedArgs a) {
     if (a.stop && *a.stop) return;
@@ -330,13 +330,27 @@ __global__ void __launch_bounds__(gather_threads(K)) k_gather_G(SortedArgs a) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int n4 = (int)(a.Pst >> 2);
     double tt = 0.0;   // lane 0: sum of the warp's centered t_s^2
-    for (int64_t s = (int64_t)blockIdx.x * nw + wid; s < a.n_s; s += (int64_t)gridDim.x * nw) {
+    const int64_t gstride = (int64_t)gridDim.x * nw;
+    uint4 g[U];
+    {
+        const int64_t s = (int64_t)blockIdx.x * nw + wid;
         const uint4* g4 = (const uint4*)(a.G + s * a.Pst);
-        uint4 g[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int i = lane + 32 * u;
-            g[u] = i < n4 ? __ldcs(g4 + i) : make_uint4(0u, 0u, 0u, 0u);
+            g[u] = (s < a.n_s && i < n4) ? __ldcs(g4 + i) : make_uint4(0u, 0u, 0u, 0u);
+        }
+    }
+    for (int64_t s = (int64_t)blockIdx.x * nw + wid; s < a.n_s; s += gstride) {
+        uint4 gn[U];
+        {
+            const int64_t sn = s + gstride;
+            const uint4* g4n = (const uint4*)(a.G + sn * a.Pst);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int i = lane + 32 * u;
+                gn[u] = (sn < a.n_s && i < n4) ? __ldcs(g4n + i) : make_uint4(0u, 0u, 0u, 0u);
+            }
         }
         float t[K], w[K];
 #pragma unroll
@@ -370,6 +384,8 @@ __global__ void __launch_bounds__(gather_threads(K)) k_gather_G(SortedArgs a) {
             const double c = (double)(t[0] - obv[0]);
             tt += c * c;
         }
+#pragma unroll
+        for (int u = 0; u < U; ++u) g[u] = gn[u];
     }
     if (K == 1 && a.tt_part) {   // p . S p of a centered product, for CG
         __shared__ double red[32];
