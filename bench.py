@@ -111,8 +111,8 @@ def run_gpu(args, rank, world, dist):
 
     local = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(local)
-    wl = inputs.config(5)
-    seed = inputs.seed_sampling_for(5) + 7919 * rank
+    wl = inputs.workload("hubbard8x8_2x3")
+    seed = inputs.seed_sampling_for("hubbard8x8_2x3") + 7919 * rank
     shift, tol = wl.shift, 1e-6
     max_iter = 20000
 
@@ -264,7 +264,7 @@ def run_gpu(args, rank, world, dist):
                      "algorithmic_bytes_per_launch": per_launch_bytes,
                      "launches": prof["pass_launches"] if prof else None,
                      # DRAM bytes per pass (gather + scatter) from the ncu capture summarised in
-                     # profiles/k_gather_G_k_scatter_T_bf16_cfg5.md
+                     # profiles/k_gather_G_k_scatter_T_bf16_hubbard8x8_2x3.md
                      "traffic": SORTED_PASS_DRAM_BYTES},
         "e2e": {"value": round(float(np.median(e2e_ms)) / 1e3, 6), "unit": "s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
@@ -288,7 +288,7 @@ def oracle_step(n_walkers: int, spw: int, seed: int, cg_iters_full: float):
     import oracle
     from paper_1108_0900_gb300 import inputs
 
-    wl = inputs.config(5, n_walkers=n_walkers, samples_per_walker=spw)
+    wl = inputs.workload("hubbard8x8_2x3", n_walkers=n_walkers, samples_per_walker=spw)
     P = oracle.Problem(wl)
     occ = wl.init_occ.copy()
     step = np.zeros(n_walkers, np.uint64)
@@ -356,7 +356,7 @@ def run_sv_only(args):
     from paper_1108_0900_gb300 import vmcsr as V
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
-    wl = inputs.config(5)
+    wl = inputs.workload("hubbard8x8_2x3")
     h = V.vmc_create(wl, walker_precision=V.VMC_FP32, keep_fp64_store=True, keep_lowp_store=True)
     V.vmc_set_params(h, wl.C, wl.f)
     cfgs = inputs.draw_configs(np.random.default_rng(555), wl.n_samples, wl.n_sites, wl.n_up, wl.n_dn)

@@ -265,30 +265,36 @@ def abinitio(name, n_orb, n_up, n_dn, n_chol=48, seed=0, n_walkers=64,
                     init_occ=init)
 
 
-def config(i: int, **over) -> Workload:
-    """The five synthetic workloads of the hot-path scope table (1-based)."""
-    if i == 1:
-        kw = dict(n_walkers=64, samples_per_walker=64, shift=1e-3, tol=1e-8)
-        kw.update(over)
-        return hubbard("cfg1_4x4_pair_fp64", 4, 4, 8, 8, "pair", seed=1001, **kw)
-    if i == 2:
-        kw = dict(n_walkers=4096, samples_per_walker=16, tol=1e-6)
-        kw.update(over)
-        return hubbard("cfg2_4x4_2x2plaq", 4, 4, 8, 8, "2x2", seed=1002, **kw)
-    if i == 3:
-        kw = dict(n_walkers=8192, samples_per_walker=8, tol=1e-6)
-        kw.update(over)
-        return abinitio("cfg3_abinitio24", 24, 12, 12, seed=1003, **kw)
-    if i == 4:
-        kw = dict(n_walkers=16384, samples_per_walker=8, tol=1e-6)
-        kw.update(over)
-        return hubbard("cfg4_8x8_2x2plaq", 8, 8, 28, 28, "2x2", seed=1004, **kw)
-    if i == 5:
-        kw = dict(n_walkers=16384, samples_per_walker=4, tol=1e-6)
-        kw.update(over)
-        return hubbard("cfg5_8x8_2x3plaq", 8, 8, 28, 28, "2x3", seed=1005, **kw)
-    raise ValueError(i)
+_WORKLOADS = {
+    # name: (constructor, default sizes, problem seed, sampling seed)
+    "hubbard4x4_pair": (lambda **kw: hubbard("hubbard4x4_pair", 4, 4, 8, 8, "pair", **kw),
+                        dict(n_walkers=64, samples_per_walker=64, shift=1e-3, tol=1e-8), 1001, 2001),
+    "hubbard4x4_2x2": (lambda **kw: hubbard("hubbard4x4_2x2", 4, 4, 8, 8, "2x2", **kw),
+                       dict(n_walkers=4096, samples_per_walker=16, tol=1e-6), 1002, 2002),
+    "abinitio24": (lambda **kw: abinitio("abinitio24", 24, 12, 12, **kw),
+                   dict(n_walkers=8192, samples_per_walker=8, tol=1e-6), 1003, 2003),
+    "hubbard8x8_2x2": (lambda **kw: hubbard("hubbard8x8_2x2", 8, 8, 28, 28, "2x2", **kw),
+                       dict(n_walkers=16384, samples_per_walker=8, tol=1e-6), 1004, 2004),
+    "hubbard8x8_2x3": (lambda **kw: hubbard("hubbard8x8_2x3", 8, 8, 28, 28, "2x3", **kw),
+                       dict(n_walkers=16384, samples_per_walker=4, tol=1e-6), 1005, 2005),
+}
+WORKLOAD_NAMES = tuple(_WORKLOADS)
 
 
-def seed_sampling_for(i: int) -> int:
-    return 2000 + i
+def workload(name: str, **over) -> Workload:
+    """One of the five synthetic workloads of the hot path, by name:
+    hubbard4x4_pair (4x4 Hubbard, 8+8 electrons, pair correlators, 4,096
+    samples, FP64 checks), hubbard4x4_2x2 (2x2 plaquettes, 65,536 samples),
+    abinitio24 (24 orbitals, 12+12 electrons, all pair correlators, 65,536
+    samples), hubbard8x8_2x2 (8x8, 28+28 electrons, 2x2 plaquettes, 131,072
+    samples) and hubbard8x8_2x3 (8x8, 28+28 electrons, 2x3 plaquettes, 65,536
+    samples).  Keyword arguments override the sizes."""
+    ctor, kw, seed, _ = _WORKLOADS[name]
+    kw = dict(kw)
+    kw.update(over)
+    return ctor(seed=seed, **kw)
+
+
+def seed_sampling_for(name: str) -> int:
+    """Seed of the Metropolis chains used with the named workload."""
+    return _WORKLOADS[name][3]

@@ -66,17 +66,17 @@ def make(wl, prec=V.VMC_FP64, keep64=True, keeplow=True, n_walkers=None, spw=Non
 
 
 SMALL = {
-    "cfg1": lambda: inputs.config(1, n_walkers=24, samples_per_walker=6),
-    "cfg2": lambda: inputs.config(2, n_walkers=37, samples_per_walker=5),
-    "cfg5geom": lambda: inputs.config(5, n_walkers=9, samples_per_walker=3),
-    "cfg3abinitio": lambda: inputs.config(3, n_walkers=8, samples_per_walker=2),
+    "hubbard4x4_pair": lambda: inputs.workload("hubbard4x4_pair", n_walkers=24, samples_per_walker=6),
+    "hubbard4x4_2x2": lambda: inputs.workload("hubbard4x4_2x2", n_walkers=37, samples_per_walker=5),
+    "hubbard8x8_2x3_geometry": lambda: inputs.workload("hubbard8x8_2x3", n_walkers=9, samples_per_walker=3),
+    "abinitio24": lambda: inputs.workload("abinitio24", n_walkers=8, samples_per_walker=2),
     "tiny2x2": lambda: inputs.hubbard("t", 2, 2, 1, 1, "2x2", seed=5, n_walkers=7, samples_per_walker=4),
     "nocorr3x2": lambda: inputs.hubbard("t", 3, 2, 2, 2, "none", seed=6, n_walkers=11, samples_per_walker=3),
     # translation-invariant correlators: x and y bonds share two blocks; every
     # 2x3 plaquette of the 8x8 lattice reads one block of 4,096 amplitudes
-    "cfg1shared": lambda: inputs.hubbard("s1", 4, 4, 8, 8, "pair", seed=12, n_walkers=24, samples_per_walker=6,
+    "hubbard4x4_pair_shared": lambda: inputs.hubbard("s1", 4, 4, 8, 8, "pair", seed=12, n_walkers=24, samples_per_walker=6,
                                          shared=True),
-    "cfg5shared": lambda: inputs.hubbard("s5", 8, 8, 28, 28, "2x3", seed=13, n_walkers=9, samples_per_walker=3,
+    "hubbard8x8_2x3_shared": lambda: inputs.hubbard("s5", 8, 8, 28, 28, "2x3", seed=13, n_walkers=9, samples_per_walker=3,
                                          shared=True),
     # the paper's 4x4 layout: a 3x3 correlator at every site, one shared block
     # of 4^9 amplitudes per sublattice (524,784 parameters)
@@ -88,7 +88,7 @@ SMALL = {
 @pytest.fixture(scope="module", params=list(SMALL))
 def case(request):
     wl = SMALL[request.param]()
-    P, smp, mm, occ_end, step_end = oracle_chains(wl, 3, wl.samples_per_walker, inputs.seed_sampling_for(1))
+    P, smp, mm, occ_end, step_end = oracle_chains(wl, 3, wl.samples_per_walker, inputs.seed_sampling_for("hubbard4x4_pair"))
     E, O = P.measure(smp)
     return dict(name=request.param, wl=wl, P=P, smp=smp, E=E, O=O, mm=mm, occ_end=occ_end, step_end=step_end)
 
@@ -145,11 +145,11 @@ def _chain_compare(case, prec, margin, max_bad=0.0):
     n_burn = 3
     P = oracle.Problem(wl)
     o_occ, o_step = wl.init_occ.copy(), np.zeros(wl.n_walkers, np.uint64)
-    smp, _, _, fc = P.sample(o_occ, o_step, inputs.seed_sampling_for(1), n_burn, wl.samples_per_walker,
+    smp, _, _, fc = P.sample(o_occ, o_step, inputs.seed_sampling_for("hubbard4x4_pair"), n_burn, wl.samples_per_walker,
                              close_tol=margin, return_first_close=True)
     h = make(wl, prec=prec)
     V.vmc_set_walkers(h, wl.init_occ)
-    V.vmc_sample(h, n_burn, inputs.seed_sampling_for(1))
+    V.vmc_sample(h, n_burn, inputs.seed_sampling_for("hubbard4x4_pair"))
     occ, E, cs, pf = V.vmc_get_samples(h, V.VMC_STORE_FP64 if prec == V.VMC_FP64 else V.VMC_STORE_FP32)
     wocc, wstep = V.vmc_get_walkers(h)
     assert np.array_equal(wstep, o_step)
@@ -192,12 +192,12 @@ def test_sampler_outputs_fp64(case, refresh, tol):
     n_burn = 3
     P = oracle.Problem(wl)
     o_occ, o_step = wl.init_occ.copy(), np.zeros(wl.n_walkers, np.uint64)
-    smp, mm, _ = P.sample(o_occ, o_step, inputs.seed_sampling_for(1), n_burn, wl.samples_per_walker)
+    smp, mm, _ = P.sample(o_occ, o_step, inputs.seed_sampling_for("hubbard4x4_pair"), n_burn, wl.samples_per_walker)
     E_or, O_or = P.measure(smp)
     ref = oracle_compact(wl, smp, O_or)
     h = make(wl, prec=V.VMC_FP64, refresh_every=refresh)
     V.vmc_set_walkers(h, wl.init_occ)
-    V.vmc_sample(h, n_burn, inputs.seed_sampling_for(1))
+    V.vmc_sample(h, n_burn, inputs.seed_sampling_for("hubbard4x4_pair"))
     occ, E, cs, pf = V.vmc_get_samples(h, V.VMC_STORE_FP64)
     safe = np.repeat(mm > 1e-9, wl.samples_per_walker)
     assert safe.mean() >= 0.9
@@ -299,7 +299,7 @@ def test_logpsi_and_backward(case):
 
 
 def test_autograd_logpsi():
-    wl = SMALL["cfg1"]()
+    wl = SMALL["hubbard4x4_pair"]()
     P, smp, *_ = oracle_chains(wl, 2, wl.samples_per_walker, 11)
     h = make(wl)
     V.vmc_measure(h, smp)
@@ -370,27 +370,27 @@ def test_errors_and_edges():
 _FULL = {}
 
 
-def full5(prec, cfg=5):
-    if (prec, cfg) not in _FULL:
-        wl = inputs.config(cfg)
+def full_size(prec, name="hubbard8x8_2x3"):
+    if (prec, name) not in _FULL:
+        wl = inputs.workload(name)
         h = make(wl, prec=prec, keep64=True, keeplow=True)
         cfgs = inputs.draw_configs(np.random.default_rng(555), wl.n_samples, wl.n_sites, wl.n_up, wl.n_dn)
         V.vmc_measure(h, cfgs)
         _FULL.clear()
-        _FULL[(prec, cfg)] = (wl, h, cfgs)
-    return _FULL[(prec, cfg)]
+        _FULL[(prec, name)] = (wl, h, cfgs)
+    return _FULL[(prec, name)]
 
 
-@pytest.mark.parametrize("cfg,prec,tol", [(5, V.VMC_FP64, 1e-10), (5, V.VMC_FP32, 5e-3),
-                                          (3, V.VMC_FP64, 1e-10), (3, V.VMC_FP32, 5e-3)])
-def test_full_size_sampled_outputs(cfg, prec, tol):
+@pytest.mark.parametrize("name,prec,tol", [("hubbard8x8_2x3", V.VMC_FP64, 1e-10), ("hubbard8x8_2x3", V.VMC_FP32, 5e-3),
+                                           ("abinitio24", V.VMC_FP64, 1e-10), ("abinitio24", V.VMC_FP32, 5e-3)])
+def test_full_size_sampled_outputs(name, prec, tol):
     """Every sample of the full workload is evaluated on the GPU; a random
     subset (and the last sample) is recomputed by the oracle."""
-    wl, h, cfgs = full5(prec, cfg)
+    wl, h, cfgs = full_size(prec, name)
     occ, E, cs, pf = V.vmc_get_samples(h, V.VMC_STORE_FP64 if prec == V.VMC_FP64 else V.VMC_STORE_FP32)
     assert np.array_equal(occ, cfgs)
     P = oracle.Problem(wl)
-    pick = np.random.default_rng(1).choice(len(cfgs), 24 if cfg == 5 else 8, replace=False)
+    pick = np.random.default_rng(1).choice(len(cfgs), 24 if name == "hubbard8x8_2x3" else 8, replace=False)
     pick[-1] = len(cfgs) - 1
     E_or, O_or = P.measure(cfgs[pick])
     ref = oracle_compact(wl, cfgs[pick], O_or)
@@ -407,10 +407,10 @@ def test_full_size_invariants():
     # (rebuilding every walker's inverse from scratch before each stored
     # sample, so no rank-2 update drift enters O)
     _FULL.clear()
-    wl = inputs.config(5)
+    wl = inputs.workload("hubbard8x8_2x3")
     h = make(wl, prec=V.VMC_FP64, keep64=True, keeplow=True, refresh_every=1)
     V.vmc_set_walkers(h, wl.init_occ)
-    V.vmc_sample(h, 10, inputs.seed_sampling_for(5))
+    V.vmc_sample(h, 10, inputs.seed_sampling_for("hubbard8x8_2x3"))
     g, stats = V.sr_gradient(h, V.VMC_STORE_FP64)
     ncp = wl.n_corr_params
     eps = wl.shift
@@ -446,10 +446,10 @@ def test_full_size_invariants():
 
 
 def test_full_size_sampling_run():
-    wl = inputs.config(5)
+    wl = inputs.workload("hubbard8x8_2x3")
     h = make(wl, prec=V.VMC_FP32, keep64=False, keeplow=True)
     V.vmc_set_walkers(h, wl.init_occ)
-    V.vmc_sample(h, 2, inputs.seed_sampling_for(5))
+    V.vmc_sample(h, 2, inputs.seed_sampling_for("hubbard8x8_2x3"))
     occ, E, cs, pf = V.vmc_get_samples(h, V.VMC_STORE_FP32)
     assert np.all(np.isfinite(E)) and np.all(np.isfinite(pf))
     assert np.all(occ[:, :wl.n_up] < wl.n_sites) and np.all(occ[:, wl.n_up:] >= wl.n_sites)
@@ -464,7 +464,7 @@ def test_bf16_product_over_several_sample_chunks():
     it must equal the FP64 product of the same stored BF16 values
     (FP32 accumulation: 2e-5)."""
     sp = pytest.importorskip("scipy.sparse")
-    wl = inputs.config(1, n_walkers=16512, samples_per_walker=8)
+    wl = inputs.workload("hubbard4x4_pair", n_walkers=16512, samples_per_walker=8)
     n = wl.n_walkers * wl.samples_per_walker
     assert n > 2 * 65536
     cfgs = inputs.draw_configs(np.random.default_rng(31), n, wl.n_sites, wl.n_up, wl.n_dn)

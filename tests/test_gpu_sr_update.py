@@ -27,9 +27,9 @@ def rel(a, b):
 
 
 CASES = {
-    "cfg1": lambda: inputs.config(1, n_walkers=24, samples_per_walker=6),
+    "hubbard4x4_pair": lambda: inputs.workload("hubbard4x4_pair", n_walkers=24, samples_per_walker=6),
     "tiny2x2": lambda: inputs.hubbard("t", 2, 2, 2, 2, "2x2", seed=5, n_walkers=16, samples_per_walker=4),
-    "cfg3abinitio": lambda: inputs.config(3, n_walkers=8, samples_per_walker=2),
+    "abinitio24": lambda: inputs.workload("abinitio24", n_walkers=8, samples_per_walker=2),
 }
 
 
@@ -95,7 +95,7 @@ def _dense_mean(wl, occ, cs, pf):
 
 def test_sr_update_fp32_walkers_and_lowp_means():
     """x_0 uses the mean of the store the gradient was taken over."""
-    wl = CASES["cfg1"]()
+    wl = CASES["hubbard4x4_pair"]()
     P, smp, E, O, h = _measured(wl, prec=V.VMC_FP32)
     y = np.random.default_rng(4).standard_normal(wl.n_params)
     alpha = np.concatenate([wl.C, wl.f])
@@ -221,7 +221,7 @@ class _SumLocal:
 @pytest.mark.parametrize("store", [V.VMC_STORE_FP64, V.VMC_STORE_FP32])
 def test_rank_local_sums_add_up_to_the_whole(store):
     from paper_1108_0900_gb300 import shard
-    wl = CASES["cfg1"]()
+    wl = CASES["hubbard4x4_pair"]()
     P = oracle.Problem(wl)
     occ = wl.init_occ.copy()
     step = np.zeros(wl.n_walkers, np.uint64)

@@ -35,9 +35,9 @@ def _pair_index(wl, occ):
     return p * M - p * (p + 1) // 2 + (q - p - 1)
 
 
-@pytest.mark.parametrize("cfg,nw,spw", [(5, 1024, 4), (1, 64, 8)])
-def test_noalloc_matches_existing_entry_points(cfg, nw, spw):
-    wl = inputs.config(cfg, n_walkers=nw, samples_per_walker=spw)
+@pytest.mark.parametrize("name,nw,spw", [("hubbard8x8_2x3", 1024, 4), ("hubbard4x4_pair", 64, 8)])
+def test_noalloc_matches_existing_entry_points(name, nw, spw):
+    wl = inputs.workload(name, n_walkers=nw, samples_per_walker=spw)
     h = V.vmc_create(wl, walker_precision=V.VMC_FP64, keep_fp64_store=True, keep_lowp_store=True)
     V.vmc_set_params(h, wl.C, wl.f)
     cfgs = inputs.draw_configs(np.random.default_rng(77), nw * spw, wl.n_sites, wl.n_up, wl.n_dn)
