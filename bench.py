@@ -218,6 +218,46 @@ def run_gpu(args, rank, world, dist):
                            "converged": all(i["converged"] for i in infos_s)}
             hs.close()
 
+    # ---- synthetic ab initio Hamiltonian (24 orbitals, 12+12 electrons, all
+    # 276 pair correlators, two-electron integrals from 48 Cholesky vectors),
+    # 8,192 walkers x 8 samples, mixed path: the SR step and, alone, the
+    # sampling + local-energy pass (every single and double excitation of
+    # each sample) ----------------------------------------------------------
+    abinit = None
+    if args.abinitio_steps > 0:
+        wla = inputs.workload("abinitio24")
+        ha = V.vmc_create(wla, walker_precision=V.VMC_FP32, keep_fp64_store=False, keep_lowp_store=True)
+        V.vmc_set_params(ha, wla.C, wla.f)
+        V.vmc_set_walkers(ha, wla.init_occ)
+        sa = inputs.seed_sampling_for("abinitio24") + 7919 * rank
+        V.vmc_sample(ha, wla.burn_in_sweeps, sa)
+        ms_a, infos_a, prof_a, _ = timed(ha, "mixed", args.abinitio_steps, 1, profile=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record()
+        for k in range(args.abinitio_steps):
+            V.vmc_sample(ha, 0, sa + 100 + k)
+        e1.record()
+        barrier()
+        ms_walk = e0.elapsed_time(e1) / args.abinitio_steps
+        ns_orb, nu, nd = wla.n_sites, wla.n_up, wla.n_dn
+        eu, ed = ns_orb - nu, ns_orb - nd
+        n_dbl = (nu * (nu - 1) // 2) * (eu * (eu - 1) // 2) + (nd * (nd - 1) // 2) * (ed * (ed - 1) // 2) \
+            + nu * nd * eu * ed
+        n_sgl = nu * eu + nd * ed
+        abinit = {"workload": f"synthetic ab initio, 24 orbitals, 12+12 electrons, 276 pair correlators + pfaffian "
+                              f"(n_v={wla.n_params:,}), (pq|rs) from 48 Cholesky vectors, 8,192 walkers x 8 samples",
+                  "ms_per_step": round(ms_a, 3),
+                  "sample_and_local_energy_ms": round(ms_walk, 3),
+                  "excitations_per_sample": {"single": n_sgl, "double": n_dbl},
+                  "double_excitations_per_s": round(wla.n_samples * n_dbl / (ms_walk * 1e-3), 1),
+                  "sv_gbs": round(prof_a["pass_bytes"] / (prof_a["pass_ms"] * 1e-3) / 1e9, 1)
+                  if prof_a and prof_a["pass_ms"] > 0 else None,
+                  "cg_inner_iterations": float(np.mean([i["iterations"] for i in infos_a])),
+                  "true_rel_residual": max(i["true_rel_residual"] for i in infos_a),
+                  "converged": all(i["converged"] for i in infos_a)}
+        ha.close()
+
     # ---- plain FP64 path ------------------------------------------------------
     fp64 = None
     if not args.no_fp64:
@@ -257,6 +297,7 @@ def run_gpu(args, rank, world, dist):
         "sv_gbs": round(ach, 1) if ach else None,
         "fp64_path": fp64,
         "shared_correlators": shared,
+        "abinitio": abinit,
         "speedup_vs_fp64_path": round(fp64["ms_per_step"] / ms, 3) if fp64 else None,
         "roofline": {"bound": "hbm", "kernel": "k_gather_G<1,U> + k_scatter_T<1> (sorted two-pass Eq. 7 product, BF16 store)",
                      "achieved": round(ach, 1) if ach else None, "peak": peak, "unit": "GB/s",
@@ -397,6 +438,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--shared-steps", type=int, default=2,
                     help="SR steps timed on the shared-correlator 8x8 workload (0: skip)")
+    ap.add_argument("--abinitio-steps", type=int, default=2,
+                    help="SR steps timed on the 24-orbital ab initio workload (0: skip)")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-cg-iters", type=float, default=350.0)
