@@ -90,6 +90,10 @@ def lib():
             L.orc_enumerate.argtypes = [vp, vp]
             L.orc_enumerate.restype = i64
             L.orc_exact_weights.argtypes = [vp, i64, vp, vp]
+            L.orc_lm_apply.argtypes = [vp, i64, vp, vp, i32, vp, vp, dbl, vp, vp, vp]
+            L.orc_lm_apply.restype = i32
+            L.orc_apply_hop.argtypes = [i32, vp, i32, i32, vp]
+            L.orc_apply_hop.restype = i32
             _lib = L
     return _lib
 
@@ -196,6 +200,27 @@ class Problem:
             raise ArithmeticError("singular pairing submatrix")
         return E, O
 
+    # --- linear method (Sec. II.B) -----------------------------------------
+    def lm_apply(self, occ, factors, x, weights=None, want_S: bool = True):
+        """(Hx, Sx) over the basis {Psi, Psi^1 .. Psi^nv} by Eq. 10 with the
+        factored Hamiltonian of Eq. 9 (``factors`` = (L, R, c0) from
+        ``lm_factors``); weights None = 1/n_s per sample."""
+        occ = np.ascontiguousarray(occ, np.uint8)
+        Lf, Rf, c0 = factors
+        Lf = np.ascontiguousarray(Lf, np.float64)
+        Rf = np.ascontiguousarray(Rf, np.float64)
+        x = np.ascontiguousarray(x, np.float64)
+        nv1 = self.n_params() + 1
+        assert x.shape == (nv1,)
+        w = None if weights is None else np.ascontiguousarray(weights, np.float64)
+        Hx = np.zeros(nv1)
+        Sx = np.zeros(nv1) if want_S else None
+        rc = lib().orc_lm_apply(self.ref, occ.shape[0], _ptr(occ), _ptr(w), Lf.shape[0], _ptr(Lf),
+                                _ptr(Rf), float(c0), _ptr(x), _ptr(Hx), _ptr(Sx))
+        if rc != 0:
+            raise ArithmeticError("singular pairing submatrix")
+        return Hx, Sx
+
     # --- enumeration ---------------------------------------------------------
     def enumerate(self):
         n = int(lib().orc_sector_size(self.ref))
@@ -296,3 +321,126 @@ def cg(O, g, eps, tol, max_iter=None):
     rc = lib().orc_cg(O.shape[0], nv, _ptr(O), _ptr(g), float(eps), float(tol),
                       nv if max_iter is None else int(max_iter), _ptr(x), ct.byref(it), ct.byref(res))
     return x, it.value, res.value, rc == 0
+
+
+# --- linear method (Sec. II.B) ------------------------------------------------
+
+def lm_factors(wl):
+    """The Hamiltonian in the factored form of Eq. 9,
+    H = c0 + sum_mu Lhat_mu Rhat_mu,  Lhat_mu = sum_ij L^mu_ij E_ij,
+    E_ij = sum_sigma a+_{i sigma} a_{j sigma}  (spatial n x n matrices).
+
+    A one-body operator K = sum k_ij E_ij commutes with the particle number
+    Nhat and Nhat = N in the sector, so K = (K Nhat + Nhat K) / (2N): two terms
+    (L, R) = (k / 2N, I) and (I, k / 2N).
+    Hubbard: k_ij = -t per bond and direction; U n_up n_dn = (U/2)(E_ii E_ii -
+    E_ii) per site, so one term (U/2 e_i e_i^T, e_i e_i^T) per site and
+    c0 = -U N / 2.
+    Ab initio: a+_p a+_r a_s a_q = E_pq E_rs - delta_qr E_ps (spins summed),
+    so the two-body part is 1/2 sum_mu (sum_pq L^mu_pq E_pq)^2 - 1/2 sum_ps J_ps
+    E_ps with J_ps = sum_q (pq|qs): terms (L^mu / sqrt 2, L^mu / sqrt 2) and
+    k = h - J / 2."""
+    n, N = wl.n_sites, wl.n_up + wl.n_dn
+    Ls, Rs = [], []
+    c0 = 0.0
+    I = np.eye(n)
+    if wl.ham == 0:
+        k = np.zeros((n, n))
+        for (i, j), t in zip(wl.bonds, wl.bond_t):
+            if i == j:
+                continue
+            k[i, j] -= t
+            k[j, i] -= t
+        for i in range(n):
+            e = np.zeros((n, n))
+            e[i, i] = 1.0
+            Ls.append(0.5 * wl.U * e)
+            Rs.append(e)
+        c0 = -0.5 * wl.U * N
+    else:
+        chol = np.asarray(wl.chol, np.float64)
+        J = np.einsum("mpq,mqs->ps", chol, chol)
+        k = np.asarray(wl.h, np.float64) - 0.5 * J
+        for Lm in chol:
+            Ls.append(Lm / np.sqrt(2.0))
+            Rs.append(Lm / np.sqrt(2.0))
+    Ls += [k / (2.0 * N), I]
+    Rs += [I, k / (2.0 * N)]
+    return np.array(Ls), np.array(Rs), float(c0)
+
+
+def lm_davidson(apply, diag_S, shift_H: float, shift_S: float, tol: float = 1e-8,
+                max_iter: int = 300, max_sub: int = 24):
+    """Lowest eigenpair of (H + a D) x = lam (S + eps D) x (Eq. 8, shifts on
+    the parameter block D = diag(0, 1, .., 1)) by the generalized Davidson
+    method: Rayleigh-Ritz on a growing orthonormal basis V, residual
+    r = (H + a D) u - theta (S + eps D) u of the lowest Ritz pair, new
+    direction r / d with d the diagonal of S + eps D (the matrix-free
+    stand-in for diag(H - theta S)), Gram-Schmidt against V (twice); on
+    reaching max_sub columns the basis restarts from the current and the
+    previous Ritz vectors.  ``apply(v)`` returns (H v, S v).  Starts from
+    x = e_0 (the current wavefunction).  Returns (theta, x, iterations,
+    relative residual |r| / |theta (S + eps D) u|)."""
+    import scipy.linalg
+    n = diag_S.shape[0]
+    Dm = np.ones(n)
+    Dm[0] = 0.0
+    d = diag_S + shift_S * Dm
+
+    def op(v):
+        Hv, Sv = apply(v)
+        return Hv + shift_H * Dm * v, Sv + shift_S * Dm * v
+
+    V = np.zeros((n, 0))
+    HV = np.zeros((n, 0))
+    SV = np.zeros((n, 0))
+    t = np.zeros(n)
+    t[0] = 1.0
+    u_prev = None
+    theta, u, rel = np.nan, t, np.inf
+    for it in range(1, max_iter + 1):
+        for _ in range(2):
+            t = t - V @ (V.T @ t)
+        t = t / np.linalg.norm(t)
+        Ht, St = op(t)
+        V = np.column_stack([V, t])
+        HV = np.column_stack([HV, Ht])
+        SV = np.column_stack([SV, St])
+        h = V.T @ HV
+        s = V.T @ SV
+        h = 0.5 * (h + h.T)
+        s = 0.5 * (s + s.T)
+        w, c = scipy.linalg.eigh(h, s)
+        theta, cv = w[0], c[:, 0]
+        u = V @ cv
+        Hu, Su = HV @ cv, SV @ cv
+        r = Hu - theta * Su
+        rel = np.linalg.norm(r) / abs(theta * np.linalg.norm(Su))
+        if rel <= tol:
+            return theta, u / u[0], it, rel
+        t = -r / d
+        if V.shape[1] >= max_sub:
+            keep = [u] if u_prev is None else [u, u_prev]
+            Q, _ = np.linalg.qr(np.column_stack(keep))
+            prods = [op(q) for q in Q.T]
+            V = Q
+            HV = np.column_stack([a for a, _ in prods])
+            SV = np.column_stack([b for _, b in prods])
+        u_prev = u
+    return theta, u / u[0], max_iter, rel
+
+
+def lm_update(alpha, x, Sx0: float):
+    """Parameter update of the linear method (Sec. II.B): the eigenvector
+    x = (x_0, x_1 ..) taken relative to the component along Psi of the basis
+    orthogonalised to Psi, (S x)_0 = x_0 + sum_j Obar_j x_j; alpha' =
+    alpha + x_{1:} / (S x)_0."""
+    return np.asarray(alpha) + np.asarray(x[1:]) / Sx0
+
+
+def apply_hop(M: int, bits, p: int, q: int):
+    """a+_p a_q on a determinant given as occupation bits: (sign, bits')."""
+    b = np.ascontiguousarray(bits, np.uint8)
+    out = np.zeros(M, np.uint8)
+    sg = int(lib().orc_apply_hop(M, _ptr(b), p, q, _ptr(out)))
+    return sg, out

@@ -911,3 +911,114 @@ void orc_exact_weights(const orc_problem* P, int64_t n_conf, const uint8_t* occ,
     for (int64_t i = 0; i < n_conf; ++i) w[i] /= tot;
     free(la);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Accelerated linear method (Sec. II.B)                                     */
+/* ------------------------------------------------------------------------ */
+
+/* Products of the linear method's matrices with x = (x_0, x_1 .. x_nv) over
+ * the basis {Psi, Psi^1 .. Psi^nv}, Psi^j = dPsi/dalpha_j (component 0 is
+ * Psi itself, O_0 = 1):
+ *   Hx_i = sum_n w_n sum_{pq} Q_{n q p i} sum_mu L^mu_pq sum_{rs} R^mu_rs sum_j Q_{n r s j} x_j
+ *          + c0 Sx_i                                                  (Eq. 10)
+ *   Sx_i = sum_n w_n O_i(n) sum_j O_j(n) x_j,
+ * with Q_{n r s j} = <n| a+_r a_s |Psi^j> / Psi_n (Eq. 10) and the
+ * Hamiltonian in the factored form of Eq. 9, H = c0 + sum_mu Lhat_mu Rhat_mu,
+ * Lhat_mu = sum_{ij} L^mu_ij sum_sigma a+_{i sigma} a_{j sigma} (spatial
+ * matrices L^mu, R^mu of n_sites^2 entries).  w_n = 1/n_s when wgt is NULL.
+ * Every Q is built from scratch: the configuration n' with
+ * <n| a+_r a_s |n'> != 0, its explicit Jordan-Wigner sign, a fresh amplitude
+ * Psi_n' and a fresh O(n') (so Psi^j_n' = Psi_n' O_j(n')).  Sx may be NULL.
+ * Returns -1 if a pairing submatrix is singular. */
+int orc_lm_apply(const orc_problem* P, int64_t n_s, const uint8_t* occ, const double* wgt,
+                 int n_mu, const double* Lf, const double* Rf, double c0, const double* x,
+                 double* Hx, double* Sx)
+{
+    const int M = n_orb_M(P), N = P->n_up + P->n_dn, ns = P->n_sites;
+    const int64_t nv = orc_n_params(P);
+    memset(Hx, 0, sizeof(double) * (nv + 1));
+    if (Sx) memset(Sx, 0, sizeof(double) * (nv + 1));
+    /* per sample: every (r, s) of one spin with <n| a+_r a_s |n'> != 0 */
+    const int nmax = M * M;
+    double* ratio = (double*)malloc(sizeof(double) * nmax);
+    double* Op = (double*)malloc(sizeof(double) * (size_t)nmax * nv);   /* O(n') rows */
+    int* er = (int*)malloc(sizeof(int) * nmax);
+    int* es = (int*)malloc(sizeof(int) * nmax);
+    double* On = (double*)malloc(sizeof(double) * nv);
+    double* w = (double*)malloc(sizeof(double) * (n_mu > 0 ? n_mu : 1));
+    uint8_t bits[512], bnp[512], tmp[512], occp[256];
+    int rc = 0;
+    for (int64_t n = 0; n < n_s && rc == 0; ++n) {
+        const uint8_t* o = occ + n * N;
+        const double wn = wgt ? wgt[n] : 1.0 / (double)n_s;
+        occ_to_bits(P, o, bits);
+        double la0;
+        int s0;
+        orc_log_psi(P, o, &la0, &s0);
+        if (s0 == 0 || orc_logderiv(P, o, On) != 0) { rc = -1; break; }
+        int ne = 0;
+        for (int r = 0; r < M; ++r) {
+            if (!bits[r]) continue;
+            const int lo = r < ns ? 0 : ns;
+            for (int s = lo; s < lo + ns; ++s) {
+                if (s != r && bits[s]) continue;
+                /* n' = n with the electron at r moved to s */
+                memcpy(bnp, bits, M);
+                bnp[r] = 0;
+                bnp[s] = 1;
+                const int sg = hop_sign(M, bnp, r, s, tmp);      /* a+_r a_s |n'> = sg |n> */
+                bits_to_occ(M, bnp, occp);
+                double* row = Op + (size_t)ne * nv;
+                if (orc_logderiv(P, occp, row) != 0) { rc = -1; break; }
+                ratio[ne] = (double)sg * amp_ratio(P, occp, la0, s0);
+                er[ne] = r;
+                es[ne] = s;
+                ++ne;
+            }
+            if (rc) break;
+        }
+        if (rc) break;
+        /* y_rs = sum_j Q_{n r s j} x_j, w_mu = sum_rs R^mu_rs y_rs */
+        for (int mu = 0; mu < n_mu; ++mu) w[mu] = 0.0;
+        for (int e = 0; e < ne; ++e) {
+            double ox = x[0];
+            const double* row = Op + (size_t)e * nv;
+            for (int64_t j = 0; j < nv; ++j) ox += row[j] * x[1 + j];
+            const double y = ratio[e] * ox;
+            const int i = er[e] % ns, k = es[e] % ns;
+            for (int mu = 0; mu < n_mu; ++mu) w[mu] += Rf[((size_t)mu * ns + i) * ns + k] * y;
+        }
+        /* z_pq = sum_mu L^mu_pq w_mu; Hx_i += w_n sum_{pq} z_pq Q_{n q p i}:
+         * the excitation of Q_{n q p i} moves the electron at q to p, i.e.
+         * entry e with (er, es) = (q, p) */
+        for (int e = 0; e < ne; ++e) {
+            const int q = er[e] % ns, p = es[e] % ns;
+            double z = 0.0;
+            for (int mu = 0; mu < n_mu; ++mu) z += Lf[((size_t)mu * ns + p) * ns + q] * w[mu];
+            const double c = wn * z * ratio[e];
+            if (c == 0.0) continue;
+            const double* row = Op + (size_t)e * nv;
+            Hx[0] += c;
+            for (int64_t i = 0; i < nv; ++i) Hx[1 + i] += c * row[i];
+        }
+        /* overlap and the constant c0 */
+        double ox = x[0];
+        for (int64_t j = 0; j < nv; ++j) ox += On[j] * x[1 + j];
+        Hx[0] += wn * c0 * ox;
+        for (int64_t i = 0; i < nv; ++i) Hx[1 + i] += wn * c0 * ox * On[i];
+        if (Sx) {
+            Sx[0] += wn * ox;
+            for (int64_t i = 0; i < nv; ++i) Sx[1 + i] += wn * ox * On[i];
+        }
+    }
+    free(ratio); free(Op); free(er); free(es); free(On); free(w);
+    return rc;
+}
+
+/* Annihilation / creation on a determinant given as occupation bits (for the
+ * operator-matrix checks of the factored Hamiltonian): returns the sign and
+ * rewrites bits, 0 if the result vanishes. */
+int orc_apply_hop(int M, const uint8_t* bits, int p, int q, uint8_t* out)
+{
+    return hop_sign(M, bits, p, q, out);
+}

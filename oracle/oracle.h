@@ -60,5 +60,12 @@ double orc_sr_update(int64_t nv, const double* alpha, const double* y, double ta
 int64_t orc_sector_size(const orc_problem* P);
 int64_t orc_enumerate(const orc_problem* P, uint8_t* occ_out);
 void orc_exact_weights(const orc_problem* P, int64_t n_conf, const uint8_t* occ, double* w);
+/* Linear method (Sec. II.B): Hx and Sx over the basis {Psi, Psi^1 .. Psi^nv}
+ * by Eq. 10 with the factored Hamiltonian of Eq. 9 (spatial L^mu, R^mu,
+ * [n_mu][n_sites][n_sites], plus the constant c0); wgt NULL = 1/n_s. */
+int orc_lm_apply(const orc_problem* P, int64_t n_s, const uint8_t* occ, const double* wgt,
+                 int n_mu, const double* Lf, const double* Rf, double c0, const double* x,
+                 double* Hx, double* Sx);
+int orc_apply_hop(int M, const uint8_t* bits, int p, int q, uint8_t* out);
 
 #endif
