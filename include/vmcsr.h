@@ -248,6 +248,29 @@ int sr_update(vmc_handle h, const double* y, double tau, int store, double* x0, 
 int sr_local_moments(vmc_handle h, double* sumO, double* sumEO, double* scal, int store, void* stream);
 int sr_local_product(vmc_handle h, const double* v, double* out, int store, void* stream);
 
+/* Accelerated linear method (Sec. II.B).  The products with x = (x_0, x_1 ..
+ * x_nv) of the matrices of Eq. 8 over the basis {Psi, Psi^1 .. Psi^nv}
+ * (Psi^j = dPsi/dalpha_j; component 0 is Psi itself), estimated from the
+ * stored samples by Eq. 10:
+ *   Hx_i = (1/n_s) sum_n sum_pq Q_{n q p i} sum_mu L^mu_pq sum_rs R^mu_rs
+ *          sum_j Q_{n r s j} x_j + c0 Sx_i,   Q_{n r s j} = <n|a+_r a_s|Psi^j>/Psi_n,
+ *   Sx_i = (1/n_s) sum_n O_i(n) sum_j O_j(n) x_j   (O_0 = 1),
+ * with the Hamiltonian written in the factored form of Eq. 9,
+ * H = c0 + sum_mu Lhat_mu Rhat_mu over spin-summed one-body operators
+ * Lhat = sum_ij L_ij sum_s a+_is a_js.  The handle builds the factors from
+ * its Hamiltonian: a one-body term K enters as (K Nhat + Nhat K) / 2N (exact
+ * at fixed N; this split makes the sampled H symmetric); Hubbard U as
+ * (U/2) E_ii E_ii per site with c0 = -U N / 2; the ab initio two-body part
+ * as the pairs (L^mu, L^mu)/sqrt(2) with h - J/2, J_ps = sum_q (pq|qs).
+ * x, Hx, Sx: device [n_v + 1] FP64 (Sx may be NULL); Hx and Sx are
+ * overwritten.  store: VMC_STORE_FP64 (FP64 arithmetic) or VMC_STORE_FP32
+ * (FP32 arithmetic, FP64 accumulation into Hx / Sx) over the samples of the
+ * last vmc_sample / vmc_measure.  Errors: INVALID_ARG, STATE (no samples,
+ * no parameters, store not kept), UNSUPPORTED (the per-sample workspace of
+ * (2N + 3(M - N))(N + 1) + n_sites^2 + n_mu values exceeds shared memory),
+ * OOM, CUDA. */
+int lm_apply(vmc_handle h, const double* x, double* Hx, double* Sx, int store, void* stream);
+
 /* Measurement support (no counterpart in the paper).  vmc_profile(h, 1)
  * resets the counters and starts recording: every kernel the handle launches
  * is counted, and each launch of the O-store streaming kernel (the Eq. 7

@@ -938,8 +938,9 @@ int orc_lm_apply(const orc_problem* P, int64_t n_s, const uint8_t* occ, const do
     const int64_t nv = orc_n_params(P);
     memset(Hx, 0, sizeof(double) * (nv + 1));
     if (Sx) memset(Sx, 0, sizeof(double) * (nv + 1));
-    /* per sample: every (r, s) of one spin with <n| a+_r a_s |n'> != 0 */
-    const int nmax = M * M;
+    /* per sample: every (r, s) of one spin with <n| a+_r a_s |n'> != 0
+     * (r occupied, s = r or empty: at most ns per electron) */
+    const int nmax = N * ns;
     double* ratio = (double*)malloc(sizeof(double) * nmax);
     double* Op = (double*)malloc(sizeof(double) * (size_t)nmax * nv);   /* O(n') rows */
     int* er = (int*)malloc(sizeof(int) * nmax);

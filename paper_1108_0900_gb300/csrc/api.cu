@@ -113,6 +113,14 @@ struct vmc_ctx {
     double *d_x64 = nullptr, *d_r64 = nullptr, *d_p64 = nullptr, *d_q64 = nullptr, *d_t64 = nullptr;
     float *d_x32 = nullptr, *d_r32 = nullptr, *d_p32 = nullptr, *d_q32 = nullptr, *d_b32 = nullptr;
     double* h_pinned = nullptr;  // small host staging
+    // linear method: the Hamiltonian as c0 + sum_mu Lhat_mu Rhat_mu (Eq. 9),
+    // spatial factors [n_mu][ns][ns] built at creation, uploaded on first use
+    int lm_nmu = 0;
+    double lm_c0 = 0.0;
+    std::vector<double> lm_L, lm_R;
+    double *d_lmL64 = nullptr, *d_lmR64 = nullptr, *d_lmXt = nullptr, *d_lmxc = nullptr;
+    float *d_lmL32 = nullptr, *d_lmR32 = nullptr;
+    int *d_lmLptr = nullptr, *d_lmLidx = nullptr, *d_lmRptr = nullptr, *d_lmRidx = nullptr;
 
     // measurement support (vmc_profile)
     bool prof = false;
@@ -304,6 +312,51 @@ extern "C" int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, co
                 for (size_t rs = 0; rs < n2; ++rs) row[rs] += l * L[rs];
             }
         }
+    }
+    // Eq. 9 factors for the linear method.  A one-body K = sum k_ij E_ij
+    // (E_ij = sum_s a+_is a_js) commutes with the particle number, so in the
+    // N-electron sector K = (K Nhat + Nhat K) / 2N: the pairs (k/2N, I) and
+    // (I, k/2N).  Hubbard: k = -t per bond and direction; U n_up n_dn =
+    // (U/2)(E_ii E_ii - E_ii): (U/2 e_i e_i^T, e_i e_i^T) per site and the
+    // constant -U N / 2.  Ab initio: a+_p a+_r a_s a_q = E_pq E_rs - delta_qr
+    // E_ps, so the pairs (L^mu/sqrt2, L^mu/sqrt2) and k = h - J/2 with
+    // J_ps = sum_q (pq|qs).
+    {
+        const size_t n2 = (size_t)ns * ns;
+        std::vector<double> k(n2, 0.0);
+        auto push = [&](const std::vector<double>& L, const std::vector<double>& R) {
+            h->lm_L.insert(h->lm_L.end(), L.begin(), L.end());
+            h->lm_R.insert(h->lm_R.end(), R.begin(), R.end());
+            h->lm_nmu++;
+        };
+        if (ham->kind == VMC_HUBBARD) {
+            for (int i = 0; i < ns; ++i)
+                for (auto& pr : nb[i]) k[(size_t)i * ns + pr.first] -= pr.second;
+            for (int i = 0; i < ns; ++i) {
+                std::vector<double> L(n2, 0.0), R(n2, 0.0);
+                L[(size_t)i * ns + i] = 0.5 * ham->U;
+                R[(size_t)i * ns + i] = 1.0;
+                push(L, R);
+            }
+            h->lm_c0 = -0.5 * ham->U * N;
+        } else {
+            std::vector<double> J(n2, 0.0);
+            for (int mu = 0; mu < ham->n_chol; ++mu) {
+                const double* L = ham->chol + (size_t)mu * n2;
+                for (int p = 0; p < ns; ++p)
+                    for (int q = 0; q < ns; ++q)
+                        for (int r = 0; r < ns; ++r) J[(size_t)p * ns + r] += L[(size_t)p * ns + q] * L[(size_t)q * ns + r];
+                std::vector<double> Ls(L, L + n2);
+                for (auto& v : Ls) v *= std::sqrt(0.5);
+                push(Ls, Ls);
+            }
+            for (size_t t = 0; t < n2; ++t) k[t] = ham->h[t] - 0.5 * J[t];
+        }
+        std::vector<double> I(n2, 0.0), kh(n2);
+        for (int i = 0; i < ns; ++i) I[(size_t)i * ns + i] = 1.0;
+        for (size_t t = 0; t < n2; ++t) kh[t] = k[t] / (2.0 * N);
+        push(kh, I);
+        push(I, kh);
     }
     // pairing block order: up-up triangle, down-down triangle, up-down rectangle
     std::vector<uint16_t> pt;
@@ -1589,6 +1642,104 @@ extern "C" int sr_local_product(vmc_handle h, const double* v, double* out, int 
     h->n_launch++;
     VCK(cudaGetLastError());
     return VMC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// accelerated linear method (Sec. II.B)
+// ---------------------------------------------------------------------------
+static int lm_ensure(vmc_ctx* h) {
+    if (h->d_lmL64) return VMC_OK;
+    // the factors as sparse matrices: nonzeros of each L^mu (R^mu) in row order
+    const size_t n2 = (size_t)h->ns * h->ns;
+    std::vector<int> ptr[2], idx[2];
+    std::vector<double> val[2];
+    for (int side = 0; side < 2; ++side) {
+        const std::vector<double>& F = side == 0 ? h->lm_L : h->lm_R;
+        ptr[side].push_back(0);
+        for (int mu = 0; mu < h->lm_nmu; ++mu) {
+            for (size_t t = 0; t < n2; ++t) {
+                const double v = F[(size_t)mu * n2 + t];
+                if (v != 0.0) { idx[side].push_back((int)t); val[side].push_back(v); }
+            }
+            ptr[side].push_back((int)idx[side].size());
+        }
+    }
+    std::vector<float> L32(val[0].begin(), val[0].end()), R32(val[1].begin(), val[1].end());
+    VCK(h->alloc(&h->d_lmL64, val[0].size()));
+    VCK(h->alloc(&h->d_lmR64, val[1].size()));
+    VCK(h->alloc(&h->d_lmL32, val[0].size()));
+    VCK(h->alloc(&h->d_lmR32, val[1].size()));
+    VCK(h->alloc(&h->d_lmLptr, ptr[0].size()));
+    VCK(h->alloc(&h->d_lmRptr, ptr[1].size()));
+    VCK(h->alloc(&h->d_lmLidx, idx[0].size()));
+    VCK(h->alloc(&h->d_lmRidx, idx[1].size()));
+    VCK(h->alloc(&h->d_lmXt, (size_t)h->M * h->M));
+    VCK(h->alloc(&h->d_lmxc, (size_t)std::max<int64_t>(h->ncp, 1)));
+    auto up = [](void* d, const void* s, size_t b) { return b ? cudaMemcpy(d, s, b, cudaMemcpyHostToDevice) : cudaSuccess; };
+    VCK(up(h->d_lmL64, val[0].data(), val[0].size() * sizeof(double)));
+    VCK(up(h->d_lmR64, val[1].data(), val[1].size() * sizeof(double)));
+    VCK(up(h->d_lmL32, L32.data(), L32.size() * sizeof(float)));
+    VCK(up(h->d_lmR32, R32.data(), R32.size() * sizeof(float)));
+    VCK(up(h->d_lmLptr, ptr[0].data(), ptr[0].size() * sizeof(int)));
+    VCK(up(h->d_lmRptr, ptr[1].data(), ptr[1].size() * sizeof(int)));
+    VCK(up(h->d_lmLidx, idx[0].data(), idx[0].size() * sizeof(int)));
+    VCK(up(h->d_lmRidx, idx[1].data(), idx[1].size() * sizeof(int)));
+    return VMC_OK;
+}
+
+template <typename R>
+static int lm_launch(vmc_ctx* h, const double* x, double* Hx, double* Sx, const R* pf, const R* Lf,
+                     const R* Rf, cudaStream_t st) {
+    R* Xt = (R*)h->d_lmXt;
+    R* xc = (R*)h->d_lmxc;
+    const int64_t nprep = (int64_t)h->M * h->M + h->ncp;
+    k_lm_prep<R><<<(unsigned)std::min<int64_t>((nprep + 255) / 256, 4 * h->nsm), 256, 0, st>>>(h->pb, x, Xt, xc);
+    h->n_launch++;
+    LmArgs a{};
+    a.pb = h->pb;
+    a.n_s = h->n_s;
+    a.s_occ = h->d_socc; a.Nst = h->Nst;
+    a.s_cidx = h->d_cidx; a.ncst = h->ncst;
+    a.pf = pf; a.Pst = h->Pst;
+    a.x = x; a.Xt = Xt; a.xc = xc;
+    a.n_mu = h->lm_nmu; a.c0 = h->lm_c0;
+    a.Lptr = h->d_lmLptr; a.Lidx = h->d_lmLidx; a.Lval = Lf;
+    a.Rptr = h->d_lmRptr; a.Ridx = h->d_lmRidx; a.Rval = Rf;
+    a.inv_n = 1.0 / (double)h->n_s;
+    a.Hx = Hx; a.Sx = Sx;
+    a.XS = h->N + 1; a.GS = h->N + 1;
+    a.warp_bytes = (int)lm_warp_bytes(h->N, h->M, h->ns, h->lm_nmu, h->ncorr, (int)sizeof(R));
+    const int wpb = (int)std::min<size_t>(8, h->smem_optin / (size_t)a.warp_bytes);
+    if (wpb < 1) {
+        set_err("linear-method product: per-sample workspace exceeds shared memory");
+        return VMC_ERR_UNSUPPORTED;
+    }
+    const size_t smem = (size_t)wpb * a.warp_bytes;
+    VCK(cudaFuncSetAttribute(k_lm_apply<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    VCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lm_apply<R>, 32 * wpb, smem));
+    const int64_t need = (h->n_s + wpb - 1) / wpb;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)h->nsm * std::max(per_sm, 1)));
+    k_lm_apply<R><<<grid, 32 * wpb, smem, st>>>(a);
+    h->n_launch++;
+    VCK(cudaGetLastError());
+    return VMC_OK;
+}
+
+extern "C" int lm_apply(vmc_handle h, const double* x, double* Hx, double* Sx, int store, void* stream) {
+    if (!h || !x || !Hx) return VMC_ERR_INVALID_ARG;
+    if (store != VMC_STORE_FP64 && store != VMC_STORE_FP32) return VMC_ERR_INVALID_ARG;
+    if (h->n_s == 0 || !h->params_set) return VMC_ERR_STATE;
+    if (store == VMC_STORE_FP64 ? !h->d_pf64 : !h->d_pf32) return VMC_ERR_STATE;
+    int rc = lm_ensure(h);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t nb = sizeof(double) * (size_t)(h->nv + 1);
+    VCK(cudaMemsetAsync(Hx, 0, nb, st));
+    if (Sx) VCK(cudaMemsetAsync(Sx, 0, nb, st));
+    return store == VMC_STORE_FP64
+               ? lm_launch<double>(h, x, Hx, Sx, h->d_pf64, h->d_lmL64, h->d_lmR64, st)
+               : lm_launch<float>(h, x, Hx, Sx, h->d_pf32, h->d_lmL32, h->d_lmR32, st);
 }
 
 // ---------------------------------------------------------------------------

@@ -288,4 +288,38 @@ __global__ void __launch_bounds__(512) k_fill_C(DevProblem pb, int64_t n_s, cons
 __global__ void k_corr_item_count(const uint32_t* cbase, int64_t ncp, uint32_t* n_items);
 __global__ void k_corr_item_fill(const uint32_t* cbase, int64_t ncp, const uint32_t* item_base, uint2* items);
 
+// ---------------------------------------------------------------------------
+// accelerated linear method (Sec. II.B): Eq. 10 products with the basis
+// {Psi, Psi^1 .. Psi^nv} from a stored sample set (lm.cu)
+// ---------------------------------------------------------------------------
+struct LmArgs {
+    DevProblem pb;
+    int64_t n_s;
+    const uint8_t* s_occ;   // [n_s][Nst] ascending occupied spin orbitals
+    int Nst;
+    const cstate_t* s_cidx; // [n_s][ncst]
+    int ncst;
+    const void* pf;         // [n_s][Pst] pairing block in the kernel's precision R
+    int64_t Pst;
+    const double* x;        // [nv + 1]: x_0 then the parameter block
+    const void* Xt;         // [M][M] antisymmetric matrix of the pairing part of x (R)
+    const void* xc;         // [ncp] x_k / C_k for the correlator part of x (R)
+    int n_mu;               // factor pairs of Eq. 9, each a sparse ns x ns matrix:
+    const int* Lptr;        // [n_mu + 1] rows of the nonzeros of L^mu
+    const int* Lidx;        // i ns + j of each nonzero
+    const void* Lval;       // its value (R)
+    const int* Rptr;        // the same for R^mu
+    const int* Ridx;
+    const void* Rval;
+    double c0;
+    double inv_n;
+    double* Hx;             // [nv + 1], accumulated (zeroed by the caller)
+    double* Sx;             // [nv + 1] or null
+    int XS, GS;             // row strides of the per-warp matrices
+    int warp_bytes;
+};
+size_t lm_warp_bytes(int N, int M, int ns, int n_mu, int ncorr, int elem);
+template <typename R> __global__ void k_lm_prep(DevProblem pb, const double* x, R* Xt, R* xc);
+template <typename R> __global__ void k_lm_apply(LmArgs a);
+
 }  // namespace vmc

@@ -96,6 +96,7 @@ def lib(build_if_missing: bool = True):
         "sr_update": [vp, vp, dbl, i32, vp, vp],
         "sr_local_moments": [vp, vp, vp, vp, i32, vp],
         "sr_local_product": [vp, vp, vp, i32, vp],
+        "lm_apply": [vp, vp, vp, vp, i32, vp],
         "vmc_set_walkers": [vp, vp, vp],
         "vmc_get_walkers": [vp, vp, vp, vp],
         "vmc_sample": [vp, i32, u64, vp],
@@ -335,6 +336,19 @@ def sr_local_product(h: Handle, v, store=VMC_STORE_FP64, stream=None, out=None):
         out = torch.empty_like(v)
     _check(lib().sr_local_product(h.h, _dev_ptr(v), _dev_ptr(out), int(store), _stream(stream)), "sr_local_product")
     return out
+
+
+def lm_apply(h: Handle, x, store=VMC_STORE_FP64, want_S: bool = True, stream=None, Hx=None, Sx=None):
+    """Linear-method products (Hx, Sx) over the basis {Psi, Psi^1 .. Psi^nv}
+    by Eq. 10 (x: device FP64 [n_v + 1]); Sx is None unless want_S."""
+    import torch
+    if Hx is None:
+        Hx = torch.empty_like(x)
+    if want_S and Sx is None:
+        Sx = torch.empty_like(x)
+    _check(lib().lm_apply(h.h, _dev_ptr(x), _dev_ptr(Hx), _dev_ptr(Sx) if want_S else None, int(store),
+                          _stream(stream)), "lm_apply")
+    return Hx, (Sx if want_S else None)
 
 
 def sr_optimize(h: Handle, n_iter: int, tau: float, shift: float, tol: float, mode=VMC_CG_FP64, seed: int = 1,
