@@ -271,6 +271,37 @@ int sr_local_product(vmc_handle h, const double* v, double* out, int store, void
  * OOM, CUDA. */
 int lm_apply(vmc_handle h, const double* x, double* Hx, double* Sx, int store, void* stream);
 
+typedef struct {
+    int iterations;          /* Davidson steps (one lm_apply each)                  */
+    int restarts;            /* basis restarts                                      */
+    int converged;           /* 1 if the relative residual met tol                  */
+    double eigenvalue;       /* lowest eigenvalue theta of the shifted Eq. 8         */
+    double rel_residual;     /* |(H + aD) u - theta (S + eps D) u| / |theta (S + eps D) u| */
+    double Sx0;              /* (S x)_0 = x_0 + sum_j Obar_j x_j of the returned x   */
+} vmc_lm_info;
+
+/* Lowest eigenpair of Eq. 8 with diagonal shifts on the parameter block,
+ * (H + shift_H D) x = theta (S + shift_S D) x, D = diag(0, 1, .., 1), by the
+ * generalized Davidson method (Sec. II.B; Morgan's method: Rayleigh-Ritz on
+ * an orthonormal basis grown by the preconditioned residual
+ * -r / diag(S + shift_S D); at max_sub columns the basis restarts from the
+ * current and the previous Ritz vectors), every product through lm_apply,
+ * starting from x = e_0 (the current wavefunction).  Returns x (device
+ * [n_v + 1] FP64) scaled to x_0 = 1.  shift_S > 0 keeps S + shift_S D
+ * positive definite.  The projected problem (at most max_sub = 3..64
+ * columns) is solved on the host.  Errors: INVALID_ARG, STATE (as
+ * lm_apply), NOT_CONVERGED (max_iter reached; x and info hold the last Ritz
+ * pair), NONFINITE, OOM, CUDA. */
+int lm_solve(vmc_handle h, double shift_H, double shift_S, double tol, int max_iter, int max_sub, double* x,
+             vmc_lm_info* info, int store, void* stream);
+
+/* Linear-method parameter update (Sec. II.B): alpha_k += x_k / Sx0 with Sx0
+ * = (S x)_0 from lm_solve (the new state's component along Psi once the
+ * basis is orthogonalised to Psi).  x: device [n_v + 1].  The stored samples
+ * are then stale.  Errors: INVALID_ARG (Sx0 zero or not finite), STATE,
+ * SINGULAR (a correlator amplitude became 0), NONFINITE, CUDA. */
+int lm_update(vmc_handle h, const double* x, double Sx0, void* stream);
+
 /* Measurement support (no counterpart in the paper).  vmc_profile(h, 1)
  * resets the counters and starts recording: every kernel the handle launches
  * is counted, and each launch of the O-store streaming kernel (the Eq. 7

@@ -121,6 +121,11 @@ struct vmc_ctx {
     double *d_lmL64 = nullptr, *d_lmR64 = nullptr, *d_lmXt = nullptr, *d_lmxc = nullptr;
     float *d_lmL32 = nullptr, *d_lmR32 = nullptr;
     int *d_lmLptr = nullptr, *d_lmLidx = nullptr, *d_lmRptr = nullptr, *d_lmRidx = nullptr;
+    // Davidson workspace: basis V and its images (column-major, ld = lm_ld),
+    // work vectors, dot partials
+    int lm_cap = 0;
+    int64_t lm_ld = 0;
+    double *d_lmV = nullptr, *d_lmHV = nullptr, *d_lmSV = nullptr, *d_lmW = nullptr, *d_lmdot = nullptr;
 
     // measurement support (vmc_profile)
     bool prof = false;
@@ -1740,6 +1745,307 @@ extern "C" int lm_apply(vmc_handle h, const double* x, double* Hx, double* Sx, i
     return store == VMC_STORE_FP64
                ? lm_launch<double>(h, x, Hx, Sx, h->d_pf64, h->d_lmL64, h->d_lmR64, st)
                : lm_launch<float>(h, x, Hx, Sx, h->d_pf32, h->d_lmL32, h->d_lmR32, st);
+}
+
+namespace {
+
+// lowest eigenpair of h c = theta s c (m x m symmetric, s positive
+// definite): s = L L^T, A = L^{-1} h L^{-T}, cyclic Jacobi on A, c = L^{-T} y
+bool small_gen_eig(int m, const std::vector<double>& hm, const std::vector<double>& sm, double* theta,
+                   std::vector<double>& c) {
+    std::vector<double> L(sm);
+    for (int j = 0; j < m; ++j) {
+        double d = L[j * m + j];
+        for (int k = 0; k < j; ++k) d -= L[j * m + k] * L[j * m + k];
+        if (!(d > 0.0)) return false;
+        d = std::sqrt(d);
+        L[j * m + j] = d;
+        for (int i = j + 1; i < m; ++i) {
+            double v = L[i * m + j];
+            for (int k = 0; k < j; ++k) v -= L[i * m + k] * L[j * m + k];
+            L[i * m + j] = v / d;
+        }
+        for (int k = j + 1; k < m; ++k) L[j * m + k] = 0.0;
+    }
+    // B = L^{-1} h (forward substitution per column), A = B L^{-T}
+    std::vector<double> B(hm), A((size_t)m * m);
+    for (int col = 0; col < m; ++col)
+        for (int i = 0; i < m; ++i) {
+            double v = B[i * m + col];
+            for (int k = 0; k < i; ++k) v -= L[i * m + k] * B[k * m + col];
+            B[i * m + col] = v / L[i * m + i];
+        }
+    for (int row = 0; row < m; ++row)
+        for (int i = 0; i < m; ++i) {
+            double v = B[row * m + i];
+            for (int k = 0; k < i; ++k) v -= A[row * m + k] * L[i * m + k];
+            A[row * m + i] = v / L[i * m + i];
+        }
+    for (int i = 0; i < m; ++i)
+        for (int j = i + 1; j < m; ++j) A[i * m + j] = A[j * m + i] = 0.5 * (A[i * m + j] + A[j * m + i]);
+    std::vector<double> Q((size_t)m * m, 0.0);
+    for (int i = 0; i < m; ++i) Q[i * m + i] = 1.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < m; ++j) (i == j ? tot : off) += A[i * m + j] * A[i * m + j];
+        if (off <= 1e-30 * (tot + off) || off == 0.0) break;
+        for (int p = 0; p < m; ++p)
+            for (int q = p + 1; q < m; ++q) {
+                const double apq = A[p * m + q];
+                if (apq == 0.0) continue;
+                const double tau = (A[q * m + q] - A[p * m + p]) / (2.0 * apq);
+                const double t = (tau >= 0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));
+                const double cs = 1.0 / std::sqrt(1.0 + t * t), sn = t * cs;
+                for (int k = 0; k < m; ++k) {
+                    const double akp = A[k * m + p], akq = A[k * m + q];
+                    A[k * m + p] = cs * akp - sn * akq;
+                    A[k * m + q] = sn * akp + cs * akq;
+                }
+                for (int k = 0; k < m; ++k) {
+                    const double apk = A[p * m + k], aqk = A[q * m + k];
+                    A[p * m + k] = cs * apk - sn * aqk;
+                    A[q * m + k] = sn * apk + cs * aqk;
+                }
+                for (int k = 0; k < m; ++k) {
+                    const double qkp = Q[k * m + p], qkq = Q[k * m + q];
+                    Q[k * m + p] = cs * qkp - sn * qkq;
+                    Q[k * m + q] = sn * qkp + cs * qkq;
+                }
+            }
+    }
+    int lo = 0;
+    for (int i = 1; i < m; ++i)
+        if (A[i * m + i] < A[lo * m + lo]) lo = i;
+    *theta = A[lo * m + lo];
+    c.assign(m, 0.0);
+    for (int i = m - 1; i >= 0; --i) {   // L^T c = y
+        double v = Q[i * m + lo];
+        for (int k = i + 1; k < m; ++k) v -= L[k * m + i] * c[k];
+        c[i] = v / L[i * m + i];
+    }
+    return std::isfinite(*theta);
+}
+
+}  // namespace
+
+static int lm_dots(vmc_ctx* h, const double* V, int k, const double* u, double* out_host, cudaStream_t st) {
+    const int64_t n = h->nv + 1;
+    k_lm_dots<<<kNumPart, 256, 0, st>>>(V, h->lm_ld, k, u, n, h->d_lmdot);
+    k_lm_dots_reduce<<<1, 64, 0, st>>>(h->d_lmdot, kNumPart, k, h->d_lmdot + (size_t)kNumPart * h->lm_cap);
+    h->n_launch += 2;
+    VCK(cudaMemcpyAsync(out_host, h->d_lmdot + (size_t)kNumPart * h->lm_cap, sizeof(double) * k,
+                        cudaMemcpyDeviceToHost, st));
+    VCK(cudaStreamSynchronize(st));
+    return VMC_OK;
+}
+
+extern "C" int lm_solve(vmc_handle h, double shift_H, double shift_S, double tol, int max_iter, int max_sub,
+                        double* x, vmc_lm_info* info, int store, void* stream) {
+    if (!h || !x || !(shift_S > 0.0) || !std::isfinite(shift_H) || !(tol > 0.0) || max_iter < 1 || max_sub < 3 ||
+        max_sub > 64)
+        return VMC_ERR_INVALID_ARG;
+    if (store != VMC_STORE_FP64 && store != VMC_STORE_FP32) return VMC_ERR_INVALID_ARG;
+    if (h->n_s == 0 || !h->params_set) return VMC_ERR_STATE;
+    if (store == VMC_STORE_FP64 ? !h->d_pf64 : !h->d_pf32) return VMC_ERR_STATE;
+    int rc = lm_ensure(h);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = h->nv + 1;
+    if (h->lm_cap < max_sub) {
+        h->lm_cap = max_sub;
+        h->lm_ld = round_up(n, 32);
+        VCK(h->alloc(&h->d_lmV, (size_t)h->lm_ld * max_sub));
+        VCK(h->alloc(&h->d_lmHV, (size_t)h->lm_ld * max_sub));
+        VCK(h->alloc(&h->d_lmSV, (size_t)h->lm_ld * max_sub));
+        VCK(h->alloc(&h->d_lmW, (size_t)h->lm_ld * 12));
+        VCK(h->alloc(&h->d_lmdot, (size_t)(kNumPart + 1) * h->lm_cap + 64));
+    }
+    const int64_t ld = h->lm_ld;
+    double* W = h->d_lmW;
+    double *t = W, *Ht = W + ld, *St = W + 2 * ld, *u = W + 3 * ld, *Hu = W + 4 * ld, *Su = W + 5 * ld;
+    double *r = W + 6 * ld, *up = W + 7 * ld, *Hup = W + 8 * ld, *Sup = W + 9 * ld, *d = W + 10 * ld;
+    double* dc = h->d_lmdot + (size_t)(kNumPart + 1) * h->lm_cap;   // 64 coefficients on the device
+    double *V = h->d_lmV, *HV = h->d_lmHV, *SV = h->d_lmSV;
+    const unsigned vg = (unsigned)vgrid(h, 1);
+    auto launch_ok = [&]() { return cudaGetLastError(); };
+
+    // preconditioner: diag(S) + shift_S D
+    VCK(cudaMemsetAsync(d, 0, sizeof(double) * n, st));
+    {
+        LmArgs a{};
+        a.pb = h->pb; a.n_s = h->n_s; a.s_occ = h->d_socc; a.Nst = h->Nst; a.s_cidx = h->d_cidx; a.ncst = h->ncst;
+        a.pf = store == VMC_STORE_FP64 ? (const void*)h->d_pf64 : (const void*)h->d_pf32;
+        a.Pst = h->Pst; a.inv_n = 1.0 / (double)h->n_s;
+        const unsigned g = (unsigned)std::min<int64_t>((h->n_s + 7) / 8, 8 * h->nsm);
+        if (store == VMC_STORE_FP64) k_lm_diag<double><<<g, 256, 0, st>>>(a, d);
+        else k_lm_diag<float><<<g, 256, 0, st>>>(a, d);
+        h->n_launch++;
+        const double one = 1.0;
+        VCK(cudaMemcpyAsync(d, &one, sizeof(double), cudaMemcpyHostToDevice, st));
+        VCK(cudaStreamSynchronize(st));
+    }
+    // start from e_0 (the current wavefunction)
+    VCK(cudaMemsetAsync(t, 0, sizeof(double) * n, st));
+    {
+        const double one = 1.0;
+        VCK(cudaMemcpyAsync(t, &one, sizeof(double), cudaMemcpyHostToDevice, st));
+        VCK(cudaStreamSynchronize(st));
+    }
+    std::vector<double> hm((size_t)max_sub * max_sub), sm((size_t)max_sub * max_sub), cv, col(max_sub), row(max_sub);
+    int m = 0, iters = 0, restarts = 0;
+    bool have_prev = false, conv = false;
+    double theta = 0.0, relres = INFINITY;
+    auto orthonormalize = [&](double* vec) -> int {
+        for (int pass = 0; pass < 2 && m > 0; ++pass) {
+            int e = lm_dots(h, V, m, vec, col.data(), st);
+            if (e) return e;
+            for (int j = 0; j < m; ++j) col[j] = -col[j];
+            VCK(cudaMemcpyAsync(dc, col.data(), sizeof(double) * m, cudaMemcpyHostToDevice, st));
+            k_lm_combine<<<vg, 256, 0, st>>>(vec, V, ld, m, dc, n, 1.0); h->n_launch++;
+        }
+        double nrm2;
+        int e = lm_dots(h, vec, 1, vec, &nrm2, st);
+        if (e) return e;
+        if (!(nrm2 > 0.0) || !std::isfinite(nrm2)) return VMC_ERR_NONFINITE;
+        k_axpby<<<vg, 256, 0, st>>>(0.0, vec, 1.0 / std::sqrt(nrm2), vec, n); h->n_launch++;
+        return VMC_OK;
+    };
+    // append column m (vec, H vec, S vec) and extend the projected matrices
+    auto append = [&](const double* vec, const double* Hvec, const double* Svec) -> int {
+        VCK(cudaMemcpyAsync(V + (size_t)m * ld, vec, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        VCK(cudaMemcpyAsync(HV + (size_t)m * ld, Hvec, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        VCK(cudaMemcpyAsync(SV + (size_t)m * ld, Svec, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        ++m;
+        int e;
+        if ((e = lm_dots(h, V, m, HV + (size_t)(m - 1) * ld, col.data(), st))) return e;   // V^T H v_new
+        if ((e = lm_dots(h, HV, m, V + (size_t)(m - 1) * ld, row.data(), st))) return e;   // (H V)^T v_new
+        for (int i = 0; i < m; ++i) hm[(size_t)i * max_sub + (m - 1)] = hm[(size_t)(m - 1) * max_sub + i] = 0.5 * (col[i] + row[i]);
+        if ((e = lm_dots(h, V, m, SV + (size_t)(m - 1) * ld, col.data(), st))) return e;
+        if ((e = lm_dots(h, SV, m, V + (size_t)(m - 1) * ld, row.data(), st))) return e;
+        for (int i = 0; i < m; ++i) sm[(size_t)i * max_sub + (m - 1)] = sm[(size_t)(m - 1) * max_sub + i] = 0.5 * (col[i] + row[i]);
+        return VMC_OK;
+    };
+    auto combine3 = [&](const std::vector<double>& c, int k) -> int {
+        VCK(cudaMemcpyAsync(dc, c.data(), sizeof(double) * k, cudaMemcpyHostToDevice, st));
+        k_lm_combine<<<vg, 256, 0, st>>>(u, V, ld, k, dc, n, 0.0);
+        k_lm_combine<<<vg, 256, 0, st>>>(Hu, HV, ld, k, dc, n, 0.0);
+        k_lm_combine<<<vg, 256, 0, st>>>(Su, SV, ld, k, dc, n, 0.0);
+        h->n_launch += 3;
+        return VMC_OK;
+    };
+    for (iters = 1; iters <= max_iter; ++iters) {
+        if ((rc = orthonormalize(t))) return rc;
+        if ((rc = lm_apply(h, t, Ht, St, store, stream))) return rc;
+        // shifts on the parameter block (component 0 untouched)
+        k_axpby<<<vg, 256, 0, st>>>(shift_H, t + 1, 1.0, Ht + 1, n - 1);
+        k_axpby<<<vg, 256, 0, st>>>(shift_S, t + 1, 1.0, St + 1, n - 1);
+        h->n_launch += 2;
+        if ((rc = append(t, Ht, St))) return rc;
+        std::vector<double> hh((size_t)m * m), ss((size_t)m * m);
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < m; ++j) {
+                hh[(size_t)i * m + j] = hm[(size_t)i * max_sub + j];
+                ss[(size_t)i * m + j] = sm[(size_t)i * max_sub + j];
+            }
+        if (!small_gen_eig(m, hh, ss, &theta, cv)) {
+            set_err("lm_solve: projected overlap not positive definite");
+            return VMC_ERR_NONFINITE;
+        }
+        if ((rc = combine3(cv, m))) return rc;
+        k_axpby<<<vg, 256, 0, st>>>(1.0, Hu, 0.0, r, n);
+        k_axpby<<<vg, 256, 0, st>>>(-theta, Su, 1.0, r, n);
+        h->n_launch += 2;
+        double rr, ss2;
+        if ((rc = lm_dots(h, r, 1, r, &rr, st))) return rc;
+        if ((rc = lm_dots(h, Su, 1, Su, &ss2, st))) return rc;
+        relres = std::sqrt(rr) / (std::fabs(theta) * std::sqrt(ss2));
+        if (relres <= tol) { conv = true; break; }
+        k_lm_precond<<<vg, 256, 0, st>>>(t, r, d, shift_S, n); h->n_launch++;
+        if (m >= max_sub) {
+            // restart from the current and the previous Ritz vectors (their
+            // images are the same combinations of H V and S V: no products)
+            ++restarts;
+            double nu2;
+            if ((rc = lm_dots(h, u, 1, u, &nu2, st))) return rc;
+            const double iu = 1.0 / std::sqrt(nu2);
+            k_axpby<<<vg, 256, 0, st>>>(iu, u, 0.0, V, n);
+            k_axpby<<<vg, 256, 0, st>>>(iu, Hu, 0.0, HV, n);
+            k_axpby<<<vg, 256, 0, st>>>(iu, Su, 0.0, SV, n);
+            h->n_launch += 3;
+            m = 1;
+            if (have_prev) {
+                double b, g2;
+                if ((rc = lm_dots(h, V, 1, up, &b, st))) return rc;
+                // r, Ht, St are free here: w = u_prev - b v0 and its images
+                k_axpby<<<vg, 256, 0, st>>>(1.0, up, 0.0, r, n);
+                k_axpby<<<vg, 256, 0, st>>>(-b, V, 1.0, r, n);
+                k_axpby<<<vg, 256, 0, st>>>(1.0, Hup, 0.0, Ht, n);
+                k_axpby<<<vg, 256, 0, st>>>(-b, HV, 1.0, Ht, n);
+                k_axpby<<<vg, 256, 0, st>>>(1.0, Sup, 0.0, St, n);
+                k_axpby<<<vg, 256, 0, st>>>(-b, SV, 1.0, St, n);
+                h->n_launch += 6;
+                if ((rc = lm_dots(h, r, 1, r, &g2, st))) return rc;
+                if (g2 > 1e-24) {
+                    const double ig = 1.0 / std::sqrt(g2);
+                    k_axpby<<<vg, 256, 0, st>>>(ig, r, 0.0, V + ld, n);
+                    k_axpby<<<vg, 256, 0, st>>>(ig, Ht, 0.0, HV + ld, n);
+                    k_axpby<<<vg, 256, 0, st>>>(ig, St, 0.0, SV + ld, n);
+                    h->n_launch += 3;
+                    m = 2;
+                }
+            }
+            // the projected matrices of the kept columns
+            for (int j = 0; j < m; ++j) {
+                if ((rc = lm_dots(h, V, m, HV + (size_t)j * ld, col.data(), st))) return rc;
+                if ((rc = lm_dots(h, HV, m, V + (size_t)j * ld, row.data(), st))) return rc;
+                for (int i = 0; i < m; ++i) hm[(size_t)i * max_sub + j] = hm[(size_t)j * max_sub + i] = 0.5 * (col[i] + row[i]);
+                if ((rc = lm_dots(h, V, m, SV + (size_t)j * ld, col.data(), st))) return rc;
+                if ((rc = lm_dots(h, SV, m, V + (size_t)j * ld, row.data(), st))) return rc;
+                for (int i = 0; i < m; ++i) sm[(size_t)i * max_sub + j] = sm[(size_t)j * max_sub + i] = 0.5 * (col[i] + row[i]);
+            }
+        }
+        // keep the current Ritz triple as the previous one
+        VCK(cudaMemcpyAsync(up, u, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        VCK(cudaMemcpyAsync(Hup, Hu, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        VCK(cudaMemcpyAsync(Sup, Su, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        have_prev = true;
+        VCK(launch_ok());
+    }
+    // x = u / u_0 and (S x)_0
+    double u0, su0;
+    VCK(cudaMemcpyAsync(&u0, u, sizeof(double), cudaMemcpyDeviceToHost, st));
+    VCK(cudaMemcpyAsync(&su0, Su, sizeof(double), cudaMemcpyDeviceToHost, st));
+    VCK(cudaStreamSynchronize(st));
+    if (!(u0 != 0.0) || !std::isfinite(u0)) return VMC_ERR_NONFINITE;
+    k_axpby<<<vg, 256, 0, st>>>(1.0 / u0, u, 0.0, x, n); h->n_launch++;
+    VCK(cudaGetLastError());
+    VCK(cudaStreamSynchronize(st));
+    if (info) {
+        info->iterations = std::min(iters, max_iter);
+        info->restarts = restarts;
+        info->converged = conv ? 1 : 0;
+        info->eigenvalue = theta;
+        info->rel_residual = relres;
+        info->Sx0 = su0 / u0;
+    }
+    return conv ? VMC_OK : VMC_ERR_NOT_CONVERGED;
+}
+
+extern "C" int lm_update(vmc_handle h, const double* x, double Sx0, void* stream) {
+    if (!h || !x || !std::isfinite(Sx0) || Sx0 == 0.0) return VMC_ERR_INVALID_ARG;
+    if (!h->params_set) return VMC_ERR_STATE;
+    cudaStream_t st = (cudaStream_t)stream;
+    UpdateArgs a{};
+    a.C64 = h->d_C64; a.C32 = h->d_C32; a.invC64 = h->d_invC64; a.invC32 = h->d_invC32;
+    a.F64 = h->d_F64; a.F32 = h->d_F32; a.pq_of = h->d_pq_of;
+    a.ncp = h->ncp; a.npf = h->npf; a.M = h->M;
+    a.status = h->d_status;
+    k_lm_update<<<vgrid(h, 1), 256, 0, st>>>(a, x, 1.0 / Sx0); h->n_launch++;
+    VCK(cudaGetLastError());
+    h->obar_ok[0] = h->obar_ok[1] = h->obar_ok[2] = false;
+    h->sorted_ok = false;
+    return read_status(h, st);
 }
 
 // ---------------------------------------------------------------------------

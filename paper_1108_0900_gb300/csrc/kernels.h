@@ -321,5 +321,11 @@ struct LmArgs {
 size_t lm_warp_bytes(int N, int M, int ns, int n_mu, int ncorr, int elem);
 template <typename R> __global__ void k_lm_prep(DevProblem pb, const double* x, R* Xt, R* xc);
 template <typename R> __global__ void k_lm_apply(LmArgs a);
+template <typename R> __global__ void k_lm_diag(LmArgs a, double* d);
+__global__ void k_lm_dots(const double* V, int64_t ld, int k, const double* u, int64_t n, double* part);
+__global__ void k_lm_dots_reduce(const double* part, int nb, int k, double* out);
+__global__ void k_lm_combine(double* out, const double* V, int64_t ld, int k, const double* c, int64_t n, double alpha);
+__global__ void k_lm_precond(double* t, const double* r, const double* d, double eps, int64_t n);
+__global__ void k_lm_update(UpdateArgs a, const double* x, double scale);
 
 }  // namespace vmc

@@ -321,6 +321,106 @@ __global__ void __launch_bounds__(256) k_lm_apply(LmArgs a) {
     }
 }
 
+// diag of S over the basis (without its 0 entry, which is 1): the mean of
+// O_k(n)^2 over the samples, one warp per sample
+template <typename R>
+__global__ void k_lm_diag(LmArgs a, double* d) {
+    const DevProblem& pb = a.pb;
+    const int lane = threadIdx.x & 31;
+    const R* pf = (const R*)a.pf;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < a.n_s; s += nwarps) {
+        for (int c = lane; c < pb.ncorr; c += 32) {
+            const int64_t k = pb.corr_off[c] + a.s_cidx[s * a.ncst + c];
+            const double ic = 1.0 / __ldg(pb.C64 + k);
+            atomicAdd(d + 1 + k, ic * ic * a.inv_n);
+        }
+        for (int e = lane; e < pb.P; e += 32) {
+            const uint16_t t = pb.pairtab[e];
+            const int p = a.s_occ[s * a.Nst + (t & 255)], q = a.s_occ[s * a.Nst + (t >> 8)];
+            const double v = (double)pf[s * a.Pst + e];
+            atomicAdd(d + 1 + pb.ncp + pb.rowbase[p] + q, v * v * a.inv_n);
+        }
+    }
+}
+
+// part[b * k + j] = partial sums of V[:, j] . u over block b's slice
+__global__ void __launch_bounds__(256) k_lm_dots(const double* V, int64_t ld, int k, const double* u, int64_t n,
+                                                 double* part) {
+    __shared__ double red[8];
+    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t i0 = (int64_t)blockIdx.x * per, i1 = min(n, i0 + per);
+    for (int j = 0; j < k; ++j) {
+        double acc = 0.0;
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) acc += V[(int64_t)j * ld + i] * u[i];
+        acc = warp_sum(acc);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+            part[(int64_t)blockIdx.x * k + j] = t;
+        }
+        __syncthreads();
+    }
+}
+
+// out[j] = sum over blocks of part[b * k + j]
+__global__ void k_lm_dots_reduce(const double* part, int nb, int k, double* out) {
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        double t = 0.0;
+        for (int b = 0; b < nb; ++b) t += part[(int64_t)b * k + j];
+        out[j] = t;
+    }
+}
+
+// out = alpha out + sum_j c[j] V[:, j]
+__global__ void __launch_bounds__(256) k_lm_combine(double* out, const double* V, int64_t ld, int k, const double* c,
+                                                    int64_t n, double alpha) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double acc = alpha == 0.0 ? 0.0 : alpha * out[i];
+        for (int j = 0; j < k; ++j) acc += c[j] * V[(int64_t)j * ld + i];
+        out[i] = acc;
+    }
+}
+
+// t = -r / (d + eps D), D = diag(0, 1, .., 1)
+__global__ void __launch_bounds__(256) k_lm_precond(double* t, const double* r, const double* d, double eps, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        t[i] = -r[i] / (d[i] + (i > 0 ? eps : 0.0));
+}
+
+// alpha += x_{1:} / Sx0 (Sec. II.B: the update relative to the component of
+// the new state along Psi in the basis orthogonalised to Psi)
+__global__ void __launch_bounds__(256) k_lm_update(UpdateArgs a, const double* x, double scale) {
+    const int64_t nv = a.ncp + a.npf;
+    int bad = 0;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nv; k += (int64_t)gridDim.x * blockDim.x) {
+        const double d = scale * x[1 + k];
+        if (k < a.ncp) {
+            const double c = a.C64[k] + d;
+            if (c == 0.0) bad |= ST_SINGULAR;
+            if (!isfinite(c)) bad |= ST_NONFINITE;
+            a.C64[k] = c;
+            a.C32[k] = (float)c;
+            a.invC64[k] = 1.0 / c;
+            a.invC32[k] = (float)(1.0 / c);
+        } else {
+            const uint32_t pq = a.pq_of[k - a.ncp];
+            const int p = (int)(pq & 0xFFFFu), q = (int)(pq >> 16);
+            const double f = a.F64[(int64_t)p * a.M + q] + d;
+            if (!isfinite(f)) bad |= ST_NONFINITE;
+            a.F64[(int64_t)p * a.M + q] = f;
+            a.F64[(int64_t)q * a.M + p] = -f;
+            a.F32[(int64_t)p * a.M + q] = (float)f;
+            a.F32[(int64_t)q * a.M + p] = -(float)f;
+        }
+    }
+    if (bad) atomicOr(a.status, bad);
+}
+
+template __global__ void k_lm_diag<double>(LmArgs, double*);
+template __global__ void k_lm_diag<float>(LmArgs, double*);
 template __global__ void k_lm_prep<double>(DevProblem, const double*, double*, double*);
 template __global__ void k_lm_prep<float>(DevProblem, const double*, float*, float*);
 template __global__ void k_lm_apply<double>(LmArgs);

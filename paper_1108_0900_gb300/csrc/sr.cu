@@ -621,7 +621,7 @@ __global__ void k_sub(const double* a, const double* b, double* y, int64_t n, do
 // y = a x + b y (FP64)
 __global__ void k_axpby(double a, const double* x, double b, double* y, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        y[i] = a * x[i] + b * y[i];
+        y[i] = b == 0.0 ? a * x[i] : a * x[i] + b * y[i];   // b = 0: y may hold anything
 }
 
 // x64 += scale * d

@@ -58,6 +58,14 @@ class vmc_options(ct.Structure):
                 ("keep_fp64_store", ct.c_int), ("keep_lowp_store", ct.c_int), ("refresh_every", ct.c_int)]
 
 
+class vmc_lm_info(ct.Structure):
+    _fields_ = [("iterations", ct.c_int), ("restarts", ct.c_int), ("converged", ct.c_int),
+                ("eigenvalue", ct.c_double), ("rel_residual", ct.c_double), ("Sx0", ct.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class vmc_cg_info(ct.Structure):
     _fields_ = [("iterations", ct.c_int), ("refinements", ct.c_int), ("residual_products", ct.c_int),
                 ("converged", ct.c_int), ("true_rel_residual", ct.c_double)]
@@ -97,6 +105,8 @@ def lib(build_if_missing: bool = True):
         "sr_local_moments": [vp, vp, vp, vp, i32, vp],
         "sr_local_product": [vp, vp, vp, i32, vp],
         "lm_apply": [vp, vp, vp, vp, i32, vp],
+        "lm_solve": [vp, dbl, dbl, dbl, i32, i32, vp, vp, i32, vp],
+        "lm_update": [vp, vp, dbl, vp],
         "vmc_set_walkers": [vp, vp, vp],
         "vmc_get_walkers": [vp, vp, vp, vp],
         "vmc_sample": [vp, i32, u64, vp],
@@ -349,6 +359,40 @@ def lm_apply(h: Handle, x, store=VMC_STORE_FP64, want_S: bool = True, stream=Non
     _check(lib().lm_apply(h.h, _dev_ptr(x), _dev_ptr(Hx), _dev_ptr(Sx) if want_S else None, int(store),
                           _stream(stream)), "lm_apply")
     return Hx, (Sx if want_S else None)
+
+
+def lm_solve(h: Handle, shift_H: float, shift_S: float, tol: float, max_iter: int = 500, max_sub: int = 24,
+             store=VMC_STORE_FP64, stream=None, allow_not_converged=False):
+    """Lowest eigenpair of the shifted Eq. 8 by generalized Davidson; returns
+    (x with x_0 = 1, info dict with eigenvalue, residual and Sx0)."""
+    import torch
+    x = torch.empty(h.n_params + 1, dtype=torch.float64, device="cuda")
+    info = vmc_lm_info()
+    rc = lib().lm_solve(h.h, float(shift_H), float(shift_S), float(tol), int(max_iter), int(max_sub), _dev_ptr(x),
+                        ct.byref(info), int(store), _stream(stream))
+    if not (allow_not_converged and rc == -5):
+        _check(rc, "lm_solve")
+    return x, info.as_dict()
+
+
+def lm_update(h: Handle, x, Sx0: float, stream=None):
+    """alpha += x_{1:} / Sx0 (the linear method's step, Sec. II.B)."""
+    _check(lib().lm_update(h.h, _dev_ptr(x), float(Sx0), _stream(stream)), "lm_update")
+
+
+def lm_optimize(h: Handle, n_iter: int, shift_H: float, shift_S: float, tol: float, store=VMC_STORE_FP64,
+                seed: int = 1, max_iter: int = 500, max_sub: int = 24):
+    """The linear-method loop of Sec. II.B: sample, lowest eigenpair of the
+    shifted Eq. 8, update; returns one record per iteration (energy
+    statistics before the update and the solver info)."""
+    hist = []
+    for it in range(n_iter):
+        vmc_sample(h, 0, seed + it)
+        _, es = sr_gradient(h, store)
+        x, info = lm_solve(h, shift_H, shift_S, tol, max_iter, max_sub, store, allow_not_converged=True)
+        lm_update(h, x, info["Sx0"])
+        hist.append({"energy": es, "lm": info})
+    return hist
 
 
 def sr_optimize(h: Handle, n_iter: int, tau: float, shift: float, tol: float, mode=VMC_CG_FP64, seed: int = 1,

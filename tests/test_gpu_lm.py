@@ -133,3 +133,66 @@ def test_full_size_null_directions(name, prec, tol, nw):
         assert rel(Sx.cpu().numpy(), S0) <= tol
         assert rel(Hx.cpu().numpy(), H0) <= tol
     h.close()
+
+
+def _dense(P, smp, fac, nv1):
+    H = np.zeros((nv1, nv1))
+    S = np.zeros((nv1, nv1))
+    for j in range(nv1):
+        e = np.zeros(nv1)
+        e[j] = 1.0
+        H[:, j], S[:, j] = P.lm_apply(smp, fac, e)
+    return H, S
+
+
+@pytest.mark.parametrize("name,nw,spw", [("hubbard3x2_pair", 256, 2), ("abinitio6", 256, 2)])
+def test_lm_solve_matches_dense_eigensolver(name, nw, spw):
+    """lm_solve (Davidson on the GPU products) against the lowest eigenpair of
+    the oracle's dense matrices (one oracle product per column)."""
+    import scipy.linalg
+    if name == "hubbard3x2_pair":
+        wl = inputs.hubbard("t", 3, 2, 2, 2, "pair", seed=9, n_walkers=nw, samples_per_walker=spw)
+    else:
+        wl = inputs.abinitio("t", 6, 3, 3, n_chol=6, seed=35, n_walkers=nw, samples_per_walker=spw)
+    P, smp, h = _setup(wl)
+    fac = oracle.lm_factors(wl)
+    nv1 = wl.n_params + 1
+    H, S = _dense(P, smp, fac, nv1)
+    a_shift, eps = 1.0, 1e-2
+    D = np.eye(nv1)
+    D[0, 0] = 0.0
+    lam, vec = scipy.linalg.eigh(0.5 * (H + H.T) + a_shift * D, 0.5 * (S + S.T) + eps * D)
+    ref = vec[:, 0] / vec[0, 0]
+    x, info = V.lm_solve(h, a_shift, eps, 1e-10, max_iter=2000, max_sub=40, store=V.VMC_STORE_FP64)
+    assert info["converged"] == 1
+    assert info["eigenvalue"] == pytest.approx(lam[0], rel=1e-8)
+    xs = x.cpu().numpy()
+    assert rel(xs, ref) <= 1e-5
+    assert info["Sx0"] == pytest.approx((S @ xs)[0], rel=1e-9)
+    # the update: alpha += x_{1:} / Sx0 on the device
+    alpha0 = np.concatenate([wl.C, wl.f])
+    V.lm_update(h, x, info["Sx0"])
+    C, f = V.vmc_get_params(h)
+    assert rel(np.concatenate([C, f]), oracle.lm_update(alpha0, xs, info["Sx0"])) <= 1e-14
+    # FP32 store: same eigenvalue to FP32 accuracy
+    V.vmc_set_params(h, wl.C, wl.f)
+    V.vmc_measure(h, smp)
+    x32, info32 = V.lm_solve(h, a_shift, eps, 1e-6, max_iter=2000, max_sub=40, store=V.VMC_STORE_FP32)
+    assert info32["eigenvalue"] == pytest.approx(lam[0], rel=1e-4)
+    h.close()
+
+
+def test_lm_optimize_lowers_the_energy():
+    """Three linear-method steps from random parameters on the 4x4 lattice
+    lower the sampled energy well beyond its statistical error."""
+    wl = inputs.workload("hubbard4x4_pair", n_walkers=1024, samples_per_walker=4)
+    h = V.vmc_create(wl, walker_precision=V.VMC_FP64, keep_fp64_store=True, keep_lowp_store=False)
+    V.vmc_set_params(h, wl.C, wl.f)
+    V.vmc_set_walkers(h, wl.init_occ)
+    V.vmc_sample(h, 20, 5)
+    hist = V.lm_optimize(h, 3, 2.0, 1e-2, 1e-6, store=V.VMC_STORE_FP64, seed=11, max_iter=600, max_sub=32)
+    V.vmc_sample(h, 0, 99)
+    _, es = V.sr_gradient(h, V.VMC_STORE_FP64)
+    e0, err0 = hist[0]["energy"][0], hist[0]["energy"][2]    # mean, variance, standard error
+    assert es[0] < e0 - 5 * max(err0, es[2])
+    h.close()
