@@ -1864,7 +1864,7 @@ extern "C" int lm_solve(vmc_handle h, double shift_H, double shift_S, double tol
     const int64_t ld = h->lm_ld;
     double* W = h->d_lmW;
     double *t = W, *Ht = W + ld, *St = W + 2 * ld, *u = W + 3 * ld, *Hu = W + 4 * ld, *Su = W + 5 * ld;
-    double *r = W + 6 * ld, *up = W + 7 * ld, *Hup = W + 8 * ld, *Sup = W + 9 * ld, *d = W + 10 * ld;
+    double *r = W + 6 * ld, *up = W + 7 * ld, *d = W + 8 * ld;
     double* dc = h->d_lmdot + (size_t)(kNumPart + 1) * h->lm_cap;   // 64 coefficients on the device
     double *V = h->d_lmV, *HV = h->d_lmHV, *SV = h->d_lmSV;
     const unsigned vg = (unsigned)vgrid(h, 1);
@@ -1963,37 +1963,34 @@ extern "C" int lm_solve(vmc_handle h, double shift_H, double shift_S, double tol
         if (relres <= tol) { conv = true; break; }
         k_lm_precond<<<vg, 256, 0, st>>>(t, r, d, shift_S, n); h->n_launch++;
         if (m >= max_sub) {
-            // restart from the current and the previous Ritz vectors (their
-            // images are the same combinations of H V and S V: no products)
+            // restart from the current and the previous Ritz vectors; their
+            // images are recomputed (near convergence the two are almost
+            // parallel, and combining the old images would amplify rounding)
             ++restarts;
             double nu2;
             if ((rc = lm_dots(h, u, 1, u, &nu2, st))) return rc;
-            const double iu = 1.0 / std::sqrt(nu2);
-            k_axpby<<<vg, 256, 0, st>>>(iu, u, 0.0, V, n);
-            k_axpby<<<vg, 256, 0, st>>>(iu, Hu, 0.0, HV, n);
-            k_axpby<<<vg, 256, 0, st>>>(iu, Su, 0.0, SV, n);
-            h->n_launch += 3;
+            k_axpby<<<vg, 256, 0, st>>>(1.0 / std::sqrt(nu2), u, 0.0, V, n);
+            h->n_launch++;
             m = 1;
             if (have_prev) {
                 double b, g2;
                 if ((rc = lm_dots(h, V, 1, up, &b, st))) return rc;
-                // r, Ht, St are free here: w = u_prev - b v0 and its images
-                k_axpby<<<vg, 256, 0, st>>>(1.0, up, 0.0, r, n);
-                k_axpby<<<vg, 256, 0, st>>>(-b, V, 1.0, r, n);
-                k_axpby<<<vg, 256, 0, st>>>(1.0, Hup, 0.0, Ht, n);
-                k_axpby<<<vg, 256, 0, st>>>(-b, HV, 1.0, Ht, n);
-                k_axpby<<<vg, 256, 0, st>>>(1.0, Sup, 0.0, St, n);
-                k_axpby<<<vg, 256, 0, st>>>(-b, SV, 1.0, St, n);
-                h->n_launch += 6;
-                if ((rc = lm_dots(h, r, 1, r, &g2, st))) return rc;
-                if (g2 > 1e-24) {
-                    const double ig = 1.0 / std::sqrt(g2);
-                    k_axpby<<<vg, 256, 0, st>>>(ig, r, 0.0, V + ld, n);
-                    k_axpby<<<vg, 256, 0, st>>>(ig, Ht, 0.0, HV + ld, n);
-                    k_axpby<<<vg, 256, 0, st>>>(ig, St, 0.0, SV + ld, n);
-                    h->n_launch += 3;
+                k_axpby<<<vg, 256, 0, st>>>(1.0, up, 0.0, V + ld, n);
+                k_axpby<<<vg, 256, 0, st>>>(-b, V, 1.0, V + ld, n);
+                h->n_launch += 2;
+                if ((rc = lm_dots(h, V + ld, 1, V + ld, &g2, st))) return rc;
+                if (g2 > 0.0 && std::isfinite(g2)) {
+                    k_axpby<<<vg, 256, 0, st>>>(0.0, V + ld, 1.0 / std::sqrt(g2), V + ld, n);
+                    h->n_launch++;
                     m = 2;
                 }
+            }
+            for (int j = 0; j < m; ++j) {
+                if ((rc = lm_apply(h, V + (size_t)j * ld, HV + (size_t)j * ld, SV + (size_t)j * ld, store, stream)))
+                    return rc;
+                k_axpby<<<vg, 256, 0, st>>>(shift_H, V + (size_t)j * ld + 1, 1.0, HV + (size_t)j * ld + 1, n - 1);
+                k_axpby<<<vg, 256, 0, st>>>(shift_S, V + (size_t)j * ld + 1, 1.0, SV + (size_t)j * ld + 1, n - 1);
+                h->n_launch += 2;
             }
             // the projected matrices of the kept columns
             for (int j = 0; j < m; ++j) {
@@ -2005,10 +2002,8 @@ extern "C" int lm_solve(vmc_handle h, double shift_H, double shift_S, double tol
                 for (int i = 0; i < m; ++i) sm[(size_t)i * max_sub + j] = sm[(size_t)j * max_sub + i] = 0.5 * (col[i] + row[i]);
             }
         }
-        // keep the current Ritz triple as the previous one
+        // keep the current Ritz vector as the previous one
         VCK(cudaMemcpyAsync(up, u, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-        VCK(cudaMemcpyAsync(Hup, Hu, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-        VCK(cudaMemcpyAsync(Sup, Su, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
         have_prev = true;
         VCK(launch_ok());
     }
