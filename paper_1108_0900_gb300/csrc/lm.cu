@@ -76,10 +76,32 @@ __device__ R corr_ratio_move(const DevProblem& pb, const uint32_t* cidx, int p, 
     return prod;
 }
 
+// Sums into the products go to a per-CTA shared-memory image of the
+// parameter block when it fits (many samples of one CTA hit the same few
+// thousand amplitudes; global atomics on them serialise), else to global
+// memory.  Image layout: correlator amplitudes [0, ncp) if corr_local, then
+// the pairing block if pf_local.
+template <typename R>
+struct LmAcc {
+    double* g;          // global vector, parameter k at g[1 + k]
+    R* img;             // shared image or null
+    int corr_local, pf_local;
+    int64_t ncp;
+    __device__ __forceinline__ void corr(int64_t k, double v) const {
+        if (corr_local) atomicAdd(img + k, (R)v);
+        else atomicAdd(g + 1 + k, v);
+    }
+    __device__ __forceinline__ void pf(int64_t idx, double v) const {
+        if (pf_local) atomicAdd(img + (corr_local ? ncp : 0) + idx, (R)v);
+        else atomicAdd(g + 1 + ncp + idx, v);
+    }
+};
+
 // Adjoint of the correlator ratio: coef (1/C at the new state) and
 // -coef (1/C at the old state) for every correlator the move changes.
+template <typename R>
 __device__ void corr_ratio_adjoint(const DevProblem& pb, const uint32_t* cidx, int p, int q, double coef,
-                                   double* out) {
+                                   const LmAcc<R>& out) {
     const int ns = pb.ns;
     const int sf = p >= ns ? 2 : 1;
     const int sp = p >= ns ? p - ns : p, sq = q >= ns ? q - ns : q;
@@ -89,8 +111,8 @@ __device__ void corr_ratio_adjoint(const DevProblem& pb, const uint32_t* cidx, i
         const int newi = corr_entry(pb, cidx, sp, sq, sf, e, &c);
         if (c < 0) continue;
         const int64_t k1 = pb.corr_off[c] + newi, k0 = pb.corr_off[c] + cidx[c];
-        atomicAdd(out + k1, coef / __ldg(pb.C64 + k1));
-        atomicAdd(out + k0, -coef / __ldg(pb.C64 + k0));
+        out.corr(k1, coef / __ldg(pb.C64 + k1));
+        out.corr(k0, -coef / __ldg(pb.C64 + k0));
     }
 }
 
@@ -104,6 +126,49 @@ __device__ __forceinline__ void decode_move(int t, int nu, int eu, int ed, int* 
         const int u = t - nup;
         *a = nu + u / ed;
         *ie = eu + u % ed;
+    }
+}
+
+// C (+)= alpha A B over one warp with T x T register tiles per lane:
+// A(i, k) = A[i sai + k sak], B(k, j) = B[k sbk + j sbj], C[i sc + j]; i < m,
+// j < n, k < K.  Ragged tiles clamp their loads and skip their stores.
+template <typename R, int T>
+__device__ void warp_gemm(int m, int n, int K, const R* A, int sai, int sak, const R* B, int sbk, int sbj, R* C,
+                          int sc, R alpha, bool accumulate) {
+    const int lane = threadIdx.x & 31;
+    const int tn = (n + T - 1) / T, nt = ((m + T - 1) / T) * tn;
+    for (int tile = lane; tile < nt; tile += 32) {
+        const int i0 = (tile / tn) * T, j0 = (tile % tn) * T;
+        const R* Ar[T];
+        const R* Bc[T];
+#pragma unroll
+        for (int r = 0; r < T; ++r) Ar[r] = A + min(i0 + r, m - 1) * sai;
+#pragma unroll
+        for (int c = 0; c < T; ++c) Bc[c] = B + min(j0 + c, n - 1) * sbj;
+        R acc[T][T];
+#pragma unroll
+        for (int r = 0; r < T; ++r)
+#pragma unroll
+            for (int c = 0; c < T; ++c) acc[r][c] = R(0);
+        for (int k = 0; k < K; ++k) {
+            R av[T], bv[T];
+#pragma unroll
+            for (int r = 0; r < T; ++r) av[r] = Ar[r][k * sak];
+#pragma unroll
+            for (int c = 0; c < T; ++c) bv[c] = Bc[c][k * sbk];
+#pragma unroll
+            for (int r = 0; r < T; ++r)
+#pragma unroll
+                for (int c = 0; c < T; ++c) acc[r][c] += av[r] * bv[c];
+        }
+#pragma unroll
+        for (int r = 0; r < T; ++r)
+#pragma unroll
+            for (int c = 0; c < T; ++c)
+                if (i0 + r < m && j0 + c < n) {
+                    R* q = C + (i0 + r) * sc + j0 + c;
+                    *q = accumulate ? *q + alpha * acc[r][c] : alpha * acc[r][c];
+                }
     }
 }
 
@@ -164,6 +229,13 @@ __global__ void __launch_bounds__(256) k_lm_apply(LmArgs a) {
     const int nex = nu * eu + nd * ed;
     const uint64_t smask = ns == 64 ? ~0ull : ((1ull << ns) - 1ull);
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t nimg = (a.corr_local ? pb.ncp : 0) + (a.pf_local ? pb.npf : 0);
+    R* imgH = (R*)(smem_raw + (size_t)(blockDim.x >> 5) * a.warp_bytes);
+    R* imgS = imgH + nimg;
+    for (int64_t i = threadIdx.x; i < nimg * (a.Sx ? 2 : 1); i += blockDim.x) imgH[i] = R(0);
+    __syncthreads();
+    const LmAcc<R> accH{a.Hx, nimg ? imgH : nullptr, a.corr_local, a.pf_local, pb.ncp};
+    const LmAcc<R> accS{a.Sx, nimg ? imgS : nullptr, a.corr_local, a.pf_local, pb.ncp};
 
     for (int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid; s < a.n_s; s += nwarps) {
         // ---- configuration, A^{-1} and O(n) . x ---------------------------
@@ -198,31 +270,25 @@ __global__ void __launch_bounds__(256) k_lm_apply(LmArgs a) {
 
         // ---- G = F[emp, occ] A^{-1}; Xo = X[occ, occ] ----------------------
         for (int t = lane; t < E * N; t += 32) {
-            const int ie = t / N, ia = t % N;
-            const int v = emp[ie];
-            R acc = R(0);
-            for (int k = 0; k < N; ++k) acc += load_F<R>(pb, v, occ[k]) * X[k * XS + ia];
-            G[ie * GS + ia] = acc;
+            const int ie = t / N, k = t % N;
+            Pm[ie * GS + k] = load_F<R>(pb, emp[ie], occ[k]);
         }
         for (int t = lane; t < N * N; t += 32) {
             const int l = t / N, k = t % N;
             Xo[l * XS + k] = Xt[occ[l] * M + occ[k]];
         }
         __syncwarp();
+        warp_gemm<R, 2>(E, N, N, Pm, GS, 1, X, XS, 1, G, GS, R(1), false);
+        __syncwarp();
         // ---- P = X[emp, occ] - G Xo; D = P A^{-1} (dG along x) -------------
         for (int t = lane; t < E * N; t += 32) {
             const int ie = t / N, k = t % N;
-            R acc = Xt[emp[ie] * M + occ[k]];
-            for (int l = 0; l < N; ++l) acc -= G[ie * GS + l] * Xo[l * XS + k];
-            Pm[ie * GS + k] = acc;
+            Pm[ie * GS + k] = Xt[emp[ie] * M + occ[k]];
         }
         __syncwarp();
-        for (int t = lane; t < E * N; t += 32) {
-            const int ie = t / N, ia = t % N;
-            R acc = R(0);
-            for (int k = 0; k < N; ++k) acc += Pm[ie * GS + k] * X[k * XS + ia];
-            D[ie * GS + ia] = acc;
-        }
+        warp_gemm<R, 2>(E, N, N, G, GS, 1, Xo, XS, 1, Pm, GS, R(-1), true);
+        __syncwarp();
+        warp_gemm<R, 2>(E, N, N, Pm, GS, 1, X, XS, 1, D, GS, R(1), false);
         for (int t = lane; t < nn; t += 32) Y[t] = R(0);
         __syncwarp();
         for (int t = lane; t < E * N; t += 32) Pm[(t / N) * GS + t % N] = R(0);
@@ -269,24 +335,14 @@ __global__ void __launch_bounds__(256) k_lm_apply(LmArgs a) {
             const R g = G[ie * GS + ia];
             W += z * rc * g;
             Pm[ie * GS + ia] = z * rc;
-            corr_ratio_adjoint(pb, cidx, p, v, (double)(z * rc * g) * sc, a.Hx + 1);
+            corr_ratio_adjoint<R>(pb, cidx, p, v, (double)(z * rc * g) * sc, accH);
         }
         W = warp_sum(W);
         __syncwarp();
         // B = Cbar A^{-T}; G^T B
-        for (int t = lane; t < E * N; t += 32) {
-            const int ie = t / N, k = t % N;
-            R acc = R(0);
-            for (int ia = 0; ia < N; ++ia) acc += Pm[ie * GS + ia] * X[k * XS + ia];
-            D[ie * GS + k] = acc;
-        }
+        warp_gemm<R, 2>(E, N, N, Pm, GS, 1, X, 1, XS, D, GS, R(1), false);
         __syncwarp();
-        for (int t = lane; t < N * N; t += 32) {
-            const int l = t / N, k = t % N;
-            R acc = R(0);
-            for (int ie = 0; ie < E; ++ie) acc += G[ie * GS + l] * D[ie * GS + k];
-            Xo[l * XS + k] = acc;
-        }
+        warp_gemm<R, 2>(N, N, E, G, 1, GS, D, GS, 1, Xo, XS, R(1), false);
         __syncwarp();
 
         // ---- scatter ------------------------------------------------------
@@ -297,27 +353,36 @@ __global__ void __launch_bounds__(256) k_lm_apply(LmArgs a) {
         for (int c = lane; c < ncorr; c += 32) {
             const int64_t k = pb.corr_off[c] + cidx[c];
             const double ic = 1.0 / __ldg(pb.C64 + k);
-            atomicAdd(a.Hx + 1 + k, (double)W * ic * sc);
-            if (a.Sx) atomicAdd(a.Sx + 1 + k, (double)xt * ic * sc);
+            accH.corr(k, (double)W * ic * sc);
+            if (a.Sx) accS.corr(k, (double)xt * ic * sc);
         }
-        double* Hf = a.Hx + 1 + pb.ncp;
         for (int e = lane; e < pb.P; e += 32) {
             const uint16_t t = pb.pairtab[e];
             const int aa = t & 255, bb = t >> 8;
             const int64_t idx = pb.rowbase[occ[aa]] + occ[bb];
             const R xba = X[bb * XS + aa];
-            atomicAdd(Hf + idx, (double)(W * xba - Xo[aa * XS + bb] + Xo[bb * XS + aa]) * sc);
-            if (a.Sx) atomicAdd(a.Sx + 1 + pb.ncp + idx, (double)(xt * xba) * sc);
+            accH.pf(idx, (double)(W * xba - Xo[aa * XS + bb] + Xo[bb * XS + aa]) * sc);
+            if (a.Sx) accS.pf(idx, (double)(xt * xba) * sc);
         }
         for (int t = lane; t < E * N; t += 32) {
             const int ie = t / N, k = t % N;
             const R b = D[ie * GS + k];
             if (b == R(0)) continue;
             const int v = emp[ie], o = occ[k];
-            if (v < o) atomicAdd(Hf + pb.rowbase[v] + o, (double)b * sc);
-            else atomicAdd(Hf + pb.rowbase[o] + v, -(double)b * sc);
+            if (v < o) accH.pf(pb.rowbase[v] + o, (double)b * sc);
+            else accH.pf(pb.rowbase[o] + v, -(double)b * sc);
         }
         __syncwarp();
+    }
+    // ---- shared images to global memory -----------------------------------
+    if (nimg) {
+        __syncthreads();
+        const int64_t ncl = a.corr_local ? pb.ncp : 0;
+        for (int64_t i = threadIdx.x; i < nimg; i += blockDim.x) {
+            const int64_t gk = 1 + (i < ncl ? i : (a.corr_local ? 0 : pb.ncp) + i);
+            if (imgH[i] != R(0)) atomicAdd(a.Hx + gk, (double)imgH[i]);
+            if (a.Sx && imgS[i] != R(0)) atomicAdd(a.Sx + gk, (double)imgS[i]);
+        }
     }
 }
 

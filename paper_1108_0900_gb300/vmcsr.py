@@ -381,17 +381,32 @@ def lm_update(h: Handle, x, Sx0: float, stream=None):
 
 
 def lm_optimize(h: Handle, n_iter: int, shift_H: float, shift_S: float, tol: float, store=VMC_STORE_FP64,
-                seed: int = 1, max_iter: int = 500, max_sub: int = 24):
-    """The linear-method loop of Sec. II.B: sample, lowest eigenpair of the
-    shifted Eq. 8, update; returns one record per iteration (energy
-    statistics before the update and the solver info)."""
+                seed: int = 1, max_iter: int = 500, max_sub: int = 24, grow: float = 10.0):
+    """The linear-method loop of Sec. II.B with its safeguard: sample, lowest
+    eigenpair of the shifted Eq. 8, update, then sample again at the new
+    parameters; a step whose energy is higher than before beyond three
+    combined standard errors is undone and retried with shift_H * grow
+    (the larger diagonal shift rotates the step towards the gradient and
+    shortens it).  Returns one record per iteration."""
+    import math
+    vmc_sample(h, 0, seed)
+    _, es = sr_gradient(h, store)
     hist = []
     for it in range(n_iter):
-        vmc_sample(h, 0, seed + it)
-        _, es = sr_gradient(h, store)
+        C0, f0 = vmc_get_params(h)
         x, info = lm_solve(h, shift_H, shift_S, tol, max_iter, max_sub, store, allow_not_converged=True)
         lm_update(h, x, info["Sx0"])
-        hist.append({"energy": es, "lm": info})
+        vmc_sample(h, 0, seed + 1 + it)
+        _, es_new = sr_gradient(h, store)
+        ok = bool(es_new[0] <= es[0] + 3.0 * math.hypot(es[2], es_new[2]))
+        hist.append({"energy": es, "energy_after": es_new, "lm": info, "shift_H": shift_H, "accepted": ok})
+        if ok:
+            es = es_new
+        else:
+            vmc_set_params(h, C0, f0)
+            shift_H *= grow
+            vmc_sample(h, 0, seed + 100000 + it)
+            _, es = sr_gradient(h, store)
     return hist
 
 
