@@ -1718,21 +1718,8 @@ static int lm_launch(vmc_ctx* h, const double* x, double* Hx, double* Sx, const 
         set_err("linear-method product: per-sample workspace exceeds shared memory");
         return VMC_ERR_UNSUPPORTED;
     }
-    // per-CTA images of the correlator and pairing blocks (H and S sums) if
-    // they fit next to at least two warps' workspaces
-    const size_t img_el = (size_t)(Sx ? 2 : 1) * sizeof(R);
-    auto warps_with = [&](size_t img) -> int {
-        if (img >= h->smem_optin) return 0;
-        return (int)std::min<size_t>(8, (h->smem_optin - img) / (size_t)a.warp_bytes);
-    };
-    size_t img = 0;
-    if (warps_with(img_el * (h->ncp + h->npf)) >= 2) {
-        a.corr_local = 1; a.pf_local = 1; img = img_el * (h->ncp + h->npf);
-    } else if (warps_with(img_el * h->npf) >= 2) {
-        a.pf_local = 1; img = img_el * h->npf;
-    }
-    const int wpb = warps_with(img);
-    const size_t smem = (size_t)wpb * a.warp_bytes + (img + 15) / 16 * 16;
+    const int wpb = (int)std::min<size_t>(8, h->smem_optin / (size_t)a.warp_bytes);
+    const size_t smem = (size_t)wpb * a.warp_bytes;
     VCK(cudaFuncSetAttribute(k_lm_apply<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     VCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lm_apply<R>, 32 * wpb, smem));

@@ -317,7 +317,6 @@ struct LmArgs {
     double* Sx;             // [nv + 1] or null
     int XS, GS;             // row strides of the per-warp matrices
     int warp_bytes;
-    int corr_local, pf_local;  // accumulate those blocks in a per-CTA shared image
 };
 size_t lm_warp_bytes(int N, int M, int ns, int n_mu, int ncorr, int elem);
 template <typename R> __global__ void k_lm_prep(DevProblem pb, const double* x, R* Xt, R* xc);

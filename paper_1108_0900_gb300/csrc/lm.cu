@@ -76,32 +76,10 @@ __device__ R corr_ratio_move(const DevProblem& pb, const uint32_t* cidx, int p, 
     return prod;
 }
 
-// Sums into the products go to a per-CTA shared-memory image of the
-// parameter block when it fits (many samples of one CTA hit the same few
-// thousand amplitudes; global atomics on them serialise), else to global
-// memory.  Image layout: correlator amplitudes [0, ncp) if corr_local, then
-// the pairing block if pf_local.
-template <typename R>
-struct LmAcc {
-    double* g;          // global vector, parameter k at g[1 + k]
-    R* img;             // shared image or null
-    int corr_local, pf_local;
-    int64_t ncp;
-    __device__ __forceinline__ void corr(int64_t k, double v) const {
-        if (corr_local) atomicAdd(img + k, (R)v);
-        else atomicAdd(g + 1 + k, v);
-    }
-    __device__ __forceinline__ void pf(int64_t idx, double v) const {
-        if (pf_local) atomicAdd(img + (corr_local ? ncp : 0) + idx, (R)v);
-        else atomicAdd(g + 1 + ncp + idx, v);
-    }
-};
-
 // Adjoint of the correlator ratio: coef (1/C at the new state) and
 // -coef (1/C at the old state) for every correlator the move changes.
-template <typename R>
 __device__ void corr_ratio_adjoint(const DevProblem& pb, const uint32_t* cidx, int p, int q, double coef,
-                                   const LmAcc<R>& out) {
+                                   double* out) {
     const int ns = pb.ns;
     const int sf = p >= ns ? 2 : 1;
     const int sp = p >= ns ? p - ns : p, sq = q >= ns ? q - ns : q;
@@ -111,8 +89,8 @@ __device__ void corr_ratio_adjoint(const DevProblem& pb, const uint32_t* cidx, i
         const int newi = corr_entry(pb, cidx, sp, sq, sf, e, &c);
         if (c < 0) continue;
         const int64_t k1 = pb.corr_off[c] + newi, k0 = pb.corr_off[c] + cidx[c];
-        out.corr(k1, coef / __ldg(pb.C64 + k1));
-        out.corr(k0, -coef / __ldg(pb.C64 + k0));
+        atomicAdd(out + k1, coef / __ldg(pb.C64 + k1));
+        atomicAdd(out + k0, -coef / __ldg(pb.C64 + k0));
     }
 }
 
@@ -229,13 +207,7 @@ __global__ void __launch_bounds__(256) k_lm_apply(LmArgs a) {
     const int nex = nu * eu + nd * ed;
     const uint64_t smask = ns == 64 ? ~0ull : ((1ull << ns) - 1ull);
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const int64_t nimg = (a.corr_local ? pb.ncp : 0) + (a.pf_local ? pb.npf : 0);
-    R* imgH = (R*)(smem_raw + (size_t)(blockDim.x >> 5) * a.warp_bytes);
-    R* imgS = imgH + nimg;
-    for (int64_t i = threadIdx.x; i < nimg * (a.Sx ? 2 : 1); i += blockDim.x) imgH[i] = R(0);
-    __syncthreads();
-    const LmAcc<R> accH{a.Hx, nimg ? imgH : nullptr, a.corr_local, a.pf_local, pb.ncp};
-    const LmAcc<R> accS{a.Sx, nimg ? imgS : nullptr, a.corr_local, a.pf_local, pb.ncp};
+    double* Hf = a.Hx + 1 + pb.ncp;
 
     for (int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid; s < a.n_s; s += nwarps) {
         // ---- configuration, A^{-1} and O(n) . x ---------------------------
@@ -335,7 +307,7 @@ __global__ void __launch_bounds__(256) k_lm_apply(LmArgs a) {
             const R g = G[ie * GS + ia];
             W += z * rc * g;
             Pm[ie * GS + ia] = z * rc;
-            corr_ratio_adjoint<R>(pb, cidx, p, v, (double)(z * rc * g) * sc, accH);
+            corr_ratio_adjoint(pb, cidx, p, v, (double)(z * rc * g) * sc, a.Hx + 1);
         }
         W = warp_sum(W);
         __syncwarp();
@@ -353,36 +325,26 @@ __global__ void __launch_bounds__(256) k_lm_apply(LmArgs a) {
         for (int c = lane; c < ncorr; c += 32) {
             const int64_t k = pb.corr_off[c] + cidx[c];
             const double ic = 1.0 / __ldg(pb.C64 + k);
-            accH.corr(k, (double)W * ic * sc);
-            if (a.Sx) accS.corr(k, (double)xt * ic * sc);
+            atomicAdd(a.Hx + 1 + k, (double)W * ic * sc);
+            if (a.Sx) atomicAdd(a.Sx + 1 + k, (double)xt * ic * sc);
         }
         for (int e = lane; e < pb.P; e += 32) {
             const uint16_t t = pb.pairtab[e];
             const int aa = t & 255, bb = t >> 8;
             const int64_t idx = pb.rowbase[occ[aa]] + occ[bb];
             const R xba = X[bb * XS + aa];
-            accH.pf(idx, (double)(W * xba - Xo[aa * XS + bb] + Xo[bb * XS + aa]) * sc);
-            if (a.Sx) accS.pf(idx, (double)(xt * xba) * sc);
+            atomicAdd(Hf + idx, (double)(W * xba - Xo[aa * XS + bb] + Xo[bb * XS + aa]) * sc);
+            if (a.Sx) atomicAdd(a.Sx + 1 + pb.ncp + idx, (double)(xt * xba) * sc);
         }
         for (int t = lane; t < E * N; t += 32) {
             const int ie = t / N, k = t % N;
             const R b = D[ie * GS + k];
             if (b == R(0)) continue;
             const int v = emp[ie], o = occ[k];
-            if (v < o) accH.pf(pb.rowbase[v] + o, (double)b * sc);
-            else accH.pf(pb.rowbase[o] + v, -(double)b * sc);
+            if (v < o) atomicAdd(Hf + pb.rowbase[v] + o, (double)b * sc);
+            else atomicAdd(Hf + pb.rowbase[o] + v, -(double)b * sc);
         }
         __syncwarp();
-    }
-    // ---- shared images to global memory -----------------------------------
-    if (nimg) {
-        __syncthreads();
-        const int64_t ncl = a.corr_local ? pb.ncp : 0;
-        for (int64_t i = threadIdx.x; i < nimg; i += blockDim.x) {
-            const int64_t gk = 1 + (i < ncl ? i : (a.corr_local ? 0 : pb.ncp) + i);
-            if (imgH[i] != R(0)) atomicAdd(a.Hx + gk, (double)imgH[i]);
-            if (a.Sx && imgS[i] != R(0)) atomicAdd(a.Sx + gk, (double)imgS[i]);
-        }
     }
 }
 

@@ -384,11 +384,10 @@ def lm_optimize(h: Handle, n_iter: int, shift_H: float, shift_S: float, tol: flo
                 seed: int = 1, max_iter: int = 500, max_sub: int = 24, grow: float = 10.0):
     """The linear-method loop of Sec. II.B with its safeguard: sample, lowest
     eigenpair of the shifted Eq. 8, update, then sample again at the new
-    parameters; a step whose energy is higher than before beyond three
-    combined standard errors is undone and retried with shift_H * grow
+    parameters; a step whose energy is higher than before by more than three
+    standard errors of the earlier estimate is undone and retried with shift_H * grow
     (the larger diagonal shift rotates the step towards the gradient and
     shortens it).  Returns one record per iteration."""
-    import math
     vmc_sample(h, 0, seed)
     _, es = sr_gradient(h, store)
     hist = []
@@ -398,7 +397,9 @@ def lm_optimize(h: Handle, n_iter: int, shift_H: float, shift_S: float, tol: flo
         lm_update(h, x, info["Sx0"])
         vmc_sample(h, 0, seed + 1 + it)
         _, es_new = sr_gradient(h, store)
-        ok = bool(es_new[0] <= es[0] + 3.0 * math.hypot(es[2], es_new[2]))
+        # judged against the error of the energy before the step: a bad step
+        # often also inflates the error of the new estimate
+        ok = bool(es_new[0] <= es[0] + 3.0 * es[2])
         hist.append({"energy": es, "energy_after": es_new, "lm": info, "shift_H": shift_H, "accepted": ok})
         if ok:
             es = es_new
