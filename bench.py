@@ -256,6 +256,30 @@ def run_gpu(args, rank, world, dist):
                   "cg_inner_iterations": float(np.mean([i["iterations"] for i in infos_a])),
                   "true_rel_residual": max(i["true_rel_residual"] for i in infos_a),
                   "converged": all(i["converged"] for i in infos_a)}
+        # accelerated linear method (Sec. II.B) on the same samples: the Eq. 10
+        # product (H x, S x) through the Eq. 9 factors, and a bounded Davidson
+        # solve of the shifted Eq. 8
+        lm = None
+        if args.lm_iters > 0:
+            xl = torch.from_numpy(np.random.default_rng(0).standard_normal(wla.n_params + 1)).cuda()
+            V.lm_apply(ha, xl, V.VMC_STORE_FP32)
+            barrier()
+            e0.record()
+            for _ in range(3):
+                V.lm_apply(ha, xl, V.VMC_STORE_FP32)
+            e1.record()
+            barrier()
+            ms_lm = e0.elapsed_time(e1) / 3
+            t0 = time.perf_counter()
+            _, linfo = V.lm_solve(ha, 1.0, 1e-2, 1e-6, max_iter=args.lm_iters, max_sub=32,
+                                  store=V.VMC_STORE_FP32, allow_not_converged=True)
+            barrier()
+            lm = {"product_ms": round(ms_lm, 3),
+                  "products_per_s": round(1e3 / ms_lm, 2),
+                  "davidson_s": round(time.perf_counter() - t0, 3),
+                  "davidson": {k: (round(v, 6) if isinstance(v, float) else v) for k, v in linfo.items()},
+                  "shifts": {"H": 1.0, "S": 1e-2}, "store": "fp32 (FP64 sums)"}
+        abinit["linear_method"] = lm
         ha.close()
 
     # ---- plain FP64 path ------------------------------------------------------
@@ -440,6 +464,8 @@ def main():
                     help="SR steps timed on the shared-correlator 8x8 workload (0: skip)")
     ap.add_argument("--abinitio-steps", type=int, default=2,
                     help="SR steps timed on the 24-orbital ab initio workload (0: skip)")
+    ap.add_argument("--lm-iters", type=int, default=60,
+                    help="Davidson steps of the linear-method leg on the ab initio workload (0: skip)")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-cg-iters", type=float, default=350.0)
