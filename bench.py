@@ -453,6 +453,39 @@ def run_sv_only(args):
             "passes": args.sv_only, "stores": out}
 
 
+def run_lm_only(args):
+    """Linear-method product timing on the 24-orbital ab initio workload:
+    the stores filled from seeded sector configurations (vmc_measure, FP64
+    walkers), then `--lm-only` Eq. 10 products per store, CUDA events on the
+    launching stream."""
+    import torch
+    from paper_1108_0900_gb300 import inputs
+    from paper_1108_0900_gb300 import vmcsr as V
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    wl = inputs.workload("abinitio24")
+    h = V.vmc_create(wl, walker_precision=V.VMC_FP64, keep_fp64_store=True, keep_lowp_store=True)
+    V.vmc_set_params(h, wl.C, wl.f)
+    cfgs = inputs.draw_configs(np.random.default_rng(555), wl.n_samples, wl.n_sites, wl.n_up, wl.n_dn)
+    V.vmc_measure(h, cfgs)
+    x = torch.from_numpy(np.random.default_rng(2).standard_normal(wl.n_params + 1)).cuda()
+    out = {}
+    for name, store in (("fp32", V.VMC_STORE_FP32), ("fp64", V.VMC_STORE_FP64)):
+        V.lm_apply(h, x, store)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.lm_only):
+            V.lm_apply(h, x, store)
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = {"product_ms": round(e0.elapsed_time(e1) / args.lm_only, 3)}
+    h.close()
+    return {"metric": "linear-method product ms", "workload": "synthetic ab initio, 24 orbitals, 12+12 electrons, "
+            "276 pair correlators + pfaffian (n_v=5,544), 65,536 seeded sector configurations",
+            "products": args.lm_only, "stores": out}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -470,9 +503,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-cg-iters", type=float, default=350.0)
     ap.add_argument("--sv-only", type=int, default=0, help="time N S products per store kind and exit")
+    ap.add_argument("--lm-only", type=int, default=0, help="time N linear-method products per store and exit")
     args = ap.parse_args()
     if args.sv_only:
         print(json.dumps(run_sv_only(args)))
+        return
+    if args.lm_only:
+        print(json.dumps(run_lm_only(args)))
         return
     args.warmup = max(args.warmup, 1)
 

@@ -77,9 +77,14 @@ __device__ R corr_ratio_move(const DevProblem& pb, const uint32_t* cidx, int p, 
 }
 
 // Adjoint of the correlator ratio: coef (1/C at the new state) and
-// -coef (1/C at the old state) for every correlator the move changes.
+// -coef (1/C at the old state) for every correlator the move changes.  The
+// old-state parts of all moves of a sample share one parameter per
+// correlator, so they are summed per correlator in shared memory (old[c])
+// and leave with the sample's own O(n) term: one global atomic per
+// correlator instead of one per move.
+template <typename R>
 __device__ void corr_ratio_adjoint(const DevProblem& pb, const uint32_t* cidx, int p, int q, double coef,
-                                   double* out) {
+                                   double* out, R* old) {
     const int ns = pb.ns;
     const int sf = p >= ns ? 2 : 1;
     const int sp = p >= ns ? p - ns : p, sq = q >= ns ? q - ns : q;
@@ -88,9 +93,9 @@ __device__ void corr_ratio_adjoint(const DevProblem& pb, const uint32_t* cidx, i
         int c;
         const int newi = corr_entry(pb, cidx, sp, sq, sf, e, &c);
         if (c < 0) continue;
-        const int64_t k1 = pb.corr_off[c] + newi, k0 = pb.corr_off[c] + cidx[c];
+        const int64_t k1 = pb.corr_off[c] + newi;
         atomicAdd(out + k1, coef / __ldg(pb.C64 + k1));
-        atomicAdd(out + k0, -coef / __ldg(pb.C64 + k0));
+        atomicAdd(old + c, (R)coef);
     }
 }
 
@@ -154,7 +159,8 @@ __device__ void warp_gemm(int m, int n, int K, const R* A, int sai, int sak, con
 
 size_t lm_warp_bytes(int N, int M, int ns, int n_mu, int ncorr, int elem) {
     const size_t XS = N + 1, GS = N + 1, E = M - N;
-    const size_t nr = 2 * N * XS + 3 * E * GS + (size_t)ns * ns + (size_t)((n_mu + 1) / 2 * 2);
+    const size_t nr = 2 * N * XS + 3 * E * GS + (size_t)ns * ns + (size_t)((n_mu + 1) / 2 * 2) +
+                      (size_t)((ncorr + 1) / 2 * 2);
     const size_t b = nr * elem + (size_t)((ncorr + 3) / 4 * 4) * 4 + 64 + 128;
     return (b + 15) / 16 * 16;
 }
@@ -193,7 +199,8 @@ __global__ void __launch_bounds__(256) k_lm_apply(LmArgs a) {
     R* D = Pm + E * GS;                                     // P A^{-1}, later B = Cbar A^{-T}
     R* Y = D + E * GS;                                      // y summed over spins, later z
     R* w = Y + nn;
-    uint32_t* cidx = (uint32_t*)(w + (n_mu + 1) / 2 * 2);
+    R* cold = w + (n_mu + 1) / 2 * 2;                       // old-state adjoint sums per correlator
+    uint32_t* cidx = (uint32_t*)(cold + (ncorr + 1) / 2 * 2);
     uint8_t* occ = (uint8_t*)(cidx + (ncorr + 3) / 4 * 4);
     uint8_t* emp = occ + 64;
     const R* Xt = (const R*)a.Xt;
@@ -294,6 +301,8 @@ __global__ void __launch_bounds__(256) k_lm_apply(LmArgs a) {
         __syncwarp();
 
         // ---- backward: z over the moves ------------------------------------
+        for (int c = lane; c < ncorr; c += 32) cold[c] = R(0);
+        __syncwarp();
         R W = R(0);
         for (int i = lane; i < N; i += 32) W += Y[(occ[i] % ns) * (ns + 1)];
         if (lane == 0) W += c0 * xt;
@@ -307,7 +316,7 @@ __global__ void __launch_bounds__(256) k_lm_apply(LmArgs a) {
             const R g = G[ie * GS + ia];
             W += z * rc * g;
             Pm[ie * GS + ia] = z * rc;
-            corr_ratio_adjoint(pb, cidx, p, v, (double)(z * rc * g) * sc, a.Hx + 1);
+            corr_ratio_adjoint<R>(pb, cidx, p, v, (double)(z * rc * g) * sc, a.Hx + 1, cold);
         }
         W = warp_sum(W);
         __syncwarp();
@@ -325,7 +334,7 @@ __global__ void __launch_bounds__(256) k_lm_apply(LmArgs a) {
         for (int c = lane; c < ncorr; c += 32) {
             const int64_t k = pb.corr_off[c] + cidx[c];
             const double ic = 1.0 / __ldg(pb.C64 + k);
-            atomicAdd(a.Hx + 1 + k, (double)W * ic * sc);
+            atomicAdd(a.Hx + 1 + k, ((double)W * sc - (double)cold[c]) * ic);
             if (a.Sx) atomicAdd(a.Sx + 1 + k, (double)xt * ic * sc);
         }
         for (int e = lane; e < pb.P; e += 32) {
