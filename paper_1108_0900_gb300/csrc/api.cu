@@ -1718,9 +1718,7 @@ static int lm_launch(vmc_ctx* h, const double* x, double* Hx, double* Sx, const 
         set_err("linear-method product: per-sample workspace exceeds shared memory");
         return VMC_ERR_UNSUPPORTED;
     }
-    // as many warps (samples in flight) as shared memory holds, up to 16: the
-    // per-sample products are latency-bound
-    const int wpb = (int)std::min<size_t>(16, h->smem_optin / (size_t)a.warp_bytes);
+    const int wpb = (int)std::min<size_t>(8, h->smem_optin / (size_t)a.warp_bytes);
     const size_t smem = (size_t)wpb * a.warp_bytes;
     VCK(cudaFuncSetAttribute(k_lm_apply<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;

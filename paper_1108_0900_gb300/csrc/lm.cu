@@ -185,7 +185,7 @@ __global__ void k_lm_prep(DevProblem pb, const double* x, R* Xt, R* xc) {
 }
 
 template <typename R>
-__global__ void __launch_bounds__(512) k_lm_apply(LmArgs a) {
+__global__ void __launch_bounds__(256) k_lm_apply(LmArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const DevProblem& pb = a.pb;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
