@@ -132,9 +132,9 @@ def run_gpu(args, rank, world, dist):
 
     def step(h, path, k, info_out):
         V.vmc_sample(h, 0, seed + 1 + k)
-        store = V.VMC_STORE_FP32 if path == "mixed" else V.VMC_STORE_FP64
+        store = V.VMC_STORE_FP64 if path == "fp64" else V.VMC_STORE_FP32
         g, _ = V.sr_gradient(h, store, stats=False)
-        mode = V.VMC_CG_MIXED if path == "mixed" else V.VMC_CG_FP64
+        mode = {"mixed": V.VMC_CG_MIXED, "block4": V.VMC_CG_BLOCK4}.get(path, V.VMC_CG_FP64)
         x, info = V.sr_cg_solve(h, g, shift, tol, max_iter, mode, allow_not_converged=True)
         info_out.append(info)
         return x
@@ -167,6 +167,19 @@ def run_gpu(args, rank, world, dist):
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
+
+    # ---- the same step with the enlarged block CG (four parameter-group
+    # columns, four-vector BF16 products) as the inner solve ----------------
+    block = None
+    if args.block_steps > 0:
+        ms_b, infos_b, prof_b, _ = timed(hm, "block4", args.block_steps, 1, profile=True)
+        block = {"ms_per_step": round(ms_b, 3),
+                 "inner_block_iterations": float(np.mean([i["iterations"] for i in infos_b])),
+                 "outer_steps": float(np.mean([i["refinements"] for i in infos_b])),
+                 "four_vector_product_ms": round(prof_b["pass_ms"] / max(1, prof_b["pass_launches"]), 4)
+                 if prof_b and prof_b["pass_launches"] else None,
+                 "true_rel_residual": max(i["true_rel_residual"] for i in infos_b),
+                 "converged": all(i["converged"] for i in infos_b)}
 
     # ---- end to end through the public API with host buffers ----------------
     import ctypes as ct
@@ -320,6 +333,7 @@ def run_gpu(args, rank, world, dist):
                "converged": all(i["converged"] for i in infos)},
         "sv_gbs": round(ach, 1) if ach else None,
         "fp64_path": fp64,
+        "block_cg": block,
         "shared_correlators": shared,
         "abinitio": abinit,
         "speedup_vs_fp64_path": round(fp64["ms_per_step"] / ms, 3) if fp64 else None,
@@ -495,6 +509,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--shared-steps", type=int, default=2,
                     help="SR steps timed on the shared-correlator 8x8 workload (0: skip)")
+    ap.add_argument("--block-steps", type=int, default=2,
+                    help="SR steps timed with the block-CG inner solve (0: skip)")
     ap.add_argument("--abinitio-steps", type=int, default=2,
                     help="SR steps timed on the 24-orbital ab initio workload (0: skip)")
     ap.add_argument("--lm-iters", type=int, default=60,

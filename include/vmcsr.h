@@ -69,6 +69,12 @@ extern "C" {
 #define VMC_CG_MIXED 1  /* BF16-stream inner CG (FP32 vectors, FP64 scalars),
                            refined against the FP32 store with FP64 accumulation  */
 #define VMC_CG_FP32 2   /* like MIXED but the inner product streams FP32          */
+#define VMC_CG_BLOCK4 3 /* like MIXED with an enlarged block CG as the inner solve:
+                           the right-hand side split into four parameter-group
+                           columns (first / second half of the correlators,
+                           same-spin / opposite-spin pairing), one four-vector
+                           BF16 product per inner iteration, solution = column
+                           sum; needs >= 2 correlators (else UNSUPPORTED)       */
 
 typedef struct vmc_ctx* vmc_handle;
 

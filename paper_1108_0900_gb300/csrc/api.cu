@@ -123,6 +123,7 @@ struct vmc_ctx {
     int *d_lmLptr = nullptr, *d_lmLidx = nullptr, *d_lmRptr = nullptr, *d_lmRidx = nullptr;
     // Davidson workspace: basis V and its images (column-major, ld = lm_ld),
     // work vectors, dot partials
+    double* d_bcg = nullptr;   // block CG: Gram partials, reduced Gram, alpha, beta
     int lm_cap = 0;
     int64_t lm_ld = 0;
     double *d_lmV = nullptr, *d_lmHV = nullptr, *d_lmSV = nullptr, *d_lmW = nullptr, *d_lmdot = nullptr;
@@ -1450,8 +1451,12 @@ static double dot64(vmc_ctx* h, const double* a, const double* b, cudaStream_t s
 
 // z = M^{-1} r: the inner low-precision CG on (S_lowp + shift I) with the
 // right-hand side scaled to unit norm, to relative tolerance itol.
+static int inner_block(vmc_ctx* h, const double* r, double rnorm, double* z, double shift, double itol,
+                       int max_iter, int* iters, cudaStream_t st);
+
 static int inner_solve(vmc_ctx* h, int mode, const double* r, double rnorm, double* z, double shift, double itol,
                        int max_iter, int* iters, cudaStream_t st) {
+    if (mode == VMC_CG_BLOCK4) return inner_block(h, r, rnorm, z, shift, itol, max_iter, iters, st);
     k_cast<float><<<kNumPart, 256, 0, st>>>(r, h->d_b32, h->nv, 1.0 / rnorm); h->n_launch++;
     VCK(cudaGetLastError());
     int rc = mode == VMC_CG_MIXED
@@ -1462,6 +1467,95 @@ static int inner_solve(vmc_ctx* h, int mode, const double* r, double rnorm, doub
     if (rc) return rc;
     VCK(cudaMemsetAsync(z, 0, sizeof(double) * h->nv, st));
     k_axpy_to64<float><<<kNumPart, 256, 0, st>>>(z, h->d_x32, rnorm, h->nv); h->n_launch++;
+    VCK(cudaGetLastError());
+    return VMC_OK;
+}
+
+// 4 x 4 system A X = B (row-major) by Gaussian elimination with partial
+// pivoting; false if a pivot vanishes relative to the matrix scale
+static bool solve4(const double* A_in, const double* B_in, double* X) {
+    double A[16], B[16], scale = 0.0;
+    memcpy(A, A_in, sizeof(A));
+    memcpy(B, B_in, sizeof(B));
+    for (double v : A) scale = std::max(scale, std::fabs(v));
+    if (!(scale > 0.0) || !std::isfinite(scale)) return false;
+    for (int k = 0; k < 4; ++k) {
+        int piv = k;
+        for (int i = k + 1; i < 4; ++i)
+            if (std::fabs(A[4 * i + k]) > std::fabs(A[4 * piv + k])) piv = i;
+        if (!(std::fabs(A[4 * piv + k]) > 1e-14 * scale)) return false;
+        if (piv != k)
+            for (int j = 0; j < 4; ++j) { std::swap(A[4 * k + j], A[4 * piv + j]); std::swap(B[4 * k + j], B[4 * piv + j]); }
+        for (int i = k + 1; i < 4; ++i) {
+            const double f = A[4 * i + k] / A[4 * k + k];
+            for (int j = 0; j < 4; ++j) { A[4 * i + j] -= f * A[4 * k + j]; B[4 * i + j] -= f * B[4 * k + j]; }
+        }
+    }
+    for (int c = 0; c < 4; ++c)
+        for (int i = 3; i >= 0; --i) {
+            double v = B[4 * i + c];
+            for (int j = i + 1; j < 4; ++j) v -= A[4 * i + j] * X[4 * j + c];
+            X[4 * i + c] = v / A[4 * i + i];
+        }
+    return true;
+}
+
+static int gram4(vmc_ctx* h, const float* U, const float* V, double* out, cudaStream_t st) {
+    k_bcg_gram<<<kNumPart, 256, 0, st>>>(U, V, h->nv, h->d_bcg);
+    k_lm_dots_reduce<<<1, 64, 0, st>>>(h->d_bcg, kNumPart, 16, h->d_bcg + (size_t)kNumPart * 16);
+    h->n_launch += 2;
+    VCK(cudaMemcpyAsync(out, h->d_bcg + (size_t)kNumPart * 16, 16 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    VCK(cudaStreamSynchronize(st));
+    return VMC_OK;
+}
+
+// z = M^{-1} r by enlarged block CG on the BF16 operator: the unit-norm
+// right-hand side split into four parameter-group columns, O'Leary's block
+// recurrences (alpha = (P^T Q)^{-1} R^T R, beta = (R^T R)^{-1} R_new^T R_new),
+// stopped when the residual of the column sum, |sum_j R_j|^2 = sum of the
+// entries of R^T R, meets itol; z = |r| sum_j X_j.
+static int inner_block(vmc_ctx* h, const double* r, double rnorm, double* z, double shift, double itol,
+                       int max_iter, int* iters, cudaStream_t st) {
+    const int64_t n = h->nv;
+    if (!h->d_bcg) VCK(h->alloc(&h->d_bcg, (size_t)kNumPart * 16 + 64));
+    float *X = h->d_x32, *R = h->d_r32, *P = h->d_p32, *Q = h->d_q32;
+    double* dal = h->d_bcg + (size_t)kNumPart * 16 + 16;
+    double* dbe = dal + 16;
+    const unsigned vg = (unsigned)vgrid(h, 1);
+    k_cast<float><<<kNumPart, 256, 0, st>>>(r, h->d_b32, n, 1.0 / rnorm);
+    k_bcg_split<<<vg, 256, 0, st>>>(h->d_b32, R, n, h->ncp, h->corr_off[h->ncorr / 2], h->d_pq_of, h->ns);
+    h->n_launch += 2;
+    VCK(cudaMemsetAsync(X, 0, sizeof(float) * 4 * n, st));
+    VCK(cudaMemcpyAsync(P, R, sizeof(float) * 4 * n, cudaMemcpyDeviceToDevice, st));
+    double RR[16], RRn[16], PQ[16], al[16], be[16];
+    int rc = gram4(h, R, R, RR, st);
+    if (rc) return rc;
+    double b2 = 0.0;
+    for (double v : RR) b2 += v;
+    int it = 0;
+    while (it < max_iter) {
+        rc = apply_S_impl<__nv_bfloat16, float, 4>(h, h->d_pf16, 2, P, Q, shift, nullptr, nullptr, nullptr, st);
+        if (rc) return rc;
+        ++it;
+        if ((rc = gram4(h, P, Q, PQ, st))) return rc;
+        if (!solve4(PQ, RR, al)) break;
+        VCK(cudaMemcpyAsync(dal, al, sizeof(al), cudaMemcpyHostToDevice, st));
+        k_bcg_step<<<vg, 256, 0, st>>>(X, R, P, Q, dal, n); h->n_launch++;
+        if ((rc = gram4(h, R, R, RRn, st))) return rc;
+        double res2 = 0.0;
+        for (double v : RRn) res2 += v;
+        if (res2 <= itol * itol * b2) break;
+        if (!solve4(RR, RRn, be)) break;
+        VCK(cudaMemcpyAsync(dbe, be, sizeof(be), cudaMemcpyHostToDevice, st));
+        k_bcg_dir<<<vg, 256, 0, st>>>(P, R, dbe, n); h->n_launch++;
+        memcpy(RR, RRn, sizeof(RR));
+    }
+    *iters = it;
+    VCK(cudaMemsetAsync(z, 0, sizeof(double) * n, st));
+    for (int j = 0; j < 4; ++j) {
+        k_axpy_to64<float><<<kNumPart, 256, 0, st>>>(z, X + (size_t)j * n, rnorm, n);
+        h->n_launch++;
+    }
     VCK(cudaGetLastError());
     return VMC_OK;
 }
@@ -1485,7 +1579,7 @@ static int fcg_mixed(vmc_ctx* h, const double* g, double shift, double tol, int 
     const double target = tol * tol * gn2;
     // inner accuracy beyond a few percent buys little: the BF16 operator's own
     // error limits what one preconditioner application can contribute
-    const double itol_floor = mode == VMC_CG_MIXED ? 3e-2 : 1e-3;
+    const double itol_floor = mode == VMC_CG_FP32 ? 1e-3 : 3e-2;
     int used = 0;
     if (rr == 0.0) { inf->true_rel_residual = 0.0; return VMC_OK; }
     double rn = std::sqrt(rr);
@@ -1559,10 +1653,18 @@ extern "C" int sr_cg_solve(vmc_handle h, const double* g, double shift, double t
         inf.iterations = it;
         inf.residual_products = 1;
         inf.true_rel_residual = gn2 > 0 ? std::sqrt(rr / gn2) : 0.0;
-    } else if (mode == VMC_CG_MIXED || mode == VMC_CG_FP32) {
+    } else if (mode == VMC_CG_MIXED || mode == VMC_CG_FP32 || mode == VMC_CG_BLOCK4) {
         if (!h->d_pf32 || !h->d_pf16) return VMC_ERR_STATE;
+        if (mode == VMC_CG_BLOCK4) {
+            // the four parameter groups must all be non-empty
+            const int64_t split = h->ncorr >= 2 ? h->corr_off[h->ncorr / 2] : 0;
+            if (split <= 0 || split >= h->ncp || h->ns < 2) {
+                set_err("block CG needs at least two correlator blocks and two sites");
+                return VMC_ERR_UNSUPPORTED;
+            }
+        }
         rc = ensure_obar(h, 1, st);
-        if (!rc && mode == VMC_CG_MIXED) rc = ensure_obar(h, 2, st);
+        if (!rc && mode != VMC_CG_FP32) rc = ensure_obar(h, 2, st);
         if (rc) return rc;
         rc = fcg_mixed(h, g, shift, tol, max_iter, mode, x, gn2, &inf, st);
         if (rc) return rc;

@@ -328,4 +328,11 @@ __global__ void k_lm_combine(double* out, const double* V, int64_t ld, int k, co
 __global__ void k_lm_precond(double* t, const double* r, const double* d, double eps, int64_t n);
 __global__ void k_lm_update(UpdateArgs a, const double* x, double scale);
 
+// enlarged block CG (bcg.cu): [4][n] FP32 block vectors, FP64 4 x 4 algebra
+__global__ void k_bcg_split(const float* b, float* B, int64_t n, int64_t ncp, int64_t corr_split,
+                            const uint32_t* pq_of, int ns);
+__global__ void k_bcg_gram(const float* U, const float* V, int64_t n, double* part);
+__global__ void k_bcg_step(float* X, float* R, const float* P, const float* Q, const double* alpha, int64_t n);
+__global__ void k_bcg_dir(float* P, const float* R, const double* beta, int64_t n);
+
 }  // namespace vmc

@@ -26,7 +26,7 @@ VMC_OK = 0
 VMC_HUBBARD, VMC_ABINITIO = 0, 1
 VMC_FP64, VMC_FP32 = 0, 1
 VMC_STORE_FP64, VMC_STORE_FP32, VMC_STORE_BF16, VMC_STORE_FP32_F32ACC = 0, 1, 2, 3
-VMC_CG_FP64, VMC_CG_MIXED, VMC_CG_FP32 = 0, 1, 2
+VMC_CG_FP64, VMC_CG_MIXED, VMC_CG_FP32, VMC_CG_BLOCK4 = 0, 1, 2, 3
 ERRORS = {
     -1: "INVALID_ARG", -2: "OOM", -3: "SINGULAR", -4: "NONFINITE", -5: "NOT_CONVERGED",
     -6: "TIMEOUT", -7: "CUDA", -8: "UNSUPPORTED", -9: "STATE",

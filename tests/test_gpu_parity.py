@@ -277,6 +277,28 @@ def test_cg_mixed_refinement(case, mode):
     assert np.linalg.norm(r) / np.linalg.norm(g_or) <= 2e-6
 
 
+def test_cg_block4_refinement(case):
+    """Enlarged block CG (four parameter-group columns, four-vector BF16
+    products) as the inner solve of the flexible outer loop: same tolerance
+    and the same residual against the oracle's FP64 store as the one-vector
+    mode.  Ansatz with all correlators in one parameter block cannot be split
+    four ways (UNSUPPORTED)."""
+    wl = case["wl"]
+    h = make(wl)
+    V.vmc_measure(h, case["smp"])
+    g, _ = V.sr_gradient(h, V.VMC_STORE_FP64)
+    try:
+        x, info = V.sr_cg_solve(h, g, wl.shift, 1e-6, 50 * wl.n_params, V.VMC_CG_BLOCK4)
+    except V.VmcError as e:
+        split = int(wl.corr_param_off[wl.n_corr // 2]) if wl.n_corr >= 2 else 0
+        assert e.code == -8 and not (0 < split < wl.n_corr_params)
+        pytest.skip("four-way split needs two correlator blocks")
+    assert info["converged"] and info["true_rel_residual"] <= 1e-6
+    g_or, _ = oracle.gradient(case["O"], case["E"])
+    r = g_or - oracle.apply_S(case["O"], x.cpu().numpy(), wl.shift)
+    assert np.linalg.norm(r) / np.linalg.norm(g_or) <= 2e-6
+
+
 # ---------------------------------------------------------------------------
 # log-amplitude and its adjoint
 # ---------------------------------------------------------------------------
