@@ -1456,7 +1456,11 @@ static int inner_block(vmc_ctx* h, const double* r, double rnorm, double* z, dou
 
 static int inner_solve(vmc_ctx* h, int mode, const double* r, double rnorm, double* z, double shift, double itol,
                        int max_iter, int* iters, cudaStream_t st) {
-    if (mode == VMC_CG_BLOCK4) return inner_block(h, r, rnorm, z, shift, itol, max_iter, iters, st);
+    if (mode == VMC_CG_BLOCK4) {
+        int rc = inner_block(h, r, rnorm, z, shift, itol, max_iter, iters, st);
+        if (rc || *iters > 0) return rc;
+        mode = VMC_CG_MIXED;   // no block step possible: one-vector inner CG
+    }
     k_cast<float><<<kNumPart, 256, 0, st>>>(r, h->d_b32, h->nv, 1.0 / rnorm); h->n_launch++;
     VCK(cudaGetLastError());
     int rc = mode == VMC_CG_MIXED
@@ -1500,6 +1504,20 @@ static bool solve4(const double* A_in, const double* B_in, double* X) {
     return true;
 }
 
+// the same with A + delta I, delta = 1e-12 max |A_ii|, when A is singular:
+// a block column that is zero (a parameter group with no right-hand side)
+// or has become dependent (the block Krylov space of a rank-deficient S is
+// exhausted) then gets a zero row in the solution instead of a breakdown
+static bool solve4_reg(const double* A, const double* B, double* X) {
+    if (solve4(A, B, X)) return true;
+    double d = 0.0, Ar[16];
+    for (int i = 0; i < 4; ++i) d = std::max(d, std::fabs(A[5 * i]));
+    if (!(d > 0.0)) return false;
+    memcpy(Ar, A, sizeof(Ar));
+    for (int i = 0; i < 4; ++i) Ar[5 * i] += 1e-12 * d;
+    return solve4(Ar, B, X);
+}
+
 static int gram4(vmc_ctx* h, const float* U, const float* V, double* out, cudaStream_t st) {
     k_bcg_gram<<<kNumPart, 256, 0, st>>>(U, V, h->nv, h->d_bcg);
     k_lm_dots_reduce<<<1, 64, 0, st>>>(h->d_bcg, kNumPart, 16, h->d_bcg + (size_t)kNumPart * 16);
@@ -1532,25 +1550,26 @@ static int inner_block(vmc_ctx* h, const double* r, double rnorm, double* z, dou
     if (rc) return rc;
     double b2 = 0.0;
     for (double v : RR) b2 += v;
-    int it = 0;
+    int it = 0, steps = 0;
     while (it < max_iter) {
         rc = apply_S_impl<__nv_bfloat16, float, 4>(h, h->d_pf16, 2, P, Q, shift, nullptr, nullptr, nullptr, st);
         if (rc) return rc;
         ++it;
         if ((rc = gram4(h, P, Q, PQ, st))) return rc;
-        if (!solve4(PQ, RR, al)) break;
+        if (!solve4_reg(PQ, RR, al)) break;
         VCK(cudaMemcpyAsync(dal, al, sizeof(al), cudaMemcpyHostToDevice, st));
         k_bcg_step<<<vg, 256, 0, st>>>(X, R, P, Q, dal, n); h->n_launch++;
+        ++steps;
         if ((rc = gram4(h, R, R, RRn, st))) return rc;
         double res2 = 0.0;
         for (double v : RRn) res2 += v;
         if (res2 <= itol * itol * b2) break;
-        if (!solve4(RR, RRn, be)) break;
+        if (!solve4_reg(RR, RRn, be)) break;
         VCK(cudaMemcpyAsync(dbe, be, sizeof(be), cudaMemcpyHostToDevice, st));
         k_bcg_dir<<<vg, 256, 0, st>>>(P, R, dbe, n); h->n_launch++;
         memcpy(RR, RRn, sizeof(RR));
     }
-    *iters = it;
+    *iters = steps > 0 ? it : 0;   // 0: no block step was possible
     VCK(cudaMemsetAsync(z, 0, sizeof(double) * n, st));
     for (int j = 0; j < 4; ++j) {
         k_axpy_to64<float><<<kNumPart, 256, 0, st>>>(z, X + (size_t)j * n, rnorm, n);
