@@ -1504,18 +1504,21 @@ static bool solve4(const double* A_in, const double* B_in, double* X) {
     return true;
 }
 
-// the same with A + delta I, delta = 1e-12 max |A_ii|, when A is singular:
-// a block column that is zero (a parameter group with no right-hand side)
-// or has become dependent (the block Krylov space of a rank-deficient S is
-// exhausted) then gets a zero row in the solution instead of a breakdown
+// the same, where a block column is exactly zero (a parameter group with no
+// right-hand side, e.g. same-spin pairing with one electron per spin): its
+// row and column of A and its row of B vanish, so it gets a unit diagonal
+// and a zero row in X.  Any other singular A is a breakdown (false).
 static bool solve4_reg(const double* A, const double* B, double* X) {
     if (solve4(A, B, X)) return true;
-    double d = 0.0, Ar[16];
-    for (int i = 0; i < 4; ++i) d = std::max(d, std::fabs(A[5 * i]));
-    if (!(d > 0.0)) return false;
+    double Ar[16];
     memcpy(Ar, A, sizeof(Ar));
-    for (int i = 0; i < 4; ++i) Ar[5 * i] += 1e-12 * d;
-    return solve4(Ar, B, X);
+    bool any = false;
+    for (int i = 0; i < 4; ++i) {
+        bool zero = true;
+        for (int j = 0; j < 4; ++j) zero = zero && A[4 * i + j] == 0.0 && A[4 * j + i] == 0.0 && B[4 * i + j] == 0.0;
+        if (zero) { Ar[5 * i] = 1.0; any = true; }
+    }
+    return any && solve4(Ar, B, X);
 }
 
 static int gram4(vmc_ctx* h, const float* U, const float* V, double* out, cudaStream_t st) {
