@@ -508,3 +508,35 @@ def test_bf16_product_over_several_sample_chunks():
     out = V.sr_apply_S(h, torch.from_numpy(v).cuda(), wl.shift, V.VMC_STORE_BF16).cpu().numpy()
     assert rel(out, ref) <= 2e-5
     h.close()
+
+
+def test_abinitio_eigenstate_closed_form_at_24_orbitals():
+    """The CUDA local energy at 24 orbitals, 12 + 12 electrons, against a
+    closed form instead of the oracle: H = Khat^2 / 2 - Jhat / 2 (one
+    Cholesky vector K, J = K^2) and Psi the determinants of the 12 lowest
+    eigenvectors of K (C = 1) is an eigenstate, so every configuration has
+    E_L = kappa^2 / 2 - sum lambda_k^2, kappa = 2 sum lambda_k (singles and
+    doubles both contribute)."""
+    n, M = 24, 48
+    wl = inputs.abinitio("b", n, 12, 12, n_chol=1, seed=79, n_walkers=256, samples_per_walker=4)
+    A = np.random.default_rng(9).standard_normal((n, n))
+    K = 0.1 * (A + A.T)
+    wl.h = np.zeros((n, n))
+    wl.chol = K[None].copy()
+    wl.C = np.ones_like(wl.C)
+    lam, phi = np.linalg.eigh(K)
+    F = phi[:, :12] @ phi[:, :12].T
+    f = np.zeros(M * (M - 1) // 2)
+    for i in range(n):
+        for j in range(n):
+            p, q = i, n + j
+            f[p * M - p * (p + 1) // 2 + (q - p - 1)] = F[i, j]
+    wl.f = f
+    E0 = 0.5 * (2 * lam[:12].sum()) ** 2 - lam[:12] @ lam[:12]
+    h = V.vmc_create(wl, walker_precision=V.VMC_FP64, keep_fp64_store=True, keep_lowp_store=False)
+    V.vmc_set_params(h, wl.C, wl.f)
+    cfgs = inputs.draw_configs(np.random.default_rng(12), wl.n_samples, n, 12, 12)
+    V.vmc_measure(h, cfgs)
+    _, E, _, _ = V.vmc_get_samples(h, V.VMC_STORE_FP64)
+    assert np.abs(E - E0).max() <= 1e-9 * abs(E0)
+    h.close()

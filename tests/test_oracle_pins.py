@@ -272,6 +272,69 @@ def test_hamiltonian_elements_and_energy_identity(kind):
     assert lhs == pytest.approx(rhs, rel=1e-10, abs=1e-12)
 
 
+def _closed_shell_pairing(M, phi_occ):
+    """f_{i up, j dn} = sum_k phi_k(i) phi_k(j): with C = 1, Psi is the
+    product of the up and down Slater determinants of the orbitals phi_k."""
+    ns = M // 2
+    F = phi_occ @ phi_occ.T
+    f = np.zeros(M * (M - 1) // 2)
+    for i in range(ns):
+        for j in range(ns):
+            p, q = i, ns + j
+            f[p * M - p * (p + 1) // 2 + (q - p - 1)] = F[i, j]
+    return f
+
+
+def test_abinitio_eigenstates_at_24_orbitals():
+    """Closed forms for the ab initio local energy at the full 24-orbital,
+    12 + 12 electron size (every single and double excitation enumerated):
+    (a) one-body H (no Cholesky vectors), Psi = determinants of the 12 lowest
+        eigenvectors of h: E_L = 2 (sum of those eigenvalues) on every sample;
+    (b) H = 1/2 sum (pq|rs) a+ a+ a a with one Cholesky vector K (so H =
+        Khat^2 / 2 - Jhat / 2, J = K^2), Psi = determinants of the 12 lowest
+        eigenvectors of K: an eigenstate, E_L = kappa^2 / 2 - sum lambda_k^2
+        with kappa = 2 sum lambda_k, on every sample (this exercises the
+        double excitations);
+    (c) diagonal h and a diagonal Cholesky vector d: H is diagonal and E_L(n)
+        = sum_P h_pp n_P + (sum_P d_p n_P)^2 / 2 - sum_P d_p^2 n_P / 2 for any
+        Psi."""
+    n, M = 24, 48
+    wl = inputs.abinitio("a", n, 12, 12, n_chol=1, seed=77, n_walkers=3)
+    wl.C = np.ones_like(wl.C)
+    wl.chol = np.zeros((1, n, n))
+    eps, phi = np.linalg.eigh(wl.h)
+    wl.f = _closed_shell_pairing(M, phi[:, :12])
+    P = oracle.Problem(wl)
+    for o in wl.init_occ:
+        assert P.local_energy(o) == pytest.approx(2 * eps[:12].sum(), rel=1e-12, abs=1e-12)
+
+    wl = inputs.abinitio("b", n, 12, 12, n_chol=1, seed=79, n_walkers=3)
+    A = np.random.default_rng(9).standard_normal((n, n))
+    K = 0.1 * (A + A.T)
+    wl.h = np.zeros((n, n))
+    wl.chol = K[None].copy()
+    wl.C = np.ones_like(wl.C)
+    lam, phi = np.linalg.eigh(K)
+    wl.f = _closed_shell_pairing(M, phi[:, :12])
+    P = oracle.Problem(wl)
+    kappa = 2 * lam[:12].sum()
+    for o in wl.init_occ:
+        assert P.local_energy(o) == pytest.approx(0.5 * kappa ** 2 - lam[:12] @ lam[:12], rel=1e-12)
+
+    wl = inputs.abinitio("c", n, 12, 12, n_chol=1, seed=78, n_walkers=3)
+    d = np.random.default_rng(5).standard_normal(n)
+    hd = np.random.default_rng(6).standard_normal(n)
+    wl.h = np.diag(hd)
+    wl.chol = np.diag(d)[None]
+    P = oracle.Problem(wl)
+    dd, hh = np.concatenate([d, d]), np.concatenate([hd, hd])
+    for o in wl.init_occ:
+        nocc = np.zeros(M)
+        nocc[o] = 1.0
+        ref = hh @ nocc + 0.5 * (dd @ nocc) ** 2 - 0.5 * (dd ** 2) @ nocc
+        assert P.local_energy(o) == pytest.approx(ref, rel=1e-12, abs=1e-12)
+
+
 @pytest.mark.parametrize("no,nu,nd", [(3, 1, 1), (4, 2, 2), (5, 2, 2), (5, 3, 1)])
 def test_abinitio_local_energy_restricted_strings(no, nu, nd):
     """The local energy used at scale applies only the operator strings that
