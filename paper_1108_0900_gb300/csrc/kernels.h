@@ -246,9 +246,7 @@ struct SortedArgs {
     const float* invC;
     const double* obv_part; // [n_obv_part][K] partial dots Obar . V (centering)
     int n_obv_part;
-    void* Tv;               // centered per-sample dots O_s . V - Obar . V: FP16 [n_s] for
-                            // one vector (half the footprint, so the scatter's random
-                            // lookups stay in L1), FP32 [n_s][K] otherwise
+    float* Tv;              // [n_s][K] centered per-sample dots O_s . V - Obar . V
     const uint32_t* T;      // parameter-major (s_local << 16) | bf16
     const uint32_t* base;   // [nchunk][npf + 1] run offsets
     int nchunk;

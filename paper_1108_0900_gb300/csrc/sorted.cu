@@ -379,15 +379,10 @@ __global__ void __launch_bounds__(gather_threads(K)) k_gather_G(SortedArgs a) {
 #pragma unroll
         for (int kk = 0; kk < K; ++kk) t[kk] = warp_sum(t[kk] + w[kk]);
         if (lane == 0) {
-            if constexpr (K == 1) {
-                const __half hv = __float2half_rn(t[0] - obv[0]);
-                ((__half*)a.Tv)[s] = hv;
-                const double c = (double)__half2float(hv);   // the curvature of the rounded product
-                tt += c * c;
-            } else {
 #pragma unroll
-                for (int kk = 0; kk < K; ++kk) ((float*)a.Tv)[s * K + kk] = t[kk] - obv[kk];
-            }
+            for (int kk = 0; kk < K; ++kk) a.Tv[s * K + kk] = t[kk] - obv[kk];
+            const double c = (double)(t[0] - obv[0]);
+            tt += c * c;
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) g[u] = gn[u];
@@ -404,20 +399,13 @@ __global__ void __launch_bounds__(gather_threads(K)) k_gather_G(SortedArgs a) {
     }
 }
 
-// t_s for vector kk (FP16 storage for one vector)
-template <int K>
-__device__ __forceinline__ float load_t(const void* Tv, int64_t s, int kk) {
-    if constexpr (K == 1) return __half2float(__ushort_as_half(__ldg((const unsigned short*)Tv + s)));
-    else return __ldg((const float*)Tv + s * K + kk);
-}
-
 // one T entry of a parameter's run: acc += W * t_s
 template <int K>
-__device__ __forceinline__ void scatter_entry(const void* __restrict__ Tv, int64_t s0, uint32_t v, float (&acc)[K]) {
+__device__ __forceinline__ void scatter_entry(const float* __restrict__ Tv, int64_t s0, uint32_t v, float (&acc)[K]) {
     const float wv = __uint_as_float(v << 16);
-    const int64_t s = s0 + (v >> 16);
+    const int64_t t0 = (s0 + (v >> 16)) * K;
 #pragma unroll
-    for (int kk = 0; kk < K; ++kk) acc[kk] += wv * load_t<K>(Tv, s, kk);
+    for (int kk = 0; kk < K; ++kk) acc[kk] += wv * __ldg(Tv + t0 + kk);
 }
 
 // scatter: raw[pq][kk] = sum over samples containing pq of W t_s for the warp's
@@ -486,7 +474,7 @@ __device__ __forceinline__ void scatter_C_item(const SortedArgs& a, uint2 item, 
         const int ls = in ? (int)(v & 31u) : 32 + lane;        // past the end: a segment of its own
         float t[K];
 #pragma unroll
-        for (int kk = 0; kk < K; ++kk) t[kk] = in ? load_t<K>(a.Tv, (int64_t)(v >> 5), kk) : 0.f;
+        for (int kk = 0; kk < K; ++kk) t[kk] = in ? __ldg(a.Tv + (int64_t)(v >> 5) * K + kk) : 0.f;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int lo_ls = __shfl_up_sync(0xffffffffu, ls, o);
