@@ -5,13 +5,17 @@ Every rank holds its own walkers and O rows; only sums cross ranks:
 
 * per SR step, one sum all-reduce of (sum O, sum E_L O, sum E_L, n_s):
   2 n_v + 2 numbers;
-* per S product, one sum all-reduce of sum_s (O_s . v) O_s: n_v numbers.
+* per S product, one sum all-reduce of sum_s (O_s . v) O_s: n_v numbers;
+* per linear-method product (Sec. II.B, Eq. 10: a sample mean like Eq. 7),
+  one sum all-reduce of n_r (H x)_r, n_r (S x)_r and n_r: 2 n_v + 3 numbers.
 
 Everything else (the CG vectors and scalars, x_0) is then the same on every
 rank.  ``local`` supplies the rank-local sums:
 
 * ``local.moments() -> (sumO, sumEO, sumE, n)`` (float64 tensors [n_v], floats)
 * ``local.product(v) -> sum_s (O_s . v) O_s`` (float64 tensor [n_v])
+* ``local.lm_product(x) -> ((H x)_r, (S x)_r, n_r)``, the rank's own sample
+  means (float64 tensors [n_v + 1]) and its sample count
 
 ``LibraryLocal`` provides them from a library handle (``sr_local_moments`` /
 ``sr_local_product``).  ``reduce`` sums a tensor over the ranks in place;
@@ -82,6 +86,18 @@ def sr_step(local, tau, shift, tol, max_iter, reduce=_dist_sum):
     return dict(y=y, x0=x0, E_mean=E, n=N, g=g, Obar=Obar, iterations=it, true_rel_residual=res)
 
 
+def lm_apply(local, x, reduce=_dist_sum):
+    """Linear-method products (H x, S x) over every rank's samples: the
+    rank means weighted by the ranks' sample counts, from one all-reduce."""
+    Hx, Sx, n = local.lm_product(x)
+    nv1 = Hx.numel()
+    buf = torch.cat([Hx.reshape(-1) * n, Sx.reshape(-1) * n,
+                     torch.tensor([float(n)], dtype=torch.float64, device=Hx.device)])
+    reduce(buf)
+    N = float(buf[2 * nv1])
+    return buf[:nv1] / N, buf[nv1:2 * nv1] / N
+
+
 class LibraryLocal:
     """Rank-local sums from a library handle over one O store."""
 
@@ -96,3 +112,7 @@ class LibraryLocal:
 
     def product(self, v):
         return self.V.sr_local_product(self.h, v, self.store)
+
+    def lm_product(self, x):
+        Hx, Sx = self.V.lm_apply(self.h, x, self.store)
+        return Hx, Sx, self.V.vmc_num_samples(self.h)

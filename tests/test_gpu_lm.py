@@ -200,3 +200,31 @@ def test_lm_optimize_lowers_the_energy():
     e1, err1 = acc[-1]["energy_after"][0], acc[-1]["energy_after"][2]
     assert e1 < e0 - 5 * max(err0, err1)
     h.close()
+
+
+def test_lm_rank_local_products_add_up():
+    """Two handles holding 1/3 and 2/3 of the samples: their sample-count
+    weighted products (what the sharded solve all-reduces) equal the product
+    of one handle holding all samples."""
+    from paper_1108_0900_gb300 import shard
+    wl = CASES["abinitio10_odd_spin"]()
+    P, smp, h = _setup(wl)
+    cut = len(smp) // 3
+    parts = []
+    for sl in (slice(0, cut), slice(cut, None)):
+        hp = V.vmc_create(wl, walker_precision=V.VMC_FP64, keep_fp64_store=True, keep_lowp_store=False)
+        V.vmc_set_params(hp, wl.C, wl.f)
+        V.vmc_measure(hp, np.ascontiguousarray(smp[sl]))
+        parts.append(hp)
+    x = torch.from_numpy(np.random.default_rng(4).standard_normal(wl.n_params + 1)).cuda()
+    locs = [shard.LibraryLocal(hp, V.VMC_STORE_FP64) for hp in parts]
+    res = [loc.lm_product(x) for loc in locs]
+    N = sum(n for _, _, n in res)
+    Hx = sum(H * n for H, _, n in res) / N
+    Sx = sum(S * n for _, S, n in res) / N
+    H_all, S_all = V.lm_apply(h, x, V.VMC_STORE_FP64)
+    assert rel(Hx.cpu().numpy(), H_all.cpu().numpy()) <= 1e-12
+    assert rel(Sx.cpu().numpy(), S_all.cpu().numpy()) <= 1e-12
+    for hp in parts:
+        hp.close()
+    h.close()

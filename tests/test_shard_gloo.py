@@ -77,3 +77,53 @@ def test_two_cpu_ranks_reproduce_the_single_process_solve(tmp_path):
         assert x0 == pytest.approx(x0_ref, rel=1e-10)
     # every rank holds the same solution
     assert np.array_equal(np.load(tmp_path / "y0.npy"), np.load(tmp_path / "y1.npy"))
+
+
+class OracleLMLocal:
+    """Rank-local linear-method sample means from the oracle (Eq. 10 over the
+    rank's own samples)."""
+
+    def __init__(self, P, smp, factors):
+        self.P, self.smp, self.factors = P, smp, factors
+
+    def lm_product(self, x):
+        Hx, Sx = self.P.lm_apply(self.smp, self.factors, x.numpy())
+        return torch.from_numpy(Hx), torch.from_numpy(Sx), len(self.smp)
+
+
+def _lm_problem():
+    wl = inputs.hubbard("shl", 3, 2, 2, 2, "pair", seed=73, n_walkers=10)
+    P = oracle.Problem(wl)
+    occ = wl.init_occ.copy()
+    step = np.zeros(wl.n_walkers, np.uint64)
+    smp, _, _ = P.sample(occ, step, 74, 5, 3)
+    x = np.random.default_rng(75).standard_normal(wl.n_params + 1)
+    return wl, P, smp, x
+
+
+def _lm_rank(rank, world, port, out):
+    import torch.distributed as dist
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        wl, P, smp, x = _lm_problem()
+        idx, cut = np.arange(len(smp)), len(smp) // 3
+        mine = idx < cut if rank == 0 else idx >= cut      # uneven shares: 1/3 and 2/3
+        Hx, Sx = shard.lm_apply(OracleLMLocal(P, smp[mine], oracle.lm_factors(wl)), torch.from_numpy(x))
+        np.save(os.path.join(out, f"lmH{rank}.npy"), Hx.numpy())
+        np.save(os.path.join(out, f"lmS{rank}.npy"), Sx.numpy())
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_cpu_ranks_reproduce_the_linear_method_product(tmp_path):
+    """Ranks holding 1/3 and 2/3 of the samples, one all-reduce: the Eq. 10
+    products equal the single-process ones over all samples."""
+    world = 2
+    mp.spawn(_lm_rank, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
+    wl, P, smp, x = _lm_problem()
+    H_ref, S_ref = P.lm_apply(smp, oracle.lm_factors(wl), x)
+    for r in range(world):
+        Hx = np.load(tmp_path / f"lmH{r}.npy")
+        Sx = np.load(tmp_path / f"lmS{r}.npy")
+        assert np.linalg.norm(Hx - H_ref) <= 1e-12 * np.linalg.norm(H_ref)
+        assert np.linalg.norm(Sx - S_ref) <= 1e-12 * np.linalg.norm(S_ref)
