@@ -61,21 +61,6 @@ __device__ R corr_ratio_dir(const DevProblem& pb, const uint32_t* cidx, int p, i
     return prod;
 }
 
-template <typename R>
-__device__ R corr_ratio_move(const DevProblem& pb, const uint32_t* cidx, int p, int q) {
-    const int ns = pb.ns;
-    const int sf = p >= ns ? 2 : 1;
-    const int sp = p >= ns ? p - ns : p, sq = q >= ns ? q - ns : q;
-    const int total = (pb.site_cptr[sp + 1] - pb.site_cptr[sp]) + (pb.site_cptr[sq + 1] - pb.site_cptr[sq]);
-    R prod = R(1);
-    for (int e = 0; e < total; ++e) {
-        int c;
-        const int newi = corr_entry(pb, cidx, sp, sq, sf, e, &c);
-        if (c >= 0) prod *= load_C<R>(pb, pb.corr_off[c] + newi) / load_C<R>(pb, pb.corr_off[c] + cidx[c]);
-    }
-    return prod;
-}
-
 // Adjoint of the correlator ratio: coef (1/C at the new state) and
 // -coef (1/C at the old state) for every correlator the move changes.  The
 // old-state parts of all moves of a sample share one parameter per
@@ -159,8 +144,9 @@ __device__ void warp_gemm(int m, int n, int K, const R* A, int sai, int sak, con
 
 size_t lm_warp_bytes(int N, int M, int ns, int n_mu, int ncorr, int elem) {
     const size_t XS = N + 1, GS = N + 1, E = M - N;
+    const size_t nmove = (size_t)(N / 2 + 1) * (size_t)(M - N + 2);   // >= nu eu + nd ed
     const size_t nr = 2 * N * XS + 3 * E * GS + (size_t)ns * ns + (size_t)((n_mu + 1) / 2 * 2) +
-                      (size_t)((ncorr + 1) / 2 * 2);
+                      (size_t)((ncorr + 1) / 2 * 2) + (nmove + 1) / 2 * 2;
     const size_t b = nr * elem + (size_t)((ncorr + 3) / 4 * 4) * 4 + 64 + 128;
     return (b + 15) / 16 * 16;
 }
@@ -200,7 +186,9 @@ __global__ void __launch_bounds__(256) k_lm_apply(LmArgs a) {
     R* Y = D + E * GS;                                      // y summed over spins, later z
     R* w = Y + nn;
     R* cold = w + (n_mu + 1) / 2 * 2;                       // old-state adjoint sums per correlator
-    uint32_t* cidx = (uint32_t*)(cold + (ncorr + 1) / 2 * 2);
+    R* rcm = cold + (ncorr + 1) / 2 * 2;                    // correlator ratio of every move
+    const int nmove = (N / 2 + 1) * (M - N + 2);
+    uint32_t* cidx = (uint32_t*)(rcm + (nmove + 1) / 2 * 2);
     uint8_t* occ = (uint8_t*)(cidx + (ncorr + 3) / 4 * 4);
     uint8_t* emp = occ + 64;
     const R* Xt = (const R*)a.Xt;
@@ -279,6 +267,7 @@ __global__ void __launch_bounds__(256) k_lm_apply(LmArgs a) {
             const int p = occ[ia], v = emp[ie];
             R dl;
             const R rc = corr_ratio_dir<R>(pb, cidx, p, v, xc, &dl);
+            rcm[t] = rc;
             const R y = rc * (G[ie * GS + ia] * (xt + dl) + D[ie * GS + ia]);
             atomicAdd(&Y[(p % ns) * ns + (v % ns)], y);
         }
@@ -312,7 +301,7 @@ __global__ void __launch_bounds__(256) k_lm_apply(LmArgs a) {
             const int p = occ[ia], v = emp[ie];
             const R z = Y[(v % ns) * ns + (p % ns)];   // z_{v p}: the move p -> v
             if (z == R(0)) continue;
-            const R rc = corr_ratio_move<R>(pb, cidx, p, v);
+            const R rc = rcm[t];
             const R g = G[ie * GS + ia];
             W += z * rc * g;
             Pm[ie * GS + ia] = z * rc;
