@@ -65,3 +65,21 @@ def test_create_rejects_invalid_problems():
     badbond.bonds = np.array([[0, 9]], np.int32)
     badbond.bond_t = np.ones(1)
     assert _create_rc(badbond) == -1
+
+
+def test_null_handles_are_rejected_before_any_device_work(L):
+    """Every entry point that takes a handle checks its arguments first:
+    a NULL handle is INVALID_ARG, with no CUDA call made (so this runs
+    without a GPU)."""
+    import ctypes as ct
+    vp = ct.c_void_p
+    info = ct.create_string_buffer(256)
+    calls = {
+        "lm_apply": (vp(), vp(), vp(), vp(), 0, vp()),
+        "lm_solve": (vp(), ct.c_double(1.0), ct.c_double(1e-2), ct.c_double(1e-6), 10, 8, vp(), info, 0, vp()),
+        "lm_update": (vp(), vp(), ct.c_double(1.0), vp()),
+        "sr_update": (vp(), vp(), ct.c_double(0.1), 0, vp(), vp()),
+        "sr_local_product": (vp(), vp(), vp(), 0, vp()),
+    }
+    for name, args in calls.items():
+        assert getattr(L, name)(*args) == -1, name
