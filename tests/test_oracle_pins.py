@@ -247,7 +247,7 @@ def _bits(occ):
     return sum(1 << int(o) for o in occ)
 
 
-@pytest.mark.parametrize("kind", ["hubbard2x2", "hubbard3x2", "abinitio3_11", "abinitio3_22"])
+@pytest.mark.parametrize("kind", ["hubbard2x2", "hubbard3x2", "abinitio3_11", "abinitio3_22", "abinitio4_22"])
 def test_hamiltonian_elements_and_energy_identity(kind):
     if kind == "hubbard2x2":
         wl = inputs.hubbard("t", 2, 2, 2, 2, "2x2", seed=3, n_walkers=1)
@@ -255,8 +255,10 @@ def test_hamiltonian_elements_and_energy_identity(kind):
         wl = inputs.hubbard("t", 3, 2, 1, 1, "pair", seed=3, n_walkers=1)
     elif kind == "abinitio3_11":
         wl = inputs.abinitio("t", 3, 1, 1, n_chol=4, seed=4, n_walkers=1)
-    else:
+    elif kind == "abinitio3_22":
         wl = inputs.abinitio("t", 3, 2, 2, n_chol=4, seed=5, n_walkers=1)
+    else:                                   # the 4-orbital toy: 36 configurations, 256-dim Fock space
+        wl = inputs.abinitio("t", 4, 2, 2, n_chol=5, seed=6, n_walkers=1)
     P = oracle.Problem(wl)
     H = _jw_hamiltonian(wl)
     occ_all, w = P.enumerate()
