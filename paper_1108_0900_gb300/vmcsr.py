@@ -244,6 +244,25 @@ def vmc_get_walkers(h: Handle, stream=None):
     return occ, step
 
 
+def save_state(h: Handle, path: str, **extra):
+    """Checkpoint of an optimisation: the parameters (C, f), every walker's
+    configuration and step counter (the counter of its Philox stream), and
+    any extra values (e.g. the iteration and the next sampling seed).  With
+    the same seed, vmc_sample after load_state reproduces the next batch bit
+    for bit.  `path` is an .npz file."""
+    C, f = vmc_get_params(h)
+    occ, step = vmc_get_walkers(h)
+    np.savez(path, C=C, f=f, occ=occ, step=step, **{k: np.asarray(v) for k, v in extra.items()})
+
+
+def load_state(h: Handle, path: str) -> dict:
+    """Restore a checkpoint written by save_state; returns its extra values."""
+    d = np.load(path)
+    vmc_set_params(h, d["C"], d["f"])
+    vmc_set_walkers(h, d["occ"], d["step"])
+    return {k: d[k] for k in d.files if k not in ("C", "f", "occ", "step")}
+
+
 def vmc_sample(h: Handle, n_burn: int, seed: int, stream=None):
     _check(lib().vmc_sample(h.h, int(n_burn), ct.c_uint64(seed), _stream(stream)), "vmc_sample")
 

@@ -245,3 +245,34 @@ def test_rank_local_sums_add_up_to_the_whole(store):
     assert res["x0"] == pytest.approx(x0_ref, rel=tol)
     for h in halves:
         h.close()
+
+
+def test_checkpoint_resume_reproduces_the_next_batch(tmp_path):
+    """save_state after an SR update, load_state into a fresh handle, and the
+    next vmc_sample with the same seed gives the same samples bit for bit
+    (configurations, correlator states, E_L, pairing block)."""
+    wl = inputs.workload("hubbard4x4_pair", n_walkers=32, samples_per_walker=4)
+
+    def fresh():
+        return V.vmc_create(wl, walker_precision=V.VMC_FP64, keep_fp64_store=True, keep_lowp_store=False)
+
+    h = fresh()
+    V.vmc_set_params(h, wl.C, wl.f)
+    V.vmc_set_walkers(h, wl.init_occ)
+    V.vmc_sample(h, 5, 11)
+    g, _ = V.sr_gradient(h, V.VMC_STORE_FP64)
+    y, _ = V.sr_cg_solve(h, g, 1e-3, 1e-8, 5000, V.VMC_CG_FP64)
+    V.sr_update(h, y, 0.02, V.VMC_STORE_FP64)
+    path = str(tmp_path / "state.npz")
+    V.save_state(h, path, next_seed=12, iteration=1)
+    V.vmc_sample(h, 0, 12)
+    a = V.vmc_get_samples(h, V.VMC_STORE_FP64)
+    h2 = fresh()
+    extra = V.load_state(h2, path)
+    assert int(extra["iteration"]) == 1
+    V.vmc_sample(h2, 0, int(extra["next_seed"]))
+    b = V.vmc_get_samples(h2, V.VMC_STORE_FP64)
+    for u, v in zip(a, b):
+        assert np.array_equal(u, v)
+    h.close()
+    h2.close()
