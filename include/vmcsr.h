@@ -150,7 +150,9 @@ int vmc_destroy(vmc_handle h);
 int vmc_num_params(vmc_handle h, int64_t* n_v, int64_t* n_corr_params);
 
 /* Set the correlator amplitudes C[n_corr_params] and pairing f[M(M-1)/2]
- * (host, FP64, layout above).  Errors: SINGULAR if some C is zero. */
+ * (host, FP64, layout above).  Waits for all work queued on the device (any
+ * stream) before it overwrites the parameters.  Errors: SINGULAR if some C is
+ * zero. */
 int vmc_set_params(vmc_handle h, const double* C, const double* f);
 
 /* Read the current parameters back (host C[n_corr_params], f[M(M-1)/2],
@@ -159,10 +161,13 @@ int vmc_get_params(vmc_handle h, double* C, double* f, void* stream);
 
 /* Set walker configurations: occ[n_walkers][N] ascending occupied spin
  * orbitals (host, uint8) with n_up orbitals below n_sites; step[n_walkers]
- * (host, may be NULL = 0) is each chain's proposal counter.  Errors:
- * INVALID_ARG for a configuration outside the sector. */
+ * (host, may be NULL = 0) is each chain's proposal counter.  Waits for all
+ * work queued on the device (any stream) before it overwrites the walkers.
+ * Errors: INVALID_ARG for a configuration outside the sector. */
 int vmc_set_walkers(vmc_handle h, const uint8_t* occ, const uint64_t* step);
-/* Read back walker configurations (ascending) and counters (host, may be NULL). */
+/* Read back walker configurations (ascending) and counters (host, may be
+ * NULL) once the work queued on `stream` is done; a sampling call queued on
+ * another stream must be waited for by the caller. */
 int vmc_get_walkers(vmc_handle h, uint8_t* occ, uint64_t* step, void* stream);
 
 /* Metropolis sampling from |Psi_n|^2 in the fixed sector (Sec. II.A, Sec. III).
@@ -215,7 +220,9 @@ int sr_gradient(vmc_handle h, double* g, double* e_stats, int store, void* strea
 /* out = (S + shift I) V for k right-hand sides (Eq. 7 with the covariance
  * term): V and out are device [k][n_v] FP64 (column j at offset j n_v),
  * 1 <= k <= 4; `store` picks the O store and arithmetic (VMC_STORE_*).
- * sr_gradient must have run since the last sampling call (it sets Obar). */
+ * sr_gradient must have run since the last sampling call (it sets Obar).
+ * Synchronizes `stream` to read the kernels' status (TIMEOUT, see
+ * vmc_set_wait_limit). */
 int sr_apply_S(vmc_handle h, const double* V, double* out, int k, double shift, int store,
                void* stream);
 
@@ -339,7 +346,10 @@ int vmc_profile_read(vmc_handle h, int store, int64_t* launches_all, int64_t* pa
  *   out  [M(M-1)/2] FP64 out: out[pq] = sum_s t_s pf_s[e] at pq(e) (FP32
  *        accumulation per CTA, FP64 across CTAs).
  * This is the pairing-block half of the Eq. 7 product without the 1/n_s and
- * the mean term.  Sizes beyond the scratch (n_sites > 64) and bad strides or
+ * the mean term.  A sample whose occupation is not a configuration of the
+ * sector (not strictly ascending, an up orbital >= n_sites, a down orbital
+ * outside n_sites .. M-1) is skipped: its t_s is NaN and it adds nothing to
+ * out; the call still returns VMC_OK.  Sizes beyond the scratch (n_sites > 64) and bad strides or
  * pointers return INVALID_ARG (vmc_last_error_detail says which).  The first
  * call on each device looks up the scratch's device address with that device
  * current (cudaGetSymbolAddress), so make that first call before any stream
@@ -350,6 +360,57 @@ int vmc_profile_read(vmc_handle h, int store, int64_t* launches_all, int64_t* pa
 int sr_pairing_product_noalloc(int64_t n_s, int n_sites, int n_up, int n_dn, const uint8_t* occ,
                                int64_t occ_stride, const float* pf, int64_t pf_stride, const float* v, float* t,
                                double* out, void* stream);
+
+/* Product paths of the BF16-store S product (no counterpart in the paper:
+ * the same Eq. 7 arithmetic organised in different passes).
+ *   VMC_PATH_SORTED  two passes over index-carrying copies built once per set
+ *                    of samples: a sample-major gather of t_s = O_s . v, then
+ *                    a parameter-major sum of t_s O_s (no atomics);
+ *   VMC_PATH_FUSED   one vector only: one pass over the sample-major copy,
+ *                    scattering t_s O_s into private shared-memory images;
+ *   VMC_PATH_STAGED  one or two vectors: a per-sample pass over the store
+ *                    itself, samples staged in shared memory by bulk copies;
+ *   VMC_PATH_GENERIC the plain per-sample pass (any number of vectors).
+ * A path that does not apply to a problem falls back to the next applicable
+ * one in this order.  VMC_PATH_STAGED / GENERIC also select the pass of the
+ * FP32 store with FP32 accumulation. */
+#define VMC_PATH_AUTO 0
+#define VMC_PATH_SORTED 1
+#define VMC_PATH_FUSED 2
+#define VMC_PATH_STAGED 3
+#define VMC_PATH_GENERIC 4
+int vmc_set_product_path(vmc_handle h, int path);
+
+typedef struct {
+    int path;        /* fastest one-vector path (VMC_PATH_*), used under AUTO     */
+    int path4;       /* fastest four-vector path, used under AUTO for 2 and 4     */
+    double ms[5];    /* mean time of one one-vector product per path, < 0 if n/a  */
+    double ms4[5];   /* the same for four vectors                                 */
+} vmc_tune_info;
+
+/* Autotuner: times `reps` BF16 products of one and of four vectors on every
+ * applicable path over the handle's current samples (CUDA events on
+ * `stream`, after one warm-up product that also builds the path's copies)
+ * and makes the fastest the handle's AUTO choice.  info (host, may be NULL)
+ * receives the timings.  Errors: STATE (no samples or no BF16 store). */
+int sr_autotune(vmc_handle h, int reps, vmc_tune_info* info, void* stream);
+/* Set the AUTO choice directly (a choice sr_autotune made earlier for the
+ * same workload, e.g. read back from a cache): one-vector products on
+ * `path`, two- and four-vector products on `path4` (VMC_PATH_SORTED ..
+ * VMC_PATH_GENERIC). */
+int vmc_set_auto_paths(vmc_handle h, int path, int path4);
+
+/* Failure detection (no counterpart in the paper).  The streaming products
+ * stage samples in shared memory with bulk copies and wait for each copy a
+ * bounded number of times (mbarrier try-wait); a wait that runs out makes
+ * the kernel drain its own copies and stop, and the call returns
+ * VMC_ERR_TIMEOUT instead of hanging (sr_apply_S reads the kernels' status
+ * word before it returns; sr_cg_solve at its next convergence check).  This
+ * sets the number of tries of those waits (default 4,194,304); the drain
+ * before a kernel exits always uses the default.  A caller that must bound
+ * the time a product can wait on memory lowers it; 0 makes every wait give
+ * up at once (every staged product then returns VMC_ERR_TIMEOUT). */
+int vmc_set_wait_limit(vmc_handle h, uint32_t tries);
 
 const char* vmc_error_string(int code);
 /* Text of the last failing CUDA call or internal check on the calling

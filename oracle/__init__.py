@@ -82,6 +82,7 @@ def lib():
             L.orc_dense_S.argtypes = [i64, i64, vp, vp]
             L.orc_apply_S.argtypes = [i64, i64, vp, vp, vp, dbl, vp]
             L.orc_cg.argtypes = [i64, i64, vp, vp, dbl, dbl, i32, vp, vp, vp]
+            L.orc_apply_S_compact.argtypes = [vp, i64, vp, vp, i32, vp, vp, i32, vp, dbl, vp, vp]
             L.orc_cg.restype = i32
             L.orc_sr_update.argtypes = [i64, vp, vp, dbl, dbl, vp, vp]
             L.orc_sr_update.restype = dbl
@@ -299,6 +300,25 @@ def apply_S(O, v, eps, Obar=None):
     lib().orc_apply_S(O.shape[0], O.shape[1], _ptr(O), _ptr(np.ascontiguousarray(Obar)), _ptr(v),
                       float(eps), _ptr(out))
     return out
+
+
+def apply_S_compact(P: "Problem", occ, cstate, pairs, pf, v, eps):
+    """Eq. 7 from compact rows (see orc_apply_S_compact): occ [n_s, N] uint8,
+    cstate [n_s, n_corr] correlator states, pairs [n_pair, 2] positions
+    (a, b) of each stored pairing value, pf [n_s, n_pair] the values, v [nv]
+    or [k, nv].  Returns (out with the shape of v, Obar)."""
+    occ = np.ascontiguousarray(occ, np.uint8)
+    cs = np.ascontiguousarray(cstate, np.int64).reshape(occ.shape[0], -1)
+    pairs = np.ascontiguousarray(pairs, np.int32)
+    pf = np.ascontiguousarray(pf, np.float64)
+    v = np.ascontiguousarray(v, np.float64)
+    k = 1 if v.ndim == 1 else v.shape[0]
+    nv = v.shape[-1]
+    out = np.zeros_like(v)
+    Obar = np.zeros(nv)
+    lib().orc_apply_S_compact(P.ref, occ.shape[0], _ptr(occ), _ptr(cs), len(pairs), _ptr(pairs), _ptr(pf), k,
+                              _ptr(v), float(eps), _ptr(out), _ptr(Obar))
+    return out, Obar
 
 
 def sr_update(alpha, y, tau, E_mean, Obar):

@@ -790,6 +790,62 @@ void orc_apply_S(int64_t n_s, int64_t nv, const double* O, const double* Obar, c
     for (int64_t k = 0; k < nv; ++k) out[k] = out[k] / (double)n_s - Obar[k] * ob_v + eps * v[k];
 }
 
+/* Eq. 7 evaluated from compact per-sample rows, with v given for k vectors.
+ * Sample s holds its ascending occupation occ[s][N], its correlator states
+ * cs[s][n_corr] and the values of its n_pair pairing derivatives
+ * pf[s][n_pair]; value e is O of f_pq with p = occ[a_e], q = occ[b_e],
+ * (a_e, b_e) = (pairs[2e], pairs[2e+1]), a_e < b_e.  A correlator factor
+ * C_c[n_c] contributes O = 1/C at parameter off_c + state (Eq. 3 for one
+ * factor; correlators of one class add up on their shared amplitude); every
+ * other entry of O_s is zero.  Obar_out[nv] receives the mean of these rows
+ * (weight 1/n_s) and, for each of the k columns v_j = v[j nv ..],
+ *   out_j = (1/n_s) sum_s O_s (O_s . v_j) - Obar (Obar . v_j) + eps v_j,
+ * all in FP64, summed over the samples in order. */
+void orc_apply_S_compact(const orc_problem* P, int64_t n_s, const uint8_t* occ, const int64_t* cs, int n_pair,
+                         const int32_t* pairs, const double* pf, int k, const double* v, double eps,
+                         double* out, double* Obar_out)
+{
+    const int M = n_orb_M(P), N = P->n_up + P->n_dn;
+    const int64_t nv = orc_n_params(P), ncp = orc_n_corr_params(P);
+    int64_t* off = (int64_t*)malloc(sizeof(int64_t) * ((size_t)P->n_corr + 1));
+    corr_offsets(P, off);
+    int64_t* idx = (int64_t*)malloc(sizeof(int64_t) * ((size_t)P->n_corr + (size_t)n_pair + 1));
+    double* val = (double*)malloc(sizeof(double) * ((size_t)P->n_corr + (size_t)n_pair + 1));
+    double* t = (double*)malloc(sizeof(double) * (size_t)(k > 0 ? k : 1));
+    for (int64_t i = 0; i < nv; ++i) Obar_out[i] = 0.0;
+    for (int64_t i = 0; i < nv * k; ++i) out[i] = 0.0;
+    for (int64_t s = 0; s < n_s; ++s) {
+        /* the nonzero entries of O_s: (index, value) pairs */
+        const uint8_t* o = occ + s * N;
+        int n = 0;
+        for (int c = 0; c < P->n_corr; ++c) {
+            idx[n] = off[c] + cs[s * P->n_corr + c];
+            val[n] = 1.0 / P->C[idx[n]];
+            ++n;
+        }
+        for (int e = 0; e < n_pair; ++e) {
+            idx[n] = ncp + pf_index(M, o[pairs[2 * e]], o[pairs[2 * e + 1]]);
+            val[n] = pf[s * n_pair + e];
+            ++n;
+        }
+        for (int i = 0; i < n; ++i) Obar_out[idx[i]] += val[i];
+        for (int j = 0; j < k; ++j) {
+            t[j] = 0.0;
+            for (int i = 0; i < n; ++i) t[j] += val[i] * v[j * nv + idx[i]];
+        }
+        for (int j = 0; j < k; ++j)
+            for (int i = 0; i < n; ++i) out[j * nv + idx[i]] += val[i] * t[j];
+    }
+    for (int64_t i = 0; i < nv; ++i) Obar_out[i] /= (double)n_s;
+    for (int j = 0; j < k; ++j) {
+        double ob_v = 0.0;
+        for (int64_t i = 0; i < nv; ++i) ob_v += Obar_out[i] * v[j * nv + i];
+        for (int64_t i = 0; i < nv; ++i)
+            out[j * nv + i] = out[j * nv + i] / (double)n_s - Obar_out[i] * ob_v + eps * v[j * nv + i];
+    }
+    free(off); free(idx); free(val); free(t);
+}
+
 static double dot(int64_t n, const double* a, const double* b)
 {
     double s = 0.0;

@@ -51,6 +51,12 @@ void orc_gradient(int64_t n_s, int64_t nv, const double* O, const double* E, dou
 void orc_dense_S(int64_t n_s, int64_t nv, const double* O, double* S);
 void orc_apply_S(int64_t n_s, int64_t nv, const double* O, const double* Obar, const double* v,
                  double eps, double* out);
+/* Eq. 7 from compact rows (ascending occupation, correlator states, the
+ * values of the nonzero pairing derivatives with their position pairs), for
+ * k vectors [k][nv]; Obar_out[nv] = mean of the rows.  See oracle.c. */
+void orc_apply_S_compact(const orc_problem* P, int64_t n_s, const uint8_t* occ, const int64_t* cs, int n_pair,
+                         const int32_t* pairs, const double* pf, int k, const double* v, double eps,
+                         double* out, double* Obar_out);
 int orc_cg(int64_t n_s, int64_t nv, const double* O, const double* g, double eps, double tol,
            int max_iter, double* x, int* iters, double* true_rel_res);
 /* SR parameter update (Sec. II.A, after Eq. 2): x = -tau y, x_0 = 1 - tau E_mean - Obar . x,

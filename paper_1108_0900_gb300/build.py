@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libvmcsr.so")
-SOURCES = ["api.cu", "sampler.cu", "sr.cu", "stream.cu", "sorted.cu", "noalloc.cu", "lm.cu", "bcg.cu"]
+SOURCES = ["api.cu", "sampler.cu", "sr.cu", "stream.cu", "sorted.cu", "noalloc.cu", "lm.cu", "bcg.cu", "fused.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-static-global-template-stub=false",

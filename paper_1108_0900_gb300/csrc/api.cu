@@ -51,6 +51,14 @@ struct vmc_ctx {
     bool use_sorted = true;      // sorted two-pass product for the BF16 store
     int last_gather_grid = 0;    // CTAs (tt partials) of the last sorted gather
     bool sorted_ok = false;      // G / T built for the current samples
+    bool use_fused = true;       // fused single-pass product over G (BF16 store, one vector)
+    int path = VMC_PATH_AUTO;    // product path set by the caller (VMC_PATH_*)
+    int auto_path = VMC_PATH_SORTED;   // one-vector BF16 path used under AUTO (sr_autotune may change it)
+    int auto_path4 = VMC_PATH_SORTED;  // two- and four-vector BF16 path used under AUTO
+    bool g_ok = false;           // G built for the current samples
+    bool corr_ok = false;        // correlator runs built for the current samples
+    uint32_t wait_limit = 1u << 22;  // tries of each bounded wait on a staged sample
+    int last_fused_grid = 0;     // CTAs (tt partials) of the last fused pass
     int sort_nblk = 0, sort_nchunk = 0;
     size_t t_chunk = 0;          // T entries reserved per 65,536-sample chunk
     bool obar_ok[3] = {false, false, false};  // per store: FP64, FP32, BF16
@@ -81,6 +89,9 @@ struct vmc_ctx {
     double *d_C64 = nullptr, *d_invC64 = nullptr, *d_F64 = nullptr;
     float *d_C32 = nullptr, *d_invC32 = nullptr, *d_F32 = nullptr;
     uint16_t* d_pairtab = nullptr;
+    uint32_t* d_fulltab = nullptr;   // [P] full row-major rank -> block index e | a << 16 | b << 24
+    int64_t Gst = 0;                 // row stride of G (kGParts regions of gwq 16-byte words)
+    int gwq = 0;
     int* d_rowbase = nullptr;
     // walkers
     uint8_t* d_wocc = nullptr;
@@ -461,7 +472,26 @@ extern "C" int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, co
         // sorted two-pass structures for the BF16 product
         h->sort_nblk = 2 * h->nsm;
         h->sort_nchunk = (int)((h->ncap + 65535) / 65536);
-        ACK(h->alloc(&h->d_G, (size_t)h->ncap * h->Pst));
+        {
+            const int QE = (h->P + kGParts - 1) / kGParts;
+            h->gwq = (QE + 3) / 4;
+            h->Gst = (int64_t)kGParts * h->gwq * 4;
+            std::vector<uint32_t> ft;
+            const int Puu = nu * (nu - 1) / 2, Pdd = nd * (nd - 1) / 2;
+            for (int a = 0; a < N; ++a)
+                for (int b = a + 1; b < N; ++b) {
+                    int e;
+                    if (b < nu) e = a * nu - a * (a + 1) / 2 + (b - a - 1);
+                    else if (a >= nu) e = Puu + (a - nu) * nd - (a - nu) * (a - nu + 1) / 2 + (b - a - 1);
+                    else e = Puu + Pdd + a * nd + (b - nu);
+                    ft.push_back((uint32_t)e | ((uint32_t)a << 16) | ((uint32_t)b << 24));
+                }
+            ACK(h->alloc(&h->d_fulltab, std::max<size_t>(ft.size(), 1)));
+            if (!ft.empty() && cudaMemcpy(h->d_fulltab, ft.data(), sizeof(uint32_t) * ft.size(),
+                                          cudaMemcpyHostToDevice) != cudaSuccess)
+                return fail(VMC_ERR_CUDA);
+        }
+        ACK(h->alloc(&h->d_G, (size_t)h->ncap * h->Gst));
         h->t_chunk = (size_t)65536 * h->P + (size_t)h->npf * kTRun;   // padded runs of one chunk
         ACK(h->alloc(&h->d_Tsort, (size_t)h->sort_nchunk * h->t_chunk));
         ACK(h->alloc(&h->d_counts, (size_t)h->sort_nblk * h->npf));
@@ -559,6 +589,9 @@ extern "C" int vmc_set_params(vmc_handle h, const double* C, const double* f) {
             F32[(size_t)p * M + q] = (float)v;
             F32[(size_t)q * M + p] = -(float)v;
         }
+    // the copies below overwrite buffers that kernels queued on any stream
+    // may still read: wait for all work on the device first
+    VCK(cudaDeviceSynchronize());
     VCK(cudaMemcpy(h->d_C64, c64.data(), sizeof(double) * h->ncp, cudaMemcpyHostToDevice));
     VCK(cudaMemcpy(h->d_invC64, ic64.data(), sizeof(double) * h->ncp, cudaMemcpyHostToDevice));
     VCK(cudaMemcpy(h->d_C32, c32.data(), sizeof(float) * h->ncp, cudaMemcpyHostToDevice));
@@ -567,7 +600,7 @@ extern "C" int vmc_set_params(vmc_handle h, const double* C, const double* f) {
     VCK(cudaMemcpy(h->d_F32, F32.data(), sizeof(float) * M * M, cudaMemcpyHostToDevice));
     h->params_set = true;
     h->obar_ok[0] = h->obar_ok[1] = h->obar_ok[2] = false;
-    h->sorted_ok = false;
+    h->sorted_ok = h->g_ok = h->corr_ok = false;
     return VMC_OK;
 }
 
@@ -605,6 +638,7 @@ extern "C" int vmc_set_walkers(vmc_handle h, const uint8_t* occ, const uint64_t*
     if (!h || !occ) return VMC_ERR_INVALID_ARG;
     int rc = check_configs(h, occ, h->n_walkers);
     if (rc) return rc;
+    VCK(cudaDeviceSynchronize());   // a sampling call on any stream may still use the walkers
     VCK(cudaMemcpy(h->d_wocc, occ, (size_t)h->n_walkers * h->N, cudaMemcpyHostToDevice));
     if (step) VCK(cudaMemcpy(h->d_wstep, step, sizeof(uint64_t) * h->n_walkers, cudaMemcpyHostToDevice));
     else VCK(cudaMemset(h->d_wstep, 0, sizeof(uint64_t) * h->n_walkers));
@@ -706,7 +740,7 @@ extern "C" int vmc_sample(vmc_handle h, int n_burn, uint64_t seed, void* stream)
     if (rc) return rc;
     h->n_s = h->ncap;
     h->obar_ok[0] = h->obar_ok[1] = h->obar_ok[2] = false;
-    h->sorted_ok = false;
+    h->sorted_ok = h->g_ok = h->corr_ok = false;
     rc = transpose_states(h, st);
     if (rc) return rc;
     return read_status(h, st);
@@ -740,7 +774,7 @@ extern "C" int vmc_measure(vmc_handle h, const uint8_t* occ, int64_t n_s, void* 
     if (rc) return rc;
     h->n_s = n_s;
     h->obar_ok[0] = h->obar_ok[1] = h->obar_ok[2] = false;
-    h->sorted_ok = false;
+    h->sorted_ok = h->g_ok = h->corr_ok = false;
     rc = transpose_states(h, st);
     if (rc) return rc;
     return read_status(h, st);
@@ -817,7 +851,7 @@ extern "C" int vmc_logpsi_backward(vmc_handle h, const double* w, double* grad, 
     } else {
         rc = measure_device_configs(h, h->n_s, true, nullptr, nullptr, true, st);
         h->obar_ok[0] = h->obar_ok[1] = h->obar_ok[2] = false;
-    h->sorted_ok = false;
+    h->sorted_ok = h->g_ok = h->corr_ok = false;
     }
     if (rc) return rc;
     return read_status(h, st);
@@ -914,6 +948,7 @@ static int launch_stream(vmc_ctx* h, const void* s_pf, const float* V, const flo
     a.pf_partial = (float*)h->d_pfpart;
     a.stop = stop;
     a.status = h->d_status;
+    a.spin_limit = h->wait_limit;
     a.buf_bytes = buf;
     kern<<<grid, 32 * nw, smem, st>>>(a);
     VCK(cudaGetLastError());
@@ -976,14 +1011,25 @@ static int fin_grid(const vmc_ctx* h, int K = 1) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)kNumPart * kMaxK / K));
 }
 
+static int ensure_corr_runs(vmc_ctx* h, cudaStream_t st);
+
 // Build G (sample-major packed) and T (parameter-major, per 65,536-sample
 // chunk) from the BF16 store, once per set of samples.
+static int ensure_G(vmc_ctx* h, cudaStream_t st) {
+    if (h->g_ok) return VMC_OK;
+    if (!h->d_G || h->n_s == 0) return VMC_ERR_STATE;
+    k_build_G<<<(unsigned)((h->n_s + 7) / 8), 256, 0, st>>>(h->pb, h->n_s, h->d_socc, h->Nst, h->d_pf16, h->Pst,
+                                                           h->d_fulltab, h->gwq, h->Gst, h->d_G); h->n_launch++;
+    VCK(cudaGetLastError());
+    h->g_ok = true;
+    return VMC_OK;
+}
+
 static int ensure_sorted(vmc_ctx* h, cudaStream_t st) {
     if (h->sorted_ok) return VMC_OK;
     if (!h->d_G || h->n_s == 0) return VMC_ERR_STATE;
-    k_build_G<<<(unsigned)((h->n_s + 7) / 8), 256, 0, st>>>(h->pb, h->n_s, h->d_socc, h->Nst, h->d_pf16, h->Pst,
-                                                           h->d_G); h->n_launch++;
-    VCK(cudaGetLastError());
+    int rc0 = ensure_G(h, st);
+    if (rc0) return rc0;
     const size_t smem = (size_t)h->npf * 4;
     VCK(cudaFuncSetAttribute(k_count_G, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     VCK(cudaFuncSetAttribute(k_fill_T, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * smem)));
@@ -993,13 +1039,24 @@ static int ensure_sorted(vmc_ctx* h, cudaStream_t st) {
     for (int c = 0; c < nchunk; ++c) {
         const int64_t sb = (int64_t)c * 65536, se = std::min<int64_t>(h->n_s, sb + 65536);
         uint32_t* base = h->d_base + (size_t)c * (h->npf + 1);
-        k_count_G<<<h->sort_nblk, 512, smem, st>>>(h->d_G, h->Pst, h->P, sb, se, h->npf, h->d_counts); h->n_launch++;
+        k_count_G<<<h->sort_nblk, 512, smem, st>>>(h->d_G, h->Gst, h->P, sb, se, h->npf, h->d_counts); h->n_launch++;
         k_scan_blocks<<<(h->npf + 255) / 256, 256, 0, st>>>(h->d_counts, h->sort_nblk, h->npf, h->d_total); h->n_launch++;
         k_scan_params<<<1, 1024, 0, st>>>(h->d_total, h->npf, (uint32_t)(c * h->t_chunk), base); h->n_launch++;
-        k_fill_T<<<h->sort_nblk, 512, 2 * smem, st>>>(h->d_G, h->Pst, h->P, sb, se, h->npf, h->d_counts, base,
+        k_fill_T<<<h->sort_nblk, 512, 2 * smem, st>>>(h->d_G, h->Gst, h->P, sb, se, h->npf, h->d_counts, base,
                                                   h->d_Tsort); h->n_launch++;
         VCK(cudaGetLastError());
     }
+    int rc = ensure_corr_runs(h, st);
+    if (rc) return rc;
+    h->sorted_ok = true;
+    return VMC_OK;
+}
+
+// Correlator runs (the samples of every correlator parameter grouped by
+// parameter) and the work items of their scatter, once per set of samples.
+static int ensure_corr_runs(vmc_ctx* h, cudaStream_t st) {
+    if (h->corr_ok) return VMC_OK;
+    if (!h->d_Tc || h->n_s == 0) return VMC_ERR_STATE;
     if (h->ncorr > 0) {
         // (class, slice) grid: a class shared by many correlators spreads over
         // several CTAs
@@ -1021,7 +1078,7 @@ static int ensure_sorted(vmc_ctx* h, cudaStream_t st) {
                                                                         h->d_items); h->n_launch++;
         VCK(cudaGetLastError());
     }
-    h->sorted_ok = true;
+    h->corr_ok = true;
     return VMC_OK;
 }
 
@@ -1051,7 +1108,7 @@ template <int K>
 static bool sorted_usable(const vmc_ctx* h) {
     if (!h->use_sorted || !h->d_G || h->ncorr > 32 * kCorrPerLane) return false;
     if ((size_t)h->npf * K * 4 + (size_t)(h->ncorr + 1) * 4 > h->smem_optin) return false;   // gather table
-    return gather_kernel<K>((int)((h->Pst / 4 + 31) / 32)) != nullptr;
+    return gather_kernel<K>((int)((h->Gst / 4 + 31) / 32)) != nullptr;
 }
 
 // gather + parameter-major scatter for the BF16 store; the centered t_s go to
@@ -1074,7 +1131,7 @@ static int launch_sorted(vmc_ctx* h, const float* V, const float* invC, const do
     a.pb = h->pb;
     a.n_s = h->n_s;
     a.s_cidx = h->d_cidx; a.ncst = h->ncst;
-    a.G = h->d_G; a.Pst = h->Pst;
+    a.G = h->d_G; a.Pst = h->Gst;
     a.V = V; a.invC = invC; a.Tv = Tv;
     a.obv_part = obv_part; a.n_obv_part = vgrid(h, K);
     a.T = h->d_Tsort; a.base = h->d_base; a.nchunk = (int)((h->n_s + 65535) / 65536);
@@ -1086,7 +1143,7 @@ static int launch_sorted(vmc_ctx* h, const float* V, const float* invC, const do
     a.tt_part = tt_part;
     a.stop = stop;
     const size_t smem = (size_t)h->npf * K * 4 + (size_t)(h->ncorr + 1) * 4;
-    auto gk = gather_kernel<K>((int)((h->Pst / 4 + 31) / 32));
+    auto gk = gather_kernel<K>((int)((h->Gst / 4 + 31) / 32));
     VCK(cudaFuncSetAttribute(gk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     const int gthreads = gather_threads(K), gwarps = gthreads / 32;
@@ -1107,6 +1164,80 @@ static int launch_sorted(vmc_ctx* h, const float* V, const float* invC, const do
         h->recs.push_back(rec);
     }
     return VMC_OK;
+}
+
+// Fused single-pass product over G (fused.cu): the BF16 store's sorted rows,
+// one vector; six private pairing images and the v table in shared memory.
+static size_t fused_smem(const vmc_ctx* h) {
+    return (size_t)h->npf * 4 * (1 + kFusedImages) + (size_t)(h->ncorr + 1) * 4;
+}
+
+static bool fused_usable(const vmc_ctx* h) {
+    if (!h->use_fused || !h->d_G || h->ncorr > 32 * kCorrPerLane) return false;
+    if ((size_t)h->nsm * h->npf * sizeof(float) > h->pfpart_bytes) return false;
+    if (fused_smem(h) + 512 > h->smem_optin) return false;
+    return (h->gwq + 31) / 32 <= 4;
+}
+
+using FusedKern = void (*)(SortedArgs, float*, int);
+static FusedKern fused_kernel(int u) {
+    static const FusedKern tab[4] = {k_sv_fused<1>, k_sv_fused<2>, k_sv_fused<3>, k_sv_fused<4>};
+    return u >= 1 && u <= 4 ? tab[u - 1] : nullptr;
+}
+
+// one pass over G: centered t_s to Tv, the pairing sums to d_pfraw and the
+// correlator sums to d_corrraw (FP32), as launch_sorted
+static int launch_fused(vmc_ctx* h, const float* V, const float* invC, const double* obv_part, float* Tv,
+                        const int* stop, cudaStream_t st, double* tt_part = nullptr, bool craw_zero = false) {
+    if (!fused_usable(h)) return VMC_ERR_UNSUPPORTED;
+    int rc = ensure_G(h, st);
+    if (!rc) rc = ensure_corr_runs(h, st);
+    if (rc) return rc;
+    vmc_ctx::PassRec rec{};
+    if (h->prof) {
+        rec.a = h->get_event();
+        rec.b = h->get_event();
+        rec.kind = VMC_STORE_BF16;
+        rec.bytes = (double)h->n_s * (2.0 * h->ncorr + h->N + (double)h->P * 2);
+        VCK(cudaEventRecord(rec.a, st));
+    }
+    SortedArgs a{};
+    a.pb = h->pb;
+    a.n_s = h->n_s;
+    a.s_cidx = h->d_cidx; a.ncst = h->ncst;
+    a.G = h->d_G; a.Pst = h->Gst;
+    a.V = V; a.invC = invC; a.Tv = Tv;
+    a.obv_part = obv_part; a.n_obv_part = vgrid(h, 1);
+    a.raw = (float*)h->d_pfraw;
+    a.Tc = h->d_Tc; a.cbase = h->d_cbase; a.craw = (float*)h->d_corrraw;
+    a.items = h->d_items;
+    a.n_items = h->d_item_base + (h->ncp + 31) / 32;
+    a.ncb = h->ncorr > 0 ? (int)((h->max_items + 7) / 8) : 0;
+    a.tt_part = tt_part;
+    a.stop = stop;
+    const size_t smem = fused_smem(h);
+    auto fk = fused_kernel((h->gwq + 31) / 32);
+    VCK(cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int64_t need = (h->n_s + kFusedImages - 1) / kFusedImages;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(h->nsm, need));
+    fk<<<grid, kFusedWarps * 32, smem, st>>>(a, (float*)h->d_pfpart, h->gwq); h->n_launch++;
+    VCK(cudaGetLastError());
+    h->last_fused_grid = grid;
+    if (h->ncp > 0 && !craw_zero) VCK(cudaMemsetAsync(h->d_corrraw, 0, sizeof(float) * h->ncp, st));
+    k_sv_finish<<<a.ncb + (h->npf + 255) / 256, 256, 0, st>>>(a, (const float*)h->d_pfpart, grid); h->n_launch++;
+    VCK(cudaGetLastError());
+    if (h->prof) {
+        VCK(cudaEventRecord(rec.b, st));
+        h->recs.push_back(rec);
+    }
+    return VMC_OK;
+}
+
+// product path of a K-vector product (VMC_PATH_*): the caller's choice, or
+// under AUTO the autotuner's (default: the sorted two-pass product)
+static int product_path(const vmc_ctx* h, int K) {
+    if (h->path != VMC_PATH_AUTO) return h->path;
+    return K == 1 ? h->auto_path : h->auto_path4;
 }
 
 // out = (S + shift I) V with K vectors, V/out in AT precision ([K][nv]), over
@@ -1131,14 +1262,23 @@ static int apply_S_impl(vmc_ctx* h, const void* s_pf, int kind, const AT* V, AT*
     int nblk = 0;
     int rc = VMC_ERR_UNSUPPORTED;
     bool sorted = false;
+    const int path = product_path(h, K);
+    if constexpr (sizeof(AT) == 4 && sizeof(ST) == 2 && K == 1) {
+        if (path == VMC_PATH_FUSED) {
+            rc = launch_fused(h, (const float*)V, (const float*)invC, obv_part, (float*)T, stop, st);
+            if (rc != VMC_OK && rc != VMC_ERR_UNSUPPORTED) return rc;
+            sorted = rc == VMC_OK;
+        }
+    }
     if constexpr (sizeof(AT) == 4 && sizeof(ST) == 2) {
-        if (h->use_sorted && h->d_G) {
+        if (!sorted && (path == VMC_PATH_SORTED || path == VMC_PATH_FUSED) && h->use_sorted && h->d_G) {
             rc = launch_sorted<K>(h, (const float*)V, (const float*)invC, obv_part, (float*)T, stop, st);
+            if (rc != VMC_OK && rc != VMC_ERR_UNSUPPORTED) return rc;
             sorted = rc == VMC_OK;
         }
     }
     if constexpr (sizeof(AT) == 4 && K <= 2) {
-        if (rc == VMC_ERR_UNSUPPORTED && h->use_stream)
+        if (rc == VMC_ERR_UNSUPPORTED && path != VMC_PATH_GENERIC && h->use_stream)
             rc = launch_stream<ST, K>(h, s_pf, (const float*)V, (const float*)invC, (float*)T, stop, st, &nblk);
     }
     if (rc == VMC_ERR_UNSUPPORTED) rc = launch_main<ST, AT, K, true>(h, s_pf, V, invC, T, stop, st, &nblk);
@@ -1325,11 +1465,92 @@ extern "C" int sr_apply_S(vmc_handle h, const double* V, double* out, int k, dou
     if (!h || !V || !out || k < 1 || k > kMaxK || k == 3) return VMC_ERR_INVALID_ARG;
     if (h->n_s == 0) return VMC_ERR_STATE;
     cudaStream_t st = (cudaStream_t)stream;
+    int rc;
     switch (k) {
-        case 1: return apply_S_dispatch<1>(h, V, out, shift, store, st);
-        case 2: return apply_S_dispatch<2>(h, V, out, shift, store, st);
-        default: return apply_S_dispatch<4>(h, V, out, shift, store, st);
+        case 1: rc = apply_S_dispatch<1>(h, V, out, shift, store, st); break;
+        case 2: rc = apply_S_dispatch<2>(h, V, out, shift, store, st); break;
+        default: rc = apply_S_dispatch<4>(h, V, out, shift, store, st); break;
     }
+    if (rc) return rc;
+    return read_status(h, st);   // a staged wait that ran out (synchronizes the stream)
+}
+
+extern "C" int vmc_set_product_path(vmc_handle h, int path) {
+    if (!h || path < VMC_PATH_AUTO || path > VMC_PATH_GENERIC) return VMC_ERR_INVALID_ARG;
+    h->path = path;
+    return VMC_OK;
+}
+
+extern "C" int vmc_set_auto_paths(vmc_handle h, int path, int path4) {
+    if (!h || path < VMC_PATH_SORTED || path > VMC_PATH_GENERIC || path4 < VMC_PATH_SORTED ||
+        path4 > VMC_PATH_GENERIC)
+        return VMC_ERR_INVALID_ARG;
+    h->auto_path = path;
+    h->auto_path4 = path4;
+    return VMC_OK;
+}
+
+// time `reps` BF16 products of K vectors on path `path`; ms < 0 if the path
+// does not apply
+template <int K>
+static int time_path(vmc_ctx* h, int path, int reps, cudaStream_t st, double* ms) {
+    *ms = -1.0;
+    if (path == VMC_PATH_FUSED && (K != 1 || !fused_usable(h))) return VMC_OK;
+    if (path == VMC_PATH_SORTED && !sorted_usable<K>(h)) return VMC_OK;
+    if (path == VMC_PATH_STAGED && (K > 2 || !h->use_stream)) return VMC_OK;
+    const int saved = h->path;
+    h->path = path;
+    const int64_t n = h->nv * K;
+    // a zero vector: the passes do the same work for any input
+    if (cudaMemsetAsync(h->d_b32, 0, sizeof(float) * n, st) != cudaSuccess) return VMC_ERR_CUDA;
+    int rc = apply_S_impl<__nv_bfloat16, float, K>(h, h->d_pf16, 2, h->d_b32, h->d_q32, 1e-3, nullptr, nullptr,
+                                                  nullptr, st);   // warm-up (builds the path's copies)
+    cudaEvent_t e0 = h->get_event(), e1 = h->get_event();
+    if (!rc) rc = cudaEventRecord(e0, st) == cudaSuccess ? VMC_OK : VMC_ERR_CUDA;
+    for (int r = 0; r < reps && !rc; ++r)
+        rc = apply_S_impl<__nv_bfloat16, float, K>(h, h->d_pf16, 2, h->d_b32, h->d_q32, 1e-3, nullptr, nullptr,
+                                                  nullptr, st);
+    if (!rc) rc = cudaEventRecord(e1, st) == cudaSuccess ? VMC_OK : VMC_ERR_CUDA;
+    float t = 0.f;
+    if (!rc) rc = cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess
+                      ? VMC_OK : VMC_ERR_CUDA;
+    h->ev_pool.push_back(e0);
+    h->ev_pool.push_back(e1);
+    h->path = saved;
+    if (rc == VMC_ERR_UNSUPPORTED) return VMC_OK;
+    if (!rc) *ms = (double)t / reps;
+    return rc;
+}
+
+extern "C" int sr_autotune(vmc_handle h, int reps, vmc_tune_info* info, void* stream) {
+    if (!h || reps < 1) return VMC_ERR_INVALID_ARG;
+    if (h->n_s == 0 || !h->d_pf16) return VMC_ERR_STATE;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = ensure_obar(h, 2, st);
+    if (rc) return rc;
+    vmc_tune_info inf{};
+    double best = -1.0, best4 = -1.0;
+    inf.path = VMC_PATH_SORTED;
+    inf.path4 = VMC_PATH_SORTED;
+    for (int p = VMC_PATH_SORTED; p <= VMC_PATH_GENERIC; ++p) {
+        double ms = -1.0, ms4 = -1.0;
+        if ((rc = time_path<1>(h, p, reps, st, &ms))) return rc;
+        if ((rc = time_path<4>(h, p, reps, st, &ms4))) return rc;
+        inf.ms[p] = ms;
+        inf.ms4[p] = ms4;
+        if (ms > 0 && (best < 0 || ms < best)) { best = ms; inf.path = p; }
+        if (ms4 > 0 && (best4 < 0 || ms4 < best4)) { best4 = ms4; inf.path4 = p; }
+    }
+    h->auto_path = inf.path;
+    h->auto_path4 = inf.path4;
+    if (info) *info = inf;
+    return VMC_OK;
+}
+
+extern "C" int vmc_set_wait_limit(vmc_handle h, uint32_t tries) {
+    if (!h) return VMC_ERR_INVALID_ARG;
+    h->wait_limit = tries;
+    return VMC_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -1358,15 +1579,21 @@ static int cg_loop(vmc_ctx* h, const void* s_pf, int kind, const VT* b, VT* x, V
     *iters = 0;
     if (max_iter <= 0) return VMC_OK;
     // centered sorted product with the fused update: gather, scatter, x/r, p
-    bool fused = false;
-    if constexpr (sizeof(ST) == 2 && sizeof(VT) == 4) fused = sorted_usable<1>(h);
+    bool fused = false, single = false;
+    if constexpr (sizeof(ST) == 2 && sizeof(VT) == 4) {
+        const int path = product_path(h, 1);
+        single = path == VMC_PATH_FUSED && fused_usable(h);
+        fused = single || ((path == VMC_PATH_SORTED || path == VMC_PATH_FUSED) && sorted_usable<1>(h));
+    }
     if (fused && h->ncp > 0) VCK(cudaMemsetAsync(h->d_corrraw, 0, sizeof(float) * h->ncp, st));
     while (!done) {
         for (int j = 0; j < kChunk; ++j) {
             if (fused) {
                 if constexpr (sizeof(ST) == 2 && sizeof(VT) == 4) {
-                    int rc = launch_sorted<1>(h, p, h->d_invC32, obp_part, (float*)h->d_T, h->d_stop, st, tt_part,
-                                              true);
+                    int rc = single ? launch_fused(h, p, h->d_invC32, obp_part, (float*)h->d_T, h->d_stop, st, tt_part,
+                                                   true)
+                                   : launch_sorted<1>(h, p, h->d_invC32, obp_part, (float*)h->d_T, h->d_stop, st,
+                                                      tt_part, true);
                     if (rc) return rc;
                     CgFusedArgs<float> f{};
                     f.x = x; f.r = r; f.p = p;
@@ -1376,7 +1603,7 @@ static int cg_loop(vmc_ctx* h, const void* s_pf, int kind, const VT* b, VT* x, V
                     f.n = n; f.ncp = h->ncp;
                     f.inv_n = 1.0 / (double)h->n_s;
                     f.shift = shift;
-                    f.tt_part = tt_part; f.ntt = h->last_gather_grid;
+                    f.tt_part = tt_part; f.ntt = single ? h->last_fused_grid : h->last_gather_grid;
                     f.pp_part = pp_part; f.npp = vg;
                     f.scal = h->d_scal;
                     f.rr_part = rr_part;
@@ -1394,9 +1621,16 @@ static int cg_loop(vmc_ctx* h, const void* s_pf, int kind, const VT* b, VT* x, V
         }
         VCK(cudaMemcpyAsync(h->h_pinned, h->d_scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
         VCK(cudaMemcpyAsync(h->h_pinned + 8, h->d_stop, sizeof(int), cudaMemcpyDeviceToHost, st));
+        VCK(cudaMemcpyAsync(h->h_pinned + 9, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
         VCK(cudaStreamSynchronize(st));
-        int stop;
+        int stop, status;
         memcpy(&stop, h->h_pinned + 8, sizeof(int));
+        memcpy(&status, h->h_pinned + 9, sizeof(int));
+        if (status & ST_TIMEOUT) {
+            VCK(cudaMemsetAsync(h->d_status, 0, sizeof(int), st));
+            set_err("a staged wait in the S product ran out");
+            return VMC_ERR_TIMEOUT;
+        }
         *iters = (int)h->h_pinned[CG_IT];
         if (stop) done = 1;
     }
@@ -1721,7 +1955,7 @@ extern "C" int sr_update(vmc_handle h, const double* y, double tau, int store, d
     VCK(cudaGetLastError());
     // the stored samples belong to the old parameters
     h->obar_ok[0] = h->obar_ok[1] = h->obar_ok[2] = false;
-    h->sorted_ok = false;
+    h->sorted_ok = h->g_ok = h->corr_ok = false;
     VCK(cudaMemcpyAsync(h->h_pinned + 1, h->d_scal + kScalX0, sizeof(double), cudaMemcpyDeviceToHost, st));
     int rc = read_status(h, st);   // synchronizes the stream
     if (x0) *x0 = h->h_pinned[1];
@@ -2163,7 +2397,7 @@ extern "C" int lm_update(vmc_handle h, const double* x, double Sx0, void* stream
     k_lm_update<<<vgrid(h, 1), 256, 0, st>>>(a, x, 1.0 / Sx0); h->n_launch++;
     VCK(cudaGetLastError());
     h->obar_ok[0] = h->obar_ok[1] = h->obar_ok[2] = false;
-    h->sorted_ok = false;
+    h->sorted_ok = h->g_ok = h->corr_ok = false;
     return read_status(h, st);
 }
 

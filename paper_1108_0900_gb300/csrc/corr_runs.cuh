@@ -1,0 +1,78 @@
+// Correlator half of the transposed product from the correlator runs: the
+// samples of every correlator parameter grouped by parameter (built once per
+// set of samples, see sorted.cu), summed against the per-sample dots t_s.
+#pragma once
+#include "common.cuh"
+#include "kernels.h"
+
+namespace vmc {
+
+// Correlator part of the gather for one sample: lane L looks up V[k_c] / C[k_c]
+// for c = L + 32 j (at most 32 kCorrPerLane correlators).  The loads are only
+// issued here; the caller adds cv after its pairing work, which hides them.
+template <int K>
+__device__ __forceinline__ void corr_lookups(const DevProblem& pb, const int* coff, const cstate_t* cid,
+                                             const float* V, const float* invC, int lane,
+                                             float (&cv)[kCorrPerLane][K]) {
+#pragma unroll
+    for (int j = 0; j < kCorrPerLane; ++j) {
+        const int c = lane + 32 * j;
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) cv[j][kk] = 0.f;
+        if (c < pb.ncorr) {
+            const int k = coff[c] + (int)cid[c];
+            const float ic = __ldg(invC + k);
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) cv[j][kk] = __ldg(V + kk * pb.nv + k) * ic;
+        }
+    }
+}
+
+// Correlator work item (group g, entries e0 .. min(e0 + kCorrItem, end of g)):
+// the group's parameters 32 g .. 32 g + 31 have contiguous runs, read as one
+// coalesced stream; entries carry k mod 32, equal values are contiguous, and
+// a segmented warp scan hands each segment's sum to its last lane, which adds
+// it to the parameter's slot in shared memory (one writer per parameter per
+// step).  The slots are then added to craw (zeroed by the caller): a long run
+// (a parameter shared by many correlators) spreads over several items.
+template <int K>
+__device__ __forceinline__ void scatter_C_item(const SortedArgs& a, uint2 item, float* slot) {
+    const int lane = threadIdx.x & 31;
+    const int64_t k0 = (int64_t)item.x * 32;
+    const int64_t kend = min(a.pb.ncp, k0 + 32);
+#pragma unroll
+    for (int kk = 0; kk < K; ++kk) slot[lane * K + kk] = 0.f;
+    __syncwarp();
+    const uint32_t lo = item.y, hi = min(a.cbase[kend], lo + (uint32_t)kCorrItem);
+    for (uint32_t e0 = lo; e0 < hi; e0 += 32) {
+        const uint32_t e = e0 + lane;
+        const bool in = e < hi;
+        const uint32_t v = in ? __ldcs(a.Tc + e) : 0u;
+        const int ls = in ? (int)(v & 31u) : 32 + lane;        // past the end: a segment of its own
+        float t[K];
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) t[kk] = in ? __ldg(a.Tv + (int64_t)(v >> 5) * K + kk) : 0.f;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int lo_ls = __shfl_up_sync(0xffffffffu, ls, o);
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) {
+                const float u = __shfl_up_sync(0xffffffffu, t[kk], o);
+                if (lane >= o && lo_ls == ls) t[kk] += u;
+            }
+        }
+        const int next_ls = __shfl_down_sync(0xffffffffu, ls, 1);
+        if (in && (lane == 31 || next_ls != ls))
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) slot[ls * K + kk] += t[kk];
+        __syncwarp();
+    }
+    if (k0 + lane < kend)
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) {
+            const float v = slot[lane * K + kk];
+            if (v != 0.f) atomicAdd(a.craw + (k0 + lane) * K + kk, v);
+        }
+}
+
+}  // namespace vmc

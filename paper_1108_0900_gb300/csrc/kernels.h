@@ -224,6 +224,7 @@ struct StreamArgs {
     float* pf_partial;      // [gridDim][npf][K]
     const int* stop;
     int* status;            // ST_TIMEOUT on a wait that ran out
+    uint32_t spin_limit;    // tries of each bounded wait on a staged sample
     size_t buf_bytes;       // one staging buffer (occ | pf)
 };
 
@@ -266,8 +267,10 @@ constexpr int kTRun = 128;         // T runs are padded to whole blocks of this 
 constexpr int kCorrItem = 2048;    // entries per correlator work item of the sorted scatter
 constexpr int kInstPerUnit = 4;    // correlators of one class per cluster of the histogram scatter
 
+constexpr int kGParts = 4;         // parts of consecutive pq per G row (warps per image of the single pass)
 __global__ void __launch_bounds__(256) k_build_G(DevProblem pb, int64_t n_s, const uint8_t* s_occ, int Nst,
-                                                 const __nv_bfloat16* pf16, int64_t Pst, uint32_t* G);
+                                                 const __nv_bfloat16* pf16, int64_t Pst, const uint32_t* fulltab,
+                                                 int wq, int64_t Gst, uint32_t* G);
 __global__ void __launch_bounds__(512) k_count_G(const uint32_t* G, int64_t Pst, int P, int64_t s_begin,
                                                  int64_t s_end, int npf, uint32_t* counts);
 __global__ void k_scan_blocks(uint32_t* counts, int nblk, int npf, uint32_t* total);
@@ -287,6 +290,17 @@ __global__ void __launch_bounds__(512) k_fill_C(DevProblem pb, int64_t n_s, cons
                                                 uint32_t* cursor, uint32_t* Tc);
 __global__ void k_corr_item_count(const uint32_t* cbase, int64_t ncp, uint32_t* n_items);
 __global__ void k_corr_item_fill(const uint32_t* cbase, int64_t ncp, const uint32_t* item_base, uint2* items);
+
+// Fused single-pass product over the sorted BF16 rows G, one vector
+// (fused.cu): per sample the gather t_s = O_s . v and, in the same pass, the
+// scatter of t_s O_s into a private shared-memory image of the pairing block
+// per warp (no atomics, no parameter-major copy).
+constexpr int kFusedImages = 6;   // private pairing images per CTA (one per group of kGParts warps)
+constexpr int kFusedWarps = kFusedImages * kGParts;
+constexpr int kFusedAhead = 4;    // rows per group requested into L2 ahead of the register loads
+template <int U> __global__ void __launch_bounds__(kFusedWarps * 32, 1) k_sv_fused(SortedArgs a, float* pf_partial,
+                                                                                 int wq);
+__global__ void __launch_bounds__(256) k_sv_finish(SortedArgs a, const float* pf_partial, int nblk);
 
 // ---------------------------------------------------------------------------
 // accelerated linear method (Sec. II.B): Eq. 10 products with the basis

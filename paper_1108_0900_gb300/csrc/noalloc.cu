@@ -67,8 +67,25 @@ __global__ void __launch_bounds__(512) k_pairing_product_static(int64_t n_s, int
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     uint8_t* my = occw + wid * 64;
+    const int ns = M >> 1;
     for (int64_t s = (int64_t)blockIdx.x * nw + wid; s < n_s; s += (int64_t)gridDim.x * nw) {
-        for (int i = lane; i < N; i += 32) my[i] = occ[s * occ_stride + i];
+        // the occupation must be a configuration of the sector: strictly
+        // ascending, n_up orbitals below n_sites, n_dn from n_sites to M - 1;
+        // otherwise some pairing index would fall outside the images, so the
+        // sample gets t_s = NaN and adds nothing
+        bool bad = false;
+        for (int i = lane; i < N; i += 32) {
+            const int o = occ[s * occ_stride + i];
+            my[i] = (uint8_t)o;
+            const bool spin_ok = i < nu ? o < ns : (o >= ns && o < M);
+            const bool asc = i == 0 || o > (int)occ[s * occ_stride + i - 1];
+            bad = bad || !spin_ok || !asc;
+        }
+        if (__any_sync(VMC_FULL_MASK, bad)) {
+            if (lane == 0) t_out[s] = __int_as_float(0x7fc00000);
+            __syncwarp();
+            continue;
+        }
         __syncwarp();
         const float* W = pf + s * pf_stride;
         float t = 0.f;

@@ -17,23 +17,31 @@
 // The build (count, scan, fill) streams G three times once per SR step.
 #include "common.cuh"
 #include "kernels.h"
+#include "corr_runs.cuh"
 
 namespace vmc {
 
-// G rows in a bank-aware order.  The gather reads lane L's 16-byte word
-// L + 32 u of a row and looks up v[pq] in shared memory for its element j, so
-// the 32 lanes of one lookup instruction (u, j) read the row slots
-// 128 u + 4 L + j.  Lookups whose pq fall in the same shared-memory bank
-// (pq mod 32) but at different addresses serialise, and random pq give about
-// 3.5-way conflicts.  Here the P elements of a sample are ranked within their
-// bank and placed in rank-major order (rank 0 of every bank, then rank 1, ...)
-// along the instruction groups, so a group holds at most two elements of a
-// bank: all ranks below the smallest bank count fill whole conflict-free
-// groups.  Padding slots hold (0, 0.0); samples whose largest bank count
-// exceeds kBankRanks keep the plain element order.
+// G rows: the P pairing elements of a sample as (pq << 16) | bf16, cut into
+// kGParts parts of consecutive pq (part f holds the elements of full-matrix
+// row-major rank f QE .. (f+1) QE - 1 over ascending positions, which is pq
+// order, QE = ceil(P / kGParts)), each part in a region of WQ = ceil(QE / 4)
+// 16-byte words, so the row stride is kGParts * WQ * 4 entries.  The
+// single-pass product gives each part to one warp of a group, and the parts'
+// pq ranges are disjoint.
+//
+// Inside a part the elements are placed in a bank-aware order.  A reader's
+// lane L holds word L + 32 u of the region and looks up v[pq] in shared
+// memory for element j of it, so the 32 lanes of one lookup instruction
+// (u, j) read the region slots 128 u + 4 L + j.  Lookups whose pq fall in the
+// same shared-memory bank (pq mod 32) at different addresses serialise, and
+// random pq give about 3.5-way conflicts.  So the elements of a part are
+// ranked within their bank and placed in rank-major order (rank 0 of every
+// bank, then rank 1, ...) along the instruction groups: a group holds at
+// most two elements of a bank.  Padding slots hold (0, 0.0); parts whose
+// largest bank count exceeds kBankRanks keep the plain order.
 constexpr int kBankRanks = 128;
 
-// row position of slot k in the gather's instruction-group order
+// region position of slot k in the reader's instruction-group order
 __device__ __forceinline__ int group_slot_pos(int k, int n4) {
     const int nfull = n4 >> 5, m = n4 & 31;
     if (k < 128 * nfull) return 128 * (k >> 7) + 4 * (k & 31) + ((k >> 5) & 3);
@@ -41,8 +49,11 @@ __device__ __forceinline__ int group_slot_pos(int k, int n4) {
     return 128 * nfull + 4 * (kr % m) + kr / m;
 }
 
+// fulltab[r] = e | a << 16 | b << 24: rank r in the full row-major order over
+// positions a < b, and e the element's index in the store's block order
 __global__ void __launch_bounds__(256) k_build_G(DevProblem pb, int64_t n_s, const uint8_t* s_occ, int Nst,
-                                                 const __nv_bfloat16* pf16, int64_t Pst, uint32_t* G) {
+                                                 const __nv_bfloat16* pf16, int64_t Pst, const uint32_t* fulltab,
+                                                 int wq, int64_t Gst, uint32_t* G) {
     __shared__ uint8_t occw[8][64];
     __shared__ uint32_t cnt[8][32];
     __shared__ uint32_t msk[8][kBankRanks];
@@ -51,52 +62,57 @@ __global__ void __launch_bounds__(256) k_build_G(DevProblem pb, int64_t n_s, con
     const int64_t s = (int64_t)blockIdx.x * 8 + wid;
     if (s >= n_s) return;
     for (int i = lane; i < pb.N; i += 32) occw[wid][i] = s_occ[s * Nst + i];
-    cnt[wid][lane] = 0u;
     __syncwarp();
     const uint16_t* src = (const uint16_t*)(pf16 + s * Pst);
-    uint32_t* dst = G + s * Pst;
-    const int P = pb.P, n4 = (int)(Pst >> 2);
-    for (int e = lane; e < P; e += 32) {
-        const uint16_t pt = pb.pairtab[e];
-        const int pq = (int)pf_row_base(pb.M, occw[wid][pt & 255]) + occw[wid][pt >> 8];
-        atomicAdd(&cnt[wid][pq & 31], 1u);
-    }
-    __syncwarp();
-    const uint32_t c = cnt[wid][lane];
-    uint32_t maxc = c;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) maxc = max(maxc, __shfl_xor_sync(0xffffffffu, maxc, o));
-    const bool ranked = maxc <= (uint32_t)kBankRanks;
-    if (ranked) {
-        // banks with more than r elements, and the slots before rank r
-        for (int r = 0; r < (int)maxc; ++r) {
-            const uint32_t m = __ballot_sync(0xffffffffu, c > (uint32_t)r);
-            if (lane == 0) msk[wid][r] = m;
-        }
-        __syncwarp();
-        if (lane == 0) {
-            uint32_t run = 0;
-            for (int r = 0; r < (int)maxc; ++r) {
-                rbase[wid][r] = (uint16_t)run;
-                run += __popc(msk[wid][r]);
-            }
-        }
+    const int P = pb.P, QE = (P + kGParts - 1) / kGParts;
+    for (int f = 0; f < kGParts; ++f) {
+        uint32_t* dst = G + s * Gst + (int64_t)f * wq * 4;
+        const int r0 = f * QE, r1 = min(P, r0 + QE), n = max(0, r1 - r0);
         cnt[wid][lane] = 0u;
         __syncwarp();
-    }
-    for (int e = lane; e < P; e += 32) {
-        const uint16_t pt = pb.pairtab[e];
-        const int pq = (int)pf_row_base(pb.M, occw[wid][pt & 255]) + occw[wid][pt >> 8];
-        const uint32_t g = ((uint32_t)pq << 16) | (uint32_t)src[e];
-        int slot = e;
-        if (ranked) {
-            const int b = pq & 31;
-            const uint32_t r = atomicAdd(&cnt[wid][b], 1u);
-            slot = rbase[wid][r] + __popc(msk[wid][r] & ((1u << b) - 1u));
+        for (int r = r0 + lane; r < r1; r += 32) {
+            const uint32_t ft = fulltab[r];
+            const int pq = (int)pf_row_base(pb.M, occw[wid][(ft >> 16) & 255]) + occw[wid][ft >> 24];
+            atomicAdd(&cnt[wid][pq & 31], 1u);
         }
-        dst[group_slot_pos(slot, n4)] = g;
+        __syncwarp();
+        const uint32_t c = cnt[wid][lane];
+        uint32_t maxc = c;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) maxc = max(maxc, __shfl_xor_sync(0xffffffffu, maxc, o));
+        const bool ranked = maxc <= (uint32_t)kBankRanks;
+        if (ranked) {
+            // banks with more than r elements, and the slots before rank r
+            for (int r = 0; r < (int)maxc; ++r) {
+                const uint32_t m = __ballot_sync(0xffffffffu, c > (uint32_t)r);
+                if (lane == 0) msk[wid][r] = m;
+            }
+            __syncwarp();
+            if (lane == 0) {
+                uint32_t run = 0;
+                for (int r = 0; r < (int)maxc; ++r) {
+                    rbase[wid][r] = (uint16_t)run;
+                    run += __popc(msk[wid][r]);
+                }
+            }
+            cnt[wid][lane] = 0u;
+            __syncwarp();
+        }
+        for (int r = r0 + lane; r < r1; r += 32) {
+            const uint32_t ft = fulltab[r];
+            const int pq = (int)pf_row_base(pb.M, occw[wid][(ft >> 16) & 255]) + occw[wid][ft >> 24];
+            const uint32_t g = ((uint32_t)pq << 16) | (uint32_t)src[ft & 0xFFFFu];
+            int slot = r - r0;
+            if (ranked) {
+                const int b = pq & 31;
+                const uint32_t k = atomicAdd(&cnt[wid][b], 1u);
+                slot = rbase[wid][k] + __popc(msk[wid][k] & ((1u << b) - 1u));
+            }
+            dst[group_slot_pos(slot, wq)] = g;
+        }
+        for (int k = n + lane; k < 4 * wq; k += 32) dst[group_slot_pos(k, wq)] = 0u;
+        __syncwarp();
     }
-    for (int k = P + lane; k < (int)Pst; k += 32) dst[group_slot_pos(k, n4)] = 0u;
 }
 
 // Block b of a chunk [s_begin, s_end) owns samples s_begin + [b*per, (b+1)*per).
@@ -279,27 +295,6 @@ __global__ void k_corr_item_fill(const uint32_t* cbase, int64_t ncp, const uint3
     for (uint32_t e = e0; e == e0 || e < e1; e += kCorrItem) items[i++] = make_uint2((uint32_t)g, e);
 }
 
-// Correlator part of the gather for one sample: lane L looks up V[k_c] / C[k_c]
-// for c = L + 32 j (at most 32 kCorrPerLane correlators).  The loads are only
-// issued here; the caller adds cv after its pairing work, which hides them.
-template <int K>
-__device__ __forceinline__ void corr_lookups(const DevProblem& pb, const int* coff, const cstate_t* cid,
-                                             const float* V, const float* invC, int lane,
-                                             float (&cv)[kCorrPerLane][K]) {
-#pragma unroll
-    for (int j = 0; j < kCorrPerLane; ++j) {
-        const int c = lane + 32 * j;
-#pragma unroll
-        for (int kk = 0; kk < K; ++kk) cv[j][kk] = 0.f;
-        if (c < pb.ncorr) {
-            const int k = coff[c] + (int)cid[c];
-            const float ic = __ldg(invC + k);
-#pragma unroll
-            for (int kk = 0; kk < K; ++kk) cv[j][kk] = __ldg(V + kk * pb.nv + k) * ic;
-        }
-    }
-}
-
 // gather: t_s = sum_c V[k_c]/C[k_c] + sum_e W_e v[pq(e)] - Obar . V, warp per
 // sample.  Centering t_s makes the scatter produce the covariance
 // (1/n) sum_s (t_s - Obar . V) O_s = S V directly, with no cancellation
@@ -449,53 +444,6 @@ __device__ __forceinline__ void scatter_T_param(const SortedArgs& a, int pq) {
         const float v = warp_sum(acc[kk] + acc2[kk]);
         if (lane == 0) a.raw[(size_t)pq * K + kk] = v;
     }
-}
-
-// Correlator work item (group g, entries e0 .. min(e0 + kCorrItem, end of g)):
-// the group's parameters 32 g .. 32 g + 31 have contiguous runs, read as one
-// coalesced stream; entries carry k mod 32, equal values are contiguous, and
-// a segmented warp scan hands each segment's sum to its last lane, which adds
-// it to the parameter's slot in shared memory (one writer per parameter per
-// step).  The slots are then added to craw (zeroed by the caller): a long run
-// (a parameter shared by many correlators) spreads over several items.
-template <int K>
-__device__ __forceinline__ void scatter_C_item(const SortedArgs& a, uint2 item, float* slot) {
-    const int lane = threadIdx.x & 31;
-    const int64_t k0 = (int64_t)item.x * 32;
-    const int64_t kend = min(a.pb.ncp, k0 + 32);
-#pragma unroll
-    for (int kk = 0; kk < K; ++kk) slot[lane * K + kk] = 0.f;
-    __syncwarp();
-    const uint32_t lo = item.y, hi = min(a.cbase[kend], lo + (uint32_t)kCorrItem);
-    for (uint32_t e0 = lo; e0 < hi; e0 += 32) {
-        const uint32_t e = e0 + lane;
-        const bool in = e < hi;
-        const uint32_t v = in ? __ldcs(a.Tc + e) : 0u;
-        const int ls = in ? (int)(v & 31u) : 32 + lane;        // past the end: a segment of its own
-        float t[K];
-#pragma unroll
-        for (int kk = 0; kk < K; ++kk) t[kk] = in ? __ldg(a.Tv + (int64_t)(v >> 5) * K + kk) : 0.f;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int lo_ls = __shfl_up_sync(0xffffffffu, ls, o);
-#pragma unroll
-            for (int kk = 0; kk < K; ++kk) {
-                const float u = __shfl_up_sync(0xffffffffu, t[kk], o);
-                if (lane >= o && lo_ls == ls) t[kk] += u;
-            }
-        }
-        const int next_ls = __shfl_down_sync(0xffffffffu, ls, 1);
-        if (in && (lane == 31 || next_ls != ls))
-#pragma unroll
-            for (int kk = 0; kk < K; ++kk) slot[ls * K + kk] += t[kk];
-        __syncwarp();
-    }
-    if (k0 + lane < kend)
-#pragma unroll
-        for (int kk = 0; kk < K; ++kk) {
-            const float v = slot[lane * K + kk];
-            if (v != 0.f) atomicAdd(a.craw + (k0 + lane) * K + kk, v);
-        }
 }
 
 // Both halves of the scatter in one launch: CTAs [0, ncb) take 8 correlator

@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(768, 1) k_sr_stream(StreamArgs a) {
 #pragma unroll
             for (int kk = 0; kk < K; ++kk) t[kk] += __ldg(a.V + kk * pb.nv + k) * ic;
         }
-        if (!mbar_wait_bounded(&bars[2 * wid + b], (uint32_t)((it >> 1) & 1))) { timed_out = true; break; }
+        if (!mbar_wait_limit(&bars[2 * wid + b], (uint32_t)((it >> 1) & 1), a.spin_limit)) { timed_out = true; break; }
         const unsigned char* buf = mybuf0 + (size_t)b * a.buf_bytes;
         const uint8_t* occ = buf;
         const ST* W = (const ST*)(buf + occ_b);
@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(512, 1) k_sr_stream_bf16c(StreamArgs a) {
             const int k = coff[c] + (int)__ldg(cid + c);
             t += __ldg(a.V + k) * __ldg(a.invC + k);
         }
-        if (!mbar_wait_bounded(&bars[2 * wid + b], (uint32_t)((it >> 1) & 1))) { timed_out = true; break; }
+        if (!mbar_wait_limit(&bars[2 * wid + b], (uint32_t)((it >> 1) & 1), a.spin_limit)) { timed_out = true; break; }
         const unsigned char* buf = mybuf0 + (size_t)b * a.buf_bytes;
         const uint16_t* W = (const uint16_t*)(buf + occ_b);
         const int ou = lane < nu ? (int)buf[lane] : 0;

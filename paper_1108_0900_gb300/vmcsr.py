@@ -121,6 +121,10 @@ def lib(build_if_missing: bool = True):
         "vmc_profile": [vp, i32],
         "sr_pairing_product_noalloc": [i64, i32, i32, i32, vp, i64, vp, i64, vp, vp, vp, vp],
         "vmc_profile_read": [vp, i32, vp, vp, vp, vp],
+        "vmc_set_wait_limit": [vp, ct.c_uint32],
+        "vmc_set_product_path": [vp, i32],
+        "sr_autotune": [vp, i32, vp, vp],
+        "vmc_set_auto_paths": [vp, i32, i32],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -244,19 +248,23 @@ def vmc_get_walkers(h: Handle, stream=None):
     return occ, step
 
 
-def save_state(h: Handle, path: str, **extra):
+def save_state(h: Handle, path: str, stream=None, **extra):
     """Checkpoint of an optimisation: the parameters (C, f), every walker's
     configuration and step counter (the counter of its Philox stream), and
     any extra values (e.g. the iteration and the next sampling seed).  With
     the same seed, vmc_sample after load_state reproduces the next batch bit
-    for bit.  `path` is an .npz file."""
-    C, f = vmc_get_params(h)
-    occ, step = vmc_get_walkers(h)
+    for bit.  `path` is an .npz file.  The state is read once the work queued
+    on `stream` (the stream the sampling ran on; None = torch's current
+    stream) is done."""
+    C, f = vmc_get_params(h, stream)
+    occ, step = vmc_get_walkers(h, stream)
     np.savez(path, C=C, f=f, occ=occ, step=step, **{k: np.asarray(v) for k, v in extra.items()})
 
 
 def load_state(h: Handle, path: str) -> dict:
-    """Restore a checkpoint written by save_state; returns its extra values."""
+    """Restore a checkpoint written by save_state; returns its extra values.
+    The parameter and walker uploads wait for all work queued on the device
+    (any stream) before they overwrite anything."""
     d = np.load(path)
     vmc_set_params(h, d["C"], d["f"])
     vmc_set_walkers(h, d["occ"], d["step"])
@@ -488,6 +496,63 @@ def LogPsi():
     if _LogPsi is None:
         _LogPsi = _make_logpsi()
     return _LogPsi
+
+
+VMC_PATH_AUTO, VMC_PATH_SORTED, VMC_PATH_FUSED, VMC_PATH_STAGED, VMC_PATH_GENERIC = 0, 1, 2, 3, 4
+PATH_NAMES = {0: "auto", 1: "sorted", 2: "fused", 3: "staged", 4: "generic"}
+
+
+class vmc_tune_info(ct.Structure):
+    _fields_ = [("path", ct.c_int), ("path4", ct.c_int), ("ms", ct.c_double * 5), ("ms4", ct.c_double * 5)]
+
+
+def vmc_set_product_path(h: Handle, path: int):
+    """Product path of the BF16 S products (VMC_PATH_*; AUTO = the autotuner's
+    choice, by default the sorted two-pass product)."""
+    _check(lib().vmc_set_product_path(h.h, int(path)), "vmc_set_product_path")
+
+
+def sr_autotune(h: Handle, reps: int = 5, stream=None) -> dict:
+    """Time every applicable product path on the handle's samples and make the
+    fastest the AUTO choice; returns {"path", "path4", "ms": {name: ms}, "ms4": ...}."""
+    info = vmc_tune_info()
+    _check(lib().sr_autotune(h.h, int(reps), ct.byref(info), _stream(stream)), "sr_autotune")
+    ms = {PATH_NAMES[p]: info.ms[p] for p in range(1, 5) if info.ms[p] > 0}
+    ms4 = {PATH_NAMES[p]: info.ms4[p] for p in range(1, 5) if info.ms4[p] > 0}
+    return {"path": PATH_NAMES[info.path], "path4": PATH_NAMES[info.path4], "ms": ms, "ms4": ms4}
+
+
+def tuned(h: Handle, cache_path: str, key: str, reps: int = 5, stream=None) -> dict:
+    """The autotuner's choice for workload `key`, cached as JSON in
+    `cache_path`: a cached choice is applied to the handle without timing;
+    otherwise sr_autotune runs and its result is stored."""
+    import json
+    cache = {}
+    if os.path.exists(cache_path):
+        with open(cache_path) as fh:
+            cache = json.load(fh)
+    names = {v: k for k, v in PATH_NAMES.items()}
+    if key in cache:
+        ent = cache[key]
+        _set_auto(h, names[ent["path"]], names[ent["path4"]])
+        return dict(ent, cached=True)
+    ent = sr_autotune(h, reps, stream)
+    cache[key] = ent
+    with open(cache_path, "w") as fh:
+        json.dump(cache, fh, indent=1, sort_keys=True)
+    return dict(ent, cached=False)
+
+
+def _set_auto(h: Handle, path: int, path4: int):
+    """Apply a cached autotuner choice: one-vector products on `path`,
+    two- and four-vector products on `path4`."""
+    _check(lib().vmc_set_auto_paths(h.h, int(path), int(path4)), "vmc_set_auto_paths")
+
+
+def vmc_set_wait_limit(h: Handle, tries: int):
+    """Tries of every bounded wait on a staged tile in the streaming products
+    (default 4,194,304; 0 makes every wait give up: VMC_ERR_TIMEOUT)."""
+    _check(lib().vmc_set_wait_limit(h.h, int(tries)), "vmc_set_wait_limit")
 
 
 def vmc_profile(h: Handle, enable: bool):

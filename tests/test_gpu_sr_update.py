@@ -7,6 +7,7 @@ exact first-order energy change.  Tolerances: FP64 parameters and x_0 1e-12
 relative, with the mean of whichever store the gradient was taken over (the
 FP32 and BF16 cases rebuild that mean from the store's own values).
 """
+import contextlib
 import copy
 
 import numpy as np
@@ -247,11 +248,21 @@ def test_rank_local_sums_add_up_to_the_whole(store):
         h.close()
 
 
-def test_checkpoint_resume_reproduces_the_next_batch(tmp_path):
+@pytest.mark.parametrize("side_stream", [False, True])
+def test_checkpoint_resume_reproduces_the_next_batch(tmp_path, side_stream):
     """save_state after an SR update, load_state into a fresh handle, and the
     next vmc_sample with the same seed gives the same samples bit for bit
-    (configurations, correlator states, E_L, pairing block)."""
+    (configurations, correlator states, E_L, pairing block).  With
+    side_stream, every call runs on a non-blocking torch stream and the
+    checkpoint is taken on that stream."""
     wl = inputs.workload("hubbard4x4_pair", n_walkers=32, samples_per_walker=4)
+    stream = torch.cuda.Stream() if side_stream else None
+    ctx = torch.cuda.stream(stream) if side_stream else contextlib.nullcontext()
+    with ctx:
+        _checkpoint_roundtrip(tmp_path, wl, stream)
+
+
+def _checkpoint_roundtrip(tmp_path, wl, stream):
 
     def fresh():
         return V.vmc_create(wl, walker_precision=V.VMC_FP64, keep_fp64_store=True, keep_lowp_store=False)
@@ -264,7 +275,7 @@ def test_checkpoint_resume_reproduces_the_next_batch(tmp_path):
     y, _ = V.sr_cg_solve(h, g, 1e-3, 1e-8, 5000, V.VMC_CG_FP64)
     V.sr_update(h, y, 0.02, V.VMC_STORE_FP64)
     path = str(tmp_path / "state.npz")
-    V.save_state(h, path, next_seed=12, iteration=1)
+    V.save_state(h, path, stream=stream, next_seed=12, iteration=1)
     V.vmc_sample(h, 0, 12)
     a = V.vmc_get_samples(h, V.VMC_STORE_FP64)
     h2 = fresh()

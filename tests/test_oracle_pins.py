@@ -495,6 +495,49 @@ def test_apply_S_equals_dense_covariance():
     assert np.abs(g - g_np).max() < 1e-12 * max(1, np.abs(g_np).max())
 
 
+@pytest.mark.parametrize("shared", [False, True])
+def test_apply_S_compact_equals_dense_rows(shared):
+    """Eq. 7 from compact rows (occupation, correlator states, the N(N-1)/2
+    pairing values in the documented block order) equals Eq. 7 over the dense
+    O rows of the same samples.  The compact rows are first shown to be the
+    dense rows: scattered back to n_v entries they reproduce every entry of
+    the oracle's O (each correlator at 1/C of its state, each pairing value
+    at f_{occ[a] occ[b]}), so nothing is dropped or misplaced."""
+    from pair_blocks import block_pairs
+    if shared:
+        wl = inputs.hubbard("cmp", 3, 2, 2, 2, "2x2", seed=31, n_walkers=8, shared=True)
+    else:
+        wl = inputs.hubbard("cmp", 3, 2, 2, 2, "pair", seed=32, n_walkers=8)
+    P = oracle.Problem(wl)
+    occ = wl.init_occ.copy()
+    samples, _, _ = P.sample(occ, np.zeros(wl.n_walkers, np.uint64), 77, 4, 6)
+    _, O = P.measure(samples)
+    n, N, M, ncp = len(samples), wl.N, wl.M, wl.n_corr_params
+    pairs = block_pairs(wl.n_up, wl.n_dn)
+    cs = np.array([[P.corr_state(o, c) for c in range(wl.n_corr)] for o in samples], np.int64)
+    p = samples[:, pairs[:, 0]].astype(np.int64)
+    q = samples[:, pairs[:, 1]].astype(np.int64)
+    pq = ncp + p * M - p * (p + 1) // 2 + (q - p - 1)
+    pf = np.take_along_axis(O, pq, axis=1)
+    dense = np.zeros_like(O)
+    for s_ in range(n):
+        for c in range(wl.n_corr):
+            k = wl.corr_param_off[c] + cs[s_, c]
+            dense[s_, k] += 1.0 / wl.C[k]
+        dense[s_, pq[s_]] = pf[s_]
+    assert np.abs(dense - O).max() <= 1e-15 * max(1.0, np.abs(O).max())
+    rng = np.random.default_rng(3)
+    V = rng.standard_normal((2, wl.n_params))
+    for eps in (0.0, 1e-3):
+        out, Obar = oracle.apply_S_compact(P, samples, cs, pairs, pf, V, eps)
+        assert np.abs(Obar - O.mean(0)).max() <= 1e-14
+        for j in range(2):
+            ref = oracle.apply_S(O, V[j], eps)
+            assert np.linalg.norm(out[j] - ref) <= 1e-12 * np.linalg.norm(ref)
+    out1, _ = oracle.apply_S_compact(P, samples, cs, pairs, pf, V[1], 1e-3)
+    assert np.linalg.norm(out1 - oracle.apply_S(O, V[1], 1e-3)) <= 1e-12 * np.linalg.norm(out1)
+
+
 def test_cg_matches_direct_solve():
     wl, P, samples, E, O = _small_samples(seed=43, nw=32, spw=8)
     g, _ = oracle.gradient(O, E)

@@ -81,3 +81,34 @@ def test_noalloc_rejects_oversized_and_bad_strides():
     with pytest.raises(V.VmcError) as e:
         V.sr_pairing_product_noalloc(4, 2, 2, occ, pf, v)      # rows shorter than N / P
     assert e.value.code == -1
+
+
+def test_noalloc_skips_occupations_outside_the_sector():
+    """A caller-given occupation that is not a configuration of the sector
+    (an orbital beyond M, a repeated orbital, an up electron in the down
+    block) would index outside the pairing images; the kernel checks every
+    sample, gives it t_s = NaN and leaves it out of the sum, so the result
+    equals the product over the valid samples alone."""
+    wl = inputs.workload("hubbard4x4_pair", n_walkers=8, samples_per_walker=4)
+    n = 32
+    cfgs = inputs.draw_configs(np.random.default_rng(3), n, wl.n_sites, wl.n_up, wl.n_dn)
+    P = wl.n_up * (wl.n_up - 1) // 2 + wl.n_dn * (wl.n_dn - 1) // 2 + wl.n_up * wl.n_dn
+    pf = np.random.default_rng(4).standard_normal((n, P)).astype(np.float32)
+    v = np.random.default_rng(5).standard_normal(wl.n_pf_params).astype(np.float32)
+    bad = cfgs.copy()
+    bad[3, -1] = 2 * wl.n_sites + 5          # orbital beyond M - 1
+    bad[7, 1] = bad[7, 0]                    # repeated orbital (not ascending)
+    bad[11, 0] = wl.n_sites                  # an up electron in the down block
+    bad[11] = np.sort(bad[11])
+    good = np.setdiff1d(np.arange(n), [3, 7, 11])
+    to = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    t_all, out_all = V.sr_pairing_product_noalloc(wl.n_sites, wl.n_up, wl.n_dn, to(bad), to(pf), to(v))
+    t_good, out_good = V.sr_pairing_product_noalloc(wl.n_sites, wl.n_up, wl.n_dn, to(bad[good]), to(pf[good]),
+                                                     to(v))
+    torch.cuda.synchronize()
+    t_all = t_all.cpu().numpy()
+    assert np.isnan(t_all[[3, 7, 11]]).all()
+    assert np.isfinite(t_all[good]).all()
+    assert np.array_equal(t_all[good], t_good.cpu().numpy())
+    o1, o2 = out_all.cpu().numpy(), out_good.cpu().numpy()
+    assert np.linalg.norm(o1 - o2) <= 1e-5 * np.linalg.norm(o2)
