@@ -75,6 +75,10 @@ extern "C" {
                            same-spin / opposite-spin pairing), one four-vector
                            BF16 product per inner iteration, solution = column
                            sum; needs >= 2 correlators (else UNSUPPORTED)       */
+#define VMC_CG_MIXED64 4 /* like MIXED, but the flexible outer iteration and the
+                           reported true residual use the FP64 store (needs
+                           keep_fp64_store; pass g from sr_gradient over the FP64
+                           store): the residual is against the FP64 operator    */
 
 typedef struct vmc_ctx* vmc_handle;
 
@@ -128,6 +132,12 @@ typedef struct {
     int refresh_every;      /* sweeps between from-scratch rebuilds of each walker's
                                pairing inverse during vmc_sample (0: only at the start
                                of each call); bounds the drift of the rank-2 updates   */
+    int fp64_refresh;       /* FP32 walkers only, 1: after the chains have run, every
+                               stored sample's pairing inverse, log-amplitude, E_L and
+                               O are evaluated from scratch in FP64 and the stores are
+                               written from those values (FP32 / BF16 rounding of FP64
+                               results); the chains' own E_L is kept for
+                               vmc_sample_stats                                        */
 } vmc_options;
 
 typedef struct {
@@ -182,6 +192,25 @@ int vmc_get_walkers(vmc_handle h, uint8_t* occ, uint64_t* step, void* stream);
  * the pairing block of O into the handle's O store.  Errors: SINGULAR (a
  * walker's pairing submatrix could not be inverted), NONFINITE, CUDA. */
 int vmc_sample(vmc_handle h, int n_burn, uint64_t seed, void* stream);
+
+/* Health of the last vmc_sample (no counterpart in the paper).  Every chain
+ * sums ln|Psi'/Psi| over its accepted moves (FP64 sum of its ratios); for the
+ * stored samples j > 0 of walker w this running change is compared with the
+ * change of ln|Psi| evaluated from scratch in FP64 (vmc_logpsi):
+ *   drift = |(run_j - run_0) - (lnPsi_j - lnPsi_0)|,
+ * which measures the accumulated error of the rank-2 inverse updates and
+ * ratios.  With fp64_refresh, el_refresh_change is |E_L(chain) -
+ * E_L(FP64 refresh)| / max(1, |E_L(FP64 refresh)|) per sample.  Needs the
+ * samples of a vmc_sample call (n_walkers x samples_per_walker).  Errors:
+ * STATE. */
+typedef struct {
+    double lnpsi_drift_max;
+    double lnpsi_drift_mean;
+    int refreshed;                 /* 1 if the stored samples come from an FP64 refresh */
+    double el_refresh_change_max;
+    double el_refresh_change_mean;
+} vmc_sample_stats_t;
+int vmc_sample_stats(vmc_handle h, vmc_sample_stats_t* out, void* stream);
 
 /* Evaluate E_L and O for caller-given configurations occ[n_s][N] (host,
  * ascending, n_s <= n_walkers * samples_per_walker), recomputing each

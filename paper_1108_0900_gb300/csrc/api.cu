@@ -42,7 +42,7 @@ struct vmc_ctx {
     int64_t ncp = 0, nv = 0;
     int n_walkers = 0, spw = 0;
     int64_t ncap = 0, n_s = 0;
-    int wprec = VMC_FP64, keep64 = 1, keeplow = 0, refresh_every = 0;
+    int wprec = VMC_FP64, keep64 = 1, keeplow = 0, refresh_every = 0, fp64_refresh = 0;
     int ham = 0;
     int maxd = 1;
     bool params_set = false, walkers_set = false;
@@ -103,6 +103,10 @@ struct vmc_ctx {
     uint8_t* d_socc = nullptr;
     cstate_t *d_cidx = nullptr, *d_cidxT = nullptr;
     double* d_E = nullptr;
+    double* d_lnrun = nullptr;   // [ncap] chains' running ln|Psi| at each stored sample
+    double* d_Echain = nullptr;  // [ncap] E_L of the FP32 chains before an FP64 refresh
+    bool refreshed = false;      // the stored samples come from an FP64 refresh
+    double* d_lnps = nullptr;    // [ncap] scratch for vmc_sample_stats
     double* d_pf64 = nullptr;
     float* d_pf32 = nullptr;
     __nv_bfloat16* d_pf16 = nullptr;
@@ -214,6 +218,7 @@ extern "C" int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, co
     h->keep64 = opt->keep_fp64_store ? 1 : 0;
     h->keeplow = opt->keep_lowp_store ? 1 : 0;
     h->refresh_every = opt->refresh_every > 0 ? opt->refresh_every : 0;
+    h->fp64_refresh = (opt->fp64_refresh && opt->walker_precision == VMC_FP32) ? 1 : 0;
     h->ham = ham->kind;
     auto fail = [&](int code) { vmc_destroy(h); return code; };
     if (h->ncap > (int64_t)1 << 31) return fail(VMC_ERR_INVALID_ARG);
@@ -465,6 +470,8 @@ extern "C" int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, co
     ACK(h->alloc(&h->d_cidx, (size_t)h->ncap * h->ncst));
     ACK(h->alloc(&h->d_cidxT, (size_t)h->ncap * std::max(h->ncorr, 1)));
     ACK(h->alloc(&h->d_E, h->ncap));
+    ACK(h->alloc(&h->d_lnrun, h->ncap));
+    if (h->fp64_refresh) ACK(h->alloc(&h->d_Echain, h->ncap));
     if (h->keep64) ACK(h->alloc(&h->d_pf64, (size_t)h->ncap * h->Pst));
     if (h->keeplow) {
         ACK(h->alloc(&h->d_pf32, (size_t)h->ncap * h->Pst));
@@ -706,6 +713,7 @@ static void store_targets(vmc_ctx* h, SampleArgs& a) {
     a.s_occ = h->d_socc; a.Nst = h->Nst;
     a.s_cidx = h->d_cidx; a.ncst = h->ncst;
     a.s_E = h->d_E;
+    a.s_lnrun = h->d_lnrun;
     a.s_pf64 = h->keep64 ? h->d_pf64 : nullptr;
     a.s_pf32 = h->keeplow ? h->d_pf32 : nullptr;
     a.s_pf16 = h->keeplow ? h->d_pf16 : nullptr;
@@ -741,6 +749,24 @@ extern "C" int vmc_sample(vmc_handle h, int n_burn, uint64_t seed, void* stream)
     h->n_s = h->ncap;
     h->obar_ok[0] = h->obar_ok[1] = h->obar_ok[2] = false;
     h->sorted_ok = h->g_ok = h->corr_ok = false;
+    h->refreshed = false;
+    if (h->wprec == VMC_FP32 && h->fp64_refresh) {
+        // FP64 refresh of every stored sample: the pairing inverse, E_L and O
+        // from scratch in FP64, rounded into the stores; the chains' own E_L
+        // is kept for the statistics
+        VCK(cudaMemcpyAsync(h->d_Echain, h->d_E, sizeof(double) * h->n_s, cudaMemcpyDeviceToDevice, st));
+        VCK(cudaMemcpy2DAsync(h->d_mocc, h->N, h->d_socc, h->Nst, h->N, h->n_s, cudaMemcpyDeviceToDevice, st));
+        SampleArgs m{};
+        m.n_walkers = (int)h->n_s;
+        m.spw = 1;
+        m.want_energy = 1;
+        m.walker_occ = h->d_mocc;
+        store_targets(h, m);
+        m.s_lnrun = nullptr;   // keep the chains' running log-amplitudes
+        rc = launch_walkers(h, m, true, st);
+        if (rc) return rc;
+        h->refreshed = true;
+    }
     rc = transpose_states(h, st);
     if (rc) return rc;
     return read_status(h, st);
@@ -778,6 +804,51 @@ extern "C" int vmc_measure(vmc_handle h, const uint8_t* occ, int64_t n_s, void* 
     rc = transpose_states(h, st);
     if (rc) return rc;
     return read_status(h, st);
+}
+
+extern "C" int vmc_sample_stats(vmc_handle h, vmc_sample_stats_t* out, void* stream) {
+    if (!h || !out) return VMC_ERR_INVALID_ARG;
+    if (h->n_s == 0 || h->spw < 1 || h->n_s != (int64_t)h->n_walkers * h->spw) return VMC_ERR_STATE;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = h->n_s;
+    if (!h->d_lnps) VCK(h->alloc(&h->d_lnps, h->ncap));
+    double* lnps = h->d_lnps;
+    int rc = vmc_logpsi(h, lnps, stream);
+    if (rc) return rc;
+    std::vector<double> lp(n), lr(n), E(n), Ec;
+    VCK(cudaMemcpyAsync(lp.data(), lnps, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+    VCK(cudaMemcpyAsync(lr.data(), h->d_lnrun, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+    VCK(cudaMemcpyAsync(E.data(), h->d_E, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+    if (h->refreshed) {
+        Ec.resize(n);
+        VCK(cudaMemcpyAsync(Ec.data(), h->d_Echain, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+    }
+    VCK(cudaStreamSynchronize(st));
+    vmc_sample_stats_t r{};
+    double sd = 0.0, se = 0.0;
+    int64_t cnt = 0;
+    for (int64_t w = 0; w < h->n_walkers; ++w) {
+        const int64_t s0 = w * h->spw;
+        for (int j = 1; j < h->spw; ++j) {
+            const int64_t s = s0 + j;
+            const double d = std::fabs((lr[s] - lr[s0]) - (lp[s] - lp[s0]));
+            r.lnpsi_drift_max = std::max(r.lnpsi_drift_max, d);
+            sd += d;
+            ++cnt;
+        }
+    }
+    r.lnpsi_drift_mean = cnt ? sd / cnt : 0.0;
+    r.refreshed = h->refreshed ? 1 : 0;
+    if (h->refreshed) {
+        for (int64_t s = 0; s < n; ++s) {
+            const double d = std::fabs(Ec[s] - E[s]) / std::max(1.0, std::fabs(E[s]));
+            r.el_refresh_change_max = std::max(r.el_refresh_change_max, d);
+            se += d;
+        }
+        r.el_refresh_change_mean = se / n;
+    }
+    *out = r;
+    return VMC_OK;
 }
 
 extern "C" int vmc_get_samples(vmc_handle h, uint8_t* occ, double* E_L, uint32_t* corr_state, double* pf,
@@ -1111,6 +1182,24 @@ static bool sorted_usable(const vmc_ctx* h) {
     return gather_kernel<K>((int)((h->Gst / 4 + 31) / 32)) != nullptr;
 }
 
+// correlator half of the single pass's finish as shared-memory histograms
+// when every class's 4^m amplitudes (K values each) fit 64 KB: (class, slice)
+// CTAs with about two CTAs per SM in total; else the correlator work items
+static size_t corr_hist_setup(const vmc_ctx* h, int K, SortedArgs* a) {
+    a->cidxT = h->d_cidxT;
+    a->nhist = 0;
+    a->hist_slices = 1;
+    if (h->ncorr == 0) { a->ncb = 0; return 0; }
+    const size_t bytes = (size_t)h->maxd * K * sizeof(float);
+    if (bytes > 65536) { a->ncb = (int)((h->max_items + 7) / 8); return 0; }
+    const int64_t by_n = std::max<int64_t>(1, h->n_s / 1024);
+    const int nsl = (int)std::max<int64_t>(1, std::min<int64_t>(by_n, (2 * h->nsm + h->n_class - 1) / h->n_class));
+    a->hist_slices = nsl;
+    a->nhist = h->n_class * nsl;
+    a->ncb = 0;
+    return bytes;
+}
+
 // gather + parameter-major scatter for the BF16 store; the centered t_s go to
 // Tv, the pairing sums to d_pfraw and the correlator sums to d_corrraw (FP32)
 template <int K>
@@ -1139,7 +1228,13 @@ static int launch_sorted(vmc_ctx* h, const float* V, const float* invC, const do
     a.Tc = h->d_Tc; a.cbase = h->d_cbase; a.craw = (float*)h->d_corrraw;
     a.items = h->d_items;
     a.n_items = h->d_item_base + (h->ncp + 31) / 32;
+    // the correlator work items run beside the long pairing runs of the
+    // scatter (measured faster there than the histograms)
+    a.cidxT = h->d_cidxT;
+    a.nhist = 0;
+    a.hist_slices = 1;
     a.ncb = h->ncorr > 0 ? (int)((h->max_items + 7) / 8) : 0;
+    const size_t hsm = 0;
     a.tt_part = tt_part;
     a.stop = stop;
     const size_t smem = (size_t)h->npf * K * 4 + (size_t)(h->ncorr + 1) * 4;
@@ -1157,7 +1252,8 @@ static int launch_sorted(vmc_ctx* h, const float* V, const float* invC, const do
     // correlator sums accumulate into zero (the fused CG update re-zeroes
     // them as it reads them, so its products skip this)
     if (h->ncp > 0 && !craw_zero) VCK(cudaMemsetAsync(h->d_corrraw, 0, sizeof(float) * h->ncp * K, st));
-    k_scatter_T<K><<<a.ncb + (h->npf + 7) / 8, 256, 0, st>>>(a); h->n_launch++;
+    if (hsm) VCK(cudaFuncSetAttribute(k_scatter_T<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm));
+    k_scatter_T<K><<<a.nhist + a.ncb + (h->npf + 7) / 8, 256, hsm, st>>>(a); h->n_launch++;
     VCK(cudaGetLastError());
     if (h->prof) {
         VCK(cudaEventRecord(rec.b, st));
@@ -1212,7 +1308,7 @@ static int launch_fused(vmc_ctx* h, const float* V, const float* invC, const dou
     a.Tc = h->d_Tc; a.cbase = h->d_cbase; a.craw = (float*)h->d_corrraw;
     a.items = h->d_items;
     a.n_items = h->d_item_base + (h->ncp + 31) / 32;
-    a.ncb = h->ncorr > 0 ? (int)((h->max_items + 7) / 8) : 0;
+    const size_t hsm = corr_hist_setup(h, 1, &a);
     a.tt_part = tt_part;
     a.stop = stop;
     const size_t smem = fused_smem(h);
@@ -1224,7 +1320,9 @@ static int launch_fused(vmc_ctx* h, const float* V, const float* invC, const dou
     VCK(cudaGetLastError());
     h->last_fused_grid = grid;
     if (h->ncp > 0 && !craw_zero) VCK(cudaMemsetAsync(h->d_corrraw, 0, sizeof(float) * h->ncp, st));
-    k_sv_finish<<<a.ncb + (h->npf + 255) / 256, 256, 0, st>>>(a, (const float*)h->d_pfpart, grid); h->n_launch++;
+    if (hsm) VCK(cudaFuncSetAttribute(k_sv_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm));
+    k_sv_finish<<<a.nhist + a.ncb + (h->npf + 255) / 256, 256, hsm, st>>>(a, (const float*)h->d_pfpart, grid);
+    h->n_launch++;
     VCK(cudaGetLastError());
     if (h->prof) {
         VCK(cudaEventRecord(rec.b, st));
@@ -1697,7 +1795,7 @@ static int inner_solve(vmc_ctx* h, int mode, const double* r, double rnorm, doub
     }
     k_cast<float><<<kNumPart, 256, 0, st>>>(r, h->d_b32, h->nv, 1.0 / rnorm); h->n_launch++;
     VCK(cudaGetLastError());
-    int rc = mode == VMC_CG_MIXED
+    int rc = (mode == VMC_CG_MIXED || mode == VMC_CG_MIXED64)
                  ? cg_loop<__nv_bfloat16, float>(h, h->d_pf16, 2, h->d_b32, h->d_x32, h->d_r32, h->d_p32,
                                                 h->d_q32, shift, itol, max_iter, iters, st)
                  : cg_loop<float, float>(h, h->d_pf32, 1, h->d_b32, h->d_x32, h->d_r32, h->d_p32, h->d_q32,
@@ -1846,8 +1944,12 @@ static int fcg_mixed(vmc_ctx* h, const double* g, double shift, double tol, int 
     VCK(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
     double zr = dot64(h, z, r, st, &rc);
     if (rc) return rc;
+    // the outer operator: the FP64 store (MIXED64) or the FP32 store with
+    // FP64 accumulation
+    const bool outer64 = mode == VMC_CG_MIXED64;
     for (int outer = 0; outer < 200; ++outer) {
-        rc = apply_S_impl<float, double, 1>(h, h->d_pf32, 1, p, q, shift, nullptr, nullptr, nullptr, st);
+        rc = outer64 ? apply_S_impl<double, double, 1>(h, h->d_pf64, 0, p, q, shift, nullptr, nullptr, nullptr, st)
+                     : apply_S_impl<float, double, 1>(h, h->d_pf32, 1, p, q, shift, nullptr, nullptr, nullptr, st);
         if (rc) return rc;
         inf->residual_products++;
         double pq = dot64(h, p, q, st, &rc);
@@ -1875,9 +1977,10 @@ static int fcg_mixed(vmc_ctx* h, const double* g, double shift, double tol, int 
         VCK(cudaGetLastError());
         zr = zr_new;
     }
-    // true residual of the returned x, FP64 accumulation over the FP32 store
+    // true residual of the returned x, FP64 accumulation over the outer store
     double rt = 0.0;
-    rc = residual64<float>(h, h->d_pf32, 1, g, x, h->d_r64, shift, &rt, st);
+    rc = outer64 ? residual64<double>(h, h->d_pf64, 0, g, x, h->d_r64, shift, &rt, st)
+                 : residual64<float>(h, h->d_pf32, 1, g, x, h->d_r64, shift, &rt, st);
     if (rc) return rc;
     inf->residual_products++;
     inf->iterations = used;
@@ -1909,8 +2012,13 @@ extern "C" int sr_cg_solve(vmc_handle h, const double* g, double shift, double t
         inf.iterations = it;
         inf.residual_products = 1;
         inf.true_rel_residual = gn2 > 0 ? std::sqrt(rr / gn2) : 0.0;
-    } else if (mode == VMC_CG_MIXED || mode == VMC_CG_FP32 || mode == VMC_CG_BLOCK4) {
+    } else if (mode == VMC_CG_MIXED || mode == VMC_CG_FP32 || mode == VMC_CG_BLOCK4 || mode == VMC_CG_MIXED64) {
         if (!h->d_pf32 || !h->d_pf16) return VMC_ERR_STATE;
+        if (mode == VMC_CG_MIXED64) {
+            if (!h->d_pf64) return VMC_ERR_STATE;
+            rc = ensure_obar(h, 0, st);
+            if (rc) return rc;
+        }
         if (mode == VMC_CG_BLOCK4) {
             // the four parameter groups must all be non-empty
             const int64_t split = h->ncorr >= 2 ? h->corr_off[h->ncorr / 2] : 0;

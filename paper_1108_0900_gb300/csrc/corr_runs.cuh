@@ -28,6 +28,36 @@ __device__ __forceinline__ void corr_lookups(const DevProblem& pb, const int* co
     }
 }
 
+// Correlator half of the transposed product as a weighted histogram: CTA
+// (class q, slice j) adds the centered t_s of its slice of the samples at
+// the state of every correlator of class q into a shared-memory histogram of
+// the class's 4^m amplitudes, then adds each nonzero bin to craw (one global
+// atomic per bin and slice).  The states are read correlator-major
+// (coalesced), t_s sample-major.
+template <int K>
+__device__ __forceinline__ void corr_hist_cta(const SortedArgs& a, int q, int j, int nsl, float* hist) {
+    const DevProblem& pb = a.pb;
+    const int64_t off = pb.class_off[q];
+    const int d = (int)(pb.class_off[q + 1] - off);
+    for (int i = threadIdx.x; i < d * K; i += blockDim.x) hist[i] = 0.f;
+    __syncthreads();
+    const int64_t per = (a.n_s + nsl - 1) / nsl;
+    const int64_t s0 = min(a.n_s, (int64_t)j * per), s1 = min(a.n_s, s0 + per);
+    for (int ci = pb.class_ptr[q]; ci < pb.class_ptr[q + 1]; ++ci) {
+        const cstate_t* st = a.cidxT + (int64_t)pb.class_inst[ci] * a.n_s;
+        for (int64_t s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+            const int k = (int)st[s];
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) atomicAdd(&hist[k * K + kk], a.Tv[s * K + kk]);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < d * K; i += blockDim.x) {
+        const float v = hist[i];
+        if (v != 0.f) atomicAdd(a.craw + off * K + i, v);
+    }
+}
+
 // Correlator work item (group g, entries e0 .. min(e0 + kCorrItem, end of g)):
 // the group's parameters 32 g .. 32 g + 31 have contiguous runs, read as one
 // coalesced stream; entries carry k mod 32, equal values are contiguous, and

@@ -174,18 +174,27 @@ __global__ void __launch_bounds__(kFusedWarps * 32, 1) k_sv_fused(SortedArgs a, 
     }
 }
 
-// Correlator half of the transposed product (CTAs [0, ncb): 8 work items of
-// the correlator runs each) and the sum of the per-CTA pairing images (the
-// other CTAs, one pairing amplitude per thread, CTAs in a fixed order).
+// Correlator half of the transposed product (CTAs [0, nhist): shared-memory
+// histograms of (class, sample slice); or, for classes too large for shared
+// memory, CTAs [0, ncb): 8 work items of the correlator runs each) and the sum
+// of the per-CTA pairing images (the other CTAs, one pairing amplitude per
+// thread, CTAs in a fixed order).
 __global__ void __launch_bounds__(256) k_sv_finish(SortedArgs a, const float* pf_partial, int nblk) {
     if (a.stop && *a.stop) return;
+    extern __shared__ __align__(16) unsigned char hist_smem[];
     __shared__ float slots[8][32];
-    if ((int)blockIdx.x < a.ncb) {
-        const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    int b = (int)blockIdx.x;
+    if (b < a.nhist) {
+        corr_hist_cta<1>(a, b / a.hist_slices, b % a.hist_slices, a.hist_slices, (float*)hist_smem);
+        return;
+    }
+    b -= a.nhist;
+    if (b < a.ncb) {
+        const int64_t i = (int64_t)b * 8 + (threadIdx.x >> 5);
         if (i < (int64_t)*a.n_items) scatter_C_item<1>(a, a.items[i], slots[threadIdx.x >> 5]);
         return;
     }
-    const int pq = ((int)blockIdx.x - a.ncb) * blockDim.x + threadIdx.x;
+    const int pq = (b - a.ncb) * blockDim.x + threadIdx.x;
     if (pq >= a.pb.npf) return;
     const int npf = a.pb.npf;
     // 16 independent loads in flight per thread, summed in a fixed order

@@ -32,6 +32,7 @@ struct SampleArgs {
     cstate_t* s_cidx;     // [n_s][ncst]
     int ncst;
     double* s_E;
+    double* s_lnrun;      // [n_s] the chain's running ln|Psi| since the call started (may be null)
     double* s_pf64;
     float* s_pf32;
     __nv_bfloat16* s_pf16;
@@ -260,6 +261,12 @@ struct SortedArgs {
     float* craw;            // [ncp][K] correlator sums (without the 1/C factor), zeroed by the caller
     double* tt_part;        // [gridDim] partial sums of centered t_s^2 (K = 1; may be null)
     const int* stop;
+    // correlator half as shared-memory histograms: CTAs [0, nhist) take
+    // (class, sample slice) = (b / hist_slices, b % hist_slices); when nhist is
+    // 0 the ncb CTAs of correlator work items do it instead
+    int nhist;
+    int hist_slices;
+    const cstate_t* cidxT;  // [ncorr][n_s] correlator states, correlator-major
 };
 
 constexpr int kCorrPerLane = 4;    // the sorted gather handles up to 128 correlators

@@ -14,7 +14,9 @@
 // Woodbury capacitance is r I, so
 //   X' = X + (c y^T - y c^T) / r,  c = X_{:,a},  y = X b + e_a.
 // The inverse is rebuilt from scratch (Gauss-Jordan, partial pivoting) at
-// the start of every call.
+// the start of every call.  The chain also sums ln|ratio| of its accepted
+// moves (FP64), the running log-amplitude that a from-scratch evaluation of
+// the stored samples checks (vmc_sample_stats).
 #include "ansatz.cuh"
 #include "common.cuh"
 #include "kernels.h"
@@ -404,6 +406,7 @@ __global__ void k_walkers(SampleArgs a) {
 
     const uint64_t sitemask = (ns == 64) ? ~0ull : ((1ull << ns) - 1ull);
     uint64_t step = a.walker_step ? a.walker_step[w] : 0ull;
+    double lnrun = 0.0;   // ln|Psi| of the chain relative to its start, summed from the accepted ratios
     const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
     const int n_sweeps = a.n_burn + a.spw;
 
@@ -433,6 +436,7 @@ __global__ void k_walkers(SampleArgs a) {
             R ratio = rpf * rc;
             bool accept = u < ratio * ratio;
             if (!accept) continue;
+            lnrun += log(fabs((double)ratio));
             __syncwarp();
             for (int i = lane; i < N; i += 32) {
                 R yi = R(0);
@@ -526,6 +530,7 @@ __global__ void k_walkers(SampleArgs a) {
             }
         } else {
             if (a.s_E && lane == 0) a.s_E[s] = e_lane;
+            if (a.s_lnrun && lane == 0) a.s_lnrun[s] = lnrun;
             if (a.s_cidx)
                 for (int c = lane; c < pb.ncorr; c += 32) a.s_cidx[s * a.ncst + c] = (cstate_t)cidx[c];
             for (int e = lane; e < pb.P; e += 32) {

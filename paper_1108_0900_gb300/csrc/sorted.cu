@@ -446,20 +446,28 @@ __device__ __forceinline__ void scatter_T_param(const SortedArgs& a, int pq) {
     }
 }
 
-// Both halves of the scatter in one launch: CTAs [0, ncb) take 8 correlator
-// work items each (a warp per item), the rest one pairing amplitude per
-// warp.  The short correlator CTAs go first so that they do not form a tail
-// behind the long pairing runs.
+// Both halves of the scatter in one launch: the correlator CTAs first
+// (histograms of [0, nhist), or correlator work items of [0, ncb), 8 per CTA,
+// a warp per item), then one pairing amplitude per warp.  The short
+// correlator CTAs go first so that they do not form a tail behind the long
+// pairing runs.
 template <int K>
 __global__ void __launch_bounds__(256) k_scatter_T(SortedArgs a) {
     if (a.stop && *a.stop) return;
+    extern __shared__ __align__(16) unsigned char hist_smem[];
     __shared__ float slots[8][32 * K];
-    if ((int)blockIdx.x < a.ncb) {
-        const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    int b = (int)blockIdx.x;
+    if (b < a.nhist) {
+        corr_hist_cta<K>(a, b / a.hist_slices, b % a.hist_slices, a.hist_slices, (float*)hist_smem);
+        return;
+    }
+    b -= a.nhist;
+    if (b < a.ncb) {
+        const int64_t i = (int64_t)b * 8 + (threadIdx.x >> 5);
         if (i < (int64_t)*a.n_items) scatter_C_item<K>(a, a.items[i], slots[threadIdx.x >> 5]);
         return;
     }
-    const int pq = ((int)blockIdx.x - a.ncb) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int pq = (b - a.ncb) * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (pq < a.pb.npf) scatter_T_param<K>(a, pq);
 }
 

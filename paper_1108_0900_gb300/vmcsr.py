@@ -26,7 +26,7 @@ VMC_OK = 0
 VMC_HUBBARD, VMC_ABINITIO = 0, 1
 VMC_FP64, VMC_FP32 = 0, 1
 VMC_STORE_FP64, VMC_STORE_FP32, VMC_STORE_BF16, VMC_STORE_FP32_F32ACC = 0, 1, 2, 3
-VMC_CG_FP64, VMC_CG_MIXED, VMC_CG_FP32, VMC_CG_BLOCK4 = 0, 1, 2, 3
+VMC_CG_FP64, VMC_CG_MIXED, VMC_CG_FP32, VMC_CG_BLOCK4, VMC_CG_MIXED64 = 0, 1, 2, 3, 4
 ERRORS = {
     -1: "INVALID_ARG", -2: "OOM", -3: "SINGULAR", -4: "NONFINITE", -5: "NOT_CONVERGED",
     -6: "TIMEOUT", -7: "CUDA", -8: "UNSUPPORTED", -9: "STATE",
@@ -55,7 +55,13 @@ class vmc_ansatz(ct.Structure):
 
 class vmc_options(ct.Structure):
     _fields_ = [("n_walkers", ct.c_int), ("samples_per_walker", ct.c_int), ("walker_precision", ct.c_int),
-                ("keep_fp64_store", ct.c_int), ("keep_lowp_store", ct.c_int), ("refresh_every", ct.c_int)]
+                ("keep_fp64_store", ct.c_int), ("keep_lowp_store", ct.c_int), ("refresh_every", ct.c_int),
+                ("fp64_refresh", ct.c_int)]
+
+
+class vmc_sample_stats_t(ct.Structure):
+    _fields_ = [("lnpsi_drift_max", ct.c_double), ("lnpsi_drift_mean", ct.c_double), ("refreshed", ct.c_int),
+                ("el_refresh_change_max", ct.c_double), ("el_refresh_change_mean", ct.c_double)]
 
 
 class vmc_lm_info(ct.Structure):
@@ -125,6 +131,7 @@ def lib(build_if_missing: bool = True):
         "vmc_set_product_path": [vp, i32],
         "sr_autotune": [vp, i32, vp, vp],
         "vmc_set_auto_paths": [vp, i32, i32],
+        "vmc_sample_stats": [vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -167,7 +174,7 @@ def _stream(stream=None):
 # ---------------------------------------------------------------------------
 
 def vmc_create(wl, n_walkers=None, samples_per_walker=None, walker_precision=VMC_FP64,
-               keep_fp64_store=True, keep_lowp_store=False, refresh_every=0):
+               keep_fp64_store=True, keep_lowp_store=False, refresh_every=0, fp64_refresh=False):
     """Create a handle for a problem description (``inputs.Workload``)."""
     keep = dict(
         bonds=np.ascontiguousarray(wl.bonds, np.int32),
@@ -185,7 +192,7 @@ def vmc_create(wl, n_walkers=None, samples_per_walker=None, walker_precision=VMC
                      _np_ptr(keep["corr_class"]))
     opt = vmc_options(int(n_walkers or wl.n_walkers), int(samples_per_walker or wl.samples_per_walker),
                       int(walker_precision), int(bool(keep_fp64_store)), int(bool(keep_lowp_store)),
-                      int(refresh_every))
+                      int(refresh_every), int(bool(fp64_refresh)))
     h = ct.c_void_p()
     _check(lib().vmc_create(ct.byref(lat), ct.byref(ham), ct.byref(ans), ct.byref(opt), ct.byref(h)), "vmc_create")
     return Handle(h, wl, opt)
@@ -273,6 +280,14 @@ def load_state(h: Handle, path: str) -> dict:
 
 def vmc_sample(h: Handle, n_burn: int, seed: int, stream=None):
     _check(lib().vmc_sample(h.h, int(n_burn), ct.c_uint64(seed), _stream(stream)), "vmc_sample")
+
+
+def vmc_sample_stats(h: Handle, stream=None) -> dict:
+    """Drift of the chains' running ln|Psi| against FP64 from-scratch values
+    and, with fp64_refresh, the change of E_L made by the refresh."""
+    r = vmc_sample_stats_t()
+    _check(lib().vmc_sample_stats(h.h, ct.byref(r), _stream(stream)), "vmc_sample_stats")
+    return {k: getattr(r, k) for k, _ in r._fields_}
 
 
 def vmc_measure(h: Handle, occ, stream=None):
@@ -443,7 +458,7 @@ def sr_optimize(h: Handle, n_iter: int, tau: float, shift: float, tol: float, mo
     """The SR loop of Sec. II.A: sample, gradient, CG solve of Eq. 2, update;
     returns one record per iteration (energy statistics before the update,
     CG info, x_0).  The walkers must be set and thermalised."""
-    store = VMC_STORE_FP64 if mode == VMC_CG_FP64 else VMC_STORE_FP32
+    store = VMC_STORE_FP64 if mode in (VMC_CG_FP64, VMC_CG_MIXED64) else VMC_STORE_FP32
     hist = []
     for it in range(n_iter):
         vmc_sample(h, 0, seed + it)
