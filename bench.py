@@ -98,10 +98,20 @@ class Clocks:
 # GPU arm
 # ---------------------------------------------------------------------------
 
-# DRAM bytes read per sorted BF16 product (k_gather_G + k_scatter_T launches) on
-# this workload, as counted by ncu (dram__bytes): G 427 MB + T and correlator
-# runs 428 MB.
-SORTED_PASS_DRAM_BYTES = 855.0e6
+# DRAM bytes per BF16 product on this workload, counted by ncu
+# (dram__bytes_read + dram__bytes_write, one capture per path): the sorted
+# two-pass product reads G (426 MB) and T with the correlator runs (425 MB);
+# the fused single pass reads G once (426 MB) plus the per-CTA images and the
+# correlator states in its finish (24 MB).
+PASS_DRAM_BYTES = {"sorted": 851.0e6, "fused": 453.0e6}
+PASS_KERNELS = {"sorted": "k_gather_G<1,U> + k_scatter_T<1> (sorted two-pass Eq. 7 product, BF16 store)",
+                "fused": "k_sv_fused<U> + k_sv_finish (fused single-pass Eq. 7 product, BF16 store)",
+                "staged": "k_sr_stream<bf16,1> + k_corr_scatter + k_reduce_pf (staged per-sample pass)",
+                "generic": "k_sr_main<bf16,float,1> + k_corr_scatter + k_reduce_pf (generic per-sample pass)"}
+# nominal FP64 (non-tensor) rate of one GB300 (the peaks file measures no FP64)
+FP64_PEAK_TFLOPS = 1.25
+AUTOTUNE_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1108_0900_gb300", "_build",
+                              "autotune.json")
 
 
 def run_gpu(args, rank, world, dist):
@@ -121,25 +131,27 @@ def run_gpu(args, rank, world, dist):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def make(path):
-        prec = V.VMC_FP32 if path == "mixed" else V.VMC_FP64
-        h = V.vmc_create(wl, walker_precision=prec, keep_fp64_store=(path == "fp64"),
-                         keep_lowp_store=(path == "mixed"))
-        V.vmc_set_params(h, wl.C, wl.f)
-        V.vmc_set_walkers(h, wl.init_occ)
-        V.vmc_sample(h, wl.burn_in_sweeps, seed)      # thermalisation, outside every timed region
+    def make(path, w=None):
+        w = w or wl
+        prec = V.VMC_FP64 if path == "fp64" else V.VMC_FP32
+        h = V.vmc_create(w, walker_precision=prec, keep_fp64_store=path in ("fp64", "refresh64"),
+                         keep_lowp_store=path != "fp64", fp64_refresh=path == "refresh64")
+        V.vmc_set_params(h, w.C, w.f)
+        V.vmc_set_walkers(h, w.init_occ)
+        V.vmc_sample(h, w.burn_in_sweeps, seed)       # thermalisation, outside every timed region
         return h
 
     def step(h, path, k, info_out):
         V.vmc_sample(h, 0, seed + 1 + k)
-        store = V.VMC_STORE_FP64 if path == "fp64" else V.VMC_STORE_FP32
+        store = V.VMC_STORE_FP64 if path in ("fp64", "refresh64") else V.VMC_STORE_FP32
         g, _ = V.sr_gradient(h, store, stats=False)
-        mode = {"mixed": V.VMC_CG_MIXED, "block4": V.VMC_CG_BLOCK4}.get(path, V.VMC_CG_FP64)
+        mode = {"mixed": V.VMC_CG_MIXED, "block4": V.VMC_CG_BLOCK4,
+                "refresh64": V.VMC_CG_MIXED64}.get(path, V.VMC_CG_FP64)
         x, info = V.sr_cg_solve(h, g, shift, tol, max_iter, mode, allow_not_converged=True)
         info_out.append(info)
         return x
 
-    def timed(h, path, steps, warmup, profile=False):
+    def timed(h, path, steps, warmup, profile=False, store=None):
         infos = []
         for k in range(warmup):
             step(h, path, k, infos)
@@ -155,13 +167,21 @@ def run_gpu(args, rank, world, dist):
             e1.record()
             barrier()
         ms = e0.elapsed_time(e1) / steps
-        prof = V.vmc_profile_read(h, V.VMC_STORE_BF16) if profile else None
+        if store is None:
+            store = V.VMC_STORE_FP64 if path == "fp64" else V.VMC_STORE_BF16
+        prof = V.vmc_profile_read(h, store) if profile else None
         if profile:
             V.vmc_profile(h, False)
         return ms, infos, prof, clk.summary()
 
+    def tune(h, key):
+        V.vmc_sample(h, 0, seed + 991)
+        V.sr_gradient(h, V.VMC_STORE_BF16, stats=False)
+        return V.tuned(h, AUTOTUNE_CACHE, key)
+
     # ---- mixed path (headline) ----------------------------------------------
     hm = make("mixed")
+    tuning = tune(hm, f"hubbard8x8_2x3:{wl.n_samples}")
     ms, infos, prof, clocks = timed(hm, "mixed", args.steps, args.warmup, profile=True)
     if dist is not None:
         t = torch.tensor([ms], device="cuda")
@@ -180,6 +200,31 @@ def run_gpu(args, rank, world, dist):
                  if prof_b and prof_b["pass_launches"] else None,
                  "true_rel_residual": max(i["true_rel_residual"] for i in infos_b),
                  "converged": all(i["converged"] for i in infos_b)}
+
+    # ---- the same step with the FP64 refresh of the stored samples and the
+    # mixed solve reporting its residual against the FP64 operator -----------
+    refresh = None
+    if args.refresh_steps > 0:
+        hr = make("refresh64")
+        ms_r, infos_r, _, _ = timed(hr, "refresh64", args.refresh_steps, 1)
+        st = V.vmc_sample_stats(hr)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record()
+        V.vmc_sample(hr, 0, seed + 4242)
+        e1.record()
+        barrier()
+        ms_walk_r = e0.elapsed_time(e1)
+        refresh = {"ms_per_step": round(ms_r, 3),
+                   "sample_with_fp64_refresh_ms": round(ms_walk_r, 3),
+                   "cg": "VMC_CG_MIXED64: BF16 inner products, outer iteration and true residual over the FP64 store",
+                   "true_rel_residual_vs_fp64_operator": max(i["true_rel_residual"] for i in infos_r),
+                   "converged": all(i["converged"] for i in infos_r),
+                   "cg_inner_iterations": float(np.mean([i["iterations"] for i in infos_r])),
+                   "fp32_chain_lnpsi_drift": {"max": st["lnpsi_drift_max"], "mean": st["lnpsi_drift_mean"]},
+                   "fp32_chain_el_error_removed_by_refresh": {"max": st["el_refresh_change_max"],
+                                                              "mean": st["el_refresh_change_mean"]}}
+        hr.close()
 
     # ---- end to end through the public API with host buffers ----------------
     import ctypes as ct
@@ -296,18 +341,57 @@ def run_gpu(args, rank, world, dist):
         ha.close()
 
     # ---- plain FP64 path ------------------------------------------------------
+    peak, peak_kind = peaks()
     fp64 = None
     if not args.no_fp64:
         hf = make("fp64")
-        ms64, infos64, _, clocks64 = timed(hf, "fp64", max(1, args.fp64_steps), 1)
+        ms64, infos64, prof64, clocks64 = timed(hf, "fp64", max(1, args.fp64_steps), 1, profile=True)
+        V.vmc_profile(hf, True)
+        for _ in range(3):
+            V.sr_apply_S(hf, torch.ones(wl.n_params, dtype=torch.float64, device="cuda"), shift, V.VMC_STORE_FP64)
+        p64 = V.vmc_profile_read(hf, V.VMC_STORE_FP64)
+        V.vmc_profile(hf, False)
+        ms_p64 = p64["pass_ms"] / max(1, p64["pass_launches"])
+        # FP64 FMAs of one product: t_s and t_s O_s over n_corr + P entries per sample
+        fma = 2.0 * wl.n_samples * (wl.n_corr + wl.n_pf_block)
         fp64 = {"ms_per_step": round(ms64, 3),
                 "cg_iterations": float(np.mean([i["iterations"] for i in infos64])),
                 "true_rel_residual": max(i["true_rel_residual"] for i in infos64),
-                "converged": all(i["converged"] for i in infos64)}
+                "converged": all(i["converged"] for i in infos64),
+                "roofline": {"bound": "alu", "kernel": "k_sr_main<double,double,1> (FP64 store, FP64 FMA)",
+                             "product_ms": round(ms_p64, 4),
+                             "achieved": round(2 * fma / (ms_p64 * 1e-3) / 1e12, 3), "unit": "TFLOP/s",
+                             "peak": FP64_PEAK_TFLOPS, "peak_kind": "nominal FP64 rate of the GB300",
+                             "frac": round(2 * fma / (ms_p64 * 1e-3) / 1e12 / FP64_PEAK_TFLOPS, 4),
+                             "hbm_gbs": round(p64["pass_bytes"] / max(1, p64["pass_launches"]) / (ms_p64 * 1e-3) / 1e9, 1),
+                             "hbm_frac": round(p64["pass_bytes"] / max(1, p64["pass_launches"])
+                                               / (ms_p64 * 1e-3) / 1e9 / peak, 4)}}
         hf.close()
 
-    peak, peak_kind = peaks()
+    # ---- the other workloads: the same SR step (mixed and FP64) ---------------
+    configs = None
+    if args.config_steps > 0:
+        configs = {}
+        for name in ("hubbard4x4_pair", "hubbard4x4_2x2", "hubbard8x8_2x2"):
+            wlc = inputs.workload(name)
+            row = {"n_params": wlc.n_params, "n_samples": wlc.n_samples}
+            for path in ("mixed", "fp64"):
+                hc = make(path, wlc)
+                if path == "mixed":
+                    row["autotune"] = tune(hc, f"{name}:{wlc.n_samples}")
+                ms_c, infos_c, pc, _ = timed(hc, path, args.config_steps, 1, profile=True)
+                gbs = pc["pass_bytes"] / (pc["pass_ms"] * 1e-3) / 1e9 if pc and pc["pass_ms"] > 0 else None
+                row[path] = {"ms_per_step": round(ms_c, 3),
+                             "cg_iterations": float(np.mean([i["iterations"] for i in infos_c])),
+                             "true_rel_residual": max(i["true_rel_residual"] for i in infos_c),
+                             "converged": all(i["converged"] for i in infos_c),
+                             "sv_gbs": round(gbs, 1) if gbs else None,
+                             "sv_frac_of_hbm": round(gbs / peak, 4) if gbs else None}
+                hc.close()
+            configs[name] = row
+
     ach = prof["pass_bytes"] / (prof["pass_ms"] * 1e-3) / 1e9 if prof and prof["pass_ms"] > 0 else None
+    path1 = tuning["path"]
     per_launch_bytes = prof["pass_bytes"] / max(1, prof["pass_launches"]) if prof else None
     res = {
         "metric": METRIC,
@@ -322,7 +406,11 @@ def run_gpu(args, rank, world, dist):
         "vs_baseline": None,
         "dtype": "f32",
         "precision": {"walkers": "f32 (inverse rebuilt from scratch each step)", "O_stream": "bf16",
-                      "stream_accumulate": "f32", "scalars_and_outer_residual": "f64 over the f32 store"},
+                      "stream_accumulate": "f32", "scalars_and_outer_residual": "f64 over the f32 store",
+                      "fp64_refresh_leg": "see refresh64: stored samples from FP64, residual vs the FP64 operator"},
+        "autotune": tuning,
+        "refresh64": refresh,
+        "configs": configs,
         "data": "synthetic (seeded random CPS amplitudes 1+N(0,0.01^2), pairing N(0,0.1^2), random sector starts)",
         "config": {"workload": WORKLOAD, "n_params": wl.n_params, "n_samples": wl.n_samples,
                    "shift": shift, "tol": tol, "parallelism": f"replicas x{world}",
@@ -337,14 +425,12 @@ def run_gpu(args, rank, world, dist):
         "shared_correlators": shared,
         "abinitio": abinit,
         "speedup_vs_fp64_path": round(fp64["ms_per_step"] / ms, 3) if fp64 else None,
-        "roofline": {"bound": "hbm", "kernel": "k_gather_G<1,U> + k_scatter_T<1> (sorted two-pass Eq. 7 product, BF16 store)",
+        "roofline": {"bound": "hbm", "kernel": PASS_KERNELS.get(path1, path1),
                      "achieved": round(ach, 1) if ach else None, "peak": peak, "unit": "GB/s",
                      "frac": round(ach / peak, 4) if ach else None, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": per_launch_bytes,
                      "launches": prof["pass_launches"] if prof else None,
-                     # DRAM bytes per pass (gather + scatter) from the ncu capture summarised in
-                     # profiles/k_gather_G_k_scatter_T_bf16_hubbard8x8_2x3.md
-                     "traffic": SORTED_PASS_DRAM_BYTES},
+                     "traffic": PASS_DRAM_BYTES.get(path1)},
         "e2e": {"value": round(float(np.median(e2e_ms)) / 1e3, 6), "unit": "s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(prof["launches_all"]) if prof else None,
@@ -394,15 +480,22 @@ def oracle_step(n_walkers: int, spw: int, seed: int, cg_iters_full: float):
 
 
 def cpu_baseline(cg_iters_full: float, n_walkers=128, spw=2):
+    import oracle
     cores = os.cpu_count() or 1
-    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    oracle.set_threads(cores)
     est, parts = oracle_step(n_walkers, spw, 2005, cg_iters_full)
-    return {"value": round(est, 3), "unit": "s", "cores": int(os.environ.get("OMP_NUM_THREADS", cores)),
+    # the same on one core, on a quarter of the sample
+    oracle.set_threads(1)
+    est1, parts1 = oracle_step(max(8, n_walkers // 4), spw, 2006, cg_iters_full)
+    oracle.set_threads(cores)
+    return {"value": round(est, 3), "unit": "s", "cores": int(cores),
             "kind": "oracle",
             "sample": (f"{parts['n_samples']} samples ({n_walkers} walkers x {spw}) of the same workload: "
                        f"sampling + E_L + dense O + gradient timed and scaled x{65536 / parts['n_samples']:.0f}, "
                        f"Eq. 7 products (mean of 5) scaled to 65,536 samples x {cg_iters_full:.0f} CG products "
                        f"(the GPU FP64 path's iteration count)"),
+            "nproc": int(cores),
+            "one_core": {"value": round(est1, 3), "unit": "s", "cores": 1, "n_samples": parts1["n_samples"]},
             "parts": {k: round(v, 4) if isinstance(v, float) else v for k, v in parts.items()}}
 
 
@@ -515,6 +608,10 @@ def main():
                     help="SR steps timed on the 24-orbital ab initio workload (0: skip)")
     ap.add_argument("--lm-iters", type=int, default=60,
                     help="Davidson steps of the linear-method leg on the ab initio workload (0: skip)")
+    ap.add_argument("--refresh-steps", type=int, default=2,
+                    help="steps of the FP64-refresh / MIXED64 leg (0 to skip)")
+    ap.add_argument("--config-steps", type=int, default=2,
+                    help="steps per path of the other workloads (0 to skip)")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-cg-iters", type=float, default=350.0)

@@ -95,6 +95,7 @@ def lib():
             L.orc_lm_apply.restype = i32
             L.orc_apply_hop.argtypes = [i32, vp, i32, i32, vp]
             L.orc_apply_hop.restype = i32
+            L.orc_set_threads.argtypes = [i32]
             _lib = L
     return _lib
 
@@ -456,6 +457,11 @@ def lm_update(alpha, x, Sx0: float):
     orthogonalised to Psi, (S x)_0 = x_0 + sum_j Obar_j x_j; alpha' =
     alpha + x_{1:} / (S x)_0."""
     return np.asarray(alpha) + np.asarray(x[1:]) / Sx0
+
+
+def set_threads(n: int):
+    """OpenMP threads of the oracle's parallel loops."""
+    lib().orc_set_threads(int(n))
 
 
 def apply_hop(M: int, bits, p: int, q: int):

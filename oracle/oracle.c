@@ -24,6 +24,9 @@
  *     O_0 = 1; all sample means use weight 1/n_s; shift eps is absolute.
  */
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -1078,4 +1081,15 @@ int orc_lm_apply(const orc_problem* P, int64_t n_s, const uint8_t* occ, const do
 int orc_apply_hop(int M, const uint8_t* bits, int p, int q, uint8_t* out)
 {
     return hop_sign(M, bits, p, q, out);
+}
+
+/* Number of OpenMP threads of the oracle's parallel loops (the CPU baseline
+ * is timed on all host cores and on one). */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
 }

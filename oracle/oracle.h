@@ -74,4 +74,6 @@ int orc_lm_apply(const orc_problem* P, int64_t n_s, const uint8_t* occ, const do
                  double* Hx, double* Sx);
 int orc_apply_hop(int M, const uint8_t* bits, int p, int q, uint8_t* out);
 
+void orc_set_threads(int n);
+
 #endif

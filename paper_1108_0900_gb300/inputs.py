@@ -112,6 +112,11 @@ class Workload:
         return int(self.class_off[-1])
 
     @property
+    def n_pf_block(self) -> int:
+        """Stored pairing derivatives per sample: pairs of occupied orbitals."""
+        return self.n_up * (self.n_up - 1) // 2 + self.n_dn * (self.n_dn - 1) // 2 + self.n_up * self.n_dn
+
+    @property
     def n_pf_params(self) -> int:
         return self.M * (self.M - 1) // 2
 
