@@ -536,8 +536,12 @@ def run_sv_only(args):
     peak, peak_kind = peaks()
     v = torch.from_numpy(np.random.default_rng(1).standard_normal(wl.n_params)).cuda()
     out = {}
-    for name, store in (("bf16", V.VMC_STORE_BF16), ("fp32_f32acc", V.VMC_STORE_FP32_F32ACC),
-                        ("fp32_f64acc", V.VMC_STORE_FP32), ("fp64", V.VMC_STORE_FP64)):
+    for name, store, path in (("bf16_sorted", V.VMC_STORE_BF16, V.VMC_PATH_SORTED),
+                              ("bf16_fused", V.VMC_STORE_BF16, V.VMC_PATH_FUSED),
+                              ("fp32_f32acc", V.VMC_STORE_FP32_F32ACC, V.VMC_PATH_AUTO),
+                              ("fp32_f64acc", V.VMC_STORE_FP32, V.VMC_PATH_AUTO),
+                              ("fp64", V.VMC_STORE_FP64, V.VMC_PATH_AUTO)):
+        V.vmc_set_product_path(h, path)
         for _ in range(2):
             V.sr_apply_S(h, v, wl.shift, store)
         torch.cuda.synchronize()
@@ -558,6 +562,34 @@ def run_sv_only(args):
     h.close()
     return {"metric": "S·v GB/s", "workload": WORKLOAD, "peak_gbs": peak, "peak_kind": peak_kind,
             "passes": args.sv_only, "stores": out}
+
+
+def run_sample_only(args):
+    """vmc_sample timing (Metropolis sweeps, local energies, derivative ratios)
+    on a named workload with FP32 walkers: `--sample-only NAME`, `--sample-walkers`
+    chains x the workload's samples per walker, `--steps` timed calls."""
+    import torch
+    from paper_1108_0900_gb300 import inputs
+    from paper_1108_0900_gb300 import vmcsr as V
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    over = {"n_walkers": args.sample_walkers} if args.sample_walkers else {}
+    wl = inputs.workload(args.sample_only, **over)
+    h = V.vmc_create(wl, walker_precision=V.VMC_FP32, keep_fp64_store=False, keep_lowp_store=True)
+    V.vmc_set_params(h, wl.C, wl.f)
+    V.vmc_set_walkers(h, wl.init_occ)
+    seed = inputs.seed_sampling_for(args.sample_only)
+    V.vmc_sample(h, 2, seed)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for k in range(args.steps):
+        V.vmc_sample(h, 0, seed + 1 + k)
+    e1.record()
+    torch.cuda.synchronize()
+    h.close()
+    return {"workload": args.sample_only, "n_walkers": wl.n_walkers, "samples_per_walker": wl.samples_per_walker,
+            "sample_ms": round(e0.elapsed_time(e1) / args.steps, 3), "calls": args.steps}
 
 
 def run_lm_only(args):
@@ -617,7 +649,12 @@ def main():
     ap.add_argument("--ref-cg-iters", type=float, default=350.0)
     ap.add_argument("--sv-only", type=int, default=0, help="time N S products per store kind and exit")
     ap.add_argument("--lm-only", type=int, default=0, help="time N linear-method products per store and exit")
+    ap.add_argument("--sample-only", default="", help="time vmc_sample on the named workload and exit")
+    ap.add_argument("--sample-walkers", type=int, default=0, help="walkers of --sample-only (0: the workload's)")
     args = ap.parse_args()
+    if args.sample_only:
+        print(json.dumps(run_sample_only(args)))
+        return
     if args.sv_only:
         print(json.dumps(run_sv_only(args)))
         return

@@ -212,6 +212,29 @@ typedef struct {
 } vmc_sample_stats_t;
 int vmc_sample_stats(vmc_handle h, vmc_sample_stats_t* out, void* stream);
 
+/* Several lattices of uneven size in one launch (no counterpart in the
+ * paper, which states the method per problem).  vmc_sample_batch does
+ * vmc_sample(hs[b], n_burn, seeds[b]) for b < n (n <= 16 distinct handles of
+ * one device and one walker precision) as a single kernel launch: each warp
+ * finds its problem from the running sum of the walker counts, and every warp
+ * gets the shared-memory slice of the largest problem.  Each handle then holds
+ * exactly the samples its own vmc_sample with the same seed gives.  hs and
+ * seeds are host arrays.  Synchronizes `stream`.  Errors: INVALID_ARG (n out
+ * of range, a repeated handle, mixed precisions or devices), STATE, and the
+ * errors of vmc_sample. */
+int vmc_sample_batch(const vmc_handle* hs, int n, int n_burn, const uint64_t* seeds, void* stream);
+
+/* out[b] = (S_b + shift I) V[b] (Eq. 7 with the covariance term) for every
+ * handle b < n, each over its own samples: one streaming launch reads every
+ * handle's store (the generic per-sample pass; its CTAs are split among the
+ * problems in proportion to their stored bytes), then each handle's
+ * correlator sums and finish run.  V and out are host arrays of n device
+ * pointers to FP64 vectors of the handle's n_v; store is VMC_STORE_FP64 or
+ * VMC_STORE_FP32 (FP64 accumulation).  Synchronizes `stream`.  Errors:
+ * INVALID_ARG, STATE, UNSUPPORTED (a pairing block beyond shared memory). */
+int sr_apply_S_batch(const vmc_handle* hs, int n, const double* const* V, double* const* out, double shift,
+                     int store, void* stream);
+
 /* Evaluate E_L and O for caller-given configurations occ[n_s][N] (host,
  * ascending, n_s <= n_walkers * samples_per_walker), recomputing each
  * pairing inverse from scratch; the result replaces the O store and the

@@ -18,6 +18,7 @@ constexpr int kMaxK = 4;
 constexpr int kNumPart = 256;   // blocks of the reduction kernels
 constexpr int kChunk = 16;      // CG iterations between host convergence checks
 constexpr int kScalX0 = 7;      // d_scal slot of the SR update's x_0
+constexpr int kMaxBatch = 16;   // problems per batched launch
 
 #define VCK(x)                                                    \
     do {                                                          \
@@ -107,6 +108,8 @@ struct vmc_ctx {
     double* d_Echain = nullptr;  // [ncap] E_L of the FP32 chains before an FP64 refresh
     bool refreshed = false;      // the stored samples come from an FP64 refresh
     double* d_lnps = nullptr;    // [ncap] scratch for vmc_sample_stats
+    unsigned char* d_batch = nullptr;   // argument blocks of batched launches led by this handle
+    size_t batch_bytes = 0;
     double* d_pf64 = nullptr;
     float* d_pf32 = nullptr;
     __nv_bfloat16* d_pf16 = nullptr;
@@ -678,7 +681,9 @@ static int read_status(vmc_ctx* h, cudaStream_t st) {
     return VMC_OK;
 }
 
-static int launch_walkers(vmc_ctx* h, SampleArgs& a, bool fp64, cudaStream_t st) {
+// fills the problem-dependent fields of `a` (strides, shared-memory slice per
+// walker) and returns the slice size
+static size_t prep_walkers(vmc_ctx* h, SampleArgs& a, bool fp64) {
     a.pb = h->pb;
     a.XS = h->N + 1;
     a.GS = h->N + 1;
@@ -693,11 +698,16 @@ static int launch_walkers(vmc_ctx* h, SampleArgs& a, bool fp64, cudaStream_t st)
     }
     wb = round_up(wb, 16);
     a.warp_bytes = wb;
+    a.status = h->d_status;
+    return wb;
+}
+
+static int launch_walkers(vmc_ctx* h, SampleArgs& a, bool fp64, cudaStream_t st) {
+    const size_t wb = prep_walkers(h, a, fp64);
     int wpb = (int)std::min<size_t>(4, h->smem_optin / wb);
     if (wpb < 1) return VMC_ERR_UNSUPPORTED;
     size_t smem = wb * wpb;
     int blocks = (a.n_walkers + wpb - 1) / wpb;
-    a.status = h->d_status;
     if (fp64) {
         VCK(cudaFuncSetAttribute(k_walkers<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_walkers<double><<<blocks, 32 * wpb, smem, st>>>(a); h->n_launch++;
@@ -728,11 +738,8 @@ static int transpose_states(vmc_ctx* h, cudaStream_t st) {
     return VMC_OK;
 }
 
-extern "C" int vmc_sample(vmc_handle h, int n_burn, uint64_t seed, void* stream) {
-    if (!h || n_burn < 0) return VMC_ERR_INVALID_ARG;
-    if (!h->params_set || !h->walkers_set) return VMC_ERR_STATE;
-    cudaStream_t st = (cudaStream_t)stream;
-    SampleArgs a{};
+static void sample_args(vmc_ctx* h, int n_burn, uint64_t seed, SampleArgs& a) {
+    a = SampleArgs{};
     a.n_walkers = h->n_walkers;
     a.spw = h->spw;
     a.n_burn = n_burn;
@@ -744,8 +751,25 @@ extern "C" int vmc_sample(vmc_handle h, int n_burn, uint64_t seed, void* stream)
     a.walker_occ = h->d_wocc;
     a.walker_step = h->d_wstep;
     store_targets(h, a);
+}
+
+static int after_sampling(vmc_ctx* h, cudaStream_t st);
+
+extern "C" int vmc_sample(vmc_handle h, int n_burn, uint64_t seed, void* stream) {
+    if (!h || n_burn < 0) return VMC_ERR_INVALID_ARG;
+    if (!h->params_set || !h->walkers_set) return VMC_ERR_STATE;
+    cudaStream_t st = (cudaStream_t)stream;
+    SampleArgs a;
+    sample_args(h, n_burn, seed, a);
     int rc = launch_walkers(h, a, h->wprec == VMC_FP64, st);
     if (rc) return rc;
+    return after_sampling(h, st);
+}
+
+// the store holds a new set of samples: invalidate what was built on the old
+// one, refresh in FP64 if asked, transpose the correlator states
+static int after_sampling(vmc_ctx* h, cudaStream_t st) {
+    int rc;
     h->n_s = h->ncap;
     h->obar_ok[0] = h->obar_ok[1] = h->obar_ok[2] = false;
     h->sorted_ok = h->g_ok = h->corr_ok = false;
@@ -770,6 +794,67 @@ extern "C" int vmc_sample(vmc_handle h, int n_burn, uint64_t seed, void* stream)
     rc = transpose_states(h, st);
     if (rc) return rc;
     return read_status(h, st);
+}
+
+// device buffer for the argument blocks of the batched launches
+static int batch_buffer(vmc_ctx* h, size_t bytes, void** p) {
+    if (h->batch_bytes < bytes) {
+        if (h->d_batch) {
+            cudaFree(h->d_batch);
+            h->allocs.erase(std::find(h->allocs.begin(), h->allocs.end(), h->d_batch));
+            h->d_batch = nullptr;
+        }
+        unsigned char* q = nullptr;
+        VCK(h->alloc(&q, bytes));
+        h->d_batch = q;
+        h->batch_bytes = bytes;
+    }
+    *p = h->d_batch;
+    return VMC_OK;
+}
+
+extern "C" int vmc_sample_batch(const vmc_handle* hs, int n, int n_burn, const uint64_t* seeds, void* stream) {
+    if (!hs || !seeds || n < 1 || n > kMaxBatch || n_burn < 0) return VMC_ERR_INVALID_ARG;
+    for (int b = 0; b < n; ++b) {
+        if (!hs[b]) return VMC_ERR_INVALID_ARG;
+        if (!hs[b]->params_set || !hs[b]->walkers_set) return VMC_ERR_STATE;
+        if (hs[b]->wprec != hs[0]->wprec || hs[b]->dev != hs[0]->dev) return VMC_ERR_INVALID_ARG;
+        for (int c = 0; c < b; ++c)
+            if (hs[c] == hs[b]) return VMC_ERR_INVALID_ARG;
+    }
+    vmc_ctx* h0 = hs[0];
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool fp64 = h0->wprec == VMC_FP64;
+    std::vector<SampleArgs> args(n);
+    std::vector<int> wstart(n + 1, 0);
+    size_t wb = 0;
+    for (int b = 0; b < n; ++b) {
+        sample_args(hs[b], n_burn, seeds[b], args[b]);
+        wb = std::max(wb, prep_walkers(hs[b], args[b], fp64));
+        wstart[b + 1] = wstart[b] + hs[b]->n_walkers;
+    }
+    const int wpb = (int)std::min<size_t>(4, h0->smem_optin / wb);
+    if (wpb < 1) return VMC_ERR_UNSUPPORTED;
+    void* dbuf = nullptr;
+    const size_t abytes = round_up(sizeof(SampleArgs) * n, 256);
+    int rc = batch_buffer(h0, abytes + sizeof(int) * (n + 1), &dbuf);
+    if (rc) return rc;
+    SampleArgs* dargs = (SampleArgs*)dbuf;
+    int* dws = (int*)((unsigned char*)dbuf + abytes);
+    VCK(cudaMemcpyAsync(dargs, args.data(), sizeof(SampleArgs) * n, cudaMemcpyHostToDevice, st));
+    VCK(cudaMemcpyAsync(dws, wstart.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, st));
+    const size_t smem = wb * wpb;
+    const int blocks = (wstart[n] + wpb - 1) / wpb;
+    VCK(launch_walkers_batch(fp64, blocks, 32 * wpb, smem, st, dargs, dws, n, wb));
+    h0->n_launch++;
+    // the host copies of the argument blocks must outlive the launch's copies
+    VCK(cudaStreamSynchronize(st));
+    int first = VMC_OK;
+    for (int b = 0; b < n; ++b) {
+        rc = after_sampling(hs[b], st);
+        if (rc && !first) first = rc;
+    }
+    return first;
 }
 
 static int measure_device_configs(vmc_ctx* h, int64_t n_s, bool fp64, const double* bw, double* bgrad,
@@ -2548,3 +2633,89 @@ extern "C" int vmc_profile_read(vmc_handle h, int store, int64_t* launches_all, 
     if (pass_bytes) *pass_bytes = h->acc_bytes[store];
     return VMC_OK;
 }
+
+// ---------------------------------------------------------------------------
+// several problems in one streaming launch
+// ---------------------------------------------------------------------------
+extern "C" int sr_apply_S_batch(const vmc_handle* hs, int n, const double* const* V, double* const* out,
+                                double shift, int store, void* stream) {
+    if (!hs || !V || !out || n < 1 || n > kMaxBatch) return VMC_ERR_INVALID_ARG;
+    if (store != VMC_STORE_FP64 && store != VMC_STORE_FP32) return VMC_ERR_INVALID_ARG;
+    const int kind = store == VMC_STORE_FP64 ? 0 : 1;
+    for (int b = 0; b < n; ++b) {
+        if (!hs[b] || !V[b] || !out[b]) return VMC_ERR_INVALID_ARG;
+        if (hs[b]->n_s == 0 || !store_ptr(hs[b], kind)) return VMC_ERR_STATE;
+        if (hs[b]->dev != hs[0]->dev) return VMC_ERR_INVALID_ARG;
+        for (int c = 0; c < b; ++c)
+            if (hs[c] == hs[b]) return VMC_ERR_INVALID_ARG;
+    }
+    vmc_ctx* h0 = hs[0];
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<MainArgs<double>> args(n);
+    std::vector<int> cta0(n + 1, 0);
+    // CTAs in proportion to each problem's stored bytes, about two per SM in all
+    size_t smem = 0;
+    double work = 0.0;
+    for (int b = 0; b < n; ++b) work += (double)hs[b]->n_s * (hs[b]->P + hs[b]->ncorr);
+    for (int b = 0; b < n; ++b) {
+        vmc_ctx* h = hs[b];
+        int rc = ensure_obar(h, kind, st);
+        if (rc) return rc;
+        k_dot_part<double, double, 1><<<vgrid(h, 1), 256, 0, st>>>(h->d_Obar[kind], V[b], h->nv, h->part(0), nullptr);
+        h->n_launch++;
+        smem = std::max(smem, main_smem(h, 1, sizeof(double)));
+        const double share = (double)h->n_s * (h->P + h->ncorr) / work;
+        int g = (int)std::ceil(share * 2 * h0->nsm);
+        g = (int)std::max<int64_t>(1, std::min<int64_t>(g, (h->n_s + 15) / 16));
+        g = std::min<int64_t>(g, (int64_t)(h->pfpart_bytes / ((size_t)h->npf * sizeof(double))));
+        cta0[b + 1] = cta0[b] + g;
+        MainArgs<double>& a = args[b];
+        a.pb = h->pb;
+        a.n_s = h->n_s;
+        a.s_occ = h->d_socc; a.Nst = h->Nst;
+        a.s_cidx = h->d_cidx; a.ncst = h->ncst;
+        a.s_pf = store_ptr(h, kind); a.Pst = h->Pst;
+        a.V = V[b]; a.invC = h->d_invC64; a.T = (double*)h->d_T;
+        a.pf_partial = (double*)h->d_pfpart;
+        a.stop = nullptr;
+    }
+    if (smem > h0->smem_optin) { set_err("pairing block does not fit in shared memory"); return VMC_ERR_UNSUPPORTED; }
+    void* dbuf = nullptr;
+    const size_t abytes = round_up(sizeof(MainArgs<double>) * n, 256);
+    int rc = batch_buffer(h0, abytes + sizeof(int) * (n + 1), &dbuf);
+    if (rc) return rc;
+    MainArgs<double>* dargs = (MainArgs<double>*)dbuf;
+    int* dcta = (int*)((unsigned char*)dbuf + abytes);
+    VCK(cudaMemcpyAsync(dargs, args.data(), sizeof(MainArgs<double>) * n, cudaMemcpyHostToDevice, st));
+    VCK(cudaMemcpyAsync(dcta, cta0.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, st));
+    VCK(launch_sr_main_batch(kind == 0 ? 8 : 4, cta0[n], smem, st, dargs, dcta, n));
+    h0->n_launch++;
+    for (int b = 0; b < n; ++b) {
+        vmc_ctx* h = hs[b];
+        if ((rc = launch_corr<double, 1>(h, (double*)h->d_T, nullptr, st))) return rc;
+        if ((rc = reduce_pf<double>(h, cta0[b + 1] - cta0[b], 1, st))) return rc;
+        FinArgs<double, double> f{};
+        f.pb = h->pb;
+        f.n_s = h->n_s;
+        f.inv_n = 1.0 / (double)h->n_s;
+        f.centered = 0;
+        f.pf_partial = (const double*)h->d_pfpart;
+        f.pf_raw = h->d_pfraw;
+        f.corr_raw = h->d_corrraw;
+        f.invC = h->d_invC64;
+        f.ObarA = h->d_Obar[kind];
+        f.obv_part = h->part(0);
+        f.n_obv_part = vgrid(h, 1);
+        f.V = V[b];
+        f.shift = shift;
+        f.out = out[b];
+        f.dot_part = nullptr;
+        f.stop = nullptr;
+        k_finalize_S<double, double, 1><<<vgrid(h, 1), 256, 0, st>>>(f); h->n_launch++;
+        VCK(cudaGetLastError());
+    }
+    // the host copies of the argument blocks must outlive the launch's copies
+    VCK(cudaStreamSynchronize(st));
+    return VMC_OK;
+}
+

@@ -56,6 +56,8 @@ struct LogPsiArgs {
 };
 
 template <typename R> __global__ void k_walkers(SampleArgs a);
+cudaError_t launch_walkers_batch(bool fp64, int blocks, int threads, size_t smem, cudaStream_t st,
+                                 const SampleArgs* args, const int* wstart, int n, size_t warp_bytes);
 __global__ void k_logpsi(LogPsiArgs a);
 
 // ---------------------------------------------------------------------------
@@ -125,6 +127,8 @@ struct FinArgs {
 
 template <typename ST, typename AT, int K, bool GATHER>
 __global__ void __launch_bounds__(512) k_sr_main(MainArgs<AT> a);
+cudaError_t launch_sr_main_batch(int store_bytes, int blocks, size_t smem, cudaStream_t st,
+                                 const MainArgs<double>* args, const int* cta0, int n);
 template <typename AT, int K>
 __global__ void __cluster_dims__(kCorrCluster, 1, 1) __launch_bounds__(256) k_corr_scatter(CorrArgs<AT> a);
 template <typename AT, int K> __global__ void __launch_bounds__(256) k_corr_scatter_global(CorrArgs<AT> a);

@@ -15,8 +15,9 @@
 //   X' = X + (c y^T - y c^T) / r,  c = X_{:,a},  y = X b + e_a.
 // The inverse is rebuilt from scratch (Gauss-Jordan, partial pivoting) at
 // the start of every call.  The chain also sums ln|ratio| of its accepted
-// moves (FP64), the running log-amplitude that a from-scratch evaluation of
-// the stored samples checks (vmc_sample_stats).
+// moves (the logarithm in the chain's precision, the sum in FP64), the
+// running log-amplitude that a from-scratch evaluation of the stored samples
+// checks (vmc_sample_stats).
 #include "ansatz.cuh"
 #include "common.cuh"
 #include "kernels.h"
@@ -27,6 +28,10 @@ struct WarpMem {
     unsigned char* base;
 };
 
+
+// ln|x| in the walker's precision (FP32 chains avoid the FP64 pipe)
+__device__ __forceinline__ float log_abs(float x) { return logf(fabsf(x)); }
+__device__ __forceinline__ double log_abs(double x) { return log(fabs(x)); }
 
 template <typename R>
 __device__ R corr_ratio_warp(const DevProblem& pb, uint32_t* cidx, int p, int q, bool commit) {
@@ -342,15 +347,13 @@ template <> __device__ __forceinline__ void store_pf<double>(const SampleArgs& a
     if (a.s_pf16) a.s_pf16[idx] = __float2bfloat16_rn((float)w);
 }
 
+// One walker (or one given configuration) of the problem of `a`, run by the
+// calling warp with its shared-memory slice `base`.
 template <typename R>
-__global__ void k_walkers(SampleArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ void walker_run(const SampleArgs& a, int w, unsigned char* base) {
     const DevProblem& pb = a.pb;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int w = blockIdx.x * (blockDim.x >> 5) + wid;
-    if (w >= a.n_walkers) return;
+    const int lane = threadIdx.x & 31;
     const int N = pb.N, M = pb.M, ns = pb.ns, nu = pb.nu, XS = a.XS;
-    unsigned char* base = smem_raw + (size_t)wid * a.warp_bytes;
     R* X = (R*)base;
     R* bv = X + N * XS;
     R* yv = bv + XS;
@@ -436,7 +439,7 @@ __global__ void k_walkers(SampleArgs a) {
             R ratio = rpf * rc;
             bool accept = u < ratio * ratio;
             if (!accept) continue;
-            lnrun += log(fabs((double)ratio));
+            lnrun += (double)log_abs(ratio);
             __syncwarp();
             for (int i = lane; i < N; i += 32) {
                 R yi = R(0);
@@ -552,6 +555,30 @@ __global__ void k_walkers(SampleArgs a) {
     }
 }
 
+template <typename R>
+__global__ void k_walkers(SampleArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int wid = threadIdx.x >> 5;
+    const int w = blockIdx.x * (blockDim.x >> 5) + wid;
+    if (w >= a.n_walkers) return;
+    walker_run<R>(a, w, smem_raw + (size_t)wid * a.warp_bytes);
+}
+
+// Several problems (lattices of uneven size) in one launch: warp g runs
+// walker g - wstart[b] of problem b, wstart[b] <= g < wstart[b + 1]; every
+// warp has warp_bytes of shared memory (the largest of the problems').
+template <typename R>
+__global__ void k_walkers_batch(const SampleArgs* __restrict__ args, const int* __restrict__ wstart, int n,
+                                size_t warp_bytes) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int wid = threadIdx.x >> 5;
+    const int g = blockIdx.x * (blockDim.x >> 5) + wid;
+    if (g >= wstart[n]) return;
+    int b = 0;
+    while (b + 1 < n && g >= wstart[b + 1]) ++b;
+    walker_run<R>(args[b], g - wstart[b], smem_raw + (size_t)wid * warp_bytes);
+}
+
 // ln|Pf(F[occ, occ])| + sum_c ln|C_c| per sample, FP64 Parlett-Reid with
 // pivoting (the pfaffian reduction cited in Sec. II.C), one warp per sample.
 __global__ void k_logpsi(LogPsiArgs a) {
@@ -626,5 +653,21 @@ __global__ void k_logpsi(LogPsiArgs a) {
 
 template __global__ void k_walkers<float>(SampleArgs);
 template __global__ void k_walkers<double>(SampleArgs);
+
+// launch of the batched walker kernel from the unit that defines it
+cudaError_t launch_walkers_batch(bool fp64, int blocks, int threads, size_t smem, cudaStream_t st,
+                                 const SampleArgs* args, const int* wstart, int n, size_t warp_bytes) {
+    cudaError_t e;
+    if (fp64) {
+        e = cudaFuncSetAttribute(k_walkers_batch<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_walkers_batch<double><<<blocks, threads, smem, st>>>(args, wstart, n, warp_bytes);
+    } else {
+        e = cudaFuncSetAttribute(k_walkers_batch<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_walkers_batch<float><<<blocks, threads, smem, st>>>(args, wstart, n, warp_bytes);
+    }
+    return cudaGetLastError();
+}
 
 }  // namespace vmc

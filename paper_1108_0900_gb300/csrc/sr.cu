@@ -37,10 +37,9 @@ template <> __device__ __forceinline__ double load_st<__nv_bfloat16, double>(con
     return (double)__bfloat162float(((const __nv_bfloat16*)p)[i]);
 }
 
+// The generic pass for one problem, run by CTA `cta` of `ncta` serving it.
 template <typename ST, typename AT, int K, bool GATHER>
-__global__ void __launch_bounds__(512) k_sr_main(MainArgs<AT> a) {
-    if (a.stop && *a.stop) return;
-    extern __shared__ __align__(16) unsigned char smem[];
+__device__ void sr_main_run(const MainArgs<AT>& a, int cta, int ncta, unsigned char* smem) {
     const DevProblem& pb = a.pb;
     const int npf = pb.npf, M = pb.M, N = pb.N, P = pb.P;
     AT* acc = (AT*)smem;
@@ -56,7 +55,7 @@ __global__ void __launch_bounds__(512) k_sr_main(MainArgs<AT> a) {
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     uint8_t* my = occw + wid * 64;
-    for (int64_t s = (int64_t)blockIdx.x * nw + wid; s < a.n_s; s += (int64_t)gridDim.x * nw) {
+    for (int64_t s = (int64_t)cta * nw + wid; s < a.n_s; s += (int64_t)ncta * nw) {
         for (int i = lane; i < N; i += 32) my[i] = a.s_occ[s * a.Nst + i];
         __syncwarp();
         AT t[K];
@@ -98,8 +97,27 @@ __global__ void __launch_bounds__(512) k_sr_main(MainArgs<AT> a) {
         __syncwarp();
     }
     __syncthreads();
-    AT* dst = a.pf_partial + (size_t)blockIdx.x * npf * K;
+    AT* dst = a.pf_partial + (size_t)cta * npf * K;
     for (int i = threadIdx.x; i < npf * K; i += blockDim.x) dst[i] = acc[i];
+}
+
+template <typename ST, typename AT, int K, bool GATHER>
+__global__ void __launch_bounds__(512) k_sr_main(MainArgs<AT> a) {
+    if (a.stop && *a.stop) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    sr_main_run<ST, AT, K, GATHER>(a, blockIdx.x, gridDim.x, smem);
+}
+
+// Several problems in one launch: CTAs [cta0[b], cta0[b + 1]) serve problem
+// b, each with the shared-memory layout of its own problem.
+template <typename ST, typename AT>
+__global__ void __launch_bounds__(512) k_sr_main_batch(const MainArgs<AT>* __restrict__ args,
+                                                       const int* __restrict__ cta0, int n) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    int b = 0;
+    while (b + 1 < n && (int)blockIdx.x >= cta0[b + 1]) ++b;
+    if ((int)blockIdx.x >= cta0[n]) return;
+    sr_main_run<ST, AT, 1, true>(args[b], blockIdx.x - cta0[b], cta0[b + 1] - cta0[b], smem);
 }
 
 // correlator scatter for classes of more states than shared memory holds:
@@ -635,6 +653,7 @@ __global__ void k_axpy_to64(double* x, const VT* d, double scale, int64_t n) {
 // explicit instantiations used by the host side
 // ---------------------------------------------------------------------------
 template __global__ void k_sr_main<double, double, 1, true>(MainArgs<double>);
+
 template __global__ void k_sr_main<double, double, 2, true>(MainArgs<double>);
 template __global__ void k_sr_main<double, double, 4, true>(MainArgs<double>);
 template __global__ void k_sr_main<double, double, 2, false>(MainArgs<double>);
@@ -691,5 +710,25 @@ template __global__ void k_cg_p<float>(const float*, float*, int64_t, const doub
 template __global__ void k_cg_fxr<float>(CgFusedArgs<float>);
 template __global__ void k_axpy_to64<float>(double*, const float*, double, int64_t);
 template __global__ void k_axpy_to64<double>(double*, const double*, double, int64_t);
+
+
+// launch of the batched generic pass from the unit that defines it (store_bytes
+// 8: FP64 store, 4: FP32 store; FP64 accumulation)
+cudaError_t launch_sr_main_batch(int store_bytes, int blocks, size_t smem, cudaStream_t st,
+                                 const MainArgs<double>* args, const int* cta0, int n) {
+    cudaError_t e;
+    if (store_bytes == 8) {
+        e = cudaFuncSetAttribute(k_sr_main_batch<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        k_sr_main_batch<double, double><<<blocks, 512, smem, st>>>(args, cta0, n);
+    } else {
+        e = cudaFuncSetAttribute(k_sr_main_batch<float, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        k_sr_main_batch<float, double><<<blocks, 512, smem, st>>>(args, cta0, n);
+    }
+    return cudaGetLastError();
+}
 
 }  // namespace vmc

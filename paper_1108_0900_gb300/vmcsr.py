@@ -132,6 +132,8 @@ def lib(build_if_missing: bool = True):
         "sr_autotune": [vp, i32, vp, vp],
         "vmc_set_auto_paths": [vp, i32, i32],
         "vmc_sample_stats": [vp, vp, vp],
+        "vmc_sample_batch": [vp, i32, i32, vp, vp],
+        "sr_apply_S_batch": [vp, i32, vp, vp, dbl, i32, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -288,6 +290,28 @@ def vmc_sample_stats(h: Handle, stream=None) -> dict:
     r = vmc_sample_stats_t()
     _check(lib().vmc_sample_stats(h.h, ct.byref(r), _stream(stream)), "vmc_sample_stats")
     return {k: getattr(r, k) for k, _ in r._fields_}
+
+
+def vmc_sample_batch(handles, n_burn: int, seeds, stream=None):
+    """vmc_sample of every handle (lattices of uneven size) in one launch."""
+    n = len(handles)
+    hs = (ct.c_void_p * n)(*[h.h for h in handles])
+    sd = (ct.c_uint64 * n)(*[int(x) for x in seeds])
+    _check(lib().vmc_sample_batch(hs, n, int(n_burn), sd, _stream(stream)), "vmc_sample_batch")
+
+
+def sr_apply_S_batch(handles, Vs, shift: float, store=VMC_STORE_FP64, stream=None):
+    """(S_b + shift I) V_b for every handle b, all stores streamed by one
+    launch; Vs: CUDA float64 vectors; returns the products."""
+    import torch
+    n = len(handles)
+    Vs = [v.contiguous() for v in Vs]
+    outs = [torch.empty_like(v) for v in Vs]
+    hs = (ct.c_void_p * n)(*[h.h for h in handles])
+    vp = (ct.c_void_p * n)(*[v.data_ptr() for v in Vs])
+    op = (ct.c_void_p * n)(*[o.data_ptr() for o in outs])
+    _check(lib().sr_apply_S_batch(hs, n, vp, op, float(shift), int(store), _stream(stream)), "sr_apply_S_batch")
+    return outs
 
 
 def vmc_measure(h: Handle, occ, stream=None):
