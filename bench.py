@@ -368,6 +368,40 @@ def run_gpu(args, rank, world, dist):
                                                / (ms_p64 * 1e-3) / 1e9 / peak, 4)}}
         hf.close()
 
+    # ---- lattices of uneven size in one launch: the 8x8 / 2x2-plaquette
+    # workload (16,384 walkers x 8, N = 56) with the 4x4 pair workload (64 x 64,
+    # N = 16): sampling and the FP32-store product, batched against separate --
+    batch = None
+    if args.batch_steps > 0:
+        wb4, wb1 = inputs.workload("hubbard8x8_2x2"), inputs.workload("hubbard4x4_pair")
+        hb = [make("mixed", wb4), make("mixed", wb1)]
+        reps = args.batch_steps
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+        def clock(fn):
+            fn(0)
+            barrier()
+            e0.record()
+            for k in range(reps):
+                fn(1 + k)
+            e1.record()
+            barrier()
+            return e0.elapsed_time(e1) / reps
+
+        ms_sep = clock(lambda k: [V.vmc_sample(h, 0, seed + 50 + 2 * k + j) for j, h in enumerate(hb)])
+        ms_bat = clock(lambda k: V.vmc_sample_batch(hb, 0, [seed + 50 + 2 * k, seed + 51 + 2 * k]))
+        for h in hb:
+            V.sr_gradient(h, V.VMC_STORE_FP32, stats=False)
+        vs = [torch.ones(w.n_params, dtype=torch.float64, device="cuda") for w in (wb4, wb1)]
+        ms_psep = clock(lambda k: [V.sr_apply_S(h, v, shift, V.VMC_STORE_FP32) for h, v in zip(hb, vs)])
+        ms_pbat = clock(lambda k: V.sr_apply_S_batch(hb, vs, shift, V.VMC_STORE_FP32))
+        batch = {"workloads": ["hubbard8x8_2x2 (16,384 walkers x 8, N = 56)", "hubbard4x4_pair (64 x 64, N = 16)"],
+                 "sample_separate_ms": round(ms_sep, 3), "sample_batched_ms": round(ms_bat, 3),
+                 "fp32_store_product_separate_ms": round(ms_psep, 3),
+                 "fp32_store_product_batched_ms": round(ms_pbat, 3)}
+        for h in hb:
+            h.close()
+
     # ---- the other workloads: the same SR step (mixed and FP64) ---------------
     configs = None
     if args.config_steps > 0:
@@ -411,6 +445,7 @@ def run_gpu(args, rank, world, dist):
         "autotune": tuning,
         "refresh64": refresh,
         "configs": configs,
+        "batched_lattices": batch,
         "data": "synthetic (seeded random CPS amplitudes 1+N(0,0.01^2), pairing N(0,0.1^2), random sector starts)",
         "config": {"workload": WORKLOAD, "n_params": wl.n_params, "n_samples": wl.n_samples,
                    "shift": shift, "tol": tol, "parallelism": f"replicas x{world}",
@@ -644,6 +679,8 @@ def main():
                     help="steps of the FP64-refresh / MIXED64 leg (0 to skip)")
     ap.add_argument("--config-steps", type=int, default=2,
                     help="steps per path of the other workloads (0 to skip)")
+    ap.add_argument("--batch-steps", type=int, default=3,
+                    help="timed calls of the batched-lattice leg (0 to skip)")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-cg-iters", type=float, default=350.0)

@@ -284,6 +284,13 @@ int sr_apply_S(vmc_handle h, const double* V, double* out, int k, double shift, 
 int sr_cg_solve(vmc_handle h, const double* g, double shift, double tol, int max_iter, int mode,
                 double* x, vmc_cg_info* info, void* stream);
 
+/* Inner tolerance of the mixed solves (no counterpart in the paper): each
+ * flexible outer step asks the low-precision inner CG for a relative
+ * residual of max(floor, half of what the outer iteration still needs);
+ * floor 0 restores the default (0.1 for the BF16 inner solves, 1e-3 for
+ * VMC_CG_FP32).  Errors: INVALID_ARG unless 0 <= floor < 1. */
+int sr_set_inner_tol(vmc_handle h, double floor);
+
 /* SR parameter update (Sec. II.A): after the solve of Eq. 2 with x_0
  * eliminated, (S + shift I) y = g, the coefficients of the projected state
  * (1 - tau H)|Psi> are x = -tau y and x_0 = 1 - tau <E_L> - Obar . x, and

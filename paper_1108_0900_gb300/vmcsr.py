@@ -134,6 +134,7 @@ def lib(build_if_missing: bool = True):
         "vmc_sample_stats": [vp, vp, vp],
         "vmc_sample_batch": [vp, i32, i32, vp, vp],
         "sr_apply_S_batch": [vp, i32, vp, vp, dbl, i32, vp],
+        "sr_set_inner_tol": [vp, dbl],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -586,6 +587,11 @@ def _set_auto(h: Handle, path: int, path4: int):
     """Apply a cached autotuner choice: one-vector products on `path`,
     two- and four-vector products on `path4`."""
     _check(lib().vmc_set_auto_paths(h.h, int(path), int(path4)), "vmc_set_auto_paths")
+
+
+def sr_set_inner_tol(h: Handle, floor: float):
+    """Floor of the inner relative tolerance of the mixed solves (0: default)."""
+    _check(lib().sr_set_inner_tol(h.h, float(floor)), "sr_set_inner_tol")
 
 
 def vmc_set_wait_limit(h: Handle, tries: int):
