@@ -62,7 +62,7 @@ struct vmc_ctx {
     double itol_floor = 0.0;     // inner relative tolerance floor of the mixed solves (0: default)
     int last_fused_grid = 0;     // CTAs (tt partials) of the last fused pass
     int sort_nblk = 0, sort_nchunk = 0;
-    size_t t_chunk = 0;          // T entries reserved per 65,536-sample chunk
+    size_t t_chunk = 0;          // T entries reserved per chunk of kTChunk samples
     bool obar_ok[3] = {false, false, false};  // per store: FP64, FP32, BF16
     std::vector<int64_t> corr_off;
 
@@ -125,6 +125,11 @@ struct vmc_ctx {
     double* d_part = nullptr;   // 8 slots x kNumPart x kMaxK
     double* d_pfraw = nullptr;  // [npf][K] reduced pairing-block sums (FP64 or FP32 per pass)
     uint32_t *d_G = nullptr, *d_Tsort = nullptr, *d_counts = nullptr, *d_total = nullptr, *d_base = nullptr;
+    float* d_tpart = nullptr;    // [chunks][npf][kMaxK] per-chunk pairing sums of the sorted scatter
+    bool scatter_corr_front = true;   // correlator items of the sorted scatter as CTAs of their own
+    bool scatter_corr_hist = true;    // correlator half of the sorted scatter as class histograms
+    int scatter_in_cta_mink = 2;      // vectors from which the pairing CTAs build the correlator histograms
+    unsigned* d_tdone = nullptr; // [npf] chunks finished per parameter group (0 between launches)
     uint32_t *d_Tc = nullptr, *d_ccount = nullptr, *d_cbase = nullptr;   // correlator runs
     double* d_scal = nullptr;
     int* d_stop = nullptr;
@@ -482,7 +487,7 @@ extern "C" int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, co
         ACK(h->alloc(&h->d_pf16, (size_t)h->ncap * h->Pst));
         // sorted two-pass structures for the BF16 product
         h->sort_nblk = 2 * h->nsm;
-        h->sort_nchunk = (int)((h->ncap + 65535) / 65536);
+        h->sort_nchunk = (int)((h->ncap + kTChunk - 1) / kTChunk);
         {
             const int QE = (h->P + kGParts - 1) / kGParts;
             h->gwq = (QE + 3) / 4;
@@ -503,8 +508,11 @@ extern "C" int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, co
                 return fail(VMC_ERR_CUDA);
         }
         ACK(h->alloc(&h->d_G, (size_t)h->ncap * h->Gst));
-        h->t_chunk = (size_t)65536 * h->P + (size_t)h->npf * kTRun;   // padded runs of one chunk
+        h->t_chunk = (size_t)kTChunk * h->P + (size_t)h->npf * kTRun;   // padded runs of one chunk
         ACK(h->alloc(&h->d_Tsort, (size_t)h->sort_nchunk * h->t_chunk));
+        if (h->sort_nchunk > 1) ACK(h->alloc(&h->d_tpart, (size_t)h->sort_nchunk * h->npf * kMaxK));
+        ACK(h->alloc(&h->d_tdone, (size_t)h->npf));
+        if (cudaMemset(h->d_tdone, 0, sizeof(unsigned) * h->npf) != cudaSuccess) return fail(VMC_ERR_CUDA);
         ACK(h->alloc(&h->d_counts, (size_t)h->sort_nblk * h->npf));
         ACK(h->alloc(&h->d_total, (size_t)h->npf));
         ACK(h->alloc(&h->d_base, (size_t)h->sort_nchunk * (h->npf + 1)));
@@ -1190,11 +1198,11 @@ static int ensure_sorted(vmc_ctx* h, cudaStream_t st) {
     const size_t smem = (size_t)h->npf * 4;
     VCK(cudaFuncSetAttribute(k_count_G, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     VCK(cudaFuncSetAttribute(k_fill_T, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(2 * smem)));
-    const int nchunk = (int)((h->n_s + 65535) / 65536);
+    const int nchunk = (int)((h->n_s + kTChunk - 1) / kTChunk);
     // run padding must read as weight 0
     VCK(cudaMemsetAsync(h->d_Tsort, 0, sizeof(uint32_t) * h->t_chunk * nchunk, st));
     for (int c = 0; c < nchunk; ++c) {
-        const int64_t sb = (int64_t)c * 65536, se = std::min<int64_t>(h->n_s, sb + 65536);
+        const int64_t sb = (int64_t)c * kTChunk, se = std::min<int64_t>(h->n_s, sb + kTChunk);
         uint32_t* base = h->d_base + (size_t)c * (h->npf + 1);
         k_count_G<<<h->sort_nblk, 512, smem, st>>>(h->d_G, h->Gst, h->P, sb, se, h->npf, h->d_counts); h->n_launch++;
         k_scan_blocks<<<(h->npf + 255) / 256, 256, 0, st>>>(h->d_counts, h->sort_nblk, h->npf, h->d_total); h->n_launch++;
@@ -1253,6 +1261,7 @@ static GatherKern gather_kernel(int u) {
     } else {
         if (u <= 4) return k_gather_G<K, 4>;
         if (u <= 8) return k_gather_G<K, 8>;
+        if (u <= 13) return k_gather_G<K, 13>;   // 56 electrons: 1,540 elements in 13 words per lane
         if (u <= 16) return k_gather_G<K, 16>;
         return nullptr;
     }
@@ -1265,6 +1274,10 @@ template <int K>
 static bool sorted_usable(const vmc_ctx* h) {
     if (!h->use_sorted || !h->d_G || h->ncorr > 32 * kCorrPerLane) return false;
     if ((size_t)h->npf * K * 4 + (size_t)(h->ncorr + 1) * 4 > h->smem_optin) return false;   // gather table
+    // scatter: the chunk's t_s, the group's run ends and the correlator slots
+    if ((size_t)kTChunk * K * 4 + (size_t)(kScatterMaxPQ + 1) * 4 + (size_t)scatter_threads(K) * 4 * K + 1024 >
+        h->smem_optin)
+        return false;
     return gather_kernel<K>((int)((h->Gst / 4 + 31) / 32)) != nullptr;
 }
 
@@ -1309,18 +1322,13 @@ static int launch_sorted(vmc_ctx* h, const float* V, const float* invC, const do
     a.G = h->d_G; a.Pst = h->Gst;
     a.V = V; a.invC = invC; a.Tv = Tv;
     a.obv_part = obv_part; a.n_obv_part = vgrid(h, K);
-    a.T = h->d_Tsort; a.base = h->d_base; a.nchunk = (int)((h->n_s + 65535) / 65536);
+    a.T = h->d_Tsort; a.base = h->d_base; a.nchunk = (int)((h->n_s + kTChunk - 1) / kTChunk);
+    a.part = h->d_tpart; a.done = h->d_tdone;
     a.raw = (float*)h->d_pfraw;
     a.Tc = h->d_Tc; a.cbase = h->d_cbase; a.craw = (float*)h->d_corrraw;
     a.items = h->d_items;
     a.n_items = h->d_item_base + (h->ncp + 31) / 32;
-    // the correlator work items run beside the long pairing runs of the
-    // scatter (measured faster there than the histograms)
-    a.cidxT = h->d_cidxT;
-    a.nhist = 0;
-    a.hist_slices = 1;
-    a.ncb = h->ncorr > 0 ? (int)((h->max_items + 7) / 8) : 0;
-    const size_t hsm = 0;
+    const int sthreads = scatter_threads(K), swarps = sthreads / 32;
     a.tt_part = tt_part;
     a.stop = stop;
     const size_t smem = (size_t)h->npf * K * 4 + (size_t)(h->ncorr + 1) * 4;
@@ -1338,8 +1346,53 @@ static int launch_sorted(vmc_ctx* h, const float* V, const float* invC, const do
     // correlator sums accumulate into zero (the fused CG update re-zeroes
     // them as it reads them, so its products skip this)
     if (h->ncp > 0 && !craw_zero) VCK(cudaMemsetAsync(h->d_corrraw, 0, sizeof(float) * h->ncp * K, st));
-    if (hsm) VCK(cudaFuncSetAttribute(k_scatter_T<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm));
-    k_scatter_T<K><<<a.nhist + a.ncb + (h->npf + 7) / 8, 256, hsm, st>>>(a); h->n_launch++;
+    // scatter: one wave of pairing CTAs over the chunks, each CTA a group of
+    // consecutive parameters of one chunk (at least one per warp).  The
+    // correlator half: histograms of the chunk's t_s inside the pairing CTAs
+    // when they fit beside the chunk table (K >= scatter_in_cta_mink), else
+    // (class, sample slice) histogram CTAs ahead of the pairing CTAs, else
+    // the correlator work items (CTAs of their own ahead, or after each
+    // pairing CTA's runs)
+    {
+        const size_t ssm_tab = (size_t)kTChunk * K * sizeof(float);
+        const int pq_cap = std::min(std::max(h->npf, swarps), kScatterMaxPQ);
+        const size_t run_bytes = ((size_t)(pq_cap + 1) * 4 + 15) / 16 * 16;
+        const size_t static_bytes = (size_t)sthreads * K * sizeof(float) + 1024;
+        size_t hsm = 0;
+        a.nhist = 0;
+        a.hist_slices = 1;
+        a.ncb = 0;
+        a.corr_in_cta = 0;
+        a.hist_cap = 0;
+        a.cidxT = h->d_cidxT;
+        if (h->ncorr > 0) {
+            const int64_t one = (int64_t)h->maxd * K;
+            const int cap = (int)std::max<int64_t>(one, std::min<int64_t>(one * swarps, 8192));
+            if (K >= h->scatter_in_cta_mink &&
+                ssm_tab + run_bytes + (size_t)cap * 4 + static_bytes <= h->smem_optin) {
+                a.corr_in_cta = 1;
+                a.hist_cap = cap;
+            } else if (h->scatter_corr_hist && (hsm = corr_hist_setup(h, K, &a)) > 0) {
+                a.ncb = 0;
+            } else {
+                hsm = 0;
+                a.nhist = 0;
+                a.hist_slices = 1;
+                a.ncb = h->scatter_corr_front ? (int)((h->max_items + swarps - 1) / swarps) : 0;
+            }
+        }
+        a.hist_off = (int)(ssm_tab + run_bytes);   // bytes: the in-CTA histograms
+        const size_t in_cta = (size_t)a.hist_cap * 4;
+        const size_t ssm_max = std::max(hsm, ssm_tab + run_bytes + in_cta);
+        int per = 0;
+        VCK(cudaFuncSetAttribute(k_scatter_T<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm_max));
+        VCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_scatter_T<K>, sthreads, ssm_max));
+        const int64_t resident = (int64_t)h->nsm * std::max(1, per);
+        int ngrp = (int)std::max<int64_t>(1, std::min<int64_t>(h->npf, (resident + a.nchunk - 1) / a.nchunk));
+        a.pq_per_cta = std::min(pq_cap, std::max(swarps, (h->npf + ngrp - 1) / ngrp));
+        ngrp = (h->npf + a.pq_per_cta - 1) / a.pq_per_cta;
+        k_scatter_T<K><<<a.nhist + a.ncb + a.nchunk * ngrp, sthreads, ssm_max, st>>>(a); h->n_launch++;
+    }
     VCK(cudaGetLastError());
     if (h->prof) {
         VCK(cudaEventRecord(rec.b, st));
@@ -1604,7 +1657,10 @@ static int apply_S_dispatch(vmc_ctx* h, const double* V, double* out, double shi
     // into groups (each group streams the store once)
     if (K > 1) {
         const size_t at = (store == VMC_STORE_FP64 || store == VMC_STORE_FP32) ? 8 : 4;
-        if (main_smem(h, K, at) > h->smem_optin) {
+        // (the sorted BF16 product holds no image: it takes all K at once)
+        const bool sorted_all = store == VMC_STORE_BF16 && product_path(h, K) == VMC_PATH_SORTED &&
+                                sorted_usable<K>(h);
+        if (!sorted_all && main_smem(h, K, at) > h->smem_optin) {
             constexpr int H = K > 1 ? K / 2 : 1;
             int rc = apply_S_dispatch<H>(h, V, out, shift, store, st);
             if (rc) return rc;

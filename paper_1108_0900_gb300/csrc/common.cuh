@@ -34,6 +34,12 @@ __host__ __device__ inline u32x4 philox4x32_10(u32x4 c, uint32_t k0, uint32_t k1
 // ---------------------------------------------------------------------------
 // warp reductions
 // ---------------------------------------------------------------------------
+// request [p, p + bytes) into L2 (16-byte aligned, a multiple of 16 bytes);
+// holds no registers or shared memory while the data is on its way
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 template <typename T> __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(VMC_FULL_MASK, v, o);

@@ -28,33 +28,71 @@ __device__ __forceinline__ void corr_lookups(const DevProblem& pb, const int* co
     }
 }
 
+// dst[0..K) += x[0..K) in global memory, one (vector) reduction
+template <int K>
+__device__ __forceinline__ void red_add(float* dst, const float (&x)[K]) {
+    if constexpr (K == 4) {
+        asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst), "f"(x[0]), "f"(x[1]), "f"(x[2]),
+                     "f"(x[3])
+                     : "memory");
+    } else if constexpr (K == 2) {
+        asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(dst), "f"(x[0]), "f"(x[1]) : "memory");
+    } else {
+        atomicAdd(dst, x[0]);
+    }
+}
+
 // Correlator half of the transposed product as a weighted histogram: CTA
 // (class q, slice j) adds the centered t_s of its slice of the samples at
 // the state of every correlator of class q into a shared-memory histogram of
 // the class's 4^m amplitudes, then adds each nonzero bin to craw (one global
-// atomic per bin and slice).  The states are read correlator-major
+// vector reduction per bin and slice).  The states are read correlator-major
 // (coalesced), t_s sample-major.
 template <int K>
 __device__ __forceinline__ void corr_hist_cta(const SortedArgs& a, int q, int j, int nsl, float* hist) {
     const DevProblem& pb = a.pb;
     const int64_t off = pb.class_off[q];
     const int d = (int)(pb.class_off[q + 1] - off);
+    // hist[kk][state]: the bins of one component spread over all banks
     for (int i = threadIdx.x; i < d * K; i += blockDim.x) hist[i] = 0.f;
     __syncthreads();
     const int64_t per = (a.n_s + nsl - 1) / nsl;
     const int64_t s0 = min(a.n_s, (int64_t)j * per), s1 = min(a.n_s, s0 + per);
+    const int bd = blockDim.x;
     for (int ci = pb.class_ptr[q]; ci < pb.class_ptr[q + 1]; ++ci) {
         const cstate_t* st = a.cidxT + (int64_t)pb.class_inst[ci] * a.n_s;
-        for (int64_t s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+        int64_t s = s0 + threadIdx.x;
+        // four samples per thread in flight: the loads first, then the adds
+        for (; s + 3 * bd < s1; s += 4 * bd) {
+            int k[4];
+            float t[4][K];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                k[u] = (int)st[s + u * bd];
+#pragma unroll
+                for (int kk = 0; kk < K; ++kk) t[u][kk] = a.Tv[(s + u * bd) * K + kk];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int kk = 0; kk < K; ++kk) atomicAdd(&hist[kk * d + k[u]], t[u][kk]);
+        }
+        for (; s < s1; s += bd) {
             const int k = (int)st[s];
 #pragma unroll
-            for (int kk = 0; kk < K; ++kk) atomicAdd(&hist[k * K + kk], a.Tv[s * K + kk]);
+            for (int kk = 0; kk < K; ++kk) atomicAdd(&hist[kk * d + k], a.Tv[s * K + kk]);
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < d * K; i += blockDim.x) {
-        const float v = hist[i];
-        if (v != 0.f) atomicAdd(a.craw + off * K + i, v);
+    for (int i = threadIdx.x; i < d; i += blockDim.x) {
+        float x[K];
+        bool nz = false;
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) {
+            x[kk] = hist[kk * d + i];
+            nz |= x[kk] != 0.f;
+        }
+        if (nz) red_add<K>(a.craw + (off + i) * K, x);
     }
 }
 

@@ -253,9 +253,15 @@ struct SortedArgs {
     const double* obv_part; // [n_obv_part][K] partial dots Obar . V (centering)
     int n_obv_part;
     float* Tv;              // [n_s][K] centered per-sample dots O_s . V - Obar . V
-    const uint32_t* T;      // parameter-major (s_local << 16) | bf16
+    const uint32_t* T;      // parameter-major (s_local << 16) | bf16, per chunk of kTChunk samples
     const uint32_t* base;   // [nchunk][npf + 1] run offsets
     int nchunk;
+    int pq_per_cta;         // pairing parameters of one scatter CTA (in one chunk)
+    int corr_in_cta;        // the pairing CTAs build the correlator histograms of their chunk
+    int hist_cap;           // floats of the in-CTA histogram region
+    int hist_off;           // its byte offset in the scatter's dynamic shared memory
+    float* part;            // [nchunk][npf][K] per-chunk pairing sums (nchunk > 1)
+    unsigned* done;         // [parameter groups] chunks finished so far (0 between launches)
     float* raw;             // [npf][K] scatter result
     const uint32_t* Tc;     // correlator runs: sample << 5 | k mod 32, grouped by parameter k
     const uint32_t* cbase;  // [ncp + 1] run offsets
@@ -275,6 +281,8 @@ struct SortedArgs {
 
 constexpr int kCorrPerLane = 4;    // the sorted gather handles up to 128 correlators
 constexpr int kTRun = 128;         // T runs are padded to whole blocks of this many entries
+constexpr int kTChunk = 8192;      // samples per T chunk: the scatter stages a chunk's t_s in shared memory
+constexpr int kScatterMaxPQ = 4096; // parameters of one scatter CTA at most (their run ends sit in shared memory)
 constexpr int kCorrItem = 2048;    // entries per correlator work item of the sorted scatter
 constexpr int kInstPerUnit = 4;    // correlators of one class per cluster of the histogram scatter
 
@@ -294,7 +302,13 @@ __global__ void __launch_bounds__(512) k_fill_T(const uint32_t* G, int64_t Pst, 
 // (512 threads with the next row prefetched measured best)
 constexpr int gather_threads(int K) { return K == 1 ? 512 : 256; }
 template <int K, int U> __global__ void __launch_bounds__(gather_threads(K)) k_gather_G(SortedArgs a);
-template <int K> __global__ void __launch_bounds__(256) k_scatter_T(SortedArgs a);
+// threads per CTA of the sorted scatter: the four-vector chunk table (128 KB)
+// leaves room for one CTA per SM, which then runs 16 warps
+constexpr int scatter_threads(int K) { return K == 4 ? 512 : 256; }
+// the one-vector chunk table (32 KB) leaves room for six CTAs per SM
+constexpr int scatter_min_ctas(int K) { return K == 1 ? 6 : 1; }
+template <int K>
+__global__ void __launch_bounds__(scatter_threads(K), scatter_min_ctas(K)) k_scatter_T(SortedArgs a);
 __global__ void __launch_bounds__(512) k_count_C(DevProblem pb, int64_t n_s, const cstate_t* cidxT,
                                                  uint32_t* ccount, int shared_hist);
 __global__ void __launch_bounds__(512) k_fill_C(DevProblem pb, int64_t n_s, const cstate_t* cidxT,

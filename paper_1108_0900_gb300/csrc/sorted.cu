@@ -9,12 +9,14 @@
 //      t_s = sum_e W_e v[pq(e)] is a pure stream with a shared-memory lookup of
 //      v and no atomics;
 //   T  u32 entries (s_local << 16) | bf16 value, parameter-major per chunk of
-//      at most 65,536 samples (a counting sort of G by pq), each run padded to
-//      whole 128-entry blocks and interleaved inside a block: the scatter
-//      out[pq] = sum_s t_s W_s[pq] is one warp per parameter summing a
-//      contiguous run, with no atomics and no per-CTA partial images.
+//      kTChunk samples (a counting sort of G by pq), each run padded to whole
+//      128-entry blocks and interleaved inside a block: the scatter
+//      out[pq] = sum_s t_s W_s[pq] sums contiguous runs against the chunk's
+//      t_s staged in shared memory, with no atomics and no per-CTA partial
+//      images.
 //
 // The build (count, scan, fill) streams G three times once per SR step.
+#include <type_traits>
 #include "common.cuh"
 #include "kernels.h"
 #include "corr_runs.cuh"
@@ -295,6 +297,24 @@ __global__ void k_corr_item_fill(const uint32_t* cbase, int64_t ncp, const uint3
     for (uint32_t e = e0; e == e0 || e < e1; e += kCorrItem) items[i++] = make_uint2((uint32_t)g, e);
 }
 
+// acc += W x[j] for one (j << 16 | bf16 W) entry, x a shared-memory table of K
+// floats per index (one 4-, 8- or 16-byte load): the gather's v table
+// (j = pq) and the scatter's per-chunk t_s table (j = sample in the chunk)
+template <int K>
+__device__ __forceinline__ void scatter_entry(const float* tv, uint32_t v, float (&acc)[K]) {
+    const float wv = __uint_as_float(v << 16);
+    const uint32_t j = v >> 16;
+    if constexpr (K == 4) {
+        const float4 t = reinterpret_cast<const float4*>(tv)[j];
+        acc[0] += wv * t.x; acc[1] += wv * t.y; acc[2] += wv * t.z; acc[3] += wv * t.w;
+    } else if constexpr (K == 2) {
+        const float2 t = reinterpret_cast<const float2*>(tv)[j];
+        acc[0] += wv * t.x; acc[1] += wv * t.y;
+    } else {
+        acc[0] += wv * tv[j];
+    }
+}
+
 // gather: t_s = sum_c V[k_c]/C[k_c] + sum_e W_e v[pq(e)] - Obar . V, warp per
 // sample.  Centering t_s makes the scatter produce the covariance
 // (1/n) sum_s (t_s - Obar . V) O_s = S V directly, with no cancellation
@@ -358,13 +378,8 @@ __global__ void __launch_bounds__(gather_threads(K)) k_gather_G(SortedArgs a) {
             const uint32_t e[4] = {g[u].x, g[u].y, g[u].z, g[u].w};
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const float val = __uint_as_float(e[j] << 16);
-                const int pq = (int)(e[j] >> 16);
-#pragma unroll
-                for (int kk = 0; kk < K; ++kk) {
-                    if (j & 1) w[kk] += val * vpf[pq * K + kk];
-                    else t[kk] += val * vpf[pq * K + kk];
-                }
+                if (j & 1) scatter_entry<K>(vpf, e[j], w);   // w += W_e v[pq(e)] (K values: one load)
+                else scatter_entry<K>(vpf, e[j], t);
             }
         }
 #pragma unroll
@@ -394,81 +409,241 @@ __global__ void __launch_bounds__(gather_threads(K)) k_gather_G(SortedArgs a) {
     }
 }
 
-// one T entry of a parameter's run: acc += W * t_s
+// Pairing half of the scatter for one chunk c of kTChunk samples and one
+// group of pq_per_cta consecutive parameters: raw[pq][kk] (or the chunk's
+// partial) = sum over the chunk's samples containing pq of W t_s.
+//
+// The chunk's t_s (K floats per sample, at most 128 KB) are staged in shared
+// memory once per CTA, so every entry's lookup is a shared-memory load
+// instead of an L1/L2 round trip.  The group's runs are consecutive in T, and
+// each warp takes a consecutive share of the group's parameters, so its
+// words form one contiguous stream: the warp keeps NWF blocks of 32 words
+// (128 entries, one word per lane) in flight and loads the next NWF blocks
+// before it works on the current ones, across run boundaries; the lookups of
+// all NWF blocks are issued before their sums.  Every block belongs to one
+// parameter (runs are whole blocks, padding entries weigh zero); when a block
+// starts past the current run, the warp sums its lanes and writes the
+// finished parameter.  Lane L's word of a block holds entries L, L + 32,
+// L + 64, L + 96, so one lookup instruction covers 32 consecutive (sorted)
+// samples.
+constexpr uint32_t kScatterAhead = 4;   // iterations of the scatter's T stream prefetched into L2
+
+// Correlator half of the scatter for chunk c inside pairing CTA (c, g): for
+// every correlator j = g, g + ngrp, ... a shared-memory histogram over j's
+// 4^m states of the chunk's staged t_s (states read correlator-major,
+// coalesced; t_s in sample order, conflict-free), then each nonzero bin is
+// added to craw[corr_off_j + state] (zeroed by the caller) with one vector
+// reduction.  Blocks of few states get one copy of the histogram per warp, so
+// that fewer lanes add to one address.
 template <int K>
-__device__ __forceinline__ void scatter_entry(const float* __restrict__ Tv, int64_t s0, uint32_t v, float (&acc)[K]) {
-    const float wv = __uint_as_float(v << 16);
-    const int64_t t0 = (s0 + (v >> 16)) * K;
+__device__ __forceinline__ void chunk_corr_hist(const SortedArgs& a, int c, int g, int ngrp, const float* tv,
+                                                float* hist) {
+    using TK = typename std::conditional<K == 4, float4, typename std::conditional<K == 2, float2, float>::type>::type;
+    const DevProblem& pb = a.pb;
+    const int64_t s0 = (int64_t)c * kTChunk;
+    const int ns = (int)min((int64_t)kTChunk, a.n_s - s0);
+    const int nw = blockDim.x >> 5, wid = threadIdx.x >> 5, bd = blockDim.x;
+    const TK* tvk = reinterpret_cast<const TK*>(tv);
+    for (int j = g; j < pb.ncorr; j += ngrp) {
+        const int d = 1 << (2 * (pb.corr_ptr[j + 1] - pb.corr_ptr[j]));
+        const int copies = max(1, min(nw, a.hist_cap / (d * K)));
+        float* hw = hist + (size_t)(wid % copies) * d * K;   // [K][d]: one component's bins over all banks
+        __syncthreads();   // the previous correlator's bins are read
+        for (int i = threadIdx.x; i < copies * d * K; i += bd) hist[i] = 0.f;
+        __syncthreads();
+        const cstate_t* st = a.cidxT + (int64_t)j * a.n_s + s0;
+        int s = threadIdx.x;
+        for (; s + 3 * bd < ns; s += 4 * bd) {
+            int k[4];
+            TK t[4];
 #pragma unroll
-    for (int kk = 0; kk < K; ++kk) acc[kk] += wv * __ldg(Tv + t0 + kk);
+            for (int u = 0; u < 4; ++u) {
+                k[u] = (int)__ldcs(st + s + u * bd);
+                t[u] = tvk[s + u * bd];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float* tf = reinterpret_cast<const float*>(&t[u]);
+#pragma unroll
+                for (int kk = 0; kk < K; ++kk) atomicAdd(&hw[kk * d + k[u]], tf[kk]);
+            }
+        }
+        for (; s < ns; s += bd) {
+            const int k = (int)__ldcs(st + s);
+            const TK t = tvk[s];
+            const float* tf = reinterpret_cast<const float*>(&t);
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) atomicAdd(&hw[kk * d + k], tf[kk]);
+        }
+        __syncthreads();
+        float* dst = a.craw + (size_t)pb.corr_off[j] * K;
+        for (int i = threadIdx.x; i < d; i += bd) {
+            float x[K];
+            bool nz = false;
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) {
+                float v = 0.f;
+                for (int cp = 0; cp < copies; ++cp) v += hist[((size_t)cp * K + kk) * d + i];
+                x[kk] = v;
+                nz |= v != 0.f;
+            }
+            if (nz) red_add<K>(dst + (size_t)i * K, x);
+        }
+    }
 }
 
-// scatter: raw[pq][kk] = sum over samples containing pq of W t_s for the warp's
-// pq.  A run is a whole number of kTRun-entry blocks starting on a 512-byte
-// boundary (padding entries weigh zero); lane L's 16-byte word of a block
-// holds entries L, L + 32, L + 64, L + 96, so each t_s lookup instruction
-// covers 32 consecutive entries.  Two blocks (256 entries) per warp in flight.
 template <int K>
-__device__ __forceinline__ void scatter_T_param(const SortedArgs& a, int pq) {
-    const int lane = threadIdx.x & 31;
+__device__ __forceinline__ void scatter_T_chunk(const SortedArgs& a, int c, int grp, int ngrp, float* tv,
+                                                uint32_t* sb, float* hist) {
+    constexpr int NWF = 2;
+    using TK = typename std::conditional<K == 4, float4, typename std::conditional<K == 2, float2, float>::type>::type;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int npf = a.pb.npf;
+    const int p0 = grp * a.pq_per_cta, p1 = min(npf, p0 + a.pq_per_cta);
+    const uint32_t* base = a.base + (size_t)c * (npf + 1);
+    const int per = (p1 - p0 + nw - 1) / nw;
+    const int pa = min(p1, p0 + wid * per), pb = min(p1, pa + per);
+    const uint32_t W0 = __ldg(base + pa) >> 2, W1 = __ldg(base + pb) >> 2;   // the warp's words
+    const uint4* T4 = (const uint4*)a.T;
+    // the stream runs kScatterAhead iterations ahead of the loads as L2
+    // prefetches (bytes in flight without registers)
+    constexpr uint32_t kStep = 32u * NWF, kAhead = kStep * kScatterAhead;
+    if (lane == 0 && W0 < W1) prefetch_l2(T4 + W0, 16u * min(W1 - W0, kAhead + kStep));
+    uint4 u[NWF];
+#pragma unroll
+    for (int i = 0; i < NWF; ++i)
+        u[i] = W0 + 32u * i < W1 ? __ldcs(T4 + W0 + 32u * i + lane) : make_uint4(0u, 0u, 0u, 0u);
+    // stage the chunk's t_s and the group's run ends (in words) while the
+    // first blocks are in flight
+    {
+        const int64_t s0 = (int64_t)c * kTChunk;
+        const int nf = (int)(min((int64_t)kTChunk, a.n_s - s0) * K);
+        const float* src = a.Tv + s0 * K;
+        for (int i = threadIdx.x; i < nf / 4; i += blockDim.x)
+            reinterpret_cast<float4*>(tv)[i] = __ldcg(reinterpret_cast<const float4*>(src) + i);
+        for (int i = (nf / 4) * 4 + threadIdx.x; i < nf; i += blockDim.x) tv[i] = __ldcg(src + i);
+        for (int i = threadIdx.x; i < p1 - p0; i += blockDim.x) sb[i] = __ldg(base + p0 + i + 1) >> 2;
+    }
+    __syncthreads();
+    const TK* tvk = reinterpret_cast<const TK*>(tv);
+    float* out = a.nchunk == 1 ? a.raw : a.part + (size_t)c * npf * K;
     float acc[K], acc2[K];
 #pragma unroll
     for (int kk = 0; kk < K; ++kk) acc[kk] = acc2[kk] = 0.f;
-    const uint4* T4 = (const uint4*)a.T;
-    for (int c = 0; c < a.nchunk; ++c) {
-        const uint32_t* base = a.base + (size_t)c * (a.pb.npf + 1);
-        const uint32_t q0 = base[pq] >> 2, q1 = base[pq + 1] >> 2;
-        const int64_t s0 = (int64_t)c * 65536;
-        uint32_t q = q0 + lane;
-        for (; q + 32 < q1; q += 64) {
-            const uint4 u0 = __ldcs(T4 + q), u1 = __ldcs(T4 + q + 32);
-            scatter_entry<K>(a.Tv, s0, u0.x, acc);
-            scatter_entry<K>(a.Tv, s0, u0.y, acc2);
-            scatter_entry<K>(a.Tv, s0, u0.z, acc);
-            scatter_entry<K>(a.Tv, s0, u0.w, acc2);
-            scatter_entry<K>(a.Tv, s0, u1.x, acc);
-            scatter_entry<K>(a.Tv, s0, u1.y, acc2);
-            scatter_entry<K>(a.Tv, s0, u1.z, acc);
-            scatter_entry<K>(a.Tv, s0, u1.w, acc2);
-        }
-        if (q < q1) {
-            const uint4 u0 = __ldcs(T4 + q);
-            scatter_entry<K>(a.Tv, s0, u0.x, acc);
-            scatter_entry<K>(a.Tv, s0, u0.y, acc2);
-            scatter_entry<K>(a.Tv, s0, u0.z, acc);
-            scatter_entry<K>(a.Tv, s0, u0.w, acc2);
-        }
-    }
+    int pq = pa;
+    uint32_t pend = pa < pb ? sb[pa - p0] : 0u;   // end of pq's run
+    for (uint32_t w = W0; w < W1; w += kStep) {
+        const uint32_t wn = w + kStep;
+        if (lane == 0 && wn + kAhead < W1) prefetch_l2(T4 + wn + kAhead, 16u * min(W1 - (wn + kAhead), kStep));
+        uint4 un[NWF];
 #pragma unroll
-    for (int kk = 0; kk < K; ++kk) {
-        const float v = warp_sum(acc[kk] + acc2[kk]);
-        if (lane == 0) a.raw[(size_t)pq * K + kk] = v;
+        for (int i = 0; i < NWF; ++i)
+            un[i] = wn + 32u * i < W1 ? __ldcs(T4 + wn + 32u * i + lane) : make_uint4(0u, 0u, 0u, 0u);
+        TK x[NWF][4];
+#pragma unroll
+        for (int i = 0; i < NWF; ++i) {
+            x[i][0] = tvk[u[i].x >> 16];
+            x[i][1] = tvk[u[i].y >> 16];
+            x[i][2] = tvk[u[i].z >> 16];
+            x[i][3] = tvk[u[i].w >> 16];
+        }
+#pragma unroll
+        for (int i = 0; i < NWF; ++i) {
+            const uint32_t blk = w + 32u * i;
+            if (blk < W1) {
+                while (blk >= pend) {   // the runs before this block are complete
+#pragma unroll
+                    for (int kk = 0; kk < K; ++kk) {
+                        const float v = warp_sum(acc[kk] + acc2[kk]);
+                        if (lane == 0) out[(size_t)pq * K + kk] = v;
+                        acc[kk] = acc2[kk] = 0.f;
+                    }
+                    ++pq;
+                    pend = sb[pq - p0];
+                }
+                const uint32_t e[4] = {u[i].x, u[i].y, u[i].z, u[i].w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float wv = __uint_as_float(e[j] << 16);
+                    const float* xv = reinterpret_cast<const float*>(&x[i][j]);
+#pragma unroll
+                    for (int kk = 0; kk < K; ++kk) {
+                        if (j & 1) acc2[kk] = fmaf(wv, xv[kk], acc2[kk]);
+                        else acc[kk] = fmaf(wv, xv[kk], acc[kk]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NWF; ++i) u[i] = un[i];
     }
+    for (; pq < pb; ++pq) {   // the last run, and empty runs after it
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) {
+            const float v = warp_sum(acc[kk] + acc2[kk]);
+            if (lane == 0) out[(size_t)pq * K + kk] = v;
+            acc[kk] = acc2[kk] = 0.f;
+        }
+    }
+    if (a.corr_in_cta) chunk_corr_hist<K>(a, c, grp, ngrp, tv, hist);
+    if (a.nchunk == 1) return;
+    // the last of the group's nchunk CTAs to finish sums the chunks' partials
+    // in chunk order (deterministic) and re-arms the group's counter
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(a.done + grp, 1u) == (unsigned)(a.nchunk - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int n = (p1 - p0) * K;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        float x = 0.f;
+        for (int cc = 0; cc < a.nchunk; ++cc) x += __ldcg(a.part + ((size_t)cc * npf + p0) * K + i);
+        a.raw[(size_t)p0 * K + i] = x;
+    }
+    if (threadIdx.x == 0) a.done[grp] = 0u;
 }
 
-// Both halves of the scatter in one launch: the correlator CTAs first
-// (histograms of [0, nhist), or correlator work items of [0, ncb), 8 per CTA,
-// a warp per item), then one pairing amplitude per warp.  The short
-// correlator CTAs go first so that they do not form a tail behind the long
-// pairing runs.
+// The scatter.  Pairing CTA b is chunk b / ngrp and parameter group b % ngrp
+// (CTAs of one chunk run together and read its t_s from L2).  The correlator
+// half: with a.corr_in_cta, histograms of the chunk's staged t_s built by
+// the pairing CTAs after their runs; else shared-memory histograms in CTAs
+// [0, nhist) ahead of the pairing CTAs, taking (class, sample slice) =
+// (b / hist_slices, b % hist_slices); else correlator work items, as CTAs of
+// their own ahead (a.ncb > 0: one item per warp) or after each pairing CTA's
+// runs, strided over all warps of the grid.  Dynamic shared memory: the
+// chunk's t_s (kTChunk K floats), the group's run ends and the in-CTA
+// histograms (from byte hist_off), or a class histogram.
 template <int K>
-__global__ void __launch_bounds__(256) k_scatter_T(SortedArgs a) {
+__global__ void __launch_bounds__(scatter_threads(K), scatter_min_ctas(K)) k_scatter_T(SortedArgs a) {
     if (a.stop && *a.stop) return;
-    extern __shared__ __align__(16) unsigned char hist_smem[];
-    __shared__ float slots[8][32 * K];
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ float slots[scatter_threads(K) / 32][32 * K];
+    const int nw = blockDim.x >> 5, wid = threadIdx.x >> 5;
     int b = (int)blockIdx.x;
     if (b < a.nhist) {
-        corr_hist_cta<K>(a, b / a.hist_slices, b % a.hist_slices, a.hist_slices, (float*)hist_smem);
+        corr_hist_cta<K>(a, b / a.hist_slices, b % a.hist_slices, a.hist_slices, (float*)smem);
         return;
     }
     b -= a.nhist;
     if (b < a.ncb) {
-        const int64_t i = (int64_t)b * 8 + (threadIdx.x >> 5);
-        if (i < (int64_t)*a.n_items) scatter_C_item<K>(a, a.items[i], slots[threadIdx.x >> 5]);
+        const int64_t i = (int64_t)b * nw + wid;
+        if (i < (int64_t)*a.n_items) scatter_C_item<K>(a, a.items[i], slots[wid]);
         return;
     }
-    const int pq = (b - a.ncb) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (pq < a.pb.npf) scatter_T_param<K>(a, pq);
+    b -= a.ncb;
+    const int ngrp = (a.pb.npf + a.pq_per_cta - 1) / a.pq_per_cta;
+    float* tv = (float*)smem;
+    scatter_T_chunk<K>(a, b / ngrp, b % ngrp, ngrp, tv, (uint32_t*)(tv + (size_t)kTChunk * K),
+                       (float*)(smem + a.hist_off));
+    if (a.pb.ncorr == 0 || a.ncb > 0 || a.nhist > 0 || a.corr_in_cta) return;
+    const int64_t n_items = (int64_t)*a.n_items;
+    const int64_t stride = (int64_t)(gridDim.x - a.ncb - a.nhist) * nw;
+    for (int64_t i = (int64_t)b * nw + wid; i < n_items; i += stride) scatter_C_item<K>(a, a.items[i], slots[wid]);
 }
 
 template __global__ void k_gather_G<1, 1>(SortedArgs);
@@ -489,9 +664,11 @@ template __global__ void k_gather_G<1, 15>(SortedArgs);
 template __global__ void k_gather_G<1, 16>(SortedArgs);
 template __global__ void k_gather_G<2, 4>(SortedArgs);
 template __global__ void k_gather_G<2, 8>(SortedArgs);
+template __global__ void k_gather_G<2, 13>(SortedArgs);
 template __global__ void k_gather_G<2, 16>(SortedArgs);
 template __global__ void k_gather_G<4, 4>(SortedArgs);
 template __global__ void k_gather_G<4, 8>(SortedArgs);
+template __global__ void k_gather_G<4, 13>(SortedArgs);
 template __global__ void k_gather_G<4, 16>(SortedArgs);
 template __global__ void k_scatter_T<1>(SortedArgs);
 template __global__ void k_scatter_T<2>(SortedArgs);

@@ -97,16 +97,19 @@ def test_bf16_product_equals_exact_eq7_of_the_store(name):
     h.close()
 
 
-@pytest.mark.parametrize("n", [1, 2, 3, 7, 913])
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 913, 8193, 20001])
 def test_bf16_product_ragged_sample_counts(n):
     """One sample (S = 0: the result is shift v), two, three, seven (one warp
-    of the single pass with a sample more than the others), and a count that
-    leaves the CTAs of the pass with unequal shares."""
+    of the single pass with a sample more than the others), a count that
+    leaves the CTAs of the pass with unequal shares, and counts past one
+    8,192-sample chunk of the parameter-major copy (one sample in the second
+    chunk; two full chunks and a ragged third), whose per-chunk sums the
+    scatter adds up; those also for two and four vectors."""
     wl = inputs.workload("hubbard8x8_2x3", n_walkers=n, samples_per_walker=1)
     h = _handle(wl)
     cfgs = inputs.draw_configs(np.random.default_rng(n), n, wl.n_sites, wl.n_up, wl.n_dn)
     V.vmc_measure(h, cfgs)
-    _check_products(wl, h, ks=(1,))
+    _check_products(wl, h, ks=(1,) if n < 8192 else (1, 2, 4))
     h.close()
 
 
