@@ -17,6 +17,7 @@ namespace {
 constexpr int kMaxK = 4;
 constexpr int kNumPart = 256;   // blocks of the reduction kernels
 constexpr int kChunk = 16;      // CG iterations between host convergence checks
+constexpr int kBlockInnerMax = 4096;   // block CG steps of one inner solve at most
 constexpr int kScalX0 = 7;      // d_scal slot of the SR update's x_0
 constexpr int kMaxBatch = 16;   // problems per batched launch
 
@@ -1955,104 +1956,63 @@ static int inner_solve(vmc_ctx* h, int mode, const double* r, double rnorm, doub
     return VMC_OK;
 }
 
-// 4 x 4 system A X = B (row-major) by Gaussian elimination with partial
-// pivoting; false if a pivot vanishes relative to the matrix scale
-static bool solve4(const double* A_in, const double* B_in, double* X) {
-    double A[16], B[16], scale = 0.0;
-    memcpy(A, A_in, sizeof(A));
-    memcpy(B, B_in, sizeof(B));
-    for (double v : A) scale = std::max(scale, std::fabs(v));
-    if (!(scale > 0.0) || !std::isfinite(scale)) return false;
-    for (int k = 0; k < 4; ++k) {
-        int piv = k;
-        for (int i = k + 1; i < 4; ++i)
-            if (std::fabs(A[4 * i + k]) > std::fabs(A[4 * piv + k])) piv = i;
-        if (!(std::fabs(A[4 * piv + k]) > 1e-14 * scale)) return false;
-        if (piv != k)
-            for (int j = 0; j < 4; ++j) { std::swap(A[4 * k + j], A[4 * piv + j]); std::swap(B[4 * k + j], B[4 * piv + j]); }
-        for (int i = k + 1; i < 4; ++i) {
-            const double f = A[4 * i + k] / A[4 * k + k];
-            for (int j = 0; j < 4; ++j) { A[4 * i + j] -= f * A[4 * k + j]; B[4 * i + j] -= f * B[4 * k + j]; }
-        }
-    }
-    for (int c = 0; c < 4; ++c)
-        for (int i = 3; i >= 0; --i) {
-            double v = B[4 * i + c];
-            for (int j = i + 1; j < 4; ++j) v -= A[4 * i + j] * X[4 * j + c];
-            X[4 * i + c] = v / A[4 * i + i];
-        }
-    return true;
-}
-
-// the same, where a block column is exactly zero (a parameter group with no
-// right-hand side, e.g. same-spin pairing with one electron per spin): its
-// row and column of A and its row of B vanish, so it gets a unit diagonal
-// and a zero row in X.  Any other singular A is a breakdown (false).
-static bool solve4_reg(const double* A, const double* B, double* X) {
-    if (solve4(A, B, X)) return true;
-    double Ar[16];
-    memcpy(Ar, A, sizeof(Ar));
-    bool any = false;
-    for (int i = 0; i < 4; ++i) {
-        bool zero = true;
-        for (int j = 0; j < 4; ++j) zero = zero && A[4 * i + j] == 0.0 && A[4 * j + i] == 0.0 && B[4 * i + j] == 0.0;
-        if (zero) { Ar[5 * i] = 1.0; any = true; }
-    }
-    return any && solve4(Ar, B, X);
-}
-
-static int gram4(vmc_ctx* h, const float* U, const float* V, double* out, cudaStream_t st) {
-    k_bcg_gram<<<kNumPart, 256, 0, st>>>(U, V, h->nv, h->d_bcg);
-    k_lm_dots_reduce<<<1, 64, 0, st>>>(h->d_bcg, kNumPart, 16, h->d_bcg + (size_t)kNumPart * 16);
-    h->n_launch += 2;
-    VCK(cudaMemcpyAsync(out, h->d_bcg + (size_t)kNumPart * 16, 16 * sizeof(double), cudaMemcpyDeviceToHost, st));
-    VCK(cudaStreamSynchronize(st));
-    return VMC_OK;
-}
-
 // z = M^{-1} r by enlarged block CG on the BF16 operator: the unit-norm
 // right-hand side split into four parameter-group columns, O'Leary's block
 // recurrences (alpha = (P^T Q)^{-1} R^T R, beta = (R^T R)^{-1} R_new^T R_new),
 // stopped when the residual of the column sum, |sum_j R_j|^2 = sum of the
-// entries of R^T R, meets itol; z = |r| sum_j X_j.
+// entries of R^T R, meets itol; z = |r| sum_j X_j.  The iteration runs on the
+// device (bcg.cu): per step the four-vector product, the P^T Q Gram with the
+// alpha solve, the X/R update with the new R^T R Gram, the beta solve with
+// the stopping test, and the new directions with their Obar . P partials
+// (the next product's centering); the host reads the state every kChunk
+// steps.
 static int inner_block(vmc_ctx* h, const double* r, double rnorm, double* z, double shift, double itol,
                        int max_iter, int* iters, cudaStream_t st) {
     const int64_t n = h->nv;
-    if (!h->d_bcg) VCK(h->alloc(&h->d_bcg, (size_t)kNumPart * 16 + 64));
+    const size_t npart = (size_t)kNumPart * kMaxK * 16;
+    if (!h->d_bcg) VCK(h->alloc(&h->d_bcg, npart + (sizeof(BcgState) + 7) / 8));
+    double* gpart = h->d_bcg;
+    BcgState* S = (BcgState*)(h->d_bcg + npart);
+    double* obp_part = h->part(5);
     float *X = h->d_x32, *R = h->d_r32, *P = h->d_p32, *Q = h->d_q32;
-    double* dal = h->d_bcg + (size_t)kNumPart * 16 + 16;
-    double* dbe = dal + 16;
-    const unsigned vg = (unsigned)vgrid(h, 1);
+    const int vg = vgrid(h, 1), vg4 = vgrid(h, 4);
+    *iters = 0;
     k_cast<float><<<kNumPart, 256, 0, st>>>(r, h->d_b32, n, 1.0 / rnorm);
     k_bcg_split<<<vg, 256, 0, st>>>(h->d_b32, R, n, h->ncp, h->corr_off[h->ncorr / 2], h->d_pq_of, h->ns);
     h->n_launch += 2;
     VCK(cudaMemsetAsync(X, 0, sizeof(float) * 4 * n, st));
     VCK(cudaMemcpyAsync(P, R, sizeof(float) * 4 * n, cudaMemcpyDeviceToDevice, st));
-    double RR[16], RRn[16], PQ[16], al[16], be[16];
-    int rc = gram4(h, R, R, RR, st);
-    if (rc) return rc;
-    double b2 = 0.0;
-    for (double v : RR) b2 += v;
-    int it = 0, steps = 0;
-    while (it < max_iter) {
-        rc = apply_S_impl<__nv_bfloat16, float, 4>(h, h->d_pf16, 2, P, Q, shift, nullptr, nullptr, nullptr, st);
-        if (rc) return rc;
-        ++it;
-        if ((rc = gram4(h, P, Q, PQ, st))) return rc;
-        if (!solve4_reg(PQ, RR, al)) break;
-        VCK(cudaMemcpyAsync(dal, al, sizeof(al), cudaMemcpyHostToDevice, st));
-        k_bcg_step<<<vg, 256, 0, st>>>(X, R, P, Q, dal, n); h->n_launch++;
-        ++steps;
-        if ((rc = gram4(h, R, R, RRn, st))) return rc;
-        double res2 = 0.0;
-        for (double v : RRn) res2 += v;
-        if (res2 <= itol * itol * b2) break;
-        if (!solve4_reg(RR, RRn, be)) break;
-        VCK(cudaMemcpyAsync(dbe, be, sizeof(be), cudaMemcpyHostToDevice, st));
-        k_bcg_dir<<<vg, 256, 0, st>>>(P, R, dbe, n); h->n_launch++;
-        memcpy(RR, RRn, sizeof(RR));
+    VCK(cudaMemsetAsync(h->d_stop, 0, sizeof(int), st));
+    k_bcg_gram<<<vg, 256, 0, st>>>(R, R, n, gpart, nullptr);
+    k_bcg_start<<<1, 256, 0, st>>>(gpart, vg, S, itol);
+    k_dot_part<double, float, 4><<<vg4, 256, 0, st>>>(h->d_Obar[2], P, n, obp_part, nullptr);
+    h->n_launch += 3;
+    VCK(cudaGetLastError());
+    // an inner solve that has not met itol after kBlockInnerMax steps returns
+    // what it has: the flexible outer iteration takes any preconditioner
+    max_iter = std::min(max_iter, kBlockInnerMax);
+    for (int done = 0; !done;) {
+        for (int j = 0; j < kChunk; ++j) {
+            int rc = apply_S_impl<__nv_bfloat16, float, 4>(h, h->d_pf16, 2, P, Q, shift, h->d_stop, obp_part, nullptr, st);
+            if (rc) return rc;
+            k_bcg_gram<<<vg, 256, 0, st>>>(P, Q, n, gpart, h->d_stop);
+            k_bcg_alpha<<<1, 256, 0, st>>>(gpart, vg, S, h->d_stop);
+            k_bcg_step<<<vg, 256, 0, st>>>(X, R, P, Q, S, n, gpart, h->d_stop);
+            k_bcg_beta<<<1, 256, 0, st>>>(gpart, vg, S, h->d_stop, max_iter);
+            k_bcg_dir<<<vg4, 256, 0, st>>>(P, R, S, h->d_Obar[2], n, obp_part, h->d_stop);
+            h->n_launch += 5;
+            VCK(cudaGetLastError());
+        }
+        BcgState hs;
+        int stop = 0;
+        VCK(cudaMemcpyAsync(&hs, S, sizeof(hs), cudaMemcpyDeviceToHost, st));
+        VCK(cudaMemcpyAsync(&stop, h->d_stop, sizeof(int), cudaMemcpyDeviceToHost, st));
+        VCK(cudaStreamSynchronize(st));
+        if (stop || hs.it >= max_iter) {
+            done = 1;
+            *iters = hs.steps > 0 ? hs.it : 0;   // 0: no block step was possible
+        }
     }
-    *iters = steps > 0 ? it : 0;   // 0: no block step was possible
     VCK(cudaMemsetAsync(z, 0, sizeof(double) * n, st));
     for (int j = 0; j < 4; ++j) {
         k_axpy_to64<float><<<kNumPart, 256, 0, st>>>(z, X + (size_t)j * n, rnorm, n);

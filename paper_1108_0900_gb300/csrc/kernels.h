@@ -370,8 +370,22 @@ __global__ void k_lm_update(UpdateArgs a, const double* x, double scale);
 // enlarged block CG (bcg.cu): [4][n] FP32 block vectors, FP64 4 x 4 algebra
 __global__ void k_bcg_split(const float* b, float* B, int64_t n, int64_t ncp, int64_t corr_split,
                             const uint32_t* pq_of, int ns);
-__global__ void k_bcg_gram(const float* U, const float* V, int64_t n, double* part);
-__global__ void k_bcg_step(float* X, float* R, const float* P, const float* Q, const double* alpha, int64_t n);
-__global__ void k_bcg_dir(float* P, const float* R, const double* beta, int64_t n);
+// device state of the block CG iteration (bcg.cu)
+struct BcgState {
+    double RR[16];     // R^T R of the current residual block
+    double al[16];     // alpha = (P^T Q)^{-1} R^T R
+    double be[16];     // beta = (R^T R)^{-1} R_new^T R_new
+    double b2, thr;    // |b|^2 of the column sum, and the stopping threshold itol^2 b2
+    int it, steps;     // products, completed steps
+    int breakdown;     // a singular 4 x 4 step system stopped the solve
+};
+__global__ void k_bcg_gram(const float* U, const float* V, int64_t n, double* part, const int* stop);
+__global__ void k_bcg_start(const double* part, int nb, BcgState* S, double itol);
+__global__ void k_bcg_alpha(const double* part, int nb, BcgState* S, int* stop);
+__global__ void k_bcg_beta(const double* part, int nb, BcgState* S, int* stop, int max_iter);
+__global__ void k_bcg_step(float* X, float* R, const float* P, const float* Q, const BcgState* S, int64_t n,
+                           double* part, const int* stop);
+__global__ void k_bcg_dir(float* P, const float* R, const BcgState* S, const double* Obar, int64_t n,
+                          double* obv_part, const int* stop);
 
 }  // namespace vmc
