@@ -569,13 +569,16 @@ def run_sv_only(args):
     cfgs = inputs.draw_configs(np.random.default_rng(555), wl.n_samples, wl.n_sites, wl.n_up, wl.n_dn)
     V.vmc_measure(h, cfgs)
     peak, peak_kind = peaks()
-    v = torch.from_numpy(np.random.default_rng(1).standard_normal(wl.n_params)).cuda()
+    rng = np.random.default_rng(1)
+    v1 = torch.from_numpy(rng.standard_normal(wl.n_params)).cuda()
+    v4 = torch.from_numpy(rng.standard_normal((4, wl.n_params))).cuda()
     out = {}
-    for name, store, path in (("bf16_sorted", V.VMC_STORE_BF16, V.VMC_PATH_SORTED),
-                              ("bf16_fused", V.VMC_STORE_BF16, V.VMC_PATH_FUSED),
-                              ("fp32_f32acc", V.VMC_STORE_FP32_F32ACC, V.VMC_PATH_AUTO),
-                              ("fp32_f64acc", V.VMC_STORE_FP32, V.VMC_PATH_AUTO),
-                              ("fp64", V.VMC_STORE_FP64, V.VMC_PATH_AUTO)):
+    for name, store, path, v in (("bf16_sorted", V.VMC_STORE_BF16, V.VMC_PATH_SORTED, v1),
+                                 ("bf16_fused", V.VMC_STORE_BF16, V.VMC_PATH_FUSED, v1),
+                                 ("fp32_f32acc", V.VMC_STORE_FP32_F32ACC, V.VMC_PATH_AUTO, v1),
+                                 ("fp32_f64acc", V.VMC_STORE_FP32, V.VMC_PATH_AUTO, v1),
+                                 ("fp64", V.VMC_STORE_FP64, V.VMC_PATH_AUTO, v1),
+                                 ("bf16_sorted_4_vectors", V.VMC_STORE_BF16, V.VMC_PATH_SORTED, v4)):
         V.vmc_set_product_path(h, path)
         for _ in range(2):
             V.sr_apply_S(h, v, wl.shift, store)
