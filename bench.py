@@ -100,10 +100,11 @@ class Clocks:
 
 # DRAM bytes per BF16 product on this workload, counted by ncu
 # (dram__bytes_read + dram__bytes_write, one capture per path): the sorted
-# two-pass product reads G (426 MB) and T with the correlator runs (425 MB);
-# the fused single pass reads G once (426 MB) plus the per-CTA images and the
-# correlator states in its finish (24 MB).
-PASS_DRAM_BYTES = {"sorted": 851.0e6, "fused": 453.0e6}
+# two-pass product reads G (429 MB with its writes) and T in 8,192-sample
+# chunks with the correlator states (446 MB); the fused single pass reads G
+# once (430 MB) plus the per-CTA images and the correlator states in its
+# finish (23 MB).
+PASS_DRAM_BYTES = {"sorted": 875.0e6, "fused": 453.0e6}
 PASS_KERNELS = {"sorted": "k_gather_G<1,U> + k_scatter_T<1> (sorted two-pass Eq. 7 product, BF16 store)",
                 "fused": "k_sv_fused<U> + k_sv_finish (fused single-pass Eq. 7 product, BF16 store)",
                 "staged": "k_sr_stream<bf16,1> + k_corr_scatter + k_reduce_pf (staged per-sample pass)",
