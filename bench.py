@@ -106,6 +106,7 @@ class Clocks:
 # finish (23 MB).
 PASS_DRAM_BYTES = {"sorted": 875.0e6, "fused": 453.0e6}
 PASS_KERNELS = {"sorted": "k_gather_G<1,U> + k_scatter_T<1> (sorted two-pass Eq. 7 product, BF16 store)",
+                "compact": "k_gather_C<U> + k_scatter_T<1> (two-pass Eq. 7 product, compact gather, BF16 store)",
                 "fused": "k_sv_fused<U> + k_sv_finish (fused single-pass Eq. 7 product, BF16 store)",
                 "staged": "k_sr_stream<bf16,1> + k_corr_scatter + k_reduce_pf (staged per-sample pass)",
                 "generic": "k_sr_main<bf16,float,1> + k_corr_scatter + k_reduce_pf (generic per-sample pass)"}

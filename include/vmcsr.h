@@ -429,22 +429,29 @@ int sr_pairing_product_noalloc(int64_t n_s, int n_sites, int n_up, int n_dn, con
  *                    scattering t_s O_s into private shared-memory images;
  *   VMC_PATH_STAGED  one or two vectors: a per-sample pass over the store
  *                    itself, samples staged in shared memory by bulk copies;
- *   VMC_PATH_GENERIC the plain per-sample pass (any number of vectors).
+ *   VMC_PATH_GENERIC the plain per-sample pass (any number of vectors);
+ *   VMC_PATH_COMPACT one vector only: the two-pass product whose gather reads
+ *                    a copy of the 2-byte values alone (in the row-major
+ *                    order of electron pairs) and forms each element's index
+ *                    from the sample's occupation; more than one vector takes
+ *                    VMC_PATH_SORTED.
  * A path that does not apply to a problem falls back to the next applicable
- * one in this order.  VMC_PATH_STAGED / GENERIC also select the pass of the
- * FP32 store with FP32 accumulation. */
+ * one in the order SORTED, FUSED, STAGED, GENERIC (COMPACT to SORTED).
+ * VMC_PATH_STAGED / GENERIC also select the pass of the FP32 store with FP32
+ * accumulation. */
 #define VMC_PATH_AUTO 0
 #define VMC_PATH_SORTED 1
 #define VMC_PATH_FUSED 2
 #define VMC_PATH_STAGED 3
 #define VMC_PATH_GENERIC 4
+#define VMC_PATH_COMPACT 5
 int vmc_set_product_path(vmc_handle h, int path);
 
 typedef struct {
     int path;        /* fastest one-vector path (VMC_PATH_*), used under AUTO     */
     int path4;       /* fastest four-vector path, used under AUTO for 2 and 4     */
-    double ms[5];    /* mean time of one one-vector product per path, < 0 if n/a  */
-    double ms4[5];   /* the same for four vectors                                 */
+    double ms[6];    /* mean time of one one-vector product per path, < 0 if n/a  */
+    double ms4[6];   /* the same for four vectors                                 */
 } vmc_tune_info;
 
 /* Autotuner: times `reps` BF16 products of one and of four vectors on every
@@ -456,7 +463,7 @@ int sr_autotune(vmc_handle h, int reps, vmc_tune_info* info, void* stream);
 /* Set the AUTO choice directly (a choice sr_autotune made earlier for the
  * same workload, e.g. read back from a cache): one-vector products on
  * `path`, two- and four-vector products on `path4` (VMC_PATH_SORTED ..
- * VMC_PATH_GENERIC). */
+ * VMC_PATH_COMPACT). */
 int vmc_set_auto_paths(vmc_handle h, int path, int path4);
 
 /* Failure detection (no counterpart in the paper).  The streaming products

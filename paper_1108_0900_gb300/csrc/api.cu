@@ -54,6 +54,7 @@ struct vmc_ctx {
     int last_gather_grid = 0;    // CTAs (tt partials) of the last sorted gather
     bool sorted_ok = false;      // G / T built for the current samples
     bool use_fused = true;       // fused single-pass product over G (BF16 store, one vector)
+    bool use_compact = true;     // two-pass product with the compact gather over G16 (one vector)
     int path = VMC_PATH_AUTO;    // product path set by the caller (VMC_PATH_*)
     int auto_path = VMC_PATH_SORTED;   // one-vector BF16 path used under AUTO (sr_autotune may change it)
     int auto_path4 = VMC_PATH_SORTED;  // two- and four-vector BF16 path used under AUTO
@@ -126,6 +127,9 @@ struct vmc_ctx {
     double* d_part = nullptr;   // 8 slots x kNumPart x kMaxK
     double* d_pfraw = nullptr;  // [npf][K] reduced pairing-block sums (FP64 or FP32 per pass)
     uint32_t *d_G = nullptr, *d_Tsort = nullptr, *d_counts = nullptr, *d_total = nullptr, *d_base = nullptr;
+    uint16_t* d_G16 = nullptr;   // [ncap][Gst16] BF16 values in the row-major pair order (compact gather)
+    uint16_t* d_wtab = nullptr;  // [Gst16 / 8] pair (a | b << 8) of the first value of each 16-byte word
+    int64_t Gst16 = 0;
     float* d_tpart = nullptr;    // [chunks][npf][kMaxK] per-chunk pairing sums of the sorted scatter
     bool scatter_corr_front = true;   // correlator items of the sorted scatter as CTAs of their own
     bool scatter_corr_hist = true;    // correlator half of the sorted scatter as class histograms
@@ -509,6 +513,21 @@ extern "C" int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, co
                 return fail(VMC_ERR_CUDA);
         }
         ACK(h->alloc(&h->d_G, (size_t)h->ncap * h->Gst));
+        // compact copy: the values of each row in the row-major pair order,
+        // rows padded to 16 bytes, and the pair of each 16-byte word's first value
+        h->Gst16 = round_up(h->P, 8);
+        if (N <= 255) {
+            ACK(h->alloc(&h->d_G16, (size_t)h->ncap * h->Gst16));
+            std::vector<uint16_t> wt((size_t)(h->Gst16 / 8));
+            int a = 0, b = 1;
+            for (int64_t r = 0; r < h->Gst16; ++r) {
+                if (r % 8 == 0) wt[(size_t)(r / 8)] = r < h->P ? (uint16_t)(a | b << 8) : (uint16_t)((N - 1) | N << 8);
+                if (++b == N) { ++a; b = a + 1; }
+            }
+            ACK(h->alloc(&h->d_wtab, wt.size()));
+            if (cudaMemcpy(h->d_wtab, wt.data(), sizeof(uint16_t) * wt.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+                return fail(VMC_ERR_CUDA);
+        }
         h->t_chunk = (size_t)kTChunk * h->P + (size_t)h->npf * kTRun;   // padded runs of one chunk
         ACK(h->alloc(&h->d_Tsort, (size_t)h->sort_nchunk * h->t_chunk));
         if (h->sort_nchunk > 1) ACK(h->alloc(&h->d_tpart, (size_t)h->sort_nchunk * h->npf * kMaxK));
@@ -1185,7 +1204,8 @@ static int ensure_G(vmc_ctx* h, cudaStream_t st) {
     if (h->g_ok) return VMC_OK;
     if (!h->d_G || h->n_s == 0) return VMC_ERR_STATE;
     k_build_G<<<(unsigned)((h->n_s + 7) / 8), 256, 0, st>>>(h->pb, h->n_s, h->d_socc, h->Nst, h->d_pf16, h->Pst,
-                                                           h->d_fulltab, h->gwq, h->Gst, h->d_G); h->n_launch++;
+                                                           h->d_fulltab, h->gwq, h->Gst, h->d_G, h->d_G16,
+                                                           h->Gst16); h->n_launch++;
     VCK(cudaGetLastError());
     h->g_ok = true;
     return VMC_OK;
@@ -1300,6 +1320,34 @@ static size_t corr_hist_setup(const vmc_ctx* h, int K, SortedArgs* a) {
     return bytes;
 }
 
+// product path of a K-vector product (VMC_PATH_*): the caller's choice, or
+// under AUTO the autotuner's (default: the sorted two-pass product)
+static int product_path(const vmc_ctx* h, int K) {
+    if (h->path != VMC_PATH_AUTO) return h->path;
+    return K == 1 ? h->auto_path : h->auto_path4;
+}
+
+// the compact gather applies: its copy exists, at most 128 correlators, the
+// v table, the word table and one occupation row per warp in shared memory,
+// rows of at most 8 words per lane
+static size_t compact_smem(const vmc_ctx* h) {
+    const size_t nw16 = (size_t)(h->Gst16 / 8);
+    return (size_t)h->npf * 4 + (size_t)(h->ncorr + 1) * 4 + (nw16 + 7) / 8 * 16 +
+           (size_t)(kCompactThreads / 32) * (h->Nst + 16);
+}
+static bool compact_usable(const vmc_ctx* h) {
+    if (!h->use_compact || !h->d_G16 || !h->d_wtab || h->ncorr > 32 * kCorrPerLane) return false;
+    if (compact_smem(h) + 1024 > h->smem_optin) return false;
+    const int64_t u = (h->Gst16 / 8 + 31) / 32;
+    return u >= 1 && u <= 8;
+}
+
+using CompactKern = void (*)(SortedArgs, const uint16_t*, int64_t, const uint16_t*, const uint8_t*, int);
+static CompactKern compact_kernel(int64_t u) {
+    static const CompactKern tab[5] = {k_gather_C<4>, k_gather_C<5>, k_gather_C<6>, k_gather_C<7>, k_gather_C<8>};
+    return tab[std::max<int64_t>(0, u - 4)];
+}
+
 // gather + parameter-major scatter for the BF16 store; the centered t_s go to
 // Tv, the pairing sums to d_pfraw and the correlator sums to d_corrraw (FP32)
 template <int K>
@@ -1332,18 +1380,34 @@ static int launch_sorted(vmc_ctx* h, const float* V, const float* invC, const do
     const int sthreads = scatter_threads(K), swarps = sthreads / 32;
     a.tt_part = tt_part;
     a.stop = stop;
-    const size_t smem = (size_t)h->npf * K * 4 + (size_t)(h->ncorr + 1) * 4;
-    auto gk = gather_kernel<K>((int)((h->Gst / 4 + 31) / 32));
-    VCK(cudaFuncSetAttribute(gk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    const int gthreads = gather_threads(K), gwarps = gthreads / 32;
-    VCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gk, gthreads, smem));
-    int grid = h->nsm * std::max(1, per_sm);
-    const int64_t need = (h->n_s + gwarps - 1) / gwarps;
-    if (need < grid) grid = (int)std::max<int64_t>(1, need);
-    grid = std::min(grid, kNumPart * kMaxK);   // one partial slot of tt sums
-    gk<<<grid, gthreads, smem, st>>>(a); h->n_launch++;
-    h->last_gather_grid = grid;
+    if (K == 1 && product_path(h, 1) == VMC_PATH_COMPACT && compact_usable(h)) {
+        // the compact gather over G16 (occupation rows give the indices)
+        const size_t smem = compact_smem(h);
+        auto ck = compact_kernel((h->Gst16 / 8 + 31) / 32);
+        VCK(cudaFuncSetAttribute(ck, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0;
+        const int cwarps = kCompactThreads / 32;
+        VCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ck, kCompactThreads, smem));
+        int grid = h->nsm * std::max(1, per_sm);
+        const int64_t need = (h->n_s + cwarps - 1) / cwarps;
+        if (need < grid) grid = (int)std::max<int64_t>(1, need);
+        grid = std::min(grid, kNumPart * kMaxK);   // one partial slot of tt sums
+        ck<<<grid, kCompactThreads, smem, st>>>(a, h->d_G16, h->Gst16, h->d_wtab, h->d_socc, h->Nst); h->n_launch++;
+        h->last_gather_grid = grid;
+    } else {
+        const size_t smem = (size_t)h->npf * K * 4 + (size_t)(h->ncorr + 1) * 4;
+        auto gk = gather_kernel<K>((int)((h->Gst / 4 + 31) / 32));
+        VCK(cudaFuncSetAttribute(gk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0;
+        const int gthreads = gather_threads(K), gwarps = gthreads / 32;
+        VCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gk, gthreads, smem));
+        int grid = h->nsm * std::max(1, per_sm);
+        const int64_t need = (h->n_s + gwarps - 1) / gwarps;
+        if (need < grid) grid = (int)std::max<int64_t>(1, need);
+        grid = std::min(grid, kNumPart * kMaxK);   // one partial slot of tt sums
+        gk<<<grid, gthreads, smem, st>>>(a); h->n_launch++;
+        h->last_gather_grid = grid;
+    }
     // correlator sums accumulate into zero (the fused CG update re-zeroes
     // them as it reads them, so its products skip this)
     if (h->ncp > 0 && !craw_zero) VCK(cudaMemsetAsync(h->d_corrraw, 0, sizeof(float) * h->ncp * K, st));
@@ -1382,17 +1446,22 @@ static int launch_sorted(vmc_ctx* h, const float* V, const float* invC, const do
                 a.ncb = h->scatter_corr_front ? (int)((h->max_items + swarps - 1) / swarps) : 0;
             }
         }
-        a.hist_off = (int)(ssm_tab + run_bytes);   // bytes: the in-CTA histograms
+        // shared memory for a group of pq run ends: one estimate for the
+        // occupancy query, then the group size it gives
         const size_t in_cta = (size_t)a.hist_cap * 4;
-        const size_t ssm_max = std::max(hsm, ssm_tab + run_bytes + in_cta);
+        auto run_of = [](int pq) { return ((size_t)(pq + 1) * 4 + 15) / 16 * 16; };
+        auto smem_of = [&](int pq) { return std::max(hsm, ssm_tab + run_of(pq) + in_cta); };
+        const int pq_est = std::min(pq_cap, std::max(swarps, h->npf / h->nsm + 64));
+        VCK(cudaFuncSetAttribute(k_scatter_T<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_of(pq_cap)));
         int per = 0;
-        VCK(cudaFuncSetAttribute(k_scatter_T<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssm_max));
-        VCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_scatter_T<K>, sthreads, ssm_max));
+        VCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_scatter_T<K>, sthreads, smem_of(pq_est)));
         const int64_t resident = (int64_t)h->nsm * std::max(1, per);
         int ngrp = (int)std::max<int64_t>(1, std::min<int64_t>(h->npf, (resident + a.nchunk - 1) / a.nchunk));
         a.pq_per_cta = std::min(pq_cap, std::max(swarps, (h->npf + ngrp - 1) / ngrp));
         ngrp = (h->npf + a.pq_per_cta - 1) / a.pq_per_cta;
-        k_scatter_T<K><<<a.nhist + a.ncb + a.nchunk * ngrp, sthreads, ssm_max, st>>>(a); h->n_launch++;
+        a.hist_off = (int)(ssm_tab + run_of(a.pq_per_cta));   // bytes: the in-CTA histograms
+        k_scatter_T<K><<<a.nhist + a.ncb + a.nchunk * ngrp, sthreads, smem_of(a.pq_per_cta), st>>>(a);
+        h->n_launch++;
     }
     VCK(cudaGetLastError());
     if (h->prof) {
@@ -1471,13 +1540,6 @@ static int launch_fused(vmc_ctx* h, const float* V, const float* invC, const dou
     return VMC_OK;
 }
 
-// product path of a K-vector product (VMC_PATH_*): the caller's choice, or
-// under AUTO the autotuner's (default: the sorted two-pass product)
-static int product_path(const vmc_ctx* h, int K) {
-    if (h->path != VMC_PATH_AUTO) return h->path;
-    return K == 1 ? h->auto_path : h->auto_path4;
-}
-
 // out = (S + shift I) V with K vectors, V/out in AT precision ([K][nv]), over
 // store s_pf whose sample means are Obar of kind `kind`.  obv_part holds
 // vgrid(h, K) partial dots Obar . V unless null (then computed first: the
@@ -1509,7 +1571,8 @@ static int apply_S_impl(vmc_ctx* h, const void* s_pf, int kind, const AT* V, AT*
         }
     }
     if constexpr (sizeof(AT) == 4 && sizeof(ST) == 2) {
-        if (!sorted && (path == VMC_PATH_SORTED || path == VMC_PATH_FUSED) && h->use_sorted && h->d_G) {
+        if (!sorted && (path == VMC_PATH_SORTED || path == VMC_PATH_FUSED || path == VMC_PATH_COMPACT) &&
+            h->use_sorted && h->d_G) {
             rc = launch_sorted<K>(h, (const float*)V, (const float*)invC, obv_part, (float*)T, stop, st);
             if (rc != VMC_OK && rc != VMC_ERR_UNSUPPORTED) return rc;
             sorted = rc == VMC_OK;
@@ -1717,14 +1780,14 @@ extern "C" int sr_apply_S(vmc_handle h, const double* V, double* out, int k, dou
 }
 
 extern "C" int vmc_set_product_path(vmc_handle h, int path) {
-    if (!h || path < VMC_PATH_AUTO || path > VMC_PATH_GENERIC) return VMC_ERR_INVALID_ARG;
+    if (!h || path < VMC_PATH_AUTO || path > VMC_PATH_COMPACT) return VMC_ERR_INVALID_ARG;
     h->path = path;
     return VMC_OK;
 }
 
 extern "C" int vmc_set_auto_paths(vmc_handle h, int path, int path4) {
-    if (!h || path < VMC_PATH_SORTED || path > VMC_PATH_GENERIC || path4 < VMC_PATH_SORTED ||
-        path4 > VMC_PATH_GENERIC)
+    if (!h || path < VMC_PATH_SORTED || path > VMC_PATH_COMPACT || path4 < VMC_PATH_SORTED ||
+        path4 > VMC_PATH_COMPACT)
         return VMC_ERR_INVALID_ARG;
     h->auto_path = path;
     h->auto_path4 = path4;
@@ -1737,6 +1800,7 @@ template <int K>
 static int time_path(vmc_ctx* h, int path, int reps, cudaStream_t st, double* ms) {
     *ms = -1.0;
     if (path == VMC_PATH_FUSED && (K != 1 || !fused_usable(h))) return VMC_OK;
+    if (path == VMC_PATH_COMPACT && (K != 1 || !compact_usable(h) || !sorted_usable<1>(h))) return VMC_OK;
     if (path == VMC_PATH_SORTED && !sorted_usable<K>(h)) return VMC_OK;
     if (path == VMC_PATH_STAGED && (K > 2 || !h->use_stream)) return VMC_OK;
     const int saved = h->path;
@@ -1773,7 +1837,7 @@ extern "C" int sr_autotune(vmc_handle h, int reps, vmc_tune_info* info, void* st
     double best = -1.0, best4 = -1.0;
     inf.path = VMC_PATH_SORTED;
     inf.path4 = VMC_PATH_SORTED;
-    for (int p = VMC_PATH_SORTED; p <= VMC_PATH_GENERIC; ++p) {
+    for (int p = VMC_PATH_SORTED; p <= VMC_PATH_COMPACT; ++p) {
         double ms = -1.0, ms4 = -1.0;
         if ((rc = time_path<1>(h, p, reps, st, &ms))) return rc;
         if ((rc = time_path<4>(h, p, reps, st, &ms4))) return rc;
@@ -1830,7 +1894,8 @@ static int cg_loop(vmc_ctx* h, const void* s_pf, int kind, const VT* b, VT* x, V
     if constexpr (sizeof(ST) == 2 && sizeof(VT) == 4) {
         const int path = product_path(h, 1);
         single = path == VMC_PATH_FUSED && fused_usable(h);
-        fused = single || ((path == VMC_PATH_SORTED || path == VMC_PATH_FUSED) && sorted_usable<1>(h));
+        fused = single || ((path == VMC_PATH_SORTED || path == VMC_PATH_FUSED || path == VMC_PATH_COMPACT) &&
+                           sorted_usable<1>(h));
     }
     if (fused && h->ncp > 0) VCK(cudaMemsetAsync(h->d_corrraw, 0, sizeof(float) * h->ncp, st));
     while (!done) {

@@ -289,7 +289,11 @@ constexpr int kInstPerUnit = 4;    // correlators of one class per cluster of th
 constexpr int kGParts = 4;         // parts of consecutive pq per G row (warps per image of the single pass)
 __global__ void __launch_bounds__(256) k_build_G(DevProblem pb, int64_t n_s, const uint8_t* s_occ, int Nst,
                                                  const __nv_bfloat16* pf16, int64_t Pst, const uint32_t* fulltab,
-                                                 int wq, int64_t Gst, uint32_t* G);
+                                                 int wq, int64_t Gst, uint32_t* G, uint16_t* G16, int64_t Gst16);
+constexpr int kCompactThreads = 512;   // threads per CTA of the compact gather
+template <int U>
+__global__ void __launch_bounds__(512) k_gather_C(SortedArgs a, const uint16_t* G16, int64_t Gst16,
+                                                 const uint16_t* wtab, const uint8_t* s_occ, int Nst);
 __global__ void __launch_bounds__(512) k_count_G(const uint32_t* G, int64_t Pst, int P, int64_t s_begin,
                                                  int64_t s_end, int npf, uint32_t* counts);
 __global__ void k_scan_blocks(uint32_t* counts, int nblk, int npf, uint32_t* total);

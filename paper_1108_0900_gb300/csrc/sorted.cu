@@ -55,7 +55,7 @@ __device__ __forceinline__ int group_slot_pos(int k, int n4) {
 // positions a < b, and e the element's index in the store's block order
 __global__ void __launch_bounds__(256) k_build_G(DevProblem pb, int64_t n_s, const uint8_t* s_occ, int Nst,
                                                  const __nv_bfloat16* pf16, int64_t Pst, const uint32_t* fulltab,
-                                                 int wq, int64_t Gst, uint32_t* G) {
+                                                 int wq, int64_t Gst, uint32_t* G, uint16_t* G16, int64_t Gst16) {
     __shared__ uint8_t occw[8][64];
     __shared__ uint32_t cnt[8][32];
     __shared__ uint32_t msk[8][kBankRanks];
@@ -67,6 +67,10 @@ __global__ void __launch_bounds__(256) k_build_G(DevProblem pb, int64_t n_s, con
     __syncwarp();
     const uint16_t* src = (const uint16_t*)(pf16 + s * Pst);
     const int P = pb.P, QE = (P + kGParts - 1) / kGParts;
+    if (G16) {   // the compact copy: values only, in the row-major pair order
+        uint16_t* d16 = G16 + s * Gst16;
+        for (int r = lane; r < Gst16; r += 32) d16[r] = r < P ? src[fulltab[r] & 0xFFFFu] : (uint16_t)0;
+    }
     for (int f = 0; f < kGParts; ++f) {
         uint32_t* dst = G + s * Gst + (int64_t)f * wq * 4;
         const int r0 = f * QE, r1 = min(P, r0 + QE), n = max(0, r1 - r0);
@@ -646,6 +650,129 @@ __global__ void __launch_bounds__(scatter_threads(K), scatter_min_ctas(K)) k_sca
     for (int64_t i = (int64_t)b * nw + wid; i < n_items; i += stride) scatter_C_item<K>(a, a.items[i], slots[wid]);
 }
 
+// Compact gather (one vector): t_s = sum_c V[k_c]/C[k_c] + sum_e W_e v[pq(e)]
+// - Obar . V from G16, the sample's 2-byte values in the row-major order of
+// electron pairs (a < b), so no index is stored: pq(e) = rowbase(occ[a]) +
+// occ[b] comes from the sample's occupation row, which the warp keeps in
+// shared memory.  Half the bytes of G per product (3,088 of 6,208 B per
+// sample at 56 electrons) for one conflict-free byte lookup per element;
+// the v lookups follow the pair order (no bank ranking).  Lane L holds words
+// L + 32 u of the row (8 values each) and loads the next sample's words
+// before it works on the current ones.  wtab[w] = a | b << 8 is the pair of
+// word w's first value; the pair advances along the row (b + 1, or the next
+// row a + 1, b = a + 2).  Zero values (the row padding) are skipped.
+template <int U>
+__global__ void __launch_bounds__(512) k_gather_C(SortedArgs a, const uint16_t* G16, int64_t Gst16,
+                                                 const uint16_t* wtab_g, const uint8_t* s_occ, int Nst) {
+    if (a.stop && *a.stop) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const DevProblem& pb = a.pb;
+    const int nw16 = (int)(Gst16 >> 3);
+    const int occ_row = Nst + 16;   // bytes per warp: the row and a zero tail read past its end
+    float* vpf = (float*)smem;
+    int* coff = (int*)(vpf + pb.npf);
+    uint16_t* wtab = (uint16_t*)(coff + pb.ncorr + 1);
+    uint8_t* occs = (uint8_t*)(wtab + ((nw16 + 7) & ~7));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = threadIdx.x; i < pb.npf; i += blockDim.x) vpf[i] = a.V[pb.ncp + i];
+    for (int i = threadIdx.x; i <= pb.ncorr; i += blockDim.x) coff[i] = (int)pb.corr_off[i];
+    for (int i = threadIdx.x; i < nw16; i += blockDim.x) wtab[i] = wtab_g[i];
+    for (int i = threadIdx.x; i < nw * occ_row; i += blockDim.x) occs[i] = 0;
+    __shared__ float obv;
+    if (threadIdx.x < 32) {
+        const double c = warp_sum_partials(a.obv_part, a.n_obv_part, 0, 1);
+        if (threadIdx.x == 0) obv = (float)c;
+    }
+    __syncthreads();
+    uint8_t* occ = occs + wid * occ_row;
+    const int M = pb.M, N = pb.N;
+    double tt = 0.0;
+    const int64_t gstride = (int64_t)gridDim.x * nw;
+    const int nocc4 = Nst >> 2;   // 4-byte words of an occupation row
+    uint4 g[U];
+    uint32_t ow = 0u;
+    {
+        const int64_t s = (int64_t)blockIdx.x * nw + wid;
+        const uint4* g4 = (const uint4*)(G16 + s * Gst16);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = lane + 32 * u;
+            g[u] = (s < a.n_s && i < nw16) ? __ldcs(g4 + i) : make_uint4(0u, 0u, 0u, 0u);
+        }
+        if (s < a.n_s && lane < nocc4) ow = __ldcs((const uint32_t*)(s_occ + s * Nst) + lane);
+    }
+    for (int64_t s = (int64_t)blockIdx.x * nw + wid; s < a.n_s; s += gstride) {
+        __syncwarp();
+        if (lane < nocc4) reinterpret_cast<uint32_t*>(occ)[lane] = ow;
+        __syncwarp();
+        uint4 gn[U];
+        {
+            const int64_t sn = s + gstride;
+            const uint4* g4n = (const uint4*)(G16 + sn * Gst16);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int i = lane + 32 * u;
+                gn[u] = (sn < a.n_s && i < nw16) ? __ldcs(g4n + i) : make_uint4(0u, 0u, 0u, 0u);
+            }
+            if (sn < a.n_s && lane < nocc4) ow = __ldcs((const uint32_t*)(s_occ + sn * Nst) + lane);
+        }
+        float cv[kCorrPerLane][1];
+        corr_lookups<1>(pb, coff, a.s_cidx + s * a.ncst, a.V, a.invC, lane, cv);
+        float t = 0.f, w = 0.f;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int wd = lane + 32 * u;
+            if (wd < nw16) {
+                const uint32_t ab = wtab[wd];
+                int ea = (int)(ab & 255u), eb = (int)(ab >> 8);
+                int p = occ[ea];
+                int rb = p * M - p * (p + 1) / 2 - p - 1;
+                const uint32_t e[4] = {g[u].x, g[u].y, g[u].z, g[u].w};
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    if (j > 0 && ++eb == N) {
+                        ++ea;
+                        eb = ea + 1;
+                        p = occ[ea];
+                        rb = p * M - p * (p + 1) / 2 - p - 1;
+                    }
+                    const uint32_t bits = (j & 1) ? (e[j >> 1] >> 16) : (e[j >> 1] & 0xFFFFu);
+                    if (bits) {
+                        const float x = __uint_as_float(bits << 16) * vpf[rb + occ[eb]];
+                        if (j & 1) w += x;
+                        else t += x;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kCorrPerLane; ++j) t += cv[j][0];
+        t = warp_sum(t + w);
+        if (lane == 0) {
+            a.Tv[s] = t - obv;
+            const double c = (double)(t - obv);
+            tt += c * c;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) g[u] = gn[u];
+    }
+    if (a.tt_part) {
+        __shared__ double red[32];
+        if (lane == 0) red[wid] = tt;
+        __syncthreads();
+        if (wid == 0) {
+            double v = lane < nw ? red[lane] : 0.0;
+            v = warp_sum(v);
+            if (lane == 0) a.tt_part[blockIdx.x] = v;
+        }
+    }
+}
+
+template __global__ void k_gather_C<4>(SortedArgs, const uint16_t*, int64_t, const uint16_t*, const uint8_t*, int);
+template __global__ void k_gather_C<5>(SortedArgs, const uint16_t*, int64_t, const uint16_t*, const uint8_t*, int);
+template __global__ void k_gather_C<6>(SortedArgs, const uint16_t*, int64_t, const uint16_t*, const uint8_t*, int);
+template __global__ void k_gather_C<7>(SortedArgs, const uint16_t*, int64_t, const uint16_t*, const uint8_t*, int);
+template __global__ void k_gather_C<8>(SortedArgs, const uint16_t*, int64_t, const uint16_t*, const uint8_t*, int);
 template __global__ void k_gather_G<1, 1>(SortedArgs);
 template __global__ void k_gather_G<1, 2>(SortedArgs);
 template __global__ void k_gather_G<1, 3>(SortedArgs);

@@ -538,12 +538,12 @@ def LogPsi():
     return _LogPsi
 
 
-VMC_PATH_AUTO, VMC_PATH_SORTED, VMC_PATH_FUSED, VMC_PATH_STAGED, VMC_PATH_GENERIC = 0, 1, 2, 3, 4
-PATH_NAMES = {0: "auto", 1: "sorted", 2: "fused", 3: "staged", 4: "generic"}
+VMC_PATH_AUTO, VMC_PATH_SORTED, VMC_PATH_FUSED, VMC_PATH_STAGED, VMC_PATH_GENERIC, VMC_PATH_COMPACT = 0, 1, 2, 3, 4, 5
+PATH_NAMES = {0: "auto", 1: "sorted", 2: "fused", 3: "staged", 4: "generic", 5: "compact"}
 
 
 class vmc_tune_info(ct.Structure):
-    _fields_ = [("path", ct.c_int), ("path4", ct.c_int), ("ms", ct.c_double * 5), ("ms4", ct.c_double * 5)]
+    _fields_ = [("path", ct.c_int), ("path4", ct.c_int), ("ms", ct.c_double * 6), ("ms4", ct.c_double * 6)]
 
 
 def vmc_set_product_path(h: Handle, path: int):
@@ -557,8 +557,8 @@ def sr_autotune(h: Handle, reps: int = 5, stream=None) -> dict:
     fastest the AUTO choice; returns {"path", "path4", "ms": {name: ms}, "ms4": ...}."""
     info = vmc_tune_info()
     _check(lib().sr_autotune(h.h, int(reps), ct.byref(info), _stream(stream)), "sr_autotune")
-    ms = {PATH_NAMES[p]: info.ms[p] for p in range(1, 5) if info.ms[p] > 0}
-    ms4 = {PATH_NAMES[p]: info.ms4[p] for p in range(1, 5) if info.ms4[p] > 0}
+    ms = {PATH_NAMES[p]: info.ms[p] for p in range(1, 6) if info.ms[p] > 0}
+    ms4 = {PATH_NAMES[p]: info.ms4[p] for p in range(1, 6) if info.ms4[p] > 0}
     return {"path": PATH_NAMES[info.path], "path4": PATH_NAMES[info.path4], "ms": ms, "ms4": ms4}
 
 

@@ -38,7 +38,7 @@ def _handle(wl, prec=V.VMC_FP64):
 
 # product paths checked per number of vectors (a path that does not apply
 # to a problem falls back to the next one, which is then checked again)
-PATHS = {1: (V.VMC_PATH_SORTED, V.VMC_PATH_FUSED, V.VMC_PATH_STAGED, V.VMC_PATH_GENERIC),
+PATHS = {1: (V.VMC_PATH_SORTED, V.VMC_PATH_FUSED, V.VMC_PATH_STAGED, V.VMC_PATH_GENERIC, V.VMC_PATH_COMPACT),
          2: (V.VMC_PATH_SORTED, V.VMC_PATH_STAGED),
          4: (V.VMC_PATH_SORTED, V.VMC_PATH_GENERIC)}
 
@@ -123,7 +123,8 @@ def test_bf16_product_full_size_benchmark_store():
     V.vmc_set_walkers(h, wl.init_occ)
     V.vmc_sample(h, 4, inputs.seed_sampling_for("hubbard8x8_2x3"))
     assert V.vmc_num_samples(h) == 65536
-    _check_products(wl, h, ks=(1, 4), paths={1: (V.VMC_PATH_SORTED, V.VMC_PATH_FUSED), 4: (V.VMC_PATH_SORTED,)})
+    _check_products(wl, h, ks=(1, 4), paths={1: (V.VMC_PATH_SORTED, V.VMC_PATH_FUSED, V.VMC_PATH_COMPACT),
+                                              4: (V.VMC_PATH_SORTED,)})
     h.close()
 
 
@@ -139,7 +140,7 @@ def test_autotune_picks_a_measured_path_and_keeps_parity(tmp_path):
     res = V.sr_autotune(h, reps=3)
     # (four pairing images of 8,128 amplitudes exceed shared memory, so the
     # generic pass does not apply to four vectors here)
-    assert set(res["ms"]) >= {"sorted", "fused", "generic"} and "sorted" in res["ms4"]
+    assert set(res["ms"]) >= {"sorted", "fused", "generic", "compact"} and "sorted" in res["ms4"]
     assert res["ms"][res["path"]] == min(res["ms"].values())
     assert res["ms4"][res["path4"]] == min(res["ms4"].values())
     _check_products(wl, h, ks=(1, 4), paths={1: (V.VMC_PATH_AUTO,), 4: (V.VMC_PATH_AUTO,)})
