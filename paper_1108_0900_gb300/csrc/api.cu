@@ -55,6 +55,15 @@ struct vmc_ctx {
     bool sorted_ok = false;      // G / T built for the current samples
     bool use_fused = true;       // fused single-pass product over G (BF16 store, one vector)
     bool use_compact = true;     // two-pass product with the compact gather over G16 (one vector)
+    bool use_coop_update = true; // inner CG: x/r and p updates as one cooperative launch
+    struct SortedLaunch {        // launch shapes of the sorted product for one K (see plan_sorted)
+        int64_t n_s = -1;
+        bool compact = false;
+        int ggrid = 0, sgrid = 0;
+        size_t gsmem = 0, ssm = 0;
+        int nhist = 0, hist_slices = 1, ncb = 0, corr_in_cta = 0, hist_cap = 0, hist_off = 0, pq_per_cta = 1;
+    } sorted_launch[3];
+    bool coop_launch = false;    // the device supports cooperative launches
     int path = VMC_PATH_AUTO;    // product path set by the caller (VMC_PATH_*)
     int auto_path = VMC_PATH_SORTED;   // one-vector BF16 path used under AUTO (sr_autotune may change it)
     int auto_path4 = VMC_PATH_SORTED;  // two- and four-vector BF16 path used under AUTO
@@ -134,6 +143,11 @@ struct vmc_ctx {
     bool scatter_corr_front = true;   // correlator items of the sorted scatter as CTAs of their own
     bool scatter_corr_hist = true;    // correlator half of the sorted scatter as class histograms
     int scatter_in_cta_mink = 2;      // vectors from which the pairing CTAs build the correlator histograms
+    // waves of pairing CTAs of the sorted scatter: one wave left a tail behind
+    // the histogram CTAs inside the SR step (one vector, 8x8 / 2x3: 137.7 ms per
+    // step at one wave, 131.1 at two, 128.2 at three); four vectors (one CTA
+    // per SM) measured best at one wave (0.394 against 0.415 ms at three)
+    int scatter_waves1 = 3, scatter_waves4 = 1;
     unsigned* d_tdone = nullptr; // [npf] chunks finished per parameter group (0 between launches)
     uint32_t *d_Tc = nullptr, *d_ccount = nullptr, *d_cbase = nullptr;   // correlator runs
     double* d_scal = nullptr;
@@ -413,6 +427,7 @@ extern "C" int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, co
     if (cudaGetDeviceProperties(&prop, h->dev) != cudaSuccess) return fail(VMC_ERR_CUDA);
     h->nsm = prop.multiProcessorCount;
     h->smem_optin = prop.sharedMemPerBlockOptin;
+    h->coop_launch = prop.cooperativeLaunch != 0;
 
 #define ACK(x) do { if ((x) != cudaSuccess) { set_err(#x); return fail(VMC_ERR_OOM); } } while (0)
 #define UPL(dst, src, n) do { if (cudaMemcpy(dst, src, sizeof(*(dst)) * (n), cudaMemcpyHostToDevice) != cudaSuccess) return fail(VMC_ERR_CUDA); } while (0)
@@ -1348,6 +1363,80 @@ static CompactKern compact_kernel(int64_t u) {
     return tab[std::max<int64_t>(0, u - 4)];
 }
 
+// Launch shapes of the sorted product for K vectors.  Gather: as many CTAs
+// as fit on the GPU, at most one per warp-row of samples.  Scatter: one wave
+// of pairing CTAs over the chunks, each CTA a group of consecutive
+// parameters of one chunk (at least one per warp).  The correlator half:
+// histograms of the chunk's t_s inside the pairing CTAs when they fit beside
+// the chunk table (K >= scatter_in_cta_mink), else (class, sample slice)
+// histogram CTAs ahead of the pairing CTAs, else the correlator work items
+// (CTAs of their own ahead, or after each pairing CTA's runs).
+template <int K>
+static int plan_sorted(vmc_ctx* h, bool compact, SortedArgs a, vmc_ctx::SortedLaunch* L) {
+    const int sthreads = scatter_threads(K), swarps = sthreads / 32;
+    {
+        const int gthreads = compact ? kCompactThreads : gather_threads(K), gwarps = gthreads / 32;
+        const size_t smem = compact ? compact_smem(h) : (size_t)h->npf * K * 4 + (size_t)(h->ncorr + 1) * 4;
+        const void* gk = compact ? (const void*)compact_kernel((h->Gst16 / 8 + 31) / 32)
+                                 : (const void*)gather_kernel<K>((int)((h->Gst / 4 + 31) / 32));
+        VCK(cudaFuncSetAttribute(gk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0;
+        VCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gk, gthreads, smem));
+        int grid = h->nsm * std::max(1, per_sm);
+        const int64_t need = (h->n_s + gwarps - 1) / gwarps;
+        if (need < grid) grid = (int)std::max<int64_t>(1, need);
+        L->ggrid = std::min(grid, kNumPart * kMaxK);   // one partial slot of tt sums
+        L->gsmem = smem;
+    }
+    const size_t ssm_tab = (size_t)kTChunk * K * sizeof(float);
+    const int pq_cap = std::min(std::max(h->npf, swarps), kScatterMaxPQ);
+    const size_t run_bytes = ((size_t)(pq_cap + 1) * 4 + 15) / 16 * 16;
+    const size_t static_bytes = (size_t)sthreads * K * sizeof(float) + 1024;
+    size_t hsm = 0;
+    a.nhist = 0;
+    a.hist_slices = 1;
+    a.ncb = 0;
+    a.corr_in_cta = 0;
+    a.hist_cap = 0;
+    if (h->ncorr > 0) {
+        const int64_t one = (int64_t)h->maxd * K;
+        const int cap = (int)std::max<int64_t>(one, std::min<int64_t>(one * swarps, 8192));
+        if (K >= h->scatter_in_cta_mink && ssm_tab + run_bytes + (size_t)cap * 4 + static_bytes <= h->smem_optin) {
+            a.corr_in_cta = 1;
+            a.hist_cap = cap;
+        } else if (h->scatter_corr_hist && (hsm = corr_hist_setup(h, K, &a)) > 0) {
+            a.ncb = 0;
+        } else {
+            hsm = 0;
+            a.nhist = 0;
+            a.hist_slices = 1;
+            a.ncb = h->scatter_corr_front ? (int)((h->max_items + swarps - 1) / swarps) : 0;
+        }
+    }
+    // shared memory for a group of pq run ends: one estimate for the
+    // occupancy query, then the group size it gives
+    const size_t in_cta = (size_t)a.hist_cap * 4;
+    auto run_of = [](int pq) { return ((size_t)(pq + 1) * 4 + 15) / 16 * 16; };
+    auto smem_of = [&](int pq) { return std::max(hsm, ssm_tab + run_of(pq) + in_cta); };
+    const int pq_est = std::min(pq_cap, std::max(swarps, h->npf / h->nsm + 64));
+    VCK(cudaFuncSetAttribute(k_scatter_T<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_of(pq_cap)));
+    int per = 0;
+    VCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_scatter_T<K>, sthreads, smem_of(pq_est)));
+    const int64_t resident = (int64_t)h->nsm * std::max(1, per);
+    const int64_t target = resident * (K == 1 ? h->scatter_waves1 : h->scatter_waves4);
+    int ngrp = (int)std::max<int64_t>(1, std::min<int64_t>(h->npf, (target + a.nchunk - 1) / a.nchunk));
+    L->pq_per_cta = std::min(pq_cap, std::max(swarps, (h->npf + ngrp - 1) / ngrp));
+    ngrp = (h->npf + L->pq_per_cta - 1) / L->pq_per_cta;
+    L->hist_off = (int)(ssm_tab + run_of(L->pq_per_cta));   // bytes: the in-CTA histograms
+    L->nhist = a.nhist; L->hist_slices = a.hist_slices; L->ncb = a.ncb;
+    L->corr_in_cta = a.corr_in_cta; L->hist_cap = a.hist_cap;
+    L->sgrid = a.nhist + a.ncb + a.nchunk * ngrp;
+    L->ssm = smem_of(L->pq_per_cta);
+    L->n_s = h->n_s;
+    L->compact = compact;
+    return VMC_OK;
+}
+
 // gather + parameter-major scatter for the BF16 store; the centered t_s go to
 // Tv, the pairing sums to d_pfraw and the correlator sums to d_corrraw (FP32)
 template <int K>
@@ -1377,92 +1466,34 @@ static int launch_sorted(vmc_ctx* h, const float* V, const float* invC, const do
     a.Tc = h->d_Tc; a.cbase = h->d_cbase; a.craw = (float*)h->d_corrraw;
     a.items = h->d_items;
     a.n_items = h->d_item_base + (h->ncp + 31) / 32;
-    const int sthreads = scatter_threads(K), swarps = sthreads / 32;
     a.tt_part = tt_part;
     a.stop = stop;
-    if (K == 1 && product_path(h, 1) == VMC_PATH_COMPACT && compact_usable(h)) {
-        // the compact gather over G16 (occupation rows give the indices)
-        const size_t smem = compact_smem(h);
-        auto ck = compact_kernel((h->Gst16 / 8 + 31) / 32);
-        VCK(cudaFuncSetAttribute(ck, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        int per_sm = 0;
-        const int cwarps = kCompactThreads / 32;
-        VCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ck, kCompactThreads, smem));
-        int grid = h->nsm * std::max(1, per_sm);
-        const int64_t need = (h->n_s + cwarps - 1) / cwarps;
-        if (need < grid) grid = (int)std::max<int64_t>(1, need);
-        grid = std::min(grid, kNumPart * kMaxK);   // one partial slot of tt sums
-        ck<<<grid, kCompactThreads, smem, st>>>(a, h->d_G16, h->Gst16, h->d_wtab, h->d_socc, h->Nst); h->n_launch++;
-        h->last_gather_grid = grid;
-    } else {
-        const size_t smem = (size_t)h->npf * K * 4 + (size_t)(h->ncorr + 1) * 4;
-        auto gk = gather_kernel<K>((int)((h->Gst / 4 + 31) / 32));
-        VCK(cudaFuncSetAttribute(gk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        int per_sm = 0;
-        const int gthreads = gather_threads(K), gwarps = gthreads / 32;
-        VCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gk, gthreads, smem));
-        int grid = h->nsm * std::max(1, per_sm);
-        const int64_t need = (h->n_s + gwarps - 1) / gwarps;
-        if (need < grid) grid = (int)std::max<int64_t>(1, need);
-        grid = std::min(grid, kNumPart * kMaxK);   // one partial slot of tt sums
-        gk<<<grid, gthreads, smem, st>>>(a); h->n_launch++;
-        h->last_gather_grid = grid;
+    const bool compact = K == 1 && product_path(h, 1) == VMC_PATH_COMPACT && compact_usable(h);
+    // the launch shapes depend on the problem, K, the gather kind and n_s
+    // only: worked out (attributes, occupancy queries) once and kept, so the
+    // inner CG iteration issues its launches without host-side queries
+    vmc_ctx::SortedLaunch& L = h->sorted_launch[K == 1 ? 0 : K == 2 ? 1 : 2];
+    if (L.n_s != h->n_s || L.compact != compact) {
+        int rc2 = plan_sorted<K>(h, compact, a, &L);
+        if (rc2) return rc2;
     }
+    a.nhist = L.nhist; a.hist_slices = L.hist_slices; a.ncb = L.ncb;
+    a.corr_in_cta = L.corr_in_cta; a.hist_cap = L.hist_cap; a.hist_off = L.hist_off; a.pq_per_cta = L.pq_per_cta;
+    a.cidxT = h->d_cidxT;
+    if (compact) {
+        // the compact gather over G16 (occupation rows give the indices)
+        compact_kernel((h->Gst16 / 8 + 31) / 32)<<<L.ggrid, kCompactThreads, L.gsmem, st>>>(
+            a, h->d_G16, h->Gst16, h->d_wtab, h->d_socc, h->Nst);
+    } else {
+        gather_kernel<K>((int)((h->Gst / 4 + 31) / 32))<<<L.ggrid, gather_threads(K), L.gsmem, st>>>(a);
+    }
+    h->n_launch++;
+    h->last_gather_grid = L.ggrid;
     // correlator sums accumulate into zero (the fused CG update re-zeroes
     // them as it reads them, so its products skip this)
     if (h->ncp > 0 && !craw_zero) VCK(cudaMemsetAsync(h->d_corrraw, 0, sizeof(float) * h->ncp * K, st));
-    // scatter: one wave of pairing CTAs over the chunks, each CTA a group of
-    // consecutive parameters of one chunk (at least one per warp).  The
-    // correlator half: histograms of the chunk's t_s inside the pairing CTAs
-    // when they fit beside the chunk table (K >= scatter_in_cta_mink), else
-    // (class, sample slice) histogram CTAs ahead of the pairing CTAs, else
-    // the correlator work items (CTAs of their own ahead, or after each
-    // pairing CTA's runs)
-    {
-        const size_t ssm_tab = (size_t)kTChunk * K * sizeof(float);
-        const int pq_cap = std::min(std::max(h->npf, swarps), kScatterMaxPQ);
-        const size_t run_bytes = ((size_t)(pq_cap + 1) * 4 + 15) / 16 * 16;
-        const size_t static_bytes = (size_t)sthreads * K * sizeof(float) + 1024;
-        size_t hsm = 0;
-        a.nhist = 0;
-        a.hist_slices = 1;
-        a.ncb = 0;
-        a.corr_in_cta = 0;
-        a.hist_cap = 0;
-        a.cidxT = h->d_cidxT;
-        if (h->ncorr > 0) {
-            const int64_t one = (int64_t)h->maxd * K;
-            const int cap = (int)std::max<int64_t>(one, std::min<int64_t>(one * swarps, 8192));
-            if (K >= h->scatter_in_cta_mink &&
-                ssm_tab + run_bytes + (size_t)cap * 4 + static_bytes <= h->smem_optin) {
-                a.corr_in_cta = 1;
-                a.hist_cap = cap;
-            } else if (h->scatter_corr_hist && (hsm = corr_hist_setup(h, K, &a)) > 0) {
-                a.ncb = 0;
-            } else {
-                hsm = 0;
-                a.nhist = 0;
-                a.hist_slices = 1;
-                a.ncb = h->scatter_corr_front ? (int)((h->max_items + swarps - 1) / swarps) : 0;
-            }
-        }
-        // shared memory for a group of pq run ends: one estimate for the
-        // occupancy query, then the group size it gives
-        const size_t in_cta = (size_t)a.hist_cap * 4;
-        auto run_of = [](int pq) { return ((size_t)(pq + 1) * 4 + 15) / 16 * 16; };
-        auto smem_of = [&](int pq) { return std::max(hsm, ssm_tab + run_of(pq) + in_cta); };
-        const int pq_est = std::min(pq_cap, std::max(swarps, h->npf / h->nsm + 64));
-        VCK(cudaFuncSetAttribute(k_scatter_T<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_of(pq_cap)));
-        int per = 0;
-        VCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_scatter_T<K>, sthreads, smem_of(pq_est)));
-        const int64_t resident = (int64_t)h->nsm * std::max(1, per);
-        int ngrp = (int)std::max<int64_t>(1, std::min<int64_t>(h->npf, (resident + a.nchunk - 1) / a.nchunk));
-        a.pq_per_cta = std::min(pq_cap, std::max(swarps, (h->npf + ngrp - 1) / ngrp));
-        ngrp = (h->npf + a.pq_per_cta - 1) / a.pq_per_cta;
-        a.hist_off = (int)(ssm_tab + run_of(a.pq_per_cta));   // bytes: the in-CTA histograms
-        k_scatter_T<K><<<a.nhist + a.ncb + a.nchunk * ngrp, sthreads, smem_of(a.pq_per_cta), st>>>(a);
-        h->n_launch++;
-    }
+    k_scatter_T<K><<<L.sgrid, scatter_threads(K), L.ssm, st>>>(a);
+    h->n_launch++;
     VCK(cudaGetLastError());
     if (h->prof) {
         VCK(cudaEventRecord(rec.b, st));
@@ -1898,6 +1929,15 @@ static int cg_loop(vmc_ctx* h, const void* s_pf, int kind, const VT* b, VT* x, V
                            sorted_usable<1>(h));
     }
     if (fused && h->ncp > 0) VCK(cudaMemsetAsync(h->d_corrraw, 0, sizeof(float) * h->ncp, st));
+    // the two updates as one cooperative launch when the update grid is co-resident
+    bool coop = false;
+    if constexpr (sizeof(VT) == 4) {
+        if (fused && h->use_coop_update && h->coop_launch) {
+            int per = 0;
+            VCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cg_fxrp<float>, 256, 0));
+            coop = (int64_t)per * h->nsm >= vg;
+        }
+    }
     while (!done) {
         for (int j = 0; j < kChunk; ++j) {
             if (fused) {
@@ -1920,6 +1960,18 @@ static int cg_loop(vmc_ctx* h, const void* s_pf, int kind, const VT* b, VT* x, V
                     f.scal = h->d_scal;
                     f.rr_part = rr_part;
                     f.stop = h->d_stop;
+                    if (coop) {
+                        // both updates in one cooperative launch (a grid barrier between them)
+                        const float* ob = (const float*)ObarV;
+                        int* stp = h->d_stop;
+                        int mi = max_iter;
+                        void* args[] = {&f, &ob, &obp_part, &stp, &mi};
+                        VCK(cudaLaunchCooperativeKernel((const void*)k_cg_fxrp<float>, dim3(vg), dim3(256), args, 0,
+                                                        st));
+                        h->n_launch++;
+                        VCK(cudaGetLastError());
+                        continue;
+                    }
                     k_cg_fxr<float><<<vg, 256, 0, st>>>(f); h->n_launch++;
                 }
             } else {

@@ -14,6 +14,7 @@
 // array into shared-memory histograms of each correlator's 4^m states, one
 // per CTA of a thread-block cluster, summed through distributed shared
 // memory, so neither half uses global atomics.
+#include <cooperative_groups.h>
 #include "common.cuh"
 #include "corr.cuh"
 #include "kernels.h"
@@ -459,8 +460,7 @@ __device__ __forceinline__ void block_reduce_store2(double a, double b, double* 
 // separate dot product and Ap = raw / n + eps p is formed element by element
 // and never stored: x += alpha p; r -= alpha Ap; partial r . r.
 template <typename VT>
-__global__ void __launch_bounds__(256) k_cg_fxr(CgFusedArgs<VT> a) {
-    if (*a.stop) return;
+__device__ __forceinline__ void cg_fxr_body(const CgFusedArgs<VT>& a) {
     __shared__ double alpha;
     if (threadIdx.x < 32) {
         const double tt = warp_sum_partials(a.tt_part, a.ntt, 0, 1);
@@ -505,13 +505,18 @@ __global__ void __launch_bounds__(256) k_cg_fxr(CgFusedArgs<VT> a) {
     if (blockIdx.x == 0 && threadIdx.x == 0) a.scal[CG_RRP] = a.scal[CG_RR];
 }
 
+template <typename VT>
+__global__ void __launch_bounds__(256) k_cg_fxr(CgFusedArgs<VT> a) {
+    if (*a.stop) return;
+    cg_fxr_body(a);
+}
+
 // beta = rr_new / rr; p = r + beta p; partials Obar . p (centering of the next
 // product) and |p|^2 (its curvature)
 template <typename VT>
-__global__ void __launch_bounds__(256) k_cg_p(const VT* r, VT* p, int64_t n, const double* rr_part, int npart,
-                                              double* scal, const VT* Obar, double* obp_part, double* pp_part,
-                                              int* stop, int max_iter) {
-    if (*stop) return;
+__device__ __forceinline__ void cg_p_body(const VT* r, VT* p, int64_t n, const double* rr_part, int npart,
+                                          double* scal, const VT* Obar, double* obp_part, double* pp_part,
+                                          int* stop, int max_iter) {
     __shared__ double beta, rrn;
     if (threadIdx.x < 32) {
         double r = warp_sum_partials(rr_part, npart, 0, 1);
@@ -555,6 +560,28 @@ __global__ void __launch_bounds__(256) k_cg_p(const VT* r, VT* p, int64_t n, con
         scal[CG_IT] = it;
         if (rrn <= scal[CG_TOL2] || !isfinite(rrn) || it >= (double)max_iter) *stop = 1;
     }
+}
+
+template <typename VT>
+__global__ void __launch_bounds__(256) k_cg_p(const VT* r, VT* p, int64_t n, const double* rr_part, int npart,
+                                              double* scal, const VT* Obar, double* obp_part, double* pp_part,
+                                              int* stop, int max_iter) {
+    if (*stop) return;
+    cg_p_body(r, p, n, rr_part, npart, scal, Obar, obp_part, pp_part, stop, max_iter);
+}
+
+// Both CG updates in one cooperative launch: x/r (with the r . r partials),
+// a grid-wide barrier, then beta and p (with the partials of the next
+// product); saves a launch and its start-up per inner iteration.  The grid
+// must be co-resident (cudaLaunchCooperativeKernel checks it).
+template <typename VT>
+__global__ void __launch_bounds__(256) k_cg_fxrp(CgFusedArgs<VT> a, const VT* Obar, double* obp_part,
+                                                 int* stop, int max_iter) {
+    if (*a.stop) return;
+    cg_fxr_body(a);
+    cooperative_groups::this_grid().sync();
+    cg_p_body<VT>(a.r, const_cast<VT*>(a.p), a.n, a.rr_part, (int)gridDim.x, a.scal, Obar, obp_part,
+                  const_cast<double*>(a.pp_part), stop, max_iter);
 }
 
 // partial sums of x (FP64)
@@ -708,6 +735,7 @@ template __global__ void k_cg_p<double>(const double*, double*, int64_t, const d
 template __global__ void k_cg_p<float>(const float*, float*, int64_t, const double*, int, double*, const float*,
                                        double*, double*, int*, int);
 template __global__ void k_cg_fxr<float>(CgFusedArgs<float>);
+template __global__ void k_cg_fxrp<float>(CgFusedArgs<float>, const float*, double*, int*, int);
 template __global__ void k_axpy_to64<float>(double*, const float*, double, int64_t);
 template __global__ void k_axpy_to64<double>(double*, const double*, double, int64_t);
 
