@@ -481,16 +481,17 @@ def run_gpu(args, rank, world, dist):
 # CPU oracle (baseline and reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_step(n_walkers: int, spw: int, seed: int, cg_iters_full: float):
-    """The oracle's SR iteration on a bounded sample of the workload:
+def oracle_step(n_walkers: int, spw: int, seed: int, cg_iters_full: float, name: str = "hubbard8x8_2x3",
+                full: int = 65536):
+    """The oracle's SR iteration on a bounded sample of a workload:
     n_walkers chains x spw samples (one sweep each, chains started from the
     thermalised-free seeded starts after one sweep), E_L and dense O, the
-    gradient and one Eq. 7 product timed; scaled to 65,536 samples and the
-    FP64 CG iteration count of the full workload."""
+    gradient and one Eq. 7 product timed; scaled to the workload's `full`
+    samples and its FP64 CG iteration count."""
     import oracle
     from paper_1108_0900_gb300 import inputs
 
-    wl = inputs.workload("hubbard8x8_2x3", n_walkers=n_walkers, samples_per_walker=spw)
+    wl = inputs.workload(name, n_walkers=n_walkers, samples_per_walker=spw)
     P = oracle.Problem(wl)
     occ = wl.init_occ.copy()
     step = np.zeros(n_walkers, np.uint64)
@@ -508,7 +509,6 @@ def oracle_step(n_walkers: int, spw: int, seed: int, cg_iters_full: float):
         oracle.apply_S(O, v, wl.shift, Obar=Ob)
     t4 = t3 + (time.perf_counter() - t3) / n_prod
     n = len(smp)
-    full = 65536
     per_sample = (t1 - t0 + t2 - t1 + t3 - t2) / n
     sv_per_sample = (t4 - t3) / n
     est = per_sample * full + sv_per_sample * full * cg_iters_full
@@ -516,7 +516,10 @@ def oracle_step(n_walkers: int, spw: int, seed: int, cg_iters_full: float):
                  "n_samples": n}
 
 
-def cpu_baseline(cg_iters_full: float, n_walkers=128, spw=2):
+def cpu_baseline(cg_iters_full: float, n_walkers=128, spw=2, configs=None):
+    """The oracle on bounded samples: the headline workload on all host cores
+    and on one core, and (configs: {name: (samples of the full workload, FP64
+    CG iterations)}) the other workloads on all cores."""
     import oracle
     cores = os.cpu_count() or 1
     oracle.set_threads(cores)
@@ -525,6 +528,12 @@ def cpu_baseline(cg_iters_full: float, n_walkers=128, spw=2):
     oracle.set_threads(1)
     est1, parts1 = oracle_step(max(8, n_walkers // 4), spw, 2006, cg_iters_full)
     oracle.set_threads(cores)
+    per_config = {}
+    for name, (full, iters) in (configs or {}).items():
+        nw = 16 if name.startswith("abinitio") else 64
+        e, pc = oracle_step(nw, 1, 2007, iters, name=name, full=full)
+        per_config[name] = {"value": round(e, 3), "unit": "s", "cores": int(cores), "n_samples": pc["n_samples"],
+                            "full_samples": full, "cg_products": iters}
     return {"value": round(est, 3), "unit": "s", "cores": int(cores),
             "kind": "oracle",
             "sample": (f"{parts['n_samples']} samples ({n_walkers} walkers x {spw}) of the same workload: "
@@ -533,6 +542,7 @@ def cpu_baseline(cg_iters_full: float, n_walkers=128, spw=2):
                        f"(the GPU FP64 path's iteration count)"),
             "nproc": int(cores),
             "one_core": {"value": round(est1, 3), "unit": "s", "cores": 1, "n_samples": parts1["n_samples"]},
+            "configs": per_config,
             "parts": {k: round(v, 4) if isinstance(v, float) else v for k, v in parts.items()}}
 
 
@@ -719,7 +729,11 @@ def main():
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             iters = (res["fp64_path"] or {}).get("cg_iterations") or res["cg"]["inner_iterations"]
-            res["cpu_baseline"] = cpu_baseline(iters)
+            others = {name: (row["n_samples"], row["fp64"]["cg_iterations"])
+                      for name, row in (res.get("configs") or {}).items()}
+            if res.get("abinitio"):   # no FP64 leg there: the mixed solve's inner count
+                others["abinitio24"] = (65536, res["abinitio"]["cg_inner_iterations"])
+            res["cpu_baseline"] = cpu_baseline(iters, configs=others)
         print(json.dumps(res))
     if dist is not None:
         dist.destroy_process_group()
