@@ -47,6 +47,7 @@ struct vmc_ctx {
     int wprec = VMC_FP64, keep64 = 1, keeplow = 0, refresh_every = 0, fp64_refresh = 0;
     int ham = 0;
     int maxd = 1;
+    int max_csites = 0;          // sites of the largest correlator
     bool params_set = false, walkers_set = false;
     bool use_stream = true;     // TMA-staged pass for FP32-accumulation products
     bool stream_cached = false;  // register-cached variant for BF16, one vector (slower: 16 warps)
@@ -335,6 +336,8 @@ extern "C" int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, co
         nptr[s + 1] = (int)nsite.size();
     }
     // correlators containing both sites i and j (i != j)
+    h->max_csites = 0;
+    for (int c = 0; c < h->ncorr; ++c) h->max_csites = std::max(h->max_csites, cptr[c + 1] - cptr[c]);
     std::vector<int> pptr((size_t)ns * ns + 1, 0), pcorr;
     {
         std::vector<std::vector<int>> pl((size_t)ns * ns);
@@ -594,6 +597,7 @@ extern "C" int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, co
     pb.nbr_ptr = h->d_nbr_ptr; pb.nbr_site = h->d_nbr_site; pb.nbr_t = h->d_nbr_t;
     pb.h64 = h->d_h64; pb.h32 = h->d_h32; pb.eri64 = h->d_eri64; pb.eri32 = h->d_eri32;
     pb.pair_ptr = h->d_pair_ptr; pb.pair_corr = h->d_pair_corr;
+    pb.max_csites = h->max_csites;
     pb.C64 = h->d_C64; pb.C32 = h->d_C32; pb.F64 = h->d_F64; pb.F32 = h->d_F32;
     pb.pairtab = h->d_pairtab; pb.rowbase = h->d_rowbase;
     *out = h;
@@ -736,9 +740,10 @@ static size_t prep_walkers(vmc_ctx* h, SampleArgs& a, bool fp64) {
     size_t wb = (size_t)h->N * a.XS * rsz + 3 * (size_t)a.XS * rsz;
     wb = wb + 64 * 4 + (size_t)a.ncorr_pad * 4 + 64 + 128;
     if (h->ham == VMC_ABINITIO && a.want_energy) {
-        // G [M][GS], H [E][E], single-move factors [N][E], empty list, index map
+        // G [M][GS], H [E][E], single-move factors [N][E], empty list, index
+        // map, per-site factors [ns][4]
         const size_t E = (size_t)(h->M - h->N);
-        wb += ((size_t)h->M * a.GS + E * E + (size_t)h->N * E) * rsz + 128 + 128;
+        wb += ((size_t)h->M * a.GS + E * E + (size_t)h->N * E) * rsz + 128 + 128 + (size_t)4 * h->ns * rsz;
     }
     wb = round_up(wb, 16);
     a.warp_bytes = wb;

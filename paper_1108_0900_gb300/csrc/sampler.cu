@@ -200,6 +200,56 @@ __device__ R corr_ratio_double(const DevProblem& pb, const uint32_t* cidx, int p
     return r1 * r2 * corr;
 }
 
+// Correlators of at most two sites (the pair correlators of the ab initio
+// ansatz): the correlator factor of any move factorises over the sites it
+// touches.  Rsite[4 s + v] = prod over the correlators c on site s of
+// C_c(state with site s in local state v) / C_c(current state), all other
+// sites unchanged.  A move that changes the local states of the distinct
+// sites S (at most four) then has the factor prod_{s in S} Rsite[4 s + n'_s]
+// times, for every correlator holding two sites s, t of S, the correction
+// C(o + d_s + d_t) C(o) / (C(o + d_s) C(o + d_t)) (the two single-site
+// factors each took the other site at its old state).
+__device__ __forceinline__ int site_state(uint64_t up, uint64_t dn, int s) {
+    return (int)((up >> s) & 1ull) + 2 * (int)((dn >> s) & 1ull);
+}
+
+template <typename R>
+__device__ R pair_correction(const DevProblem& pb, const uint32_t* cidx, int s, int dvs, int t, int dvt) {
+    R f = R(1);
+    const int lo = pb.pair_ptr[s * pb.ns + t], hi = pb.pair_ptr[s * pb.ns + t + 1];
+    for (int e = lo; e < hi; ++e) {
+        const int c = pb.pair_corr[e];
+        const int o = (int)cidx[c];
+        const int ds = site_weight_in(pb, c, s) * dvs, dt = site_weight_in(pb, c, t) * dvt;
+        const int64_t off = pb.corr_off[c];
+        f *= load_C<R>(pb, off + o + ds + dt) * load_C<R>(pb, off + o) /
+             (load_C<R>(pb, off + o + ds) * load_C<R>(pb, off + o + dt));
+    }
+    return f;
+}
+
+// factor of the move changing sites S[k] by D[k] (local state units), k < n
+template <typename R>
+__device__ __forceinline__ R site_move_factor(const DevProblem& pb, const uint32_t* cidx, const R* Rsite,
+                                              uint64_t up, uint64_t dn, int (&S)[4], int (&D)[4], int n) {
+    bool alive[4] = {true, true, true, true};
+    for (int k = 1; k < n; ++k)
+        for (int m = 0; m < k; ++m)
+            if (alive[m] && S[k] == S[m]) {
+                D[m] += D[k];
+                alive[k] = false;
+                break;
+            }
+    R f = R(1);
+    for (int k = 0; k < n; ++k)
+        if (alive[k] && D[k] != 0) f *= Rsite[4 * S[k] + site_state(up, dn, S[k]) + D[k]];
+    for (int k = 0; k < n; ++k)
+        for (int m = k + 1; m < n; ++m)
+            if (alive[k] && alive[m] && D[k] != 0 && D[m] != 0)
+                f *= pair_correction<R>(pb, cidx, S[k], D[k], S[m], D[m]);
+    return f;
+}
+
 // Local energy of the ab initio Hamiltonian for the warp's walker (lane
 // partial sum; the caller reduces).  E_L = <n|H|n> + sum over single and
 // double same-spin-conserving moves of <n|H|n'> Psi_n'/Psi_n.  With the new
@@ -215,7 +265,8 @@ __device__ R corr_ratio_double(const DevProblem& pb, const uint32_t* cidx, int p
 template <typename R>
 __device__ double abinitio_energy(const DevProblem& pb, const R* X, int XS, const uint8_t* pos_orb,
                                   const int8_t* orb_pos, uint64_t up, uint64_t dn, const uint32_t* cidx,
-                                  R* G, int GS, R* Hm, R* Rs, uint8_t* emp, int8_t* eidx) {
+                                  R* G, int GS, R* Hm, R* Rs, uint8_t* emp, int8_t* eidx, R* Rsite) {
+    const bool pairs = pb.max_csites <= 2;   // the site-factorised correlator ratios apply
     const int lane = threadIdx.x & 31;
     const int ns = pb.ns, M = pb.M, N = pb.N, nu = pb.nu, nd = pb.nd;
     const int eu = ns - nu, ed = ns - nd, E = eu + ed;
@@ -243,11 +294,26 @@ __device__ double abinitio_energy(const DevProblem& pb, const R* X, int XS, cons
         for (int j = 0; j < N; ++j) acc += load_F<R>(pb, yq, pos_orb[j]) * G[xq * GS + j];
         Hm[t] = acc;
     }
-    // single-move correlator factors Rs[a][ie] (same spin only)
-    for (int t = lane; t < N * E; t += 32) {
-        const int a = t / E, ie = t % E;
-        const int p = pos_orb[a], q = emp[ie];
-        Rs[t] = ((p >= ns) == (q >= ns)) ? corr_ratio_serial<R>(pb, cidx, p, q) : R(0);
+    if (pairs) {
+        // per-site factors of every local state
+        for (int t = lane; t < 4 * ns; t += 32) {
+            const int s = t >> 2, v = t & 3, n = site_state(up, dn, s);
+            R f = R(1);
+            if (v != n)
+                for (int ent = pb.site_cptr[s]; ent < pb.site_cptr[s + 1]; ++ent) {
+                    const int c = pb.site_corr[ent];
+                    const int64_t k = pb.corr_off[c] + (int64_t)cidx[c];
+                    f *= load_C<R>(pb, k + pb.site_w[ent] * (v - n)) / load_C<R>(pb, k);
+                }
+            Rsite[t] = f;
+        }
+    } else {
+        // single-move correlator factors Rs[a][ie] (same spin only)
+        for (int t = lane; t < N * E; t += 32) {
+            const int a = t / E, ie = t % E;
+            const int p = pos_orb[a], q = emp[ie];
+            Rs[t] = ((p >= ns) == (q >= ns)) ? corr_ratio_serial<R>(pb, cidx, p, q) : R(0);
+        }
     }
     __syncwarp();
     double e = 0.0;
@@ -277,7 +343,15 @@ __device__ double abinitio_energy(const DevProblem& pb, const R* X, int XS, cons
             hm += load_eri<R>(pb, ip, ix, ik, ik);
             if ((k >= ns) == (p >= ns)) hm -= load_eri<R>(pb, ip, ik, ik, ix);
         }
-        e += (double)(hm * G[x * GS + a] * Rs[t]);
+        R rc;
+        if (pairs) {
+            const int sf = p >= ns ? 2 : 1;
+            int S[4] = {ip, ix, 0, 0}, D[4] = {-sf, sf, 0, 0};
+            rc = site_move_factor<R>(pb, cidx, Rsite, up, dn, S, D, 2);
+        } else {
+            rc = Rs[t];
+        }
+        e += (double)(hm * G[x * GS + a] * rc);
     }
     // doubles: up-up, down-down, up-down classes
     const int cu = nu * (nu - 1) / 2 * (eu * (eu - 1) / 2);
@@ -317,7 +391,14 @@ __device__ double abinitio_energy(const DevProblem& pb, const R* X, int XS, cons
         const R ytb = -Gxb + Fxp1 * Xab;
         const R Sy = -(Hm[iy * E + ix] - Fyp1 * Gxa - Fyp2 * Gxb) + Fxp1 * (-Gya - Fyp2 * Xab) + Fyx * (R(1) - r1);
         const R rpf = r1 * T1 + Sc * ytb - Sy * Xba;
-        const R rc = corr_ratio_double<R>(pb, cidx, p1, x, p2, y, Rs[a * E + ix], Rs[b * E + iy]);
+        R rc;
+        if (pairs) {
+            const int sf1 = p1 >= ns ? 2 : 1, sf2 = p2 >= ns ? 2 : 1;
+            int S[4] = {i1, jx, i2, jy}, D[4] = {-sf1, sf1, -sf2, sf2};
+            rc = site_move_factor<R>(pb, cidx, Rsite, up, dn, S, D, 4);
+        } else {
+            rc = corr_ratio_double<R>(pb, cidx, p1, x, p2, y, Rs[a * E + ix], Rs[b * E + iy]);
+        }
         e += (double)(hm * rpf * rc);
     }
     return e;
@@ -504,7 +585,9 @@ __device__ void walker_run(const SampleArgs& a, int w, unsigned char* base) {
                 R* Rs = Hm + (size_t)(M - N) * (M - N);
                 uint8_t* emp = (uint8_t*)(Rs + (size_t)N * (M - N));
                 int8_t* eidx = (int8_t*)(emp + 128);
-                e_lane = abinitio_energy<R>(pb, X, XS, pos_orb, orb_pos, up, dn, cidx, G, a.GS, Hm, Rs, emp, eidx);
+                R* Rsite = (R*)(eidx + 128);
+                e_lane = abinitio_energy<R>(pb, X, XS, pos_orb, orb_pos, up, dn, cidx, G, a.GS, Hm, Rs, emp, eidx,
+                                            Rsite);
                 __syncwarp();
             }
             e_lane = warp_sum(e_lane);
