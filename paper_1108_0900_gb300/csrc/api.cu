@@ -48,6 +48,10 @@ struct vmc_ctx {
     int ham = 0;
     int maxd = 1;
     int max_csites = 0;          // sites of the largest correlator
+    // shared-memory carveout of the FP32 ab initio walkers in percent: 58 (two
+    // 4-walker CTAs per SM, more L1 for the tables) measured 213 ms against
+    // 221 ms at the driver's choice and 333 ms at 30 (24 orbitals, 65,536 samples)
+    int walker_carveout_ab = 58;
     bool params_set = false, walkers_set = false;
     bool use_stream = true;     // TMA-staged pass for FP32-accumulation products
     bool stream_cached = false;  // register-cached variant for BF16, one vector (slower: 16 warps)
@@ -762,6 +766,10 @@ static int launch_walkers(vmc_ctx* h, SampleArgs& a, bool fp64, cudaStream_t st)
         k_walkers<double><<<blocks, 32 * wpb, smem, st>>>(a); h->n_launch++;
     } else {
         VCK(cudaFuncSetAttribute(k_walkers<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        // shared-memory carveout (percent of the maximum): the ab initio local
+        // energy reads integral, correlator and pair tables through L1
+        VCK(cudaFuncSetAttribute(k_walkers<float>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 h->ham == VMC_ABINITIO ? h->walker_carveout_ab : -1));
         k_walkers<float><<<blocks, 32 * wpb, smem, st>>>(a); h->n_launch++;
     }
     VCK(cudaGetLastError());
