@@ -48,6 +48,7 @@ struct vmc_ctx {
     int ham = 0;
     int maxd = 1;
     int max_csites = 0;          // sites of the largest correlator
+    bool ff_sums = true;         // FP32-store passes with FP64 sums in FP32-pair arithmetic
     // shared-memory carveout of the FP32 ab initio walkers in percent: 58 (two
     // 4-walker CTAs per SM, more L1 for the tables) measured 213 ms against
     // 221 ms at the driver's choice and 333 ms at 30 (24 orbitals, 65,536 samples)
@@ -602,6 +603,7 @@ extern "C" int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, co
     pb.h64 = h->d_h64; pb.h32 = h->d_h32; pb.eri64 = h->d_eri64; pb.eri32 = h->d_eri32;
     pb.pair_ptr = h->d_pair_ptr; pb.pair_corr = h->d_pair_corr;
     pb.max_csites = h->max_csites;
+    pb.ff_sums = h->ff_sums ? 1 : 0;
     pb.C64 = h->d_C64; pb.C32 = h->d_C32; pb.F64 = h->d_F64; pb.F32 = h->d_F32;
     pb.pairtab = h->d_pairtab; pb.rowbase = h->d_rowbase;
     *out = h;

@@ -101,6 +101,7 @@ struct DevProblem {
     const int* corr_sites;     // flattened site lists
     const int64_t* corr_off;   // [ncorr+1] first parameter of each correlator's block, then ncp
     int max_csites;            // sites of the largest correlator
+    int ff_sums;               // FP32-store passes with FP64 sums: FP32-pair arithmetic instead of FP64
     int n_class;               // parameter classes (correlators of a class share a block)
     const int64_t* class_off;  // [n_class+1] parameter blocks of the classes
     const int* class_ptr;      // [n_class+1] into class_inst

@@ -15,6 +15,7 @@
 // per CTA of a thread-block cluster, summed through distributed shared
 // memory, so neither half uses global atomics.
 #include <cooperative_groups.h>
+#include <type_traits>
 #include "common.cuh"
 #include "corr.cuh"
 #include "kernels.h"
@@ -38,9 +39,125 @@ template <> __device__ __forceinline__ double load_st<__nv_bfloat16, double>(con
     return (double)__bfloat162float(((const __nv_bfloat16*)p)[i]);
 }
 
+// FP32 store with FP64-accurate sums in FP32 arithmetic.  The FP64 pipe of
+// this GPU retires one warp FMA per 16 cycles per SM, and the FP64 form of
+// this pass (conversions, FMAs and FP64 shared atomics) is bound by it.
+// Here the v table holds each FP64 value as an FP32 pair (hi, lo); a product
+// w v = w hi + w lo is split exactly into its rounded value and the FMA error
+// term; the per-lane sums are FP32 pairs kept by Knuth's two-sum; the image
+// of the pairing block is two FP32 arrays: the first atomic add returns the
+// old value, so the rounding error of the add it made is known exactly and
+// is added to the second array with the product's error terms.  The rounded
+// intrinsics keep the compiler from fusing the error arithmetic.
+__device__ __forceinline__ void ff_add(float& sh, float& sl, float p, float err) {
+    const float s = __fadd_rn(sh, p);
+    const float bp = __fsub_rn(s, sh);
+    const float e = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+    sh = s;
+    sl = __fadd_rn(sl, __fadd_rn(e, err));
+}
+
+template <int K, bool GATHER>
+__device__ void sr_main_run_ff(const MainArgs<double>& a, int cta, int ncta, unsigned char* smem) {
+    const DevProblem& pb = a.pb;
+    const int npf = pb.npf, M = pb.M, N = pb.N, P = pb.P;
+    float* hi = (float*)smem;                    // [npf][K] image, rounded sums
+    float* lo = hi + (size_t)npf * K;            // [npf][K] their rounding errors
+    float2* vpf = (float2*)(lo + (size_t)npf * K);
+    int* rowbase = (int*)(vpf + (GATHER ? (size_t)npf * K : 0));
+    uint8_t* occw = (uint8_t*)(rowbase + M);
+    for (int i = threadIdx.x; i < 2 * npf * K; i += blockDim.x) hi[i] = 0.f;
+    if (GATHER)
+        for (int i = threadIdx.x; i < npf; i += blockDim.x)
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) {
+                const double v = a.V[kk * pb.nv + pb.ncp + i];
+                const float vh = (float)v;
+                vpf[i * K + kk] = make_float2(vh, (float)(v - (double)vh));
+            }
+    for (int i = threadIdx.x; i < M; i += blockDim.x) rowbase[i] = pb.rowbase[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint8_t* my = occw + wid * 64;
+    const float* pf = (const float*)a.s_pf;
+    for (int64_t s = (int64_t)cta * nw + wid; s < a.n_s; s += (int64_t)ncta * nw) {
+        for (int i = lane; i < N; i += 32) my[i] = a.s_occ[s * a.Nst + i];
+        __syncwarp();
+        double t[K];
+        if (GATHER) {
+            double tc[K];
+            float sh[K], sl[K];
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) {
+                tc[kk] = 0.0;
+                sh[kk] = sl[kk] = 0.f;
+            }
+            for (int c = lane; c < pb.ncorr; c += 32) {
+                const int64_t k = pb.corr_off[c] + a.s_cidx[s * a.ncst + c];
+                const double ic = a.invC[k];
+#pragma unroll
+                for (int kk = 0; kk < K; ++kk) tc[kk] += a.V[kk * pb.nv + k] * ic;
+            }
+            for (int e = lane; e < P; e += 32) {
+                const uint16_t pt = pb.pairtab[e];
+                const int pq = rowbase[my[pt & 255]] + my[pt >> 8];
+                const float w = __ldg(pf + s * a.Pst + e);
+#pragma unroll
+                for (int kk = 0; kk < K; ++kk) {
+                    const float2 v = vpf[pq * K + kk];
+                    const float p = __fmul_rn(w, v.x);
+                    ff_add(sh[kk], sl[kk], p, __fadd_rn(fmaf(w, v.x, -p), __fmul_rn(w, v.y)));
+                }
+            }
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) t[kk] = warp_sum((double)sh[kk] + (double)sl[kk] + tc[kk]);
+            if (lane < K) {
+                double mine = t[0];
+#pragma unroll
+                for (int kk = 1; kk < K; ++kk) if (lane == kk) mine = t[kk];
+                a.T[s * K + lane] = mine;
+            }
+        } else {
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) t[kk] = a.T[s * K + kk];
+        }
+        float th[K], tl[K];
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk) {
+            th[kk] = (float)t[kk];
+            tl[kk] = (float)(t[kk] - (double)th[kk]);
+        }
+        for (int e = lane; e < P; e += 32) {
+            const uint16_t pt = pb.pairtab[e];
+            const int pq = rowbase[my[pt & 255]] + my[pt >> 8];
+            const float w = __ldg(pf + s * a.Pst + e);
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) {
+                const float p = __fmul_rn(th[kk], w);
+                const float err = __fadd_rn(fmaf(th[kk], w, -p), __fmul_rn(tl[kk], w));
+                const float old = atomicAdd(&hi[pq * K + kk], p);
+                const float sum = __fadd_rn(old, p);
+                const float bp = __fsub_rn(sum, old);
+                const float e2 = __fadd_rn(__fsub_rn(old, __fsub_rn(sum, bp)), __fsub_rn(p, bp));
+                atomicAdd(&lo[pq * K + kk], __fadd_rn(e2, err));
+            }
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    double* dst = a.pf_partial + (size_t)cta * npf * K;
+    for (int i = threadIdx.x; i < npf * K; i += blockDim.x) dst[i] = (double)hi[i] + (double)lo[i];
+}
+
 // The generic pass for one problem, run by CTA `cta` of `ncta` serving it.
 template <typename ST, typename AT, int K, bool GATHER>
 __device__ void sr_main_run(const MainArgs<AT>& a, int cta, int ncta, unsigned char* smem) {
+    if constexpr (std::is_same<ST, float>::value && std::is_same<AT, double>::value) {
+        if (a.pb.ff_sums) {
+            sr_main_run_ff<K, GATHER>(a, cta, ncta, smem);
+            return;
+        }
+    }
     const DevProblem& pb = a.pb;
     const int npf = pb.npf, M = pb.M, N = pb.N, P = pb.P;
     AT* acc = (AT*)smem;
