@@ -98,15 +98,26 @@ __device__ void sr_main_run_ff(const MainArgs<double>& a, int cta, int ncta, uns
 #pragma unroll
                 for (int kk = 0; kk < K; ++kk) tc[kk] += a.V[kk * pb.nv + k] * ic;
             }
-            for (int e = lane; e < P; e += 32) {
-                const uint16_t pt = pb.pairtab[e];
-                const int pq = rowbase[my[pt & 255]] + my[pt >> 8];
-                const float w = __ldg(pf + s * a.Pst + e);
+            // four elements per lane in flight: the loads first
+            for (int e0 = lane; e0 < P; e0 += 128) {
+                int pq[4];
+                float w[4];
 #pragma unroll
-                for (int kk = 0; kk < K; ++kk) {
-                    const float2 v = vpf[pq * K + kk];
-                    const float p = __fmul_rn(w, v.x);
-                    ff_add(sh[kk], sl[kk], p, __fadd_rn(fmaf(w, v.x, -p), __fmul_rn(w, v.y)));
+                for (int u = 0; u < 4; ++u) {
+                    const int e = e0 + 32 * u;
+                    w[u] = e < P ? __ldg(pf + s * a.Pst + e) : 0.f;
+                    const uint16_t pt = e < P ? pb.pairtab[e] : (uint16_t)0;
+                    pq[u] = rowbase[my[pt & 255]] + my[pt >> 8];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (e0 + 32 * u >= P) continue;
+#pragma unroll
+                    for (int kk = 0; kk < K; ++kk) {
+                        const float2 v = vpf[pq[u] * K + kk];
+                        const float p = __fmul_rn(w[u], v.x);
+                        ff_add(sh[kk], sl[kk], p, __fadd_rn(fmaf(w[u], v.x, -p), __fmul_rn(w[u], v.y)));
+                    }
                 }
             }
 #pragma unroll
@@ -127,19 +138,29 @@ __device__ void sr_main_run_ff(const MainArgs<double>& a, int cta, int ncta, uns
             th[kk] = (float)t[kk];
             tl[kk] = (float)(t[kk] - (double)th[kk]);
         }
-        for (int e = lane; e < P; e += 32) {
-            const uint16_t pt = pb.pairtab[e];
-            const int pq = rowbase[my[pt & 255]] + my[pt >> 8];
-            const float w = __ldg(pf + s * a.Pst + e);
+        for (int e0 = lane; e0 < P; e0 += 128) {
+            int pq[4];
+            float w[4];
 #pragma unroll
-            for (int kk = 0; kk < K; ++kk) {
-                const float p = __fmul_rn(th[kk], w);
-                const float err = __fadd_rn(fmaf(th[kk], w, -p), __fmul_rn(tl[kk], w));
-                const float old = atomicAdd(&hi[pq * K + kk], p);
-                const float sum = __fadd_rn(old, p);
-                const float bp = __fsub_rn(sum, old);
-                const float e2 = __fadd_rn(__fsub_rn(old, __fsub_rn(sum, bp)), __fsub_rn(p, bp));
-                atomicAdd(&lo[pq * K + kk], __fadd_rn(e2, err));
+            for (int u = 0; u < 4; ++u) {
+                const int e = e0 + 32 * u;
+                w[u] = e < P ? __ldg(pf + s * a.Pst + e) : 0.f;
+                const uint16_t pt = e < P ? pb.pairtab[e] : (uint16_t)0;
+                pq[u] = rowbase[my[pt & 255]] + my[pt >> 8];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (e0 + 32 * u >= P) continue;
+#pragma unroll
+                for (int kk = 0; kk < K; ++kk) {
+                    const float p = __fmul_rn(th[kk], w[u]);
+                    const float err = __fadd_rn(fmaf(th[kk], w[u], -p), __fmul_rn(tl[kk], w[u]));
+                    const float old = atomicAdd(&hi[pq[u] * K + kk], p);
+                    const float sum = __fadd_rn(old, p);
+                    const float bp = __fsub_rn(sum, old);
+                    const float e2 = __fadd_rn(__fsub_rn(old, __fsub_rn(sum, bp)), __fsub_rn(p, bp));
+                    atomicAdd(&lo[pq[u] * K + kk], __fadd_rn(e2, err));
+                }
             }
         }
         __syncwarp();
