@@ -62,6 +62,7 @@ struct vmc_ctx {
     bool use_fused = true;       // fused single-pass product over G (BF16 store, one vector)
     bool use_compact = true;     // two-pass product with the compact gather over G16 (one vector)
     bool use_coop_update = true; // inner CG: x/r and p updates as one cooperative launch
+    bool rank_T = true;          // bank order inside T's blocks (k_rank_T)
     struct SortedLaunch {        // launch shapes of the sorted product for one K (see plan_sorted)
         int64_t n_s = -1;
         bool compact = false;
@@ -1260,6 +1261,11 @@ static int ensure_sorted(vmc_ctx* h, cudaStream_t st) {
         k_scan_params<<<1, 1024, 0, st>>>(h->d_total, h->npf, (uint32_t)(c * h->t_chunk), base); h->n_launch++;
         k_fill_T<<<h->sort_nblk, 512, 2 * smem, st>>>(h->d_G, h->Gst, h->P, sb, se, h->npf, h->d_counts, base,
                                                   h->d_Tsort); h->n_launch++;
+        VCK(cudaGetLastError());
+    }
+    if (h->rank_T) {
+        k_rank_T<<<h->nsm * 8, 256, 0, st>>>(h->d_Tsort, (int64_t)h->t_chunk, nchunk, h->d_base, h->npf, h->n_s);
+        h->n_launch++;
         VCK(cudaGetLastError());
     }
     int rc = ensure_corr_runs(h, st);

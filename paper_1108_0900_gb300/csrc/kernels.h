@@ -301,6 +301,8 @@ __global__ void __launch_bounds__(512) k_count_G(const uint32_t* G, int64_t Pst,
                                                  int64_t s_end, int npf, uint32_t* counts);
 __global__ void k_scan_blocks(uint32_t* counts, int nblk, int npf, uint32_t* total);
 __global__ void __launch_bounds__(1024) k_scan_params(const uint32_t* total, int npf, uint32_t base0, uint32_t* base);
+__global__ void __launch_bounds__(256) k_rank_T(uint32_t* T, int64_t t_chunk, int nchunk, const uint32_t* base,
+                                                int npf, int64_t n_s);
 __global__ void __launch_bounds__(512) k_fill_T(const uint32_t* G, int64_t Pst, int P, int64_t s_begin,
                                                 int64_t s_end, int npf, const uint32_t* offs, const uint32_t* base,
                                                 uint32_t* T);

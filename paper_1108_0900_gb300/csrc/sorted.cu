@@ -165,8 +165,8 @@ __global__ void k_scan_blocks(uint32_t* counts, int nblk, int npf, uint32_t* tot
 // Position inside a run of logical entry r.  Within each kTRun = 128 entry
 // block, entry 32 j + L sits at 4 L + j, so lane L's 16-byte word holds
 // entries L, L + 32, L + 64, L + 96 and the j-th lookup instruction of the
-// scatter covers 32 consecutive entries (consecutive, sorted samples: a few
-// cache lines instead of 32).
+// scatter covers 32 consecutive entries (k_rank_T then reorders each block by
+// shared-memory bank).
 __device__ __forceinline__ uint32_t run_slot(uint32_t r) {
     return (r & ~(uint32_t)(kTRun - 1)) + 4u * (r & 31u) + ((r >> 5) & 3u);
 }
@@ -219,6 +219,79 @@ __global__ void __launch_bounds__(512) k_fill_T(const uint32_t* G, int64_t Pst, 
             const uint32_t r = atomicAdd(&cur[pq], 1u);
             T[rb[pq] + run_slot(r)] = sl | (v & 0xFFFFu);
         }
+    }
+}
+
+// Bank order inside T's blocks, once per set of samples after the fill.
+// The scatter's j-th lookup instruction over a block reads t_s for the
+// entries at positions 4 L + j (lane L); with the samples in fill order
+// their shared-memory banks (s mod 32) collide about 3.5 times per
+// instruction.  One warp per 128-entry block sorts the block's entries by
+// bank (stable): each bank's entries then sit at consecutive positions and
+// go round-robin to the four instructions, about 2.2 wavefronts each.
+// Entries of weight zero (the run padding) take the last positions,
+// re-pointed at sample (position / 4) mod 32 of the chunk (a staged t_s).
+// Only the order inside each block changes: a block holds one parameter's
+// entries before and after.
+__global__ void __launch_bounds__(256) k_rank_T(uint32_t* T, int64_t t_chunk, int nchunk, const uint32_t* base,
+                                                int npf, int64_t n_s) {
+    __shared__ uint32_t cnt[8][32];
+    __shared__ __align__(16) uint32_t buf[8][kTRun];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    const int64_t nblk = t_chunk / kTRun;
+    for (int64_t gw = (int64_t)blockIdx.x * 8 + wid; gw < nchunk * nblk; gw += (int64_t)gridDim.x * 8) {
+        const int c = (int)(gw / nblk);
+        const int64_t e0 = (int64_t)c * t_chunk + (gw - (int64_t)c * nblk) * kTRun;
+        if (e0 >= (int64_t)__ldg(base + (size_t)c * (npf + 1) + npf)) continue;   // past the chunk's runs
+        const int ns = (int)min((int64_t)kTChunk, n_s - (int64_t)c * kTChunk);
+        uint4* w4 = reinterpret_cast<uint4*>(T + e0);
+        const uint4 w = w4[lane];
+        const uint32_t e[4] = {w.x, w.y, w.z, w.w};
+        cnt[wid][lane] = 0u;
+        __syncwarp();
+        uint32_t rk[4];
+        bool real[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {   // rank of each entry within its bank (block order)
+            real[j] = (e[j] & 0xFFFFu) != 0u;
+            const uint32_t b = (e[j] >> 16) & 31u;
+            const uint32_t peers = __match_any_sync(0xffffffffu, real[j] ? b : 32u + (uint32_t)lane);
+            const uint32_t pre = real[j] ? cnt[wid][b] : 0u;
+            rk[j] = pre + __popc(peers & lt);
+            __syncwarp();
+            if (real[j] && (peers & lt) == 0u) cnt[wid][b] = pre + __popc(peers);
+            __syncwarp();
+        }
+        // first position of each bank: exclusive scan of the counts (lane = bank)
+        const uint32_t cl = cnt[wid][lane];
+        uint32_t incl = cl;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        uint32_t free_pos = __shfl_sync(0xffffffffu, incl, 31);   // the real entries
+        __syncwarp();
+        cnt[wid][lane] = incl - cl;
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t fb = __ballot_sync(0xffffffffu, !real[j]);
+            uint32_t pos, v = e[j];
+            if (real[j]) {
+                pos = cnt[wid][(e[j] >> 16) & 31u] + rk[j];
+            } else {
+                pos = free_pos + __popc(fb & lt);
+                const uint32_t sf = (pos >> 2) & 31u;
+                v = ((int)sf < ns ? sf : 0u) << 16;
+            }
+            free_pos += __popc(fb);
+            buf[wid][pos] = v;
+        }
+        __syncwarp();
+        w4[lane] = reinterpret_cast<const uint4*>(buf[wid])[lane];
+        __syncwarp();
     }
 }
 
@@ -427,9 +500,9 @@ __global__ void __launch_bounds__(gather_threads(K)) k_gather_G(SortedArgs a) {
 // all NWF blocks are issued before their sums.  Every block belongs to one
 // parameter (runs are whole blocks, padding entries weigh zero); when a block
 // starts past the current run, the warp sums its lanes and writes the
-// finished parameter.  Lane L's word of a block holds entries L, L + 32,
-// L + 64, L + 96, so one lookup instruction covers 32 consecutive (sorted)
-// samples.
+// finished parameter.  Lane L's word of a block holds the block's entries
+// 4 L .. 4 L + 3; k_rank_T sorts each block by the bank of its sample, so
+// the j-th lookup instruction (entries 4 L + j) meets each bank about twice.
 constexpr uint32_t kScatterAhead = 4;   // iterations of the scatter's T stream prefetched into L2
 
 // Correlator half of the scatter for chunk c inside pairing CTA (c, g): for
