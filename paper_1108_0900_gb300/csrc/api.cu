@@ -740,12 +740,12 @@ static int read_status(vmc_ctx* h, cudaStream_t st) {
 // walker) and returns the slice size
 static size_t prep_walkers(vmc_ctx* h, SampleArgs& a, bool fp64) {
     a.pb = h->pb;
-    a.XS = h->N + 1;
+    a.XS = (h->N + 2) & ~1;   // even (the rank-2 update moves column pairs), N + 1 or N + 2
     a.GS = h->N + 1;
     a.ncorr_pad = (int)round_up(std::max(h->ncorr, 1), 4);
     const size_t rsz = fp64 ? 8 : 4;
     size_t wb = (size_t)h->N * a.XS * rsz + 3 * (size_t)a.XS * rsz;
-    wb = wb + 64 * 4 + (size_t)a.ncorr_pad * 4 + 64 + 128;
+    wb = wb + 64 + (size_t)a.ncorr_pad * 4 + 64 + 128;
     if (h->ham == VMC_ABINITIO && a.want_energy) {
         // G [M][GS], H [E][E], single-move factors [N][E], empty list, index
         // map, per-site factors [ns][4]

@@ -33,6 +33,10 @@ struct WarpMem {
 __device__ __forceinline__ float log_abs(float x) { return logf(fabsf(x)); }
 __device__ __forceinline__ double log_abs(double x) { return log(fabs(x)); }
 
+template <typename R> struct pair_of;
+template <> struct pair_of<float> { using type = float2; };
+template <> struct pair_of<double> { using type = double2; };
+
 template <typename R>
 __device__ R corr_ratio_warp(const DevProblem& pb, uint32_t* cidx, int p, int q, bool commit) {
     const int lane = threadIdx.x & 31;
@@ -77,10 +81,10 @@ __device__ R corr_ratio_serial(const DevProblem& pb, const uint32_t* cidx, int p
 }
 
 // In-place Gauss-Jordan inverse with partial pivoting of the N x N matrix X
-// (row stride XS) by one warp.  col: N scratch, piv: N ints.  Returns false
-// if a pivot column is entirely zero or not finite.
+// (row stride XS) by one warp.  col: N scratch, piv: N row indices.  Returns
+// false if a pivot column is entirely zero or not finite.
 template <typename R>
-__device__ bool gj_invert_warp(R* X, int N, int XS, R* col, int* piv) {
+__device__ bool gj_invert_warp(R* X, int N, int XS, R* col, uint8_t* piv) {
     const int lane = threadIdx.x & 31;
     for (int k = 0; k < N; ++k) {
         R best = R(-1);
@@ -96,7 +100,7 @@ __device__ bool gj_invert_warp(R* X, int N, int XS, R* col, int* piv) {
             if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
         }
         if (!(best > R(0)) || !isfinite(best)) return false;
-        if (lane == 0) piv[k] = bi;
+        if (lane == 0) piv[k] = (uint8_t)bi;
         if (bi != k) {
             for (int j = lane; j < N; j += 32) {
                 R t = X[k * XS + j];
@@ -406,7 +410,8 @@ __device__ double abinitio_energy(const DevProblem& pb, const R* X, int XS, cons
 
 // X = F[o, o]^{-1} for the current (unsorted) positions o, from scratch
 template <typename R>
-__device__ bool rebuild_inverse(const DevProblem& pb, R* X, int N, int XS, const uint8_t* pos_orb, R* col, int* piv) {
+__device__ bool rebuild_inverse(const DevProblem& pb, R* X, int N, int XS, const uint8_t* pos_orb, R* col,
+                                uint8_t* piv) {
     const int lane = threadIdx.x & 31;
     for (int i = 0; i < N; ++i) {
         int p = pos_orb[i];
@@ -439,7 +444,7 @@ __device__ void walker_run(const SampleArgs& a, int w, unsigned char* base) {
     R* bv = X + N * XS;
     R* yv = bv + XS;
     R* cv = yv + XS;
-    int* iv = (int*)(cv + XS);                 // 64 ints
+    uint8_t* iv = (uint8_t*)(cv + XS);         // 64 positions
     uint32_t* cidx = (uint32_t*)(iv + 64);     // ncorr (rounded up to 4)
     uint8_t* pos_orb = (uint8_t*)(cidx + a.ncorr_pad);
     int8_t* orb_pos = (int8_t*)(pos_orb + 64); // 128
@@ -493,11 +498,25 @@ __device__ void walker_run(const SampleArgs& a, int w, unsigned char* base) {
     double lnrun = 0.0;   // ln|Psi| of the chain relative to its start, summed from the accepted ratios
     const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
     const int n_sweeps = a.n_burn + a.spw;
+    // Philox words of 32 consecutive proposals at once: lane L holds those of
+    // counter step0 + L, and each proposal reads its own by shuffle (the same
+    // numbers as one evaluation per proposal, a 32nd of the instructions)
+    uint64_t step0 = step;
+    u32x4 rl = philox4x32_10(u32x4{(uint32_t)w, (uint32_t)(step0 + lane), (uint32_t)((step0 + lane) >> 32), 0u},
+                             k0, k1);
 
     for (int sw = 0; sw < n_sweeps; ++sw) {
         for (int t = 0; t < a.props_per_sweep; ++t) {
-            u32x4 ctr{(uint32_t)w, (uint32_t)step, (uint32_t)(step >> 32), 0u};
-            u32x4 r = philox4x32_10(ctr, k0, k1);
+            if (step - step0 >= 32u) {
+                step0 = step;
+                const uint64_t sl = step0 + (uint64_t)lane;
+                rl = philox4x32_10(u32x4{(uint32_t)w, (uint32_t)sl, (uint32_t)(sl >> 32), 0u}, k0, k1);
+            }
+            const int rsrc = (int)(step - step0);
+            u32x4 r;
+            r.x = __shfl_sync(VMC_FULL_MASK, rl.x, rsrc);
+            r.y = __shfl_sync(VMC_FULL_MASK, rl.y, rsrc);
+            r.z = __shfl_sync(VMC_FULL_MASK, rl.z, rsrc);
             ++step;
             int as = (int)mulhi32(r.x, (uint32_t)N);
             int p = as < nu ? nth_set_bit64(up, as) : ns + nth_set_bit64(dn, as - nu);
@@ -522,18 +541,43 @@ __device__ void walker_run(const SampleArgs& a, int w, unsigned char* base) {
             if (!accept) continue;
             lnrun += (double)log_abs(ratio);
             __syncwarp();
-            for (int i = lane; i < N; i += 32) {
-                R yi = R(0);
-                for (int j = 0; j < N; ++j) yi += X[i * XS + j] * bv[j];
-                if (i == ap) yi += R(1);
-                yv[i] = yi;
-                cv[i] = X[i * XS + ap];
-            }
-            __syncwarp();
-            R rinv = R(1) / rpf;
-            for (int i = lane; i < N; i += 32) {
-                R ci = cv[i] * rinv, yi = yv[i] * rinv;
-                for (int j = 0; j < N; ++j) X[i * XS + j] += ci * yv[j] - yi * cv[j];
+            {
+                // lane L owns the column pair 2L, 2L + 1 (XS even); X is
+                // antisymmetric, so c = X[:, a] = -X[a, :] and
+                // y_j = (X b)_j + [j = a] = -sum_i b_i X_ij + [j = a]
+                using R2 = typename pair_of<R>::type;
+                const int j0 = 2 * lane;
+                const bool own = j0 < N;
+                R2* cy = reinterpret_cast<R2*>(yv);   // (c_i / r, y_i / r) of every row
+                R2 cj{R(0), R(0)}, yj{R(0), R(0)};
+                const R rinv = R(1) / rpf;
+                if (own) {
+                    const R2 xa = *reinterpret_cast<const R2*>(X + ap * XS + j0);
+                    cj.x = -xa.x;
+                    cj.y = -xa.y;
+                    for (int i = 0; i < N; ++i) {
+                        const R bi = bv[i];
+                        const R2 x = *reinterpret_cast<const R2*>(X + i * XS + j0);
+                        yj.x = fma(-bi, x.x, yj.x);
+                        yj.y = fma(-bi, x.y, yj.y);
+                    }
+                    if (j0 == ap) yj.x += R(1);
+                    if (j0 + 1 == ap) yj.y += R(1);
+                    cy[j0] = R2{cj.x * rinv, yj.x * rinv};
+                    if (j0 + 1 < N) cy[j0 + 1] = R2{cj.y * rinv, yj.y * rinv};
+                }
+                __syncwarp();
+                if (own) {
+                    // X_ij += (c_i y_j - y_i c_j) / r
+                    for (int i = 0; i < N; ++i) {
+                        const R2 ci = cy[i];
+                        R2* xp = reinterpret_cast<R2*>(X + i * XS + j0);
+                        R2 x = *xp;
+                        x.x = fma(ci.x, yj.x, fma(-ci.y, cj.x, x.x));
+                        x.y = fma(ci.x, yj.y, fma(-ci.y, cj.y, x.y));
+                        *xp = x;
+                    }
+                }
             }
             corr_ratio_warp<R>(pb, cidx, p, q, true);
             if (lane == 0) {
@@ -597,7 +641,7 @@ __device__ void walker_run(const SampleArgs& a, int w, unsigned char* base) {
         // ascending occupation and the position of each sorted electron
         for (int i = lane; i < N; i += 32) {
             int o = i < nu ? nth_set_bit64(up, i) : ns + nth_set_bit64(dn, i - nu);
-            iv[i] = orb_pos[o];
+            iv[i] = (uint8_t)orb_pos[o];
             if (a.s_occ) a.s_occ[s * a.Nst + i] = (uint8_t)o;
         }
         __syncwarp();
