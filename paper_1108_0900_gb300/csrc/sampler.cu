@@ -528,6 +528,21 @@ __device__ void walker_run(const SampleArgs& a, int w, unsigned char* base) {
             int q = spin * ns + nth_set_bit64(~m & sitemask, kk);
             R u = R(r.z >> 8) * R(1.0 / 16777216.0);
             int ap = orb_pos[p];
+            // correlator factor, one membership entry per lane when the two
+            // sites have at most 32: its two parameter loads (L2) go out
+            // first and are waited on after the pfaffian row product
+            const int csf = spin + 1, csp = p - spin * ns, csq = q - spin * ns;
+            const int ctot = (pb.site_cptr[csp + 1] - pb.site_cptr[csp]) + (pb.site_cptr[csq + 1] - pb.site_cptr[csq]);
+            const bool cfast = ctot <= 32;
+            R cnum = R(1), cden = R(1);
+            int cc = -1, cnew = -1;
+            if (cfast && lane < ctot) {
+                cnew = corr_entry(pb, cidx, csp, csq, csf, lane, &cc);
+                if (cc >= 0) {
+                    cnum = load_C<R>(pb, pb.corr_off[cc] + cnew);
+                    cden = load_C<R>(pb, pb.corr_off[cc] + cidx[cc]);
+                }
+            }
             R acc = R(0);
             for (int j = lane; j < N; j += 32) {
                 R bj = (j == ap) ? R(0) : load_F<R>(pb, q, pos_orb[j]);
@@ -535,7 +550,7 @@ __device__ void walker_run(const SampleArgs& a, int w, unsigned char* base) {
                 acc += bj * X[ap * XS + j];
             }
             R rpf = -warp_sum(acc);
-            R rc = corr_ratio_warp<R>(pb, cidx, p, q, false);
+            R rc = cfast ? warp_prod(cnum / cden) : corr_ratio_warp<R>(pb, cidx, p, q, false);
             R ratio = rpf * rc;
             bool accept = u < ratio * ratio;
             if (!accept) continue;
@@ -579,7 +594,13 @@ __device__ void walker_run(const SampleArgs& a, int w, unsigned char* base) {
                     }
                 }
             }
-            corr_ratio_warp<R>(pb, cidx, p, q, true);
+            if (cfast) {
+                __syncwarp();
+                if (cc >= 0) cidx[cc] = (uint32_t)cnew;
+                __syncwarp();
+            } else {
+                corr_ratio_warp<R>(pb, cidx, p, q, true);
+            }
             if (lane == 0) {
                 pos_orb[ap] = (uint8_t)q;
                 orb_pos[p] = -1;
