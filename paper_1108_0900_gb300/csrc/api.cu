@@ -106,6 +106,8 @@ struct vmc_ctx {
     double *d_h64 = nullptr, *d_eri64 = nullptr;
     float *d_h32 = nullptr, *d_eri32 = nullptr;
     int *d_pair_ptr = nullptr, *d_pair_corr = nullptr;
+    uint16_t* d_dexc = nullptr;   // double-excitation pair tables (ab initio)
+    bool pair_unique = false;     // no site pair lies in two correlators (and ncp < 2^30)
     double *d_C64 = nullptr, *d_invC64 = nullptr, *d_F64 = nullptr;
     float *d_C32 = nullptr, *d_invC32 = nullptr, *d_F32 = nullptr;
     uint16_t* d_pairtab = nullptr;
@@ -351,9 +353,11 @@ extern "C" int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, co
             for (int j1 = cptr[c]; j1 < cptr[c + 1]; ++j1)
                 for (int j2 = cptr[c]; j2 < cptr[c + 1]; ++j2)
                     if (j1 != j2) pl[(size_t)csites[j1] * ns + csites[j2]].push_back(c);
+        h->pair_unique = h->ncp < ((int64_t)1 << 30);
         for (size_t k = 0; k < pl.size(); ++k) {
             for (int c : pl[k]) pcorr.push_back(c);
             pptr[k + 1] = (int)pcorr.size();
+            if (pl[k].size() > 1) h->pair_unique = false;
         }
     }
     // ab initio integrals: (pq|rs) = sum_mu L^mu_pq L^mu_rs (Eq. 9 with R = L)
@@ -488,6 +492,24 @@ extern "C" int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, co
         UPL(h->d_h32, h32.data(), h32.size());
         UPL(h->d_eri64, eri64.data(), eri64.size());
         UPL(h->d_eri32, eri32.data(), eri32.size());
+        // double excitations: electron-position pairs, then empty-orbital
+        // index pairs, of the up-up, down-down and up-down classes
+        const int eu = ns - nu, ed = ns - nd;
+        std::vector<uint16_t> dx;
+        for (int a = 0; a < nu; ++a)
+            for (int b = a + 1; b < nu; ++b) dx.push_back((uint16_t)(a | b << 8));
+        for (int a = nu; a < N; ++a)
+            for (int b = a + 1; b < N; ++b) dx.push_back((uint16_t)(a | b << 8));
+        for (int a = 0; a < nu; ++a)
+            for (int b = nu; b < N; ++b) dx.push_back((uint16_t)(a | b << 8));
+        for (int x = 0; x < eu; ++x)
+            for (int y = x + 1; y < eu; ++y) dx.push_back((uint16_t)(x | y << 8));
+        for (int x = eu; x < eu + ed; ++x)
+            for (int y = x + 1; y < eu + ed; ++y) dx.push_back((uint16_t)(x | y << 8));
+        for (int x = 0; x < eu; ++x)
+            for (int y = eu; y < eu + ed; ++y) dx.push_back((uint16_t)(x | y << 8));
+        ACK(h->alloc(&h->d_dexc, std::max<size_t>(dx.size(), 1)));
+        if (!dx.empty()) UPL(h->d_dexc, dx.data(), dx.size());
     }
     // parameters
     ACK(h->alloc(&h->d_C64, h->ncp));
@@ -603,6 +625,8 @@ extern "C" int vmc_create(const vmc_lattice* lat, const vmc_hamiltonian* ham, co
     pb.nbr_ptr = h->d_nbr_ptr; pb.nbr_site = h->d_nbr_site; pb.nbr_t = h->d_nbr_t;
     pb.h64 = h->d_h64; pb.h32 = h->d_h32; pb.eri64 = h->d_eri64; pb.eri32 = h->d_eri32;
     pb.pair_ptr = h->d_pair_ptr; pb.pair_corr = h->d_pair_corr;
+    pb.pair_unique = h->pair_unique ? 1 : 0;
+    pb.dexc = h->d_dexc;
     pb.max_csites = h->max_csites;
     pb.ff_sums = h->ff_sums ? 1 : 0;
     pb.C64 = h->d_C64; pb.C32 = h->d_C32; pb.F64 = h->d_F64; pb.F32 = h->d_F32;
@@ -751,6 +775,8 @@ static size_t prep_walkers(vmc_ctx* h, SampleArgs& a, bool fp64) {
         // map, per-site factors [ns][4]
         const size_t E = (size_t)(h->M - h->N);
         wb += ((size_t)h->M * a.GS + E * E + (size_t)h->N * E) * rsz + 128 + 128 + (size_t)4 * h->ns * rsz;
+        // the sample's site-pair table (pair correlators, each pair in at most one)
+        if (h->max_csites <= 2 && h->pair_unique) wb += (size_t)h->ns * (h->ns - 1) / 2 * 4;
     }
     wb = round_up(wb, 16);
     a.warp_bytes = wb;

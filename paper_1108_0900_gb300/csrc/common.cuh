@@ -123,6 +123,11 @@ struct DevProblem {
     // correlators containing both sites i and j: pair_corr[pair_ptr[i ns + j] ..]
     const int* pair_ptr;
     const int* pair_corr;
+    int pair_unique;           // no site pair lies in two correlators (and ncp < 2^30): per-sample pair table
+    // double excitations: electron-position pairs (a | b << 8) of the up-up,
+    // down-down and up-down classes, then empty-orbital index pairs (ix | iy << 8)
+    // of the same classes (ab initio only)
+    const uint16_t* dexc;
     // parameters
     const double* C64;
     const float* C32;

@@ -156,17 +156,6 @@ template <> __device__ __forceinline__ double load_eri<double>(const DevProblem&
     return __ldg(pb.eri64 + ((p * n + q) * n + r) * n + s);
 }
 
-// (i, j), i < j, of the k-th pair in row-major order over n items
-__device__ __forceinline__ void tri_decode(int k, int n, int* i, int* j) {
-    const float b = 2.f * n - 1.f;
-    int a = (int)floorf((b - sqrtf(fmaxf(b * b - 8.f * k, 0.f))) * 0.5f);
-    a = max(0, min(a, n - 2));
-    while (a > 0 && a * n - a * (a + 1) / 2 > k) --a;
-    while ((a + 1) * n - (a + 1) * (a + 2) / 2 <= k) ++a;
-    *i = a;
-    *j = a + 1 + (k - (a * n - a * (a + 1) / 2));
-}
-
 // Correlator factor of moving two electrons (p1 -> x, p2 -> y; sf = 1 up, 2
 // down for each move) given the two single-move factors r1, r2: correlators
 // touched by both moves hold a site of each, so they are found through the
@@ -232,10 +221,33 @@ __device__ R pair_correction(const DevProblem& pb, const uint32_t* cidx, int s, 
     return f;
 }
 
+// The same correction from the sample's pair table: entry k(s, t) (s < t,
+// row-major over site pairs) = the base C index corr_off[c] + state of the
+// one correlator c holding s and t (bits 0-29, all ones if none) and whether
+// s and t carry weight 4 in c (bits 30, 31).  Same arithmetic as the lists.
+__device__ __forceinline__ int site_pair_index(int s, int t, int ns) { return s * (2 * ns - s - 1) / 2 + t - s - 1; }
+
+template <typename R>
+__device__ __forceinline__ R pair_correction_tab(const DevProblem& pb, const uint32_t* ptab, int s, int dvs, int t,
+                                                 int dvt) {
+    if (s > t) {
+        const int u = s; s = t; t = u;
+        const int d = dvs; dvs = dvt; dvt = d;
+    }
+    const uint32_t en = ptab[site_pair_index(s, t, pb.ns)];
+    if (en == 0xFFFFFFFFu) return R(1);
+    const int64_t off = (int64_t)(en & 0x3FFFFFFFu);
+    const int ds = (((en >> 30) & 1u) ? 4 : 1) * dvs, dt = ((en >> 31) ? 4 : 1) * dvt;
+    R f = R(1);
+    f *= load_C<R>(pb, off + ds + dt) * load_C<R>(pb, off) / (load_C<R>(pb, off + ds) * load_C<R>(pb, off + dt));
+    return f;
+}
+
 // factor of the move changing sites S[k] by D[k] (local state units), k < n
 template <typename R>
 __device__ __forceinline__ R site_move_factor(const DevProblem& pb, const uint32_t* cidx, const R* Rsite,
-                                              uint64_t up, uint64_t dn, int (&S)[4], int (&D)[4], int n) {
+                                              const uint32_t* ptab, uint64_t up, uint64_t dn, int (&S)[4],
+                                              int (&D)[4], int n) {
     bool alive[4] = {true, true, true, true};
     for (int k = 1; k < n; ++k)
         for (int m = 0; m < k; ++m)
@@ -250,7 +262,8 @@ __device__ __forceinline__ R site_move_factor(const DevProblem& pb, const uint32
     for (int k = 0; k < n; ++k)
         for (int m = k + 1; m < n; ++m)
             if (alive[k] && alive[m] && D[k] != 0 && D[m] != 0)
-                f *= pair_correction<R>(pb, cidx, S[k], D[k], S[m], D[m]);
+                f *= ptab ? pair_correction_tab<R>(pb, ptab, S[k], D[k], S[m], D[m])
+                          : pair_correction<R>(pb, cidx, S[k], D[k], S[m], D[m]);
     return f;
 }
 
@@ -269,8 +282,10 @@ __device__ __forceinline__ R site_move_factor(const DevProblem& pb, const uint32
 template <typename R>
 __device__ double abinitio_energy(const DevProblem& pb, const R* X, int XS, const uint8_t* pos_orb,
                                   const int8_t* orb_pos, uint64_t up, uint64_t dn, const uint32_t* cidx,
-                                  R* G, int GS, R* Hm, R* Rs, uint8_t* emp, int8_t* eidx, R* Rsite) {
+                                  R* G, int GS, R* Hm, R* Rs, uint8_t* emp, int8_t* eidx, R* Rsite,
+                                  uint32_t* ptab_s) {
     const bool pairs = pb.max_csites <= 2;   // the site-factorised correlator ratios apply
+    const uint32_t* ptab = pairs && pb.pair_unique ? ptab_s : nullptr;
     const int lane = threadIdx.x & 31;
     const int ns = pb.ns, M = pb.M, N = pb.N, nu = pb.nu, nd = pb.nd;
     const int eu = ns - nu, ed = ns - nd, E = eu + ed;
@@ -310,6 +325,21 @@ __device__ double abinitio_energy(const DevProblem& pb, const R* X, int XS, cons
                     f *= load_C<R>(pb, k + pb.site_w[ent] * (v - n)) / load_C<R>(pb, k);
                 }
             Rsite[t] = f;
+        }
+        if (ptab) {
+            // the pair table of this sample (see pair_correction_tab)
+            for (int si = 0; si + 1 < ns; ++si)
+                for (int ti = si + 1 + lane; ti < ns; ti += 32) {
+                    const int lo = pb.pair_ptr[si * ns + ti], hi = pb.pair_ptr[si * ns + ti + 1];
+                    uint32_t en = 0xFFFFFFFFu;
+                    if (hi > lo) {
+                        const int c = pb.pair_corr[lo];
+                        en = (uint32_t)(pb.corr_off[c] + (int64_t)cidx[c]) |
+                             (site_weight_in(pb, c, si) == 4 ? 1u << 30 : 0u) |
+                             (site_weight_in(pb, c, ti) == 4 ? 1u << 31 : 0u);
+                    }
+                    ptab_s[site_pair_index(si, ti, ns)] = en;
+                }
         }
     } else {
         // single-move correlator factors Rs[a][ie] (same spin only)
@@ -351,59 +381,66 @@ __device__ double abinitio_energy(const DevProblem& pb, const R* X, int XS, cons
         if (pairs) {
             const int sf = p >= ns ? 2 : 1;
             int S[4] = {ip, ix, 0, 0}, D[4] = {-sf, sf, 0, 0};
-            rc = site_move_factor<R>(pb, cidx, Rsite, up, dn, S, D, 2);
+            rc = site_move_factor<R>(pb, cidx, Rsite, ptab, up, dn, S, D, 2);
         } else {
             rc = Rs[t];
         }
         e += (double)(hm * G[x * GS + a] * rc);
     }
-    // doubles: up-up, down-down, up-down classes
-    const int cu = nu * (nu - 1) / 2 * (eu * (eu - 1) / 2);
-    const int cd = nd * (nd - 1) / 2 * (ed * (ed - 1) / 2);
-    const int cx = nu * nd * eu * ed;
-    for (int t = lane; t < cu + cd + cx; t += 32) {
-        int a, b, ix, iy;
-        if (t < cu) {
-            const int nxy = eu * (eu - 1) / 2;
-            tri_decode(t / nxy, nu, &a, &b);
-            tri_decode(t % nxy, eu, &ix, &iy);
-        } else if (t < cu + cd) {
-            const int u = t - cu, nxy = ed * (ed - 1) / 2;
-            tri_decode(u / nxy, nd, &a, &b);
-            tri_decode(u % nxy, ed, &ix, &iy);
-            a += nu; b += nu; ix += eu; iy += eu;
-        } else {
-            const int u = t - cu - cd;
-            a = u / (nd * eu * ed);
-            b = nu + (u / (eu * ed)) % nd;
-            ix = (u / ed) % eu;
-            iy = eu + u % ed;
+    // doubles: up-up, down-down and up-down classes.  Within a class the
+    // lanes run over (electron pair, empty pair) with the electron pair
+    // outer; both pairs come from the host's tables (dexc), the position in
+    // each advancing by 32 per step.
+    {
+        const int nab[3] = {nu * (nu - 1) / 2, nd * (nd - 1) / 2, nu * nd};
+        const int nxy[3] = {eu * (eu - 1) / 2, ed * (ed - 1) / 2, eu * ed};
+        const uint16_t* tab_ab = pb.dexc;
+        const uint16_t* tab_xy = pb.dexc + nab[0] + nab[1] + nab[2];
+        for (int cls = 0; cls < 3; ++cls) {
+            const int nx = nxy[cls], total = nab[cls] * nx;
+            if (cls > 0) {
+                tab_ab += nab[cls - 1];
+                tab_xy += nxy[cls - 1];
+            }
+            if (total == 0) continue;
+            int kab = lane / nx, kxy = lane - (lane / nx) * nx;
+            for (int t = lane; t < total; t += 32) {
+                const uint32_t ab = tab_ab[kab], xy = tab_xy[kxy];
+                kxy += 32;
+                while (kxy >= nx) {
+                    kxy -= nx;
+                    ++kab;
+                }
+                const int a = (int)(ab & 255u), b = (int)(ab >> 8), ix = (int)(xy & 255u), iy = (int)(xy >> 8);
+                const int p1 = pos_orb[a], p2 = pos_orb[b], x = emp[ix], y = emp[iy];
+                const int i1 = p1 >= ns ? p1 - ns : p1, i2 = p2 >= ns ? p2 - ns : p2;
+                const int jx = x >= ns ? x - ns : x, jy = y >= ns ? y - ns : y;
+                R hm = load_eri<R>(pb, i1, jx, i2, jy);
+                if ((p1 >= ns) == (p2 >= ns)) hm -= load_eri<R>(pb, i1, jy, i2, jx);
+                if (hm == R(0)) continue;
+                // pfaffian ratio for a -> x then b -> y
+                const R Xab = X[a * XS + b], Xba = X[b * XS + a];
+                const R Gxa = G[x * GS + a], Gxb = G[x * GS + b], Gya = G[y * GS + a], Gyb = G[y * GS + b];
+                const R Fyp1 = load_F<R>(pb, y, p1), Fyp2 = load_F<R>(pb, y, p2), Fyx = load_F<R>(pb, y, x);
+                const R Fxp1 = load_F<R>(pb, x, p1);
+                const R r1 = Gxa;
+                const R T1 = Gyb - Fyp1 * Xab + Fyx * Xab;
+                const R Sc = Gya - Fyp2 * Xba;
+                const R ytb = -Gxb + Fxp1 * Xab;
+                const R Sy = -(Hm[iy * E + ix] - Fyp1 * Gxa - Fyp2 * Gxb) + Fxp1 * (-Gya - Fyp2 * Xab) +
+                             Fyx * (R(1) - r1);
+                const R rpf = r1 * T1 + Sc * ytb - Sy * Xba;
+                R rc;
+                if (pairs) {
+                    const int sf1 = p1 >= ns ? 2 : 1, sf2 = p2 >= ns ? 2 : 1;
+                    int S[4] = {i1, jx, i2, jy}, D[4] = {-sf1, sf1, -sf2, sf2};
+                    rc = site_move_factor<R>(pb, cidx, Rsite, ptab, up, dn, S, D, 4);
+                } else {
+                    rc = corr_ratio_double<R>(pb, cidx, p1, x, p2, y, Rs[a * E + ix], Rs[b * E + iy]);
+                }
+                e += (double)(hm * rpf * rc);
+            }
         }
-        const int p1 = pos_orb[a], p2 = pos_orb[b], x = emp[ix], y = emp[iy];
-        const int i1 = p1 % ns, i2 = p2 % ns, jx = x % ns, jy = y % ns;
-        R hm = load_eri<R>(pb, i1, jx, i2, jy);
-        if ((p1 >= ns) == (p2 >= ns)) hm -= load_eri<R>(pb, i1, jy, i2, jx);
-        if (hm == R(0)) continue;
-        // pfaffian ratio for a -> x then b -> y
-        const R Xab = X[a * XS + b], Xba = X[b * XS + a];
-        const R Gxa = G[x * GS + a], Gxb = G[x * GS + b], Gya = G[y * GS + a], Gyb = G[y * GS + b];
-        const R Fyp1 = load_F<R>(pb, y, p1), Fyp2 = load_F<R>(pb, y, p2), Fyx = load_F<R>(pb, y, x);
-        const R Fxp1 = load_F<R>(pb, x, p1);
-        const R r1 = Gxa;
-        const R T1 = Gyb - Fyp1 * Xab + Fyx * Xab;
-        const R Sc = Gya - Fyp2 * Xba;
-        const R ytb = -Gxb + Fxp1 * Xab;
-        const R Sy = -(Hm[iy * E + ix] - Fyp1 * Gxa - Fyp2 * Gxb) + Fxp1 * (-Gya - Fyp2 * Xab) + Fyx * (R(1) - r1);
-        const R rpf = r1 * T1 + Sc * ytb - Sy * Xba;
-        R rc;
-        if (pairs) {
-            const int sf1 = p1 >= ns ? 2 : 1, sf2 = p2 >= ns ? 2 : 1;
-            int S[4] = {i1, jx, i2, jy}, D[4] = {-sf1, sf1, -sf2, sf2};
-            rc = site_move_factor<R>(pb, cidx, Rsite, up, dn, S, D, 4);
-        } else {
-            rc = corr_ratio_double<R>(pb, cidx, p1, x, p2, y, Rs[a * E + ix], Rs[b * E + iy]);
-        }
-        e += (double)(hm * rpf * rc);
     }
     return e;
 }
@@ -651,8 +688,9 @@ __device__ void walker_run(const SampleArgs& a, int w, unsigned char* base) {
                 uint8_t* emp = (uint8_t*)(Rs + (size_t)N * (M - N));
                 int8_t* eidx = (int8_t*)(emp + 128);
                 R* Rsite = (R*)(eidx + 128);
+                uint32_t* ptab = (uint32_t*)(Rsite + 4 * ns);
                 e_lane = abinitio_energy<R>(pb, X, XS, pos_orb, orb_pos, up, dn, cidx, G, a.GS, Hm, Rs, emp, eidx,
-                                            Rsite);
+                                            Rsite, ptab);
                 __syncwarp();
             }
             e_lane = warp_sum(e_lane);
