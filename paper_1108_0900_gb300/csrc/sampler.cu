@@ -33,6 +33,26 @@ struct WarpMem {
 __device__ __forceinline__ float log_abs(float x) { return logf(fabsf(x)); }
 __device__ __forceinline__ double log_abs(double x) { return log(fabs(x)); }
 
+// Sum of many terms of the walker's precision with FP64 accuracy: FP64 for
+// FP64 walkers; for FP32 walkers an FP32 pair (two-sum: the rounding error of
+// each add goes to the low word), which keeps the sum off the FP64 pipe.
+template <typename R> struct term_sum;
+template <> struct term_sum<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct term_sum<float> {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float s = __fadd_rn(hi, x);
+        const float bx = __fsub_rn(s, hi);
+        lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bx)), __fsub_rn(x, bx)));
+        hi = s;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 template <typename R> struct pair_of;
 template <> struct pair_of<float> { using type = float2; };
 template <> struct pair_of<double> { using type = double2; };
@@ -394,6 +414,7 @@ __device__ double abinitio_energy(const DevProblem& pb, const R* X, int XS, cons
     {
         const int nab[3] = {nu * (nu - 1) / 2, nd * (nd - 1) / 2, nu * nd};
         const int nxy[3] = {eu * (eu - 1) / 2, ed * (ed - 1) / 2, eu * ed};
+        term_sum<R> ed;
         const uint16_t* tab_ab = pb.dexc;
         const uint16_t* tab_xy = pb.dexc + nab[0] + nab[1] + nab[2];
         for (int cls = 0; cls < 3; ++cls) {
@@ -438,9 +459,10 @@ __device__ double abinitio_energy(const DevProblem& pb, const R* X, int XS, cons
                 } else {
                     rc = corr_ratio_double<R>(pb, cidx, p1, x, p2, y, Rs[a * E + ix], Rs[b * E + iy]);
                 }
-                e += (double)(hm * rpf * rc);
+                ed.add(hm * rpf * rc);
             }
         }
+        e += ed.value();
     }
     return e;
 }
