@@ -1978,10 +1978,13 @@ static int cg_loop(vmc_ctx* h, const void* s_pf, int kind, const VT* b, VT* x, V
     if (fused && h->ncp > 0) VCK(cudaMemsetAsync(h->d_corrraw, 0, sizeof(float) * h->ncp, st));
     // the two updates as one cooperative launch when the update grid is co-resident
     bool coop = false;
+    // one pass of the update grid covers the vectors: the register-resident form
+    const bool one_pass = (int64_t)vg * 256 * 4 >= n;
     if constexpr (sizeof(VT) == 4) {
         if (fused && h->use_coop_update && h->coop_launch) {
             int per = 0;
-            VCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cg_fxrp<float>, 256, 0));
+            if (one_pass) VCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cg_fxrp1<float>, 256, 0));
+            else VCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_cg_fxrp<float>, 256, 0));
             coop = (int64_t)per * h->nsm >= vg;
         }
     }
@@ -2013,8 +2016,9 @@ static int cg_loop(vmc_ctx* h, const void* s_pf, int kind, const VT* b, VT* x, V
                         int* stp = h->d_stop;
                         int mi = max_iter;
                         void* args[] = {&f, &ob, &obp_part, &stp, &mi};
-                        VCK(cudaLaunchCooperativeKernel((const void*)k_cg_fxrp<float>, dim3(vg), dim3(256), args, 0,
-                                                        st));
+                        VCK(cudaLaunchCooperativeKernel(one_pass ? (const void*)k_cg_fxrp1<float>
+                                                                 : (const void*)k_cg_fxrp<float>,
+                                                        dim3(vg), dim3(256), args, 0, st));
                         h->n_launch++;
                         VCK(cudaGetLastError());
                         continue;

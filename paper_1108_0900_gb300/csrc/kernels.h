@@ -201,6 +201,9 @@ template <typename VT> __global__ void __launch_bounds__(256) k_cg_fxr(CgFusedAr
 template <typename VT>
 __global__ void __launch_bounds__(256) k_cg_fxrp(CgFusedArgs<VT> a, const VT* Obar, double* obp_part, int* stop,
                                                  int max_iter);
+template <typename VT>
+__global__ void __launch_bounds__(256) k_cg_fxrp1(CgFusedArgs<VT> a, const VT* Obar, double* obp_part, int* stop,
+                                                 int max_iter);
 __global__ void k_sub(const double* a, const double* b, double* y, int64_t n, double* part);
 __global__ void __launch_bounds__(256) k_vec_sum(const double* x, int64_t n, double* part);
 __global__ void __launch_bounds__(256) k_uncenter(double* out, const double* Obar, const double* obv_part, int nobv,

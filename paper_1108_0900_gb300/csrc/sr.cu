@@ -722,6 +722,88 @@ __global__ void __launch_bounds__(256) k_cg_fxrp(CgFusedArgs<VT> a, const VT* Ob
                   const_cast<double*>(a.pp_part), stop, max_iter);
 }
 
+// The same two updates when the grid covers the vectors in one pass (each
+// thread owns elements i0 + u * stride, u < kVecUnroll): the thread loads x,
+// r, p, the product and Obar once, before the partial sums that give alpha
+// are reduced, and keeps r and p in registers across the grid barrier, so
+// the p update reads nothing from memory.  Same arithmetic, element by
+// element and in every partial sum, as k_cg_fxrp.
+template <typename VT>
+__global__ void __launch_bounds__(256) k_cg_fxrp1(CgFusedArgs<VT> a, const VT* Obar, double* obp_part,
+                                                  int* stop, int max_iter) {
+    if (*a.stop) return;
+    const int64_t n = a.n, stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    VT xv[kVecUnroll], rv[kVecUnroll], pv[kVecUnroll], raw[kVecUnroll], ov[kVecUnroll];
+#pragma unroll
+    for (int u = 0; u < kVecUnroll; ++u) {
+        const int64_t i = i0 + u * stride;
+        const bool in = i < n;
+        xv[u] = in ? a.x[i] : VT(0);
+        rv[u] = in ? a.r[i] : VT(0);
+        pv[u] = in ? a.p[i] : VT(0);
+        raw[u] = !in ? VT(0) : i < a.ncp ? a.corr_raw[i] * a.invC[i] : a.pf_raw[i - a.ncp];
+        ov[u] = in ? Obar[i] : VT(0);
+        if (in && i < a.ncp) a.corr_raw[i] = VT(0);   // ready for the next product's additions
+    }
+    __shared__ double alpha, beta, rrn;
+    if (threadIdx.x < 32) {
+        const double tt = warp_sum_partials(a.tt_part, a.ntt, 0, 1);
+        const double pp = warp_sum_partials(a.pp_part, a.npp, 0, 1);
+        if (threadIdx.x == 0) {
+            const double pAp = tt * a.inv_n + a.shift * pp;
+            alpha = a.scal[CG_RR] / pAp;
+            if (!isfinite(alpha) || pAp <= 0.0) alpha = 0.0;
+        }
+    }
+    __syncthreads();
+    const VT al = (VT)alpha, inv_n = (VT)a.inv_n, sh = (VT)a.shift;
+    VT part = VT(0);
+#pragma unroll
+    for (int u = 0; u < kVecUnroll; ++u) {
+        const int64_t i = i0 + u * stride;
+        if (i < n) {
+            const VT q = raw[u] * inv_n + sh * pv[u];
+            const VT ri = rv[u] - al * q;
+            a.x[i] = xv[u] + al * pv[u];
+            a.r[i] = ri;
+            rv[u] = ri;
+            part += ri * ri;
+        }
+    }
+    double loc[1] = {(double)part};
+    block_reduce_store<1>(loc, a.rr_part);
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.scal[CG_RRP] = a.scal[CG_RR];
+    cooperative_groups::this_grid().sync();
+    if (threadIdx.x < 32) {
+        const double r2 = warp_sum_partials(a.rr_part, (int)gridDim.x, 0, 1);
+        if (threadIdx.x == 0) {
+            rrn = r2;
+            beta = r2 / a.scal[CG_RRP];
+        }
+    }
+    __syncthreads();
+    const VT be = (VT)beta;
+    VT po = VT(0), pp = VT(0);
+#pragma unroll
+    for (int u = 0; u < kVecUnroll; ++u) {
+        const int64_t i = i0 + u * stride;
+        if (i < n) {
+            const VT pi = rv[u] + be * pv[u];
+            const_cast<VT*>(a.p)[i] = pi;
+            po += ov[u] * pi;
+            pp += pi * pi;
+        }
+    }
+    block_reduce_store2((double)po, (double)pp, obp_part, const_cast<double*>(a.pp_part));
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.scal[CG_RR] = rrn;
+        const double it = a.scal[CG_IT] + 1.0;
+        a.scal[CG_IT] = it;
+        if (rrn <= a.scal[CG_TOL2] || !isfinite(rrn) || it >= (double)max_iter) *stop = 1;
+    }
+}
+
 // partial sums of x (FP64)
 __global__ void __launch_bounds__(256) k_vec_sum(const double* x, int64_t n, double* part) {
     double loc[1] = {0.0};
@@ -874,6 +956,7 @@ template __global__ void k_cg_p<float>(const float*, float*, int64_t, const doub
                                        double*, double*, int*, int);
 template __global__ void k_cg_fxr<float>(CgFusedArgs<float>);
 template __global__ void k_cg_fxrp<float>(CgFusedArgs<float>, const float*, double*, int*, int);
+template __global__ void k_cg_fxrp1<float>(CgFusedArgs<float>, const float*, double*, int*, int);
 template __global__ void k_axpy_to64<float>(double*, const float*, double, int64_t);
 template __global__ void k_axpy_to64<double>(double*, const double*, double, int64_t);
 
