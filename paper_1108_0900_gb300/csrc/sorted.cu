@@ -399,6 +399,13 @@ __device__ __forceinline__ void scatter_entry(const float* tv, uint32_t v, float
 // holds its U 16-byte words of a row, and the warp loads its next row while
 // it works on the current one, so a whole row (6 KB at 56 electrons) is
 // always in flight per warp.
+// rows per warp ahead of the current one whose bulk L2 prefetch the gather
+// issues (0: none).  One row ahead, the same row as the register loads that
+// follow: one bulk request per row reaches DRAM ahead of the 13 loads per lane
+// (measured: 1,380 against 1,354 GB/s per product; two rows ahead 1,341,
+// four 1,316)
+constexpr int kGatherAhead = 1;
+
 template <int K, int U>
 __global__ void __launch_bounds__(gather_threads(K)) k_gather_G(SortedArgs a) {
     if (a.stop && *a.stop) return;
@@ -434,6 +441,10 @@ __global__ void __launch_bounds__(gather_threads(K)) k_gather_G(SortedArgs a) {
         }
     }
     for (int64_t s = (int64_t)blockIdx.x * nw + wid; s < a.n_s; s += gstride) {
+        // a bulk L2 request for row s + kGatherAhead gstride (no registers
+        // held) ahead of the per-lane loads of the next row below
+        if (kGatherAhead > 0 && lane == 0 && s + kGatherAhead * gstride < a.n_s)
+            prefetch_l2(a.G + (s + kGatherAhead * gstride) * a.Pst, (uint32_t)(a.Pst * 4));
         uint4 gn[U];
         {
             const int64_t sn = s + gstride;
