@@ -149,12 +149,26 @@ __global__ void __launch_bounds__(512) k_count_G(const uint32_t* G, int64_t Pst,
 }
 
 // per parameter: running offsets over the blocks (in place) and the run
-// length padded to a whole number of kTRun-entry blocks
+// length padded to a whole number of kTRun-entry blocks.  Sixteen blocks'
+// counts are loaded before they are summed, so a thread waits on one round
+// trip per sixteen blocks instead of one per block.
 __global__ void k_scan_blocks(uint32_t* counts, int nblk, int npf, uint32_t* total) {
     const int pq = blockIdx.x * blockDim.x + threadIdx.x;
     if (pq >= npf) return;
+    constexpr int kAhead = 16;
     uint32_t run = 0u;
-    for (int b = 0; b < nblk; ++b) {
+    int b = 0;
+    for (; b + kAhead <= nblk; b += kAhead) {
+        uint32_t c[kAhead];
+#pragma unroll
+        for (int u = 0; u < kAhead; ++u) c[u] = counts[(size_t)(b + u) * npf + pq];
+#pragma unroll
+        for (int u = 0; u < kAhead; ++u) {
+            counts[(size_t)(b + u) * npf + pq] = run;
+            run += c[u];
+        }
+    }
+    for (; b < nblk; ++b) {
         const uint32_t c = counts[(size_t)b * npf + pq];
         counts[(size_t)b * npf + pq] = run;
         run += c;
@@ -239,14 +253,27 @@ __global__ void __launch_bounds__(256) k_rank_T(uint32_t* T, int64_t t_chunk, in
     __shared__ __align__(16) uint32_t buf[8][kTRun];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
-    const int64_t nblk = t_chunk / kTRun;
-    for (int64_t gw = (int64_t)blockIdx.x * 8 + wid; gw < nchunk * nblk; gw += (int64_t)gridDim.x * 8) {
+    const int64_t nblk = t_chunk / kTRun, gstep = (int64_t)gridDim.x * 8;
+    // block gw of the warp's sequence, or -1 past the chunk's runs; the next
+    // block's word is loaded before the current one is sorted
+    auto block_start = [&](int64_t gw) -> int64_t {
+        if (gw >= nchunk * nblk) return -1;
         const int c = (int)(gw / nblk);
         const int64_t e0 = (int64_t)c * t_chunk + (gw - (int64_t)c * nblk) * kTRun;
-        if (e0 >= (int64_t)__ldg(base + (size_t)c * (npf + 1) + npf)) continue;   // past the chunk's runs
+        return e0 < (int64_t)__ldg(base + (size_t)c * (npf + 1) + npf) ? e0 : -1;
+    };
+    int64_t gw = (int64_t)blockIdx.x * 8 + wid;
+    int64_t e_next = block_start(gw);
+    uint4 w_next = e_next >= 0 ? reinterpret_cast<const uint4*>(T + e_next)[lane] : make_uint4(0u, 0u, 0u, 0u);
+    for (; gw < nchunk * nblk; gw += gstep) {
+        const int64_t e0 = e_next;
+        const uint4 w = w_next;
+        e_next = block_start(gw + gstep);
+        if (e_next >= 0) w_next = reinterpret_cast<const uint4*>(T + e_next)[lane];
+        if (e0 < 0) continue;   // past the chunk's runs
+        const int c = (int)(gw / nblk);
         const int ns = (int)min((int64_t)kTChunk, n_s - (int64_t)c * kTChunk);
         uint4* w4 = reinterpret_cast<uint4*>(T + e0);
-        const uint4 w = w4[lane];
         const uint32_t e[4] = {w.x, w.y, w.z, w.w};
         cnt[wid][lane] = 0u;
         __syncwarp();
